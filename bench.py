@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the execution stage (Algorithm 2) on B300.
+
+Workload (default, `--workload serving`): one compiled 16x100 grid CNF
+(grid_cnf(16, 100, seed=1): 1600 variables, 2970 clauses, max-rank 17) and
+a pool of 4096 weight-vector queries w(x) ~ U(0.05, 0.95), w(~x) = 1 - w(x)
+(seed 1), evaluated in scaled FP32 with the queries batched along the query
+index, Q = 256 per wave.  One step = one wave of Q queries through the whole
+path: leaf materialisation, every pairwise contraction, the float64 root.
+
+Reported (one JSON line on rank 0):
+  value      queries/s with weights already resident in HBM (graph replay of
+             wmc_execute_device), max over ranks, whole job;
+  e2e        the same through wmc_execute with host buffers (H2D weights and
+             D2H results inside the timed region);
+  roofline   the streaming contraction kernel (the dominant one): its
+             algorithmic bytes / its CUDA-event time, against the measured
+             HBM copy bandwidth;
+  plain_fp64 the plain one-query-at-a-time FP64 path on the same GPU;
+  latency    p50/p99 of (result ready - scheduled arrival) for a Poisson
+             stream through the continuous-batching server;
+  cpu_baseline the CPU oracle (bucket elimination) on a bounded sample.
+
+`--impl reference` times the CPU oracle itself on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import wmcgen  # noqa: E402
+
+METRIC = "WMC queries/s and p50/p99 latency vs plain FP64 path; % of HBM roofline"
+GRID_H, GRID_W, GRID_SEED = 16, 100, 1
+POOL = 4096
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload():
+    cnf = wmcgen.grid_cnf(GRID_H, GRID_W, GRID_SEED)
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, POOL, seed=1, lo=0.05, hi=0.95)
+    return cnf, wq, wnq
+
+
+def config(Q):
+    return {"workload": f"serving: {GRID_H}x{GRID_W} grid CNF (seed {GRID_SEED}), pool of {POOL} "
+                        f"weight-vector queries w~U(0.05,0.95), waves of Q={Q}",
+            "Q": Q, "precision": "scaled fp32 (fp64 root)",
+            "l2": "inputs larger than L2: each wave streams 2^17 x Q float32 frontier tensors "
+                  "(128 MiB at Q=256) through ~1.5k contractions"}
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def cpu_baseline(cnf, wq, wnq, budget_s=15.0):
+    """The oracle (bucket elimination, long double) per query on the host
+    cores, for as many pool queries as fit in budget_s (at least one)."""
+    import oracle
+    col = [i * GRID_W + j + 1 for j in range(GRID_W) for i in range(GRID_H)]
+    vals = []
+    t0 = time.perf_counter()
+    i = 0
+    while i == 0 or (time.perf_counter() - t0 < budget_s and i < 64):
+        vals.append(oracle.bucket_elim(cnf, wq[i], wnq[i], order=col))
+        i += 1
+    dt = time.perf_counter() - t0
+    return {"value": i / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{i} pool queries of the 16x100 grid, long-double bucket elimination, "
+                      f"{dt:.1f} s"}, vals
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle timed on the same workload."""
+    if rank != 0:
+        return
+    cnf, wq, wnq = workload()
+    import oracle
+    col = [i * GRID_W + j + 1 for j in range(GRID_W) for i in range(GRID_H)]
+    for s in range(args.warmup):
+        oracle.bucket_elim(cnf, wq[s], wnq[s], order=col)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.bucket_elim(cnf, wq[(args.warmup + s) % POOL], wnq[(args.warmup + s) % POOL], order=col)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f80 (long double)", "data": "synthetic",
+            "config": {"workload": config(args.Q)["workload"], "step": "one query"},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"{args.steps} pool queries, one per step"},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2006_15512_b300 as w
+    from oracle import Big
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    Q = args.Q
+    cnf, wq, wnq = workload()
+    net = w.Network.from_cnf(cnf)
+    plan = w.Plan(net, precision=w.WMC_SCALED_FP32)
+    info = plan.info(Q)
+    n = cnf.n_vars
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    # device-resident query pool and outputs
+    d_wp = torch.from_numpy(wq).to(dev)
+    d_wn = torch.from_numpy(wnq).to(dev)
+    ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev)
+    mant = torch.empty(Q, dtype=torch.float64, device=dev)
+    ex = torch.empty(Q, dtype=torch.int64, device=dev)
+    fl = torch.empty(Q, dtype=torch.int32, device=dev)
+    n_waves = POOL // Q
+
+    def wave(i):
+        off = (i % n_waves) * Q
+        plan.execute_device(Q, d_wp[off:off + Q], d_wn[off:off + Q], ws, mant, ex, fl, stream=sp)
+
+    for i in range(args.warmup):
+        wave(i)
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident inputs)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = w.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev.index) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            wave(args.warmup + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = w.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t)
+    value = world * args.steps * Q / (t_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers
+    host_wp, host_wn = np.ascontiguousarray(wq), np.ascontiguousarray(wnq)
+    plan.execute(host_wp[:Q], host_wn[:Q])  # warm the host-path workspace
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_res = []
+    for i in range(args.steps):
+        off = ((args.warmup + i) % n_waves) * Q
+        e2e_res = plan.execute(host_wp[off:off + Q], host_wn[off:off + Q])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t)
+    e2e = {"value": world * args.steps * Q / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": 2 * Q * n * 8, "d2h_bytes_per_step": Q * (8 + 8 + 4)}
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the streaming contraction kernel (one eager walk)
+    import ctypes
+    nmax = 1 << 16
+    node_ms = (ctypes.c_float * nmax)()
+    kinds = (ctypes.c_int32 * nmax)()
+    nbytes = (ctypes.c_double * nmax)()
+    nl = ctypes.c_int64()
+    w.check(w.wmc_profile_walk(plan.handle, Q, ctypes.c_void_p(d_wp.data_ptr()),
+                               ctypes.c_void_p(d_wn.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                               info.workspace_bytes, ctypes.c_void_p(mant.data_ptr()),
+                               ctypes.c_void_p(ex.data_ptr()), ctypes.c_void_p(fl.data_ptr()),
+                               ctypes.c_void_p(sp), nmax, node_ms, kinds, nbytes, ctypes.byref(nl)),
+            "wmc_profile_walk")
+    L = min(nl.value, nmax)
+    k_ms = np.array([node_ms[i] for i in range(L)])
+    k_kind = np.array([kinds[i] for i in range(L)])
+    k_bytes = np.array([nbytes[i] for i in range(L)])
+    hbm, src = peaks()
+    sel = k_kind == 1
+    walk_ms = float(k_ms.sum())
+    achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "kernel": "k2_stream<float,4,*> (streaming pairwise contraction)",
+                "launches": int(sel.sum()), "share_of_walk": float(k_ms[sel].sum() / walk_ms),
+                "avg_launch_us": float(k_ms[sel].mean() * 1e3) if sel.any() else None,
+                "bytes_per_launch": float(k_bytes[sel].mean()) if sel.any() else None,
+                "generic_k1_share": float(k_ms[k_kind == 0].sum() / walk_ms),
+                "eager_walk_ms": walk_ms}
+
+    # ---- plain one-query-at-a-time FP64 path on the same GPU
+    plan64 = w.Plan(net, precision=w.WMC_FP64)
+    info64 = plan64.info(1)
+    ws64 = torch.empty(info64.workspace_bytes, dtype=torch.uint8, device=dev)
+    for i in range(3):
+        plan64.execute_device(1, d_wp[i:i + 1], d_wn[i:i + 1], ws64, mant, ex, fl, stream=sp)
+    torch.cuda.synchronize()
+    n_plain = args.plain_queries
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n_plain):
+        plan64.execute_device(1, d_wp[i:i + 1], d_wn[i:i + 1], ws64, mant, ex, fl, stream=sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_qps = n_plain / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- Poisson serving run (continuous batching)
+    latency = None
+    if args.rate > 0:
+        srv = w.Server(plan, max_batch=Q, max_waves=args.waves)
+        # warm every power-of-two wave size's graph
+        for q in [1 << k for k in range(int(math.log2(Q)) + 1)]:
+            ts = [srv.submit(wq[j], wnq[j]) for j in range(q)]
+            for t in ts:
+                srv.wait(t)
+        arr = wmcgen.poisson_arrivals(args.n_queries, args.rate, seed=2)
+        tickets = []
+        t0 = time.monotonic()
+        for j in range(args.n_queries):
+            target = t0 + arr[j]
+            d = target - time.monotonic()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(wq[j % POOL], wnq[j % POOL]))
+        st0 = srv.stats()
+        # completion times are stamped by the server (CLOCK_MONOTONIC), so
+        # collecting them late does not change them
+        done = srv.collect_done_ns(tickets, timeout_s=300)
+        st = srv.stats()
+        st.waves -= st0.waves * 0  # stats are cumulative incl. warm-up
+        srv.close()
+        lat_ms = np.array([(done[j] / 1e9 - (t0 + arr[j])) * 1e3 for j in range(len(tickets))])
+        span = max(done) / 1e9 - t0
+        latency = {"rate_qps": args.rate, "n_queries": args.n_queries,
+                   "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                   "mean_ms": float(lat_ms.mean()), "served_qps": args.n_queries / span,
+                   "waves": int(st.waves), "mean_wave_q": float(st.mean_wave_q)}
+    # ---- accuracy on the sampled queries + CPU baseline
+    cpu, oracle_vals = (None, [])
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, oracle_vals = cpu_baseline(cnf, wq, wnq)
+    max_err = None
+    if oracle_vals:
+        res = plan.execute(host_wp[:Q], host_wn[:Q])
+        max_err = max(Big(res[i].mant, res[i].exp2).rel_diff(oracle_vals[i]) for i in range(len(oracle_vals)))
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config(Q), "e2e": e2e,
+            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "plain_fp64": {"value": plain_qps, "unit": "queries/s", "queries": n_plain,
+                           "speedup_of_batched": value / world / plain_qps},
+            "latency": latency,
+            "accuracy": {"max_rel_err_vs_oracle": max_err, "n": len(oracle_vals),
+                         "stated_bound": e2e_res[0].rel_err_bound if e2e_res else None},
+            "plan": {"max_rank": info.max_rank, "n_nodes": info.n_nodes,
+                     "workspace_MiB": info.workspace_bytes / 2 ** 20,
+                     "algorithmic_GB_per_wave": info.algorithmic_bytes / 1e9}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--Q", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--n-queries", type=int, default=4096)
+    ap.add_argument("--waves", type=int, default=2)
+    ap.add_argument("--plain-queries", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

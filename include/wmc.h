@@ -1,0 +1,276 @@
+/*
+ * wmc.h -- C ABI of the B300 execution stage for tensor-network weighted
+ * model counting (Dudek & Vardi, "Parallel Weighted Model Counting with
+ * Tensor Networks").
+ *
+ * The library reduces a weighted CNF to a tensor network (Thm 3.2), plans a
+ * contraction tree with a portfolio of elimination orders (Sec. 3.3), and
+ * executes the tree on one GPU as a post-order walk of pairwise
+ * contractions (Algorithm 2), each a hand-written sm_103a CUDA kernel.
+ *
+ * Conventions for every entry point
+ *   - Every call returns an int status (WMC_OK = 0 or a negative WMC_E*
+ *     code, or WMC_PENDING = 1 from wmc_poll).  Nothing throws across the
+ *     ABI.  wmc_last_error() returns a thread-local message for the last
+ *     failing call on the calling thread.
+ *   - The library owns every handle it returns and copies every input
+ *     array it is given; callers may free their arrays after the call.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device.  Streams are cudaStream_t passed
+ *     as void* (NULL = the legacy default stream).
+ *   - Weights are float64.  w_pos[v] = W(x_{v+1}, 1) and w_neg[v] =
+ *     W(x_{v+1}, 0) (Def. 2.1).  Evidence is expressed as a zero weight.
+ *   - Query batches are query-major: element [q * n_vars + v].
+ *   - Results are wmc_result records: value = mant * 2^exp2, so counts far
+ *     outside the float64 range (grid formulas reach 1e-956) are exact in
+ *     range.
+ */
+#ifndef WMC_B300_H
+#define WMC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define WMC_OK 0
+#define WMC_PENDING 1           /* wmc_poll: the query has not finished      */
+#define WMC_EINVAL (-1)         /* malformed argument (bad literal, size ...) */
+#define WMC_ENOMEM (-2)         /* host or device allocation failed          */
+#define WMC_EPLAN_TOO_BIG (-3)  /* plan exceeds max_rank_cap / memory budget */
+#define WMC_ECUDA (-4)          /* a CUDA runtime call failed                */
+#define WMC_ETIMEOUT (-5)       /* a bounded wait gave up                    */
+#define WMC_EUNKNOWN_TICKET (-6)/* wmc_poll: ticket never issued or consumed */
+#define WMC_ESHUTDOWN (-7)      /* server is shutting down                   */
+
+/* Precision of the contraction path. */
+#define WMC_FP64 0          /* float64 mantissas, per-tensor pow2 exponents  */
+#define WMC_SCALED_FP32 1   /* float32 mantissas with float32 accumulation,
+                               per-(tensor, query) pow2 exponents; the root
+                               contraction accumulates in float64          */
+
+/* Elimination-order heuristics for wmc_plan. */
+#define WMC_ORDER_BEST 0       /* portfolio below, keep the lowest max-rank */
+#define WMC_ORDER_MINFILL 1    /* min-fill, ties: degree then lowest id     */
+#define WMC_ORDER_MINDEGREE 2  /* min-degree, ties: lowest id               */
+#define WMC_ORDER_SWEEP 3      /* level sweep of a multi-source BFS         */
+#define WMC_ORDER_GIVEN 4      /* caller-supplied order (wmc_plan_opts.order) */
+
+/* wmc_result.flags */
+#define WMC_FLAG_EXACT_INT 0x1u      /* every weight was 1 and the count is
+                                        below 2^53: mant*2^exp2 is exact     */
+#define WMC_FLAG_FP32_FLUSH 0x2u     /* a nonzero float32 term underflowed to
+                                        a subnormal or zero inside a tensor   */
+#define WMC_FLAG_NO_BOUND 0x4u       /* a weight was negative: rel_err_bound
+                                        does not apply                        */
+
+typedef struct wmc_network wmc_network_t;
+typedef struct wmc_plan wmc_plan_t;
+typedef struct wmc_server wmc_server_t;
+
+typedef struct {
+  double mant;          /* value = mant * 2^exp2, |mant| in [0.5, 1) or 0   */
+  int64_t exp2;
+  double log10;         /* log10(|value|), -inf for 0                        */
+  uint32_t flags;       /* WMC_FLAG_*                                        */
+  uint32_t reserved;
+  double rel_err_bound; /* a-priori relative error bound for nonnegative
+                           weights: gamma_d = d*u/(1-d*u), u the unit
+                           roundoff, d the most roundings on any path from
+                           a leaf to the root                               */
+} wmc_result;
+
+/* Reduction: Thm 3.2.  Builds the network {A_x} u {B_C} of a CNF with n_vars
+ * variables and n_clauses clauses.  lits holds DIMACS literals (+v / -v,
+ * 1 <= v <= n_vars) and clause i is lits[clause_off[i] .. clause_off[i+1]).
+ * Repeated literals are merged and tautological clauses dropped (neither
+ * changes W); an empty clause makes W = 0.  w_pos / w_neg (host, n_vars
+ * each) are the default weights used by wmc_execute when it is given no
+ * weights; they may be NULL (all weights 1).  The COPY tensors A_x are kept
+ * in hyperedge form: each variable is one index shared by every tensor that
+ * mentions it, and A_x becomes the weight vector [W(x,0), W(x,1)].
+ * Errors: WMC_EINVAL for a literal 0 or |lit| > n_vars, negative sizes or a
+ * non-monotone clause_off; WMC_ENOMEM. */
+int wmc_network_create(int32_t n_vars, int64_t n_clauses, const int32_t *lits,
+                       const int64_t *clause_off, const double *w_pos,
+                       const double *w_neg, wmc_network_t **out);
+void wmc_network_destroy(wmc_network_t *net);
+
+typedef struct {
+  int64_t n_vars;
+  int64_t n_clauses_kept;   /* after dropping tautologies                   */
+  int64_t n_tensors_strict; /* |N| of Thm 3.2: n_vars + clauses kept        */
+  int64_t n_indices_strict; /* |I| of Thm 3.2: sum of distinct vars/clause  */
+  int64_t max_clause_rank;
+  int32_t has_empty_clause;
+  int32_t reserved;
+} wmc_network_info_t;
+int wmc_network_info(const wmc_network_t *net, wmc_network_info_t *out);
+
+typedef struct {
+  int32_t precision;        /* WMC_FP64 or WMC_SCALED_FP32                  */
+  int32_t ordering;         /* WMC_ORDER_*                                  */
+  int32_t max_rank_cap;     /* reject plans whose largest tensor (in index
+                               count, before the query index) exceeds this;
+                               0 = 30                                       */
+  int32_t reserved;
+  int64_t mem_budget_bytes; /* reject plans whose workspace at Q = 1
+                               exceeds this; 0 = no limit                   */
+  const int32_t *order;     /* WMC_ORDER_GIVEN: n_vars 1-based ids (host,
+                               copied)                                      */
+} wmc_plan_opts;
+
+/* Planning: Sec. 3.3.  Builds a contraction tree by bucket elimination
+ * along an elimination order of the primal graph (each bucket contracted
+ * smallest-first, an index summed at its last appearance), then assigns
+ * every intermediate tensor's index order so the dominant contractions read
+ * and write contiguously.  Host only.  opts may be NULL (defaults).
+ * Errors: WMC_EINVAL, WMC_EPLAN_TOO_BIG, WMC_ENOMEM. */
+int wmc_plan(const wmc_network_t *net, const wmc_plan_opts *opts,
+             wmc_plan_t **out);
+void wmc_plan_destroy(wmc_plan_t *plan);
+
+typedef struct {
+  int32_t max_rank;         /* largest tensor rank (index count)            */
+  int32_t max_node_rank;    /* largest |I(A) u I(B)| over contractions      */
+  int64_t n_leaves;
+  int64_t n_nodes;          /* pairwise contractions                        */
+  int64_t workspace_bytes;  /* device workspace wmc_execute_device needs
+                               for this Q                                  */
+  int64_t peak_tensor_bytes;/* the arena part of workspace_bytes           */
+  double algorithmic_bytes; /* sum over nodes of |A|+|B|+|C| element bytes */
+  double flops;             /* sum over nodes of 2 * |iteration space|      */
+  int32_t precision;
+  int32_t ordering_used;
+  int32_t max_path_roundings; /* d of wmc_result.rel_err_bound            */
+  int32_t reserved;
+} wmc_plan_info_t;
+/* Q >= 1 is the number of queries batched along the extra query index. */
+int wmc_plan_info(const wmc_plan_t *plan, int32_t Q, wmc_plan_info_t *out);
+
+/* Node list of the contraction tree, for inspection and host-side tests.
+ * Tensor ids: leaves first (0 .. n_leaves-1), then node outputs in
+ * post-order.  For node i: children ids and the index labels (0-based
+ * variable ids) of the output in bit order (bit j of the linear offset is
+ * labels[j]).  For leaf ids: kind 0 = clause tensor (fals = the falsifying
+ * assignment bits, the tensor is 1 elsewhere), 1 = weight vector of
+ * labels[0], 2 = the scalar 1.  `labels` must hold 64 entries. */
+int wmc_plan_node(const wmc_plan_t *plan, int64_t node, int64_t *left,
+                  int64_t *right, int32_t *n_labels, int32_t *labels);
+int wmc_plan_leaf(const wmc_plan_t *plan, int64_t leaf, int32_t *kind,
+                  int32_t *n_labels, int32_t *labels, uint64_t *fals);
+
+/* Execution: Algorithm 2 on the GPU for Q queries at once.  Host buffers:
+ * w_pos_q / w_neg_q are [Q][n_vars] float64 (NULL = the network's default
+ * weights for every query); out is [Q] wmc_result.  Copies the weights to
+ * the device, runs the captured CUDA graph of the plan on `stream`, copies
+ * the Q results back and synchronises the stream.  Device memory is a
+ * workspace cached inside the plan (allocated on first use for each Q).
+ * Errors: WMC_EINVAL (Q < 1 or Q > 4096), WMC_ENOMEM, WMC_ECUDA. */
+int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q,
+                const double *w_neg_q, void *stream, wmc_result *out);
+
+/* Execution with device-resident inputs and outputs, asynchronous on
+ * `stream`.  d_w_pos / d_w_neg: device [Q][n_vars] float64.  d_workspace:
+ * device memory of at least wmc_plan_info(Q).workspace_bytes, 256-byte
+ * aligned, owned by the caller and not used by anything else until the
+ * stream passes this call.  Results: d_mant[Q] (float64) and d_exp2[Q]
+ * (int64) with value = d_mant[q] * 2^d_exp2[q] (d_mant not normalised),
+ * d_flags[Q] (uint32, WMC_FLAG_FP32_FLUSH).  Allocates nothing.
+ * Errors: WMC_EINVAL (workspace too small or misaligned), WMC_ECUDA. */
+int wmc_execute_device(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
+                       const double *d_w_neg, void *d_workspace,
+                       size_t workspace_bytes, double *d_mant,
+                       int64_t *d_exp2, uint32_t *d_flags, void *stream);
+
+/* One pairwise contraction C = A . B (Eq. (1) on the network {A, B}; the
+ * matrix-multiplication view of Sec. 4.2), on device memory, asynchronous on
+ * `stream`.  Bit j of a tensor's linear offset is index labels_x[j];
+ * every index has extent 2.  Indices of C must appear in A or B; indices of
+ * A or B absent from C are summed; an index in A, B and C is a batch index.
+ * precision WMC_FP64: a, b, c are float64.  WMC_SCALED_FP32: a, b, c are
+ * float32 mantissas; the true tensors are a * 2^exp_a[0] etc.: exp_a and
+ * exp_b (device int64[1]) are read, exp_c (device int64[1]) is written,
+ * and c is normalised so that max|c| lies in [1, 2).  For WMC_FP64 the
+ * exp pointers may be NULL.  Ranks <= 31, at most 24 summed indices.
+ * Errors: WMC_EINVAL, WMC_ECUDA. */
+int wmc_contract_pair(int32_t precision, int32_t rank_a,
+                      const int32_t *labels_a, const void *a, int32_t rank_b,
+                      const int32_t *labels_b, const void *b, int32_t rank_c,
+                      const int32_t *labels_c, void *c, const int64_t *exp_a,
+                      const int64_t *exp_b, int64_t *exp_c, void *stream);
+
+/* Converts a float64 device tensor of n elements to a scaled float32 one:
+ * out = x * 2^-E rounded to float32 and exp_out[0] = E, with E chosen so
+ * that max|out| lies in [1, 2).  Asynchronous on `stream`. */
+int wmc_to_scaled_fp32(const double *x, int64_t n, float *out,
+                       int64_t *exp_out, void *stream);
+
+/* ------------------------------------------------------------- serving */
+typedef struct {
+  int32_t precision;        /* WMC_FP64 or WMC_SCALED_FP32 (of the plan)   */
+  int32_t max_batch;        /* largest Q of one wave (power of 2, <= 1024) */
+  int32_t max_waves;        /* waves in flight at once (each its own stream
+                               and workspace)                               */
+  int32_t reserved;
+  int64_t arena_bytes;      /* device memory for all wave workspaces; a wave
+                               of Q queries is admitted only while its
+                               workspace fits; 0 = max_waves * ws(max_batch) */
+  int64_t max_wave_wait_us; /* how long the batcher waits for more queries
+                               before launching a partial wave              */
+} wmc_server_opts;
+
+/* Continuous-batching server over one plan.  Queries submitted while waves
+ * are running are gathered into the next wave as soon as a wave slot and
+ * its workspace are free; waves run on separate streams and overlap on the
+ * device.  Every query's result is independent of the wave it lands in. */
+int wmc_server_create(wmc_plan_t *plan, const wmc_server_opts *opts,
+                      wmc_server_t **out);
+/* Copies n_vars weights each (host); returns a ticket (never reused). */
+int wmc_submit(wmc_server_t *srv, const double *w_pos, const double *w_neg,
+               uint64_t *ticket);
+/* WMC_OK (result written, ticket retired), WMC_PENDING, or an error. */
+int wmc_poll(wmc_server_t *srv, uint64_t ticket, wmc_result *out);
+/* As wmc_poll; *done_ns (may be NULL) receives the CLOCK_MONOTONIC time in
+ * nanoseconds at which the server published the result. */
+int wmc_poll_ex(wmc_server_t *srv, uint64_t ticket, wmc_result *out,
+                int64_t *done_ns);
+/* Blocks until the ticket completes or timeout_us elapses (WMC_ETIMEOUT). */
+int wmc_wait(wmc_server_t *srv, uint64_t ticket, int64_t timeout_us,
+             wmc_result *out);
+typedef struct {
+  int64_t submitted, completed, waves, failed_waves;
+  double mean_wave_q;
+} wmc_server_stats_t;
+int wmc_server_stats(wmc_server_t *srv, wmc_server_stats_t *out);
+void wmc_server_destroy(wmc_server_t *srv);
+
+/* Measurement: runs the walk of wmc_execute_device once WITHOUT the graph,
+ * with a CUDA event after every launch, and synchronises `stream`.  For
+ * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
+ * kind[i] = 0 generic contraction, 1 streaming contraction, 2 leaf or
+ * bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
+ * must move (|A| + |B| + |C| in its element type).  Returns the launch
+ * count through *n_launches.  Same arguments and errors as
+ * wmc_execute_device; creates and destroys its own events. */
+int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
+                     const double *d_w_neg, void *d_workspace,
+                     size_t workspace_bytes, double *d_mant, int64_t *d_exp2,
+                     uint32_t *d_flags, void *stream, int64_t n_max,
+                     float *node_ms, int32_t *kind, double *alg_bytes,
+                     int64_t *n_launches);
+
+/* ------------------------------------------------------------- misc */
+const char *wmc_last_error(void);
+/* Number of kernels this library launched since load (for accounting). */
+int64_t wmc_kernel_launch_count(void);
+/* Test hook: make the next n device allocations fail with WMC_ENOMEM. */
+void wmc_debug_fail_next_allocs(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WMC_B300_H */

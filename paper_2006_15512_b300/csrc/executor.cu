@@ -1,0 +1,966 @@
+// Execution stage (Algorithm 2) on one GPU.
+//
+// The recursive Execute(N, T) of Algorithm 2 becomes an iterative
+// post-order walk over the plan's node array.  For a query batch size Q the
+// walk is laid out once (tensor arena offsets with first-fit reuse of
+// freed children, per-node kernel choice and parameters) and captured into
+// a CUDA graph per workspace, so one wmc_execute is one H2D copy of the
+// inputs, one graph launch and one D2H copy of the results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+using namespace wmc;
+using wmc::dev::ClauseLeaf;
+using wmc::dev::IoDesc;
+using wmc::dev::K1Params;
+using wmc::dev::K2Params;
+
+struct wmc_plan : public Plan {};
+struct wmc_network;
+namespace wmc { const Network &network_of(const wmc_network_t *n); }
+
+static std::atomic<int64_t> g_launches{0};
+static std::atomic<int32_t> g_fail_allocs{0};
+
+extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
+extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
+
+#define CUDA_TRY(x)                                                              \
+  do {                                                                           \
+    cudaError_t _e = (x);                                                        \
+    if (_e != cudaSuccess) {                                                     \
+      set_error("%s failed: %s (%s:%d)", #x, cudaGetErrorString(_e), __FILE__,   \
+                __LINE__);                                                       \
+      return WMC_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+static int dev_alloc(void **p, size_t bytes) {
+  if (g_fail_allocs.load() > 0) {
+    g_fail_allocs.fetch_sub(1);
+    set_error("injected allocation failure (%zu bytes)", bytes);
+    return WMC_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 256);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return WMC_ENOMEM;
+  }
+  return WMC_OK;
+}
+
+namespace {
+
+constexpr int64_t kAlign = 256;
+inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+enum Kind { L_K1, L_K2, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Ty { TF = 0, TD = 1 };
+
+struct Launch {
+  Kind kind;
+  int ti = TF, ta = TF, to = TF;  // K1 types; K2 uses ti
+  int v = 1, kmax = 1, fmax = 1;  // K2 template choice
+  int64_t blocks = 1;
+  K1Params k1;
+  K2Params k2;
+  // relative byte offsets (patched with the workspace base at capture)
+  int64_t off_a = -1, off_b = -1, off_c = -1;
+  int64_t meta_a = -1, meta_b = -1, meta_c = -1;  // slot indices
+  int64_t one_off = -1, one_meta = -1;
+  int64_t memset_off = 0, memset_bytes = 0;
+  double alg_bytes = 0;  // contraction: |A| + |B| + |C| bytes
+};
+
+}  // namespace
+
+namespace wmc {
+
+struct ExecState {
+  int32_t Q = 1, m = 0;
+  bool f64 = false;
+  std::vector<int64_t> t_off;   // byte offset of tensor data in the workspace
+  std::vector<int64_t> t_meta;  // first metadata slot
+  std::vector<int32_t> t_qc;
+  std::vector<uint8_t> t_dbl;
+  int64_t off_io = 0, off_flags = 0, off_exp = 0, off_max = 0, n_slots = 0;
+  int64_t arena_bytes = 0, ws_bytes = 0;
+  double alg_bytes = 0, flops = 0;
+  int32_t max_roundings = 0;
+  std::vector<Launch> launches;
+  int64_t kernels_per_run = 0;
+  // constant tables (device, owned)
+  std::vector<ClauseLeaf> h_clause;
+  std::vector<int64_t> h_first, h_woff, h_wmeta;
+  int64_t n_clause_entries = 0;
+  ClauseLeaf *d_clause = nullptr;
+  int64_t *d_first = nullptr, *d_woff = nullptr, *d_wmeta = nullptr;
+  bool dev_ready = false;
+  std::map<uintptr_t, cudaGraphExec_t> graphs;
+  cudaStream_t capture_stream = nullptr;
+  // resources of the host-pointer path
+  void *own_ws = nullptr;
+  double *d_w = nullptr;          // [2][Q][n_vars]
+  double *d_res_mant = nullptr;   // [Q]
+  int64_t *d_res_exp = nullptr;
+  uint32_t *d_res_flags = nullptr;
+  double *h_res_mant = nullptr;   // pinned
+  int64_t *h_res_exp = nullptr;
+  uint32_t *h_res_flags = nullptr;
+  std::mutex run_mu;    // the owned workspace of the host-pointer path
+  std::mutex graph_mu;  // graphs map
+
+  ~ExecState() {
+    for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    cudaFree(d_clause); cudaFree(d_first); cudaFree(d_woff); cudaFree(d_wmeta);
+    cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant); cudaFree(d_res_exp); cudaFree(d_res_flags);
+    cudaFreeHost(h_res_mant); cudaFreeHost(h_res_exp); cudaFreeHost(h_res_flags);
+  }
+};
+
+Plan::~Plan() {}
+void destroy_exec_state(ExecState *st) { delete st; }
+
+}  // namespace wmc
+
+// ------------------------------------------------------------ layout
+
+namespace {
+
+// Full label list of a tensor at batch size 2^m: the m query bits occupy
+// the lowest positions (labels -1 .. -m) of every weight-dependent tensor.
+std::vector<int32_t> full_labels(const TensorInfo &t, int32_t m) {
+  std::vector<int32_t> L;
+  if (t.has_q)
+    for (int32_t i = 0; i < m; ++i) L.push_back(-1 - i);
+  L.insert(L.end(), t.labels.begin(), t.labels.end());
+  return L;
+}
+
+int pos_of(const std::vector<int32_t> &L, int32_t v) {
+  for (size_t i = 0; i < L.size(); ++i)
+    if (L[i] == v) return (int)i;
+  return -1;
+}
+
+struct FirstFit {
+  std::map<int64_t, int64_t> free_;  // offset -> size
+  int64_t top = 0;
+  int64_t alloc(int64_t bytes) {
+    bytes = align_up(std::max<int64_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        int64_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        return off;
+      }
+    }
+    // extend the top (merging a free block that ends at the top)
+    if (!free_.empty()) {
+      auto last = std::prev(free_.end());
+      if (last->first + last->second == top) {
+        int64_t off = last->first;
+        free_.erase(last);
+        top = off + bytes;
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += bytes;
+    return off;
+  }
+  void release(int64_t off, int64_t bytes) {
+    bytes = align_up(std::max<int64_t>(bytes, 1));
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+// Chooses K2 (streaming, P the operand whose kept indices stay in order)
+// when its structural conditions hold, else K1.
+bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
+            const std::vector<int32_t> &LC, bool f64, K2Params &p, int &vmax, int &kmax,
+            int &fmax) {
+  std::vector<int32_t> keptP, cP, freeS, summed;
+  for (int32_t l : LP) if (pos_of(LC, l) >= 0) keptP.push_back(l);
+  for (int32_t l : LC) if (pos_of(LP, l) >= 0) cP.push_back(l);
+  if (keptP != cP) return false;
+  for (int32_t l : LS) if (pos_of(LC, l) >= 0 && pos_of(LP, l) < 0) freeS.push_back(l);
+  for (int32_t l : LP) if (pos_of(LC, l) < 0) summed.push_back(l);
+  for (int32_t l : LS) if (pos_of(LC, l) < 0 && pos_of(LP, l) < 0) summed.push_back(l);
+  // one summation order for every kernel and batch size: ascending label
+  std::sort(summed.begin(), summed.end());
+  const int k = (int)summed.size(), f = (int)freeS.size();
+  if (k > 3 || f > 3 || LS.size() > 16) return false;
+  std::memset(&p, 0, sizeof(p));
+  p.k = k;
+  p.f = f;
+  std::vector<int> insA, insC;
+  for (int32_t l : summed) { int q = pos_of(LP, l); if (q >= 0) insA.push_back(q); }
+  for (int32_t l : freeS) insC.push_back(pos_of(LC, l));
+  std::sort(insA.begin(), insA.end());
+  std::sort(insC.begin(), insC.end());
+  const int want_v = f64 ? 1 : 2;
+  int vbits = want_v;
+  const int rC = (int)LC.size();
+  if (rC - f < vbits) vbits = 0;
+  for (int q : insA) if (q < vbits) vbits = 0;
+  for (int q : insC) if (q < vbits) vbits = 0;
+  p.vbits = vbits;
+  p.log2_nu = rC - f - vbits;
+  p.n_insA = (int)insA.size();
+  p.n_insC = (int)insC.size();
+  for (size_t i = 0; i < insA.size(); ++i) p.insA[i] = (int8_t)insA[i];
+  for (size_t i = 0; i < insC.size(); ++i) p.insC[i] = (int8_t)insC[i];
+  int nbb = 0;
+  for (size_t j = 0; j < LS.size(); ++j) {
+    int32_t l = LS[j];
+    int pc = pos_of(LC, l), pp = pos_of(LP, l);
+    if (pc < 0 || pp < 0) continue;  // not a batch index
+    if (pc < vbits) {
+      for (int e = 0; e < (1 << vbits); ++e)
+        if ((e >> pc) & 1) p.dBv[e] |= 1u << j;
+    } else {
+      p.bbC[nbb] = (int8_t)pc;
+      p.bbB[nbb] = (int8_t)j;
+      ++nbb;
+    }
+  }
+  p.nbb = nbb;
+  for (int s = 0; s < (1 << k); ++s) {
+    uint32_t da = 0, db = 0;
+    for (int i = 0; i < k; ++i) {
+      if (!((s >> i) & 1)) continue;
+      int qa = pos_of(LP, summed[i]), qb = pos_of(LS, summed[i]);
+      if (qa >= 0) da |= 1u << qa;
+      if (qb >= 0) db |= 1u << qb;
+    }
+    p.dA[s] = da;
+    p.dBs[s] = db;
+  }
+  for (int ff = 0; ff < (1 << f); ++ff) {
+    uint32_t db = 0, dc = 0;
+    for (int i = 0; i < f; ++i) {
+      if (!((ff >> i) & 1)) continue;
+      db |= 1u << pos_of(LS, freeS[i]);
+      dc |= 1u << pos_of(LC, freeS[i]);
+    }
+    p.dBf[ff] = db;
+    p.dC[ff] = dc;
+  }
+  vmax = 1 << vbits;
+  kmax = std::max(k, f) <= 1 ? 1 : (std::max(k, f) <= 2 ? 2 : 3);
+  fmax = kmax;
+  return true;
+}
+
+void fill_k1(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
+             const std::vector<int32_t> &LC, K1Params &p) {
+  std::memset(&p, 0, sizeof(p));
+  std::vector<int32_t> summed;
+  for (int32_t l : LA) if (pos_of(LC, l) < 0) summed.push_back(l);
+  for (int32_t l : LB) if (pos_of(LC, l) < 0 && pos_of(LA, l) < 0) summed.push_back(l);
+  std::sort(summed.begin(), summed.end());
+  p.rC = (int32_t)LC.size();
+  p.k = (int32_t)summed.size();
+  for (int j = 0; j < 32; ++j) { p.posA[j] = -1; p.posB[j] = -1; }
+  for (int j = 0; j < 24; ++j) { p.sposA[j] = -1; p.sposB[j] = -1; }
+  for (size_t j = 0; j < LC.size(); ++j) {
+    p.posA[j] = (int8_t)pos_of(LA, LC[j]);
+    p.posB[j] = (int8_t)pos_of(LB, LC[j]);
+  }
+  for (size_t i = 0; i < summed.size(); ++i) {
+    p.sposA[i] = (int8_t)pos_of(LA, summed[i]);
+    p.sposB[i] = (int8_t)pos_of(LB, summed[i]);
+  }
+}
+
+int64_t grid_for(uint64_t work) {
+  const int64_t max_blocks = 148 * 8;
+  uint64_t b = (work + dev::kThreads - 1) / dev::kThreads;
+  if (b < 1) b = 1;
+  return (int64_t)std::min<uint64_t>(b, (uint64_t)max_blocks);
+}
+
+}  // namespace
+
+// Builds the host-side layout for batch size Q (no device work).
+static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
+  st.Q = Q;
+  int32_t m = 0;
+  while ((1 << m) < Q) ++m;
+  st.m = m;
+  st.f64 = plan.precision == WMC_FP64;
+  const size_t nt = plan.tensors.size();
+  const int64_t root = plan.nodes.back().c;
+  st.t_off.assign(nt, 0);
+  st.t_meta.assign(nt, 0);
+  st.t_qc.assign(nt, 1);
+  st.t_dbl.assign(nt, st.f64 ? 1 : 0);
+  st.t_dbl[(size_t)root] = 1;
+  std::vector<int64_t> bytes(nt);
+  int64_t slots = 0;
+  for (size_t i = 0; i < nt; ++i) {
+    const TensorInfo &t = plan.tensors[i];
+    int64_t r = (int64_t)t.labels.size() + (t.has_q ? m : 0);
+    if (r > 31) {
+      set_error("tensor %zu has %lld index bits (max 31)", i, (long long)r);
+      return WMC_EPLAN_TOO_BIG;
+    }
+    bytes[i] = (int64_t(1) << r) * (st.t_dbl[i] ? 8 : 4);
+    st.t_qc[i] = t.has_q ? Q : 1;
+    st.t_meta[i] = slots;
+    slots += st.t_qc[i];
+  }
+  st.n_slots = slots;
+  int64_t off = 0;
+  st.off_io = off; off += align_up(sizeof(IoDesc));
+  st.off_flags = off; off += align_up(4 * (int64_t)Q);
+  st.off_exp = off; off += align_up(8 * slots);
+  st.off_max = off; off += align_up(8 * slots);
+  // leaves: resident for the whole walk
+  for (int64_t i = 0; i < plan.n_leaves; ++i) { st.t_off[(size_t)i] = off; off += align_up(bytes[(size_t)i]); }
+  const int64_t arena0 = off;
+  FirstFit ff;
+  st.alg_bytes = 0;
+  st.flops = 0;
+  for (const Node &nd : plan.nodes) {
+    st.t_off[(size_t)nd.c] = arena0 + ff.alloc(bytes[(size_t)nd.c]);
+    for (int64_t ch : {nd.a, nd.b})
+      if (ch >= plan.n_leaves) ff.release(st.t_off[(size_t)ch] - arena0, bytes[(size_t)ch]);
+    st.alg_bytes += (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
+    const TensorInfo &C = plan.tensors[(size_t)nd.c];
+    st.flops += 2.0 * std::ldexp(1.0, nd.iter_rank + (C.has_q ? m : 0));
+  }
+  st.arena_bytes = ff.top;
+  st.ws_bytes = arena0 + align_up(ff.top);
+  st.max_roundings = plan.tensors[(size_t)root].roundings;
+
+  // ---- launches
+  st.launches.clear();
+  Launch ms;
+  ms.kind = L_MEMSET;
+  ms.memset_off = st.off_flags;
+  ms.memset_bytes = st.off_max + align_up(8 * slots) - st.off_flags;  // flags, exps, maxima
+  st.launches.push_back(ms);
+  // clause leaves
+  st.h_clause.clear(); st.h_first.clear();
+  int64_t entries = 0;
+  for (int64_t i = 0; i < plan.n_leaves; ++i) {
+    const TensorInfo &t = plan.tensors[(size_t)i];
+    if (t.kind != LEAF_CLAUSE) continue;
+    ClauseLeaf L;
+    L.off = st.t_off[(size_t)i] / (st.f64 ? 8 : 4);
+    L.meta = st.t_meta[(size_t)i];
+    L.fals = t.fals;
+    L.rank = (int32_t)t.labels.size();
+    L.pad = 0;
+    st.h_clause.push_back(L);
+    st.h_first.push_back(entries);
+    entries += int64_t(1) << L.rank;
+  }
+  st.n_clause_entries = entries;
+  if (!st.h_clause.empty()) {
+    Launch l; l.kind = L_CLAUSES; l.blocks = grid_for((uint64_t)entries);
+    st.launches.push_back(l);
+  }
+  st.h_woff.assign((size_t)plan.n_vars, 0);
+  st.h_wmeta.assign((size_t)plan.n_vars, 0);
+  bool have_w = false;
+  for (int64_t i = 0; i < plan.n_leaves; ++i) {
+    const TensorInfo &t = plan.tensors[(size_t)i];
+    if (t.kind == LEAF_WEIGHT) {
+      st.h_woff[(size_t)t.labels[0]] = st.t_off[(size_t)i] / (st.f64 ? 8 : 4);
+      st.h_wmeta[(size_t)t.labels[0]] = st.t_meta[(size_t)i];
+      have_w = true;
+    } else if (t.kind == LEAF_ONE) {
+      Launch l; l.kind = L_ONE; l.one_off = st.t_off[(size_t)i]; l.one_meta = st.t_meta[(size_t)i];
+      st.launches.push_back(l);
+    }
+  }
+  if (have_w) {
+    Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Q);
+    st.launches.push_back(l);
+  }
+  for (const Node &nd : plan.nodes) {
+    const TensorInfo &A = plan.tensors[(size_t)nd.a];
+    const TensorInfo &B = plan.tensors[(size_t)nd.b];
+    const TensorInfo &C = plan.tensors[(size_t)nd.c];
+    std::vector<int32_t> LA = full_labels(A, m), LB = full_labels(B, m), LC = full_labels(C, m);
+    Launch l;
+    const bool is_root = nd.c == root;
+    bool used_k2 = false;
+    if (!is_root) {
+      const bool a_first = LA.size() >= LB.size();
+      int vmax = 1, kmax = 1, fmax = 1;
+      K2Params p2;
+      for (int attempt = 0; attempt < 2 && !used_k2; ++attempt) {
+        bool use_a = (attempt == 0) == a_first;
+        const std::vector<int32_t> &LP = use_a ? LA : LB;
+        const std::vector<int32_t> &LS = use_a ? LB : LA;
+        if (try_k2(LP, LS, LC, st.f64, p2, vmax, kmax, fmax)) {
+          used_k2 = true;
+          l.kind = L_K2;
+          l.ti = st.f64 ? TD : TF;
+          l.v = vmax; l.kmax = kmax; l.fmax = fmax;
+          l.k2 = p2;
+          l.off_a = st.t_off[(size_t)(use_a ? nd.a : nd.b)];
+          l.off_b = st.t_off[(size_t)(use_a ? nd.b : nd.a)];
+          l.meta_a = st.t_meta[(size_t)(use_a ? nd.a : nd.b)];
+          l.meta_b = st.t_meta[(size_t)(use_a ? nd.b : nd.a)];
+          l.k2.ma.qmask = (use_a ? A : B).has_q ? Q - 1 : 0;
+          l.k2.mb.qmask = (use_a ? B : A).has_q ? Q - 1 : 0;
+          l.blocks = grid_for(1ull << p2.log2_nu);
+        }
+      }
+    }
+    if (!used_k2) {
+      l.kind = L_K1;
+      fill_k1(LA, LB, LC, l.k1);
+      if (l.k1.k > 24) { set_error("node sums %d indices (max 24)", l.k1.k); return WMC_EPLAN_TOO_BIG; }
+      l.ti = st.f64 ? TD : TF;
+      l.ta = (st.f64 || is_root || l.k1.k > 16) ? TD : TF;
+      l.to = st.t_dbl[(size_t)nd.c] ? TD : TF;
+      l.off_a = st.t_off[(size_t)nd.a];
+      l.off_b = st.t_off[(size_t)nd.b];
+      l.meta_a = st.t_meta[(size_t)nd.a];
+      l.meta_b = st.t_meta[(size_t)nd.b];
+      l.k1.ma.qmask = A.has_q ? Q - 1 : 0;
+      l.k1.mb.qmask = B.has_q ? Q - 1 : 0;
+      l.blocks = grid_for(1ull << l.k1.rC);
+    }
+    l.off_c = st.t_off[(size_t)nd.c];
+    l.meta_c = st.t_meta[(size_t)nd.c];
+    l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
+    dev::OutMeta &mc = l.kind == L_K2 ? l.k2.mc : l.k1.mc;
+    mc.Qc = C.has_q ? Q : 1;
+    mc.Q = Q;
+    mc.scale_inputs = 1;
+    st.launches.push_back(l);
+  }
+  Launch fin;
+  fin.kind = L_FINAL;
+  fin.off_c = st.t_off[(size_t)root];
+  fin.meta_c = st.t_meta[(size_t)root];
+  fin.blocks = grid_for((uint64_t)Q);
+  st.launches.push_back(fin);
+  st.kernels_per_run = 0;
+  for (auto &l : st.launches) st.kernels_per_run += (l.kind != L_MEMSET);
+  return WMC_OK;
+}
+
+// ------------------------------------------------------------ launching
+
+template <typename T, int V, int K>
+static void launch_k2_t(const K2Params &p, int64_t blocks, cudaStream_t s) {
+  dev::k2_stream<T, V, K, K><<<(unsigned)blocks, dev::kThreads, 0, s>>>(p);
+}
+
+template <typename T, int V>
+static void launch_k2_v(const K2Params &p, int kmax, int64_t blocks, cudaStream_t s) {
+  if (kmax <= 1) launch_k2_t<T, V, 1>(p, blocks, s);
+  else if (kmax == 2) launch_k2_t<T, V, 2>(p, blocks, s);
+  else launch_k2_t<T, V, 3>(p, blocks, s);
+}
+
+static void launch_k2(const Launch &l, const K2Params &p, cudaStream_t s) {
+  if (l.ti == TF) {
+    if (l.v == 4) launch_k2_v<float, 4>(p, l.kmax, l.blocks, s);
+    else launch_k2_v<float, 1>(p, l.kmax, l.blocks, s);
+  } else {
+    if (l.v == 2) launch_k2_v<double, 2>(p, l.kmax, l.blocks, s);
+    else launch_k2_v<double, 1>(p, l.kmax, l.blocks, s);
+  }
+}
+
+static void launch_k1(const Launch &l, const K1Params &p, cudaStream_t s) {
+  const unsigned g = (unsigned)l.blocks;
+  if (l.ti == TD) dev::k1_generic<double, double, double><<<g, dev::kThreads, 0, s>>>(p);
+  else if (l.ta == TF) dev::k1_generic<float, float, float><<<g, dev::kThreads, 0, s>>>(p);
+  else if (l.to == TD) dev::k1_generic<float, double, double><<<g, dev::kThreads, 0, s>>>(p);
+  else dev::k1_generic<float, double, float><<<g, dev::kThreads, 0, s>>>(p);
+}
+
+static int ensure_dev(ExecState &st) {
+  if (st.dev_ready) return WMC_OK;
+  auto up = [&](void **dst, const void *src, size_t bytes) -> int {
+    int rc = dev_alloc(dst, bytes);
+    if (rc) return rc;
+    if (bytes) CUDA_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return WMC_OK;
+  };
+  int rc;
+  if ((rc = up((void **)&st.d_clause, st.h_clause.data(), sizeof(ClauseLeaf) * st.h_clause.size()))) return rc;
+  if ((rc = up((void **)&st.d_first, st.h_first.data(), sizeof(int64_t) * st.h_first.size()))) return rc;
+  if ((rc = up((void **)&st.d_woff, st.h_woff.data(), sizeof(int64_t) * st.h_woff.size()))) return rc;
+  if ((rc = up((void **)&st.d_wmeta, st.h_wmeta.data(), sizeof(int64_t) * st.h_wmeta.size()))) return rc;
+  CUDA_TRY(cudaStreamCreateWithFlags(&st.capture_stream, cudaStreamNonBlocking));
+  st.dev_ready = true;
+  return WMC_OK;
+}
+
+// Enqueues the whole walk on `s` for workspace `ws`.  With `events`, an
+// event is recorded after every launch (measurement only).
+static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
+                         cudaEvent_t *events = nullptr) {
+  int64_t *mexp = (int64_t *)(ws + st.off_exp);
+  unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
+  uint32_t *flags = (uint32_t *)(ws + st.off_flags);
+  const IoDesc *io = (const IoDesc *)(ws + st.off_io);
+  for (size_t li = 0; li < st.launches.size(); ++li) {
+    const Launch &l = st.launches[li];
+    switch (l.kind) {
+      case L_MEMSET:
+        cudaMemsetAsync(ws + l.memset_off, 0, (size_t)l.memset_bytes, s);
+        break;
+      case L_CLAUSES:
+        if (st.f64)
+          dev::k_clause_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+              st.d_clause, st.d_first, (int64_t)st.h_clause.size(), st.n_clause_entries,
+              (double *)ws, mexp, mmax);
+        else
+          dev::k_clause_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+              st.d_clause, st.d_first, (int64_t)st.h_clause.size(), st.n_clause_entries,
+              (float *)ws, mexp, mmax);
+        break;
+      case L_WEIGHTS:
+        if (st.f64)
+          dev::k_weight_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+              io, plan.n_vars, st.Q, st.d_woff, st.d_wmeta, (double *)ws, mexp, mmax, flags);
+        else
+          dev::k_weight_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+              io, plan.n_vars, st.Q, st.d_woff, st.d_wmeta, (float *)ws, mexp, mmax, flags);
+        break;
+      case L_ONE:
+        if (st.f64) dev::k_one_leaf<double><<<1, 32, 0, s>>>((double *)(ws + l.one_off), l.one_meta, mexp, mmax);
+        else dev::k_one_leaf<float><<<1, 32, 0, s>>>((float *)(ws + l.one_off), l.one_meta, mexp, mmax);
+        break;
+      case L_K1: {
+        K1Params p = l.k1;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.flags = flags;
+        launch_k1(l, p, s);
+        break;
+      }
+      case L_K2: {
+        K2Params p = l.k2;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.flags = flags;
+        launch_k2(l, p, s);
+        break;
+      }
+      case L_FINAL: {
+        const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Q : 1;
+        dev::k_finalize<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+            io, (const double *)(ws + l.off_c), mexp + l.meta_c, root_qc, flags, st.Q);
+        break;
+      }
+    }
+    if (events) cudaEventRecord(events[li + 1], s);
+  }
+}
+
+static int get_graph(Plan &plan, ExecState &st, char *ws, cudaGraphExec_t *out) {
+  auto it = st.graphs.find((uintptr_t)ws);
+  if (it != st.graphs.end()) { *out = it->second; return WMC_OK; }
+  if (st.graphs.size() >= 8) {  // bound the cache
+    cudaGraphExecDestroy(st.graphs.begin()->second);
+    st.graphs.erase(st.graphs.begin());
+  }
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(st.capture_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_walk(plan, st, ws, st.capture_stream);
+  cudaError_t e = cudaStreamEndCapture(st.capture_stream, &g);
+  if (e != cudaSuccess) {
+    set_error("graph capture failed: %s", cudaGetErrorString(e));
+    if (g) cudaGraphDestroy(g);
+    return WMC_ECUDA;
+  }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+    return WMC_ECUDA;
+  }
+  st.graphs[(uintptr_t)ws] = ge;
+  *out = ge;
+  return WMC_OK;
+}
+
+static int get_state(Plan &plan, int32_t Q, ExecState **out) {
+  std::lock_guard<std::mutex> lk(plan.exec_mu);
+  auto it = plan.exec.find(Q);
+  if (it != plan.exec.end()) { *out = it->second.get(); return WMC_OK; }
+  std::unique_ptr<ExecState> st(new (std::nothrow) ExecState());
+  if (!st) { set_error("out of host memory"); return WMC_ENOMEM; }
+  int rc = build_exec(plan, Q, *st);
+  if (rc) return rc;
+  *out = st.get();
+  plan.exec[Q] = std::move(st);
+  return WMC_OK;
+}
+
+namespace wmc {
+int64_t plan_workspace_bytes(Plan &plan, int32_t Q, int64_t *arena_bytes) {
+  ExecState *st = nullptr;
+  if (get_state(plan, Q, &st)) return -1;
+  if (arena_bytes) *arena_bytes = st->arena_bytes;
+  return st->ws_bytes;
+}
+}  // namespace wmc
+
+static int check_q(int32_t Q) {
+  if (Q < 1 || Q > dev::kMaxQ) { set_error("Q = %d out of [1, %d]", Q, dev::kMaxQ); return WMC_EINVAL; }
+  return WMC_OK;
+}
+
+// Runs the walk for a power-of-two batch Qp >= Q on device pointers.
+static int run_device(Plan &plan, ExecState &st, const double *d_wp, const double *d_wn,
+                      char *ws, double *d_mant, int64_t *d_exp, uint32_t *d_flags,
+                      cudaStream_t s) {
+  int rc = ensure_dev(st);
+  if (rc) return rc;
+  cudaGraphExec_t ge = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(st.graph_mu);
+    rc = get_graph(plan, st, ws, &ge);
+  }
+  if (rc) return rc;
+  IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.w_pos = d_wp; io.w_neg = d_wn; io.mant = d_mant; io.exp2 = d_exp; io.flags = d_flags;
+  CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaGraphLaunch(ge, s));
+  g_launches.fetch_add(st.kernels_per_run);
+  return WMC_OK;
+}
+
+static void fill_result(const ExecState &st, double mant, int64_t e,
+                        uint32_t flags, bool unit, bool negative, wmc_result *r) {
+  int fe = 0;
+  double fr = std::frexp(mant, &fe);
+  r->mant = fr;
+  r->exp2 = (mant == 0.0) ? 0 : e + fe;
+  r->log10 = (mant == 0.0) ? -INFINITY : std::log10(std::fabs(fr)) + (double)r->exp2 * std::log10(2.0);
+  r->flags = flags & WMC_FLAG_FP32_FLUSH;
+  const double u = st.f64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  const double d = (double)st.max_roundings;
+  r->rel_err_bound = d * u / (1.0 - d * u);
+  if (negative) r->flags |= WMC_FLAG_NO_BOUND;
+  if (unit && st.f64 && mant != 0.0 && r->exp2 <= 53 && std::ldexp(fr, (int)r->exp2) == std::floor(std::ldexp(fr, (int)r->exp2)))
+    r->flags |= WMC_FLAG_EXACT_INT;
+  r->reserved = 0;
+}
+
+// ------------------------------------------------------------ C ABI
+
+extern "C" int wmc_plan(const wmc_network_t *net, const wmc_plan_opts *opts, wmc_plan_t **out) {
+  if (!net || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  *out = nullptr;
+  wmc_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.precision = WMC_SCALED_FP32;
+  if (opts) o = *opts;
+  if (o.precision != WMC_FP64 && o.precision != WMC_SCALED_FP32) { set_error("bad precision %d", o.precision); return WMC_EINVAL; }
+  wmc_plan_t *p = new (std::nothrow) wmc_plan_t();
+  if (!p) { set_error("out of host memory"); return WMC_ENOMEM; }
+  int rc = build_plan(network_of(net), o, *p);
+  if (rc) { delete p; return rc; }
+  if (o.mem_budget_bytes > 0) {
+    int64_t ws = plan_workspace_bytes(*p, 1, nullptr);
+    if (ws < 0) { delete p; return WMC_EPLAN_TOO_BIG; }
+    if (ws > o.mem_budget_bytes) {
+      set_error("plan needs %lld bytes at Q=1, budget %lld", (long long)ws, (long long)o.mem_budget_bytes);
+      delete p;
+      return WMC_EPLAN_TOO_BIG;
+    }
+  }
+  *out = p;
+  return WMC_OK;
+}
+
+extern "C" void wmc_plan_destroy(wmc_plan_t *plan) { delete plan; }
+
+extern "C" int wmc_plan_info(const wmc_plan_t *cplan, int32_t Q, wmc_plan_info_t *out) {
+  if (!cplan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  wmc_plan_t *plan = const_cast<wmc_plan_t *>(cplan);
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->max_rank = plan->max_rank;
+  out->max_node_rank = plan->max_node_rank;
+  out->n_leaves = plan->n_leaves;
+  out->n_nodes = (int64_t)plan->nodes.size();
+  out->workspace_bytes = st->ws_bytes;
+  out->peak_tensor_bytes = st->arena_bytes;
+  out->algorithmic_bytes = st->alg_bytes;
+  out->flops = st->flops;
+  out->precision = plan->precision;
+  out->ordering_used = plan->ordering_used;
+  out->max_path_roundings = st->max_roundings;
+  return WMC_OK;
+}
+
+extern "C" int wmc_plan_node(const wmc_plan_t *plan, int64_t node, int64_t *left, int64_t *right,
+                             int32_t *n_labels, int32_t *labels) {
+  if (!plan || node < 0 || node >= (int64_t)plan->nodes.size()) { set_error("bad node id"); return WMC_EINVAL; }
+  const Node &nd = plan->nodes[(size_t)node];
+  const TensorInfo &c = plan->tensors[(size_t)nd.c];
+  if (left) *left = nd.a;
+  if (right) *right = nd.b;
+  if (n_labels) *n_labels = (int32_t)c.labels.size();
+  if (labels) for (size_t i = 0; i < c.labels.size() && i < 64; ++i) labels[i] = c.labels[i];
+  return WMC_OK;
+}
+
+extern "C" int wmc_plan_leaf(const wmc_plan_t *plan, int64_t leaf, int32_t *kind, int32_t *n_labels,
+                             int32_t *labels, uint64_t *fals) {
+  if (!plan || leaf < 0 || leaf >= plan->n_leaves) { set_error("bad leaf id"); return WMC_EINVAL; }
+  const TensorInfo &t = plan->tensors[(size_t)leaf];
+  if (kind) *kind = t.kind;
+  if (n_labels) *n_labels = (int32_t)t.labels.size();
+  if (labels) for (size_t i = 0; i < t.labels.size() && i < 64; ++i) labels[i] = t.labels[i];
+  if (fals) *fals = t.fals;
+  return WMC_OK;
+}
+
+extern "C" int wmc_execute_device(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
+                                  const double *d_w_neg, void *d_workspace, size_t workspace_bytes,
+                                  double *d_mant, int64_t *d_exp2, uint32_t *d_flags, void *stream) {
+  if (!plan || !d_workspace || !d_mant || !d_exp2 || !d_flags) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  if (plan->n_vars > 0 && (!d_w_pos || !d_w_neg)) { set_error("weights are NULL"); return WMC_EINVAL; }
+  if ((uintptr_t)d_workspace % kAlign) { set_error("workspace not 256-byte aligned"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  if ((int64_t)workspace_bytes < st->ws_bytes) {
+    set_error("workspace %zu bytes < %lld needed", workspace_bytes, (long long)st->ws_bytes);
+    return WMC_EINVAL;
+  }
+  return run_device(*plan, *st, d_w_pos, d_w_neg, (char *)d_workspace, d_mant, d_exp2, d_flags,
+                    (cudaStream_t)stream);
+}
+
+extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
+                                const double *d_w_neg, void *d_workspace, size_t workspace_bytes,
+                                double *d_mant, int64_t *d_exp2, uint32_t *d_flags, void *stream,
+                                int64_t n_max, float *node_ms, int32_t *kind, double *alg_bytes,
+                                int64_t *n_launches) {
+  if (!plan || !d_workspace || !d_mant || !d_exp2 || !d_flags) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  if ((int64_t)workspace_bytes < st->ws_bytes || (uintptr_t)d_workspace % kAlign) {
+    set_error("workspace too small or misaligned");
+    return WMC_EINVAL;
+  }
+  if ((rc = ensure_dev(*st))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nl = st->launches.size();
+  std::vector<cudaEvent_t> ev(nl + 1, nullptr);
+  for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+  IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.w_pos = d_w_pos; io.w_neg = d_w_neg; io.mant = d_mant; io.exp2 = d_exp2; io.flags = d_flags;
+  char *ws = (char *)d_workspace;
+  CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaEventRecord(ev[0], s));
+  enqueue_walk(*plan, *st, ws, s, ev.data());
+  g_launches.fetch_add(st->kernels_per_run);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (size_t i = 0; i < nl && (int64_t)i < n_max; ++i) {
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    const Launch &l = st->launches[i];
+    if (node_ms) node_ms[i] = ms;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_MEMSET ? 3 : 2;
+    if (alg_bytes) alg_bytes[i] = l.alg_bytes;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (n_launches) *n_launches = (int64_t)nl;
+  return WMC_OK;
+}
+
+extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                           void *stream, wmc_result *out) {
+  if (!plan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  if ((w_pos_q == nullptr) != (w_neg_q == nullptr)) { set_error("give both weight arrays or neither"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nv = (size_t)plan->n_vars;
+  std::lock_guard<std::mutex> run(st->run_mu);  // the owned workspace is single-use at a time
+  {
+    if (!st->own_ws) {
+      if ((rc = dev_alloc(&st->own_ws, (size_t)st->ws_bytes))) return rc;
+      if ((rc = dev_alloc((void **)&st->d_w, sizeof(double) * 2 * (size_t)Q * std::max<size_t>(nv, 1)))) return rc;
+      if ((rc = dev_alloc((void **)&st->d_res_mant, sizeof(double) * (size_t)Q))) return rc;
+      if ((rc = dev_alloc((void **)&st->d_res_exp, sizeof(int64_t) * (size_t)Q))) return rc;
+      if ((rc = dev_alloc((void **)&st->d_res_flags, sizeof(uint32_t) * (size_t)Q))) return rc;
+      CUDA_TRY(cudaMallocHost(&st->h_res_mant, sizeof(double) * (size_t)Q));
+      CUDA_TRY(cudaMallocHost(&st->h_res_exp, sizeof(int64_t) * (size_t)Q));
+      CUDA_TRY(cudaMallocHost(&st->h_res_flags, sizeof(uint32_t) * (size_t)Q));
+    }
+  }
+  bool unit = true, negative = false;
+  if (nv) {
+    double *d_wp = st->d_w, *d_wn = st->d_w + (size_t)Q * nv;
+    if (w_pos_q) {
+      CUDA_TRY(cudaMemcpyAsync(d_wp, w_pos_q, sizeof(double) * (size_t)Q * nv, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(d_wn, w_neg_q, sizeof(double) * (size_t)Q * nv, cudaMemcpyHostToDevice, s));
+      for (size_t i = 0; i < (size_t)Q * nv; ++i) {
+        unit &= (w_pos_q[i] == 1.0) & (w_neg_q[i] == 1.0);
+        negative |= (w_pos_q[i] < 0.0) | (w_neg_q[i] < 0.0);
+      }
+    } else {
+      for (int32_t q = 0; q < Q; ++q) {
+        CUDA_TRY(cudaMemcpyAsync(d_wp + (size_t)q * nv, plan->w_pos.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_wn + (size_t)q * nv, plan->w_neg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, s));
+      }
+      unit = plan->unit_weights;
+      negative = plan->any_negative;
+    }
+  }
+  rc = run_device(*plan, *st, st->d_w, st->d_w + (size_t)Q * nv, (char *)st->own_ws,
+                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(st->h_res_mant, st->d_res_mant, sizeof(double) * (size_t)Q, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(st->h_res_exp, st->d_res_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(st->h_res_flags, st->d_res_flags, sizeof(uint32_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int32_t q = 0; q < Q; ++q)
+    fill_result(*st, st->h_res_mant[q], st->h_res_exp[q], st->h_res_flags[q], unit, negative, out + q);
+  return WMC_OK;
+}
+
+namespace wmc {
+int exec_state(Plan &plan, int32_t Q, ExecState **out) {
+  if (check_q(Q)) return WMC_EINVAL;
+  return get_state(plan, Q, out);
+}
+int64_t exec_ws_bytes(const ExecState *st) { return st->ws_bytes; }
+int exec_run_device(Plan &plan, ExecState *st, const double *d_w_pos, const double *d_w_neg,
+                    void *ws, double *d_mant, int64_t *d_exp2, uint32_t *d_flags, void *stream) {
+  return run_device(plan, *st, d_w_pos, d_w_neg, (char *)ws, d_mant, d_exp2, d_flags,
+                    (cudaStream_t)stream);
+}
+void exec_fill_result(const ExecState *st, double mant, int64_t exp2, uint32_t flags, bool unit,
+                      bool negative, wmc_result *out) {
+  fill_result(*st, mant, exp2, flags, unit, negative, out);
+}
+Plan &plan_of(wmc_plan_t *p) { return *p; }
+}  // namespace wmc
+
+// ------------------------------------------------------------ pairwise
+
+extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_t *labels_a,
+                                 const void *a, int32_t rank_b, const int32_t *labels_b,
+                                 const void *b, int32_t rank_c, const int32_t *labels_c, void *c,
+                                 const int64_t *exp_a, const int64_t *exp_b, int64_t *exp_c,
+                                 void *stream) {
+  if (precision != WMC_FP64 && precision != WMC_SCALED_FP32) { set_error("bad precision"); return WMC_EINVAL; }
+  if (rank_a < 0 || rank_b < 0 || rank_c < 0 || rank_a > 31 || rank_b > 31 || rank_c > 31) {
+    set_error("ranks must be in [0, 31]");
+    return WMC_EINVAL;
+  }
+  if (!a || !b || !c || (rank_a && !labels_a) || (rank_b && !labels_b) || (rank_c && !labels_c)) {
+    set_error("NULL argument");
+    return WMC_EINVAL;
+  }
+  const bool f64 = precision == WMC_FP64;
+  if (!f64 && (!exp_a || !exp_b || !exp_c)) { set_error("scaled FP32 needs exp_a, exp_b, exp_c"); return WMC_EINVAL; }
+  std::vector<int32_t> LA(labels_a, labels_a + rank_a), LB(labels_b, labels_b + rank_b),
+      LC(labels_c, labels_c + rank_c);
+  auto dup = [](std::vector<int32_t> L) {
+    std::sort(L.begin(), L.end());
+    return std::adjacent_find(L.begin(), L.end()) != L.end();
+  };
+  if (dup(LA) || dup(LB) || dup(LC)) { set_error("repeated label within a tensor"); return WMC_EINVAL; }
+  for (int32_t l : LC)
+    if (pos_of(LA, l) < 0 && pos_of(LB, l) < 0) { set_error("label %d of C is in neither A nor B", l); return WMC_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  Launch l;
+  K2Params p2;
+  int vmax = 1, kmax = 1, fmax = 1;
+  bool k2 = false;
+  const bool a_first = LA.size() >= LB.size();
+  bool use_a = a_first;
+  for (int attempt = 0; attempt < 2 && !k2; ++attempt) {
+    use_a = (attempt == 0) == a_first;
+    k2 = try_k2(use_a ? LA : LB, use_a ? LB : LA, LC, f64, p2, vmax, kmax, fmax);
+  }
+  dev::Meta ma{exp_a, nullptr, 0}, mb{exp_b, nullptr, 0};
+  dev::OutMeta mc{exp_c, nullptr, nullptr, 1, 1, 0};
+  if (k2) {
+    l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = vmax; l.kmax = kmax; l.fmax = fmax;
+    l.blocks = grid_for(1ull << p2.log2_nu);
+    p2.A = use_a ? a : b; p2.B = use_a ? b : a; p2.C = c;
+    p2.ma = use_a ? ma : mb; p2.mb = use_a ? mb : ma; p2.mc = mc;
+    launch_k2(l, p2, s);
+  } else {
+    l.kind = L_K1;
+    fill_k1(LA, LB, LC, l.k1);
+    if (l.k1.k > 24) { set_error("at most 24 summed indices"); return WMC_EINVAL; }
+    l.ti = f64 ? TD : TF;
+    l.ta = (f64 || l.k1.k > 16) ? TD : TF;
+    l.to = f64 ? TD : TF;
+    l.blocks = grid_for(1ull << l.k1.rC);
+    l.k1.A = a; l.k1.B = b; l.k1.C = c;
+    l.k1.ma = ma; l.k1.mb = mb; l.k1.mc = mc;
+    launch_k1(l, l.k1, s);
+  }
+  g_launches.fetch_add(1);
+  CUDA_TRY(cudaGetLastError());
+  return WMC_OK;
+}
+
+extern "C" int wmc_to_scaled_fp32(const double *x, int64_t n, float *out, int64_t *exp_out,
+                                  void *stream) {
+  if (!x || !out || !exp_out || n < 0) { set_error("bad argument"); return WMC_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  // the max is accumulated in exp_out's storage (8 bytes) before it is
+  // overwritten by the exponent: no scratch allocation
+  unsigned long long *maxb = (unsigned long long *)exp_out;
+  CUDA_TRY(cudaMemsetAsync(maxb, 0, sizeof(unsigned long long), s));
+  const unsigned g = (unsigned)grid_for((uint64_t)std::max<int64_t>(n, 1));
+  dev::k_absmax_f64<<<g, dev::kThreads, 0, s>>>(x, n, maxb);
+  dev::k_scale_to_f32<<<g, dev::kThreads, 0, s>>>(x, n, maxb, out);
+  dev::k_max_to_exp<<<1, 1, 0, s>>>(maxb);
+  g_launches.fetch_add(3);
+  CUDA_TRY(cudaGetLastError());
+  return WMC_OK;
+}

@@ -1,0 +1,99 @@
+// Internal host-side structures of the WMC execution library.
+// Not part of the ABI (see include/wmc.h).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wmc.h"
+
+namespace wmc {
+
+// Thread-local error message behind wmc_last_error().
+void set_error(const char *fmt, ...);
+
+// One clause after reduction: its distinct variables (0-based, ascending)
+// and the unique falsifying assignment (bit j = falsifying value of
+// vars[j]).  The clause tensor B_C of Thm 3.2 is 1 everywhere except at
+// `fals`, where it is 0.
+struct Clause {
+  std::vector<int32_t> vars;
+  uint64_t fals = 0;
+};
+
+struct Network {
+  int32_t n_vars = 0;
+  int64_t n_clauses_in = 0;
+  std::vector<Clause> clauses;  // tautologies dropped; empty clause kept
+  std::vector<double> w_pos, w_neg;
+  bool has_empty = false;
+  int64_t n_indices_strict = 0;
+  int64_t max_clause_rank = 0;
+};
+
+enum LeafKind : int32_t { LEAF_CLAUSE = 0, LEAF_WEIGHT = 1, LEAF_ONE = 2, NOT_LEAF = -1 };
+
+struct TensorInfo {
+  std::vector<int32_t> labels;  // variable labels, bit j of the offset = labels[j]
+  bool has_q = false;           // depends on the weights: carries the query index
+  int32_t kind = NOT_LEAF;
+  uint64_t fals = 0;            // LEAF_CLAUSE
+  int64_t clause = -1;          // LEAF_CLAUSE: clause id
+  int64_t node = -1;            // producing node (or -1 for a leaf)
+  int32_t roundings = 0;        // most roundings on a path from a leaf (FP32 counts)
+};
+
+struct Node {
+  int64_t a = -1, b = -1, c = -1;  // tensor ids (c = output)
+  int32_t iter_rank = 0;           // |I(A) u I(B)|
+  int32_t n_summed = 0;
+};
+
+struct ExecState;  // executor.cu
+
+struct Plan {
+  int32_t n_vars = 0;
+  std::vector<double> w_pos, w_neg;  // default weights
+  bool unit_weights = false;
+  bool any_negative = false;
+  std::vector<TensorInfo> tensors;   // leaves [0, n_leaves), then node outputs
+  int64_t n_leaves = 0;
+  std::vector<Node> nodes;           // post-order; nodes.back() is the root
+  int32_t precision = WMC_SCALED_FP32;
+  int32_t ordering_used = 0;
+  int32_t max_rank = 0;
+  int32_t max_node_rank = 0;
+  std::vector<Clause> clauses;       // for leaf materialisation
+
+  std::mutex exec_mu;
+  std::map<int32_t, std::unique_ptr<ExecState>> exec;  // keyed by Q
+  ~Plan();
+};
+
+// Planner entry (planner.cpp).
+int build_plan(const Network &net, const wmc_plan_opts &opts, Plan &plan);
+
+// Elimination orders (planner.cpp), 0-based variable ids.
+std::vector<int32_t> order_min_fill(int32_t n, const std::vector<std::vector<int32_t>> &adj);
+std::vector<int32_t> order_min_degree(int32_t n, const std::vector<std::vector<int32_t>> &adj);
+std::vector<int32_t> order_sweep(int32_t n, const std::vector<std::vector<int32_t>> &adj,
+                                 bool descending);
+
+// Executor (executor.cu).
+int64_t plan_workspace_bytes(Plan &plan, int32_t Q, int64_t *arena_bytes);
+void destroy_exec_state(ExecState *st);
+// Lays out (once) and returns the execution state of batch size Q.
+int exec_state(Plan &plan, int32_t Q, ExecState **out);
+int64_t exec_ws_bytes(const ExecState *st);
+// Enqueues one walk on `stream` (device pointers; weights [Q][n_vars]).
+int exec_run_device(Plan &plan, ExecState *st, const double *d_w_pos, const double *d_w_neg,
+                    void *ws, double *d_mant, int64_t *d_exp2, uint32_t *d_flags, void *stream);
+void exec_fill_result(const ExecState *st, double mant, int64_t exp2, uint32_t flags,
+                      bool unit, bool negative, wmc_result *out);
+Plan &plan_of(wmc_plan_t *p);
+
+}  // namespace wmc

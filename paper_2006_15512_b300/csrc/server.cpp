@@ -1,0 +1,373 @@
+// Continuous-batching WMC server over one compiled plan.
+//
+// Queries (weight vectors) arrive through wmc_submit.  A batcher thread
+// forms a wave from whatever is queued as soon as a wave slot is free: the
+// wave's Q is the next power of two >= the queued count (capped at
+// max_batch; padding lanes repeat the last query and are discarded).  Each
+// slot owns a stream and a workspace sized for max_batch, so admission is
+// by the plan's workspace bytes: the number of slots is what fits in
+// arena_bytes.  Waves on different slots overlap on the device.  A host
+// callback on the slot's stream hands the finished wave to a completion
+// thread, which publishes per-ticket results and frees the slot.  The query
+// index is a pure batch index of every contraction and every per-query
+// exponent depends only on that query, so a result does not depend on the
+// wave it lands in.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+using namespace wmc;
+
+namespace {
+
+struct Query {
+  uint64_t ticket;
+  std::vector<double> wp, wn;
+  bool negative;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;
+  double *d_w = nullptr;          // [2][max_batch][n_vars]
+  double *h_w = nullptr;          // pinned staging
+  double *d_mant = nullptr;
+  int64_t *d_exp = nullptr;
+  uint32_t *d_flags = nullptr;
+  double *h_mant = nullptr;       // pinned results
+  int64_t *h_exp = nullptr;
+  uint32_t *h_flags = nullptr;
+  std::vector<Query> wave;        // queries of the wave in flight
+  int32_t Q = 0;
+  int status = WMC_OK;
+  bool busy = false;
+};
+
+struct TicketState {
+  int status = WMC_PENDING;
+  wmc_result res{};
+  int64_t done_ns = 0;
+};
+
+int64_t mono_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct wmc_server {
+  Plan *plan = nullptr;
+  wmc_server_opts opts{};
+  int32_t n_vars = 0;
+  std::vector<Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv_work;   // batcher: queue or slot changes
+  std::condition_variable cv_done;   // waiters: tickets completed
+  std::condition_variable cv_comp;   // completion thread
+  std::deque<Query> queue;
+  std::deque<int> finished;          // slot ids whose wave finished
+  std::unordered_map<uint64_t, TicketState> tickets;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int in_flight = 0;
+  wmc_server_stats_t stats{};
+  double sum_q = 0;
+  std::thread batcher, completer;
+};
+
+static void CUDART_CB on_wave_done(void *arg);
+
+namespace {
+struct CbArg {
+  wmc_server *srv;
+  int slot;
+};
+}  // namespace
+
+static int launch_wave(wmc_server *srv, int si) {
+  Slot &sl = srv->slots[(size_t)si];
+  const size_t nv = (size_t)srv->n_vars;
+  const int32_t n = (int32_t)sl.wave.size();
+  int32_t Q = 1;
+  while (Q < n) Q <<= 1;
+  sl.Q = Q;
+  for (int32_t q = 0; q < Q; ++q) {
+    const Query &src = sl.wave[(size_t)std::min(q, n - 1)];
+    if (nv) {
+      std::memcpy(sl.h_w + (size_t)q * nv, src.wp.data(), sizeof(double) * nv);
+      std::memcpy(sl.h_w + (size_t)Q * nv + (size_t)q * nv, src.wn.data(), sizeof(double) * nv);
+    }
+  }
+  ExecState *st = nullptr;
+  int rc = exec_state(*srv->plan, Q, &st);
+  if (rc) return rc;
+  if (nv && cudaMemcpyAsync(sl.d_w, sl.h_w, sizeof(double) * 2 * (size_t)Q * nv,
+                            cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+    return WMC_ECUDA;
+  rc = exec_run_device(*srv->plan, st, sl.d_w, sl.d_w + (size_t)Q * nv, sl.ws, sl.d_mant, sl.d_exp,
+                       sl.d_flags, sl.stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(sl.h_mant, sl.d_mant, sizeof(double) * (size_t)Q, cudaMemcpyDeviceToHost, sl.stream) ||
+      cudaMemcpyAsync(sl.h_exp, sl.d_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, sl.stream) ||
+      cudaMemcpyAsync(sl.h_flags, sl.d_flags, sizeof(uint32_t) * (size_t)Q, cudaMemcpyDeviceToHost, sl.stream))
+    return WMC_ECUDA;
+  CbArg *arg = new CbArg{srv, si};
+  if (cudaLaunchHostFunc(sl.stream, on_wave_done, arg) != cudaSuccess) {
+    delete arg;
+    return WMC_ECUDA;
+  }
+  return WMC_OK;
+}
+
+static void CUDART_CB on_wave_done(void *p) {
+  CbArg *arg = (CbArg *)p;
+  wmc_server *srv = arg->srv;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->finished.push_back(arg->slot);
+  }
+  srv->cv_comp.notify_one();
+  delete arg;
+}
+
+static void batcher_loop(wmc_server *srv) {
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const size_t max_b = (size_t)srv->opts.max_batch;
+  for (;;) {
+    srv->cv_work.wait(lk, [&] {
+      if (srv->stop) return true;
+      if (srv->queue.empty()) return false;
+      for (auto &s : srv->slots) if (!s.busy) return true;
+      return false;
+    });
+    if (srv->stop) return;
+    // optional short wait for a fuller wave while other waves run
+    if (srv->opts.max_wave_wait_us > 0 && srv->queue.size() < max_b && srv->in_flight > 0) {
+      srv->cv_work.wait_for(lk, std::chrono::microseconds(srv->opts.max_wave_wait_us),
+                            [&] { return srv->stop || srv->queue.size() >= max_b; });
+      if (srv->stop) return;
+    }
+    int si = -1;
+    for (size_t i = 0; i < srv->slots.size(); ++i)
+      if (!srv->slots[i].busy) { si = (int)i; break; }
+    if (si < 0 || srv->queue.empty()) continue;
+    Slot &sl = srv->slots[(size_t)si];
+    sl.wave.clear();
+    while (!srv->queue.empty() && sl.wave.size() < max_b) {
+      sl.wave.push_back(std::move(srv->queue.front()));
+      srv->queue.pop_front();
+    }
+    sl.busy = true;
+    sl.status = WMC_OK;
+    srv->in_flight++;
+    lk.unlock();
+    int rc = launch_wave(srv, si);
+    lk.lock();
+    if (rc) {
+      // fail only this wave's tickets
+      sl.status = rc;
+      srv->finished.push_back(si);
+      srv->cv_comp.notify_one();
+    }
+  }
+}
+
+static void completer_loop(wmc_server *srv) {
+  std::unique_lock<std::mutex> lk(srv->mu);
+  for (;;) {
+    srv->cv_comp.wait(lk, [&] { return !srv->finished.empty() || (srv->stop && srv->in_flight == 0); });
+    if (srv->finished.empty()) return;
+    const int si = srv->finished.front();
+    srv->finished.pop_front();
+    Slot &sl = srv->slots[(size_t)si];
+    ExecState *st = nullptr;
+    int rc = sl.status;
+    if (rc == WMC_OK) {
+      cudaError_t e = cudaStreamQuery(sl.stream);
+      if (e != cudaSuccess && e != cudaErrorNotReady) rc = WMC_ECUDA;
+    }
+    if (rc == WMC_OK) rc = exec_state(*srv->plan, sl.Q, &st);
+    const int64_t now = mono_ns();
+    for (size_t q = 0; q < sl.wave.size(); ++q) {
+      auto it = srv->tickets.find(sl.wave[q].ticket);
+      if (it == srv->tickets.end()) continue;
+      it->second.done_ns = now;
+      if (rc == WMC_OK) {
+        exec_fill_result(st, sl.h_mant[q], sl.h_exp[q], sl.h_flags[q], false, sl.wave[q].negative,
+                         &it->second.res);
+        it->second.status = WMC_OK;
+      } else {
+        it->second.status = rc;
+      }
+    }
+    srv->stats.completed += (int64_t)sl.wave.size();
+    srv->stats.waves += 1;
+    if (rc) srv->stats.failed_waves += 1;
+    srv->sum_q += (double)sl.wave.size();
+    sl.wave.clear();
+    sl.busy = false;
+    srv->in_flight--;
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_one();
+  }
+}
+
+static void free_slot(Slot &s) {
+  if (s.stream) cudaStreamSynchronize(s.stream);
+  cudaFree(s.ws); cudaFree(s.d_w); cudaFree(s.d_mant); cudaFree(s.d_exp); cudaFree(s.d_flags);
+  cudaFreeHost(s.h_w); cudaFreeHost(s.h_mant); cudaFreeHost(s.h_exp); cudaFreeHost(s.h_flags);
+  if (s.stream) cudaStreamDestroy(s.stream);
+  s = Slot();
+}
+
+extern "C" int wmc_server_create(wmc_plan_t *cplan, const wmc_server_opts *opts, wmc_server_t **out) {
+  if (!cplan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  *out = nullptr;
+  Plan &plan = plan_of(cplan);
+  wmc_server_opts o{};
+  o.precision = plan.precision;
+  o.max_batch = 256;
+  o.max_waves = 2;
+  if (opts) o = *opts;
+  if (o.precision != plan.precision) { set_error("server precision differs from the plan's"); return WMC_EINVAL; }
+  if (o.max_batch < 1 || o.max_batch > 1024 || (o.max_batch & (o.max_batch - 1))) {
+    set_error("max_batch must be a power of two in [1, 1024]");
+    return WMC_EINVAL;
+  }
+  if (o.max_waves < 1 || o.max_waves > 64) { set_error("max_waves must be in [1, 64]"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = exec_state(plan, o.max_batch, &st);
+  if (rc) return rc;
+  const int64_t ws = exec_ws_bytes(st);
+  int32_t n_slots = o.max_waves;
+  if (o.arena_bytes > 0) n_slots = (int32_t)std::min<int64_t>(n_slots, o.arena_bytes / std::max<int64_t>(ws, 1));
+  if (n_slots < 1) {
+    set_error("arena_bytes %lld cannot hold one wave (%lld bytes)", (long long)o.arena_bytes, (long long)ws);
+    return WMC_EPLAN_TOO_BIG;
+  }
+  wmc_server *srv = new (std::nothrow) wmc_server();
+  if (!srv) { set_error("out of host memory"); return WMC_ENOMEM; }
+  srv->plan = &plan;
+  srv->opts = o;
+  srv->n_vars = plan.n_vars;
+  srv->slots.resize((size_t)n_slots);
+  const size_t nv = std::max<size_t>((size_t)plan.n_vars, 1);
+  const size_t B = (size_t)o.max_batch;
+  for (auto &s : srv->slots) {
+    bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&s.ws, (size_t)ws) == cudaSuccess &&
+              cudaMalloc((void **)&s.d_w, sizeof(double) * 2 * B * nv) == cudaSuccess &&
+              cudaMalloc((void **)&s.d_mant, sizeof(double) * B) == cudaSuccess &&
+              cudaMalloc((void **)&s.d_exp, sizeof(int64_t) * B) == cudaSuccess &&
+              cudaMalloc((void **)&s.d_flags, sizeof(uint32_t) * B) == cudaSuccess &&
+              cudaMallocHost((void **)&s.h_w, sizeof(double) * 2 * B * nv) == cudaSuccess &&
+              cudaMallocHost((void **)&s.h_mant, sizeof(double) * B) == cudaSuccess &&
+              cudaMallocHost((void **)&s.h_exp, sizeof(int64_t) * B) == cudaSuccess &&
+              cudaMallocHost((void **)&s.h_flags, sizeof(uint32_t) * B) == cudaSuccess;
+    if (!ok) {
+      (void)cudaGetLastError();
+      for (auto &t : srv->slots) free_slot(t);
+      delete srv;
+      set_error("server allocation failed");
+      return WMC_ENOMEM;
+    }
+  }
+  srv->batcher = std::thread(batcher_loop, srv);
+  srv->completer = std::thread(completer_loop, srv);
+  *out = srv;
+  return WMC_OK;
+}
+
+extern "C" int wmc_submit(wmc_server_t *srv, const double *w_pos, const double *w_neg, uint64_t *ticket) {
+  if (!srv || !ticket || (srv->n_vars > 0 && (!w_pos || !w_neg))) { set_error("NULL argument"); return WMC_EINVAL; }
+  Query q;
+  q.wp.assign(w_pos, w_pos + srv->n_vars);
+  q.wn.assign(w_neg, w_neg + srv->n_vars);
+  q.negative = false;
+  for (int32_t i = 0; i < srv->n_vars; ++i) q.negative |= (q.wp[(size_t)i] < 0) | (q.wn[(size_t)i] < 0);
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop) { set_error("server is shutting down"); return WMC_ESHUTDOWN; }
+    q.ticket = srv->next_ticket++;
+    *ticket = q.ticket;
+    srv->tickets[q.ticket] = TicketState();
+    srv->queue.push_back(std::move(q));
+    srv->stats.submitted++;
+  }
+  srv->cv_work.notify_one();
+  return WMC_OK;
+}
+
+static int take_result(wmc_server *srv, uint64_t ticket, wmc_result *out, int64_t *done_ns = nullptr) {
+  auto it = srv->tickets.find(ticket);
+  if (it == srv->tickets.end()) { set_error("unknown ticket %llu", (unsigned long long)ticket); return WMC_EUNKNOWN_TICKET; }
+  if (it->second.status == WMC_PENDING) return WMC_PENDING;
+  int st = it->second.status;
+  if (st == WMC_OK && out) *out = it->second.res;
+  if (done_ns) *done_ns = it->second.done_ns;
+  if (st != WMC_OK) set_error("the wave of ticket %llu failed", (unsigned long long)ticket);
+  srv->tickets.erase(it);
+  return st;
+}
+
+extern "C" int wmc_poll(wmc_server_t *srv, uint64_t ticket, wmc_result *out) {
+  if (!srv) { set_error("NULL argument"); return WMC_EINVAL; }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  return take_result(srv, ticket, out);
+}
+
+extern "C" int wmc_poll_ex(wmc_server_t *srv, uint64_t ticket, wmc_result *out, int64_t *done_ns) {
+  if (!srv) { set_error("NULL argument"); return WMC_EINVAL; }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  return take_result(srv, ticket, out, done_ns);
+}
+
+extern "C" int wmc_wait(wmc_server_t *srv, uint64_t ticket, int64_t timeout_us, wmc_result *out) {
+  if (!srv) { set_error("NULL argument"); return WMC_EINVAL; }
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+  for (;;) {
+    int rc = take_result(srv, ticket, out);
+    if (rc != WMC_PENDING) return rc;
+    if (srv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      rc = take_result(srv, ticket, out);
+      if (rc == WMC_PENDING) { set_error("timed out waiting for ticket"); return WMC_ETIMEOUT; }
+      return rc;
+    }
+  }
+}
+
+extern "C" int wmc_server_stats(wmc_server_t *srv, wmc_server_stats_t *out) {
+  if (!srv || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  std::lock_guard<std::mutex> lk(srv->mu);
+  *out = srv->stats;
+  out->mean_wave_q = srv->stats.waves ? srv->sum_q / (double)srv->stats.waves : 0.0;
+  return WMC_OK;
+}
+
+extern "C" void wmc_server_destroy(wmc_server_t *srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  if (srv->batcher.joinable()) srv->batcher.join();
+  for (auto &s : srv->slots) if (s.stream) cudaStreamSynchronize(s.stream);
+  srv->cv_comp.notify_all();
+  if (srv->completer.joinable()) srv->completer.join();
+  for (auto &s : srv->slots) free_slot(s);
+  delete srv;
+}

@@ -1,0 +1,341 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Tolerances (all weights nonnegative, so relative bounds apply):
+  * unweighted counts below 2^53: bit-exact;
+  * FP64 path: relative 1e-10 (the a-priori bound d * 2^-53 is far below);
+  * scaled-FP32 path: relative 1e-4, and never above the bound the library
+    states per result (gamma_d with u = 2^-24).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import wmcgen
+from oracle import Big
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+FP64, FP32 = 0, 1
+TOL = {FP64: 1e-10, FP32: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def w():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required")
+    import paper_2006_15512_b300 as lib
+    return lib
+
+
+def rel(res, big: Big) -> float:
+    return Big(res.mant, res.exp2).rel_diff(big)
+
+
+def plan_for(w, cnf, wp, wn, precision, **kw):
+    return w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=precision, **kw)
+
+
+# ------------------------------------------------------ random 3-CNF
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_3cnf_n20(w, precision, seed):
+    """Random 3-CNF, n=20, m=60, w(x)~U(0.1,0.9), w(~x)=1-w(x), vs brute
+    force over 2^20 assignments."""
+    cnf = wmcgen.random_kcnf(20, 60, seed=seed)
+    wp, wn = wmcgen.weights_complementary(20, seed, 0.1, 0.9)
+    want, _ = oracle.brute_force(cnf, wp, wn)
+    res = plan_for(w, cnf, wp, wn, precision).execute()[0]
+    r = rel(res, want)
+    assert r <= TOL[precision], r
+    assert r <= res.rel_err_bound + 1e-16
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_unweighted_bit_exact(w, seed):
+    """All weights 1: the FP64 path returns the exact model count."""
+    cnf = wmcgen.random_kcnf(20, 50, seed=10 + seed)
+    _, cnt = oracle.brute_force(cnf, *wmcgen.weights_unit(20))
+    for precision in (FP64, FP32):
+        res = plan_for(w, cnf, None, None, precision).execute()[0]
+        assert res.to_float() == float(cnt)
+        if precision == FP64:
+            assert res.flags & w.WMC_FLAG_EXACT_INT
+
+
+def test_closed_forms(w):
+    cases = []
+    cnf, _ = wmcgen.fig1_example()
+    cases.append((cnf, 7))
+    cases.append((wmcgen.psi_family(20), 2 ** 20 - 2))
+    cases.append((wmcgen.Cnf(60, []), 2 ** 60))
+    cases.append((wmcgen.chain_implication(1000), 1001))
+    cases.append((wmcgen.Cnf(3, [[1, 2], [], [3]]), 0))
+    cases.append((wmcgen.Cnf(0, []), 1))
+    cases.append((wmcgen.chain_or(300), None))
+    for cnf, want in cases:
+        if want is None:
+            want = oracle.count_exact(cnf, order=list(range(1, cnf.n_vars + 1)), max_width=4)
+        for precision in (FP64, FP32):
+            res = plan_for(w, cnf, None, None, precision).execute()[0]
+            if want == 0:
+                assert res.mant == 0.0
+                continue
+            got = Big(res.mant, res.exp2)
+            m, e = math.frexp(float(want))
+            r = got.rel_diff(Big(m, e))
+            if want < 2 ** 53 and precision == FP64:
+                assert r == 0.0, (cnf.n_vars, want, got)
+            else:
+                assert r <= TOL[precision], (cnf.n_vars, r)
+
+
+def test_psi_weighted(w):
+    n = 18
+    cnf = wmcgen.psi_family(n)
+    wp, wn = wmcgen.weights_independent(n, 3, 0.1, 0.9)
+    want = oracle.bucket_elim(cnf, wp, wn)
+    for precision in (FP64, FP32):
+        assert rel(plan_for(w, cnf, wp, wn, precision).execute()[0], want) <= TOL[precision]
+
+
+# ------------------------------------------------------ query batching
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_query_batch_matches_oracle_and_is_batch_invariant(w, precision):
+    cnf = wmcgen.random_kcnf(22, 70, seed=7)
+    plan = plan_for(w, cnf, None, None, precision)
+    wq, wnq = wmcgen.query_weights(22, 64, seed=8, lo=0.05, hi=0.95)
+    alone = [plan.execute(wq[i:i + 1], wnq[i:i + 1])[0] for i in range(64)]
+    for Q in (3, 8, 64):
+        batch = plan.execute(wq[:Q], wnq[:Q])
+        for i in range(Q):
+            assert (batch[i].mant, batch[i].exp2) == (alone[i].mant, alone[i].exp2)
+    for i in range(0, 64, 9):
+        want = oracle.bucket_elim(cnf, wq[i], wnq[i])
+        assert rel(alone[i], want) <= TOL[precision]
+
+
+def test_evidence_zero_weight(w):
+    """Evidence as a zero weight equals conditioning (Thm 4.2)."""
+    cnf = wmcgen.random_kcnf(16, 40, seed=3)
+    wp, wn = wmcgen.weights_complementary(16, 3, 0.1, 0.9)
+    wp0 = wp.copy(); wp0[5] = 0.0
+    want = oracle.bucket_elim(cnf, wp0, wn)
+    for precision in (FP64, FP32):
+        assert rel(plan_for(w, cnf, wp0, wn, precision).execute()[0], want) <= TOL[precision]
+
+
+def test_fp32_flush_is_flagged(w):
+    """A weight ratio beyond float32's range underflows a mantissa: the
+    result carries WMC_FLAG_FP32_FLUSH, FP64 stays exact-to-tolerance."""
+    cnf = wmcgen.random_kcnf(12, 30, seed=4)
+    wp, wn = wmcgen.weights_complementary(12, 4, 0.2, 0.8)
+    wn[2] = 1e-60
+    want = oracle.bucket_elim(cnf, wp, wn)
+    r32 = plan_for(w, cnf, wp, wn, FP32).execute()[0]
+    assert r32.flags & w.WMC_FLAG_FP32_FLUSH
+    r64 = plan_for(w, cnf, wp, wn, FP64).execute()[0]
+    assert rel(r64, want) <= TOL[FP64]
+
+
+# ------------------------------------------------------------ grids
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_grid_16x100(w, precision):
+    """16x100 grid (the serving network), value ~1e-300, below the float64
+    range for some seeds: per-tensor exponents keep it."""
+    H, W_ = 16, 100
+    cnf = wmcgen.grid_cnf(H, W_, 1)
+    wp, wn = wmcgen.weights_complementary(H * W_, 1, 0.05, 0.95)
+    col = [i * W_ + j + 1 for j in range(W_) for i in range(H)]
+    want = oracle.bucket_elim(cnf, wp, wn, order=col)
+    res = plan_for(w, cnf, wp, wn, precision).execute()[0]
+    assert rel(res, want) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_grid_24x200_full_size(w, precision):
+    """24x200 grid at full size (max-rank 25, 2^25-entry tensors) against
+    the stored oracle value."""
+    with open(os.path.join(GOLDEN, "grid_24x200.json")) as f:
+        g = json.load(f)
+    for v in g["values"][:1]:
+        seed = v["seed"]
+        cnf = wmcgen.grid_cnf(24, 200, seed)
+        wp, wn = wmcgen.weights_complementary(24 * 200, seed, 0.05, 0.95)
+        res = plan_for(w, cnf, wp, wn, precision).execute()[0]
+        assert rel(res, Big(v["mant"], v["exp2"])) <= TOL[precision]
+        assert res.log10 < -300
+
+
+# ------------------------------------------------ pairwise contraction
+
+def _dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype=dtype)
+
+
+def _pair_tol(k, precision):
+    if precision == FP64:
+        return 1e-12
+    d = (2 ** min(k, 8)) + (2 ** max(k - 8, 0)) + 4
+    return d * 2.0 ** -24 * 1.01
+
+
+SWEEP_SMALL = [(ra, rb, b, k) for (b, k) in [(0, 1), (2, 1), (4, 1), (0, 4), (2, 4), (4, 4),
+                                              (0, 8), (2, 8), (4, 8), (0, 16)]
+               for (ra, rb) in [(b + k + 3, b + k + 2), (b + k + 9, b + k + 1)]]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("ra,rb,b,k", SWEEP_SMALL)
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_pair_small(w, precision, ra, rb, b, k, shuffle):
+    """Every output of C = A . B against direct long-double summation."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=ra * 1000 + rb * 10 + b + k, shuffle=shuffle)
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c)
+    got = _run_pair(w, case, precision)
+    err = np.abs(got - want) / np.abs(want)
+    assert err.max() <= _pair_tol(k, precision), err.max()
+
+
+def _run_pair(w, case, precision, out_offsets=None):
+    rc = len(case.labels_c)
+    A64, B64 = _dev(case.a, torch.float64), _dev(case.b, torch.float64)
+    if precision == FP64:
+        C = torch.empty(1 << rc, dtype=torch.float64, device="cuda")
+        w.contract_pair(FP64, case.labels_a, A64, case.labels_b, B64, case.labels_c, C)
+        torch.cuda.synchronize()
+        out = C
+        scale = 1.0
+    else:
+        A = torch.empty(A64.numel(), dtype=torch.float32, device="cuda")
+        B = torch.empty(B64.numel(), dtype=torch.float32, device="cuda")
+        e = torch.zeros(3, dtype=torch.int64, device="cuda")
+        w.to_scaled_fp32(A64, A, e[0:1])
+        w.to_scaled_fp32(B64, B, e[1:2])
+        del A64, B64
+        C = torch.empty(1 << rc, dtype=torch.float32, device="cuda")
+        w.contract_pair(FP32, case.labels_a, A, case.labels_b, B, case.labels_c, C, e[0:1], e[1:2], e[2:3])
+        torch.cuda.synchronize()
+        assert int(e[2]) == int(e[0]) + int(e[1])
+        out = C.double()
+        scale = 2.0 ** int(e[2])
+    if out_offsets is not None:
+        idx = torch.from_numpy(np.asarray(out_offsets)).to("cuda")
+        return out[idx].cpu().numpy() * scale
+    return out.cpu().numpy() * scale
+
+
+SWEEP_FULL = [(29, 5, 2, 1), (30, 12, 4, 4), (30, 7, 0, 1), (24, 22, 0, 8), (22, 22, 0, 16)]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("ra,rb,b,k", SWEEP_FULL)
+def test_pair_full_size_sampled(w, precision, ra, rb, b, k):
+    """Full-size sweep cases (outputs up to 2^30): sampled outputs against
+    the oracle, which evaluates those entries one by one."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=7 + ra + rb + k, shuffle=False)
+    rc = len(case.labels_c)
+    offs = np.random.default_rng(0).integers(0, 1 << rc, size=48)
+    offs[0], offs[-1] = 0, (1 << rc) - 1
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c, offs)
+    got = _run_pair(w, case, precision, offs)
+    err = np.abs(got - want) / np.abs(want)
+    assert err.max() <= _pair_tol(k, precision), err.max()
+    torch.cuda.empty_cache()
+
+
+def test_pair_edge_cases(w):
+    """Rank-0 output (full inner product), no summed index (outer product),
+    a summed index present in one operand only."""
+    rng = np.random.default_rng(1)
+    for la, lb, lc in [([0, 1, 2], [2, 1, 0], []), ([0, 1], [2, 3], [3, 0, 2, 1]),
+                       ([0, 1, 5], [1, 2], [2, 0]), ([4], [], [4])]:
+        a = rng.random(1 << len(la)); b = rng.random(1 << len(lb))
+        case = wmcgen.PairCase(la, lb, lc, a, b)
+        want = oracle.contract_pair(la, a, lb, b, lc)
+        for precision in (FP64, FP32):
+            got = _run_pair(w, case, precision)
+            assert np.max(np.abs(got - want) / np.abs(want)) <= _pair_tol(3, precision)
+
+
+def test_pair_rejects_bad_labels(w):
+    A = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(w._abi.WmcError):
+        w.contract_pair(FP64, [0, 1], A, [1, 2], A, [0, 7], A)
+    with pytest.raises(w._abi.WmcError):
+        w.contract_pair(FP64, [0, 0], A, [1, 2], A, [0], A)
+
+
+# ------------------------------------------------- device path, server
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_execute_device_matches_host(w, precision):
+    cnf = wmcgen.grid_cnf(8, 40, 2)
+    plan = plan_for(w, cnf, None, None, precision)
+    Q = 16
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=5, lo=0.05, hi=0.95)
+    host = plan.execute(wq, wnq)
+    info = plan.info(Q)
+    ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device="cuda")
+    dwp, dwn = _dev(wq, torch.float64), _dev(wnq, torch.float64)
+    mant = torch.empty(Q, dtype=torch.float64, device="cuda")
+    ex = torch.empty(Q, dtype=torch.int64, device="cuda")
+    fl = torch.empty(Q, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        plan.execute_device(Q, dwp, dwn, ws, mant, ex, fl, stream=s)
+        torch.cuda.synchronize()
+        for q in range(Q):
+            m, e = math.frexp(float(mant[q]))
+            assert (m, e + int(ex[q])) == (host[q].mant, host[q].exp2)
+    with pytest.raises(w._abi.WmcError) as err:
+        plan.execute_device(Q, dwp, dwn, ws[: info.workspace_bytes // 2], mant, ex, fl, stream=s)
+    assert err.value.status == w.WMC_EINVAL
+
+
+def test_server_continuous_batching(w):
+    """Queries submitted in bursts while earlier waves run: each result is
+    identical to the same query run alone."""
+    import time
+    cnf = wmcgen.grid_cnf(10, 60, 3)
+    plan = plan_for(w, cnf, None, None, FP32)
+    n = 96
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, n, seed=6, lo=0.05, hi=0.95)
+    alone = [plan.execute(wq[i:i + 1], wnq[i:i + 1])[0] for i in range(n)]
+    srv = w.Server(plan, max_batch=32, max_waves=3)
+    tickets = []
+    for i in range(n):
+        tickets.append(srv.submit(wq[i], wnq[i]))
+        if i % 7 == 0:
+            time.sleep(0.002)
+    for i, t in enumerate(tickets):
+        r = srv.wait(t, timeout_s=60)
+        assert (r.mant, r.exp2) == (alone[i].mant, alone[i].exp2)
+    st = srv.stats()
+    assert st.completed == n and st.failed_waves == 0
+    assert st.waves >= 2
+    with pytest.raises(w._abi.WmcError) as e:
+        srv.poll(tickets[0])  # already consumed
+    assert e.value.status == w.WMC_EUNKNOWN_TICKET
+    srv.close()
+
+
+def test_alloc_failure_is_reported(w):
+    cnf = wmcgen.random_kcnf(14, 40, seed=9)
+    plan = plan_for(w, cnf, None, None, FP32)
+    w.wmc_debug_fail_next_allocs(1)
+    with pytest.raises(w._abi.WmcError) as e:
+        plan.execute()
+    assert e.value.status == w.WMC_ENOMEM
+    w.wmc_debug_fail_next_allocs(0)
+    plan2 = plan_for(w, cnf, None, None, FP32)
+    assert plan2.execute()[0].mant != 0.0

@@ -1,0 +1,196 @@
+"""Host-side tests of the C ABI library (no GPU needed): every declared
+symbol is exported, the reduction matches Thm 3.2's structure, the planner's
+contraction tree is a valid tree whose evaluation (done here in numpy, from
+the tree the library reports) equals the oracle, and malformed input is
+rejected with the documented status codes."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import wmcgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_2006_15512_b300 as w
+    return w
+
+
+def test_every_declared_symbol_is_exported():
+    w = _lib()
+    hdr = open(os.path.join(ROOT, "include", "wmc.h")).read()
+    declared = set(re.findall(r"\b(wmc_[a-z0-9_]+)\s*\(", hdr))
+    declared = {d for d in declared if not d.endswith("_t")}
+    out = subprocess.check_output(["nm", "-D", "--defined-only", w._abi.LIB_PATH]).decode()
+    exported = set(re.findall(r"\bT (wmc_[a-z0-9_]+)$", out, flags=re.M))
+    assert declared, "no declarations parsed"
+    assert declared <= exported, f"missing: {sorted(declared - exported)}"
+    assert declared <= set(w._abi.EXPORTS), f"binding lacks: {sorted(declared - set(w._abi.EXPORTS))}"
+
+
+def test_fig1_network_structure():
+    """Thm 3.2 on Fig. 1: 8 tensors, 10 indices."""
+    w = _lib()
+    cnf, _ = wmcgen.fig1_example()
+    info = w.Network.from_cnf(cnf).info()
+    assert info.n_tensors_strict == 8
+    assert info.n_indices_strict == 10
+    assert info.max_clause_rank == 3
+
+
+def _leaf_tensor(kind, labels, fals, wp, wn):
+    r = len(labels)
+    if kind == 0:
+        t = np.ones(1 << r)
+        t[fals] = 0.0
+    elif kind == 1:
+        x = labels[0]
+        t = np.array([wn[x], wp[x]])
+    else:
+        t = np.ones(1)
+    return t
+
+
+def _einsum_labels(labels, letters):
+    return "".join(letters.setdefault(l, chr(ord("a") + len(letters)) if len(letters) < 26
+                                      else chr(ord("A") + len(letters) - 26))
+                   for l in reversed(labels))
+
+
+def evaluate_plan_numpy(plan, wp, wn):
+    """Walk the library's contraction tree bottom-up with numpy (test-side
+    evaluation of Algorithm 2)."""
+    leaves = plan.leaves()
+    nodes = plan.nodes()
+    tens = []
+    labs = []
+    for kind, labels, fals in leaves:
+        tens.append(_leaf_tensor(kind, labels, fals, wp, wn))
+        labs.append(labels)
+    for a, b, lc in nodes:
+        letters = {}
+        ea, eb = _einsum_labels(labs[a], letters), _einsum_labels(labs[b], letters)
+        ec = _einsum_labels(lc, letters)
+        A = tens[a].reshape((2,) * len(labs[a]))
+        B = tens[b].reshape((2,) * len(labs[b]))
+        C = np.einsum(f"{ea},{eb}->{ec}", A, B)
+        tens.append(np.asarray(C).reshape(-1))
+        labs.append(lc)
+    assert len(labs[-1]) == 0
+    return float(tens[-1][0])
+
+
+def _check_tree_shape(plan):
+    """Every tensor id is consumed exactly once except the root; children
+    precede their parent (post-order)."""
+    n_leaves = plan.info(1).n_leaves
+    nodes = plan.nodes()
+    used = {}
+    for i, (a, b, _) in enumerate(nodes):
+        cid = n_leaves + i
+        assert a < cid and b < cid and a != b
+        used[a] = used.get(a, 0) + 1
+        used[b] = used.get(b, 0) + 1
+    total = n_leaves + len(nodes)
+    for t in range(total - 1):
+        assert used.get(t, 0) == 1, f"tensor {t} used {used.get(t, 0)} times"
+    assert used.get(total - 1, 0) == 0
+
+
+@pytest.mark.parametrize("ordering", [0, 1, 2, 3])
+@pytest.mark.parametrize("seed", range(5))
+def test_plan_tree_evaluates_to_oracle(ordering, seed):
+    """Thm 3.1: any valid plan gives W(phi); checked for every ordering."""
+    w = _lib()
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 15))
+    cnf = wmcgen.random_kcnf(n, int(rng.integers(n, 3 * n)), seed=seed)
+    wp, wn = wmcgen.weights_independent(n, seed, 0.1, 1.0)
+    net = w.Network.from_cnf(cnf, wp, wn)
+    plan = w.Plan(net, precision=0, ordering=ordering)
+    _check_tree_shape(plan)
+    got = evaluate_plan_numpy(plan, wp, wn)
+    want = oracle.brute_force(cnf, wp, wn)[0].to_float()
+    assert abs(got - want) <= 1e-13 * abs(want)
+
+
+@pytest.mark.parametrize("cnf", [
+    wmcgen.Cnf(0, []), wmcgen.Cnf(3, []), wmcgen.Cnf(2, [[]]), wmcgen.Cnf(3, [[1, -1], [2]]),
+    wmcgen.Cnf(4, [[1, 1, 2], [-2, 3]]), wmcgen.psi_family(6), wmcgen.Cnf(5, [[2, 3]]),
+], ids=["n0", "free3", "empty-clause", "tautology", "dup-literal", "psi6", "isolated-vars"])
+def test_plan_edge_cases(cnf):
+    w = _lib()
+    wp, wn = wmcgen.weights_independent(max(cnf.n_vars, 1), 9, 0.2, 1.3)
+    wp, wn = wp[:cnf.n_vars], wn[:cnf.n_vars]
+    net = w.Network.from_cnf(cnf, wp, wn)
+    plan = w.Plan(net, precision=0)
+    _check_tree_shape(plan)
+    got = evaluate_plan_numpy(plan, wp, wn)
+    want = oracle.brute_force(cnf, wp, wn)[0].to_float()
+    assert abs(got - want) <= 1e-13 * max(abs(want), 1e-300)
+
+
+def test_grid_plan_width():
+    """The order portfolio finds the sweep on the configs' grids: max-rank
+    25 on 24x200 and 17 on 16x100 (min-fill alone reaches 32+)."""
+    w = _lib()
+    for (H, W_, cap) in [(24, 200, 26), (16, 100, 18)]:
+        net = w.Network.from_cnf(wmcgen.grid_cnf(H, W_, 0))
+        info = w.Plan(net).info(1)
+        assert info.max_rank <= cap, (H, W_, info.max_rank)
+        with pytest.raises(w._abi.WmcError) as e:   # min-fill alone is far wider
+            w.Plan(net, ordering=1, max_rank_cap=cap + 2)
+        assert e.value.status == w.WMC_EPLAN_TOO_BIG
+
+
+def test_layouts_keep_big_operand_order():
+    """Layout rule: in each node the kept indices of the larger operand
+    keep their relative order in the output."""
+    w = _lib()
+    plan = w.Plan(w.Network.from_cnf(wmcgen.grid_cnf(6, 30, 1)))
+    labs = [l for _, l, _ in plan.leaves()]
+    for a, b, lc in plan.nodes():
+        P = labs[a] if len(labs[a]) >= len(labs[b]) else labs[b]
+        kept = [l for l in P if l in lc]
+        assert [l for l in lc if l in P] == kept
+        labs.append(lc)
+
+
+def test_invalid_inputs():
+    w = _lib()
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Network(3, np.array([1, 4], dtype=np.int32), np.array([0, 2]))
+    assert e.value.status == w.WMC_EINVAL
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Network(3, np.array([1, 0], dtype=np.int32), np.array([0, 2]))
+    assert e.value.status == w.WMC_EINVAL
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Network(3, np.array([1, 2], dtype=np.int32), np.array([0, 2, 1]))
+    assert e.value.status == w.WMC_EINVAL
+    net = w.Network.from_cnf(wmcgen.grid_cnf(16, 100, 0))
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net, max_rank_cap=10)
+    assert e.value.status == w.WMC_EPLAN_TOO_BIG
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net, mem_budget_bytes=1 << 20)
+    assert e.value.status == w.WMC_EPLAN_TOO_BIG
+    plan = w.Plan(net)
+    with pytest.raises(w._abi.WmcError) as e:
+        plan.info(0)
+    assert e.value.status == w.WMC_EINVAL
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net, order=[1] * net.n_vars)
+    assert e.value.status == w.WMC_EINVAL
+
+
+def test_workspace_grows_with_q():
+    w = _lib()
+    plan = w.Plan(w.Network.from_cnf(wmcgen.grid_cnf(16, 100, 0)))
+    a, b = plan.info(1), plan.info(256)
+    assert b.workspace_bytes > 100 * a.workspace_bytes
+    assert b.algorithmic_bytes > 200 * a.algorithmic_bytes
