@@ -88,6 +88,7 @@ namespace wmc {
 
 struct ExecState {
   int32_t Q = 1, m = 0;
+  int32_t Qp = 1;  // Q padded to 2^m: the query index is m bits
   bool f64 = false;
   std::vector<int64_t> t_off;   // byte offset of tensor data in the workspace
   std::vector<int64_t> t_meta;  // first metadata slot
@@ -313,6 +314,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
   st.m = m;
+  const int32_t Qp = 1 << m;
+  st.Qp = Qp;
   st.f64 = plan.precision == WMC_FP64;
   const size_t nt = plan.tensors.size();
   const int64_t root = plan.nodes.back().c;
@@ -331,14 +334,14 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
       return WMC_EPLAN_TOO_BIG;
     }
     bytes[i] = (int64_t(1) << r) * (st.t_dbl[i] ? 8 : 4);
-    st.t_qc[i] = t.has_q ? Q : 1;
+    st.t_qc[i] = t.has_q ? Qp : 1;
     st.t_meta[i] = slots;
     slots += st.t_qc[i];
   }
   st.n_slots = slots;
   int64_t off = 0;
   st.off_io = off; off += align_up(sizeof(IoDesc));
-  st.off_flags = off; off += align_up(4 * (int64_t)Q);
+  st.off_flags = off; off += align_up(4 * (int64_t)Qp);
   st.off_exp = off; off += align_up(8 * slots);
   st.off_max = off; off += align_up(8 * slots);
   // leaves: resident for the whole walk
@@ -402,7 +405,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     }
   }
   if (have_w) {
-    Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Q);
+    Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Qp);
     st.launches.push_back(l);
   }
   for (const Node &nd : plan.nodes) {
@@ -431,8 +434,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
           l.off_b = st.t_off[(size_t)(use_a ? nd.b : nd.a)];
           l.meta_a = st.t_meta[(size_t)(use_a ? nd.a : nd.b)];
           l.meta_b = st.t_meta[(size_t)(use_a ? nd.b : nd.a)];
-          l.k2.ma.qmask = (use_a ? A : B).has_q ? Q - 1 : 0;
-          l.k2.mb.qmask = (use_a ? B : A).has_q ? Q - 1 : 0;
+          l.k2.ma.qmask = (use_a ? A : B).has_q ? Qp - 1 : 0;
+          l.k2.mb.qmask = (use_a ? B : A).has_q ? Qp - 1 : 0;
           l.blocks = grid_for(1ull << p2.log2_nu);
         }
       }
@@ -448,16 +451,16 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
       l.off_b = st.t_off[(size_t)nd.b];
       l.meta_a = st.t_meta[(size_t)nd.a];
       l.meta_b = st.t_meta[(size_t)nd.b];
-      l.k1.ma.qmask = A.has_q ? Q - 1 : 0;
-      l.k1.mb.qmask = B.has_q ? Q - 1 : 0;
+      l.k1.ma.qmask = A.has_q ? Qp - 1 : 0;
+      l.k1.mb.qmask = B.has_q ? Qp - 1 : 0;
       l.blocks = grid_for(1ull << l.k1.rC);
     }
     l.off_c = st.t_off[(size_t)nd.c];
     l.meta_c = st.t_meta[(size_t)nd.c];
     l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
     dev::OutMeta &mc = l.kind == L_K2 ? l.k2.mc : l.k1.mc;
-    mc.Qc = C.has_q ? Q : 1;
-    mc.Q = Q;
+    mc.Qc = C.has_q ? Qp : 1;
+    mc.Q = Qp;
     mc.scale_inputs = 1;
     st.launches.push_back(l);
   }
@@ -549,10 +552,10 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
       case L_WEIGHTS:
         if (st.f64)
           dev::k_weight_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.d_woff, st.d_wmeta, (double *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, st.d_woff, st.d_wmeta, (double *)ws, mexp, mmax, flags);
         else
           dev::k_weight_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.d_woff, st.d_wmeta, (float *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, st.d_woff, st.d_wmeta, (float *)ws, mexp, mmax, flags);
         break;
       case L_ONE:
         if (st.f64) dev::k_one_leaf<double><<<1, 32, 0, s>>>((double *)(ws + l.one_off), l.one_meta, mexp, mmax);
@@ -577,7 +580,7 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         break;
       }
       case L_FINAL: {
-        const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Q : 1;
+        const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Qp : 1;
         dev::k_finalize<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
             io, (const double *)(ws + l.off_c), mexp + l.meta_c, root_qc, flags, st.Q);
         break;

@@ -411,18 +411,22 @@ struct IoDesc {
   int64_t pad[3];
 };
 
+// Q queries fill the Qp = 2^m query lanes; padding lanes repeat the last
+// query (their results are never read).
 template <typename T>
-__global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, const int64_t *off,
-                                const int64_t *meta, T *arena, int64_t *meta_exp,
-                                unsigned long long *meta_max, uint32_t *flags) {
+__global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int32_t Qp,
+                                const int64_t *off, const int64_t *meta, T *arena,
+                                int64_t *meta_exp, unsigned long long *meta_max,
+                                uint32_t *flags) {
   const double *w_pos = io->w_pos;
   const double *w_neg = io->w_neg;
-  const int64_t total = (int64_t)n_vars * Q;
+  const int64_t total = (int64_t)n_vars * Qp;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = (int32_t)(i / Q), q = (int32_t)(i % Q);
-    const double w1 = w_pos[(int64_t)q * n_vars + x];
-    const double w0 = w_neg[(int64_t)q * n_vars + x];
+    const int32_t x = (int32_t)(i / Qp), q = (int32_t)(i % Qp);
+    const int32_t qs = q < Q ? q : Q - 1;
+    const double w1 = w_pos[(int64_t)qs * n_vars + x];
+    const double w0 = w_neg[(int64_t)qs * n_vars + x];
     const double m = fmax(fabs(w0), fabs(w1));
     int e = 0;
     if (m > 0) {
@@ -433,7 +437,7 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, con
     const double s = __longlong_as_double((long long)(1023 - e) << 52);
     const T v0 = (T)(w0 * s), v1 = (T)(w1 * s);
     arena[off[x] + q] = v0;
-    arena[off[x] + Q + q] = v1;
+    arena[off[x] + Qp + q] = v1;
     if (((w0 * s != 0.0) && below_normal(v0)) || ((w1 * s != 0.0) && below_normal(v1)))
       atomicOr(flags + q, 2u);
     meta_exp[meta[x] + q] = e;
