@@ -186,6 +186,28 @@ int wmc_execute_device(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                        size_t workspace_bytes, double *d_mant,
                        int64_t *d_exp2, uint32_t *d_flags, void *stream);
 
+/* Allocation-free variant of wmc_execute_device (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory:
+ * code enqueuing work while a stream is being captured into a CUDA graph,
+ * serving loops that cannot afford the synchronisation or latency of
+ * cudaMalloc/cudaFree, and hosts whose device memory belongs to another
+ * allocator).  Same walk, kernels and results as wmc_execute_device, but
+ * the leaf tables and the workspace live in a fixed 32 MiB scratch array
+ * that is part of the library's device image (every GPU that loads the
+ * library holds it until exit).  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Plans whose tables plus workspace at this Q exceed
+ * 32 MiB are rejected with WMC_EINVAL (wmc_last_error gives the size).
+ * The first call on each device looks up the scratch's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one scratch array and the walk clears what it
+ * accumulates into, but calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race on it: serialise them.
+ * Inputs and outputs as for wmc_execute_device. */
+int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q,
+                               const double *d_w_pos, const double *d_w_neg,
+                               double *d_mant, int64_t *d_exp2,
+                               uint32_t *d_flags, void *stream);
+
 /* One pairwise contraction C = A . B (Eq. (1) on the network {A, B}; the
  * matrix-multiplication view of Sec. 4.2), on device memory, asynchronous on
  * `stream`.  Bit j of a tensor's linear offset is index labels_x[j];

@@ -101,6 +101,7 @@ EXPORTS = {
     "wmc_plan_leaf": (c_i32, [c_vp, c_i64, P(c_i32), P(c_i32), P(c_i32), P(c_u64)]),
     "wmc_execute": (c_i32, [c_vp, c_i32, P(c_dbl), P(c_dbl), c_vp, P(wmc_result)]),
     "wmc_execute_device": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_size, c_vp, c_vp, c_vp, c_vp]),
+    "wmc_execute_device_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_contract_pair": (c_i32, [c_i32, c_i32, P(c_i32), c_vp, c_i32, P(c_i32), c_vp, c_i32,
                                   P(c_i32), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_to_scaled_fp32": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),

@@ -527,8 +527,15 @@ static int ensure_dev(ExecState &st) {
 
 // Enqueues the whole walk on `s` for workspace `ws`.  With `events`, an
 // event is recorded after every launch (measurement only).
+struct LeafTables {
+  const ClauseLeaf *clause;
+  const int64_t *first, *woff, *wmeta;
+};
+
 static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
-                         cudaEvent_t *events = nullptr) {
+                         cudaEvent_t *events = nullptr, const LeafTables *tables = nullptr) {
+  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta};
+  const LeafTables &tb = tables ? *tables : own;
   int64_t *mexp = (int64_t *)(ws + st.off_exp);
   unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
   uint32_t *flags = (uint32_t *)(ws + st.off_flags);
@@ -542,20 +549,20 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
       case L_CLAUSES:
         if (st.f64)
           dev::k_clause_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              st.d_clause, st.d_first, (int64_t)st.h_clause.size(), st.n_clause_entries,
+              tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
               (double *)ws, mexp, mmax);
         else
           dev::k_clause_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              st.d_clause, st.d_first, (int64_t)st.h_clause.size(), st.n_clause_entries,
+              tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
               (float *)ws, mexp, mmax);
         break;
       case L_WEIGHTS:
         if (st.f64)
           dev::k_weight_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.Qp, st.d_woff, st.d_wmeta, (double *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (double *)ws, mexp, mmax, flags);
         else
           dev::k_weight_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.Qp, st.d_woff, st.d_wmeta, (float *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (float *)ws, mexp, mmax, flags);
         break;
       case L_ONE:
         if (st.f64) dev::k_one_leaf<double><<<1, 32, 0, s>>>((double *)(ws + l.one_off), l.one_meta, mexp, mmax);
@@ -964,6 +971,89 @@ extern "C" int wmc_to_scaled_fp32(const double *x, int64_t n, float *out, int64_
   dev::k_scale_to_f32<<<g, dev::kThreads, 0, s>>>(x, n, maxb, out);
   dev::k_max_to_exp<<<1, 1, 0, s>>>(maxb);
   g_launches.fetch_add(3);
+  CUDA_TRY(cudaGetLastError());
+  return WMC_OK;
+}
+
+// ------------------------------------------------- allocation-free variant
+//
+// Some callers cannot call cudaMalloc: code that enqueues work while a
+// stream is being captured into a CUDA graph (allocation is not a
+// capturable operation), serving loops that must not take the device-wide
+// synchronisation of a cudaMalloc/cudaFree or its latency spikes, and hosts
+// whose device memory is entirely owned by another allocator.  For them,
+// wmc_execute_device_noalloc runs the same walk on a fixed scratch array
+// that is part of this library's device image instead of on caller- or
+// library-allocated memory.
+
+// The scratch lives for as long as the library stays loaded, on every GPU
+// that uses it.  Host code must not take its address directly (that is a
+// host-side shadow); the device address comes from cudaGetSymbolAddress.
+static constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[256];  // device address of the scratch, per device
+
+static int noalloc_scratch(void **out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) { set_error("device id %d out of range", dev); return WMC_EINVAL; }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      return WMC_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return WMC_OK;
+}
+
+extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
+                                          const double *d_w_neg, double *d_mant, int64_t *d_exp2,
+                                          uint32_t *d_flags, void *stream) {
+  if (!plan || !d_mant || !d_exp2 || !d_flags) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  if (plan->n_vars > 0 && (!d_w_pos || !d_w_neg)) { set_error("weights are NULL"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);  // host-side layout only
+  if (rc) return rc;
+  // scratch layout: [leaf tables][workspace]
+  const size_t b_clause = sizeof(ClauseLeaf) * st->h_clause.size();
+  const size_t b_first = sizeof(int64_t) * st->h_first.size();
+  const size_t b_woff = sizeof(int64_t) * st->h_woff.size();
+  const size_t b_wmeta = sizeof(int64_t) * st->h_wmeta.size();
+  const size_t o_first = (size_t)align_up((int64_t)b_clause);
+  const size_t o_woff = o_first + (size_t)align_up((int64_t)b_first);
+  const size_t o_wmeta = o_woff + (size_t)align_up((int64_t)b_woff);
+  const size_t o_ws = o_wmeta + (size_t)align_up((int64_t)b_wmeta);
+  const size_t need = o_ws + (size_t)st->ws_bytes;
+  if (need > kNoAllocScratchBytes) {
+    set_error("this plan needs %zu bytes of scratch at Q = %d; the static scratch holds %zu",
+              need, Q, kNoAllocScratchBytes);
+    return WMC_EINVAL;
+  }
+  char *base = nullptr;
+  if ((rc = noalloc_scratch((void **)&base))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b_clause) CUDA_TRY(cudaMemcpyAsync(base, st->h_clause.data(), b_clause, cudaMemcpyHostToDevice, s));
+  if (b_first) CUDA_TRY(cudaMemcpyAsync(base + o_first, st->h_first.data(), b_first, cudaMemcpyHostToDevice, s));
+  if (b_woff) CUDA_TRY(cudaMemcpyAsync(base + o_woff, st->h_woff.data(), b_woff, cudaMemcpyHostToDevice, s));
+  if (b_wmeta) CUDA_TRY(cudaMemcpyAsync(base + o_wmeta, st->h_wmeta.data(), b_wmeta, cudaMemcpyHostToDevice, s));
+  char *ws = base + o_ws;
+  IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.w_pos = d_w_pos; io.w_neg = d_w_neg; io.mant = d_mant; io.exp2 = d_exp2; io.flags = d_flags;
+  CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+  const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
+                          (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta)};
+  // the walk's first launch zeroes the flags and metadata it accumulates into
+  enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
+  g_launches.fetch_add(st->kernels_per_run);
   CUDA_TRY(cudaGetLastError());
   return WMC_OK;
 }
