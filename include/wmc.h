@@ -62,10 +62,16 @@ extern "C" {
 /* wmc_result.flags */
 #define WMC_FLAG_EXACT_INT 0x1u      /* every weight was 1 and the count is
                                         below 2^53: mant*2^exp2 is exact     */
-#define WMC_FLAG_FP32_FLUSH 0x2u     /* a nonzero float32 term underflowed to
-                                        a subnormal or zero inside a tensor   */
+#define WMC_FLAG_FP32_FLUSH 0x2u     /* a float32 product of nonzero entries
+                                        may have underflowed (conservative:
+                                        set whenever the smallest nonzero
+                                        scaled operands' product is below the
+                                        smallest normal float)                */
 #define WMC_FLAG_NO_BOUND 0x4u       /* a weight was negative: rel_err_bound
                                         does not apply                        */
+#define WMC_FLAG_DEVICE_TIMEOUT 0x8u /* a bounded wait inside a kernel gave up;
+                                        the value is invalid (wmc_execute and
+                                        the server report WMC_ETIMEOUT)       */
 
 typedef struct wmc_network wmc_network_t;
 typedef struct wmc_plan wmc_plan_t;
@@ -273,8 +279,9 @@ void wmc_server_destroy(wmc_server_t *srv);
 /* Measurement: runs the walk of wmc_execute_device once WITHOUT the graph,
  * with a CUDA event after every launch, and synchronises `stream`.  For
  * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
- * kind[i] = 0 generic contraction, 1 streaming contraction, 2 leaf or
- * bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
+ * kind[i] = 0 generic contraction, 1 streaming contraction, 4 streaming
+ * contraction with TMA-staged operand, 2 leaf or bookkeeping kernel,
+ * 3 memset; alg_bytes[i] = the bytes a contraction
  * must move (|A| + |B| + |C| in its element type).  Returns the launch
  * count through *n_launches.  Same arguments and errors as
  * wmc_execute_device; creates and destroys its own events. */
@@ -285,12 +292,24 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                      float *node_ms, int32_t *kind, double *alg_bytes,
                      int64_t *n_launches);
 
+/* Host-side bounds check of the walk for batch size Q: replays the index
+ * arithmetic of every contraction launch (all bulk copies of every tile,
+ * the extreme and sampled per-thread offsets) on the CPU and verifies each
+ * access lies inside its tensor.  *n_checked (may be NULL) receives the
+ * number of work units checked.  WMC_EINVAL names the first violation. */
+int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_checked);
+
 /* ------------------------------------------------------------- misc */
 const char *wmc_last_error(void);
 /* Number of kernels this library launched since load (for accounting). */
 int64_t wmc_kernel_launch_count(void);
 /* Test hook: make the next n device allocations fail with WMC_ENOMEM. */
 void wmc_debug_fail_next_allocs(int32_t n);
+/* Test hook: while on != 0, the TMA-staged contraction kernel never issues
+ * its first tile's copy, so its bounded mbarrier wait runs out (about a
+ * second) and the call reports WMC_ETIMEOUT; no fault, trap or hang.
+ * Affects graphs captured while it is set. */
+void wmc_debug_stall_copies(int32_t on);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,7 @@ WMC_ORDER_GIVEN = 4
 WMC_FLAG_EXACT_INT = 0x1
 WMC_FLAG_FP32_FLUSH = 0x2
 WMC_FLAG_NO_BOUND = 0x4
+WMC_FLAG_DEVICE_TIMEOUT = 0x8
 
 c_i32 = ctypes.c_int32
 c_i64 = ctypes.c_int64
@@ -117,6 +118,8 @@ EXPORTS = {
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_kernel_launch_count": (c_i64, []),
     "wmc_debug_fail_next_allocs": (None, [c_i32]),
+    "wmc_debug_stall_copies": (None, [c_i32]),
+    "wmc_debug_check_bounds": (c_i32, [c_vp, c_i32, P(c_i64)]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

@@ -14,6 +14,8 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <cstdio>
+#include <cstdlib>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -30,9 +32,11 @@ namespace wmc { const Network &network_of(const wmc_network_t *n); }
 
 static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_fail_allocs{0};
+static std::atomic<int32_t> g_debug_stall{0};
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
+extern "C" void wmc_debug_stall_copies(int32_t on) { g_debug_stall.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -64,7 +68,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -74,11 +78,15 @@ struct Launch {
   int64_t blocks = 1;
   K1Params k1;
   K2Params k2;
+  wmc::dev::K2TParams k2t;
+  size_t smem = 0;
   // relative byte offsets (patched with the workspace base at capture)
   int64_t off_a = -1, off_b = -1, off_c = -1;
   int64_t meta_a = -1, meta_b = -1, meta_c = -1;  // slot indices
+  int64_t id_a = -1, id_b = -1, id_c = -1;        // tensor ids (A/P, B/S, C)
   int64_t one_off = -1, one_meta = -1;
   int64_t memset_off = 0, memset_bytes = 0;
+  int memset_value = 0;
   double alg_bytes = 0;  // contraction: |A| + |B| + |C| bytes
 };
 
@@ -94,7 +102,8 @@ struct ExecState {
   std::vector<int64_t> t_meta;  // first metadata slot
   std::vector<int32_t> t_qc;
   std::vector<uint8_t> t_dbl;
-  int64_t off_io = 0, off_flags = 0, off_exp = 0, off_max = 0, n_slots = 0;
+  std::vector<int64_t> t_bytes;
+  int64_t off_io = 0, off_flags = 0, off_err = 0, off_exp = 0, off_max = 0, off_min = 0, n_slots = 0;
   int64_t arena_bytes = 0, ws_bytes = 0;
   double alg_bytes = 0, flops = 0;
   int32_t max_roundings = 0;
@@ -236,7 +245,9 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   p.n_insC = (int)insC.size();
   for (size_t i = 0; i < insA.size(); ++i) p.insA[i] = (int8_t)insA[i];
   for (size_t i = 0; i < insC.size(); ++i) p.insC[i] = (int8_t)insC[i];
-  int nbb = 0;
+  // S batch bits (in P, S and C): lanes below vbits go to dBv, the rest
+  // are grouped into runs that are consecutive in both C and S
+  std::vector<std::pair<int, int>> bb;  // (C position, S position)
   for (size_t j = 0; j < LS.size(); ++j) {
     int32_t l = LS[j];
     int pc = pos_of(LC, l), pp = pos_of(LP, l);
@@ -245,12 +256,29 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
       for (int e = 0; e < (1 << vbits); ++e)
         if ((e >> pc) & 1) p.dBv[e] |= 1u << j;
     } else {
-      p.bbC[nbb] = (int8_t)pc;
-      p.bbB[nbb] = (int8_t)j;
-      ++nbb;
+      bb.push_back({pc, (int)j});
     }
   }
-  p.nbb = nbb;
+  std::sort(bb.begin(), bb.end());
+  int nseg = 0;
+  for (size_t i = 0; i < bb.size();) {
+    size_t j = i + 1;
+    while (j < bb.size() && bb[j].first == bb[j - 1].first + 1 && bb[j].second == bb[j - 1].second + 1) ++j;
+    if (nseg >= 16) return false;
+    p.seg_c[nseg] = (int8_t)bb[i].first;
+    p.seg_b[nseg] = (int8_t)bb[i].second;
+    p.seg_len[nseg] = (int8_t)(j - i);
+    ++nseg;
+    i = j;
+  }
+  p.n_seg = nseg;
+  // S lanes: 1 = contiguous (vector load), 2 = one value for all lanes
+  bool contiguous = true, broadcast = true;
+  for (int e = 0; e < (1 << vbits); ++e) {
+    contiguous &= (p.dBv[e] == (uint32_t)e);
+    broadcast &= (p.dBv[e] == 0u);
+  }
+  p.b_vec = contiguous ? 1 : (broadcast ? 2 : 0);
   for (int s = 0; s < (1 << k); ++s) {
     uint32_t da = 0, db = 0;
     for (int i = 0; i < k; ++i) {
@@ -276,6 +304,56 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   kmax = std::max(k, f) <= 1 ? 1 : (std::max(k, f) <= 2 ? 2 : 3);
   fmax = kmax;
   return true;
+}
+
+// Tiles for the TMA-staged variant of K2; false when the node is too
+// small or its lanes would not keep one query per thread.
+bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
+                bool f64, bool p_has_q, bool s_has_q, int32_t Qp, wmc::dev::K2TParams &tp,
+                size_t &smem) {
+  const int V = 1 << p2.vbits;
+  const int J = V == 1 ? 4 : 2;  // work units per thread per tile (<= kMaxJ)
+  int tb = 0;
+  while ((1 << tb) < dev::kThreads * V * J) ++tb;
+  const int total_w_log2 = p2.log2_nu + p2.vbits;
+  if (total_w_log2 < tb + 3) return false;
+  if (p_has_q && (dev::kThreads * V) % Qp != 0) return false;
+  if (LS.size() > 12) return false;  // S is staged in shared memory
+  std::vector<int> ins(p2.insA, p2.insA + p2.n_insA);
+  std::vector<int> kept;
+  for (int q = 0; q < (int)LP.size(); ++q)
+    if (std::find(ins.begin(), ins.end(), q) == ins.end()) kept.push_back(q);
+  if ((int)kept.size() < tb) return false;
+  const int top = kept[(size_t)tb - 1] + 1;
+  std::vector<int> low, high;
+  for (int q : ins) (q < top ? low : high).push_back(q);
+  std::memset(&tp, 0, sizeof(tp));
+  tp.k = p2;
+  tp.tb = tb;
+  tp.run_log2 = top;
+  tp.nruns = 1 << (int)high.size();
+  tp.n_lowA = (int)low.size();
+  tp.s_log2 = (int)LS.size();
+  // P's scale can be folded into the staged S when S's query bits are
+  // exactly P's (both carry the query index at their lowest positions)
+  tp.fold_sa = (p_has_q && s_has_q) ? 1 : 0;
+  for (size_t j = 0; j < low.size(); ++j) tp.lowA[j] = (int8_t)low[j];
+  for (int r = 0; r < tp.nruns; ++r) {
+    uint32_t o = 0;
+    for (size_t j = 0; j < high.size(); ++j)
+      if ((r >> j) & 1) o |= 1u << high[j];
+    tp.run_off[r] = o;
+  }
+  for (int s = 0; s < (1 << p2.k); ++s) {
+    const uint32_t da = p2.dA[s];
+    uint32_t r = 0;
+    for (size_t j = 0; j < high.size(); ++j)
+      if ((da >> high[j]) & 1) r |= 1u << j;
+    tp.sA_off[s] = (r << top) | (da & ((1u << top) - 1u));
+  }
+  const size_t es = f64 ? 8 : 4;
+  smem = (size_t)dev::kStages * ((size_t)tp.nruns << top) * es + (es << tp.s_log2);
+  return smem <= 160 * 1024;
 }
 
 void fill_k1(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
@@ -324,7 +402,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   st.t_qc.assign(nt, 1);
   st.t_dbl.assign(nt, st.f64 ? 1 : 0);
   st.t_dbl[(size_t)root] = 1;
-  std::vector<int64_t> bytes(nt);
+  std::vector<int64_t> &bytes = st.t_bytes;
+  bytes.assign(nt, 0);
   int64_t slots = 0;
   for (size_t i = 0; i < nt; ++i) {
     const TensorInfo &t = plan.tensors[i];
@@ -342,8 +421,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   int64_t off = 0;
   st.off_io = off; off += align_up(sizeof(IoDesc));
   st.off_flags = off; off += align_up(4 * (int64_t)Qp);
+  st.off_err = off; off += align_up(4);
   st.off_exp = off; off += align_up(8 * slots);
   st.off_max = off; off += align_up(8 * slots);
+  st.off_min = off; off += align_up(8 * slots);
   // leaves: resident for the whole walk
   for (int64_t i = 0; i < plan.n_leaves; ++i) { st.t_off[(size_t)i] = off; off += align_up(bytes[(size_t)i]); }
   const int64_t arena0 = off;
@@ -368,7 +449,13 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   ms.kind = L_MEMSET;
   ms.memset_off = st.off_flags;
   ms.memset_bytes = st.off_max + align_up(8 * slots) - st.off_flags;  // flags, exps, maxima
+  ms.memset_value = 0;
   st.launches.push_back(ms);
+  Launch ms1 = ms;
+  ms1.memset_off = st.off_min;  // minima start at "none" (all ones)
+  ms1.memset_bytes = align_up(8 * slots);
+  ms1.memset_value = 0xff;
+  st.launches.push_back(ms1);
   // clause leaves
   st.h_clause.clear(); st.h_first.clear();
   int64_t entries = 0;
@@ -434,9 +521,18 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
           l.off_b = st.t_off[(size_t)(use_a ? nd.b : nd.a)];
           l.meta_a = st.t_meta[(size_t)(use_a ? nd.a : nd.b)];
           l.meta_b = st.t_meta[(size_t)(use_a ? nd.b : nd.a)];
+          l.id_a = use_a ? nd.a : nd.b;
+          l.id_b = use_a ? nd.b : nd.a;
           l.k2.ma.qmask = (use_a ? A : B).has_q ? Qp - 1 : 0;
           l.k2.mb.qmask = (use_a ? B : A).has_q ? Qp - 1 : 0;
           l.blocks = grid_for(1ull << p2.log2_nu);
+          if (try_k2_tma(l.k2, use_a ? LA : LB, use_a ? LB : LA, st.f64, (use_a ? A : B).has_q,
+                         (use_a ? B : A).has_q, Qp, l.k2t, l.smem)) {
+            l.kind = L_K2T;
+            const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
+            const int per_sm = l.smem <= 80 * 1024 ? 2 : 1;
+            l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
+          }
         }
       }
     }
@@ -451,14 +547,17 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
       l.off_b = st.t_off[(size_t)nd.b];
       l.meta_a = st.t_meta[(size_t)nd.a];
       l.meta_b = st.t_meta[(size_t)nd.b];
+      l.id_a = nd.a;
+      l.id_b = nd.b;
       l.k1.ma.qmask = A.has_q ? Qp - 1 : 0;
       l.k1.mb.qmask = B.has_q ? Qp - 1 : 0;
       l.blocks = grid_for(1ull << l.k1.rC);
     }
     l.off_c = st.t_off[(size_t)nd.c];
     l.meta_c = st.t_meta[(size_t)nd.c];
+    l.id_c = nd.c;
     l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
-    dev::OutMeta &mc = l.kind == L_K2 ? l.k2.mc : l.k1.mc;
+    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : l.k2.mc;
     mc.Qc = C.has_q ? Qp : 1;
     mc.Q = Qp;
     mc.scale_inputs = 1;
@@ -496,6 +595,34 @@ static void launch_k2(const Launch &l, const K2Params &p, cudaStream_t s) {
   } else {
     if (l.v == 2) launch_k2_v<double, 2>(p, l.kmax, l.blocks, s);
     else launch_k2_v<double, 1>(p, l.kmax, l.blocks, s);
+  }
+}
+
+template <typename T, int V, int K>
+static void launch_k2t_t(const wmc::dev::K2TParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
+  static bool attr_set = false;  // opt in to large dynamic shared memory once
+  if (!attr_set) {
+    cudaFuncSetAttribute(dev::k2_tma<T, V, K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr_set = true;
+  }
+  dev::k2_tma<T, V, K, K><<<(unsigned)blocks, dev::kThreads + 32, smem, s>>>(p);
+}
+
+template <typename T, int V>
+static void launch_k2t_v(const wmc::dev::K2TParams &p, int kmax, int64_t blocks, size_t smem,
+                         cudaStream_t s) {
+  if (kmax <= 1) launch_k2t_t<T, V, 1>(p, blocks, smem, s);
+  else if (kmax == 2) launch_k2t_t<T, V, 2>(p, blocks, smem, s);
+  else launch_k2t_t<T, V, 3>(p, blocks, smem, s);
+}
+
+static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream_t s) {
+  if (l.ti == TF) {
+    if (l.v == 4) launch_k2t_v<float, 4>(p, l.kmax, l.blocks, l.smem, s);
+    else launch_k2t_v<float, 1>(p, l.kmax, l.blocks, l.smem, s);
+  } else {
+    if (l.v == 2) launch_k2t_v<double, 2>(p, l.kmax, l.blocks, l.smem, s);
+    else launch_k2t_v<double, 1>(p, l.kmax, l.blocks, l.smem, s);
   }
 }
 
@@ -538,58 +665,78 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
   const LeafTables &tb = tables ? *tables : own;
   int64_t *mexp = (int64_t *)(ws + st.off_exp);
   unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
+  unsigned long long *mmin = (unsigned long long *)(ws + st.off_min);
   uint32_t *flags = (uint32_t *)(ws + st.off_flags);
   const IoDesc *io = (const IoDesc *)(ws + st.off_io);
+  bool stall_armed = g_debug_stall.load() != 0;  // test hook: first staged launch only
   for (size_t li = 0; li < st.launches.size(); ++li) {
     const Launch &l = st.launches[li];
     switch (l.kind) {
       case L_MEMSET:
-        cudaMemsetAsync(ws + l.memset_off, 0, (size_t)l.memset_bytes, s);
+        cudaMemsetAsync(ws + l.memset_off, l.memset_value, (size_t)l.memset_bytes, s);
         break;
       case L_CLAUSES:
         if (st.f64)
           dev::k_clause_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
               tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
-              (double *)ws, mexp, mmax);
+              (double *)ws, mexp, mmax, mmin);
         else
           dev::k_clause_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
               tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
-              (float *)ws, mexp, mmax);
+              (float *)ws, mexp, mmax, mmin);
         break;
       case L_WEIGHTS:
         if (st.f64)
           dev::k_weight_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (double *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (double *)ws, mexp, mmax, mmin, flags);
         else
           dev::k_weight_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (float *)ws, mexp, mmax, flags);
+              io, plan.n_vars, st.Q, st.Qp, tb.woff, tb.wmeta, (float *)ws, mexp, mmax, mmin, flags);
         break;
       case L_ONE:
-        if (st.f64) dev::k_one_leaf<double><<<1, 32, 0, s>>>((double *)(ws + l.one_off), l.one_meta, mexp, mmax);
-        else dev::k_one_leaf<float><<<1, 32, 0, s>>>((float *)(ws + l.one_off), l.one_meta, mexp, mmax);
+        if (st.f64) dev::k_one_leaf<double><<<1, 32, 0, s>>>((double *)(ws + l.one_off), l.one_meta, mexp, mmax, mmin);
+        else dev::k_one_leaf<float><<<1, 32, 0, s>>>((float *)(ws + l.one_off), l.one_meta, mexp, mmax, mmin);
         break;
       case L_K1: {
         K1Params p = l.k1;
         p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
-        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a;
-        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b;
-        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.flags = flags;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
         launch_k1(l, p, s);
+        break;
+      }
+      case L_K2T: {
+        dev::K2TParams tp = l.k2t;
+        K2Params &p = tp.k;
+        p = l.k2;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
+        tp.err = (uint32_t *)(ws + st.off_err);
+        tp.debug_stall = stall_armed ? 1 : 0;
+        stall_armed = false;
+        launch_k2t(l, tp, s);
         break;
       }
       case L_K2: {
         K2Params p = l.k2;
         p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
-        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a;
-        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b;
-        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.flags = flags;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
         launch_k2(l, p, s);
         break;
       }
       case L_FINAL: {
         const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Qp : 1;
         dev::k_finalize<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
-            io, (const double *)(ws + l.off_c), mexp + l.meta_c, root_qc, flags, st.Q);
+            io, (const double *)(ws + l.off_c), mexp + l.meta_c, root_qc, flags,
+            (const uint32_t *)(ws + st.off_err), st.Q);
         break;
       }
     }
@@ -680,7 +827,7 @@ static void fill_result(const ExecState &st, double mant, int64_t e,
   r->mant = fr;
   r->exp2 = (mant == 0.0) ? 0 : e + fe;
   r->log10 = (mant == 0.0) ? -INFINITY : std::log10(std::fabs(fr)) + (double)r->exp2 * std::log10(2.0);
-  r->flags = flags & WMC_FLAG_FP32_FLUSH;
+  r->flags = flags & (WMC_FLAG_FP32_FLUSH | WMC_FLAG_DEVICE_TIMEOUT);
   const double u = st.f64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
   const double d = (double)st.max_roundings;
   r->rel_err_bound = d * u / (1.0 - d * u);
@@ -815,7 +962,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -872,6 +1019,11 @@ extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, c
   CUDA_TRY(cudaMemcpyAsync(st->h_res_exp, st->d_res_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(st->h_res_flags, st->d_res_flags, sizeof(uint32_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
+  for (int32_t q = 0; q < Q; ++q)
+    if (st->h_res_flags[q] & WMC_FLAG_DEVICE_TIMEOUT) {
+      set_error("a bounded wait inside a contraction kernel timed out; results discarded");
+      return WMC_ETIMEOUT;
+    }
   for (int32_t q = 0; q < Q; ++q)
     fill_result(*st, st->h_res_mant[q], st->h_res_exp[q], st->h_res_flags[q], unit, negative, out + q);
   return WMC_OK;
@@ -933,8 +1085,8 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
     use_a = (attempt == 0) == a_first;
     k2 = try_k2(use_a ? LA : LB, use_a ? LB : LA, LC, f64, p2, vmax, kmax, fmax);
   }
-  dev::Meta ma{exp_a, nullptr, 0}, mb{exp_b, nullptr, 0};
-  dev::OutMeta mc{exp_c, nullptr, nullptr, 1, 1, 0};
+  dev::Meta ma{exp_a, nullptr, nullptr, 0}, mb{exp_b, nullptr, nullptr, 0};
+  dev::OutMeta mc{exp_c, nullptr, nullptr, nullptr, 1, 1, 0};
   if (k2) {
     l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = vmax; l.kmax = kmax; l.fmax = fmax;
     l.blocks = grid_for(1ull << p2.log2_nu);
@@ -1055,5 +1207,127 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
   g_launches.fetch_add(st->kernels_per_run);
   CUDA_TRY(cudaGetLastError());
+  return WMC_OK;
+}
+
+// ------------------------------------------------------ host bounds check
+//
+// Replays, on the CPU, the index arithmetic of every contraction launch of
+// the walk for batch size Q (every bulk copy of every tile, and the
+// per-thread offsets of sampled work units including the first and last)
+// and checks each access against the tensor it touches.  Used by the CPU
+// test suite before kernels run on a GPU.
+namespace {
+inline uint32_t h_insert0(uint32_t x, int p) {
+  uint32_t lo = x & ((1u << p) - 1u);
+  return ((x >> p) << (p + 1)) | lo;
+}
+}  // namespace
+
+extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_checked) {
+  if (!plan) { set_error("NULL argument"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  int64_t checked = 0;
+  size_t li = 0;
+  for (const Launch &l : st->launches) {
+    ++li;
+    if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1) continue;
+    const int64_t ta = l.id_a, tb = l.id_b, tc = l.id_c;
+    if (ta < 0 || tb < 0 || tc < 0) { set_error("launch %zu: unknown tensor", li); return WMC_EINVAL; }
+    const int64_t es_in = l.kind == L_K1 ? (l.ti == TD ? 8 : 4) : (l.ti == TD ? 8 : 4);
+    const int64_t es_out = l.kind == L_K1 ? (l.to == TD ? 8 : 4) : es_in;
+    const int64_t na = st->t_bytes[(size_t)ta] / es_in, nb = st->t_bytes[(size_t)tb] / es_in,
+                  nc = st->t_bytes[(size_t)tc] / es_out;
+    auto bad = [&](const char *what, int64_t o, int64_t n) {
+      set_error("launch %zu: %s offset %lld outside [0, %lld)", li, what, (long long)o, (long long)n);
+      if (getenv("WMC_DEBUG_BOUNDS")) {
+        const K2Params &q = l.kind == L_K2T ? l.k2t.k : l.k2;
+        fprintf(stderr, "kind %d vbits %d log2_nu %d k %d f %d insA[%d]={%d,%d} insC[%d]={%d,%d} dC={%u,%u} dA={%u,%u} na %lld nb %lld nc %lld\n",
+                (int)l.kind, q.vbits, q.log2_nu, q.k, q.f, q.n_insA, q.insA[0], q.insA[1], q.n_insC, q.insC[0], q.insC[1], q.dC[0], q.dC[1], q.dA[0], q.dA[1],
+                (long long)na, (long long)nb, (long long)nc);
+      }
+      return WMC_EINVAL;
+    };
+    if (l.kind == L_K1) {
+      const K1Params &p = l.k1;
+      // the largest offsets: all bits set
+      int64_t ma = 0, mb = 0;
+      for (int j = 0; j < p.rC; ++j) {
+        if (p.posA[j] >= 0) ma |= 1ll << p.posA[j];
+        if (p.posB[j] >= 0) mb |= 1ll << p.posB[j];
+      }
+      for (int j = 0; j < p.k; ++j) {
+        if (p.sposA[j] >= 0) ma |= 1ll << p.sposA[j];
+        if (p.sposB[j] >= 0) mb |= 1ll << p.sposB[j];
+      }
+      if (ma >= na) return bad("A", ma, na);
+      if (mb >= nb) return bad("B", mb, nb);
+      if ((1ll << p.rC) > nc) return bad("C", (1ll << p.rC) - 1, nc);
+      ++checked;
+      continue;
+    }
+    const K2Params &p = l.kind == L_K2T ? l.k2t.k : l.k2;
+    const int V = 1 << p.vbits;
+    const uint64_t nu = 1ull << p.log2_nu;
+    std::vector<uint64_t> us;
+    if (nu <= (1u << 14)) for (uint64_t u = 0; u < nu; ++u) us.push_back(u);
+    else {
+      for (uint64_t u = 0; u < 4096; ++u) { us.push_back(u); us.push_back(nu - 1 - u); }
+      uint64_t x = 0x9e3779b97f4a7c15ull;
+      for (int i = 0; i < 8192; ++i) { x ^= x << 13; x ^= x >> 7; x ^= x << 17; us.push_back(x % nu); }
+    }
+    for (uint64_t u : us) {
+      const uint32_t w = (uint32_t)(u << p.vbits);
+      uint32_t oa = w, oc = w, gb = 0;
+      for (int i = 0; i < p.n_insA; ++i) oa = h_insert0(oa, p.insA[i]);
+      for (int i = 0; i < p.n_insC; ++i) oc = h_insert0(oc, p.insC[i]);
+      for (int i = 0; i < p.n_seg; ++i)
+        gb |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+      if ((oa % (uint32_t)V) || (oc % (uint32_t)V)) return bad("unaligned vector", oa, V);
+      for (int s = 0; s < (1 << p.k); ++s) {
+        const int64_t o = (int64_t)oa + p.dA[s] + V - 1;
+        if (o >= na) return bad("P", o, na);
+        for (int f = 0; f < (1 << p.f); ++f) {
+          for (int e = 0; e < V; ++e) {
+            const int64_t ob = (int64_t)gb + p.dBs[s] + p.dBf[f] + p.dBv[e];
+            if (ob >= nb) return bad("S", ob, nb);
+          }
+          const int64_t o2 = (int64_t)oc + p.dC[f] + V - 1;
+          if (o2 >= nc) return bad("C", o2, nc);
+        }
+      }
+      ++checked;
+    }
+    if (l.kind == L_K2T) {
+      const dev::K2TParams &tp = l.k2t;
+      const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
+      const int64_t run_len = 1ll << tp.run_log2;
+      const int64_t tile_elems = (int64_t)tp.nruns * run_len;
+      if ((int64_t)l.smem != tile_elems * dev::kStages * es_in + (es_in << tp.s_log2))
+        return bad("stage bytes", (int64_t)l.smem, tile_elems);
+      if ((1ll << tp.s_log2) != nb) return bad("staged S size", 1ll << tp.s_log2, nb);
+      for (uint64_t t = 0; t < n_tiles; ++t) {
+        uint32_t base = (uint32_t)(t << tp.tb);
+        for (int j = 0; j < p.n_insA; ++j) base = h_insert0(base, p.insA[j]);
+        for (int r = 0; r < tp.nruns; ++r) {
+          const int64_t lo = (int64_t)base + tp.run_off[r];
+          if (lo % 4 || lo + run_len > na) return bad("bulk copy", lo + run_len - 1, na);
+        }
+        ++checked;
+      }
+      // shared-memory reads of one tile (all local work units)
+      for (uint32_t wl = 0; wl < (1u << tp.tb); wl += (uint32_t)V) {
+        uint32_t la = wl;
+        for (int j = 0; j < tp.n_lowA; ++j) la = h_insert0(la, tp.lowA[j]);
+        for (int s = 0; s < (1 << p.k); ++s) {
+          const int64_t o = (int64_t)tp.sA_off[s] + la + V - 1;
+          if (o >= tile_elems) return bad("stage", o, tile_elems);
+        }
+      }
+    }
+  }
+  if (n_checked) *n_checked = checked;
   return WMC_OK;
 }

@@ -60,22 +60,89 @@ __device__ __forceinline__ uint32_t insert0(uint32_t x, int p) {
   return ((x >> p) << (p + 1)) | lo;
 }
 
-// Per-operand metadata: exponents and max bit patterns, one entry per
-// query if the tensor carries the query index (qmask = Q-1), else one.
+// Per-operand metadata, one entry per query if the tensor carries the
+// query index (qmask = Qp-1), else one: the exponent, and the IEEE bit
+// patterns of max|x| and of the smallest nonzero |x| (all-ones: none).
 struct Meta {
   const int64_t *exp;
   const unsigned long long *maxb;
+  const unsigned long long *minb;
   int32_t qmask;
 };
 
 struct OutMeta {
   int64_t *exp;
   unsigned long long *maxb;
-  uint32_t *flags;  // per query
-  int32_t Qc;       // entries of C's metadata (Q or 1)
-  int32_t Q;        // queries in the batch (flags entries)
+  unsigned long long *minb;
+  uint32_t *flags;       // per query lane
+  int32_t Qc;            // entries of C's metadata (Qp or 1)
+  int32_t Q;             // query lanes (flags entries)
   int32_t scale_inputs;  // 0: inputs are used as stored (contract_pair)
 };
+
+constexpr unsigned long long kNoMin = ~0ull;
+
+template <typename T> __device__ __forceinline__ T from_bits(unsigned long long b);
+template <> __device__ __forceinline__ float from_bits<float>(unsigned long long b) {
+  return __uint_as_float((uint32_t)b);
+}
+template <> __device__ __forceinline__ double from_bits<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+template <typename T>
+__device__ __forceinline__ T operand_scale(const Meta &m, int q, int scale_inputs) {
+  return scale_inputs ? pow2_scale(pow2_exp_of(m.maxb[q & m.qmask], T()), T()) : (T)1;
+}
+
+// Block epilogue: C's exponents (block 0), the per-query max and min of
+// |C| (atomics on the bit patterns), and the float32 flush test.  A flush
+// is possible only when the smallest nonzero scaled operands' product is
+// below the smallest normal number; with nonnegative terms no sum can then
+// be below it either, so the test is conservative and complete.
+template <typename T>
+__device__ __forceinline__ void finish_meta(const Meta &ma, const Meta &mb, const OutMeta &mc,
+                                            unsigned long long *smax, unsigned long long *smin) {
+  if (blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < mc.Qc; q += blockDim.x) {
+      const int qa = q & ma.qmask, qb = q & mb.qmask;
+      if (mc.exp) {
+        int64_t e = 0;
+        if (ma.exp) e += ma.exp[qa] + (mc.scale_inputs ? pow2_exp_of(ma.maxb[qa], T()) : 0);
+        if (mb.exp) e += mb.exp[qb] + (mc.scale_inputs ? pow2_exp_of(mb.maxb[qb], T()) : 0);
+        mc.exp[q] = e;
+      }
+      if (mc.flags && ma.minb && mb.minb && ma.minb[qa] != kNoMin && mb.minb[qb] != kNoMin) {
+        const T lo = (from_bits<T>(ma.minb[qa]) * operand_scale<T>(ma, qa, 1)) *
+                     (from_bits<T>(mb.minb[qb]) * operand_scale<T>(mb, qb, 1));
+        if (below_normal(lo)) {
+          if (mc.Qc > 1) atomicOr(mc.flags + q, 2u);
+          else
+            for (int qq = 0; qq < mc.Q; ++qq) atomicOr(mc.flags + qq, 2u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < mc.Qc; q += blockDim.x) {
+    if (mc.maxb && smax[q]) atomicMax(mc.maxb + q, smax[q]);
+    if (mc.minb && smin[q] != kNoMin) atomicMin(mc.minb + q, smin[q]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void track(T c, T &tmax, T &tmin) {
+  const T a = c < (T)0 ? -c : c;
+  tmax = a > tmax ? a : tmax;
+  tmin = (a != (T)0 && a < tmin) ? a : tmin;
+}
+
+template <typename T>
+__device__ __forceinline__ void publish(unsigned long long *smax, unsigned long long *smin, int q,
+                                        T tmax, T tmin) {
+  if (tmax != (T)0) atomicMax(smax + q, abs_bits(tmax));
+  if (tmin != (T)INFINITY) atomicMin(smin + q, abs_bits(tmin));
+}
 
 // ------------------------------------------------------------ K1 generic
 
@@ -93,44 +160,15 @@ struct K1Params {
   int8_t sposB[24];
 };
 
-template <typename T>
-__device__ __forceinline__ void finish_meta(const Meta &ma, const Meta &mb, const OutMeta &mc,
-                                            unsigned long long *smax, bool flush_any,
-                                            int qc_thread) {
-  // exponent of C: sum of both operands' effective exponents
-  if (blockIdx.x == 0 && mc.exp) {
-    for (int q = threadIdx.x; q < mc.Qc; q += blockDim.x) {
-      int64_t e = 0;
-      if (ma.exp) {
-        int qa = q & ma.qmask;
-        e += ma.exp[qa] + (mc.scale_inputs ? pow2_exp_of(ma.maxb[qa], T()) : 0);
-      }
-      if (mb.exp) {
-        int qb = q & mb.qmask;
-        e += mb.exp[qb] + (mc.scale_inputs ? pow2_exp_of(mb.maxb[qb], T()) : 0);
-      }
-      mc.exp[q] = e;
-    }
-  }
-  __syncthreads();
-  if (mc.maxb)
-    for (int q = threadIdx.x; q < mc.Qc; q += blockDim.x)
-      if (smax[q]) atomicMax(mc.maxb + q, smax[q]);
-  if (flush_any && mc.flags) {
-    if (mc.Qc > 1) atomicOr(mc.flags + qc_thread, 2u);
-    else
-      for (int q = 0; q < mc.Q; ++q) atomicOr(mc.flags + q, 2u);
-  }
-}
-
-// TI: stored type of A and B; TA: accumulation; TO: stored type of C.
-// The grid is sized so that the grid-stride step is a multiple of Qc, so
-// every thread sees one query for all its outputs.
+// Any bit mapping.  Offsets come from per-byte lookup tables built in
+// shared memory.  TI: stored type of A and B; TA: accumulation; TO: stored
+// type of C.  The grid-stride step is a multiple of Qc, so each thread
+// sees one query for all of its outputs.
 template <typename TI, typename TA, typename TO>
 __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
   __shared__ uint32_t lutA[4][256], lutB[4][256];
   __shared__ uint32_t slutA[3][256], slutB[3][256];
-  __shared__ unsigned long long smax[kMaxQ];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
     int byte = i >> 8, v = i & 255;
     uint32_t oa = 0, ob = 0;
@@ -157,24 +195,20 @@ __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
     slutA[byte][v] = oa;
     slutB[byte][v] = ob;
   }
-  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) smax[q] = 0;
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
   __syncthreads();
 
   const uint64_t n_out = 1ull << p.rC;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int qc = (int)(gtid & (uint64_t)(p.mc.Qc - 1));
-  TA sa = (TA)1, sb = (TA)1;
-  if (p.mc.scale_inputs) {
-    sa = (TA)pow2_scale(pow2_exp_of(p.ma.maxb[qc & p.ma.qmask], TI()), TI());
-    sb = (TA)pow2_scale(pow2_exp_of(p.mb.maxb[qc & p.mb.qmask], TI()), TI());
-  }
+  const TA sa = (TA)operand_scale<TI>(p.ma, qc, p.mc.scale_inputs);
+  const TA sb = (TA)operand_scale<TI>(p.mb, qc, p.mc.scale_inputs);
   const TI *A = (const TI *)p.A;
   const TI *B = (const TI *)p.B;
   TO *C = (TO *)p.C;
   const uint32_t ns = 1u << p.k;
-  unsigned long long tmax = 0;
-  bool flush = false;
+  TO tmax = (TO)0, tmin = (TO)INFINITY;
   for (uint64_t o = gtid; o < n_out; o += stride) {
     const uint32_t oo = (uint32_t)o;
     const uint32_t ba = lutA[0][oo & 255] | lutA[1][(oo >> 8) & 255] | lutA[2][(oo >> 16) & 255] |
@@ -182,12 +216,10 @@ __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
     const uint32_t bb = lutB[0][oo & 255] | lutB[1][(oo >> 8) & 255] | lutB[2][(oo >> 16) & 255] |
                         lutB[3][oo >> 24];
     TA acc = (TA)0;
-    bool nz = false;
     if (p.k <= 8) {
       for (uint32_t s = 0; s < ns; ++s) {
         const TA a = (TA)__ldg(A + (ba | slutA[0][s])) * sa;
         const TA b = (TA)__ldg(B + (bb | slutB[0][s])) * sb;
-        nz |= (a != (TA)0) & (b != (TA)0);
         acc = fma_t(a, b, acc);
       }
     } else {
@@ -199,7 +231,6 @@ __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
         for (uint32_t lo = 0; lo < 256; ++lo) {
           const TA a = (TA)__ldg(A + (ha | slutA[0][lo])) * sa;
           const TA b = (TA)__ldg(B + (hb | slutB[0][lo])) * sb;
-          nz |= (a != (TA)0) & (b != (TA)0);
           part = fma_t(a, b, part);
         }
         acc += part;
@@ -207,12 +238,11 @@ __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
     }
     const TO c = (TO)acc;
     C[o] = c;
-    const unsigned long long bits = abs_bits(c);
-    tmax = bits > tmax ? bits : tmax;
-    flush |= nz && below_normal(c);
+    track(c, tmax, tmin);
   }
-  if (tmax) atomicMax(smax + qc, tmax);
-  finish_meta<TI>(p.ma, p.mb, p.mc, smax, __syncthreads_or(flush), qc);
+  publish(smax, smin, qc, tmax, tmin);
+  __syncthreads();
+  finish_meta<TI>(p.ma, p.mb, p.mc, smax, smin);
 }
 
 // ------------------------------------------------------------ K2 stream
@@ -233,11 +263,13 @@ struct K2Params {
   int32_t log2_nu;  // work units
   int32_t vbits;    // log2 V
   int32_t k, f;     // summed bits, free bits of S
-  int32_t n_insA, n_insC, nbb;
-  int8_t insA[8];   // ascending positions of summed bits in P
-  int8_t insC[8];   // ascending positions of S's free bits in C
-  int8_t bbC[32];   // S batch bit i: position in C
-  int8_t bbB[32];   //               position in S
+  int32_t n_insA, n_insC, n_seg;
+  int32_t b_vec;      // S lanes: 0 per-lane loads, 1 contiguous, 2 broadcast
+  int8_t insA[4];     // ascending positions of summed bits in P
+  int8_t insC[4];     // ascending positions of S's free bits in C
+  int8_t seg_c[16];   // S batch bits as runs: C position of the run's low bit,
+  int8_t seg_b[16];   //   S position of the run's low bit,
+  int8_t seg_len[16]; //   run length (C vector lanes excluded)
   uint32_t dA[8];   // offset of summed assignment s in P
   uint32_t dBs[8];  // ... in S
   uint32_t dBf[8];  // offset of S-free assignment f in S
@@ -273,9 +305,9 @@ __device__ __forceinline__ void vstore(T *p, const T (&r)[V]) {
 // K (summed bits) and F (S-free bits) are compile-time upper bounds; the
 // runtime p.k / p.f select the active terms.
 template <typename T, int V, int K, int F>
-__global__ void __launch_bounds__(kThreads) k2_stream(K2Params p) {
-  __shared__ unsigned long long smax[kMaxQ];
-  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) smax[q] = 0;
+__global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 ? 2 : 1))) k2_stream(K2Params p) {
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
   __syncthreads();
   constexpr int NS = 1 << K, NF = 1 << F;
   const int ns = 1 << p.k, nf = 1 << p.f;
@@ -285,81 +317,374 @@ __global__ void __launch_bounds__(kThreads) k2_stream(K2Params p) {
   const uint64_t nu = 1ull << p.log2_nu;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  T sa[V], sb[NF][V];
-  unsigned long long tmax[NF][V];
-  int qcs[NF][V];
-  bool flush = false;
-  bool first = true;
+  const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
+  T sa[V], sb[NF][V], tmax[NF][V], tmin[NF][V];
+  uint32_t qbase = 0;
 #pragma unroll
   for (int f = 0; f < NF; ++f)
 #pragma unroll
-    for (int e = 0; e < V; ++e) tmax[f][e] = 0, qcs[f][e] = 0;
+    for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tmin[f][e] = (T)INFINITY; sb[f][e] = (T)1; }
+#pragma unroll
+  for (int e = 0; e < V; ++e) sa[e] = (T)1;
+  bool first = true;
   for (uint64_t u = gtid; u < nu; u += stride) {
-    const uint32_t w = (uint32_t)(u << p.vbits);
+    const uint32_t w = (uint32_t)u << p.vbits;
     uint32_t oa = w, oc = w, gb = 0;
-    for (int i = 0; i < p.n_insA; ++i) oa = insert0(oa, p.insA[i]);
-    for (int i = 0; i < p.n_insC; ++i) oc = insert0(oc, p.insC[i]);
-    for (int i = 0; i < p.nbb; ++i) gb |= ((oc >> p.bbC[i]) & 1u) << p.bbB[i];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < p.n_insA) oa = insert0(oa, p.insA[i]);
+#pragma unroll
+    for (int i = 0; i < F; ++i)
+      if (i < p.n_insC) oc = insert0(oc, p.insC[i]);
+    for (int i = 0; i < p.n_seg; ++i)
+      gb |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
     if (first) {
-      // the query of every lane is fixed across the grid-stride loop
+      // each lane's query is fixed across the grid-stride loop (the stride
+      // is a multiple of the query lanes)
       first = false;
+      qbase = oc;
+      if (p.mc.scale_inputs) {
 #pragma unroll
-      for (int e = 0; e < V; ++e) {
-        sa[e] = (T)1;
-        if (p.mc.scale_inputs)
-          sa[e] = pow2_scale(pow2_exp_of(p.ma.maxb[(oa + e) & p.ma.qmask], T()), T());
+        for (int e = 0; e < V; ++e) {
+          sa[e] = operand_scale<T>(p.ma, (int)(oa + e), 1);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          sb[f][e] = (T)1;
-          if (f < nf) {
-            if (p.mc.scale_inputs)
-              sb[f][e] = pow2_scale(
-                  pow2_exp_of(p.mb.maxb[(gb + p.dBf[f] + p.dBv[e]) & p.mb.qmask], T()), T());
-            qcs[f][e] = (int)((oc + p.dC[f] + e) & (uint32_t)(p.mc.Qc - 1));
-          }
+          for (int f = 0; f < NF; ++f)
+            if (f < nf) sb[f][e] = operand_scale<T>(p.mb, (int)(gb + p.dBf[f] + p.dBv[e]), 1);
         }
       }
     }
     T a[NS][V];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NS; ++s)
       if (s < ns) {
         vload<T, V>(A + oa + p.dA[s], a[s]);
 #pragma unroll
         for (int e = 0; e < V; ++e) a[s][e] *= sa[e];
       }
-    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (f < nf) {
         T c[V];
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-          T acc = (T)0;
-          bool nz = false;
+        for (int e = 0; e < V; ++e) c[e] = (T)0;
 #pragma unroll
-          for (int s = 0; s < NS; ++s) {
-            if (s < ns) {
-              const T b = __ldg(B + (gb + p.dBs[s] + p.dBf[f] + p.dBv[e])) * sb[f][e];
-              nz |= (a[s][e] != (T)0) & (b != (T)0);
-              acc = fma_t(a[s][e], b, acc);
+        for (int s = 0; s < NS; ++s) {
+          if (s < ns) {
+            T b[V];
+            const uint32_t ob = gb + p.dBs[s] + p.dBf[f];
+            if (V > 1 && p.b_vec == 1) {
+              vload<T, V>(B + ob, b);
+            } else if (p.b_vec == 2) {
+              const T v = __ldg(B + ob);
+#pragma unroll
+              for (int e = 0; e < V; ++e) b[e] = v;
+            } else {
+#pragma unroll
+              for (int e = 0; e < V; ++e) b[e] = __ldg(B + ob + p.dBv[e]);
             }
+#pragma unroll
+            for (int e = 0; e < V; ++e) c[e] = fma_t(a[s][e], b[e] * sb[f][e], c[e]);
           }
-          c[e] = acc;
-          const unsigned long long bits = abs_bits(acc);
-          tmax[f][e] = bits > tmax[f][e] ? bits : tmax[f][e];
-          flush |= nz && below_normal(acc);
         }
         vstore<T, V>(C + oc + p.dC[f], c);
+#pragma unroll
+        for (int e = 0; e < V; ++e) track(c[e], tmax[f][e], tmin[f][e]);
       }
     }
   }
+  if (!first) {
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (f < nf) publish(smax, smin, (int)((qbase + p.dC[f] + e) & qmask_c), tmax[f][e], tmin[f][e]);
+  }
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
+// ------------------------------------------------- K2 with TMA staging
+//
+// Same contraction as k2_stream, but P is brought on chip by bulk async
+// copies (cp.async.bulk, the TMA engine) into a ring of shared-memory
+// stages guarded by mbarriers: one elected thread keeps kStages tiles in
+// flight while every thread computes the current tile, so HBM latency is
+// hidden by the copy engine rather than by warps.  A tile is 2^tb
+// consecutive assignments w of P's kept indices; its P data are nruns
+// contiguous runs of 2^run_log2 elements (one per assignment of the summed
+// indices that lie above the tile's bit range).
+//
+// Bit deposits are linear over disjoint bits, so every offset splits into
+// a per-tile part (computed once per tile by the issuing thread) and a
+// per-thread part (computed once per launch): the inner loop only ORs.  S
+// is small: each block stages it in shared memory already multiplied by
+// its per-query scale.
+//
+// Every mbarrier wait is bounded by %globaltimer (about one second): on
+// timeout the block records an error word, drains its own copies (again
+// bounded) and returns.
+
+struct K2TParams {
+  K2Params k;           // mapping shared with k2_stream
+  int32_t tb;           // log2 tile size (in w)
+  int32_t run_log2;     // log2 elements per run
+  int32_t nruns;
+  int32_t n_lowA;       // summed positions of P inside the tile's span
+  int8_t lowA[4];
+  int32_t s_log2;       // log2 elements of S (staged in shared memory)
+  int32_t fold_sa;      // S carries P's query lanes: P's scale is folded into S
+  uint32_t run_off[8];  // P offset of run r (high summed bits)
+  uint32_t sA_off[8];   // shared-memory offset of summed assignment s
+  uint32_t *err;        // error word (bit 0: an mbarrier wait timed out)
+  int32_t debug_stall;  // test hook: never issue the first tile's copy
+};
+
+constexpr int kStages = 4;
+constexpr int kMaxJ = 4;                        // work units per thread per tile
+constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of one wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// wait bounded in time; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void track_fast(T c, T &tmax, T &tmin) {
+  const T a = fabs(c);
+  tmax = fmax(tmax, a);
+  tmin = fmin(tmin, a != (T)0 ? a : (T)INFINITY);
+}
+
+constexpr int kConsumerWarps = kThreads / 32;
+
+// Warp-specialised: warps 0..kConsumerWarps-1 compute, the last warp's
+// lane 0 produces.  full[st] completes when a tile's bytes have landed
+// (arrive.expect_tx + complete_tx); empty[st] completes when every consumer
+// warp has finished reading the stage.  No block-wide barrier in the loop.
+template <typename T, int V, int K, int F>
+__global__ void __launch_bounds__(kThreads + 32, (K <= 2 ? 2 : 1)) k2_tma(K2TParams tp) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ uint32_t tile_oc[kStages], tile_gb[kStages];
+  __shared__ int s_skip;
+  const K2Params &p = tp.k;
+  if (threadIdx.x == 0) s_skip = (tp.err && *(volatile uint32_t *)tp.err) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;  // an earlier launch of this walk gave up: skip the work
+  const uint32_t run_len = 1u << tp.run_log2;
+  const uint32_t tile_elems = (uint32_t)tp.nruns * run_len;
+  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
+  const uint32_t T_w = 1u << tp.tb;
+  const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
+  T *stage_buf = reinterpret_cast<T *>(dyn_smem);
+  T *sS = stage_buf + (size_t)kStages * tile_elems;  // S, pre-scaled
+  const T *A = (const T *)p.A;
+  const T *B = (const T *)p.B;
+  T *C = (T *)p.C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nthr = kConsumerWarps * 32;
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  // stage S, multiplied by its own scale and, when S carries every query
+  // lane of P (tp.fold_sa), by P's scale too: both are exact powers of two
+  const uint32_t n_s = 1u << tp.s_log2;
+  for (uint32_t j = threadIdx.x; j < n_s; j += blockDim.x) {
+    T v = B[j] * operand_scale<T>(p.mb, (int)j, p.mc.scale_inputs);
+    if (tp.fold_sa) v *= operand_scale<T>(p.ma, (int)j, p.mc.scale_inputs);
+    sS[j] = v;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto tile_of = [&](uint64_t i) { return (uint64_t)blockIdx.x + i * gridDim.x; };
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint64_t i = 0;
+      bool ok = true;
+      for (; tile_of(i) < n_tiles; ++i) {
+        const int st = (int)(i % kStages);
+        if (i >= (uint64_t)kStages && !mbar_wait(&empty[st], (uint32_t)(((i / kStages) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const uint32_t bw = (uint32_t)(tile_of(i) << tp.tb);
+        uint32_t base = bw, oc = bw, gb = 0;
+        for (int j = 0; j < p.n_insA; ++j) base = insert0(base, p.insA[j]);
+        for (int j = 0; j < p.n_insC; ++j) oc = insert0(oc, p.insC[j]);
+        for (int j = 0; j < p.n_seg; ++j)
+          gb |= ((oc >> p.seg_c[j]) & ((1u << p.seg_len[j]) - 1u)) << p.seg_b[j];
+        tile_oc[st] = oc;
+        tile_gb[st] = gb;
+        fence_proxy_async_smem();
+        mbar_expect_tx(&full[st], tile_bytes);  // release: tile_oc/gb visible
+        if (tp.debug_stall && i == 0) continue;  // test hook: the wait must run out
+        for (int r = 0; r < tp.nruns; ++r)
+          bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len,
+                   A + base + tp.run_off[r], run_len * (uint32_t)sizeof(T), &full[st]);
+      }
+      if (!ok && tp.err) atomicOr(tp.err, 1u);
+      // drain: copies of the last kStages issued tiles may still be in flight
+      const uint64_t n_issued = i;
+      for (uint64_t j = n_issued > (uint64_t)kStages ? n_issued - kStages : 0; j < n_issued; ++j)
+        if (!mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1)) && tp.err)
+          atomicOr(tp.err, 1u);
+    }
+    __syncwarp();  // the producer warp reconverges before the block barrier
+  } else {
+    // ----------------------------------------------------------- consumers
+    constexpr int NS = 1 << K, NF = 1 << F;
+    const int ns = 1 << p.k, nf = 1 << p.f;
+    const int J = (int)(T_w / (uint32_t)(nthr * V));
+    uint32_t la[kMaxJ], ocl[kMaxJ], gbl[kMaxJ];
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      const uint32_t wl = (threadIdx.x + (uint32_t)j * nthr) * V;
+      uint32_t a = wl, c = wl, g = 0;
+      for (int i = 0; i < tp.n_lowA; ++i) a = insert0(a, tp.lowA[i]);
+      for (int i = 0; i < p.n_insC; ++i) c = insert0(c, p.insC[i]);
+      for (int i = 0; i < p.n_seg; ++i)
+        g |= ((c >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+      la[j] = a; ocl[j] = c; gbl[j] = g;
+    }
+    // each lane's query is the same in every tile
+    T sa[V];
 #pragma unroll
     for (int e = 0; e < V; ++e)
-      if (tmax[f][e]) atomicMax(smax + qcs[f][e], tmax[f][e]);
-  finish_meta<T>(p.ma, p.mb, p.mc, smax, __syncthreads_or(flush), qcs[0][0]);
+      sa[e] = tp.fold_sa ? (T)1 : operand_scale<T>(p.ma, (int)(threadIdx.x * V + e), p.mc.scale_inputs);
+    T tmax[NF][V], tmin[NF][V];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tmin[f][e] = (T)INFINITY; }
+    for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
+      const int st = (int)(i % kStages);
+      // every lane waits (acquire), the warp agrees on the outcome
+      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / kStages) & 1)));
+      if (!landed) {
+        if (lane == 0 && tp.err) atomicOr(tp.err, 1u);
+        break;
+      }
+      const T *tile = stage_buf + (size_t)st * tile_elems;
+      const uint32_t ocb = tile_oc[st], gbb = tile_gb[st];
+#pragma unroll
+      for (int j = 0; j < kMaxJ; ++j) {
+        if (j < J) {
+          const uint32_t oc = ocb | ocl[j], gb = gbb | gbl[j];
+          T a[NS][V];
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            if (s < ns) {
+              typedef typename VecT<T, V>::t VT;
+              const VT v = *reinterpret_cast<const VT *>(tile + tp.sA_off[s] + la[j]);
+              const T *ev = reinterpret_cast<const T *>(&v);
+#pragma unroll
+              for (int e = 0; e < V; ++e) a[s][e] = ev[e] * sa[e];
+            }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            if (f < nf) {
+              T c[V];
+#pragma unroll
+              for (int e = 0; e < V; ++e) c[e] = (T)0;
+#pragma unroll
+              for (int s = 0; s < NS; ++s) {
+                if (s < ns) {
+                  T b[V];
+                  const uint32_t ob = gb + p.dBs[s] + p.dBf[f];
+                  if (V > 1 && p.b_vec == 1) {
+                    typedef typename VecT<T, V>::t VT;
+                    const VT v = *reinterpret_cast<const VT *>(sS + ob);
+                    const T *ev = reinterpret_cast<const T *>(&v);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) b[e] = ev[e];
+                  } else if (p.b_vec == 2) {
+                    const T v = sS[ob];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) b[e] = v;
+                  } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) b[e] = sS[ob + p.dBv[e]];
+                  }
+#pragma unroll
+                  for (int e = 0; e < V; ++e) c[e] = fma_t(a[s][e], b[e], c[e]);
+                }
+              }
+              vstore<T, V>(C + oc + p.dC[f], c);
+#pragma unroll
+              for (int e = 0; e < V; ++e) track_fast(c[e], tmax[f][e], tmin[f][e]);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        if (f < nf) publish(smax, smin, (int)((ocl[0] + p.dC[f] + e) & qmask_c), tmax[f][e], tmin[f][e]);
+  }
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
 // --------------------------------------------------------------- leaves
@@ -378,7 +703,7 @@ struct ClauseLeaf {
 template <typename T>
 __global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, int64_t n_leaves,
                                 int64_t n_entries, T *arena, int64_t *meta_exp,
-                                unsigned long long *meta_max) {
+                                unsigned long long *meta_max, unsigned long long *meta_min) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_entries;
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t lo = 0, hi = n_leaves - 1;
@@ -393,6 +718,7 @@ __global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, 
       meta_exp[L.meta] = 0;
       // max is 1 unless the tensor is the rank-0 empty clause (value 0)
       meta_max[L.meta] = (L.rank == 0) ? 0ull : abs_bits((T)1);
+      meta_min[L.meta] = (L.rank == 0) ? kNoMin : abs_bits((T)1);
     }
   }
 }
@@ -417,7 +743,7 @@ template <typename T>
 __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int32_t Qp,
                                 const int64_t *off, const int64_t *meta, T *arena,
                                 int64_t *meta_exp, unsigned long long *meta_max,
-                                uint32_t *flags) {
+                                unsigned long long *meta_min, uint32_t *flags) {
   const double *w_pos = io->w_pos;
   const double *w_neg = io->w_neg;
   const int64_t total = (int64_t)n_vars * Qp;
@@ -443,22 +769,27 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int
     meta_exp[meta[x] + q] = e;
     const unsigned long long b0 = abs_bits(v0), b1 = abs_bits(v1);
     meta_max[meta[x] + q] = b0 > b1 ? b0 : b1;
+    const unsigned long long n0 = b0 ? b0 : kNoMin, n1 = b1 ? b1 : kNoMin;
+    meta_min[meta[x] + q] = n0 < n1 ? n0 : n1;
   }
 }
 
 template <typename T>
-__global__ void k_one_leaf(T *dst, int64_t meta, int64_t *meta_exp, unsigned long long *meta_max) {
+__global__ void k_one_leaf(T *dst, int64_t meta, int64_t *meta_exp, unsigned long long *meta_max,
+                           unsigned long long *meta_min) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     dst[0] = (T)1;
     meta_exp[meta] = 0;
     meta_max[meta] = abs_bits((T)1);
+    meta_min[meta] = abs_bits((T)1);
   }
 }
 
 // Root: value[q] = mant[q] * 2^exp[q] with the root tensor stored in
 // float64 (its exponents already account for its inputs' scales).
 __global__ void k_finalize(const IoDesc *io, const double *root, const int64_t *root_exp,
-                           int32_t root_qc, const uint32_t *flags, int32_t Q) {
+                           int32_t root_qc, const uint32_t *flags, const uint32_t *err,
+                           int32_t Q) {
   double *mant = io->mant;
   int64_t *exp2 = io->exp2;
   uint32_t *out_flags = io->flags;
@@ -466,7 +797,7 @@ __global__ void k_finalize(const IoDesc *io, const double *root, const int64_t *
     const int qr = root_qc > 1 ? q : 0;
     mant[q] = root[qr];
     exp2[q] = root_exp[qr];
-    out_flags[q] = flags[q];
+    out_flags[q] = flags[q] | (*err ? 0x8u : 0u);
   }
 }
 

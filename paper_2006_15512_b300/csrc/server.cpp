@@ -204,7 +204,9 @@ static void completer_loop(wmc_server *srv) {
       auto it = srv->tickets.find(sl.wave[q].ticket);
       if (it == srv->tickets.end()) continue;
       it->second.done_ns = now;
-      if (rc == WMC_OK) {
+      if (rc == WMC_OK && (sl.h_flags[q] & WMC_FLAG_DEVICE_TIMEOUT)) {
+        it->second.status = WMC_ETIMEOUT;
+      } else if (rc == WMC_OK) {
         exec_fill_result(st, sl.h_mant[q], sl.h_exp[q], sl.h_flags[q], false, sl.wave[q].negative,
                          &it->second.res);
         it->second.status = WMC_OK;

@@ -349,3 +349,24 @@ def test_alloc_failure_is_reported(w):
     w.wmc_debug_fail_next_allocs(0)
     plan2 = plan_for(w, cnf, None, None, FP32)
     assert plan2.execute()[0].mant != 0.0
+
+
+def test_bounded_wait_times_out_cleanly(w):
+    """Failure detection without a GPU fault: the test hook keeps the TMA
+    kernel's first copy from being issued, its bounded mbarrier wait runs
+    out, the call returns WMC_ETIMEOUT, and the context stays usable."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    w.wmc_debug_stall_copies(1)
+    try:
+        plan = plan_for(w, cnf, None, None, FP32)
+        wq, wnq = wmcgen.query_weights(cnf.n_vars, 64, seed=2, lo=0.05, hi=0.95)
+        with pytest.raises(w._abi.WmcError) as e:
+            plan.execute(wq, wnq)
+        assert e.value.status == w.WMC_ETIMEOUT
+    finally:
+        w.wmc_debug_stall_copies(0)
+    plan2 = plan_for(w, cnf, None, None, FP32)
+    res = plan2.execute(wq[:4], wnq[:4])
+    col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
+    want = oracle.bucket_elim(cnf, wq[0], wnq[0], order=col)
+    assert rel(res[0], want) <= TOL[FP32]

@@ -194,3 +194,20 @@ def test_workspace_grows_with_q():
     a, b = plan.info(1), plan.info(256)
     assert b.workspace_bytes > 100 * a.workspace_bytes
     assert b.algorithmic_bytes > 200 * a.algorithmic_bytes
+
+
+@pytest.mark.parametrize("Q", [1, 3, 256])
+def test_bounds_check_of_every_launch(Q):
+    """CPU replay of every contraction launch's index arithmetic (bulk
+    copies of every tile, extreme and sampled per-thread offsets): every
+    access stays inside its tensor."""
+    import ctypes
+    w = _lib()
+    for cnf in (wmcgen.grid_cnf(16, 100, 1), wmcgen.random_kcnf(30, 90, 2), wmcgen.psi_family(16),
+                wmcgen.grid_cnf(8, 40, 2)):
+        for precision in (0, 1):
+            plan = w.Plan(w.Network.from_cnf(cnf), precision=precision)
+            n = ctypes.c_int64()
+            rc = w.wmc_debug_check_bounds(plan.handle, Q, ctypes.byref(n))
+            assert rc == 0, w.wmc_last_error()
+            assert n.value > 0
