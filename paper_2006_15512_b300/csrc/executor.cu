@@ -352,7 +352,8 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
     tp.sA_off[s] = (r << top) | (da & ((1u << top) - 1u));
   }
   const size_t es = f64 ? 8 : 4;
-  smem = (size_t)dev::kStages * ((size_t)tp.nruns << top) * es + (es << tp.s_log2);
+  smem = (size_t)dev::kStages * ((size_t)tp.nruns << top) * es + (((es << tp.s_log2) + 15) & ~(size_t)15) +
+         (16 + es) * (size_t)Qp;  // stages, staged S (16-byte padded), per-query max/min/scale
   return smem <= 160 * 1024;
 }
 
@@ -530,7 +531,9 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
                          (use_a ? B : A).has_q, Qp, l.k2t, l.smem)) {
             l.kind = L_K2T;
             const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
-            const int per_sm = l.smem <= 80 * 1024 ? 2 : 1;
+            const int kf = l.k2.k + l.k2.f;  // register-limited CTAs per SM (launch bounds)
+            const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
+            const int per_sm = std::min(per_sm_regs, l.smem <= 72 * 1024 ? 3 : (l.smem <= 108 * 1024 ? 2 : 1));
             l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
           }
         }
@@ -598,31 +601,39 @@ static void launch_k2(const Launch &l, const K2Params &p, cudaStream_t s) {
   }
 }
 
-template <typename T, int V, int K>
+template <typename T, int V, int K, int F, bool EXACT>
 static void launch_k2t_t(const wmc::dev::K2TParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
   static bool attr_set = false;  // opt in to large dynamic shared memory once
   if (!attr_set) {
-    cudaFuncSetAttribute(dev::k2_tma<T, V, K, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(dev::k2_tma<T, V, K, F, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         160 * 1024);
     attr_set = true;
   }
-  dev::k2_tma<T, V, K, K><<<(unsigned)blocks, dev::kThreads + 32, smem, s>>>(p);
+  dev::k2_tma<T, V, K, F, EXACT><<<(unsigned)blocks, dev::kThreads + 32, smem, s>>>(p);
 }
 
+// Exact specialisations for the common (summed, S-free) splits, a bounded
+// generic one for the rest.
 template <typename T, int V>
-static void launch_k2t_v(const wmc::dev::K2TParams &p, int kmax, int64_t blocks, size_t smem,
-                         cudaStream_t s) {
-  if (kmax <= 1) launch_k2t_t<T, V, 1>(p, blocks, smem, s);
-  else if (kmax == 2) launch_k2t_t<T, V, 2>(p, blocks, smem, s);
-  else launch_k2t_t<T, V, 3>(p, blocks, smem, s);
+static void launch_k2t_v(const wmc::dev::K2TParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
+  const int k = p.k.k, f = p.k.f;
+  if (k == 1 && f == 1) launch_k2t_t<T, V, 1, 1, true>(p, blocks, smem, s);
+  else if (k == 1 && f == 0) launch_k2t_t<T, V, 1, 0, true>(p, blocks, smem, s);
+  else if (k == 0 && f == 1) launch_k2t_t<T, V, 0, 1, true>(p, blocks, smem, s);
+  else if (k == 1 && f == 2) launch_k2t_t<T, V, 1, 2, true>(p, blocks, smem, s);
+  else if (k == 2 && f == 1) launch_k2t_t<T, V, 2, 1, true>(p, blocks, smem, s);
+  else if (k == 2 && f == 2) launch_k2t_t<T, V, 2, 2, true>(p, blocks, smem, s);
+  else if (k <= 1 && f <= 1) launch_k2t_t<T, V, 1, 1, false>(p, blocks, smem, s);
+  else launch_k2t_t<T, V, 3, 3, false>(p, blocks, smem, s);
 }
 
 static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream_t s) {
   if (l.ti == TF) {
-    if (l.v == 4) launch_k2t_v<float, 4>(p, l.kmax, l.blocks, l.smem, s);
-    else launch_k2t_v<float, 1>(p, l.kmax, l.blocks, l.smem, s);
+    if (l.v == 4) launch_k2t_v<float, 4>(p, l.blocks, l.smem, s);
+    else launch_k2t_v<float, 1>(p, l.blocks, l.smem, s);
   } else {
-    if (l.v == 2) launch_k2t_v<double, 2>(p, l.kmax, l.blocks, l.smem, s);
-    else launch_k2t_v<double, 1>(p, l.kmax, l.blocks, l.smem, s);
+    if (l.v == 2) launch_k2t_v<double, 2>(p, l.blocks, l.smem, s);
+    else launch_k2t_v<double, 1>(p, l.blocks, l.smem, s);
   }
 }
 
@@ -1305,7 +1316,8 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
       const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
       const int64_t run_len = 1ll << tp.run_log2;
       const int64_t tile_elems = (int64_t)tp.nruns * run_len;
-      if ((int64_t)l.smem != tile_elems * dev::kStages * es_in + (es_in << tp.s_log2))
+      if ((int64_t)l.smem != tile_elems * dev::kStages * es_in + (((es_in << tp.s_log2) + 15) & ~15ll) +
+                                 (16 + es_in) * st->Qp)
         return bad("stage bytes", (int64_t)l.smem, tile_elems);
       if ((1ll << tp.s_log2) != nb) return bad("staged S size", 1ll << tp.s_log2, nb);
       for (uint64_t t = 0; t < n_tiles; ++t) {

@@ -439,7 +439,7 @@ struct K2TParams {
   int32_t debug_stall;  // test hook: never issue the first tile's copy
 };
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kMaxJ = 4;                        // work units per thread per tile
 constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of one wait
 
@@ -507,14 +507,60 @@ __device__ __forceinline__ void track_fast(T c, T &tmax, T &tmin) {
 
 constexpr int kConsumerWarps = kThreads / 32;
 
+template <typename T> struct Bits;
+template <> struct Bits<float> { typedef uint32_t t; };
+template <> struct Bits<double> { typedef unsigned long long t; };
+
+// 32-bit shared-memory vector loads at a byte address
+template <typename T, int V> struct LdsV;
+template <> struct LdsV<float, 4> {
+  static __device__ __forceinline__ void ld(uint32_t a, float (&r)[4]) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]) : "r"(a));
+  }
+};
+template <> struct LdsV<float, 1> {
+  static __device__ __forceinline__ void ld(uint32_t a, float (&r)[1]) {
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r[0]) : "r"(a));
+  }
+};
+template <> struct LdsV<double, 2> {
+  static __device__ __forceinline__ void ld(uint32_t a, double (&r)[2]) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r[0]), "=d"(r[1]) : "r"(a));
+  }
+};
+template <> struct LdsV<double, 1> {
+  static __device__ __forceinline__ void ld(uint32_t a, double (&r)[1]) {
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(r[0]) : "r"(a));
+  }
+};
+__device__ __forceinline__ float lds1(uint32_t a, float) {
+  float r;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ double lds1(uint32_t a, double) {
+  double r;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(r) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ uint32_t to_bits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long to_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+
 // Warp-specialised: warps 0..kConsumerWarps-1 compute, the last warp's
 // lane 0 produces.  full[st] completes when a tile's bytes have landed
 // (arrive.expect_tx + complete_tx); empty[st] completes when every consumer
 // warp has finished reading the stage.  No block-wide barrier in the loop.
-template <typename T, int V, int K, int F>
-__global__ void __launch_bounds__(kThreads + 32, (K <= 2 ? 2 : 1)) k2_tma(K2TParams tp) {
+// With EXACT the runtime k, f equal K, F and every guard folds away.
+// Tracking: max|c| as a float max, min nonzero as an unsigned min of the
+// bit pattern minus one (zero wraps to the largest value; nonnegative
+// entries, which is what the flush test covers).
+template <typename T, int V, int K, int F, bool EXACT>
+__global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ? 2 : 1))) k2_tma(K2TParams tp) {
+  typedef typename Bits<T>::t BT;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
   __shared__ uint32_t tile_oc[kStages], tile_gb[kStages];
   __shared__ int s_skip;
@@ -525,150 +571,180 @@ __global__ void __launch_bounds__(kThreads + 32, (K <= 2 ? 2 : 1)) k2_tma(K2TPar
   const uint32_t run_len = 1u << tp.run_log2;
   const uint32_t tile_elems = (uint32_t)tp.nruns * run_len;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
-  const uint32_t T_w = 1u << tp.tb;
-  const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
+  const uint32_t n_tiles = 1u << (p.log2_nu + p.vbits - tp.tb);
   T *stage_buf = reinterpret_cast<T *>(dyn_smem);
   T *sS = stage_buf + (size_t)kStages * tile_elems;  // S, pre-scaled
+  const size_t s_bytes = (((size_t)sizeof(T) << tp.s_log2) + 15) & ~(size_t)15;
+  unsigned long long *smax =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(sS) + s_bytes);
+  unsigned long long *smin = smax + p.mc.Qc;
   const T *A = (const T *)p.A;
   const T *B = (const T *)p.B;
   T *C = (T *)p.C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nthr = kConsumerWarps * 32;
-  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
-  // stage S, multiplied by its own scale and, when S carries every query
-  // lane of P (tp.fold_sa), by P's scale too: both are exact powers of two
-  const uint32_t n_s = 1u << tp.s_log2;
-  for (uint32_t j = threadIdx.x; j < n_s; j += blockDim.x) {
-    T v = B[j] * operand_scale<T>(p.mb, (int)j, p.mc.scale_inputs);
-    if (tp.fold_sa) v *= operand_scale<T>(p.ma, (int)j, p.mc.scale_inputs);
-    sS[j] = v;
-  }
-  if (threadIdx.x == 0) {
+  constexpr int nthr = kConsumerWarps * 32;
+  // The producer sets up the barriers and puts the first tiles in flight
+  // before the block stages S, so the copies overlap the prologue.
+  auto produce = [&](uint32_t i) -> bool {
+    const int st = (int)(i % kStages);
+    if (i >= (uint32_t)kStages && !mbar_wait(&empty[st], ((i / kStages) - 1) & 1)) return false;
+    const uint32_t bw = (blockIdx.x + i * gridDim.x) << tp.tb;
+    uint32_t base = bw, oc = bw, gb = 0;
+    for (int j = 0; j < p.n_insA; ++j) base = insert0(base, p.insA[j]);
+    for (int j = 0; j < p.n_insC; ++j) oc = insert0(oc, p.insC[j]);
+    for (int j = 0; j < p.n_seg; ++j)
+      gb |= ((oc >> p.seg_c[j]) & ((1u << p.seg_len[j]) - 1u)) << p.seg_b[j];
+    tile_oc[st] = oc;
+    tile_gb[st] = gb;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&full[st], tile_bytes);  // release: tile_oc/gb visible
+    if (tp.debug_stall && i == 0) return true;  // test hook: the wait must run out
+    for (int r = 0; r < tp.nruns; ++r)
+      bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len, A + base + tp.run_off[r],
+               run_len * (uint32_t)sizeof(T), &full[st]);
+    return true;
+  };
+  const bool producer = (warp == kConsumerWarps) && lane == 0;
+  uint32_t n_pre = 0;
+  if (producer) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], kConsumerWarps);
     }
     mbar_fence_init();
+    for (; n_pre < (uint32_t)kStages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
+  }
+  // per-query scale of the staged S (S's own scale, times P's when folded)
+  T *sscale = reinterpret_cast<T *>(smin + p.mc.Qc);
+  const int qs = p.mb.qmask + 1;
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  for (int q = threadIdx.x; q < qs; q += blockDim.x) {
+    T v = operand_scale<T>(p.mb, q, p.mc.scale_inputs);
+    if (tp.fold_sa) v *= operand_scale<T>(p.ma, q, p.mc.scale_inputs);
+    sscale[q] = v;
   }
   __syncthreads();
-  auto tile_of = [&](uint64_t i) { return (uint64_t)blockIdx.x + i * gridDim.x; };
+  // stage S (independent coalesced loads)
+  const uint32_t n_s = 1u << tp.s_log2;
+#pragma unroll 4
+  for (uint32_t j = threadIdx.x; j < n_s; j += blockDim.x) sS[j] = __ldg(B + j) * sscale[j & p.mb.qmask];
+  __syncthreads();
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint64_t i = 0;
+      uint32_t i = n_pre;
       bool ok = true;
-      for (; tile_of(i) < n_tiles; ++i) {
-        const int st = (int)(i % kStages);
-        if (i >= (uint64_t)kStages && !mbar_wait(&empty[st], (uint32_t)(((i / kStages) - 1) & 1))) {
+      for (; blockIdx.x + i * gridDim.x < n_tiles; ++i) {
+        if (!produce(i)) {
           ok = false;
           break;
         }
-        const uint32_t bw = (uint32_t)(tile_of(i) << tp.tb);
-        uint32_t base = bw, oc = bw, gb = 0;
-        for (int j = 0; j < p.n_insA; ++j) base = insert0(base, p.insA[j]);
-        for (int j = 0; j < p.n_insC; ++j) oc = insert0(oc, p.insC[j]);
-        for (int j = 0; j < p.n_seg; ++j)
-          gb |= ((oc >> p.seg_c[j]) & ((1u << p.seg_len[j]) - 1u)) << p.seg_b[j];
-        tile_oc[st] = oc;
-        tile_gb[st] = gb;
-        fence_proxy_async_smem();
-        mbar_expect_tx(&full[st], tile_bytes);  // release: tile_oc/gb visible
-        if (tp.debug_stall && i == 0) continue;  // test hook: the wait must run out
-        for (int r = 0; r < tp.nruns; ++r)
-          bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len,
-                   A + base + tp.run_off[r], run_len * (uint32_t)sizeof(T), &full[st]);
       }
       if (!ok && tp.err) atomicOr(tp.err, 1u);
       // drain: copies of the last kStages issued tiles may still be in flight
-      const uint64_t n_issued = i;
-      for (uint64_t j = n_issued > (uint64_t)kStages ? n_issued - kStages : 0; j < n_issued; ++j)
-        if (!mbar_wait(&full[j % kStages], (uint32_t)((j / kStages) & 1)) && tp.err)
-          atomicOr(tp.err, 1u);
+      const uint32_t n_issued = i;
+      for (uint32_t j = n_issued > (uint32_t)kStages ? n_issued - kStages : 0; j < n_issued; ++j)
+        if (!mbar_wait(&full[j % kStages], (j / kStages) & 1) && tp.err) atomicOr(tp.err, 1u);
     }
     __syncwarp();  // the producer warp reconverges before the block barrier
   } else {
     // ----------------------------------------------------------- consumers
     constexpr int NS = 1 << K, NF = 1 << F;
-    const int ns = 1 << p.k, nf = 1 << p.f;
-    const int J = (int)(T_w / (uint32_t)(nthr * V));
-    uint32_t la[kMaxJ], ocl[kMaxJ], gbl[kMaxJ];
+    const int ns = EXACT ? NS : (1 << p.k);
+    const int nf = EXACT ? NF : (1 << p.f);
+    constexpr int J = (V == 1) ? 4 : 2;  // work units per thread per tile (host: T_w = 256*V*J)
+    constexpr uint32_t es = (uint32_t)sizeof(T);
+    const uint32_t stage0 = smem_addr(stage_buf), sS0 = smem_addr(sS);
+    // per-thread parts of the offsets (constant across tiles), in bytes
+    uint32_t la4[J], ocl[J], gbl4[J];
 #pragma unroll
-    for (int j = 0; j < kMaxJ; ++j) {
+    for (int j = 0; j < J; ++j) {
       const uint32_t wl = (threadIdx.x + (uint32_t)j * nthr) * V;
       uint32_t a = wl, c = wl, g = 0;
       for (int i = 0; i < tp.n_lowA; ++i) a = insert0(a, tp.lowA[i]);
       for (int i = 0; i < p.n_insC; ++i) c = insert0(c, p.insC[i]);
       for (int i = 0; i < p.n_seg; ++i)
         g |= ((c >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
-      la[j] = a; ocl[j] = c; gbl[j] = g;
+      la4[j] = a * es; ocl[j] = c; gbl4[j] = g * es + sS0;
     }
+    uint32_t aoff[NS], boff[NS][NF];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      aoff[s] = (s < ns) ? tp.sA_off[s] * es : 0u;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) boff[s][f] = (s < ns && f < nf) ? (p.dBs[s] + p.dBf[f]) * es : 0u;
+    }
+    uint32_t dCf[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dCf[f] = (f < nf) ? p.dC[f] : 0u;
     // each lane's query is the same in every tile
     T sa[V];
 #pragma unroll
     for (int e = 0; e < V; ++e)
       sa[e] = tp.fold_sa ? (T)1 : operand_scale<T>(p.ma, (int)(threadIdx.x * V + e), p.mc.scale_inputs);
-    T tmax[NF][V], tmin[NF][V];
+    T tmax[NF][V];
+    BT tminm1[NF][V];  // (bits of the smallest nonzero) - 1
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tmin[f][e] = (T)INFINITY; }
-    for (uint64_t i = 0; tile_of(i) < n_tiles; ++i) {
+      for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tminm1[f][e] = (BT)~(BT)0; }
+    for (uint32_t i = 0; blockIdx.x + i * gridDim.x < n_tiles; ++i) {
       const int st = (int)(i % kStages);
       // every lane waits (acquire), the warp agrees on the outcome
-      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / kStages) & 1)));
+      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (i / kStages) & 1));
       if (!landed) {
         if (lane == 0 && tp.err) atomicOr(tp.err, 1u);
         break;
       }
-      const T *tile = stage_buf + (size_t)st * tile_elems;
-      const uint32_t ocb = tile_oc[st], gbb = tile_gb[st];
+      const uint32_t tile0 = stage0 + (uint32_t)st * tile_bytes;
+      const uint32_t ocb = tile_oc[st], gbb4 = tile_gb[st] * es;
 #pragma unroll
-      for (int j = 0; j < kMaxJ; ++j) {
-        if (j < J) {
-          const uint32_t oc = ocb | ocl[j], gb = gbb | gbl[j];
-          T a[NS][V];
+      for (int j = 0; j < J; ++j) {
+        const uint32_t oc = ocb | ocl[j];
+        const uint32_t gaddr = gbb4 + gbl4[j];
+        T a[NS][V];
 #pragma unroll
-          for (int s = 0; s < NS; ++s)
-            if (s < ns) {
-              typedef typename VecT<T, V>::t VT;
-              const VT v = *reinterpret_cast<const VT *>(tile + tp.sA_off[s] + la[j]);
-              const T *ev = reinterpret_cast<const T *>(&v);
+        for (int s = 0; s < NS; ++s)
+          if (s < ns) {
+            LdsV<T, V>::ld(tile0 + la4[j] + aoff[s], a[s]);
+            if (!tp.fold_sa) {
 #pragma unroll
-              for (int e = 0; e < V; ++e) a[s][e] = ev[e] * sa[e];
+              for (int e = 0; e < V; ++e) a[s][e] *= sa[e];
             }
+          }
+        T *cptr = C + oc;
 #pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            if (f < nf) {
-              T c[V];
+        for (int f = 0; f < NF; ++f) {
+          if (f < nf) {
+            T c[V];
 #pragma unroll
-              for (int e = 0; e < V; ++e) c[e] = (T)0;
+            for (int e = 0; e < V; ++e) c[e] = (T)0;
 #pragma unroll
-              for (int s = 0; s < NS; ++s) {
-                if (s < ns) {
-                  T b[V];
-                  const uint32_t ob = gb + p.dBs[s] + p.dBf[f];
-                  if (V > 1 && p.b_vec == 1) {
-                    typedef typename VecT<T, V>::t VT;
-                    const VT v = *reinterpret_cast<const VT *>(sS + ob);
-                    const T *ev = reinterpret_cast<const T *>(&v);
+            for (int s = 0; s < NS; ++s) {
+              if (s < ns) {
+                T b[V];
+                const uint32_t ba = gaddr + boff[s][f];
+                if (V > 1 && p.b_vec == 1) {
+                  LdsV<T, V>::ld(ba, b);
+                } else if (p.b_vec == 2) {
+                  const T v = lds1(ba, T());
 #pragma unroll
-                    for (int e = 0; e < V; ++e) b[e] = ev[e];
-                  } else if (p.b_vec == 2) {
-                    const T v = sS[ob];
+                  for (int e = 0; e < V; ++e) b[e] = v;
+                } else {
 #pragma unroll
-                    for (int e = 0; e < V; ++e) b[e] = v;
-                  } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) b[e] = sS[ob + p.dBv[e]];
-                  }
-#pragma unroll
-                  for (int e = 0; e < V; ++e) c[e] = fma_t(a[s][e], b[e], c[e]);
+                  for (int e = 0; e < V; ++e) b[e] = lds1(ba + p.dBv[e] * es, T());
                 }
-              }
-              vstore<T, V>(C + oc + p.dC[f], c);
 #pragma unroll
-              for (int e = 0; e < V; ++e) track_fast(c[e], tmax[f][e], tmin[f][e]);
+                for (int e = 0; e < V; ++e) c[e] = fma_t(a[s][e], b[e], c[e]);
+              }
+            }
+            vstore<T, V>(cptr + dCf[f], c);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+              tmax[f][e] = fmax(tmax[f][e], fabs(c[e]));
+              const BT bm1 = to_bits(c[e]) - (BT)1;
+              tminm1[f][e] = bm1 < tminm1[f][e] ? bm1 : tminm1[f][e];
             }
           }
         }
@@ -681,7 +757,11 @@ __global__ void __launch_bounds__(kThreads + 32, (K <= 2 ? 2 : 1)) k2_tma(K2TPar
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int e = 0; e < V; ++e)
-        if (f < nf) publish(smax, smin, (int)((ocl[0] + p.dC[f] + e) & qmask_c), tmax[f][e], tmin[f][e]);
+        if (f < nf) {
+          const int q = (int)((ocl[0] + dCf[f] + e) & qmask_c);
+          if (tmax[f][e] != (T)0) atomicMax(smax + q, abs_bits(tmax[f][e]));
+          if (tminm1[f][e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[f][e] + (BT)1));
+        }
   }
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
