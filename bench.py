@@ -47,6 +47,23 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 
 
+def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
+    """Query-pool offset of a rank's wave: ranks take disjoint waves of the
+    pool (replicas with no data exchange; each rank's work is fixed as the
+    world grows, i.e. weak scaling)."""
+    return ((step * world + rank) % n_waves) * Q
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The job's time is the slowest rank's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -190,7 +207,7 @@ def run_ours(args, rank, world):
     n_waves = POOL // Q
 
     def wave(i):
-        off = (i % n_waves) * Q
+        off = wave_offset(i, rank, world, n_waves, Q)
         plan.execute_device(Q, d_wp[off:off + Q], d_wn[off:off + Q], ws, mant, ex, fl, stream=sp)
 
     for i in range(args.warmup):
@@ -216,11 +233,7 @@ def run_ours(args, rank, world):
         if rank == 0:
             print(json.dumps({"waves": args.warmup + args.steps, "Q": Q, "ms": ms}), flush=True)
         return
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t)
+    t_max = max_over_ranks(ms, dist, dev)
     value = world * args.steps * Q / (t_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers
@@ -231,13 +244,9 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     e2e_res = []
     for i in range(args.steps):
-        off = ((args.warmup + i) % n_waves) * Q
+        off = wave_offset(args.warmup + i, rank, world, n_waves, Q)
         e2e_res = plan.execute(host_wp[off:off + Q], host_wn[off:off + Q])
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": world * args.steps * Q / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": 2 * Q * n * 8, "d2h_bytes_per_step": Q * (8 + 8 + 4)}
 
@@ -348,6 +357,135 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, reps):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
+
+
+def run_other(args):
+    """Measurements of the non-headline configs (one JSON line each)."""
+    import ctypes
+    import torch
+    import paper_2006_15512_b300 as w
+    import oracle
+    from oracle import Big
+    hbm, src = peaks()
+    out = {"workload": args.workload}
+    if args.workload == "random3cnf":
+        # n=20, m=60 random 3-CNF, FP64, one query per call (latency)
+        lat, errs = [], []
+        for seed in range(10):
+            cnf = wmcgen.random_kcnf(20, 60, seed=seed)
+            wp, wn = wmcgen.weights_complementary(20, seed, 0.1, 0.9)
+            plan = w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=w.WMC_FP64)
+            plan.execute()
+            lat.append(_timed(lambda: plan.execute(), 20))
+            r = plan.execute()[0]
+            errs.append(Big(r.mant, r.exp2).rel_diff(oracle.brute_force(cnf, wp, wn)[0]))
+        t0 = time.perf_counter()
+        oracle.brute_force(wmcgen.random_kcnf(20, 60, seed=0), *wmcgen.weights_complementary(20, 0, 0.1, 0.9))
+        out.update({"metric": "latency per query (host buffers, FP64)", "p50_us": float(np.median(lat) * 1e6),
+                    "max_us": float(max(lat) * 1e6), "max_rel_err": float(max(errs)),
+                    "oracle_brute_force_s": time.perf_counter() - t0, "oracle_threads": oracle.num_threads()})
+    elif args.workload == "grid":
+        # 24x200 grid, one query, scaled FP32 and FP64
+        with open(os.path.join(ROOT, "tests", "golden", "grid_24x200.json")) as f:
+            g = json.load(f)["values"][0]
+        cnf = wmcgen.grid_cnf(24, 200, g["seed"])
+        wp, wn = wmcgen.weights_complementary(4800, g["seed"], 0.05, 0.95)
+        net = w.Network.from_cnf(cnf, wp, wn)
+        for name, prec in (("fp32", w.WMC_SCALED_FP32), ("fp64", w.WMC_FP64)):
+            plan = w.Plan(net, precision=prec)
+            info = plan.info(1)
+            plan.execute()
+            t = _timed(lambda: plan.execute(), 3)
+            r = plan.execute()[0]
+            out[name] = {"ms": t * 1e3, "alg_GB": info.algorithmic_bytes / 1e9,
+                         "frac_hbm": info.algorithmic_bytes / t / 1e9 / hbm,
+                         "rel_err": Big(r.mant, r.exp2).rel_diff(Big(g["mant"], g["exp2"])),
+                         "log10": r.log10, "max_rank": info.max_rank, "stated_bound": r.rel_err_bound}
+    elif args.workload == "sweep":
+        rows = []
+        for (ra, rb, b, k) in [(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)]:
+            case = wmcgen.pair_case(ra, rb, b, k, seed=7 + ra + rb + k, shuffle=False)
+            rc = len(case.labels_c)
+            A = torch.from_numpy(case.a).cuda(); B = torch.from_numpy(case.b).cuda()
+            C = torch.empty(1 << rc, dtype=torch.float64, device="cuda")
+            f64 = lambda: w.contract_pair(0, case.labels_a, A, case.labels_b, B, case.labels_c, C)
+            f64()
+            t64 = _timed(f64, 3)
+            A32 = torch.empty(A.numel(), dtype=torch.float32, device="cuda")
+            B32 = torch.empty(B.numel(), dtype=torch.float32, device="cuda")
+            e = torch.zeros(3, dtype=torch.int64, device="cuda")
+            w.to_scaled_fp32(A, A32, e[0:1]); w.to_scaled_fp32(B, B32, e[1:2])
+            del C
+            C32 = torch.empty(1 << rc, dtype=torch.float32, device="cuda")
+            f32 = lambda: w.contract_pair(1, case.labels_a, A32, case.labels_b, B32, case.labels_c, C32,
+                                          e[0:1], e[1:2], e[2:3])
+            f32()
+            t32 = _timed(f32, 3)
+            n_el = (1 << ra) + (1 << rb) + (1 << rc)
+            flops = 2.0 * (1 << (rc + k))
+            rows.append({"rank_a": ra, "rank_b": rb, "batch": b, "summed": k,
+                         "fp64_ms": t64 * 1e3, "fp64_GBs": 8 * n_el / t64 / 1e9, "fp64_GFLOPs": flops / t64 / 1e9,
+                         "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9})
+            del A, B, A32, B32, C32
+            torch.cuda.empty_cache()
+        out["rows"] = rows
+        out["hbm_peak_GBs"] = hbm
+    elif args.workload == "uneven":
+        plans, rejected, kinds = [], 0, {}
+        t0 = time.perf_counter()
+        for kind, cnf, wp, wn, sub in wmcgen.uneven_candidates(3):
+            try:
+                plans.append((w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=w.WMC_SCALED_FP32,
+                                     max_rank_cap=26), cnf, wp, wn, kind))
+                kinds[kind[:4]] = kinds.get(kind[:4], 0) + 1
+            except w._abi.WmcError:
+                rejected += 1
+            if len(plans) == args.n_formulas:
+                break
+        plan_s = time.perf_counter() - t0
+        batch = w.Batch([x[0] for x in plans])
+        info = batch.info()
+        batch.execute()
+        t = _timed(lambda: batch.execute(), max(1, args.steps // 10))
+        res = batch.execute()
+        # per-formula graph loop on the same formulas
+        for x in plans:
+            x[0].execute()
+        t_loop = _timed(lambda: [x[0].execute() for x in plans], 1)
+        errs = []
+        for i in range(len(plans)):
+            p, cnf, wp, wn, kind = plans[i]
+            if p.info(1).max_rank > 18 or len(errs) >= 12:
+                continue
+            order = None
+            if kind.startswith("grid"):
+                h_, w_ = (int(v) for v in kind[4:].split("x"))
+                order = wmcgen.grid_column_order(h_, w_)
+            try:
+                want = oracle.bucket_elim(cnf, wp, wn, order=order, max_width=22)
+            except RuntimeError:
+                continue
+            errs.append(Big(res[i].mant, res[i].exp2).rel_diff(want))
+        out.update({"metric": "formulas/s", "value": len(plans) / t, "persistent_ms": t * 1e3,
+                    "graph_loop_ms": t_loop * 1e3, "speedup_vs_graph_loop": t_loop / t,
+                    "formulas": len(plans), "rejected": rejected, "mix": kinds,
+                    "nodes": info.n_nodes, "tasks": info.n_tasks,
+                    "workspace_GiB": info.workspace_bytes / 2 ** 30,
+                    "alg_GB": info.algorithmic_bytes / 1e9,
+                    "frac_hbm": info.algorithmic_bytes / t / 1e9 / hbm,
+                    "max_rel_err_sampled": max(errs) if errs else None, "sampled": len(errs),
+                    "planning_s": plan_s})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,6 +498,9 @@ def main():
     ap.add_argument("--waves", type=int, default=2)
     ap.add_argument("--plain-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="serving",
+                    choices=["serving", "random3cnf", "grid", "sweep", "uneven"])
+    ap.add_argument("--n-formulas", type=int, default=512)
     ap.add_argument("--only-waves", action="store_true",
                     help="run the warm-up and timed waves only (profiling driver)")
     args = ap.parse_args()
@@ -372,6 +513,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload != "serving":
+        run_other(args)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":

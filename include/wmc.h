@@ -76,6 +76,7 @@ extern "C" {
 typedef struct wmc_network wmc_network_t;
 typedef struct wmc_plan wmc_plan_t;
 typedef struct wmc_server wmc_server_t;
+typedef struct wmc_batch wmc_batch_t;
 
 typedef struct {
   double mant;          /* value = mant * 2^exp2, |mant| in [0.5, 1) or 0   */
@@ -236,6 +237,33 @@ int wmc_contract_pair(int32_t precision, int32_t rank_a,
  * that max|out| lies in [1, 2).  Asynchronous on `stream`. */
 int wmc_to_scaled_fp32(const double *x, int64_t n, float *out,
                        int64_t *exp_out, void *stream);
+
+/* ------------------------------------------------------- uneven batches */
+/* Many formulas of different shapes in one persistent launch (Alg. 2 for
+ * each).  wmc_batch_create admits plans in order while the sum of their
+ * single-query workspaces fits mem_budget_bytes (0 = no limit); *n_admitted
+ * receives how many.  All plans must share a precision.  Each formula is
+ * evaluated with its network's default weights.  Execution: one graph of
+ * four kernels -- clear, leaves, a persistent task-queue contraction kernel
+ * (tasks = chunks of 2^14 outputs of one node; within a formula the nodes
+ * run in post-order, across formulas and within a node concurrently; every
+ * dependency wait is bounded at one second), and the results.
+ * Errors: WMC_EINVAL, WMC_EPLAN_TOO_BIG (nothing fits), WMC_ENOMEM,
+ * WMC_ECUDA, WMC_ETIMEOUT. */
+int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans,
+                     int64_t mem_budget_bytes, wmc_batch_t **out,
+                     int32_t *n_admitted);
+typedef struct {
+  int64_t n_formulas, n_nodes, n_tasks;
+  int64_t workspace_bytes;
+  double algorithmic_bytes;
+  int32_t max_rank;
+  int32_t grid;             /* persistent blocks (set after first execute) */
+} wmc_batch_info_t;
+int wmc_batch_info(const wmc_batch_t *batch, wmc_batch_info_t *out);
+/* Synchronous on `stream`; out[i] is the result of admitted formula i. */
+int wmc_batch_execute(wmc_batch_t *batch, void *stream, wmc_result *out);
+void wmc_batch_destroy(wmc_batch_t *batch);
 
 /* ------------------------------------------------------------- serving */
 typedef struct {

@@ -24,7 +24,7 @@ from . import _abi
 from ._abi import *  # noqa: F401,F403  (the C names)
 from ._abi import check, lib
 
-__all__ = ["Network", "Plan", "Server", "Result", "contract_pair", "to_scaled_fp32",
+__all__ = ["Network", "Plan", "Server", "Batch", "Result", "contract_pair", "to_scaled_fp32",
            "launch_count"] + list(_abi.EXPORTS)
 
 P = ctypes.POINTER
@@ -207,6 +207,35 @@ def contract_pair(precision: int, labels_a, a, labels_b, b, labels_c, c,
 def to_scaled_fp32(x, out, exp_out, stream: int = 0) -> None:
     check(lib.wmc_to_scaled_fp32(_dptr(x), int(x.numel()), _dptr(out), _dptr(exp_out),
                                  ctypes.c_void_p(stream)), "wmc_to_scaled_fp32")
+
+
+class Batch:
+    """Uneven batch of formulas in one persistent launch (wmc_batch_*)."""
+
+    def __init__(self, plans, mem_budget_bytes: int = 0):
+        arr = (ctypes.c_void_p * len(plans))(*[p.handle.value for p in plans])
+        h = ctypes.c_void_p()
+        n = ctypes.c_int32()
+        check(lib.wmc_batch_create(arr, len(plans), int(mem_budget_bytes), ctypes.byref(h),
+                                   ctypes.byref(n)), "wmc_batch_create")
+        self.handle = h
+        self.plans = list(plans)[: n.value]
+        self.n_admitted = n.value
+
+    def info(self) -> _abi.wmc_batch_info_t:
+        out = _abi.wmc_batch_info_t()
+        check(lib.wmc_batch_info(self.handle, ctypes.byref(out)), "wmc_batch_info")
+        return out
+
+    def execute(self, stream: int = 0) -> List[Result]:
+        out = (_abi.wmc_result * self.n_admitted)()
+        check(lib.wmc_batch_execute(self.handle, ctypes.c_void_p(stream), out), "wmc_batch_execute")
+        return [Result.from_c(out[i]) for i in range(self.n_admitted)]
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.wmc_batch_destroy(self.handle)
+            self.handle = None
 
 
 class Server:

@@ -78,6 +78,12 @@ class wmc_server_opts(ctypes.Structure):
                 ("reserved", c_i32), ("arena_bytes", c_i64), ("max_wave_wait_us", c_i64)]
 
 
+class wmc_batch_info_t(ctypes.Structure):
+    _fields_ = [("n_formulas", c_i64), ("n_nodes", c_i64), ("n_tasks", c_i64),
+                ("workspace_bytes", c_i64), ("algorithmic_bytes", c_dbl), ("max_rank", c_i32),
+                ("grid", c_i32)]
+
+
 class wmc_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_i64), ("completed", c_i64), ("waves", c_i64),
                 ("failed_waves", c_i64), ("mean_wave_q", c_dbl)]
@@ -106,6 +112,10 @@ EXPORTS = {
     "wmc_contract_pair": (c_i32, [c_i32, c_i32, P(c_i32), c_vp, c_i32, P(c_i32), c_vp, c_i32,
                                   P(c_i32), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_to_scaled_fp32": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "wmc_batch_create": (c_i32, [P(c_vp), c_i32, c_i64, P(c_vp), P(c_i32)]),
+    "wmc_batch_info": (c_i32, [c_vp, P(wmc_batch_info_t)]),
+    "wmc_batch_execute": (c_i32, [c_vp, c_vp, P(wmc_result)]),
+    "wmc_batch_destroy": (None, [c_vp]),
     "wmc_server_create": (c_i32, [c_vp, P(wmc_server_opts), P(c_vp)]),
     "wmc_submit": (c_i32, [c_vp, P(c_dbl), P(c_dbl), P(c_u64)]),
     "wmc_poll": (c_i32, [c_vp, c_u64, P(wmc_result)]),

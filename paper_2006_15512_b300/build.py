@@ -17,8 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libwmc_b300.so")
 
-SOURCES = ["network.cpp", "planner.cpp", "executor.cu", "server.cpp"]
-HEADERS = ["internal.h", "kernels.cuh"]
+SOURCES = ["network.cpp", "planner.cpp", "executor.cu", "batch.cu", "server.cpp"]
+HEADERS = ["internal.h", "kernels.cuh", "dev_common.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -1041,6 +1041,38 @@ extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, c
 }
 
 namespace wmc {
+int exec_layout(Plan &plan, int32_t Q, LayoutView *out) {
+  ExecState *st = nullptr;
+  int rc = get_state(plan, Q, &st);
+  if (rc) return rc;
+  out->ws_bytes = st->ws_bytes;
+  out->off_io = st->off_io;
+  out->off_flags = st->off_flags;
+  out->off_err = st->off_err;
+  out->off_exp = st->off_exp;
+  out->off_max = st->off_max;
+  out->off_min = st->off_min;
+  out->n_slots = st->n_slots;
+  out->t_off = &st->t_off;
+  out->t_meta = &st->t_meta;
+  out->t_bytes = &st->t_bytes;
+  out->t_dbl = &st->t_dbl;
+  return WMC_OK;
+}
+void k1_bitmaps(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
+                const std::vector<int32_t> &LC, int32_t *rC, int32_t *k, int8_t *posA,
+                int8_t *posB, int8_t *sposA, int8_t *sposB) {
+  K1Params p;
+  fill_k1(LA, LB, LC, p);
+  *rC = p.rC;
+  *k = p.k;
+  std::memcpy(posA, p.posA, 32);
+  std::memcpy(posB, p.posB, 32);
+  std::memcpy(sposA, p.sposA, 24);
+  std::memcpy(sposB, p.sposB, 24);
+}
+void count_launches(int64_t n) { g_launches.fetch_add(n); }
+int device_alloc(void **p, size_t bytes) { return dev_alloc(p, bytes); }
 int exec_state(Plan &plan, int32_t Q, ExecState **out) {
   if (check_q(Q)) return WMC_EINVAL;
   return get_state(plan, Q, out);

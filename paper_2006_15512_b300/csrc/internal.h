@@ -96,4 +96,23 @@ void exec_fill_result(const ExecState *st, double mant, int64_t exp2, uint32_t f
                       bool unit, bool negative, wmc_result *out);
 Plan &plan_of(wmc_plan_t *p);
 
+// Host-side layout of a plan's walk at batch size Q (executor.cu).
+struct LayoutView {
+  int64_t ws_bytes = 0, off_io = 0, off_flags = 0, off_err = 0, off_exp = 0, off_max = 0,
+          off_min = 0, n_slots = 0;
+  const std::vector<int64_t> *t_off = nullptr;   // byte offset of each tensor
+  const std::vector<int64_t> *t_meta = nullptr;  // first metadata slot
+  const std::vector<int64_t> *t_bytes = nullptr;
+  const std::vector<uint8_t> *t_dbl = nullptr;   // stored as float64
+};
+int exec_layout(Plan &plan, int32_t Q, LayoutView *out);
+// Bit maps of the generic kernel for C = A . B given full label lists.
+void k1_bitmaps(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
+                const std::vector<int32_t> &LC, int32_t *rC, int32_t *k, int8_t *posA,
+                int8_t *posB, int8_t *sposA, int8_t *sposB);
+// Kernel launches issued by this library (accounting).
+void count_launches(int64_t n);
+// Test hook state: allocation failures to inject (consumed by device_alloc).
+int device_alloc(void **p, size_t bytes);
+
 }  // namespace wmc

@@ -370,3 +370,44 @@ def test_bounded_wait_times_out_cleanly(w):
     col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
     want = oracle.bucket_elim(cnf, wq[0], wnq[0], order=col)
     assert rel(res[0], want) <= TOL[FP32]
+
+
+# ---------------------------------------------------------- uneven batch
+
+def _uneven(w, count, precision, **kw):
+    plans, cnfs, rejected = [], [], 0
+    for kind, cnf, wp, wn, sub in wmcgen.uneven_candidates(**kw):
+        try:
+            plans.append(w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=precision, max_rank_cap=20))
+            cnfs.append((cnf, wp, wn))
+        except w._abi.WmcError:
+            rejected += 1
+        if len(plans) == count:
+            return plans, cnfs, rejected
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_uneven_batch_persistent(w, precision):
+    """Mixed random 3-CNF and grid formulas in one persistent launch: each
+    result equals the oracle and the formula's own graph walk."""
+    plans, cnfs, _ = _uneven(w, 24, precision, seed=5, n3=(14, 40), grid_w=(3, 8), grid_h=(4, 30))
+    batch = w.Batch(plans)
+    assert batch.n_admitted == 24
+    for rep in range(2):
+        res = batch.execute()
+        for i, (p, (cnf, wp, wn)) in enumerate(zip(plans, cnfs)):
+            alone = p.execute()[0]
+            assert Big(res[i].mant, res[i].exp2).rel_diff(Big(alone.mant, alone.exp2)) <= TOL[precision]
+            if i % 3 == 0:
+                want = oracle.bucket_elim(cnf, wp, wn, max_width=26)
+                assert rel(res[i], want) <= TOL[precision], (i, rep)
+
+
+def test_uneven_batch_admission(w):
+    """Admission by workspace bytes: only the prefix that fits is taken."""
+    plans, _, _ = _uneven(w, 10, FP32, seed=6, n3=(14, 30), grid_w=(3, 6), grid_h=(4, 20))
+    sizes = [p.info(1).workspace_bytes for p in plans]
+    budget = sum((s_ + 255) // 256 * 256 for s_ in sizes[:4])
+    batch = w.Batch(plans, mem_budget_bytes=budget)
+    assert batch.n_admitted == 4
+    assert len(batch.execute()) == 4

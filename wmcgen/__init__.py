@@ -149,7 +149,40 @@ def independent_clauses(n_clauses: int, width: int, seed: int) -> Cnf:
     return Cnf(n_clauses * width, clauses)
 
 
+def uneven_candidates(seed: int, n3: Tuple[int, int] = (40, 120), ratio=(2.0, 3.5),
+                      grid_w=(6, 20), grid_h=(20, 150)):
+    """Endless stream of uneven-batch candidates: random 3-CNF (n in n3,
+    clause ratio in `ratio`) and grid CNFs (width in grid_w, height in
+    grid_h), alternating, each with complementary weights U(0.05, 0.95).
+    Yields (kind, cnf, w_pos, w_neg, sub_seed) with kind "3cnf" or
+    "grid<H>x<W>".  Candidates whose plans are too wide are skipped by the
+    caller (rejection sampling)."""
+    rng = rng_for(seed)
+    i = 0
+    while True:
+        sub = int(rng.integers(0, 2 ** 31 - 1))
+        if i % 2 == 0:
+            n = int(rng.integers(n3[0], n3[1] + 1))
+            m = int(round(n * rng.uniform(*ratio)))
+            cnf = random_kcnf(n, m, sub)
+            kind = "3cnf"
+        else:
+            w = int(rng.integers(grid_w[0], grid_w[1] + 1))
+            h = int(rng.integers(grid_h[0], grid_h[1] + 1))
+            cnf = grid_cnf(h, w, sub)
+            kind = f"grid{h}x{w}"
+        wp, wn = weights_complementary(cnf.n_vars, sub, 0.05, 0.95)
+        yield kind, cnf, wp, wn, sub
+        i += 1
+
+
 # ----------------------------------------------------------------- weights
+
+def grid_column_order(height: int, width: int) -> List[int]:
+    """Column-by-column variable order of grid_cnf (an input for the
+    oracle's elimination; it carries no arithmetic)."""
+    return [i * width + j + 1 for j in range(width) for i in range(height)]
+
 
 def weights_complementary(n_vars: int, seed: int, lo: float, hi: float):
     """w(x) ~ U(lo, hi), w(~x) = 1 - w(x)."""
