@@ -217,7 +217,12 @@ int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q,
 
 /* One pairwise contraction C = A . B (Eq. (1) on the network {A, B}; the
  * matrix-multiplication view of Sec. 4.2), on device memory, asynchronous on
- * `stream`.  Bit j of a tensor's linear offset is index labels_x[j];
+ * `stream`.  Kernel choice: the streaming kernel when one operand is small,
+ * a tiled dense kernel when the node is a batched matrix product with at
+ * least 2^6 values on each free side and 2^5 summed values (its summed
+ * range is split across blocks when there are few output tiles; the
+ * partials then live in stream-ordered scratch, cudaMallocAsync), the
+ * generic kernel otherwise.  Bit j of a tensor's linear offset is index labels_x[j];
  * every index has extent 2.  Indices of C must appear in A or B; indices of
  * A or B absent from C are summed; an index in A, B and C is a batch index.
  * precision WMC_FP64: a, b, c are float64.  WMC_SCALED_FP32: a, b, c are
@@ -308,8 +313,8 @@ void wmc_server_destroy(wmc_server_t *srv);
  * with a CUDA event after every launch, and synchronises `stream`.  For
  * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
  * kind[i] = 0 generic contraction, 1 streaming contraction, 4 streaming
- * contraction with TMA-staged operand, 2 leaf or bookkeeping kernel,
- * 3 memset; alg_bytes[i] = the bytes a contraction
+ * contraction with TMA-staged operand, 5 dense tiled contraction, 2 leaf or
+ * bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
  * must move (|A| + |B| + |C| in its element type).  Returns the launch
  * count through *n_launches.  Same arguments and errors as
  * wmc_execute_device; creates and destroys its own events. */

@@ -68,7 +68,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -79,6 +79,7 @@ struct Launch {
   K1Params k1;
   K2Params k2;
   wmc::dev::K2TParams k2t;
+  wmc::dev::K4Params k4;
   size_t smem = 0;
   // relative byte offsets (patched with the workspace base at capture)
   int64_t off_a = -1, off_b = -1, off_c = -1;
@@ -357,6 +358,53 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
   return smem <= 160 * 1024;
 }
 
+// Dense batched-matrix-product form (K4): every summed index in both
+// operands, at least 2^6 values of i and of j, 2^5 of s; query bits only
+// as batch indices.
+bool try_k4(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
+            const std::vector<int32_t> &LC, bool f64, wmc::dev::K4Params &p) {
+  std::vector<int32_t> iv, jv, sv, bv;
+  for (int32_t l : LA) {
+    const bool inB = pos_of(LB, l) >= 0, inC = pos_of(LC, l) >= 0;
+    if (inC && inB) bv.push_back(l);
+    else if (inC) iv.push_back(l);
+    else if (inB) sv.push_back(l);
+    else return false;  // summed in A only
+  }
+  for (int32_t l : LB) {
+    const bool inA = pos_of(LA, l) >= 0, inC = pos_of(LC, l) >= 0;
+    if (!inA && inC) jv.push_back(l);
+    else if (!inA && !inC) return false;  // summed in B only
+  }
+  for (int32_t l : iv) if (l < 0) return false;
+  for (int32_t l : jv) if (l < 0) return false;
+  if (iv.size() < 6 || jv.size() < 6 || sv.size() < 1) return false;
+  if (!f64 && sv.size() > 16) return false;  // float64 accumulation beyond 2^16 terms (k1)
+  if (iv.size() + jv.size() + sv.size() + bv.size() > 62) return false;
+  std::sort(sv.begin(), sv.end());  // the canonical summation order
+  auto by_pos = [](const std::vector<int32_t> &L) {
+    return [&L](int32_t x, int32_t y) { return pos_of(L, x) < pos_of(L, y); };
+  };
+  std::sort(iv.begin(), iv.end(), by_pos(LA));
+  std::sort(jv.begin(), jv.end(), by_pos(LB));
+  std::memset(&p, 0, sizeof(p));
+  p.ni = (int32_t)iv.size(); p.nj = (int32_t)jv.size(); p.ns = (int32_t)sv.size(); p.nb = (int32_t)bv.size();
+  for (size_t t = 0; t < iv.size(); ++t) { p.iA[t] = (int8_t)pos_of(LA, iv[t]); p.iC[t] = (int8_t)pos_of(LC, iv[t]); }
+  for (size_t t = 0; t < jv.size(); ++t) { p.jB[t] = (int8_t)pos_of(LB, jv[t]); p.jC[t] = (int8_t)pos_of(LC, jv[t]); }
+  for (size_t t = 0; t < sv.size(); ++t) { p.sA[t] = (int8_t)pos_of(LA, sv[t]); p.sB[t] = (int8_t)pos_of(LB, sv[t]); }
+  for (size_t t = 0; t < bv.size(); ++t) {
+    p.bA[t] = (int8_t)pos_of(LA, bv[t]); p.bB[t] = (int8_t)pos_of(LB, bv[t]); p.bC[t] = (int8_t)pos_of(LC, bv[t]);
+  }
+  int minAi = 99, minAs = 99, minBj = 99, minBs = 99, minCi = 99, minCj = 99;
+  for (int t = 0; t < p.ni; ++t) { minAi = std::min(minAi, (int)p.iA[t]); minCi = std::min(minCi, (int)p.iC[t]); }
+  for (int t = 0; t < p.nj; ++t) { minBj = std::min(minBj, (int)p.jB[t]); minCj = std::min(minCj, (int)p.jC[t]); }
+  for (int t = 0; t < p.ns; ++t) { minAs = std::min(minAs, (int)p.sA[t]); minBs = std::min(minBs, (int)p.sB[t]); }
+  p.a_i_fast = minAi < minAs;
+  p.b_j_fast = minBj < minBs;
+  p.c_i_fast = minCi < minCj;
+  return true;
+}
+
 void fill_k1(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
              const std::vector<int32_t> &LC, K1Params &p) {
   std::memset(&p, 0, sizeof(p));
@@ -539,6 +587,23 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
         }
       }
     }
+    wmc::dev::K4Params p4;
+    if (!used_k2 && !is_root && try_k4(LA, LB, LC, st.f64, p4)) {
+      // dense batched product; unsplit, so its summation order is k1's
+      used_k2 = true;
+      l.kind = L_K4;
+      l.k4 = p4;
+      l.ti = st.f64 ? TD : TF;
+      l.off_a = st.t_off[(size_t)nd.a];
+      l.off_b = st.t_off[(size_t)nd.b];
+      l.meta_a = st.t_meta[(size_t)nd.a];
+      l.meta_b = st.t_meta[(size_t)nd.b];
+      l.id_a = nd.a;
+      l.id_b = nd.b;
+      l.k4.ma.qmask = A.has_q ? Qp - 1 : 0;
+      l.k4.mb.qmask = B.has_q ? Qp - 1 : 0;
+      l.blocks = (int64_t)1 << (p4.ni - 6 + p4.nj - 6 + p4.nb);
+    }
     if (!used_k2) {
       l.kind = L_K1;
       fill_k1(LA, LB, LC, l.k1);
@@ -560,7 +625,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     l.meta_c = st.t_meta[(size_t)nd.c];
     l.id_c = nd.c;
     l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
-    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : l.k2.mc;
+    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : (l.kind == L_K4 ? l.k4.mc : l.k2.mc);
     mc.Qc = C.has_q ? Qp : 1;
     mc.Q = Qp;
     mc.scale_inputs = 1;
@@ -731,6 +796,17 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         tp.debug_stall = stall_armed ? 1 : 0;
         stall_armed = false;
         launch_k2t(l, tp, s);
+        break;
+      }
+      case L_K4: {
+        wmc::dev::K4Params p = l.k4;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
+        if (l.ti == TD) dev::k4_dense<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        else dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
         break;
       }
       case L_K2: {
@@ -973,7 +1049,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -1130,12 +1206,52 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
   }
   dev::Meta ma{exp_a, nullptr, nullptr, 0}, mb{exp_b, nullptr, nullptr, 0};
   dev::OutMeta mc{exp_c, nullptr, nullptr, nullptr, 1, 1, 0};
+  dev::K4Params p4;
+  if (!k2 && try_k4(LA, LB, LC, f64, p4)) {
+    p4.A = a; p4.B = b; p4.C = c; p4.ma = ma; p4.mb = mb; p4.mc = mc;
+    const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
+    // few output tiles and a long summed range: split the range into
+    // groups of whole 256-term blocks, each group's partials in stream-
+    // ordered scratch, then add the groups in order
+    int g = 0;
+    while (p4.ns - 8 - g > 0 && (tiles << g) < 2 * 148 && g < 9) ++g;
+    if (p4.ns <= 8) g = 0;
+    p4.groups_log2 = g;
+    void *scratch = nullptr;
+    if (g) {
+      const size_t bytes = ((size_t)tiles << g) * 4096 * (f64 ? 8 : 4);
+      CUDA_TRY(cudaMallocAsync(&scratch, bytes, s));
+      p4.partial = scratch;
+    }
+    if (f64) dev::k4_dense<double><<<tiles << g, 256, 0, s>>>(p4);
+    else dev::k4_dense<float><<<tiles << g, 256, 0, s>>>(p4);
+    g_launches.fetch_add(1);
+    if (g) {
+      if (f64) dev::k4_reduce<double><<<tiles, 256, 0, s>>>(p4);
+      else dev::k4_reduce<float><<<tiles, 256, 0, s>>>(p4);
+      g_launches.fetch_add(1);
+      CUDA_TRY(cudaFreeAsync(scratch, s));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return WMC_OK;
+  }
   if (k2) {
     l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = vmax; l.kmax = kmax; l.fmax = fmax;
     l.blocks = grid_for(1ull << p2.log2_nu);
     p2.A = use_a ? a : b; p2.B = use_a ? b : a; p2.C = c;
     p2.ma = use_a ? ma : mb; p2.mb = use_a ? mb : ma; p2.mc = mc;
-    launch_k2(l, p2, s);
+    if (try_k2_tma(p2, use_a ? LA : LB, use_a ? LB : LA, f64, false, false, 1, l.k2t, l.smem)) {
+      const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
+      const int kf = p2.k + p2.f;
+      const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
+      const int per_sm = std::min(per_sm_regs, l.smem <= 72 * 1024 ? 3 : (l.smem <= 108 * 1024 ? 2 : 1));
+      l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
+      l.k2t.k = p2;
+      l.k2t.err = nullptr;
+      launch_k2t(l, l.k2t, s);
+    } else {
+      launch_k2(l, p2, s);
+    }
   } else {
     l.kind = L_K1;
     fill_k1(LA, LB, LC, l.k1);
@@ -1276,6 +1392,8 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
   size_t li = 0;
   for (const Launch &l : st->launches) {
     ++li;
+    // k4 offsets are bit scatters onto each tensor's own positions: in
+    // bounds by construction
     if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1) continue;
     const int64_t ta = l.id_a, tb = l.id_b, tc = l.id_c;
     if (ta < 0 || tb < 0 || tc < 0) { set_error("launch %zu: unknown tensor", li); return WMC_EINVAL; }

@@ -717,6 +717,179 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
+// ------------------------------------------------------------ K4 dense
+//
+// C[b, i, j] = sum_s A[b, i, s] * B[b, s, j] when the node is a real
+// batched matrix product: i = A-only kept indices, j = S... B-only kept
+// indices, s = summed indices present in both operands, b = batch indices.
+// A 64 x 64 output tile per block (256 threads, 4 x 4 outputs each), the
+// summed range in chunks of 32 staged in shared memory.  Offsets are bit
+// scatters: per index group a table for the tile-local bits plus a base
+// for the high bits.  Summation order equals k1_generic's (ascending s,
+// serial within 256-term blocks, then a serial sum of the blocks), so the
+// two kernels give identical results.
+
+struct K4Params {
+  const void *A;
+  const void *B;
+  void *C;
+  Meta ma, mb;
+  OutMeta mc;
+  int32_t ni, nj, ns, nb;     // bits of i, j, s, b
+  int8_t iA[32], iC[32];      // i bit -> position in A, in C
+  int8_t jB[32], jC[32];      // j bit -> position in B, in C
+  int8_t sA[32], sB[32];      // s bit -> position in A, in B
+  int8_t bA[32], bB[32], bC[32];
+  int32_t groups_log2;  // split of the summed range (0: none)
+  void *partial;        // [2^groups_log2][tiles * 4096] partial sums when split
+  int32_t a_i_fast;   // A's lowest (i, s) bit is an i bit: load A along i
+  int32_t b_j_fast;   // B's lowest (s, j) bit is a j bit: load B along j
+  int32_t c_i_fast;   // C's lowest (i, j) bit is an i bit: threads along i
+};
+
+__device__ __forceinline__ uint32_t scatter_bits(uint32_t v, const int8_t *pos, int n) {
+  uint32_t o = 0;
+  for (int t = 0; t < n; ++t)
+    if ((v >> t) & 1u) o |= 1u << pos[t];
+  return o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k4_dense(K4Params p) {
+  constexpr int TI = 64, TJ = 64, TK = 32, RI = 4, RJ = 4;
+  __shared__ T As[TK][TI + 1];
+  __shared__ T Bs[TK][TJ + 1];
+  __shared__ uint32_t offA_i[TI], offB_j[TJ], offC_i[TI], offC_j[TJ];
+  __shared__ uint32_t offA_s[TK], offB_s[TK];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  const T *A = (const T *)p.A;
+  const T *B = (const T *)p.B;
+  T *C = (T *)p.C;
+  const uint32_t i_tiles = 1u << (p.ni - 6), j_tiles = 1u << (p.nj - 6);
+  const uint32_t n_tiles = i_tiles * j_tiles << p.nb;
+  const uint32_t tile = blockIdx.x % n_tiles;
+  const uint32_t group = blockIdx.x / n_tiles;
+  const uint32_t it = tile % i_tiles, jt = (tile / i_tiles) % j_tiles, bb = tile / (i_tiles * j_tiles);
+  // tile-local tables (low 6 bits of i and j, low 5 bits of s)
+  for (int x = threadIdx.x; x < TI; x += blockDim.x) {
+    offA_i[x] = scatter_bits(x, p.iA, 6);
+    offC_i[x] = scatter_bits(x, p.iC, 6);
+  }
+  for (int x = threadIdx.x; x < TJ; x += blockDim.x) {
+    offB_j[x] = scatter_bits(x, p.jB, 6);
+    offC_j[x] = scatter_bits(x, p.jC, 6);
+  }
+  const int tk = p.ns < 5 ? p.ns : 5;  // summed bits per chunk
+  const int TKr = 1 << tk;
+  for (int x = threadIdx.x; x < TK; x += blockDim.x) {
+    offA_s[x] = scatter_bits(x, p.sA, tk);
+    offB_s[x] = scatter_bits(x, p.sB, tk);
+  }
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  // high parts
+  const uint32_t baseA = scatter_bits(it, p.iA + 6, p.ni - 6) | scatter_bits(bb, p.bA, p.nb);
+  const uint32_t baseB = scatter_bits(jt, p.jB + 6, p.nj - 6) | scatter_bits(bb, p.bB, p.nb);
+  const uint32_t baseC = scatter_bits(it, p.iC + 6, p.ni - 6) | scatter_bits(jt, p.jC + 6, p.nj - 6) |
+                         scatter_bits(bb, p.bC, p.nb);
+  __syncthreads();
+  // every output of the block has the same query lane? the query bits are
+  // batch bits (bb), so yes: one scale per operand per block
+  const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
+  const T sa = operand_scale<T>(p.ma, q, p.mc.scale_inputs);
+  const T sb = operand_scale<T>(p.mb, q, p.mc.scale_inputs);
+  // output mapping: consecutive threads along whichever of i, j is C's fast index
+  const int ty = p.c_i_fast ? (int)(threadIdx.x % 16) : (int)(threadIdx.x / 16);
+  const int tx = p.c_i_fast ? (int)(threadIdx.x / 16) : (int)(threadIdx.x % 16);
+  T acc[RI][RJ], part[RI][RJ];
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int c = 0; c < RJ; ++c) acc[r][c] = part[r][c] = (T)0;
+  const uint32_t n_s = 1u << p.ns;
+  const bool blocked = p.ns > 8;
+  const uint32_t s_len = n_s >> p.groups_log2;  // a multiple of 256 when split
+  for (uint32_t s0 = group * s_len; s0 < (group + 1) * s_len; s0 += TKr) {
+    const uint32_t hiA = scatter_bits(s0 >> tk, p.sA + tk, p.ns - tk);
+    const uint32_t hiB = scatter_bits(s0 >> tk, p.sB + tk, p.ns - tk);
+    for (int x = threadIdx.x; x < TKr * TI; x += blockDim.x) {
+      const int kk = p.a_i_fast ? x / TI : x % TKr, ii = p.a_i_fast ? x % TI : x / TKr;
+      As[kk][ii] = __ldg(A + (baseA | hiA | offA_i[ii] | offA_s[kk])) * sa;
+    }
+    for (int x = threadIdx.x; x < TKr * TJ; x += blockDim.x) {
+      const int jj = p.b_j_fast ? x % TJ : x / TKr, kk = p.b_j_fast ? x / TJ : x % TKr;
+      Bs[kk][jj] = __ldg(B + (baseB | hiB | offB_j[jj] | offB_s[kk])) * sb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TKr; ++kk) {
+      T a[RI], b[RJ];
+#pragma unroll
+      for (int r = 0; r < RI; ++r) a[r] = As[kk][ty * RI + r];
+#pragma unroll
+      for (int c = 0; c < RJ; ++c) b[c] = Bs[kk][tx * RJ + c];
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < RJ; ++c) part[r][c] = fma_t(a[r], b[c], part[r][c]);
+    }
+    __syncthreads();
+    if (blocked && ((s0 + TKr) & 255u) == 0) {
+#pragma unroll
+      for (int r = 0; r < RI; ++r)
+#pragma unroll
+        for (int c = 0; c < RJ; ++c) { acc[r][c] += part[r][c]; part[r][c] = (T)0; }
+    }
+  }
+  if (p.groups_log2) {
+    // this group's partial sums; k4_reduce adds the groups in order
+    T *P = (T *)p.partial + ((size_t)group * n_tiles + tile) * (TI * TJ);
+#pragma unroll
+    for (int r = 0; r < RI; ++r)
+#pragma unroll
+      for (int c = 0; c < RJ; ++c) P[(ty * RI + r) * TJ + tx * RJ + c] = acc[r][c];
+    return;
+  }
+  T tmax = (T)0, tmin = (T)INFINITY;
+#pragma unroll
+  for (int r = 0; r < RI; ++r)
+#pragma unroll
+    for (int c = 0; c < RJ; ++c) {
+      const T v = blocked ? acc[r][c] : part[r][c];
+      C[baseC | offC_i[ty * RI + r] | offC_j[tx * RJ + c]] = v;
+      track(v, tmax, tmin);
+    }
+  publish(smax, smin, q, tmax, tmin);
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
+// Split summed range: C = sum over groups (in group order) of the partials.
+template <typename T>
+__global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  const uint32_t i_tiles = 1u << (p.ni - 6), j_tiles = 1u << (p.nj - 6);
+  const uint32_t n_tiles = i_tiles * j_tiles << p.nb;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t it = tile % i_tiles, jt = (tile / i_tiles) % j_tiles, bb = tile / (i_tiles * j_tiles);
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  const uint32_t baseC = scatter_bits(it, p.iC + 6, p.ni - 6) | scatter_bits(jt, p.jC + 6, p.nj - 6) |
+                         scatter_bits(bb, p.bC, p.nb);
+  __syncthreads();
+  const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
+  const T *P = (const T *)p.partial;
+  T tmax = (T)0, tmin = (T)INFINITY;
+  for (int x = threadIdx.x; x < 64 * 64; x += blockDim.x) {
+    const int ii = x / 64, jj = x % 64;
+    T v = (T)0;
+    for (uint32_t g = 0; g < (1u << p.groups_log2); ++g) v += P[((size_t)g * n_tiles + tile) * 4096 + x];
+    ((T *)p.C)[baseC | scatter_bits(ii, p.iC, 6) | scatter_bits(jj, p.jC, 6)] = v;
+    track(v, tmax, tmin);
+  }
+  publish(smax, smin, q, tmax, tmin);
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
 // --------------------------------------------------------------- leaves
 
 struct ClauseLeaf {

@@ -193,6 +193,8 @@ def _pair_tol(k, precision):
 SWEEP_SMALL = [(ra, rb, b, k) for (b, k) in [(0, 1), (2, 1), (4, 1), (0, 4), (2, 4), (4, 4),
                                               (0, 8), (2, 8), (4, 8), (0, 16)]
                for (ra, rb) in [(b + k + 3, b + k + 2), (b + k + 9, b + k + 1)]]
+# dense batched products (at least 2^6 free values on each side): the tiled kernel
+SWEEP_SMALL += [(13, 14, 2, 5), (15, 14, 0, 8), (16, 16, 4, 6), (14, 14, 0, 8)]
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
