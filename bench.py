@@ -274,7 +274,7 @@ def run_ours(args, rank, world):
     k_kind = np.array([kinds[i] for i in range(L)])
     k_bytes = np.array([nbytes[i] for i in range(L)])
     hbm, src = peaks()
-    sel = (k_kind == 1) | (k_kind == 4)
+    sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 6)
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
     # DRAM bytes from one ncu capture of a full-size k2_tma launch (profiles/
@@ -286,6 +286,7 @@ def run_ours(args, rank, world):
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
                 "kernel": "k2_tma / k2_stream (streaming pairwise contraction)",
                 "tma_launches": int((k_kind == 4).sum()),
+                "fused_launches": int((k_kind == 6).sum()),
                 "tma_share_of_streaming": float(k_ms[k_kind == 4].sum() / max(k_ms[sel].sum(), 1e-12)),
                 "launches": int(sel.sum()), "share_of_walk": float(k_ms[sel].sum() / walk_ms),
                 "avg_launch_us": float(k_ms[sel].mean() * 1e3) if sel.any() else None,

@@ -313,8 +313,8 @@ void wmc_server_destroy(wmc_server_t *srv);
  * with a CUDA event after every launch, and synchronises `stream`.  For
  * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
  * kind[i] = 0 generic contraction, 1 streaming contraction, 4 streaming
- * contraction with TMA-staged operand, 5 dense tiled contraction, 2 leaf or
- * bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
+ * contraction with TMA-staged operand, 5 dense tiled contraction, 6 fused
+ * pair of eliminations, 2 leaf or bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
  * must move (|A| + |B| + |C| in its element type).  Returns the launch
  * count through *n_launches.  Same arguments and errors as
  * wmc_execute_device; creates and destroys its own events. */
@@ -324,6 +324,11 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                      uint32_t *d_flags, void *stream, int64_t n_max,
                      float *node_ms, int32_t *kind, double *alg_bytes,
                      int64_t *n_launches);
+
+/* Execution option (default on): contract two consecutive frontier
+ * eliminations in one pass (the intermediate tensor never reaches memory).
+ * Affects plans laid out after the call (a plan caches its layout per Q). */
+void wmc_set_fusion(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,

@@ -33,10 +33,12 @@ namespace wmc { const Network &network_of(const wmc_network_t *n); }
 static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_fail_allocs{0};
 static std::atomic<int32_t> g_debug_stall{0};
+static std::atomic<int32_t> g_fuse{1};  // fuse consecutive frontier eliminations (k2_fused)
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
 extern "C" void wmc_debug_stall_copies(int32_t on) { g_debug_stall.store(on); }
+extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -68,7 +70,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_K4, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2F, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -80,7 +82,9 @@ struct Launch {
   K2Params k2;
   wmc::dev::K2TParams k2t;
   wmc::dev::K4Params k4;
+  wmc::dev::K2FParams k2f;
   size_t smem = 0;
+  int64_t off_s2 = -1, meta_s2 = -1, id_s2 = -1, id_c1 = -1;  // fused pair
   // relative byte offsets (patched with the workspace base at capture)
   int64_t off_a = -1, off_b = -1, off_c = -1;
   int64_t meta_a = -1, meta_b = -1, meta_c = -1;  // slot indices
@@ -358,6 +362,138 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
   return smem <= 160 * 1024;
 }
 
+// Fused pair of eliminations (k2_fused): node i = P1 . S1 -> C1 and node
+// j = C1 . S2 -> C2, both one-summed one-added index with the added index
+// at the summed index's position.  Labels are full (with query bits).
+bool try_fuse(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS1,
+              const std::vector<int32_t> &LC1, const std::vector<int32_t> &LS2,
+              const std::vector<int32_t> &LC2, bool f64, bool p_has_q, bool s1_has_q, int32_t Qp,
+              wmc::dev::K2FParams &fp, size_t &smem) {
+  auto only = [](const std::vector<int32_t> &v) { return v.size() == 1 ? v[0] : INT32_MIN; };
+  std::vector<int32_t> t;
+  for (int32_t l : LP) if (pos_of(LC1, l) < 0) t.push_back(l);
+  for (int32_t l : LS1) if (pos_of(LC1, l) < 0 && pos_of(LP, l) < 0) t.push_back(l);
+  const int32_t x1 = only(t);
+  t.clear();
+  for (int32_t l : LS1) if (pos_of(LC1, l) >= 0 && pos_of(LP, l) < 0) t.push_back(l);
+  const int32_t y1 = only(t);
+  t.clear();
+  for (int32_t l : LC1) if (pos_of(LC2, l) < 0) t.push_back(l);
+  for (int32_t l : LS2) if (pos_of(LC2, l) < 0 && pos_of(LC1, l) < 0) t.push_back(l);
+  const int32_t x2 = only(t);
+  t.clear();
+  for (int32_t l : LS2) if (pos_of(LC2, l) >= 0 && pos_of(LC1, l) < 0) t.push_back(l);
+  const int32_t y2 = only(t);
+  if (x1 == INT32_MIN || y1 == INT32_MIN || x2 == INT32_MIN || y2 == INT32_MIN) return false;
+  if (pos_of(LP, x1) < 0 || pos_of(LS1, x1) < 0 || pos_of(LP, x2) < 0 || pos_of(LS2, x2) < 0) return false;
+  if (LS1.size() > 12 || LS2.size() > 12) return false;
+  const int p1 = pos_of(LP, x1), p2 = pos_of(LP, x2);
+  // C1 = P with x1 -> y1 in place; C2 = C1 with x2 -> y2 in place
+  if (LC1.size() != LP.size() || LC2.size() != LP.size()) return false;
+  for (size_t q = 0; q < LP.size(); ++q) {
+    const int32_t want1 = (int)q == p1 ? y1 : LP[q];
+    const int32_t want2 = (int)q == p2 ? y2 : want1;
+    if (LC1[q] != want1 || LC2[q] != want2) return false;
+  }
+  const int rP = (int)LP.size();
+  std::memset(&fp, 0, sizeof(fp));
+  K2Params &k = fp.t.k;
+  const int lo = std::min(p1, p2), hi = std::max(p1, p2);
+  k.n_insA = 2; k.insA[0] = (int8_t)lo; k.insA[1] = (int8_t)hi;
+  k.n_insC = 2; k.insC[0] = (int8_t)lo; k.insC[1] = (int8_t)hi;
+  k.k = 2; k.f = 2;
+  int vbits = f64 ? 1 : 2;
+  if (rP - 2 < vbits || lo < vbits) vbits = 0;
+  k.vbits = vbits;
+  k.log2_nu = rP - 2 - vbits;
+  if (p_has_q && (dev::kThreads * (1 << vbits)) % Qp != 0) return false;
+  // gathers of the small operands' batch bits from C2's offset
+  auto gathers = [&](const std::vector<int32_t> &LSx, int32_t skip_a, int32_t skip_b, int32_t loop,
+                     int8_t *seg_c, int8_t *seg_b, int8_t *seg_len, int32_t &nseg, uint32_t *dv,
+                     int32_t &mode) -> bool {
+    std::vector<std::pair<int, int>> bb;
+    for (size_t j = 0; j < LSx.size(); ++j) {
+      const int32_t l = LSx[j];
+      if (l == skip_a || l == skip_b || l == loop) continue;
+      const int pc = pos_of(LC2, l);
+      if (pc < 0 || pc == p1 || pc == p2) return false;
+      if (pc < vbits) {
+        for (int e = 0; e < (1 << vbits); ++e)
+          if ((e >> pc) & 1) dv[e] |= 1u << j;
+      } else {
+        bb.push_back({pc, (int)j});
+      }
+    }
+    std::sort(bb.begin(), bb.end());
+    nseg = 0;
+    for (size_t i = 0; i < bb.size();) {
+      size_t j = i + 1;
+      while (j < bb.size() && bb[j].first == bb[j - 1].first + 1 && bb[j].second == bb[j - 1].second + 1) ++j;
+      if (nseg >= 16) return false;
+      seg_c[nseg] = (int8_t)bb[i].first; seg_b[nseg] = (int8_t)bb[i].second; seg_len[nseg] = (int8_t)(j - i);
+      ++nseg;
+      i = j;
+    }
+    bool contiguous = true, broadcast = true;
+    for (int e = 0; e < (1 << vbits); ++e) {
+      contiguous &= (dv[e] == (uint32_t)e);
+      broadcast &= (dv[e] == 0u);
+    }
+    mode = contiguous ? 1 : (broadcast ? 2 : 0);
+    return true;
+  };
+  if (!gathers(LS1, x1, y1, x2, k.seg_c, k.seg_b, k.seg_len, k.n_seg, fp.dv1, k.b_vec)) return false;
+  if (!gathers(LS2, x2, y2, y1, fp.seg2_c, fp.seg2_b, fp.seg2_len, fp.n_seg2, fp.dv2, fp.b_vec2)) return false;
+  const int sx1 = pos_of(LS1, x1), sy1 = pos_of(LS1, y1), sx2_1 = pos_of(LS1, x2);
+  const int sx2 = pos_of(LS2, x2), sy2 = pos_of(LS2, y2), sy1_2 = pos_of(LS2, y1);
+  for (int c = 0; c < 8; ++c) {
+    const int a0 = c & 1, a1 = (c >> 1) & 1, a2 = (c >> 2) & 1;
+    fp.d1[c] = (a0 ? 1u << sx1 : 0u) | (a1 ? 1u << sy1 : 0u) | ((a2 && sx2_1 >= 0) ? 1u << sx2_1 : 0u);
+    fp.d2[c] = (a0 ? 1u << sx2 : 0u) | (a1 ? 1u << sy2 : 0u) | ((a2 && sy1_2 >= 0) ? 1u << sy1_2 : 0u);
+  }
+  for (int c = 0; c < 4; ++c) fp.dCf[c] = ((c & 1) ? 1u << p1 : 0u) | ((c & 2) ? 1u << p2 : 0u);
+  // tiling of P over its kept indices (as try_k2_tma, half the tile: four
+  // P values per unit and two staged small operands)
+  const int V = 1 << vbits;
+  const int J = V == 1 ? 2 : 1;
+  int tb = 0;
+  while ((1 << tb) < dev::kThreads * V * J) ++tb;
+  if (k.log2_nu + vbits < tb + 3) return false;
+  std::vector<int> kept;
+  for (int q = 0; q < rP; ++q)
+    if (q != p1 && q != p2) kept.push_back(q);
+  if ((int)kept.size() < tb) return false;
+  const int top = kept[(size_t)tb - 1] + 1;
+  std::vector<int> lowv, highv;
+  for (int q : {lo, hi}) (q < top ? lowv : highv).push_back(q);
+  wmc::dev::K2TParams &tp = fp.t;
+  tp.tb = tb;
+  tp.run_log2 = top;
+  tp.nruns = 1 << (int)highv.size();
+  tp.n_lowA = (int)lowv.size();
+  for (size_t j = 0; j < lowv.size(); ++j) tp.lowA[j] = (int8_t)lowv[j];
+  for (int r = 0; r < tp.nruns; ++r) {
+    uint32_t o = 0;
+    for (size_t j = 0; j < highv.size(); ++j)
+      if ((r >> j) & 1) o |= 1u << highv[j];
+    tp.run_off[r] = o;
+  }
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t da = ((c & 1) ? 1u << p1 : 0u) | ((c & 2) ? 1u << p2 : 0u);
+    uint32_t r = 0;
+    for (size_t j = 0; j < highv.size(); ++j)
+      if ((da >> highv[j]) & 1) r |= 1u << j;
+    fp.pA[c] = (r << top) | (da & ((1u << top) - 1u));
+  }
+  tp.s_log2 = (int)LS1.size();
+  fp.s2_log2 = (int)LS2.size();
+  tp.fold_sa = (p_has_q && s1_has_q) ? 1 : 0;
+  const size_t es = f64 ? 8 : 4;
+  smem = (size_t)dev::kStages * ((size_t)tp.nruns << top) * es + (((es << tp.s_log2) + 15) & ~(size_t)15) +
+         (((es << fp.s2_log2) + 15) & ~(size_t)15) + (16 + 2 * es) * (size_t)Qp;
+  return smem <= 100 * 1024;
+}
+
 // Dense batched-matrix-product form (K4): every summed index in both
 // operands, at least 2^6 values of i and of j, 2^5 of s; query bits only
 // as batch indices.
@@ -477,20 +613,166 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   // leaves: resident for the whole walk
   for (int64_t i = 0; i < plan.n_leaves; ++i) { st.t_off[(size_t)i] = off; off += align_up(bytes[(size_t)i]); }
   const int64_t arena0 = off;
+  st.max_roundings = plan.tensors[(size_t)root].roundings;
+
+  // ---- per-node kernel choice (offsets are filled in once laid out)
+  std::vector<Launch> node_l(plan.nodes.size());
+  for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+    const Node &nd = plan.nodes[ni];
+    const TensorInfo &A = plan.tensors[(size_t)nd.a];
+    const TensorInfo &B = plan.tensors[(size_t)nd.b];
+    const TensorInfo &C = plan.tensors[(size_t)nd.c];
+    std::vector<int32_t> LA = full_labels(A, m), LB = full_labels(B, m), LC = full_labels(C, m);
+    Launch &l = node_l[ni];
+    const bool is_root = nd.c == root;
+    bool used_k2 = false;
+    if (!is_root) {
+      const bool a_first = LA.size() >= LB.size();
+      int vmax = 1, kmax = 1, fmax = 1;
+      K2Params p2;
+      for (int attempt = 0; attempt < 2 && !used_k2; ++attempt) {
+        bool use_a = (attempt == 0) == a_first;
+        const std::vector<int32_t> &LP = use_a ? LA : LB;
+        const std::vector<int32_t> &LS = use_a ? LB : LA;
+        if (try_k2(LP, LS, LC, st.f64, p2, vmax, kmax, fmax)) {
+          used_k2 = true;
+          l.kind = L_K2;
+          l.ti = st.f64 ? TD : TF;
+          l.v = vmax; l.kmax = kmax; l.fmax = fmax;
+          l.k2 = p2;
+          l.id_a = use_a ? nd.a : nd.b;
+          l.id_b = use_a ? nd.b : nd.a;
+          l.k2.ma.qmask = (use_a ? A : B).has_q ? Qp - 1 : 0;
+          l.k2.mb.qmask = (use_a ? B : A).has_q ? Qp - 1 : 0;
+          l.blocks = grid_for(1ull << p2.log2_nu);
+          if (try_k2_tma(l.k2, use_a ? LA : LB, use_a ? LB : LA, st.f64, (use_a ? A : B).has_q,
+                         (use_a ? B : A).has_q, Qp, l.k2t, l.smem)) {
+            l.kind = L_K2T;
+            const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
+            const int kf = l.k2.k + l.k2.f;  // register-limited CTAs per SM (launch bounds)
+            const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
+            const int per_sm = std::min(per_sm_regs, l.smem <= 72 * 1024 ? 3 : (l.smem <= 108 * 1024 ? 2 : 1));
+            l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
+          }
+        }
+      }
+    }
+    wmc::dev::K4Params p4;
+    if (!used_k2 && !is_root && try_k4(LA, LB, LC, st.f64, p4)) {
+      // dense batched product; unsplit, so its summation order is k1's
+      used_k2 = true;
+      l.kind = L_K4;
+      l.k4 = p4;
+      l.ti = st.f64 ? TD : TF;
+      l.id_a = nd.a;
+      l.id_b = nd.b;
+      l.k4.ma.qmask = A.has_q ? Qp - 1 : 0;
+      l.k4.mb.qmask = B.has_q ? Qp - 1 : 0;
+      l.blocks = (int64_t)1 << (p4.ni - 6 + p4.nj - 6 + p4.nb);
+    }
+    if (!used_k2) {
+      l.kind = L_K1;
+      fill_k1(LA, LB, LC, l.k1);
+      if (l.k1.k > 24) { set_error("node sums %d indices (max 24)", l.k1.k); return WMC_EPLAN_TOO_BIG; }
+      l.ti = st.f64 ? TD : TF;
+      l.ta = (st.f64 || is_root || l.k1.k > 16) ? TD : TF;
+      l.to = st.t_dbl[(size_t)nd.c] ? TD : TF;
+      l.id_a = nd.a;
+      l.id_b = nd.b;
+      l.k1.ma.qmask = A.has_q ? Qp - 1 : 0;
+      l.k1.mb.qmask = B.has_q ? Qp - 1 : 0;
+      l.blocks = grid_for(1ull << l.k1.rC);
+    }
+    l.id_c = nd.c;
+    l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
+    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : (l.kind == L_K4 ? l.k4.mc : l.k2.mc);
+    mc.Qc = C.has_q ? Qp : 1;
+    mc.Q = Qp;
+    mc.scale_inputs = 1;
+  }
+
+  // ---- fuse consecutive frontier eliminations (i, j): node j's large
+  // operand is node i's output; the nodes between them (j's small subtree)
+  // move in front of i.  Steps are listed in execution order.
+  struct Step { int64_t node; int64_t fused_with; };  // fused_with = j or -1
+  std::vector<Step> steps;
+  {
+    std::vector<int64_t> consumer(plan.tensors.size(), -1);
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+      consumer[(size_t)plan.nodes[ni].a] = (int64_t)ni;
+      consumer[(size_t)plan.nodes[ni].b] = (int64_t)ni;
+    }
+    std::vector<int64_t> fuse_next(plan.nodes.size(), -1);
+    std::vector<uint8_t> absorbed(plan.nodes.size(), 0);
+    for (size_t ni = 0; ni < plan.nodes.size() && g_fuse.load(); ++ni) {
+      if (absorbed[ni]) continue;
+      const Launch &li = node_l[ni];
+      if (li.kind != L_K2T || li.k2.k != 1 || li.k2.f != 1) continue;
+      const int64_t nj = consumer[(size_t)plan.nodes[ni].c];
+      if (nj < 0 || absorbed[(size_t)nj]) continue;
+      const Launch &lj = node_l[(size_t)nj];
+      if (lj.kind != L_K2T || lj.k2.k != 1 || lj.k2.f != 1 || lj.id_a != plan.nodes[ni].c) continue;
+      if (lj.k2.vbits != li.k2.vbits) continue;
+      bool clean = true;  // nodes between i and j must not be fused already
+      for (int64_t q = (int64_t)ni + 1; q < nj; ++q) clean &= !absorbed[(size_t)q] && fuse_next[(size_t)q] < 0;
+      if (!clean) continue;
+      const TensorInfo &P = plan.tensors[(size_t)li.id_a], &S1 = plan.tensors[(size_t)li.id_b];
+      const TensorInfo &C1 = plan.tensors[(size_t)plan.nodes[ni].c];
+      const TensorInfo &S2 = plan.tensors[(size_t)lj.id_b], &C2 = plan.tensors[(size_t)plan.nodes[(size_t)nj].c];
+      Launch f;
+      if (!try_fuse(full_labels(P, m), full_labels(S1, m), full_labels(C1, m), full_labels(S2, m),
+                    full_labels(C2, m), st.f64, P.has_q, S1.has_q, Qp, f.k2f, f.smem))
+        continue;
+      fuse_next[ni] = nj;
+      absorbed[(size_t)nj] = 1;
+      for (int64_t q = (int64_t)ni + 1; q < nj; ++q) absorbed[(size_t)q] = 2;  // moved before i
+      Launch &dst = node_l[ni];
+      f.kind = L_K2F;
+      f.ti = st.f64 ? TD : TF;
+      f.v = 1 << f.k2f.t.k.vbits;
+      f.id_a = li.id_a; f.id_b = li.id_b; f.id_s2 = lj.id_b; f.id_c = C2.node >= 0 ? plan.nodes[(size_t)nj].c : -1;
+      f.id_c1 = plan.nodes[ni].c;
+      f.k2f.t.k.ma.qmask = P.has_q ? Qp - 1 : 0;
+      f.k2f.t.k.mb.qmask = S1.has_q ? Qp - 1 : 0;
+      f.k2f.m2.qmask = S2.has_q ? Qp - 1 : 0;
+      f.k2f.t.k.mc.Qc = C2.has_q ? Qp : 1;
+      f.k2f.t.k.mc.Q = Qp;
+      f.k2f.t.k.mc.scale_inputs = 1;
+      const uint64_t n_tiles = 1ull << (f.k2f.t.k.log2_nu + f.k2f.t.k.vbits - f.k2f.t.tb);
+      f.blocks = (int64_t)std::min<uint64_t>(n_tiles, 148ull * 2);
+      f.alg_bytes = (double)bytes[(size_t)f.id_a] + (double)bytes[(size_t)f.id_b] +
+                    (double)bytes[(size_t)f.id_s2] + (double)bytes[(size_t)f.id_c];
+      dst = f;
+    }
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+      if (absorbed[ni]) continue;
+      if (fuse_next[ni] >= 0)
+        for (int64_t q = (int64_t)ni + 1; q < fuse_next[ni]; ++q) steps.push_back({q, -1});
+      steps.push_back({(int64_t)ni, fuse_next[ni]});
+    }
+  }
+
+  // ---- arena: first fit in execution order; children freed after use
   FirstFit ff;
   st.alg_bytes = 0;
   st.flops = 0;
+  auto release = [&](int64_t t) {
+    if (t >= plan.n_leaves) ff.release(st.t_off[(size_t)t] - arena0, bytes[(size_t)t]);
+  };
+  for (const Step &stp : steps) {
+    const Launch &l = node_l[(size_t)stp.node];
+    st.t_off[(size_t)l.id_c] = arena0 + ff.alloc(bytes[(size_t)l.id_c]);
+    release(l.id_a);
+    release(l.id_b);
+    if (l.kind == L_K2F) release(l.id_s2);
+    st.alg_bytes += l.alg_bytes;
+  }
   for (const Node &nd : plan.nodes) {
-    st.t_off[(size_t)nd.c] = arena0 + ff.alloc(bytes[(size_t)nd.c]);
-    for (int64_t ch : {nd.a, nd.b})
-      if (ch >= plan.n_leaves) ff.release(st.t_off[(size_t)ch] - arena0, bytes[(size_t)ch]);
-    st.alg_bytes += (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
     const TensorInfo &C = plan.tensors[(size_t)nd.c];
     st.flops += 2.0 * std::ldexp(1.0, nd.iter_rank + (C.has_q ? m : 0));
   }
   st.arena_bytes = ff.top;
   st.ws_bytes = arena0 + align_up(ff.top);
-  st.max_roundings = plan.tensors[(size_t)root].roundings;
 
   // ---- launches
   st.launches.clear();
@@ -544,91 +826,18 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Qp);
     st.launches.push_back(l);
   }
-  for (const Node &nd : plan.nodes) {
-    const TensorInfo &A = plan.tensors[(size_t)nd.a];
-    const TensorInfo &B = plan.tensors[(size_t)nd.b];
-    const TensorInfo &C = plan.tensors[(size_t)nd.c];
-    std::vector<int32_t> LA = full_labels(A, m), LB = full_labels(B, m), LC = full_labels(C, m);
-    Launch l;
-    const bool is_root = nd.c == root;
-    bool used_k2 = false;
-    if (!is_root) {
-      const bool a_first = LA.size() >= LB.size();
-      int vmax = 1, kmax = 1, fmax = 1;
-      K2Params p2;
-      for (int attempt = 0; attempt < 2 && !used_k2; ++attempt) {
-        bool use_a = (attempt == 0) == a_first;
-        const std::vector<int32_t> &LP = use_a ? LA : LB;
-        const std::vector<int32_t> &LS = use_a ? LB : LA;
-        if (try_k2(LP, LS, LC, st.f64, p2, vmax, kmax, fmax)) {
-          used_k2 = true;
-          l.kind = L_K2;
-          l.ti = st.f64 ? TD : TF;
-          l.v = vmax; l.kmax = kmax; l.fmax = fmax;
-          l.k2 = p2;
-          l.off_a = st.t_off[(size_t)(use_a ? nd.a : nd.b)];
-          l.off_b = st.t_off[(size_t)(use_a ? nd.b : nd.a)];
-          l.meta_a = st.t_meta[(size_t)(use_a ? nd.a : nd.b)];
-          l.meta_b = st.t_meta[(size_t)(use_a ? nd.b : nd.a)];
-          l.id_a = use_a ? nd.a : nd.b;
-          l.id_b = use_a ? nd.b : nd.a;
-          l.k2.ma.qmask = (use_a ? A : B).has_q ? Qp - 1 : 0;
-          l.k2.mb.qmask = (use_a ? B : A).has_q ? Qp - 1 : 0;
-          l.blocks = grid_for(1ull << p2.log2_nu);
-          if (try_k2_tma(l.k2, use_a ? LA : LB, use_a ? LB : LA, st.f64, (use_a ? A : B).has_q,
-                         (use_a ? B : A).has_q, Qp, l.k2t, l.smem)) {
-            l.kind = L_K2T;
-            const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
-            const int kf = l.k2.k + l.k2.f;  // register-limited CTAs per SM (launch bounds)
-            const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
-            const int per_sm = std::min(per_sm_regs, l.smem <= 72 * 1024 ? 3 : (l.smem <= 108 * 1024 ? 2 : 1));
-            l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
-          }
-        }
-      }
+  for (const Step &stp : steps) {
+    Launch l = node_l[(size_t)stp.node];
+    l.off_a = st.t_off[(size_t)l.id_a];
+    l.off_b = st.t_off[(size_t)l.id_b];
+    l.off_c = st.t_off[(size_t)l.id_c];
+    l.meta_a = st.t_meta[(size_t)l.id_a];
+    l.meta_b = st.t_meta[(size_t)l.id_b];
+    l.meta_c = st.t_meta[(size_t)l.id_c];
+    if (l.kind == L_K2F) {
+      l.off_s2 = st.t_off[(size_t)l.id_s2];
+      l.meta_s2 = st.t_meta[(size_t)l.id_s2];
     }
-    wmc::dev::K4Params p4;
-    if (!used_k2 && !is_root && try_k4(LA, LB, LC, st.f64, p4)) {
-      // dense batched product; unsplit, so its summation order is k1's
-      used_k2 = true;
-      l.kind = L_K4;
-      l.k4 = p4;
-      l.ti = st.f64 ? TD : TF;
-      l.off_a = st.t_off[(size_t)nd.a];
-      l.off_b = st.t_off[(size_t)nd.b];
-      l.meta_a = st.t_meta[(size_t)nd.a];
-      l.meta_b = st.t_meta[(size_t)nd.b];
-      l.id_a = nd.a;
-      l.id_b = nd.b;
-      l.k4.ma.qmask = A.has_q ? Qp - 1 : 0;
-      l.k4.mb.qmask = B.has_q ? Qp - 1 : 0;
-      l.blocks = (int64_t)1 << (p4.ni - 6 + p4.nj - 6 + p4.nb);
-    }
-    if (!used_k2) {
-      l.kind = L_K1;
-      fill_k1(LA, LB, LC, l.k1);
-      if (l.k1.k > 24) { set_error("node sums %d indices (max 24)", l.k1.k); return WMC_EPLAN_TOO_BIG; }
-      l.ti = st.f64 ? TD : TF;
-      l.ta = (st.f64 || is_root || l.k1.k > 16) ? TD : TF;
-      l.to = st.t_dbl[(size_t)nd.c] ? TD : TF;
-      l.off_a = st.t_off[(size_t)nd.a];
-      l.off_b = st.t_off[(size_t)nd.b];
-      l.meta_a = st.t_meta[(size_t)nd.a];
-      l.meta_b = st.t_meta[(size_t)nd.b];
-      l.id_a = nd.a;
-      l.id_b = nd.b;
-      l.k1.ma.qmask = A.has_q ? Qp - 1 : 0;
-      l.k1.mb.qmask = B.has_q ? Qp - 1 : 0;
-      l.blocks = grid_for(1ull << l.k1.rC);
-    }
-    l.off_c = st.t_off[(size_t)nd.c];
-    l.meta_c = st.t_meta[(size_t)nd.c];
-    l.id_c = nd.c;
-    l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
-    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : (l.kind == L_K4 ? l.k4.mc : l.k2.mc);
-    mc.Qc = C.has_q ? Qp : 1;
-    mc.Q = Qp;
-    mc.scale_inputs = 1;
     st.launches.push_back(l);
   }
   Launch fin;
@@ -699,6 +908,26 @@ static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream
   } else {
     if (l.v == 2) launch_k2t_v<double, 2>(p, l.blocks, l.smem, s);
     else launch_k2t_v<double, 1>(p, l.blocks, l.smem, s);
+  }
+}
+
+template <typename T, int V>
+static void launch_k2f_t(const wmc::dev::K2FParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(dev::k2_fused<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    attr_set = true;
+  }
+  dev::k2_fused<T, V><<<(unsigned)blocks, dev::kThreads + 32, smem, s>>>(p);
+}
+
+static void launch_k2f(const Launch &l, const wmc::dev::K2FParams &p, cudaStream_t s) {
+  if (l.ti == TF) {
+    if (l.v == 4) launch_k2f_t<float, 4>(p, l.blocks, l.smem, s);
+    else launch_k2f_t<float, 1>(p, l.blocks, l.smem, s);
+  } else {
+    if (l.v == 2) launch_k2f_t<double, 2>(p, l.blocks, l.smem, s);
+    else launch_k2f_t<double, 1>(p, l.blocks, l.smem, s);
   }
 }
 
@@ -796,6 +1025,22 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         tp.debug_stall = stall_armed ? 1 : 0;
         stall_armed = false;
         launch_k2t(l, tp, s);
+        break;
+      }
+      case L_K2F: {
+        wmc::dev::K2FParams fp = l.k2f;
+        K2Params &p = fp.t.k;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        fp.S2 = ws + l.off_s2;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        fp.m2.exp = mexp + l.meta_s2; fp.m2.maxb = mmax + l.meta_s2; fp.m2.minb = mmin + l.meta_s2;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
+        fp.t.err = (uint32_t *)(ws + st.off_err);
+        fp.t.debug_stall = stall_armed ? 1 : 0;
+        stall_armed = false;
+        launch_k2f(l, fp, s);
         break;
       }
       case L_K4: {
@@ -1049,7 +1294,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_K2F ? 6 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -1394,7 +1639,7 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     ++li;
     // k4 offsets are bit scatters onto each tensor's own positions: in
     // bounds by construction
-    if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1) continue;
+    if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1 && l.kind != L_K2F) continue;
     const int64_t ta = l.id_a, tb = l.id_b, tc = l.id_c;
     if (ta < 0 || tb < 0 || tc < 0) { set_error("launch %zu: unknown tensor", li); return WMC_EINVAL; }
     const int64_t es_in = l.kind == L_K1 ? (l.ti == TD ? 8 : 4) : (l.ti == TD ? 8 : 4);
@@ -1427,6 +1672,59 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
       if (mb >= nb) return bad("B", mb, nb);
       if ((1ll << p.rC) > nc) return bad("C", (1ll << p.rC) - 1, nc);
       ++checked;
+      continue;
+    }
+    if (l.kind == L_K2F) {
+      const wmc::dev::K2FParams &fp = l.k2f;
+      const K2Params &p = fp.t.k;
+      const int V = 1 << p.vbits;
+      const int64_t ns2 = st->t_bytes[(size_t)l.id_s2] / es_in;
+      const uint64_t nu = 1ull << p.log2_nu;
+      std::vector<uint64_t> us;
+      if (nu <= (1u << 14)) for (uint64_t u = 0; u < nu; ++u) us.push_back(u);
+      else {
+        for (uint64_t u = 0; u < 4096; ++u) { us.push_back(u); us.push_back(nu - 1 - u); }
+        uint64_t x = 0x9e3779b97f4a7c15ull;
+        for (int i = 0; i < 8192; ++i) { x ^= x << 13; x ^= x >> 7; x ^= x << 17; us.push_back(x % nu); }
+      }
+      for (uint64_t u : us) {
+        const uint32_t w = (uint32_t)(u << p.vbits);
+        uint32_t oa = w, oc = w, g1 = 0, g2 = 0;
+        for (int i = 0; i < p.n_insA; ++i) oa = h_insert0(oa, p.insA[i]);
+        for (int i = 0; i < p.n_insC; ++i) oc = h_insert0(oc, p.insC[i]);
+        for (int i = 0; i < p.n_seg; ++i) g1 |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+        for (int i = 0; i < fp.n_seg2; ++i) g2 |= ((oc >> fp.seg2_c[i]) & ((1u << fp.seg2_len[i]) - 1u)) << fp.seg2_b[i];
+        for (int c = 0; c < 8; ++c)
+          for (int e = 0; e < V; ++e) {
+            if ((int64_t)g1 + fp.d1[c] + fp.dv1[e] >= nb) return bad("S1", (int64_t)g1 + fp.d1[c] + fp.dv1[e], nb);
+            if ((int64_t)g2 + fp.d2[c] + fp.dv2[e] >= ns2) return bad("S2", (int64_t)g2 + fp.d2[c] + fp.dv2[e], ns2);
+          }
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t pa = ((c & 1) ? fp.dCf[1] : 0u) | ((c & 2) ? fp.dCf[2] : 0u);  // same positions in P
+          if ((int64_t)(oa | pa) + V - 1 >= na) return bad("P", (int64_t)(oa | pa) + V - 1, na);
+          if ((int64_t)(oc | fp.dCf[c]) + V - 1 >= nc) return bad("C", (int64_t)(oc | fp.dCf[c]) + V - 1, nc);
+        }
+        ++checked;
+      }
+      const wmc::dev::K2TParams &tp = fp.t;
+      const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
+      const int64_t run_len = 1ll << tp.run_log2;
+      const int64_t tile_elems = (int64_t)tp.nruns * run_len;
+      for (uint64_t t = 0; t < n_tiles; ++t) {
+        uint32_t base = (uint32_t)(t << tp.tb);
+        for (int j = 0; j < p.n_insA; ++j) base = h_insert0(base, p.insA[j]);
+        for (int r = 0; r < tp.nruns; ++r) {
+          const int64_t lo = (int64_t)base + tp.run_off[r];
+          if (lo % 4 || lo + run_len > na) return bad("bulk copy", lo + run_len - 1, na);
+        }
+        ++checked;
+      }
+      for (uint32_t wl = 0; wl < (1u << tp.tb); wl += (uint32_t)V) {
+        uint32_t la = wl;
+        for (int j = 0; j < tp.n_lowA; ++j) la = h_insert0(la, tp.lowA[j]);
+        for (int c = 0; c < 4; ++c)
+          if ((int64_t)fp.pA[c] + la + V - 1 >= tile_elems) return bad("stage", (int64_t)fp.pA[c] + la + V - 1, tile_elems);
+      }
       continue;
     }
     const K2Params &p = l.kind == L_K2T ? l.k2t.k : l.k2;

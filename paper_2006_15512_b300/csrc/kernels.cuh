@@ -717,6 +717,280 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
+// ------------------------------------------------- fused pair of eliminations
+//
+// Two consecutive frontier contractions C1 = P . S1 (summing x1, adding y1
+// at x1's position) and C2 = C1 . S2 (summing x2, adding y2 at x2's
+// position) in one pass over P: per work unit the thread loads P for the
+// four (x1, x2) assignments, forms C1 in registers for both values of x2
+// and y1 (stage 1), and contracts x2 against S2 (stage 2).  C1 never
+// reaches memory, so the pair moves |P| + |C2| bytes instead of
+// 2|P| + 2|C2|.  The sums run in the same order as the unfused pair; C1 is
+// not rescaled between the stages (its scale is a power of two, so only
+// the exponent bookkeeping differs).  Tiling, staging and bounded waits
+// are those of k2_tma (P's summed positions are {x1, x2}, C2's new ones
+// the same two positions); S1 and S2 are both staged in shared memory.
+
+struct K2FParams {
+  K2TParams t;            // tiling of P over its kept indices; t.k.B = S1, t.k.seg_* gather S1
+  const void *S2;
+  Meta m2;                // S2's metadata
+  int32_t s2_log2;
+  int32_t n_seg2;
+  int8_t seg2_c[16], seg2_b[16], seg2_len[16];
+  int32_t b_vec2;         // S2 lanes: 0 per lane, 1 contiguous, 2 broadcast
+  uint32_t dv1[4], dv2[4];
+  uint32_t d1[8];         // S1 offset of (x1, y1, x2): index x1 + 2 y1 + 4 x2
+  uint32_t d2[8];         // S2 offset of (x2, y2, y1): index x2 + 2 y2 + 4 y1
+  uint32_t pA[4];         // stage offset of P for (x1, x2): index x1 + 2 x2
+  uint32_t dCf[4];        // C2 offset of (y1, y2): index y1 + 2 y2
+};
+
+template <typename T, int V>
+__device__ __forceinline__ void lds_lanes(uint32_t base, int mode, const uint32_t *dv, T (&r)[V]) {
+  constexpr uint32_t es = (uint32_t)sizeof(T);
+  if (V > 1 && mode == 1) {
+    LdsV<T, V>::ld(base, r);
+  } else if (mode == 2) {
+    const T v = lds1(base, T());
+#pragma unroll
+    for (int e = 0; e < V; ++e) r[e] = v;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) r[e] = lds1(base + dv[e] * es, T());
+  }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kThreads + 32, 2) k2_fused(K2FParams fp) {
+  typedef typename Bits<T>::t BT;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
+  __shared__ uint32_t tile_oc[kStages], tile_gb[kStages], tile_gb2[kStages];
+  __shared__ int s_skip;
+  const K2TParams &tp = fp.t;
+  const K2Params &p = tp.k;
+  if (threadIdx.x == 0) s_skip = (tp.err && *(volatile uint32_t *)tp.err) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;  // an earlier launch of this walk gave up: skip the work
+  const uint32_t run_len = 1u << tp.run_log2;
+  const uint32_t tile_elems = (uint32_t)tp.nruns * run_len;
+  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
+  const uint32_t n_tiles = 1u << (p.log2_nu + p.vbits - tp.tb);
+  T *stage_buf = reinterpret_cast<T *>(dyn_smem);
+  T *sS1 = stage_buf + (size_t)kStages * tile_elems;
+  const size_t s1_bytes = (((size_t)sizeof(T) << tp.s_log2) + 15) & ~(size_t)15;
+  T *sS2 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sS1) + s1_bytes);
+  const size_t s2_bytes = (((size_t)sizeof(T) << fp.s2_log2) + 15) & ~(size_t)15;
+  unsigned long long *smax =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(sS2) + s2_bytes);
+  unsigned long long *smin = smax + p.mc.Qc;
+  T *sscale1 = reinterpret_cast<T *>(smin + p.mc.Qc);
+  T *sscale2 = sscale1 + p.mc.Qc;
+  const T *A = (const T *)p.A;
+  const T *B1 = (const T *)p.B;
+  const T *B2 = (const T *)fp.S2;
+  T *C = (T *)p.C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nthr = kConsumerWarps * 32;
+  auto produce = [&](uint32_t i) -> bool {
+    const int st = (int)(i % kStages);
+    if (i >= (uint32_t)kStages && !mbar_wait(&empty[st], ((i / kStages) - 1) & 1)) return false;
+    const uint32_t bw = (blockIdx.x + i * gridDim.x) << tp.tb;
+    uint32_t base = bw, oc = bw, gb = 0, gb2 = 0;
+    for (int j = 0; j < p.n_insA; ++j) base = insert0(base, p.insA[j]);
+    for (int j = 0; j < p.n_insC; ++j) oc = insert0(oc, p.insC[j]);
+    for (int j = 0; j < p.n_seg; ++j)
+      gb |= ((oc >> p.seg_c[j]) & ((1u << p.seg_len[j]) - 1u)) << p.seg_b[j];
+    for (int j = 0; j < fp.n_seg2; ++j)
+      gb2 |= ((oc >> fp.seg2_c[j]) & ((1u << fp.seg2_len[j]) - 1u)) << fp.seg2_b[j];
+    tile_oc[st] = oc;
+    tile_gb[st] = gb;
+    tile_gb2[st] = gb2;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&full[st], tile_bytes);
+    if (tp.debug_stall && i == 0) return true;
+    for (int r = 0; r < tp.nruns; ++r)
+      bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len, A + base + tp.run_off[r],
+               run_len * (uint32_t)sizeof(T), &full[st]);
+    return true;
+  };
+  const bool producer = (warp == kConsumerWarps) && lane == 0;
+  uint32_t n_pre = 0;
+  if (producer) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumerWarps);
+    }
+    mbar_fence_init();
+    for (; n_pre < (uint32_t)kStages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
+  }
+  // per-lane scales of S1 (times P's when folded) and of S2
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
+    smax[q] = 0;
+    smin[q] = kNoMin;
+    T v1 = operand_scale<T>(p.mb, q, p.mc.scale_inputs);
+    if (tp.fold_sa) v1 *= operand_scale<T>(p.ma, q, p.mc.scale_inputs);
+    sscale1[q] = v1;
+    sscale2[q] = operand_scale<T>(fp.m2, q, p.mc.scale_inputs);
+  }
+  __syncthreads();
+  {
+    const uint32_t n1 = 1u << tp.s_log2, n2 = 1u << fp.s2_log2;
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x; j < n1; j += blockDim.x) sS1[j] = __ldg(B1 + j) * sscale1[j & p.mb.qmask];
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x; j < n2; j += blockDim.x) sS2[j] = __ldg(B2 + j) * sscale2[j & fp.m2.qmask];
+  }
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    if (lane == 0) {
+      uint32_t i = n_pre;
+      bool ok = true;
+      for (; blockIdx.x + i * gridDim.x < n_tiles; ++i)
+        if (!produce(i)) { ok = false; break; }
+      if (!ok && tp.err) atomicOr(tp.err, 1u);
+      const uint32_t n_issued = i;
+      for (uint32_t j = n_issued > (uint32_t)kStages ? n_issued - kStages : 0; j < n_issued; ++j)
+        if (!mbar_wait(&full[j % kStages], (j / kStages) & 1) && tp.err) atomicOr(tp.err, 1u);
+    }
+    __syncwarp();
+  } else {
+    constexpr int J = (V == 1) ? 2 : 1;  // work units per thread per tile (host: T_w = 256*V*J)
+    constexpr uint32_t es = (uint32_t)sizeof(T);
+    const uint32_t stage0 = smem_addr(stage_buf), s10 = smem_addr(sS1), s20 = smem_addr(sS2);
+    uint32_t la4[J], ocl[J], g1l[J], g2l[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const uint32_t wl = (threadIdx.x + (uint32_t)j * nthr) * V;
+      uint32_t a = wl, c = wl, g = 0, g2 = 0;
+      for (int i = 0; i < tp.n_lowA; ++i) a = insert0(a, tp.lowA[i]);
+      for (int i = 0; i < p.n_insC; ++i) c = insert0(c, p.insC[i]);
+      for (int i = 0; i < p.n_seg; ++i)
+        g |= ((c >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+      for (int i = 0; i < fp.n_seg2; ++i)
+        g2 |= ((c >> fp.seg2_c[i]) & ((1u << fp.seg2_len[i]) - 1u)) << fp.seg2_b[i];
+      la4[j] = a * es; ocl[j] = c; g1l[j] = g * es + s10; g2l[j] = g2 * es + s20;
+    }
+    uint32_t pa[4], d1[8], d2[8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) pa[x] = fp.pA[x] * es;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) { d1[x] = fp.d1[x] * es; d2[x] = fp.d2[x] * es; }
+    T sa[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      sa[e] = tp.fold_sa ? (T)1 : operand_scale<T>(p.ma, (int)(threadIdx.x * V + e), p.mc.scale_inputs);
+    T tmax[4][V];
+    BT tminm1[4][V];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tminm1[f][e] = (BT)~(BT)0; }
+    for (uint32_t i = 0; blockIdx.x + i * gridDim.x < n_tiles; ++i) {
+      const int st = (int)(i % kStages);
+      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (i / kStages) & 1));
+      if (!landed) {
+        if (lane == 0 && tp.err) atomicOr(tp.err, 1u);
+        break;
+      }
+      const uint32_t tile0 = stage0 + (uint32_t)st * tile_bytes;
+      const uint32_t ocb = tile_oc[st], g1b = tile_gb[st] * es, g2b = tile_gb2[st] * es;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const uint32_t oc = ocb | ocl[j];
+        const uint32_t g1 = g1b + g1l[j], g2 = g2b + g2l[j];
+        T a[4][V];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          LdsV<T, V>::ld(tile0 + la4[j] + pa[x], a[x]);
+          if (!tp.fold_sa) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) a[x][e] *= sa[e];
+          }
+        }
+        // stage 1: C1 for (x2, y1)
+        T c1[2][2][V];
+#pragma unroll
+        for (int x2 = 0; x2 < 2; ++x2)
+#pragma unroll
+          for (int y1 = 0; y1 < 2; ++y1) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) c1[x2][y1][e] = (T)0;
+#pragma unroll
+            for (int x1 = 0; x1 < 2; ++x1) {
+              T b[V];
+              lds_lanes<T, V>(g1 + d1[x1 + 2 * y1 + 4 * x2], p.b_vec, fp.dv1, b);
+#pragma unroll
+              for (int e = 0; e < V; ++e) c1[x2][y1][e] = fma_t(a[x1 + 2 * x2][e], b[e], c1[x2][y1][e]);
+            }
+          }
+        // stage 2: C2 for (y1, y2)
+        T *cptr = C + oc;
+#pragma unroll
+        for (int y1 = 0; y1 < 2; ++y1)
+#pragma unroll
+          for (int y2 = 0; y2 < 2; ++y2) {
+            T c[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) c[e] = (T)0;
+#pragma unroll
+            for (int x2 = 0; x2 < 2; ++x2) {
+              T b[V];
+              lds_lanes<T, V>(g2 + d2[x2 + 2 * y2 + 4 * y1], fp.b_vec2, fp.dv2, b);
+#pragma unroll
+              for (int e = 0; e < V; ++e) c[e] = fma_t(c1[x2][y1][e], b[e], c[e]);
+            }
+            vstore<T, V>(cptr + fp.dCf[y1 + 2 * y2], c);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+              tmax[y1 + 2 * y2][e] = fmax(tmax[y1 + 2 * y2][e], fabs(c[e]));
+              const BT bm1 = to_bits(c[e]) - (BT)1;
+              tminm1[y1 + 2 * y2][e] = bm1 < tminm1[y1 + 2 * y2][e] ? bm1 : tminm1[y1 + 2 * y2][e];
+            }
+          }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const int q = (int)((ocl[0] + fp.dCf[f] + e) & qmask_c);
+        if (tmax[f][e] != (T)0) atomicMax(smax + q, abs_bits(tmax[f][e]));
+        if (tminm1[f][e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[f][e] + (BT)1));
+      }
+  }
+  __syncthreads();
+  // C2's exponent: P, S1 and S2 (C1 is never rescaled); flush test over the
+  // three operands' smallest nonzero scaled entries
+  if (blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
+      const int qa = q & p.ma.qmask, qb = q & p.mb.qmask, q2 = q & fp.m2.qmask;
+      if (p.mc.exp)
+        p.mc.exp[q] = p.ma.exp[qa] + pow2_exp_of(p.ma.maxb[qa], T()) + p.mb.exp[qb] +
+                      pow2_exp_of(p.mb.maxb[qb], T()) + fp.m2.exp[q2] + pow2_exp_of(fp.m2.maxb[q2], T());
+      if (p.mc.flags && p.ma.minb[qa] != kNoMin && p.mb.minb[qb] != kNoMin && fp.m2.minb[q2] != kNoMin) {
+        const T lo = (from_bits<T>(p.ma.minb[qa]) * operand_scale<T>(p.ma, qa, 1)) *
+                     (from_bits<T>(p.mb.minb[qb]) * operand_scale<T>(p.mb, qb, 1)) *
+                     (from_bits<T>(fp.m2.minb[q2]) * operand_scale<T>(fp.m2, q2, 1));
+        if (below_normal(lo)) {
+          if (p.mc.Qc > 1) atomicOr(p.mc.flags + q, 2u);
+          else
+            for (int qq = 0; qq < p.mc.Q; ++qq) atomicOr(p.mc.flags + qq, 2u);
+        }
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
+    if (p.mc.maxb && smax[q]) atomicMax(p.mc.maxb + q, smax[q]);
+    if (p.mc.minb && smin[q] != kNoMin) atomicMin(p.mc.minb + q, smin[q]);
+  }
+}
+
 // ------------------------------------------------------------ K4 dense
 //
 // C[b, i, j] = sum_s A[b, i, s] * B[b, s, j] when the node is a real

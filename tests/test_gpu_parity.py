@@ -413,3 +413,29 @@ def test_uneven_batch_admission(w):
     batch = w.Batch(plans, mem_budget_bytes=budget)
     assert batch.n_admitted == 4
     assert len(batch.execute()) == 4
+
+
+@pytest.mark.parametrize("precision", [FP32])
+def test_fused_pairs_match_unfused(w, precision):
+    """Two consecutive frontier eliminations in one pass give the same
+    values as two passes (the intermediate's pow2 scale only moves into the
+    exponent), and match the oracle; the fused plan moves far fewer bytes."""
+    H, W_ = 16, 100
+    cnf = wmcgen.grid_cnf(H, W_, 1)
+    Q = 64
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=12, lo=0.05, hi=0.95)
+    try:
+        w.wmc_set_fusion(0)
+        plain = plan_for(w, cnf, None, None, precision)
+        a = plain.execute(wq, wnq)
+        bytes_plain = plain.info(Q).algorithmic_bytes
+    finally:
+        w.wmc_set_fusion(1)
+    fused = plan_for(w, cnf, None, None, precision)
+    b = fused.execute(wq, wnq)
+    assert fused.info(Q).algorithmic_bytes < 0.7 * bytes_plain
+    for q in range(Q):
+        assert (a[q].mant, a[q].exp2) == (b[q].mant, b[q].exp2), q
+    col = wmcgen.grid_column_order(H, W_)
+    for q in (0, 33):
+        assert rel(b[q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[precision]
