@@ -47,7 +47,7 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 # DRAM traffic / algorithmic bytes of the dominant kernel, from its ncu
 # capture (None once the kernel changes until it is captured again)
-TRAFFIC_PER_ALG_BYTE = None  # dominant kernel changed (k2_fused): re-captured below
+TRAFFIC_PER_ALG_BYTE = 219.78e6 / 268.5e6
 
 
 def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
@@ -277,14 +277,14 @@ def run_ours(args, rank, world):
     sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 6)
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
-    # DRAM bytes from one ncu capture of a full-size k2_tma launch (profiles/
-    # k2_tma_serving_grid16x100_q256.md: 214.3 MB for 268.5 MB algorithmic),
+    # DRAM bytes from one ncu capture of a full-size k2_fused launch (profiles/
+    # k2_fused_serving_grid16x100_q256.md: 219.8 MB for 268.5 MB algorithmic),
     # scaled to this run's average streaming launch by its algorithmic bytes
     bpl = float(k_bytes[sel].mean()) if sel.any() else 0.0
     traffic = TRAFFIC_PER_ALG_BYTE * bpl if TRAFFIC_PER_ALG_BYTE else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                "kernel": "k2_tma / k2_stream (streaming pairwise contraction)",
+                "kernel": "k2_fused / k2_tma / k2_stream (streaming contractions)",
                 "tma_launches": int((k_kind == 4).sum()),
                 "fused_launches": int((k_kind == 6).sum()),
                 "tma_share_of_streaming": float(k_ms[k_kind == 4].sum() / max(k_ms[sel].sum(), 1e-12)),
