@@ -292,6 +292,8 @@ def run_ours(args, rank, world):
                 "avg_launch_us": float(k_ms[sel].mean() * 1e3) if sel.any() else None,
                 "bytes_per_launch": float(k_bytes[sel].mean()) if sel.any() else None,
                 "generic_k1_share": float(k_ms[k_kind == 0].sum() / walk_ms),
+                "small_phase_share": float(k_ms[k_kind == 7].sum() / walk_ms),
+                "walk_launches": int(L),
                 "eager_walk_ms": walk_ms}
 
     # ---- plain one-query-at-a-time FP64 path on the same GPU

@@ -153,7 +153,7 @@ typedef struct {
   int32_t precision;
   int32_t ordering_used;
   int32_t max_path_roundings; /* d of wmc_result.rel_err_bound            */
-  int32_t reserved;
+  int32_t launches_per_walk;  /* kernel launches one execution enqueues   */
 } wmc_plan_info_t;
 /* Q >= 1 is the number of queries batched along the extra query index. */
 int wmc_plan_info(const wmc_plan_t *plan, int32_t Q, wmc_plan_info_t *out);
@@ -314,7 +314,8 @@ void wmc_server_destroy(wmc_server_t *srv);
  * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
  * kind[i] = 0 generic contraction, 1 streaming contraction, 4 streaming
  * contraction with TMA-staged operand, 5 dense tiled contraction, 6 fused
- * pair of eliminations, 2 leaf or bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
+ * pair of eliminations, 7 small-node phase (one persistent launch), 2 leaf
+ * or bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
  * must move (|A| + |B| + |C| in its element type).  Returns the launch
  * count through *n_launches.  Same arguments and errors as
  * wmc_execute_device; creates and destroys its own events. */
@@ -329,6 +330,11 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
  * eliminations in one pass (the intermediate tensor never reaches memory).
  * Affects plans laid out after the call (a plan caches its layout per Q). */
 void wmc_set_fusion(int32_t on);
+/* Execution option (default on): every node whose whole subtree is small
+ * (at most 2^16 outputs including the query bits, at most 2^8 summed
+ * terms) runs inside one persistent launch at the start of the walk
+ * instead of a launch per node.  Affects plans laid out after the call. */
+void wmc_set_small_phase(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,

@@ -70,7 +70,7 @@ class wmc_plan_info_t(ctypes.Structure):
     _fields_ = [("max_rank", c_i32), ("max_node_rank", c_i32), ("n_leaves", c_i64),
                 ("n_nodes", c_i64), ("workspace_bytes", c_i64), ("peak_tensor_bytes", c_i64),
                 ("algorithmic_bytes", c_dbl), ("flops", c_dbl), ("precision", c_i32),
-                ("ordering_used", c_i32), ("max_path_roundings", c_i32), ("reserved", c_i32)]
+                ("ordering_used", c_i32), ("max_path_roundings", c_i32), ("launches_per_walk", c_i32)]
 
 
 class wmc_server_opts(ctypes.Structure):
@@ -131,6 +131,7 @@ EXPORTS = {
     "wmc_debug_stall_copies": (None, [c_i32]),
     "wmc_debug_check_bounds": (c_i32, [c_vp, c_i32, P(c_i64)]),
     "wmc_set_fusion": (None, [c_i32]),
+    "wmc_set_small_phase": (None, [c_i32]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

@@ -34,11 +34,13 @@ static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_fail_allocs{0};
 static std::atomic<int32_t> g_debug_stall{0};
 static std::atomic<int32_t> g_fuse{1};  // fuse consecutive frontier eliminations (k2_fused)
+static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
 extern "C" void wmc_debug_stall_copies(int32_t on) { g_debug_stall.store(on); }
 extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
+extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -70,7 +72,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2F, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2F, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -117,6 +119,11 @@ struct ExecState {
   // constant tables (device, owned)
   std::vector<ClauseLeaf> h_clause;
   std::vector<int64_t> h_first, h_woff, h_wmeta;
+  std::vector<wmc::dev::SNode> h_snodes;   // small-node phase
+  std::vector<wmc::dev::STask> h_stasks;
+  wmc::dev::SNode *d_snodes = nullptr;
+  wmc::dev::STask *d_stasks = nullptr;
+  int64_t off_sp = 0;                      // task counter + per-node completion counters
   int64_t n_clause_entries = 0;
   ClauseLeaf *d_clause = nullptr;
   int64_t *d_first = nullptr, *d_woff = nullptr, *d_wmeta = nullptr;
@@ -139,6 +146,7 @@ struct ExecState {
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     cudaFree(d_clause); cudaFree(d_first); cudaFree(d_woff); cudaFree(d_wmeta);
+    cudaFree(d_snodes); cudaFree(d_stasks);
     cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant); cudaFree(d_res_exp); cudaFree(d_res_flags);
     cudaFreeHost(h_res_mant); cudaFreeHost(h_res_exp); cudaFreeHost(h_res_flags);
   }
@@ -607,6 +615,28 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   st.off_io = off; off += align_up(sizeof(IoDesc));
   st.off_flags = off; off += align_up(4 * (int64_t)Qp);
   st.off_err = off; off += align_up(4);
+  // small-node phase: which nodes run inside the persistent launch (every
+  // node whose subtree is small: at most 2^16 outputs with the query bits,
+  // at most 2^8 summed terms)
+  std::vector<int32_t> sp_index(plan.nodes.size(), -1);
+  std::vector<int64_t> sp_nodes;
+  if (g_small_phase.load()) {
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+      const Node &nd = plan.nodes[ni];
+      const TensorInfo &C = plan.tensors[(size_t)nd.c];
+      const int rc = (int)C.labels.size() + (C.has_q ? m : 0);
+      if (rc > 16 || nd.n_summed > 8) continue;
+      bool ok = true;
+      for (int64_t ch : {nd.a, nd.b}) {
+        if (ch < plan.n_leaves) continue;
+        ok &= sp_index[(size_t)plan.tensors[(size_t)ch].node] >= 0;
+      }
+      if (!ok) continue;
+      sp_index[ni] = (int32_t)sp_nodes.size();
+      sp_nodes.push_back((int64_t)ni);
+    }
+  }
+  st.off_sp = off; off += align_up(4 * (1 + (int64_t)sp_nodes.size()));
   st.off_exp = off; off += align_up(8 * slots);
   st.off_max = off; off += align_up(8 * slots);
   st.off_min = off; off += align_up(8 * slots);
@@ -747,7 +777,9 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       if (absorbed[ni]) continue;
       if (fuse_next[ni] >= 0)
-        for (int64_t q = (int64_t)ni + 1; q < fuse_next[ni]; ++q) steps.push_back({q, -1});
+        for (int64_t q = (int64_t)ni + 1; q < fuse_next[ni]; ++q)
+          if (sp_index[(size_t)q] < 0) steps.push_back({q, -1});
+      if (sp_index[ni] >= 0) continue;  // runs in the small-node phase
       steps.push_back({(int64_t)ni, fuse_next[ni]});
     }
   }
@@ -757,8 +789,15 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   st.alg_bytes = 0;
   st.flops = 0;
   auto release = [&](int64_t t) {
-    if (t >= plan.n_leaves) ff.release(st.t_off[(size_t)t] - arena0, bytes[(size_t)t]);
+    if (t < plan.n_leaves) return;
+    if (sp_index[(size_t)plan.tensors[(size_t)t].node] >= 0) return;  // small-phase output: kept
+    ff.release(st.t_off[(size_t)t] - arena0, bytes[(size_t)t]);
   };
+  for (int64_t ni : sp_nodes) {
+    const Node &nd = plan.nodes[(size_t)ni];
+    st.t_off[(size_t)nd.c] = arena0 + ff.alloc(bytes[(size_t)nd.c]);
+    st.alg_bytes += node_l[(size_t)ni].alg_bytes;
+  }
   for (const Step &stp : steps) {
     const Launch &l = node_l[(size_t)stp.node];
     st.t_off[(size_t)l.id_c] = arena0 + ff.alloc(bytes[(size_t)l.id_c]);
@@ -824,6 +863,43 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   }
   if (have_w) {
     Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Qp);
+    st.launches.push_back(l);
+  }
+  st.h_snodes.clear();
+  st.h_stasks.clear();
+  if (!sp_nodes.empty()) {
+    double sp_bytes = 0;
+    for (int64_t ni : sp_nodes) {
+      const Node &nd = plan.nodes[(size_t)ni];
+      const TensorInfo &A = plan.tensors[(size_t)nd.a], &B = plan.tensors[(size_t)nd.b];
+      const TensorInfo &C = plan.tensors[(size_t)nd.c];
+      wmc::dev::SNode sn;
+      std::memset(&sn, 0, sizeof(sn));
+      sn.a = st.t_off[(size_t)nd.a]; sn.b = st.t_off[(size_t)nd.b]; sn.c = st.t_off[(size_t)nd.c];
+      sn.ma = st.t_meta[(size_t)nd.a]; sn.mb = st.t_meta[(size_t)nd.b]; sn.mc = st.t_meta[(size_t)nd.c];
+      sn.qmask_a = A.has_q ? Qp - 1 : 0;
+      sn.qmask_b = B.has_q ? Qp - 1 : 0;
+      sn.Qc = C.has_q ? Qp : 1;
+      sn.dep_a = nd.a < plan.n_leaves ? -1 : sp_index[(size_t)A.node];
+      sn.dep_b = nd.b < plan.n_leaves ? -1 : sp_index[(size_t)B.node];
+      int8_t pa[32], pb[32], spa[24], spb[24];
+      k1_bitmaps(full_labels(A, m), full_labels(B, m), full_labels(C, m), &sn.rC, &sn.k, pa, pb, spa, spb);
+      std::memcpy(sn.posA, pa, 16); std::memcpy(sn.posB, pb, 16);
+      std::memcpy(sn.sposA, spa, 8); std::memcpy(sn.sposB, spb, 8);
+      sn.chunk_log2 = std::min<int32_t>(sn.rC, 12);
+      sn.n_chunks = 1 << (sn.rC - sn.chunk_log2);
+      sn.ti = st.f64 ? 1 : 0;
+      sn.to = st.t_dbl[(size_t)nd.c];
+      sn.ta = (st.f64 || sn.to) ? 1 : 0;
+      const int32_t idx = (int32_t)st.h_snodes.size();
+      st.h_snodes.push_back(sn);
+      for (int32_t c = 0; c < sn.n_chunks; ++c) st.h_stasks.push_back({idx, c});
+      sp_bytes += node_l[(size_t)ni].alg_bytes;
+    }
+    Launch l;
+    l.kind = L_SMALL;
+    l.blocks = (int64_t)std::min<size_t>(st.h_stasks.size(), 148 * 4);
+    l.alg_bytes = sp_bytes;
     st.launches.push_back(l);
   }
   for (const Step &stp : steps) {
@@ -952,6 +1028,8 @@ static int ensure_dev(ExecState &st) {
   if ((rc = up((void **)&st.d_first, st.h_first.data(), sizeof(int64_t) * st.h_first.size()))) return rc;
   if ((rc = up((void **)&st.d_woff, st.h_woff.data(), sizeof(int64_t) * st.h_woff.size()))) return rc;
   if ((rc = up((void **)&st.d_wmeta, st.h_wmeta.data(), sizeof(int64_t) * st.h_wmeta.size()))) return rc;
+  if ((rc = up((void **)&st.d_snodes, st.h_snodes.data(), sizeof(wmc::dev::SNode) * st.h_snodes.size()))) return rc;
+  if ((rc = up((void **)&st.d_stasks, st.h_stasks.data(), sizeof(wmc::dev::STask) * st.h_stasks.size()))) return rc;
   CUDA_TRY(cudaStreamCreateWithFlags(&st.capture_stream, cudaStreamNonBlocking));
   st.dev_ready = true;
   return WMC_OK;
@@ -962,11 +1040,13 @@ static int ensure_dev(ExecState &st) {
 struct LeafTables {
   const ClauseLeaf *clause;
   const int64_t *first, *woff, *wmeta;
+  const wmc::dev::SNode *snodes;
+  const wmc::dev::STask *stasks;
 };
 
 static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
                          cudaEvent_t *events = nullptr, const LeafTables *tables = nullptr) {
-  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta};
+  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta, st.d_snodes, st.d_stasks};
   const LeafTables &tb = tables ? *tables : own;
   int64_t *mexp = (int64_t *)(ws + st.off_exp);
   unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
@@ -1025,6 +1105,23 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         tp.debug_stall = stall_armed ? 1 : 0;
         stall_armed = false;
         launch_k2t(l, tp, s);
+        break;
+      }
+      case L_SMALL: {
+        wmc::dev::SmallArgs a;
+        a.ws = ws;
+        a.nodes = tb.snodes;
+        a.tasks = tb.stasks;
+        a.n_tasks = (int32_t)st.h_stasks.size();
+        a.Q = st.Qp;
+        a.next = (uint32_t *)(ws + st.off_sp);
+        a.done = a.next + 1;
+        a.err = (uint32_t *)(ws + st.off_err);
+        a.flags = flags;
+        a.mexp = mexp;
+        a.mmax = mmax;
+        a.mmin = mmin;
+        dev::k_small_phase<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(a);
         break;
       }
       case L_K2F: {
@@ -1217,6 +1314,7 @@ extern "C" int wmc_plan_info(const wmc_plan_t *cplan, int32_t Q, wmc_plan_info_t
   out->precision = plan->precision;
   out->ordering_used = plan->ordering_used;
   out->max_path_roundings = st->max_roundings;
+  out->launches_per_walk = (int32_t)st->kernels_per_run;
   return WMC_OK;
 }
 
@@ -1294,7 +1392,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_K2F ? 6 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_K2F ? 6 : l.kind == L_SMALL ? 7 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -1583,10 +1681,14 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   const size_t b_first = sizeof(int64_t) * st->h_first.size();
   const size_t b_woff = sizeof(int64_t) * st->h_woff.size();
   const size_t b_wmeta = sizeof(int64_t) * st->h_wmeta.size();
+  const size_t b_sn = sizeof(wmc::dev::SNode) * st->h_snodes.size();
+  const size_t b_stk = sizeof(wmc::dev::STask) * st->h_stasks.size();
   const size_t o_first = (size_t)align_up((int64_t)b_clause);
   const size_t o_woff = o_first + (size_t)align_up((int64_t)b_first);
   const size_t o_wmeta = o_woff + (size_t)align_up((int64_t)b_woff);
-  const size_t o_ws = o_wmeta + (size_t)align_up((int64_t)b_wmeta);
+  const size_t o_sn = o_wmeta + (size_t)align_up((int64_t)b_wmeta);
+  const size_t o_stk = o_sn + (size_t)align_up((int64_t)b_sn);
+  const size_t o_ws = o_stk + (size_t)align_up((int64_t)b_stk);
   const size_t need = o_ws + (size_t)st->ws_bytes;
   if (need > kNoAllocScratchBytes) {
     set_error("this plan needs %zu bytes of scratch at Q = %d; the static scratch holds %zu",
@@ -1600,13 +1702,16 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   if (b_first) CUDA_TRY(cudaMemcpyAsync(base + o_first, st->h_first.data(), b_first, cudaMemcpyHostToDevice, s));
   if (b_woff) CUDA_TRY(cudaMemcpyAsync(base + o_woff, st->h_woff.data(), b_woff, cudaMemcpyHostToDevice, s));
   if (b_wmeta) CUDA_TRY(cudaMemcpyAsync(base + o_wmeta, st->h_wmeta.data(), b_wmeta, cudaMemcpyHostToDevice, s));
+  if (b_sn) CUDA_TRY(cudaMemcpyAsync(base + o_sn, st->h_snodes.data(), b_sn, cudaMemcpyHostToDevice, s));
+  if (b_stk) CUDA_TRY(cudaMemcpyAsync(base + o_stk, st->h_stasks.data(), b_stk, cudaMemcpyHostToDevice, s));
   char *ws = base + o_ws;
   IoDesc io;
   std::memset(&io, 0, sizeof(io));
   io.w_pos = d_w_pos; io.w_neg = d_w_neg; io.mant = d_mant; io.exp2 = d_exp2; io.flags = d_flags;
   CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
   const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
-                          (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta)};
+                          (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta),
+                          (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk)};
   // the walk's first launch zeroes the flags and metadata it accumulates into
   enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
   g_launches.fetch_add(st->kernels_per_run);
@@ -1634,6 +1739,30 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
   int rc = get_state(*plan, Q, &st);
   if (rc) return rc;
   int64_t checked = 0;
+  for (size_t i = 0; i < st->h_snodes.size(); ++i) {
+    const wmc::dev::SNode &sn = st->h_snodes[i];
+    int64_t ma = 0, mb = 0;
+    for (int j = 0; j < sn.rC; ++j) {
+      if (sn.posA[j] >= 0) ma |= 1ll << sn.posA[j];
+      if (sn.posB[j] >= 0) mb |= 1ll << sn.posB[j];
+    }
+    for (int j = 0; j < sn.k; ++j) {
+      if (sn.sposA[j] >= 0) ma |= 1ll << sn.sposA[j];
+      if (sn.sposB[j] >= 0) mb |= 1ll << sn.sposB[j];
+    }
+    const int64_t esi = sn.ti ? 8 : 4, eso = sn.to ? 8 : 4;
+    auto within = [&](int64_t off, int64_t last_elem, int64_t es) {
+      for (size_t t = 0; t < st->t_off.size(); ++t)
+        if (st->t_off[t] == off && (last_elem + 1) * es <= st->t_bytes[t]) return true;
+      return false;
+    };
+    if (!within(sn.a, ma, esi) || !within(sn.b, mb, esi) || !within(sn.c, (1ll << sn.rC) - 1, eso)) {
+      set_error("small-phase node %zu: an offset leaves its tensor", i);
+      return WMC_EINVAL;
+    }
+    if (sn.chunk_log2 > sn.rC || sn.k > 8 || sn.rC > 16) { set_error("small-phase node %zu: bad shape", i); return WMC_EINVAL; }
+    ++checked;
+  }
   size_t li = 0;
   for (const Launch &l : st->launches) {
     ++li;

@@ -1164,6 +1164,163 @@ __global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
+// ------------------------------------------------------ small-node phase
+//
+// Every node whose whole subtree is small (bucket products of clause
+// tensors and weight vectors, the small formulas of a batch of queries)
+// runs inside one persistent launch at the start of the walk: a task is a
+// chunk of one node's outputs; a block takes tasks from an atomic counter
+// in post-order and waits (bounded by %globaltimer, one second) until the
+// node's children are complete.  Tensors produced inside the launch are
+// read through L2 (ld.global.cg).
+
+struct SNode {
+  int64_t a, b, c;            // byte offsets in the workspace
+  int64_t ma, mb, mc;         // first metadata slot of A, B, C
+  int32_t qmask_a, qmask_b, Qc;
+  int32_t dep_a, dep_b;       // small-phase node of each child (-1: a leaf)
+  int32_t n_chunks, chunk_log2;
+  int32_t rC, k;
+  int8_t ti, ta, to, pad;
+  int8_t posA[16], posB[16], sposA[8], sposB[8];
+};
+
+struct STask {
+  int32_t node, chunk;
+};
+
+struct SmallArgs {
+  char *ws;
+  const SNode *nodes;
+  const STask *tasks;
+  int32_t n_tasks;
+  int32_t Q;                  // query lanes of the flags array
+  uint32_t *next, *done, *err, *flags;
+  int64_t *mexp;
+  unsigned long long *mmax, *mmin;
+};
+
+__device__ __forceinline__ bool wait_ctr(const uint32_t *ctr, uint32_t target) {
+  if (*(volatile const uint32_t *)ctr >= target) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 32; ++i) {
+      __nanosleep(64);
+      if (*(volatile const uint32_t *)ctr >= target) return true;
+    }
+    if (globaltimer_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+template <typename TI, typename TA, typename TO>
+__device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uint32_t (*lut)[256],
+                           TA *scl, unsigned long long *smax, unsigned long long *smin) {
+  char *ws = sa_.ws;
+  const TI *A = (const TI *)(ws + nd.a);
+  const TI *B = (const TI *)(ws + nd.b);
+  TO *C = (TO *)(ws + nd.c);
+  // lookup tables: rows 0-1 A, 2-3 B (output bits), 4 A, 5 B (summed bits)
+  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
+    const int row = i >> 8, v = i & 255;
+    uint32_t o = 0;
+    for (int bit = 0; bit < 8; ++bit) {
+      if (!((v >> bit) & 1)) continue;
+      if (row < 4) {
+        const int j = (row & 1) * 8 + bit;
+        const int8_t pos = row < 2 ? nd.posA[j] : nd.posB[j];
+        if (j < nd.rC && pos >= 0) o |= 1u << pos;
+      } else if (bit < nd.k) {
+        const int8_t pos = row == 4 ? nd.sposA[bit] : nd.sposB[bit];
+        if (pos >= 0) o |= 1u << pos;
+      }
+    }
+    lut[row][v] = o;
+  }
+  // per-lane operand scales (their max patterns are final: children done)
+  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
+    scl[q] = (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + nd.ma + (q & nd.qmask_a)), TI()), TI());
+    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + nd.mb + (q & nd.qmask_b)), TI()), TI());
+    smax[q] = 0;
+    smin[q] = kNoMin;
+  }
+  __syncthreads();
+  const uint32_t o0 = (uint32_t)chunk << nd.chunk_log2, o1 = o0 + (1u << nd.chunk_log2);
+  const uint32_t ns = 1u << nd.k;
+  for (uint32_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+    const uint32_t bA = lut[0][o & 255] | lut[1][(o >> 8) & 255];
+    const uint32_t bB = lut[2][o & 255] | lut[3][(o >> 8) & 255];
+    const int q = (int)(o & (uint32_t)(nd.Qc - 1));
+    const TA sa = scl[q], sb = scl[nd.Qc + q];
+    TA acc = (TA)0;
+    for (uint32_t s = 0; s < ns; ++s) {
+      const TA a = (TA)__ldcg(A + (bA | lut[4][s])) * sa;
+      const TA b = (TA)__ldcg(B + (bB | lut[5][s])) * sb;
+      acc = fma_t(a, b, acc);
+    }
+    const TO c = (TO)acc;
+    C[o] = c;
+    const unsigned long long bits = abs_bits(c);
+    if (bits) {
+      atomicMax(smax + q, bits);
+      atomicMin(smin + q, bits);
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
+    if (smax[q]) atomicMax(sa_.mmax + nd.mc + q, smax[q]);
+    if (smin[q] != kNoMin) atomicMin(sa_.mmin + nd.mc + q, smin[q]);
+    if (chunk == 0) {
+      const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+      const unsigned long long xa = __ldcg(sa_.mmax + nd.ma + qa), xb = __ldcg(sa_.mmax + nd.mb + qb);
+      sa_.mexp[nd.mc + q] = __ldcg(sa_.mexp + nd.ma + qa) + pow2_exp_of(xa, TI()) +
+                            __ldcg(sa_.mexp + nd.mb + qb) + pow2_exp_of(xb, TI());
+      const unsigned long long na = __ldcg(sa_.mmin + nd.ma + qa), nb = __ldcg(sa_.mmin + nd.mb + qb);
+      if (na != kNoMin && nb != kNoMin) {
+        const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
+                      (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
+        if (below_normal(lo)) {
+          if (nd.Qc > 1) atomicOr(sa_.flags + q, 2u);
+          else
+            for (int qq = 0; qq < sa_.Q; ++qq) atomicOr(sa_.flags + qq, 2u);
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
+  __shared__ uint32_t lut[6][256];
+  __shared__ double scl_d[2 * kMaxQ];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  __shared__ int s_task, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(a.next, 1u);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= a.n_tasks) break;
+    const STask task = a.tasks[t];
+    const SNode &nd = a.nodes[task.node];
+    if (threadIdx.x == 0) {
+      bool ok = *(volatile uint32_t *)a.err == 0;
+      if (ok && nd.dep_a >= 0) ok = wait_ctr(a.done + nd.dep_a, (uint32_t)a.nodes[nd.dep_a].n_chunks);
+      if (ok && nd.dep_b >= 0) ok = wait_ctr(a.done + nd.dep_b, (uint32_t)a.nodes[nd.dep_b].n_chunks);
+      if (!ok) atomicOr(a.err, 1u);
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    if (nd.ti == 1) small_task<double, double, double>(a, nd, task.chunk, lut, scl_d, smax, smin);
+    else if (nd.to == 1) small_task<float, double, double>(a, nd, task.chunk, lut, scl_d, smax, smin);
+    else small_task<float, float, float>(a, nd, task.chunk, lut, reinterpret_cast<float *>(scl_d), smax, smin);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // outputs and metadata before the completion count
+      atomicAdd(a.done + task.node, 1u);
+    }
+  }
+}
+
 // --------------------------------------------------------------- leaves
 
 struct ClauseLeaf {

@@ -439,3 +439,34 @@ def test_fused_pairs_match_unfused(w, precision):
     col = wmcgen.grid_column_order(H, W_)
     for q in (0, 33):
         assert rel(b[q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("case", ["random3cnf", "grid", "psi"])
+def test_small_phase_matches_per_node_launches(w, precision, case):
+    """The small-node phase (every node with at most 2^16 outputs and 2^8
+    summed terms, run as tasks of one persistent launch in post-order)
+    gives bit-identical values and flags to one launch per node, and the
+    oracle's values; it replaces most launches of the walk."""
+    if case == "random3cnf":
+        cnf, Q, order = wmcgen.random_kcnf(24, 80, seed=21), 256, None
+    elif case == "grid":
+        cnf, Q, order = wmcgen.grid_cnf(16, 100, 1), 64, wmcgen.grid_column_order(16, 100)
+    else:
+        cnf, Q, order = wmcgen.psi_family(12), 3, None
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=14, lo=0.05, hi=0.95)
+    try:
+        w.wmc_set_small_phase(0)
+        plain = plan_for(w, cnf, None, None, precision)
+        a = plain.execute(wq, wnq)
+        n_plain = plain.info(Q).launches_per_walk
+    finally:
+        w.wmc_set_small_phase(1)
+    small = plan_for(w, cnf, None, None, precision)
+    b = small.execute(wq, wnq)
+    assert small.info(Q).launches_per_walk < n_plain
+    for q in range(Q):
+        assert (a[q].mant, a[q].exp2, a[q].flags) == (b[q].mant, b[q].exp2, b[q].flags), q
+    for q in (0, Q - 1):
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q], order=order)
+        assert rel(b[q], want) <= TOL[precision]
