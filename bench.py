@@ -47,7 +47,7 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 # DRAM traffic / algorithmic bytes of the dominant kernel, from its ncu
 # capture (None once the kernel changes until it is captured again)
-TRAFFIC_PER_ALG_BYTE = 219.78e6 / 268.5e6
+TRAFFIC_PER_ALG_BYTE = None
 
 
 def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
@@ -274,7 +274,7 @@ def run_ours(args, rank, world):
     k_kind = np.array([kinds[i] for i in range(L)])
     k_bytes = np.array([nbytes[i] for i in range(L)])
     hbm, src = peaks()
-    sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 6)
+    sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 6) | (k_kind == 8)
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
     # DRAM bytes from one ncu capture of a full-size k2_fused launch (profiles/
@@ -284,9 +284,10 @@ def run_ours(args, rank, world):
     traffic = TRAFFIC_PER_ALG_BYTE * bpl if TRAFFIC_PER_ALG_BYTE else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                "kernel": "k2_fused / k2_tma / k2_stream (streaming contractions)",
+                "kernel": "k2_chain / k2_tma / k2_stream (streaming contractions)",
                 "tma_launches": int((k_kind == 4).sum()),
-                "fused_launches": int((k_kind == 6).sum()),
+                "chain_launches": int((k_kind == 8).sum()),
+                "chain_share_of_streaming": float(k_ms[k_kind == 8].sum() / max(k_ms[sel].sum(), 1e-12)),
                 "tma_share_of_streaming": float(k_ms[k_kind == 4].sum() / max(k_ms[sel].sum(), 1e-12)),
                 "launches": int(sel.sum()), "share_of_walk": float(k_ms[sel].sum() / walk_ms),
                 "avg_launch_us": float(k_ms[sel].mean() * 1e3) if sel.any() else None,

@@ -326,9 +326,11 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                      float *node_ms, int32_t *kind, double *alg_bytes,
                      int64_t *n_launches);
 
-/* Execution option (default on): contract two consecutive frontier
- * eliminations in one pass (the intermediate tensor never reaches memory).
- * Affects plans laid out after the call (a plan caches its layout per Q). */
+/* Execution option: the longest run of consecutive frontier eliminations
+ * contracted in one pass over the frontier tensor (k2_chain; the
+ * intermediates never reach memory), 2..4; 0 or 1 turns fusion off;
+ * default 4.  Affects plans laid out after the call (a plan caches its
+ * layout per Q). */
 void wmc_set_fusion(int32_t on);
 /* Execution option (default on): every node whose whole subtree is small
  * (at most 2^16 outputs including the query bits, at most 2^8 summed

@@ -33,7 +33,9 @@ namespace wmc { const Network &network_of(const wmc_network_t *n); }
 static std::atomic<int64_t> g_launches{0};
 static std::atomic<int32_t> g_fail_allocs{0};
 static std::atomic<int32_t> g_debug_stall{0};
-static std::atomic<int32_t> g_fuse{1};  // fuse consecutive frontier eliminations (k2_fused)
+// fusion of consecutive frontier eliminations into one k2_chain launch:
+// chains of up to this many (0 or 1: off)
+static std::atomic<int32_t> g_fuse{4};
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
@@ -72,7 +74,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2F, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -84,9 +86,12 @@ struct Launch {
   K2Params k2;
   wmc::dev::K2TParams k2t;
   wmc::dev::K4Params k4;
-  wmc::dev::K2FParams k2f;
+  wmc::dev::K2CParams k2c;
+  int chain_d = 0, chain_fast = 0, chain_grow = 0, chain_shrink = 0;
+  int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};  // chain: S_1..S_D
+  int64_t off_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};
+  int64_t meta_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};
   size_t smem = 0;
-  int64_t off_s2 = -1, meta_s2 = -1, id_s2 = -1, id_c1 = -1;  // fused pair
   // relative byte offsets (patched with the workspace base at capture)
   int64_t off_a = -1, off_b = -1, off_c = -1;
   int64_t meta_a = -1, meta_b = -1, meta_c = -1;  // slot indices
@@ -370,136 +375,220 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
   return smem <= 160 * 1024;
 }
 
-// Fused pair of eliminations (k2_fused): node i = P1 . S1 -> C1 and node
-// j = C1 . S2 -> C2, both one-summed one-added index with the added index
-// at the summed index's position.  Labels are full (with query bits).
-bool try_fuse(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS1,
-              const std::vector<int32_t> &LC1, const std::vector<int32_t> &LS2,
-              const std::vector<int32_t> &LC2, bool f64, bool p_has_q, bool s1_has_q, int32_t Qp,
-              wmc::dev::K2FParams &fp, size_t &smem) {
-  auto only = [](const std::vector<int32_t> &v) { return v.size() == 1 ? v[0] : INT32_MIN; };
-  std::vector<int32_t> t;
-  for (int32_t l : LP) if (pos_of(LC1, l) < 0) t.push_back(l);
-  for (int32_t l : LS1) if (pos_of(LC1, l) < 0 && pos_of(LP, l) < 0) t.push_back(l);
-  const int32_t x1 = only(t);
-  t.clear();
-  for (int32_t l : LS1) if (pos_of(LC1, l) >= 0 && pos_of(LP, l) < 0) t.push_back(l);
-  const int32_t y1 = only(t);
-  t.clear();
-  for (int32_t l : LC1) if (pos_of(LC2, l) < 0) t.push_back(l);
-  for (int32_t l : LS2) if (pos_of(LC2, l) < 0 && pos_of(LC1, l) < 0) t.push_back(l);
-  const int32_t x2 = only(t);
-  t.clear();
-  for (int32_t l : LS2) if (pos_of(LC2, l) >= 0 && pos_of(LC1, l) < 0) t.push_back(l);
-  const int32_t y2 = only(t);
-  if (x1 == INT32_MIN || y1 == INT32_MIN || x2 == INT32_MIN || y2 == INT32_MIN) return false;
-  if (pos_of(LP, x1) < 0 || pos_of(LS1, x1) < 0 || pos_of(LP, x2) < 0 || pos_of(LS2, x2) < 0) return false;
-  if (LS1.size() > 12 || LS2.size() > 12) return false;
-  const int p1 = pos_of(LP, x1), p2 = pos_of(LP, x2);
-  // C1 = P with x1 -> y1 in place; C2 = C1 with x2 -> y2 in place
-  if (LC1.size() != LP.size() || LC2.size() != LP.size()) return false;
-  for (size_t q = 0; q < LP.size(); ++q) {
-    const int32_t want1 = (int)q == p1 ? y1 : LP[q];
-    const int32_t want2 = (int)q == p2 ? y2 : want1;
-    if (LC1[q] != want1 || LC2[q] != want2) return false;
-  }
+// Chain of D frontier eliminations (k2_chain): node i = C_{i-1} . S_i -> C_i
+// (C_0 = P) for i = 1..D, each summing one index x_i of P; step i adds y_i
+// at x_i's position, except that the first step may also add a second
+// index z at the top (growth) and the last may add none (shrink; the
+// indices above x_D move down one position).  Labels are full
+// (with query bits).  `allow_gs` admits growth and shrink steps.  `fast`
+// is set when the chain has the FAST layout (S_i depends on no chain index
+// but the two added last; contiguous lanes; P's scale folds into S_1).
+bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int32_t>> &LS,
+               const std::vector<std::vector<int32_t>> &LC, bool f64, bool p_has_q, bool s1_has_q,
+               int32_t Qp, bool allow_gs, wmc::dev::K2CParams &cp, int &v_out, bool &fast, int &grow,
+               int &shrink, size_t &smem) {
+  const int D = (int)LS.size();
+  if (D < 2 || D > wmc::dev::kMaxChain || (int)LC.size() != D) return false;
   const int rP = (int)LP.size();
-  std::memset(&fp, 0, sizeof(fp));
-  K2Params &k = fp.t.k;
-  const int lo = std::min(p1, p2), hi = std::max(p1, p2);
-  k.n_insA = 2; k.insA[0] = (int8_t)lo; k.insA[1] = (int8_t)hi;
-  k.n_insC = 2; k.insC[0] = (int8_t)lo; k.insC[1] = (int8_t)hi;
-  k.k = 2; k.f = 2;
-  int vbits = f64 ? 1 : 2;
-  if (rP - 2 < vbits || lo < vbits) vbits = 0;
-  k.vbits = vbits;
-  k.log2_nu = rP - 2 - vbits;
-  if (p_has_q && (dev::kThreads * (1 << vbits)) % Qp != 0) return false;
-  // gathers of the small operands' batch bits from C2's offset
-  auto gathers = [&](const std::vector<int32_t> &LSx, int32_t skip_a, int32_t skip_b, int32_t loop,
-                     int8_t *seg_c, int8_t *seg_b, int8_t *seg_len, int32_t &nseg, uint32_t *dv,
-                     int32_t &mode) -> bool {
+  const int nthr = wmc::dev::kChainNW * 32;
+  std::vector<int32_t> x(D), y(D, INT32_MIN);
+  std::vector<int> p(D);
+  int32_t z = INT32_MIN;
+  grow = shrink = 0;
+  std::vector<int32_t> cur = LP;
+  for (int i = 0; i < D; ++i) {
+    const std::vector<int32_t> &S = LS[(size_t)i], &C = LC[(size_t)i];
+    std::vector<int32_t> summed, added;
+    for (int32_t l : cur) if (pos_of(C, l) < 0) summed.push_back(l);
+    for (int32_t l : S) if (pos_of(C, l) < 0 && pos_of(cur, l) < 0) summed.push_back(l);
+    for (int32_t l : S) if (pos_of(C, l) >= 0 && pos_of(cur, l) < 0) added.push_back(l);
+    if (summed.size() != 1 || S.size() > 12) return false;
+    x[(size_t)i] = summed[0];
+    p[(size_t)i] = pos_of(LP, x[(size_t)i]);
+    if (p[(size_t)i] < 0 || pos_of(cur, x[(size_t)i]) != p[(size_t)i] || pos_of(S, x[(size_t)i]) < 0) return false;
+    for (int j = 0; j < i; ++j) if (p[(size_t)j] == p[(size_t)i]) return false;
+    std::vector<int32_t> want = cur;
+    if (added.size() == 1) {
+      y[(size_t)i] = added[0];
+      want[(size_t)p[(size_t)i]] = y[(size_t)i];
+    } else if (added.size() == 2 && i == 0 && allow_gs) {
+      // one added index takes x_0's position, the other the new top one
+      const int32_t a0 = added[0], a1 = added[1];
+      const bool first_in_place = pos_of(C, a0) == p[0];
+      y[0] = first_in_place ? a0 : a1;
+      z = first_in_place ? a1 : a0;
+      want[(size_t)p[0]] = y[0];
+      want.push_back(z);
+      grow = 1;
+    } else if (added.empty() && i == D - 1 && allow_gs && !grow) {
+      want.erase(want.begin() + p[(size_t)i]);  // the indices above x_D move down
+      shrink = 1;
+    } else {
+      return false;
+    }
+    if (want != C) return false;
+    cur = want;
+  }
+  if (grow && shrink) return false;  // P and C of one size: not needed by any layout seen
+  const std::vector<int32_t> &LCD = LC.back();
+  const int NB = D + grow;
+  std::memset(&cp, 0, sizeof(cp));
+  std::vector<int> ins(p.begin(), p.end());
+  std::sort(ins.begin(), ins.end());
+  // C positions of the added indices (kept indices keep their order)
+  std::vector<int> insc;
+  for (int i = 0; i < D; ++i) if (y[(size_t)i] != INT32_MIN) insc.push_back(pos_of(LCD, y[(size_t)i]));
+  if (grow) insc.push_back(pos_of(LCD, z));
+  std::sort(insc.begin(), insc.end());
+  // lanes: at most 64 registers of chain values per thread, 32 KB tiles
+  int vbits = f64 ? (NB <= 3 ? 1 : 0) : (NB <= 3 ? 2 : 1);
+  if (vbits < 0 || rP - D < vbits || ins[0] < vbits || (!insc.empty() && insc[0] < vbits)) vbits = 0;
+  const int V = 1 << vbits;
+  if ((grow || shrink) && (f64 || V == 1)) return false;  // instantiated for float lanes only
+  if (p_has_q && (nthr * V) % Qp != 0) return false;
+  cp.vbits = vbits;
+  cp.log2_nu = rP - D - vbits;
+  cp.n_ins = D;
+  for (int i = 0; i < D; ++i) cp.ins[i] = (int8_t)ins[(size_t)i];
+  cp.n_insc = (int)insc.size();
+  for (size_t i = 0; i < insc.size(); ++i) cp.insc[i] = (int8_t)insc[i];
+  cp.fold_sp = (p_has_q && !s1_has_q) ? 0 : 1;
+  fast = cp.fold_sp != 0;
+  // the chain index behind state bit j at step i: y_j (j < i), x_j (j > i), z (bit D)
+  auto chain_bit_of = [&](int i, int32_t l) {
+    for (int j = 0; j < D; ++j) {
+      if (j == i) continue;
+      if (l == (j < i ? y[(size_t)j] : x[(size_t)j])) return j;
+    }
+    if (grow && i > 0 && l == z) return D;
+    return -1;
+  };
+  auto label_of_bit = [&](int i, int j) { return j == D ? z : (j < i ? y[(size_t)j] : x[(size_t)j]); };
+  const size_t es = f64 ? 8 : 4;
+  for (int i = 0; i < D; ++i) {
+    const std::vector<int32_t> &S = LS[(size_t)i];
     std::vector<std::pair<int, int>> bb;
-    for (size_t j = 0; j < LSx.size(); ++j) {
-      const int32_t l = LSx[j];
-      if (l == skip_a || l == skip_b || l == loop) continue;
-      const int pc = pos_of(LC2, l);
-      if (pc < 0 || pc == p1 || pc == p2) return false;
+    uint32_t deps = 0;
+    for (size_t j = 0; j < S.size(); ++j) {
+      const int32_t l = S[j];
+      if (l == x[(size_t)i] || l == y[(size_t)i] || (i == 0 && grow && l == z)) continue;
+      const int cb = chain_bit_of(i, l);
+      if (cb >= 0) { deps |= 1u << cb; continue; }
+      const int pc = pos_of(LCD, l);
+      if (pc < 0 || std::find(insc.begin(), insc.end(), pc) != insc.end()) return false;
       if (pc < vbits) {
-        for (int e = 0; e < (1 << vbits); ++e)
-          if ((e >> pc) & 1) dv[e] |= 1u << j;
+        for (int e = 0; e < V; ++e)
+          if ((e >> pc) & 1) cp.dv[i][e] |= 1u << j;
       } else {
         bb.push_back({pc, (int)j});
       }
     }
+    if (deps & ~wmc::dev::chain_deps(D, true, grow, i)) fast = false;
     std::sort(bb.begin(), bb.end());
-    nseg = 0;
-    for (size_t i = 0; i < bb.size();) {
-      size_t j = i + 1;
-      while (j < bb.size() && bb[j].first == bb[j - 1].first + 1 && bb[j].second == bb[j - 1].second + 1) ++j;
-      if (nseg >= 16) return false;
-      seg_c[nseg] = (int8_t)bb[i].first; seg_b[nseg] = (int8_t)bb[i].second; seg_len[nseg] = (int8_t)(j - i);
+    int nseg = 0;
+    for (size_t a = 0; a < bb.size();) {
+      size_t b = a + 1;
+      while (b < bb.size() && bb[b].first == bb[b - 1].first + 1 && bb[b].second == bb[b - 1].second + 1) ++b;
+      if (nseg >= 8) return false;
+      cp.seg_c[i][nseg] = (int8_t)bb[a].first;
+      cp.seg_b[i][nseg] = (int8_t)bb[a].second;
+      cp.seg_len[i][nseg] = (int8_t)(b - a);
       ++nseg;
-      i = j;
+      a = b;
     }
+    cp.n_seg[i] = nseg;
     bool contiguous = true, broadcast = true;
-    for (int e = 0; e < (1 << vbits); ++e) {
-      contiguous &= (dv[e] == (uint32_t)e);
-      broadcast &= (dv[e] == 0u);
+    for (int e = 0; e < V; ++e) {
+      contiguous &= (cp.dv[i][e] == (uint32_t)e);
+      broadcast &= (cp.dv[i][e] == 0u);
     }
-    mode = contiguous ? 1 : (broadcast ? 2 : 0);
-    return true;
-  };
-  if (!gathers(LS1, x1, y1, x2, k.seg_c, k.seg_b, k.seg_len, k.n_seg, fp.dv1, k.b_vec)) return false;
-  if (!gathers(LS2, x2, y2, y1, fp.seg2_c, fp.seg2_b, fp.seg2_len, fp.n_seg2, fp.dv2, fp.b_vec2)) return false;
-  const int sx1 = pos_of(LS1, x1), sy1 = pos_of(LS1, y1), sx2_1 = pos_of(LS1, x2);
-  const int sx2 = pos_of(LS2, x2), sy2 = pos_of(LS2, y2), sy1_2 = pos_of(LS2, y1);
-  for (int c = 0; c < 8; ++c) {
-    const int a0 = c & 1, a1 = (c >> 1) & 1, a2 = (c >> 2) & 1;
-    fp.d1[c] = (a0 ? 1u << sx1 : 0u) | (a1 ? 1u << sy1 : 0u) | ((a2 && sx2_1 >= 0) ? 1u << sx2_1 : 0u);
-    fp.d2[c] = (a0 ? 1u << sx2 : 0u) | (a1 ? 1u << sy2 : 0u) | ((a2 && sy1_2 >= 0) ? 1u << sy1_2 : 0u);
+    cp.b_vec[i] = contiguous ? 1 : (broadcast ? 2 : 0);
+    if (!contiguous) fast = false;
+    const int sx = pos_of(S, x[(size_t)i]);
+    const int sy = y[(size_t)i] != INT32_MIN ? pos_of(S, y[(size_t)i]) : -1;
+    const int sz = (i == 0 && grow) ? pos_of(S, z) : -1;
+    for (uint32_t st = 0; st < (1u << NB); ++st)
+      for (uint32_t av = 0; av < 4; ++av) {
+        uint32_t o = 0;
+        if ((st >> i) & 1u) o |= 1u << sx;
+        if ((av & 1u) && sy >= 0) o |= 1u << sy;
+        if ((av & 2u) && sz >= 0) o |= 1u << sz;
+        for (int j = 0; j < NB; ++j) {
+          if (j == i || !((st >> j) & 1u)) continue;
+          if (j == D && i == 0) continue;  // z is added by step 0 itself
+          const int32_t l = label_of_bit(i, j);
+          const int sj = l == INT32_MIN ? -1 : pos_of(S, l);
+          if (sj >= 0) o |= 1u << sj;
+        }
+        cp.d[i][st | (av << NB)] = o * (uint32_t)es;
+      }
+    cp.s_log2[i] = (int)S.size();
   }
-  for (int c = 0; c < 4; ++c) fp.dCf[c] = ((c & 1) ? 1u << p1 : 0u) | ((c & 2) ? 1u << p2 : 0u);
-  // tiling of P over its kept indices (as try_k2_tma, half the tile: four
-  // P values per unit and two staged small operands)
-  const int V = 1 << vbits;
-  const int J = V == 1 ? 2 : 1;
+  if (!fast && (grow || shrink)) return false;  // growth and shrink steps: FAST variants only
+  // tiling of P over its kept indices
   int tb = 0;
-  while ((1 << tb) < dev::kThreads * V * J) ++tb;
-  if (k.log2_nu + vbits < tb + 3) return false;
+  while ((1 << tb) < nthr * V) ++tb;
+  if (cp.log2_nu + vbits < tb + 3) return false;
   std::vector<int> kept;
   for (int q = 0; q < rP; ++q)
-    if (q != p1 && q != p2) kept.push_back(q);
+    if (std::find(p.begin(), p.end(), q) == p.end()) kept.push_back(q);
   if ((int)kept.size() < tb) return false;
   const int top = kept[(size_t)tb - 1] + 1;
   std::vector<int> lowv, highv;
-  for (int q : {lo, hi}) (q < top ? lowv : highv).push_back(q);
-  wmc::dev::K2TParams &tp = fp.t;
-  tp.tb = tb;
-  tp.run_log2 = top;
-  tp.nruns = 1 << (int)highv.size();
-  tp.n_lowA = (int)lowv.size();
-  for (size_t j = 0; j < lowv.size(); ++j) tp.lowA[j] = (int8_t)lowv[j];
-  for (int r = 0; r < tp.nruns; ++r) {
+  for (int q : ins) (q < top ? lowv : highv).push_back(q);
+  cp.tb = tb;
+  cp.run_log2 = top;
+  cp.nruns = 1 << (int)highv.size();
+  cp.n_low = (int)lowv.size();
+  for (size_t j = 0; j < lowv.size(); ++j) cp.low[j] = (int8_t)lowv[j];
+  for (int r = 0; r < cp.nruns; ++r) {
     uint32_t o = 0;
     for (size_t j = 0; j < highv.size(); ++j)
       if ((r >> j) & 1) o |= 1u << highv[j];
-    tp.run_off[r] = o;
+    cp.run_off[r] = o;
   }
-  for (int c = 0; c < 4; ++c) {
-    const uint32_t da = ((c & 1) ? 1u << p1 : 0u) | ((c & 2) ? 1u << p2 : 0u);
+  for (uint32_t st = 0; st < (1u << D); ++st) {
+    uint32_t da = 0;
+    for (int j = 0; j < D; ++j)
+      if ((st >> j) & 1u) da |= 1u << p[(size_t)j];
     uint32_t r = 0;
     for (size_t j = 0; j < highv.size(); ++j)
       if ((da >> highv[j]) & 1) r |= 1u << j;
-    fp.pA[c] = (r << top) | (da & ((1u << top) - 1u));
+    cp.pA[st] = (uint32_t)((((size_t)r << top) | (da & ((1u << top) - 1u))) * es);
   }
-  tp.s_log2 = (int)LS1.size();
-  fp.s2_log2 = (int)LS2.size();
-  tp.fold_sa = (p_has_q && s1_has_q) ? 1 : 0;
-  const size_t es = f64 ? 8 : 4;
-  smem = (size_t)dev::kStages * ((size_t)tp.nruns << top) * es + (((es << tp.s_log2) + 15) & ~(size_t)15) +
-         (((es << fp.s2_log2) + 15) & ~(size_t)15) + (16 + 2 * es) * (size_t)Qp;
-  return smem <= 100 * 1024;
+  // C offsets of the final states (bit D-1 of a shrink chain stays 0)
+  for (uint32_t st = 0; st < (1u << NB); ++st) {
+    uint32_t dc = 0;
+    for (int j = 0; j < NB; ++j) {
+      if (!((st >> j) & 1u)) continue;
+      const int32_t l = j == D ? z : y[(size_t)j];
+      if (l == INT32_MIN) continue;
+      dc |= 1u << pos_of(LCD, l);
+    }
+    cp.dC[st] = dc;
+  }
+  // shared memory: stages, the staged S_i (16-byte aligned bulk copies),
+  // per-lane max, min and D scales
+  size_t s_off = 0, s_copy = 0;
+  for (int i = 0; i < D; ++i) {
+    cp.s_bytes_off[i] = (uint32_t)s_off;
+    s_off += ((es << cp.s_log2[i]) + 15) & ~(size_t)15;
+    s_copy += es << cp.s_log2[i];
+    if ((es << cp.s_log2[i]) % 16) return false;
+  }
+  cp.s_bytes_off[D] = (uint32_t)s_off;
+  cp.s_copy_bytes = (uint32_t)s_copy;
+  const size_t tile_bytes = ((size_t)cp.nruns << top) * es;
+  const size_t fixed = s_off + (16 + (size_t)D * es) * (size_t)Qp;
+  const size_t limit = 220 * 1024;
+  int stages = 0;
+  for (int n = wmc::dev::kMaxStagesC; n >= 2; --n)
+    if ((size_t)n * tile_bytes + fixed <= limit) { stages = n; break; }
+  if (!stages) return false;
+  cp.n_stages = stages;
+  smem = (size_t)stages * tile_bytes + fixed;
+  v_out = V;
+  return true;
 }
 
 // Dense batched-matrix-product form (K4): every summed index in both
@@ -734,51 +823,83 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     }
     std::vector<int64_t> fuse_next(plan.nodes.size(), -1);
     std::vector<uint8_t> absorbed(plan.nodes.size(), 0);
-    for (size_t ni = 0; ni < plan.nodes.size() && g_fuse.load(); ++ni) {
-      if (absorbed[ni]) continue;
-      const Launch &li = node_l[ni];
-      if (li.kind != L_K2T || li.k2.k != 1 || li.k2.f != 1) continue;
-      const int64_t nj = consumer[(size_t)plan.nodes[ni].c];
-      if (nj < 0 || absorbed[(size_t)nj]) continue;
-      const Launch &lj = node_l[(size_t)nj];
-      if (lj.kind != L_K2T || lj.k2.k != 1 || lj.k2.f != 1 || lj.id_a != plan.nodes[ni].c) continue;
-      if (lj.k2.vbits != li.k2.vbits) continue;
-      bool clean = true;  // nodes between i and j must not be fused already
-      for (int64_t q = (int64_t)ni + 1; q < nj; ++q) clean &= !absorbed[(size_t)q] && fuse_next[(size_t)q] < 0;
-      if (!clean) continue;
-      const TensorInfo &P = plan.tensors[(size_t)li.id_a], &S1 = plan.tensors[(size_t)li.id_b];
-      const TensorInfo &C1 = plan.tensors[(size_t)plan.nodes[ni].c];
-      const TensorInfo &S2 = plan.tensors[(size_t)lj.id_b], &C2 = plan.tensors[(size_t)plan.nodes[(size_t)nj].c];
+    const int fuse_level = g_fuse.load();
+    // frontier steps: one summed index; f added ones (1 in place, 2 growth,
+    // 0 shrink); a chain starts with f >= 1 and ends at its first f = 0
+    auto frontier_f = [&](const Launch &l) { return (l.kind == L_K2T && l.k2.k == 1) ? l.k2.f : -1; };
+    for (size_t ni = 0; ni < plan.nodes.size() && fuse_level >= 2; ++ni) {
+      if (absorbed[ni] || frontier_f(node_l[ni]) < 1) continue;
+      // the longest run of frontier steps, each consuming the previous output
+      std::vector<int64_t> chain{(int64_t)ni};
+      while ((int)chain.size() < std::min(fuse_level, wmc::dev::kMaxChain)) {
+        const int64_t last = chain.back();
+        const int64_t nj = consumer[(size_t)plan.nodes[(size_t)last].c];
+        if (nj < 0 || absorbed[(size_t)nj]) break;
+        const int fj = frontier_f(node_l[(size_t)nj]);
+        if (fj != 0 && fj != 1) break;
+        if (node_l[(size_t)nj].id_a != plan.nodes[(size_t)last].c) break;
+        bool clean = true;  // nodes between must not be fused already
+        for (int64_t q = last + 1; q < nj; ++q) clean &= !absorbed[(size_t)q] && fuse_next[(size_t)q] < 0;
+        if (!clean) break;
+        chain.push_back(nj);
+        if (fj == 0) break;
+      }
+      const TensorInfo &P = plan.tensors[(size_t)node_l[ni].id_a];
       Launch f;
-      if (!try_fuse(full_labels(P, m), full_labels(S1, m), full_labels(C1, m), full_labels(S2, m),
-                    full_labels(C2, m), st.f64, P.has_q, S1.has_q, Qp, f.k2f, f.smem))
-        continue;
-      fuse_next[ni] = nj;
-      absorbed[(size_t)nj] = 1;
-      for (int64_t q = (int64_t)ni + 1; q < nj; ++q) absorbed[(size_t)q] = 2;  // moved before i
-      Launch &dst = node_l[ni];
-      f.kind = L_K2F;
+      int d_ok = 0;
+      for (int D = (int)chain.size(); D >= 2 && !d_ok; --D) {
+        std::vector<std::vector<int32_t>> LS, LC;
+        for (int i = 0; i < D; ++i) {
+          const Launch &l = node_l[(size_t)chain[(size_t)i]];
+          LS.push_back(full_labels(plan.tensors[(size_t)l.id_b], m));
+          LC.push_back(full_labels(plan.tensors[(size_t)plan.nodes[(size_t)chain[(size_t)i]].c], m));
+        }
+        const bool s1q = plan.tensors[(size_t)node_l[ni].id_b].has_q;
+        bool fast = false;
+        int grow = 0, shrink = 0;
+        if (try_chain(full_labels(P, m), LS, LC, st.f64, P.has_q, s1q, Qp, true, f.k2c, f.v, fast, grow, shrink,
+                      f.smem)) {
+          d_ok = D;
+          f.chain_fast = fast ? 1 : 0;
+          f.chain_grow = grow;
+          f.chain_shrink = shrink;
+        }
+      }
+      if (!d_ok) continue;
+      const int64_t nlast = chain[(size_t)d_ok - 1];
+      const TensorInfo &CD = plan.tensors[(size_t)plan.nodes[(size_t)nlast].c];
+      f.kind = L_K2C;
       f.ti = st.f64 ? TD : TF;
-      f.v = 1 << f.k2f.t.k.vbits;
-      f.id_a = li.id_a; f.id_b = li.id_b; f.id_s2 = lj.id_b; f.id_c = C2.node >= 0 ? plan.nodes[(size_t)nj].c : -1;
-      f.id_c1 = plan.nodes[ni].c;
-      f.k2f.t.k.ma.qmask = P.has_q ? Qp - 1 : 0;
-      f.k2f.t.k.mb.qmask = S1.has_q ? Qp - 1 : 0;
-      f.k2f.m2.qmask = S2.has_q ? Qp - 1 : 0;
-      f.k2f.t.k.mc.Qc = C2.has_q ? Qp : 1;
-      f.k2f.t.k.mc.Q = Qp;
-      f.k2f.t.k.mc.scale_inputs = 1;
-      const uint64_t n_tiles = 1ull << (f.k2f.t.k.log2_nu + f.k2f.t.k.vbits - f.k2f.t.tb);
-      f.blocks = (int64_t)std::min<uint64_t>(n_tiles, 148ull * 2);
-      f.alg_bytes = (double)bytes[(size_t)f.id_a] + (double)bytes[(size_t)f.id_b] +
-                    (double)bytes[(size_t)f.id_s2] + (double)bytes[(size_t)f.id_c];
-      dst = f;
+      f.chain_d = d_ok;
+      f.id_a = node_l[ni].id_a;
+      f.id_b = node_l[ni].id_b;
+      f.id_c = plan.nodes[(size_t)nlast].c;
+      f.k2c.mp.qmask = P.has_q ? Qp - 1 : 0;
+      f.alg_bytes = (double)bytes[(size_t)f.id_a] + (double)bytes[(size_t)f.id_c];
+      for (int i = 0; i < d_ok; ++i) {
+        const Launch &l = node_l[(size_t)chain[(size_t)i]];
+        f.id_sc[i] = l.id_b;
+        f.k2c.ms[i].qmask = plan.tensors[(size_t)l.id_b].has_q ? Qp - 1 : 0;
+        f.alg_bytes += (double)bytes[(size_t)l.id_b];
+      }
+      f.k2c.mc.Qc = CD.has_q ? Qp : 1;
+      f.k2c.mc.Q = Qp;
+      f.k2c.mc.scale_inputs = 1;
+      const uint64_t n_tiles = 1ull << (f.k2c.log2_nu + f.k2c.vbits - f.k2c.tb);
+      const int per_sm = std::max<int>(1, std::min<int>(2, (int)((227u * 1024u) / (f.smem + 2048))));
+      // (registers: NW*32+32 threads of at most 96 registers leave room for two blocks)
+      f.blocks = (int64_t)std::min<uint64_t>(n_tiles, 148ull * (uint64_t)per_sm);
+      fuse_next[ni] = nlast;
+      for (int i = 1; i < d_ok; ++i) absorbed[(size_t)chain[(size_t)i]] = 1;
+      for (int64_t q = (int64_t)ni + 1; q < nlast; ++q)
+        if (!absorbed[(size_t)q]) absorbed[(size_t)q] = 2;  // moved before the chain
+      node_l[ni] = f;
     }
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       if (absorbed[ni]) continue;
       if (fuse_next[ni] >= 0)
         for (int64_t q = (int64_t)ni + 1; q < fuse_next[ni]; ++q)
-          if (sp_index[(size_t)q] < 0) steps.push_back({q, -1});
+          if (absorbed[(size_t)q] == 2 && sp_index[(size_t)q] < 0) steps.push_back({q, -1});
       if (sp_index[ni] >= 0) continue;  // runs in the small-node phase
       steps.push_back({(int64_t)ni, fuse_next[ni]});
     }
@@ -803,7 +924,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     st.t_off[(size_t)l.id_c] = arena0 + ff.alloc(bytes[(size_t)l.id_c]);
     release(l.id_a);
     release(l.id_b);
-    if (l.kind == L_K2F) release(l.id_s2);
+    if (l.kind == L_K2C)
+      for (int i = 1; i < l.chain_d; ++i) release(l.id_sc[i]);
     st.alg_bytes += l.alg_bytes;
   }
   for (const Node &nd : plan.nodes) {
@@ -910,10 +1032,11 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     l.meta_a = st.t_meta[(size_t)l.id_a];
     l.meta_b = st.t_meta[(size_t)l.id_b];
     l.meta_c = st.t_meta[(size_t)l.id_c];
-    if (l.kind == L_K2F) {
-      l.off_s2 = st.t_off[(size_t)l.id_s2];
-      l.meta_s2 = st.t_meta[(size_t)l.id_s2];
-    }
+    if (l.kind == L_K2C)
+      for (int i = 0; i < l.chain_d; ++i) {
+        l.off_sc[i] = st.t_off[(size_t)l.id_sc[i]];
+        l.meta_sc[i] = st.t_meta[(size_t)l.id_sc[i]];
+      }
     st.launches.push_back(l);
   }
   Launch fin;
@@ -987,23 +1110,53 @@ static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream
   }
 }
 
-template <typename T, int V>
-static void launch_k2f_t(const wmc::dev::K2FParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
+template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
+static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(dev::k2_fused<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(dev::k2_chain<T, V, D, FAST, GROW, SHRINK>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  dev::k2_fused<T, V><<<(unsigned)blocks, dev::kThreads + 32, smem, s>>>(p);
+  dev::k2_chain<T, V, D, FAST, GROW, SHRINK><<<(unsigned)blocks, dev::kChainNW * 32 + 32, smem, s>>>(p);
 }
 
-static void launch_k2f(const Launch &l, const wmc::dev::K2FParams &p, cudaStream_t s) {
+// vector lanes: FAST plain chains, growth-first and shrink-last variants
+template <int V, int D>
+static void launch_k2c_vec(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
+  if (!l.chain_fast) launch_k2c_t<float, V, D, false, 0, 0>(p, l.blocks, l.smem, s);
+  else if (l.chain_grow) launch_k2c_t<float, V, D, true, 1, 0>(p, l.blocks, l.smem, s);
+  else if (l.chain_shrink) launch_k2c_t<float, V, D, true, 0, 1>(p, l.blocks, l.smem, s);
+  else launch_k2c_t<float, V, D, true, 0, 0>(p, l.blocks, l.smem, s);
+}
+template <typename T, int V, int D>
+static void launch_k2c_plain(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
+  if (l.chain_fast) launch_k2c_t<T, V, D, true, 0, 0>(p, l.blocks, l.smem, s);
+  else launch_k2c_t<T, V, D, false, 0, 0>(p, l.blocks, l.smem, s);
+}
+
+// instantiated (T, V, D) as try_chain chooses them: V at its largest for
+// the state size, or 1 when the chain positions leave no vector lanes
+static void launch_k2c(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
+  const int D = l.chain_d, V = l.v, NB = D + l.chain_grow;
   if (l.ti == TF) {
-    if (l.v == 4) launch_k2f_t<float, 4>(p, l.blocks, l.smem, s);
-    else launch_k2f_t<float, 1>(p, l.blocks, l.smem, s);
+    if (V == 1) {
+      if (D == 2) launch_k2c_plain<float, 1, 2>(l, p, s);
+      else if (D == 3) launch_k2c_plain<float, 1, 3>(l, p, s);
+      else launch_k2c_plain<float, 1, 4>(l, p, s);
+    } else if (D == 2) {
+      launch_k2c_vec<4, 2>(l, p, s);
+    } else if (D == 3 && NB == 3) {
+      launch_k2c_vec<4, 3>(l, p, s);
+    } else if (D == 3) {
+      launch_k2c_vec<2, 3>(l, p, s);
+    } else {
+      launch_k2c_vec<2, 4>(l, p, s);
+    }
   } else {
-    if (l.v == 2) launch_k2f_t<double, 2>(p, l.blocks, l.smem, s);
-    else launch_k2f_t<double, 1>(p, l.blocks, l.smem, s);
+    if (D == 2) { if (V == 2) launch_k2c_plain<double, 2, 2>(l, p, s); else launch_k2c_plain<double, 1, 2>(l, p, s); }
+    else if (D == 3) { if (V == 2) launch_k2c_plain<double, 2, 3>(l, p, s); else launch_k2c_plain<double, 1, 3>(l, p, s); }
+    else launch_k2c_plain<double, 1, 4>(l, p, s);
   }
 }
 
@@ -1124,20 +1277,21 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         dev::k_small_phase<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(a);
         break;
       }
-      case L_K2F: {
-        wmc::dev::K2FParams fp = l.k2f;
-        K2Params &p = fp.t.k;
-        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
-        fp.S2 = ws + l.off_s2;
-        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
-        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
-        fp.m2.exp = mexp + l.meta_s2; fp.m2.maxb = mmax + l.meta_s2; fp.m2.minb = mmin + l.meta_s2;
-        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
-        p.mc.flags = flags;
-        fp.t.err = (uint32_t *)(ws + st.off_err);
-        fp.t.debug_stall = stall_armed ? 1 : 0;
+      case L_K2C: {
+        wmc::dev::K2CParams cp = l.k2c;
+        cp.P = ws + l.off_a;
+        cp.C = ws + l.off_c;
+        cp.mp.exp = mexp + l.meta_a; cp.mp.maxb = mmax + l.meta_a; cp.mp.minb = mmin + l.meta_a;
+        for (int i = 0; i < l.chain_d; ++i) {
+          cp.S[i] = ws + l.off_sc[i];
+          cp.ms[i].exp = mexp + l.meta_sc[i]; cp.ms[i].maxb = mmax + l.meta_sc[i]; cp.ms[i].minb = mmin + l.meta_sc[i];
+        }
+        cp.mc.exp = mexp + l.meta_c; cp.mc.maxb = mmax + l.meta_c; cp.mc.minb = mmin + l.meta_c;
+        cp.mc.flags = flags;
+        cp.err = (uint32_t *)(ws + st.off_err);
+        cp.debug_stall = stall_armed ? 1 : 0;
         stall_armed = false;
-        launch_k2f(l, fp, s);
+        launch_k2c(l, cp, s);
         break;
       }
       case L_K4: {
@@ -1392,7 +1546,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_K2F ? 6 : l.kind == L_SMALL ? 7 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -1768,7 +1922,83 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     ++li;
     // k4 offsets are bit scatters onto each tensor's own positions: in
     // bounds by construction
-    if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1 && l.kind != L_K2F) continue;
+    if (l.kind == L_K2C) {
+      const wmc::dev::K2CParams &cp = l.k2c;
+      const int64_t es = l.ti == TD ? 8 : 4;
+      const int V = 1 << cp.vbits, D = l.chain_d;
+      const int64_t np = st->t_bytes[(size_t)l.id_a] / es, nc = st->t_bytes[(size_t)l.id_c] / es;
+      auto badc = [&](const char *what, int64_t o, int64_t n) {
+        set_error("launch %zu: chain %s offset %lld outside [0, %lld)", li, what, (long long)o, (long long)n);
+        return WMC_EINVAL;
+      };
+      for (int i = 0; i < D; ++i)
+        if (l.id_sc[i] < 0 || st->t_bytes[(size_t)l.id_sc[i]] != (int64_t)es << cp.s_log2[i])
+          return badc("S size", i, D);
+      const uint64_t nu = 1ull << cp.log2_nu;
+      std::vector<uint64_t> us;
+      if (nu <= (1u << 14)) for (uint64_t u = 0; u < nu; ++u) us.push_back(u);
+      else {
+        for (uint64_t u = 0; u < 4096; ++u) { us.push_back(u); us.push_back(nu - 1 - u); }
+        uint64_t x = 0x9e3779b97f4a7c15ull;
+        for (int i = 0; i < 8192; ++i) { x ^= x << 13; x ^= x >> 7; x ^= x << 17; us.push_back(x % nu); }
+      }
+      const int NB = D + l.chain_grow;
+      uint32_t xmask = 0;
+      for (int i = 0; i < cp.n_ins; ++i) xmask |= 1u << cp.ins[i];
+      for (uint64_t u : us) {
+        const uint32_t w = (uint32_t)(u << cp.vbits);
+        uint32_t op = w, oc = w;
+        for (int i = 0; i < cp.n_ins; ++i) op = h_insert0(op, cp.ins[i]);
+        for (int i = 0; i < cp.n_insc; ++i) oc = h_insert0(oc, cp.insc[i]);
+        if (op % (uint32_t)V || oc % (uint32_t)V) return badc("unaligned vector", oc, V);
+        if ((int64_t)(op | xmask) + V - 1 >= np) return badc("P", (int64_t)(op | xmask) + V - 1, np);
+        for (int i = 0; i < D; ++i) {
+          uint32_t g = 0;
+          for (int j = 0; j < cp.n_seg[i]; ++j)
+            g |= ((oc >> cp.seg_c[i][j]) & ((1u << cp.seg_len[i][j]) - 1u)) << cp.seg_b[i][j];
+          const int64_t ns = int64_t(1) << cp.s_log2[i];
+          for (int c = 0; c < (4 << NB); ++c)
+            for (int e = 0; e < V; ++e) {
+              const int64_t lane = cp.b_vec[i] == 1 ? e : (cp.b_vec[i] == 2 ? 0 : cp.dv[i][e]);
+              const int64_t o = (int64_t)g + cp.d[i][c] / es + lane;
+              if (cp.d[i][c] % es || o >= ns) return badc("S", o, ns);
+            }
+        }
+        for (int c = 0; c < (1 << NB); ++c)
+          if ((int64_t)(oc | cp.dC[c]) + V - 1 >= nc) return badc("C", (int64_t)(oc | cp.dC[c]) + V - 1, nc);
+        ++checked;
+      }
+      const uint64_t n_tiles = 1ull << (cp.log2_nu + cp.vbits - cp.tb);
+      const int64_t run_len = 1ll << cp.run_log2;
+      const int64_t tile_elems = (int64_t)cp.nruns * run_len;
+      for (uint64_t t = 0; t < n_tiles; ++t) {
+        uint32_t base = (uint32_t)(t << cp.tb);
+        for (int j = 0; j < cp.n_ins; ++j) base = h_insert0(base, cp.ins[j]);
+        for (int r = 0; r < cp.nruns; ++r) {
+          const int64_t lo = (int64_t)base + cp.run_off[r];
+          if ((lo * es) % 16 || (run_len * es) % 16 || lo + run_len > np) return badc("bulk copy", lo + run_len - 1, np);
+        }
+        ++checked;
+      }
+      for (uint32_t wl = 0; wl < (1u << cp.tb); wl += (uint32_t)V) {
+        uint32_t la = wl;
+        for (int j = 0; j < cp.n_low; ++j) la = h_insert0(la, cp.low[j]);
+        for (int c = 0; c < (1 << D); ++c) {
+          const int64_t o = (int64_t)cp.pA[c] / es + la + V - 1;
+          if (cp.pA[c] % es || o >= tile_elems) return badc("stage", o, tile_elems);
+        }
+      }
+      // shared memory: stages, staged S_i, per-lane max/min and D scales
+      size_t need = (size_t)cp.n_stages * (size_t)tile_elems * (size_t)es + cp.s_bytes_off[D] +
+                    (16 + (size_t)D * (size_t)es) * (size_t)cp.mc.Qc;
+      for (int i = 0; i < D; ++i)
+        if (cp.s_bytes_off[i] % 16 || cp.s_bytes_off[i] + ((size_t)es << cp.s_log2[i]) > cp.s_bytes_off[i + 1])
+          return badc("staged S", i, D);
+      if (need > l.smem || l.smem > 220 * 1024 || cp.n_stages < 2 || cp.n_stages > wmc::dev::kMaxStagesC)
+        return badc("shared memory", (int64_t)need, (int64_t)l.smem);
+      continue;
+    }
+    if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1) continue;
     const int64_t ta = l.id_a, tb = l.id_b, tc = l.id_c;
     if (ta < 0 || tb < 0 || tc < 0) { set_error("launch %zu: unknown tensor", li); return WMC_EINVAL; }
     const int64_t es_in = l.kind == L_K1 ? (l.ti == TD ? 8 : 4) : (l.ti == TD ? 8 : 4);
@@ -1801,59 +2031,6 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
       if (mb >= nb) return bad("B", mb, nb);
       if ((1ll << p.rC) > nc) return bad("C", (1ll << p.rC) - 1, nc);
       ++checked;
-      continue;
-    }
-    if (l.kind == L_K2F) {
-      const wmc::dev::K2FParams &fp = l.k2f;
-      const K2Params &p = fp.t.k;
-      const int V = 1 << p.vbits;
-      const int64_t ns2 = st->t_bytes[(size_t)l.id_s2] / es_in;
-      const uint64_t nu = 1ull << p.log2_nu;
-      std::vector<uint64_t> us;
-      if (nu <= (1u << 14)) for (uint64_t u = 0; u < nu; ++u) us.push_back(u);
-      else {
-        for (uint64_t u = 0; u < 4096; ++u) { us.push_back(u); us.push_back(nu - 1 - u); }
-        uint64_t x = 0x9e3779b97f4a7c15ull;
-        for (int i = 0; i < 8192; ++i) { x ^= x << 13; x ^= x >> 7; x ^= x << 17; us.push_back(x % nu); }
-      }
-      for (uint64_t u : us) {
-        const uint32_t w = (uint32_t)(u << p.vbits);
-        uint32_t oa = w, oc = w, g1 = 0, g2 = 0;
-        for (int i = 0; i < p.n_insA; ++i) oa = h_insert0(oa, p.insA[i]);
-        for (int i = 0; i < p.n_insC; ++i) oc = h_insert0(oc, p.insC[i]);
-        for (int i = 0; i < p.n_seg; ++i) g1 |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
-        for (int i = 0; i < fp.n_seg2; ++i) g2 |= ((oc >> fp.seg2_c[i]) & ((1u << fp.seg2_len[i]) - 1u)) << fp.seg2_b[i];
-        for (int c = 0; c < 8; ++c)
-          for (int e = 0; e < V; ++e) {
-            if ((int64_t)g1 + fp.d1[c] + fp.dv1[e] >= nb) return bad("S1", (int64_t)g1 + fp.d1[c] + fp.dv1[e], nb);
-            if ((int64_t)g2 + fp.d2[c] + fp.dv2[e] >= ns2) return bad("S2", (int64_t)g2 + fp.d2[c] + fp.dv2[e], ns2);
-          }
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t pa = ((c & 1) ? fp.dCf[1] : 0u) | ((c & 2) ? fp.dCf[2] : 0u);  // same positions in P
-          if ((int64_t)(oa | pa) + V - 1 >= na) return bad("P", (int64_t)(oa | pa) + V - 1, na);
-          if ((int64_t)(oc | fp.dCf[c]) + V - 1 >= nc) return bad("C", (int64_t)(oc | fp.dCf[c]) + V - 1, nc);
-        }
-        ++checked;
-      }
-      const wmc::dev::K2TParams &tp = fp.t;
-      const uint64_t n_tiles = 1ull << (p.log2_nu + p.vbits - tp.tb);
-      const int64_t run_len = 1ll << tp.run_log2;
-      const int64_t tile_elems = (int64_t)tp.nruns * run_len;
-      for (uint64_t t = 0; t < n_tiles; ++t) {
-        uint32_t base = (uint32_t)(t << tp.tb);
-        for (int j = 0; j < p.n_insA; ++j) base = h_insert0(base, p.insA[j]);
-        for (int r = 0; r < tp.nruns; ++r) {
-          const int64_t lo = (int64_t)base + tp.run_off[r];
-          if (lo % 4 || lo + run_len > na) return bad("bulk copy", lo + run_len - 1, na);
-        }
-        ++checked;
-      }
-      for (uint32_t wl = 0; wl < (1u << tp.tb); wl += (uint32_t)V) {
-        uint32_t la = wl;
-        for (int j = 0; j < tp.n_lowA; ++j) la = h_insert0(la, tp.lowA[j]);
-        for (int c = 0; c < 4; ++c)
-          if ((int64_t)fp.pA[c] + la + V - 1 >= tile_elems) return bad("stage", (int64_t)fp.pA[c] + la + V - 1, tile_elems);
-      }
       continue;
     }
     const K2Params &p = l.kind == L_K2T ? l.k2t.k : l.k2;

@@ -469,6 +469,11 @@ template <> struct LdsV<float, 4> {
                  : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]) : "r"(a));
   }
 };
+template <> struct LdsV<float, 2> {
+  static __device__ __forceinline__ void ld(uint32_t a, float (&r)[2]) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r[0]), "=f"(r[1]) : "r"(a));
+  }
+};
 template <> struct LdsV<float, 1> {
   static __device__ __forceinline__ void ld(uint32_t a, float (&r)[1]) {
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r[0]) : "r"(a));
@@ -717,277 +722,436 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
-// ------------------------------------------------- fused pair of eliminations
+// ---------------------------------------------- chain of frontier eliminations
 //
-// Two consecutive frontier contractions C1 = P . S1 (summing x1, adding y1
-// at x1's position) and C2 = C1 . S2 (summing x2, adding y2 at x2's
-// position) in one pass over P: per work unit the thread loads P for the
-// four (x1, x2) assignments, forms C1 in registers for both values of x2
-// and y1 (stage 1), and contracts x2 against S2 (stage 2).  C1 never
-// reaches memory, so the pair moves |P| + |C2| bytes instead of
-// 2|P| + 2|C2|.  The sums run in the same order as the unfused pair; C1 is
-// not rescaled between the stages (its scale is a power of two, so only
-// the exponent bookkeeping differs).  Tiling, staging and bounded waits
-// are those of k2_tma (P's summed positions are {x1, x2}, C2's new ones
-// the same two positions); S1 and S2 are both staged in shared memory.
+// D consecutive frontier contractions C_i = C_{i-1} . S_i (C_0 = P) in one
+// pass over P, each summing one index x_i of P.  Step i adds y_i at x_i's
+// position (in place); with GROW the first step adds a second index z at
+// the top of the frontier, with SHRINK the last step adds none (the
+// frontier's higher indices move down one position).  A work unit is one
+// assignment of P's other (kept) indices: the thread loads the 2^D values
+// of P over (x_1..x_D) into registers and applies the steps in place:
+// bit i of the register index means x_i before step i and y_i after it,
+// bit D (GROW) means z.  Only P and C_D touch memory: |P| + |C_D| bytes for
+// D eliminations instead of the sum over the D separate passes.
+//
+// Each output of a step is a two-term FMA chain over x_i = 0, 1 starting
+// from zero, the order every other kernel uses for one summed index, and
+// the intermediates are not rescaled (their scales are powers of two, so
+// only the exponent bookkeeping moves): results are bit-identical to D
+// separate launches.  S_i may depend on other chain indices; the host
+// passes S_i's offset for every state of the chain bits.  The FAST
+// variants are compiled for the common layout: S_i depends on no chain
+// index but the two added last before y_i (so each block of S_i is loaded
+// once per dependency combination, not once per pair), every S_i holds
+// its query lanes contiguously, and P's scale folds into S_1.  The S_i
+// arrive in shared memory by bulk async copies and are scaled there; P is
+// staged tile by tile by bulk async copies that the whole producer warp
+// issues, with NW consumer warps.
 
-struct K2FParams {
-  K2TParams t;            // tiling of P over its kept indices; t.k.B = S1, t.k.seg_* gather S1
-  const void *S2;
-  Meta m2;                // S2's metadata
-  int32_t s2_log2;
-  int32_t n_seg2;
-  int8_t seg2_c[16], seg2_b[16], seg2_len[16];
-  int32_t b_vec2;         // S2 lanes: 0 per lane, 1 contiguous, 2 broadcast
-  uint32_t dv1[4], dv2[4];
-  uint32_t d1[8];         // S1 offset of (x1, y1, x2): index x1 + 2 y1 + 4 x2
-  uint32_t d2[8];         // S2 offset of (x2, y2, y1): index x2 + 2 y2 + 4 y1
-  uint32_t pA[4];         // stage offset of P for (x1, x2): index x1 + 2 x2
-  uint32_t dCf[4];        // C2 offset of (y1, y2): index y1 + 2 y2
+constexpr int kMaxChain = 4;
+constexpr int kMaxStagesC = 4;
+constexpr int kChainNW = 8;  // consumer warps
+
+struct K2CParams {
+  const void *P;
+  void *C;
+  Meta mp;
+  OutMeta mc;
+  const void *S[kMaxChain];
+  Meta ms[kMaxChain];
+  int32_t vbits;
+  int32_t log2_nu;                // kept bits of P above the lane bits
+  int32_t n_ins;                  // chain positions in P (x_i), ascending
+  int8_t ins[kMaxChain];
+  int32_t n_insc;                 // positions in C of the added indices, ascending
+  int8_t insc[kMaxChain + 1];
+  int32_t tb;                     // log2 work units per tile
+  int32_t run_log2, nruns;        // P runs per tile
+  int32_t n_low;                  // chain positions inside a run
+  int8_t low[kMaxChain];
+  uint32_t run_off[1 << kMaxChain];
+  int32_t n_stages;
+  int32_t fold_sp;                // P's scale is folded into the staged S_1
+  uint32_t s_bytes_off[kMaxChain + 1];  // byte offset of staged S_i after the stages
+  uint32_t s_copy_bytes;          // sum of the S_i sizes
+  int32_t s_log2[kMaxChain];
+  int32_t n_seg[kMaxChain];       // gathers of S_i's other indices from C's offset
+  int8_t seg_c[kMaxChain][8], seg_b[kMaxChain][8], seg_len[kMaxChain][8];
+  int32_t b_vec[kMaxChain];       // S_i lanes: 0 per lane, 1 contiguous, 2 broadcast
+  uint32_t dv[kMaxChain][4];      // S_i element offset of lane e (mode 0)
+  // S_i byte offset of (state s, added value(s) a): d[i][s | a << NB], NB =
+  // D + GROW state bits; a = y_i, or y_0 + 2 z for a growth step, or 0
+  uint32_t d[kMaxChain][4 << (kMaxChain + 1)];
+  uint32_t pA[1 << kMaxChain];    // stage byte offset of P for x-state s
+  uint32_t dC[2 << kMaxChain];    // C element offset of final state s
+  uint32_t *err;
+  int32_t debug_stall;
 };
 
-template <typename T, int V>
-__device__ __forceinline__ void lds_lanes(uint32_t base, int mode, const uint32_t *dv, T (&r)[V]) {
-  constexpr uint32_t es = (uint32_t)sizeof(T);
-  if (V > 1 && mode == 1) {
-    LdsV<T, V>::ld(base, r);
+__host__ __device__ constexpr uint32_t pdep_c(uint32_t t, uint32_t mask) {
+  uint32_t r = 0;
+  int k = 0;
+  for (int j = 0; j < 32; ++j)
+    if ((mask >> j) & 1u) {
+      if ((t >> k) & 1u) r |= 1u << j;
+      ++k;
+    }
+  return r;
+}
+__host__ __device__ constexpr int popc_c(uint32_t m) { return m ? (int)(m & 1u) + popc_c(m >> 1) : 0; }
+// state bits other than x_i present at step i: the added ones of the
+// earlier steps (y_j, and z once the growth step is done) and the x_j of
+// the later steps
+__host__ __device__ constexpr uint32_t chain_others(int D, int grow, int i) {
+  return (((1u << D) - 1u) & ~(1u << i)) | ((grow && i > 0) ? 1u << D : 0u);
+}
+// chain bits that S_i may depend on: the FAST layout allows the two
+// indices added last before step i (in the order y_0, z, y_1, y_2, ...),
+// the generic one any
+__host__ __device__ constexpr uint32_t chain_deps(int D, bool fast, int grow, int i) {
+  uint32_t m = 0;
+  int n = 0;
+  for (int j = i - 1; j >= 0 && n < 2; --j) {
+    if (j == 0 && grow) {
+      m |= 1u << D;
+      if (++n == 2) break;
+    }
+    m |= 1u << j;
+    ++n;
+  }
+  return fast ? (m & chain_others(D, grow, i)) : chain_others(D, grow, i);
+}
+
+// V lanes of a staged S_i at shared-memory byte address `a`
+template <typename T, int V, bool FAST>
+__device__ __forceinline__ void ld_lanes(uint32_t a, int mode, const uint32_t *dv, T (&r)[V]) {
+  if (FAST || V == 1 || mode == 1) {
+    LdsV<T, V>::ld(a, r);
   } else if (mode == 2) {
-    const T v = lds1(base, T());
+    const T v = lds1(a, T());
 #pragma unroll
-    for (int e = 0; e < V; ++e) r[e] = v;
+    for (int i = 0; i < V; ++i) r[i] = v;
   } else {
 #pragma unroll
-    for (int e = 0; e < V; ++e) r[e] = lds1(base + dv[e] * es, T());
+    for (int i = 0; i < V; ++i) r[i] = lds1(a + dv[i] * (uint32_t)sizeof(T), T());
   }
 }
 
+// out = fma(in1, b1, fma(in0, b0, 0)) on V lanes; float lanes go two at a
+// time through the packed FP32 FMA (each half is an ordinary
+// round-to-nearest fma, so the results are those of the scalar chain)
 template <typename T, int V>
-__global__ void __launch_bounds__(kThreads + 32, 2) k2_fused(K2FParams fp) {
+__device__ __forceinline__ void fma2terms(const T (&x0)[V], const T (&x1)[V], const T (&b0)[V],
+                                          const T (&b1)[V], T (&out)[V]) {
+#pragma unroll
+  for (int e = 0; e < V; ++e) out[e] = fma_t(x1[e], b1[e], fma_t(x0[e], b0[e], (T)0));
+}
+template <int V>
+__device__ __forceinline__ void fma2terms_f2(const float (&x0)[V], const float (&x1)[V], const float (&b0)[V],
+                                             const float (&b1)[V], float (&out)[V]) {
+  const float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int h = 0; h < V; h += 2) {
+    float2 c = __ffma2_rn(make_float2(x0[h], x0[h + 1]), make_float2(b0[h], b0[h + 1]), z);
+    c = __ffma2_rn(make_float2(x1[h], x1[h + 1]), make_float2(b1[h], b1[h + 1]), c);
+    out[h] = c.x;
+    out[h + 1] = c.y;
+  }
+}
+template <>
+__device__ __forceinline__ void fma2terms<float, 2>(const float (&x0)[2], const float (&x1)[2], const float (&b0)[2],
+                                                    const float (&b1)[2], float (&out)[2]) {
+  fma2terms_f2<2>(x0, x1, b0, b1, out);
+}
+template <>
+__device__ __forceinline__ void fma2terms<float, 4>(const float (&x0)[4], const float (&x1)[4], const float (&b0)[4],
+                                                    const float (&b1)[4], float (&out)[4]) {
+  fma2terms_f2<4>(x0, x1, b0, b1, out);
+}
+
+// step I of the chain on the register block a (compile-time indices);
+// KIND 1 in place, 2 growth (adds z at bit D), 0 shrink (adds nothing)
+template <typename T, int V, int D, bool FAST, int GROW, int KIND, int I>
+__device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&a)[1 << (D + GROW)][V]) {
+  constexpr int NB = D + GROW;
+  constexpr uint32_t G = chain_deps(D, FAST, GROW, I);
+  constexpr uint32_t O = chain_others(D, GROW, I) & ~G;
+  constexpr int nG = popc_c(G), nO = popc_c(O);
+  constexpr uint32_t XB = 1u << I;
+  const int mode = cp.b_vec[I];
+#pragma unroll
+  for (uint32_t tg = 0; tg < (1u << nG); ++tg) {
+    const uint32_t sg = pdep_c(tg, G);
+    constexpr int NA = KIND == 2 ? 4 : (KIND == 1 ? 2 : 1);  // added-value combinations
+    T b[2][NA][V];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int av = 0; av < NA; ++av)
+        ld_lanes<T, V, FAST>(g + cp.d[I][(sg | (x ? XB : 0u)) | ((uint32_t)av << NB)], mode, cp.dv[I], b[x][av]);
+#pragma unroll
+    for (uint32_t to = 0; to < (1u << nO); ++to) {
+      const uint32_t s0 = sg | pdep_c(to, O), s1 = s0 | XB;
+      if (KIND == 1) {
+        T c0[V], c1[V];
+        fma2terms<T, V>(a[s0], a[s1], b[0][0], b[1][0], c0);
+        fma2terms<T, V>(a[s0], a[s1], b[0][NA - 1], b[1][NA - 1], c1);
+#pragma unroll
+        for (int e = 0; e < V; ++e) { a[s0][e] = c0[e]; a[s1][e] = c1[e]; }
+      } else if (KIND == 2) {
+        constexpr uint32_t ZB = 1u << D;
+        T c[4][V];
+#pragma unroll
+        for (int av = 0; av < 4; ++av) fma2terms<T, V>(a[s0], a[s1], b[0][av & (NA - 1)], b[1][av & (NA - 1)], c[av]);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          a[s0][e] = c[0][e];
+          a[s1][e] = c[1][e];
+          a[(s0 | ZB) & ((1u << NB) - 1u)][e] = c[2][e];
+          a[(s1 | ZB) & ((1u << NB) - 1u)][e] = c[3][e];
+        }
+      } else {
+        T c0[V];
+        fma2terms<T, V>(a[s0], a[s1], b[0][0], b[1][0], c0);
+#pragma unroll
+        for (int e = 0; e < V; ++e) a[s0][e] = c0[e];
+      }
+    }
+  }
+}
+
+template <typename T, int V, int D, bool FAST, int GROW, int SHRINK, int I>
+struct ChainSteps {
+  static __device__ __forceinline__ void run(const K2CParams &cp, const uint32_t (&g)[D],
+                                             T (&a)[1 << (D + GROW)][V]) {
+    constexpr int KIND = (I == 0 && GROW) ? 2 : ((I == D - 1 && SHRINK) ? 0 : 1);
+    chain_step<T, V, D, FAST, GROW, KIND, I>(cp, g[I], a);
+    ChainSteps<T, V, D, FAST, GROW, SHRINK, I + 1>::run(cp, g, a);
+  }
+};
+template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
+struct ChainSteps<T, V, D, FAST, GROW, SHRINK, D> {
+  static __device__ __forceinline__ void run(const K2CParams &, const uint32_t (&)[D],
+                                             T (&)[1 << (D + GROW)][V]) {}
+};
+
+// min over nonzero bit patterns, tracked as (bits - 1) with zero wrapping
+__device__ __forceinline__ uint32_t min_m1(uint32_t bits, uint32_t cur) {
+  return __viaddmin_u32(bits, 0xffffffffu, cur);
+}
+__device__ __forceinline__ unsigned long long min_m1(unsigned long long bits, unsigned long long cur) {
+  const unsigned long long m = bits - 1ull;
+  return m < cur ? m : cur;
+}
+
+template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
+__global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) {
   typedef typename Bits<T>::t BT;
+  constexpr int NW = kChainNW;
+  constexpr int NB = D + GROW;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages];
-  __shared__ uint32_t tile_oc[kStages], tile_gb[kStages], tile_gb2[kStages];
+  __shared__ __align__(8) unsigned long long full[kMaxStagesC], empty[kMaxStagesC], sbar;
+  __shared__ uint32_t tile_oc[kMaxStagesC], tile_gb[kMaxChain][kMaxStagesC];
   __shared__ int s_skip;
-  const K2TParams &tp = fp.t;
-  const K2Params &p = tp.k;
-  if (threadIdx.x == 0) s_skip = (tp.err && *(volatile uint32_t *)tp.err) ? 1 : 0;
+  if (threadIdx.x == 0) s_skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
   __syncthreads();
   if (s_skip) return;  // an earlier launch of this walk gave up: skip the work
-  const uint32_t run_len = 1u << tp.run_log2;
-  const uint32_t tile_elems = (uint32_t)tp.nruns * run_len;
+  const int n_stages = cp.n_stages;
+  const uint32_t run_len = 1u << cp.run_log2;
+  const uint32_t tile_elems = (uint32_t)cp.nruns * run_len;
   const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
-  const uint32_t n_tiles = 1u << (p.log2_nu + p.vbits - tp.tb);
+  const uint32_t n_tiles = 1u << (cp.log2_nu + cp.vbits - cp.tb);
   T *stage_buf = reinterpret_cast<T *>(dyn_smem);
-  T *sS1 = stage_buf + (size_t)kStages * tile_elems;
-  const size_t s1_bytes = (((size_t)sizeof(T) << tp.s_log2) + 15) & ~(size_t)15;
-  T *sS2 = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sS1) + s1_bytes);
-  const size_t s2_bytes = (((size_t)sizeof(T) << fp.s2_log2) + 15) & ~(size_t)15;
-  unsigned long long *smax =
-      reinterpret_cast<unsigned long long *>(reinterpret_cast<unsigned char *>(sS2) + s2_bytes);
-  unsigned long long *smin = smax + p.mc.Qc;
-  T *sscale1 = reinterpret_cast<T *>(smin + p.mc.Qc);
-  T *sscale2 = sscale1 + p.mc.Qc;
-  const T *A = (const T *)p.A;
-  const T *B1 = (const T *)p.B;
-  const T *B2 = (const T *)fp.S2;
-  T *C = (T *)p.C;
+  unsigned char *s_area = dyn_smem + (size_t)n_stages * tile_bytes;
+  unsigned long long *smax = reinterpret_cast<unsigned long long *>(s_area + cp.s_bytes_off[D]);
+  unsigned long long *smin = smax + cp.mc.Qc;
+  T *sscale = reinterpret_cast<T *>(smin + cp.mc.Qc);  // [D][Qc]
+  const T *P = (const T *)cp.P;
+  T *C = (T *)cp.C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int nthr = kConsumerWarps * 32;
+  // tile i into its stage, issued by the whole producer warp: lane s < D
+  // gathers S_s's per-tile base, lane r < nruns copies run r (one thread's
+  // serial issue of every copy would outlast the consumers' work)
   auto produce = [&](uint32_t i) -> bool {
-    const int st = (int)(i % kStages);
-    if (i >= (uint32_t)kStages && !mbar_wait(&empty[st], ((i / kStages) - 1) & 1)) return false;
-    const uint32_t bw = (blockIdx.x + i * gridDim.x) << tp.tb;
-    uint32_t base = bw, oc = bw, gb = 0, gb2 = 0;
-    for (int j = 0; j < p.n_insA; ++j) base = insert0(base, p.insA[j]);
-    for (int j = 0; j < p.n_insC; ++j) oc = insert0(oc, p.insC[j]);
-    for (int j = 0; j < p.n_seg; ++j)
-      gb |= ((oc >> p.seg_c[j]) & ((1u << p.seg_len[j]) - 1u)) << p.seg_b[j];
-    for (int j = 0; j < fp.n_seg2; ++j)
-      gb2 |= ((oc >> fp.seg2_c[j]) & ((1u << fp.seg2_len[j]) - 1u)) << fp.seg2_b[j];
-    tile_oc[st] = oc;
-    tile_gb[st] = gb;
-    tile_gb2[st] = gb2;
-    fence_proxy_async_smem();
-    mbar_expect_tx(&full[st], tile_bytes);
-    if (tp.debug_stall && i == 0) return true;
-    for (int r = 0; r < tp.nruns; ++r)
-      bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len, A + base + tp.run_off[r],
+    const int st = (int)(i % (uint32_t)n_stages);
+    if (i >= (uint32_t)n_stages &&
+        !__all_sync(0xffffffffu, mbar_wait(&empty[st], ((i / n_stages) - 1) & 1)))
+      return false;
+    const uint32_t w = (blockIdx.x + i * gridDim.x) << cp.tb;
+    uint32_t base = w, oc = w;
+    for (int j = 0; j < cp.n_ins; ++j) base = insert0(base, cp.ins[j]);
+    for (int j = 0; j < cp.n_insc; ++j) oc = insert0(oc, cp.insc[j]);
+    if (lane < D) {
+      uint32_t gb = 0;
+      for (int j = 0; j < cp.n_seg[lane]; ++j)
+        gb |= ((oc >> cp.seg_c[lane][j]) & ((1u << cp.seg_len[lane][j]) - 1u)) << cp.seg_b[lane][j];
+      tile_gb[lane][st] = gb;
+    }
+    if (lane == 0) {
+      tile_oc[st] = oc;
+      mbar_expect_tx(&full[st], tile_bytes);
+    }
+    __syncwarp();
+    if (cp.debug_stall && i == 0) return true;
+    for (int r = lane; r < cp.nruns; r += 32)
+      bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len, P + base + cp.run_off[r],
                run_len * (uint32_t)sizeof(T), &full[st]);
     return true;
   };
-  const bool producer = (warp == kConsumerWarps) && lane == 0;
   uint32_t n_pre = 0;
-  if (producer) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kConsumerWarps);
+  if (warp == NW) {
+    if (lane == 0) {
+      for (int i = 0; i < n_stages; ++i) {
+        mbar_init(&full[i], 1);
+        mbar_init(&empty[i], NW);
+      }
+      mbar_init(&sbar, 1);
+      mbar_fence_init();
+      // the S_i first (every thread waits for them), then the first tiles
+      mbar_expect_tx(&sbar, cp.s_copy_bytes);
+#pragma unroll
+      for (int s = 0; s < D; ++s)
+        bulk_g2s(s_area + cp.s_bytes_off[s], cp.S[s], (uint32_t)sizeof(T) << cp.s_log2[s], &sbar);
     }
-    mbar_fence_init();
-    for (; n_pre < (uint32_t)kStages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
+    __syncwarp();
+    for (; n_pre < (uint32_t)n_stages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
   }
-  // per-lane scales of S1 (times P's when folded) and of S2
-  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
+  // per-lane scales of each S_i (S_1's times P's when folded)
+  for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
     smax[q] = 0;
     smin[q] = kNoMin;
-    T v1 = operand_scale<T>(p.mb, q, p.mc.scale_inputs);
-    if (tp.fold_sa) v1 *= operand_scale<T>(p.ma, q, p.mc.scale_inputs);
-    sscale1[q] = v1;
-    sscale2[q] = operand_scale<T>(fp.m2, q, p.mc.scale_inputs);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      T v = operand_scale<T>(cp.ms[s], q, 1);
+      if (s == 0 && cp.fold_sp) v *= operand_scale<T>(cp.mp, q, 1);
+      sscale[s * cp.mc.Qc + q] = v;
+    }
   }
-  __syncthreads();
-  {
-    const uint32_t n1 = 1u << tp.s_log2, n2 = 1u << fp.s2_log2;
+  __syncthreads();  // barriers initialised, scales written
+  const bool s_landed = __syncthreads_and(mbar_wait(&sbar, 0) ? 1 : 0) != 0;
+  if (s_landed) {
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      T *dst = reinterpret_cast<T *>(s_area + cp.s_bytes_off[s]);
+      const uint32_t n = 1u << cp.s_log2[s];
+      const T *sc = sscale + s * cp.mc.Qc;
+      const uint32_t qm = (uint32_t)cp.ms[s].qmask;
 #pragma unroll 4
-    for (uint32_t j = threadIdx.x; j < n1; j += blockDim.x) sS1[j] = __ldg(B1 + j) * sscale1[j & p.mb.qmask];
-#pragma unroll 4
-    for (uint32_t j = threadIdx.x; j < n2; j += blockDim.x) sS2[j] = __ldg(B2 + j) * sscale2[j & fp.m2.qmask];
+      for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) dst[j] *= sc[j & qm];
+    }
+  } else if (threadIdx.x == 0 && cp.err) {
+    atomicOr(cp.err, 1u);
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
+  if (warp == NW) {
+    uint32_t i = n_pre;
+    bool ok = s_landed;
+    for (; ok && blockIdx.x + i * gridDim.x < n_tiles; ++i)
+      if (!produce(i)) { ok = false; break; }
     if (lane == 0) {
-      uint32_t i = n_pre;
-      bool ok = true;
-      for (; blockIdx.x + i * gridDim.x < n_tiles; ++i)
-        if (!produce(i)) { ok = false; break; }
-      if (!ok && tp.err) atomicOr(tp.err, 1u);
+      if (!ok && cp.err) atomicOr(cp.err, 1u);
+      // drain: copies of the last issued tiles may still be in flight
       const uint32_t n_issued = i;
-      for (uint32_t j = n_issued > (uint32_t)kStages ? n_issued - kStages : 0; j < n_issued; ++j)
-        if (!mbar_wait(&full[j % kStages], (j / kStages) & 1) && tp.err) atomicOr(tp.err, 1u);
+      for (uint32_t j = n_issued > (uint32_t)n_stages ? n_issued - n_stages : 0; j < n_issued; ++j)
+        if (!mbar_wait(&full[j % n_stages], (j / n_stages) & 1) && cp.err) atomicOr(cp.err, 1u);
     }
     __syncwarp();
-  } else {
-    constexpr int J = (V == 1) ? 2 : 1;  // work units per thread per tile (host: T_w = 256*V*J)
+  } else if (s_landed) {
     constexpr uint32_t es = (uint32_t)sizeof(T);
-    const uint32_t stage0 = smem_addr(stage_buf), s10 = smem_addr(sS1), s20 = smem_addr(sS2);
-    uint32_t la4[J], ocl[J], g1l[J], g2l[J];
+    const uint32_t wl = threadIdx.x * V;
+    uint32_t la = wl, ocl = wl;
+    for (int i = 0; i < cp.n_low; ++i) la = insert0(la, cp.low[i]);
+    for (int i = 0; i < cp.n_insc; ++i) ocl = insert0(ocl, cp.insc[i]);
+    uint32_t gl[D];
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const uint32_t wl = (threadIdx.x + (uint32_t)j * nthr) * V;
-      uint32_t a = wl, c = wl, g = 0, g2 = 0;
-      for (int i = 0; i < tp.n_lowA; ++i) a = insert0(a, tp.lowA[i]);
-      for (int i = 0; i < p.n_insC; ++i) c = insert0(c, p.insC[i]);
-      for (int i = 0; i < p.n_seg; ++i)
-        g |= ((c >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
-      for (int i = 0; i < fp.n_seg2; ++i)
-        g2 |= ((c >> fp.seg2_c[i]) & ((1u << fp.seg2_len[i]) - 1u)) << fp.seg2_b[i];
-      la4[j] = a * es; ocl[j] = c; g1l[j] = g * es + s10; g2l[j] = g2 * es + s20;
+    for (int s = 0; s < D; ++s) {
+      uint32_t g = 0;
+      for (int j = 0; j < cp.n_seg[s]; ++j)
+        g |= ((ocl >> cp.seg_c[s][j]) & ((1u << cp.seg_len[s][j]) - 1u)) << cp.seg_b[s][j];
+      gl[s] = g * es + cp.s_bytes_off[s];
     }
-    uint32_t pa[4], d1[8], d2[8];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) pa[x] = fp.pA[x] * es;
-#pragma unroll
-    for (int x = 0; x < 8; ++x) { d1[x] = fp.d1[x] * es; d2[x] = fp.d2[x] * es; }
-    T sa[V];
+    const uint32_t stage0 = smem_addr(dyn_smem) + la * es, s_area0 = smem_addr(s_area);
+    T sp[V];
 #pragma unroll
     for (int e = 0; e < V; ++e)
-      sa[e] = tp.fold_sa ? (T)1 : operand_scale<T>(p.ma, (int)(threadIdx.x * V + e), p.mc.scale_inputs);
-    T tmax[4][V];
-    BT tminm1[4][V];
+      sp[e] = (FAST || cp.fold_sp) ? (T)1 : operand_scale<T>(cp.mp, (int)(wl + e), 1);
+    T tmax[V];
+    BT tminm1[V];
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tminm1[f][e] = (BT)~(BT)0; }
+    for (int e = 0; e < V; ++e) { tmax[e] = (T)0; tminm1[e] = (BT)~(BT)0; }
     for (uint32_t i = 0; blockIdx.x + i * gridDim.x < n_tiles; ++i) {
-      const int st = (int)(i % kStages);
-      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (i / kStages) & 1));
+      const int st = (int)(i % (uint32_t)n_stages);
+      const bool landed = __all_sync(0xffffffffu, mbar_wait(&full[st], (i / n_stages) & 1));
       if (!landed) {
-        if (lane == 0 && tp.err) atomicOr(tp.err, 1u);
+        if (lane == 0 && cp.err) atomicOr(cp.err, 1u);
         break;
       }
-      const uint32_t tile0 = stage0 + (uint32_t)st * tile_bytes;
-      const uint32_t ocb = tile_oc[st], g1b = tile_gb[st] * es, g2b = tile_gb2[st] * es;
+      const uint32_t tile = stage0 + (uint32_t)st * tile_bytes;
+      T *cbase = C + (tile_oc[st] | ocl);
+      uint32_t g[D];
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const uint32_t oc = ocb | ocl[j];
-        const uint32_t g1 = g1b + g1l[j], g2 = g2b + g2l[j];
-        T a[4][V];
+      for (int s = 0; s < D; ++s) g[s] = s_area0 + gl[s] + tile_gb[s][st] * es;
+      T a[1 << NB][V];
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          LdsV<T, V>::ld(tile0 + la4[j] + pa[x], a[x]);
-          if (!tp.fold_sa) {
+      for (int s = 0; s < (1 << D); ++s) {
+        LdsV<T, V>::ld(tile + cp.pA[s], a[s]);
+        if (!FAST) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) a[x][e] *= sa[e];
-          }
+          for (int e = 0; e < V; ++e) a[s][e] *= sp[e];
         }
-        // stage 1: C1 for (x2, y1)
-        T c1[2][2][V];
-#pragma unroll
-        for (int x2 = 0; x2 < 2; ++x2)
-#pragma unroll
-          for (int y1 = 0; y1 < 2; ++y1) {
-#pragma unroll
-            for (int e = 0; e < V; ++e) c1[x2][y1][e] = (T)0;
-#pragma unroll
-            for (int x1 = 0; x1 < 2; ++x1) {
-              T b[V];
-              lds_lanes<T, V>(g1 + d1[x1 + 2 * y1 + 4 * x2], p.b_vec, fp.dv1, b);
-#pragma unroll
-              for (int e = 0; e < V; ++e) c1[x2][y1][e] = fma_t(a[x1 + 2 * x2][e], b[e], c1[x2][y1][e]);
-            }
-          }
-        // stage 2: C2 for (y1, y2)
-        T *cptr = C + oc;
-#pragma unroll
-        for (int y1 = 0; y1 < 2; ++y1)
-#pragma unroll
-          for (int y2 = 0; y2 < 2; ++y2) {
-            T c[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) c[e] = (T)0;
-#pragma unroll
-            for (int x2 = 0; x2 < 2; ++x2) {
-              T b[V];
-              lds_lanes<T, V>(g2 + d2[x2 + 2 * y2 + 4 * y1], fp.b_vec2, fp.dv2, b);
-#pragma unroll
-              for (int e = 0; e < V; ++e) c[e] = fma_t(c1[x2][y1][e], b[e], c[e]);
-            }
-            vstore<T, V>(cptr + fp.dCf[y1 + 2 * y2], c);
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-              tmax[y1 + 2 * y2][e] = fmax(tmax[y1 + 2 * y2][e], fabs(c[e]));
-              const BT bm1 = to_bits(c[e]) - (BT)1;
-              tminm1[y1 + 2 * y2][e] = bm1 < tminm1[y1 + 2 * y2][e] ? bm1 : tminm1[y1 + 2 * y2][e];
-            }
-          }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);
-    }
-    const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
+      if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers
+      ChainSteps<T, V, D, FAST, GROW, SHRINK, 0>::run(cp, g, a);
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+      for (int s = 0; s < (1 << NB); ++s) {
+        if (SHRINK && ((s >> (D - 1)) & 1)) continue;  // summed away
+        vstore<T, V>(cbase + cp.dC[s], a[s]);
 #pragma unroll
-      for (int e = 0; e < V; ++e) {
-        const int q = (int)((ocl[0] + fp.dCf[f] + e) & qmask_c);
-        if (tmax[f][e] != (T)0) atomicMax(smax + q, abs_bits(tmax[f][e]));
-        if (tminm1[f][e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[f][e] + (BT)1));
-      }
-  }
-  __syncthreads();
-  // C2's exponent: P, S1 and S2 (C1 is never rescaled); flush test over the
-  // three operands' smallest nonzero scaled entries
-  if (blockIdx.x == 0) {
-    for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
-      const int qa = q & p.ma.qmask, qb = q & p.mb.qmask, q2 = q & fp.m2.qmask;
-      if (p.mc.exp)
-        p.mc.exp[q] = p.ma.exp[qa] + pow2_exp_of(p.ma.maxb[qa], T()) + p.mb.exp[qb] +
-                      pow2_exp_of(p.mb.maxb[qb], T()) + fp.m2.exp[q2] + pow2_exp_of(fp.m2.maxb[q2], T());
-      if (p.mc.flags && p.ma.minb[qa] != kNoMin && p.mb.minb[qb] != kNoMin && fp.m2.minb[q2] != kNoMin) {
-        const T lo = (from_bits<T>(p.ma.minb[qa]) * operand_scale<T>(p.ma, qa, 1)) *
-                     (from_bits<T>(p.mb.minb[qb]) * operand_scale<T>(p.mb, qb, 1)) *
-                     (from_bits<T>(fp.m2.minb[q2]) * operand_scale<T>(fp.m2, q2, 1));
-        if (below_normal(lo)) {
-          if (p.mc.Qc > 1) atomicOr(p.mc.flags + q, 2u);
-          else
-            for (int qq = 0; qq < p.mc.Q; ++qq) atomicOr(p.mc.flags + qq, 2u);
+        for (int e = 0; e < V; ++e) {
+          tmax[e] = fmax(tmax[e], fabs(a[s][e]));
+          tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
         }
       }
     }
+    const uint32_t qmask_c = (uint32_t)(cp.mc.Qc - 1);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int q = (int)((ocl + e) & qmask_c);
+      if (tmax[e] != (T)0) atomicMax(smax + q, abs_bits(tmax[e]));
+      if (tminm1[e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[e] + (BT)1));
+    }
   }
-  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) {
-    if (p.mc.maxb && smax[q]) atomicMax(p.mc.maxb + q, smax[q]);
-    if (p.mc.minb && smin[q] != kNoMin) atomicMin(p.mc.minb + q, smin[q]);
+  __syncthreads();
+  // C_D's exponent: P and every S_i (the intermediates are never
+  // rescaled); flush test over the smallest nonzero scaled entries of all
+  // D + 1 operands (a lower bound on every product the chain forms)
+  if (blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+      const int qp = q & cp.mp.qmask;
+      int64_t e = cp.mp.exp[qp] + pow2_exp_of(cp.mp.maxb[qp], T());
+      bool any_zero = cp.mp.minb[qp] == kNoMin;
+      T lo = any_zero ? (T)0 : from_bits<T>(cp.mp.minb[qp]) * operand_scale<T>(cp.mp, qp, 1);
+#pragma unroll
+      for (int s = 0; s < D; ++s) {
+        const int qs = q & cp.ms[s].qmask;
+        e += cp.ms[s].exp[qs] + pow2_exp_of(cp.ms[s].maxb[qs], T());
+        if (cp.ms[s].minb[qs] == kNoMin) any_zero = true;
+        else lo *= from_bits<T>(cp.ms[s].minb[qs]) * operand_scale<T>(cp.ms[s], qs, 1);
+      }
+      cp.mc.exp[q] = e;
+      if (cp.mc.flags && !any_zero && below_normal(lo)) {
+        if (cp.mc.Qc > 1) atomicOr(cp.mc.flags + q, 2u);
+        else
+          for (int qq = 0; qq < cp.mc.Q; ++qq) atomicOr(cp.mc.flags + qq, 2u);
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+    if (smax[q]) atomicMax(cp.mc.maxb + q, smax[q]);
+    if (smin[q] != kNoMin) atomicMin(cp.mc.minb + q, smin[q]);
   }
 }
 

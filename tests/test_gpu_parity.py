@@ -415,30 +415,35 @@ def test_uneven_batch_admission(w):
     assert len(batch.execute()) == 4
 
 
-@pytest.mark.parametrize("precision", [FP32])
-def test_fused_pairs_match_unfused(w, precision):
-    """Two consecutive frontier eliminations in one pass give the same
-    values as two passes (the intermediate's pow2 scale only moves into the
-    exponent), and match the oracle; the fused plan moves far fewer bytes."""
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_fused_chains_match_unfused(w, precision):
+    """Consecutive frontier eliminations contracted in one pass (pairs by
+    k2_fused, chains of 2..4 by k2_chain) give the same values as one pass
+    per elimination (the intermediates' pow2 scales only move into the
+    exponent), and match the oracle; longer chains move fewer bytes."""
     H, W_ = 16, 100
     cnf = wmcgen.grid_cnf(H, W_, 1)
     Q = 64
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=12, lo=0.05, hi=0.95)
+    res, nbytes = {}, {}
     try:
-        w.wmc_set_fusion(0)
-        plain = plan_for(w, cnf, None, None, precision)
-        a = plain.execute(wq, wnq)
-        bytes_plain = plain.info(Q).algorithmic_bytes
+        for level in (0, 1, 2, 3, 4):
+            w.wmc_set_fusion(level)
+            plan = plan_for(w, cnf, None, None, precision)
+            res[level] = plan.execute(wq, wnq)
+            nbytes[level] = plan.info(Q).algorithmic_bytes
     finally:
-        w.wmc_set_fusion(1)
-    fused = plan_for(w, cnf, None, None, precision)
-    b = fused.execute(wq, wnq)
-    assert fused.info(Q).algorithmic_bytes < 0.7 * bytes_plain
-    for q in range(Q):
-        assert (a[q].mant, a[q].exp2) == (b[q].mant, b[q].exp2), q
+        w.wmc_set_fusion(4)
+    assert nbytes[4] < 0.7 * nbytes[0]
+    assert nbytes[4] < nbytes[2] <= nbytes[0]
+    a = res[0]
+    for level in (1, 2, 3, 4):
+        b = res[level]
+        for q in range(Q):
+            assert (a[q].mant, a[q].exp2) == (b[q].mant, b[q].exp2), (level, q)
     col = wmcgen.grid_column_order(H, W_)
     for q in (0, 33):
-        assert rel(b[q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[precision]
+        assert rel(res[4][q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[precision]
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
