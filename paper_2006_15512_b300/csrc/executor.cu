@@ -525,9 +525,13 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
     cp.s_log2[i] = (int)S.size();
   }
   if (!fast && (grow || shrink)) return false;  // growth and shrink steps: FAST variants only
-  // tiling of P over its kept indices
+  // tiling of P over its kept indices: 2 work units per thread when 16
+  // chain states would leave runs of only 2 KB (bulk copies that short
+  // lower the read rate)
+  cp.units = (D == 4 && !f64) ? 2 : 1;
   int tb = 0;
-  while ((1 << tb) < nthr * V) ++tb;
+  while ((1 << tb) < nthr * V * cp.units) ++tb;
+  if (cp.units == 2 && cp.log2_nu + vbits < tb + 3) { cp.units = 1; --tb; }
   if (cp.log2_nu + vbits < tb + 3) return false;
   std::vector<int> kept;
   for (int q = 0; q < rP; ++q)

@@ -787,6 +787,7 @@ struct K2CParams {
   uint32_t dC[2 << kMaxChain];    // C element offset of final state s
   uint32_t *err;
   int32_t debug_stall;
+  int32_t units;                  // work units per consumer thread per tile (1, 2)
 };
 
 __host__ __device__ constexpr uint32_t pdep_c(uint32_t t, uint32_t mask) {
@@ -1060,23 +1061,31 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
     __syncwarp();
   } else if (s_landed) {
     constexpr uint32_t es = (uint32_t)sizeof(T);
-    const uint32_t wl = threadIdx.x * V;
-    uint32_t la = wl, ocl = wl;
-    for (int i = 0; i < cp.n_low; ++i) la = insert0(la, cp.low[i]);
-    for (int i = 0; i < cp.n_insc; ++i) ocl = insert0(ocl, cp.insc[i]);
-    uint32_t gl[D];
+    // J work units per thread per tile (J = 2 doubles the tile, and so the
+    // length of its contiguous runs, without more registers)
+    const int J = cp.units;
+    uint32_t la_[2], ocl_[2], gl_[2][D];
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t wl = (threadIdx.x + (uint32_t)j * NW * 32) * V;
+      uint32_t la = wl, ocl = wl;
+      for (int i = 0; i < cp.n_low; ++i) la = insert0(la, cp.low[i]);
+      for (int i = 0; i < cp.n_insc; ++i) ocl = insert0(ocl, cp.insc[i]);
+      la_[j] = la * es;
+      ocl_[j] = ocl;
 #pragma unroll
-    for (int s = 0; s < D; ++s) {
-      uint32_t g = 0;
-      for (int j = 0; j < cp.n_seg[s]; ++j)
-        g |= ((ocl >> cp.seg_c[s][j]) & ((1u << cp.seg_len[s][j]) - 1u)) << cp.seg_b[s][j];
-      gl[s] = g * es + cp.s_bytes_off[s];
+      for (int s = 0; s < D; ++s) {
+        uint32_t g = 0;
+        for (int jj = 0; jj < cp.n_seg[s]; ++jj)
+          g |= ((ocl >> cp.seg_c[s][jj]) & ((1u << cp.seg_len[s][jj]) - 1u)) << cp.seg_b[s][jj];
+        gl_[j][s] = g * es + cp.s_bytes_off[s];
+      }
     }
-    const uint32_t stage0 = smem_addr(dyn_smem) + la * es, s_area0 = smem_addr(s_area);
+    const uint32_t wl0 = threadIdx.x * V, ocl = ocl_[0];
+    const uint32_t stage0 = smem_addr(dyn_smem), s_area0 = smem_addr(s_area);
     T sp[V];
 #pragma unroll
     for (int e = 0; e < V; ++e)
-      sp[e] = (FAST || cp.fold_sp) ? (T)1 : operand_scale<T>(cp.mp, (int)(wl + e), 1);
+      sp[e] = (FAST || cp.fold_sp) ? (T)1 : operand_scale<T>(cp.mp, (int)(wl0 + e), 1);
     T tmax[V];
     BT tminm1[V];
 #pragma unroll
@@ -1088,31 +1097,35 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
         if (lane == 0 && cp.err) atomicOr(cp.err, 1u);
         break;
       }
-      const uint32_t tile = stage0 + (uint32_t)st * tile_bytes;
-      T *cbase = C + (tile_oc[st] | ocl);
-      uint32_t g[D];
+      for (int j = 0; j < J; ++j) {
+        const uint32_t tile = stage0 + (uint32_t)st * tile_bytes + la_[j];
+        T *cbase = C + (tile_oc[st] | ocl_[j]);
+        uint32_t g[D];
 #pragma unroll
-      for (int s = 0; s < D; ++s) g[s] = s_area0 + gl[s] + tile_gb[s][st] * es;
-      T a[1 << NB][V];
+        for (int s = 0; s < D; ++s) g[s] = s_area0 + gl_[j][s] + tile_gb[s][st] * es;
+        T a[1 << NB][V];
 #pragma unroll
-      for (int s = 0; s < (1 << D); ++s) {
-        LdsV<T, V>::ld(tile + cp.pA[s], a[s]);
-        if (!FAST) {
+        for (int s = 0; s < (1 << D); ++s) {
+          LdsV<T, V>::ld(tile + cp.pA[s], a[s]);
+          if (!FAST) {
 #pragma unroll
-          for (int e = 0; e < V; ++e) a[s][e] *= sp[e];
+            for (int e = 0; e < V; ++e) a[s][e] *= sp[e];
+          }
         }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers
-      ChainSteps<T, V, D, FAST, GROW, SHRINK, 0>::run(cp, g, a);
+        if (j == J - 1) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers
+        }
+        ChainSteps<T, V, D, FAST, GROW, SHRINK, 0>::run(cp, g, a);
 #pragma unroll
-      for (int s = 0; s < (1 << NB); ++s) {
-        if (SHRINK && ((s >> (D - 1)) & 1)) continue;  // summed away
-        vstore<T, V>(cbase + cp.dC[s], a[s]);
+        for (int s = 0; s < (1 << NB); ++s) {
+          if (SHRINK && ((s >> (D - 1)) & 1)) continue;  // summed away
+          vstore<T, V>(cbase + cp.dC[s], a[s]);
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-          tmax[e] = fmax(tmax[e], fabs(a[s][e]));
-          tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
+          for (int e = 0; e < V; ++e) {
+            tmax[e] = fmax(tmax[e], fabs(a[s][e]));
+            tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
+          }
         }
       }
     }
