@@ -337,6 +337,10 @@ void wmc_set_fusion(int32_t on);
  * terms) runs inside one persistent launch at the start of the walk
  * instead of a launch per node.  Affects plans laid out after the call. */
 void wmc_set_small_phase(int32_t on);
+/* Execution option (default on): chain kernels are launched as programmatic
+ * dependent launches, so that each one's set-up overlaps the tail of the
+ * launch before it.  Affects graphs captured after the call. */
+void wmc_set_dependent_launch(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,

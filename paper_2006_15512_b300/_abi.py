@@ -132,6 +132,7 @@ EXPORTS = {
     "wmc_debug_check_bounds": (c_i32, [c_vp, c_i32, P(c_i64)]),
     "wmc_set_fusion": (None, [c_i32]),
     "wmc_set_small_phase": (None, [c_i32]),
+    "wmc_set_dependent_launch": (None, [c_i32]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

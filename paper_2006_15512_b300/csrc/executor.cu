@@ -37,12 +37,14 @@ static std::atomic<int32_t> g_debug_stall{0};
 // chains of up to this many (0 or 1: off)
 static std::atomic<int32_t> g_fuse{4};
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
+static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
 extern "C" void wmc_debug_stall_copies(int32_t on) { g_debug_stall.store(on); }
 extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
 extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
+extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -1122,7 +1124,20 @@ static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t sm
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  dev::k2_chain<T, V, D, FAST, GROW, SHRINK><<<(unsigned)blocks, dev::kChainNW * 32 + 32, smem, s>>>(p);
+  // programmatic dependent launch: the kernel's barrier set-up and S_i
+  // copies overlap the previous launch's tail (it waits for that launch
+  // before touching anything it wrote)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(dev::kChainNW * 32 + 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, dev::k2_chain<T, V, D, FAST, GROW, SHRINK>, p);
 }
 
 // vector lanes: FAST plain chains, growth-first and shrink-last variants

@@ -431,6 +431,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Programmatic dependent launch: wait until the grids this launch depends
+// on have completed and their memory is visible (no-op without the launch
+// attribute), and allow the next launch to start its independent part.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -955,9 +962,6 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
   __shared__ __align__(8) unsigned long long full[kMaxStagesC], empty[kMaxStagesC], sbar;
   __shared__ uint32_t tile_oc[kMaxStagesC], tile_gb[kMaxChain][kMaxStagesC];
   __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
-  __syncthreads();
-  if (s_skip) return;  // an earlier launch of this walk gave up: skip the work
   const int n_stages = cp.n_stages;
   const uint32_t run_len = 1u << cp.run_log2;
   const uint32_t tile_elems = (uint32_t)cp.nruns * run_len;
@@ -971,22 +975,51 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
   const T *P = (const T *)cp.P;
   T *C = (T *)cp.C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // tile i into its stage, issued by the whole producer warp: lane s < D
-  // gathers S_s's per-tile base, lane r < nruns copies run r (one thread's
-  // serial issue of every copy would outlast the consumers' work)
+  // Producer state, per lane, set up once: tile offsets advance by a masked
+  // add (the tile index's bits are deposited around the chain positions:
+  // adding the deposited grid stride with the chain bits held at 1 carries
+  // across them); lane r < nruns keeps run r's offsets, lane s < D the
+  // segments that gather S_s's per-tile base (no indexed parameter loads
+  // and no loops over them inside the tile loop).
+  uint32_t p_base = 0, p_oc = 0, p_dstride = 0, p_cstride = 0, p_pmask = 0, p_cmask = 0;
+  uint32_t p_run_src = 0, p_run_dst = 0;
+  uint32_t g_c[8], g_b[8], g_m[8];
+  int g_n = 0;
+  if (warp == NW) {
+    for (int j = 0; j < cp.n_ins; ++j) p_pmask |= 1u << cp.ins[j];
+    for (int j = 0; j < cp.n_insc; ++j) p_cmask |= 1u << cp.insc[j];
+    uint32_t b0 = blockIdx.x << cp.tb, c0 = b0, sd = gridDim.x << cp.tb, sc = sd;
+    for (int j = 0; j < cp.n_ins; ++j) { b0 = insert0(b0, cp.ins[j]); sd = insert0(sd, cp.ins[j]); }
+    for (int j = 0; j < cp.n_insc; ++j) { c0 = insert0(c0, cp.insc[j]); sc = insert0(sc, cp.insc[j]); }
+    p_base = b0; p_oc = c0; p_dstride = sd; p_cstride = sc;
+    if (lane < cp.nruns) {
+      p_run_src = cp.run_off[lane];
+      p_run_dst = (uint32_t)lane * run_len;
+    }
+    if (lane < D) {
+      g_n = cp.n_seg[lane];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        g_c[j] = j < g_n ? (uint32_t)cp.seg_c[lane][j] : 0u;
+        g_b[j] = j < g_n ? (uint32_t)cp.seg_b[lane][j] : 0u;
+        g_m[j] = j < g_n ? (1u << cp.seg_len[lane][j]) - 1u : 0u;
+      }
+    }
+  }
+  // tile i into its stage (tiles are produced in order, each call advances
+  // the offsets by one grid stride)
   auto produce = [&](uint32_t i) -> bool {
     const int st = (int)(i % (uint32_t)n_stages);
     if (i >= (uint32_t)n_stages &&
         !__all_sync(0xffffffffu, mbar_wait(&empty[st], ((i / n_stages) - 1) & 1)))
       return false;
-    const uint32_t w = (blockIdx.x + i * gridDim.x) << cp.tb;
-    uint32_t base = w, oc = w;
-    for (int j = 0; j < cp.n_ins; ++j) base = insert0(base, cp.ins[j]);
-    for (int j = 0; j < cp.n_insc; ++j) oc = insert0(oc, cp.insc[j]);
+    const uint32_t base = p_base, oc = p_oc;
+    p_base = ((p_base | p_pmask) + p_dstride) & ~p_pmask;
+    p_oc = ((p_oc | p_cmask) + p_cstride) & ~p_cmask;
     if (lane < D) {
       uint32_t gb = 0;
-      for (int j = 0; j < cp.n_seg[lane]; ++j)
-        gb |= ((oc >> cp.seg_c[lane][j]) & ((1u << cp.seg_len[lane][j]) - 1u)) << cp.seg_b[lane][j];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) gb |= ((oc >> g_c[j]) & g_m[j]) << g_b[j];
       tile_gb[lane][st] = gb;
     }
     if (lane == 0) {
@@ -995,29 +1028,39 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
     }
     __syncwarp();
     if (cp.debug_stall && i == 0) return true;
-    for (int r = lane; r < cp.nruns; r += 32)
-      bulk_g2s(stage_buf + (size_t)st * tile_elems + (size_t)r * run_len, P + base + cp.run_off[r],
+    if (lane < cp.nruns)
+      bulk_g2s(stage_buf + (size_t)st * tile_elems + p_run_dst, P + base + p_run_src,
                run_len * (uint32_t)sizeof(T), &full[st]);
     return true;
   };
-  uint32_t n_pre = 0;
-  if (warp == NW) {
-    if (lane == 0) {
-      for (int i = 0; i < n_stages; ++i) {
-        mbar_init(&full[i], 1);
-        mbar_init(&empty[i], NW);
-      }
-      mbar_init(&sbar, 1);
-      mbar_fence_init();
-      // the S_i first (every thread waits for them), then the first tiles
-      mbar_expect_tx(&sbar, cp.s_copy_bytes);
-#pragma unroll
-      for (int s = 0; s < D; ++s)
-        bulk_g2s(s_area + cp.s_bytes_off[s], cp.S[s], (uint32_t)sizeof(T) << cp.s_log2[s], &sbar);
+  // Part 1, independent of the previous launch of the walk (with
+  // programmatic dependent launch it overlaps that launch's tail): the
+  // barriers and the S_i copies (the S_i and their metadata come from
+  // launches that completed before the previous one began).
+  if (warp == NW && lane == 0) {
+    for (int i = 0; i < n_stages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NW);
     }
-    __syncwarp();
-    for (; n_pre < (uint32_t)n_stages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
+    mbar_init(&sbar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(&sbar, cp.s_copy_bytes);
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+      bulk_g2s(s_area + cp.s_bytes_off[s], cp.S[s], (uint32_t)sizeof(T) << cp.s_log2[s], &sbar);
   }
+  // Part 2: P, P's metadata and the error word are the previous launch's
+  grid_dependency_wait();
+  if (threadIdx.x == 0) s_skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) {  // an earlier launch of this walk gave up: skip the work
+    if (threadIdx.x == 0) mbar_wait(&sbar, 0);  // (the S_i copies land first)
+    __syncthreads();
+    return;
+  }
+  uint32_t n_pre = 0;
+  if (warp == NW)
+    for (; n_pre < (uint32_t)n_stages && blockIdx.x + n_pre * gridDim.x < n_tiles; ++n_pre) produce(n_pre);
   // per-lane scales of each S_i (S_1's times P's when folded)
   for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
     smax[q] = 0;
@@ -1064,23 +1107,27 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
     // J work units per thread per tile (J = 2 doubles the tile, and so the
     // length of its contiguous runs, without more registers)
     const int J = cp.units;
-    uint32_t la_[2], ocl_[2], gl_[2][D];
+    // per-unit offsets of unit 0 and unit 1, kept in named registers and
+    // selected per unit (an array indexed by the runtime unit would live
+    // in local memory)
+    uint32_t la_0 = 0, la_1 = 0, ocl_0 = 0, ocl_1 = 0, gl_0[D], gl_1[D];
+#pragma unroll
     for (int j = 0; j < 2; ++j) {
       const uint32_t wl = (threadIdx.x + (uint32_t)j * NW * 32) * V;
       uint32_t la = wl, ocl = wl;
       for (int i = 0; i < cp.n_low; ++i) la = insert0(la, cp.low[i]);
       for (int i = 0; i < cp.n_insc; ++i) ocl = insert0(ocl, cp.insc[i]);
-      la_[j] = la * es;
-      ocl_[j] = ocl;
+      (j ? la_1 : la_0) = la * es;
+      (j ? ocl_1 : ocl_0) = ocl;
 #pragma unroll
       for (int s = 0; s < D; ++s) {
         uint32_t g = 0;
         for (int jj = 0; jj < cp.n_seg[s]; ++jj)
           g |= ((ocl >> cp.seg_c[s][jj]) & ((1u << cp.seg_len[s][jj]) - 1u)) << cp.seg_b[s][jj];
-        gl_[j][s] = g * es + cp.s_bytes_off[s];
+        (j ? gl_1[s] : gl_0[s]) = g * es + cp.s_bytes_off[s];
       }
     }
-    const uint32_t wl0 = threadIdx.x * V, ocl = ocl_[0];
+    const uint32_t wl0 = threadIdx.x * V, ocl = ocl_0;
     const uint32_t stage0 = smem_addr(dyn_smem), s_area0 = smem_addr(s_area);
     T sp[V];
 #pragma unroll
@@ -1098,11 +1145,11 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
         break;
       }
       for (int j = 0; j < J; ++j) {
-        const uint32_t tile = stage0 + (uint32_t)st * tile_bytes + la_[j];
-        T *cbase = C + (tile_oc[st] | ocl_[j]);
+        const uint32_t tile = stage0 + (uint32_t)st * tile_bytes + (j ? la_1 : la_0);
+        T *cbase = C + (tile_oc[st] | (j ? ocl_1 : ocl_0));
         uint32_t g[D];
 #pragma unroll
-        for (int s = 0; s < D; ++s) g[s] = s_area0 + gl_[j][s] + tile_gb[s][st] * es;
+        for (int s = 0; s < D; ++s) g[s] = s_area0 + (j ? gl_1[s] : gl_0[s]) + tile_gb[s][st] * es;
         T a[1 << NB][V];
 #pragma unroll
         for (int s = 0; s < (1 << D); ++s) {
@@ -1138,6 +1185,7 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
     }
   }
   __syncthreads();
+  grid_dependents_launch();  // this block's tiles are done: the next launch may start
   // C_D's exponent: P and every S_i (the intermediates are never
   // rescaled); flush test over the smallest nonzero scaled entries of all
   // D + 1 operands (a lower bound on every product the chain forms)
