@@ -82,12 +82,12 @@ def workload():
     return cnf, wq, wnq
 
 
-def config(Q):
+def config(Q, slots=1):
     return {"workload": f"serving: {GRID_H}x{GRID_W} grid CNF (seed {GRID_SEED}), pool of {POOL} "
                         f"weight-vector queries w~U(0.05,0.95), waves of Q={Q}",
-            "Q": Q, "precision": "scaled fp32 (fp64 root)",
-            "l2": "inputs larger than L2: each wave streams 2^17 x Q float32 frontier tensors "
-                  "(128 MiB at Q=256) through ~1.5k contractions"}
+            "Q": Q, "precision": "scaled fp32 (fp64 root)", "waves_in_flight": slots,
+            "l2": "inputs larger than L2: each wave streams 2^16-2^17 x Q float32 frontier tensors "
+                  "(64-128 MiB at Q=256) through ~400 launches"}
 
 
 class Clocks:
@@ -203,15 +203,23 @@ def run_ours(args, rank, world):
     # device-resident query pool and outputs
     d_wp = torch.from_numpy(wq).to(dev)
     d_wn = torch.from_numpy(wnq).to(dev)
-    ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev)
-    mant = torch.empty(Q, dtype=torch.float64, device=dev)
-    ex = torch.empty(Q, dtype=torch.int64, device=dev)
-    fl = torch.empty(Q, dtype=torch.int32, device=dev)
+    # wave slots: each wave in flight has its own stream, workspace and
+    # outputs; consecutive waves alternate between the slots, so one wave's
+    # launches overlap the other's (continuous batching)
+    n_slots = max(1, args.slots)
+    slot_streams = [torch.cuda.Stream(device=dev) for _ in range(n_slots)]
+    slot_ws = [torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev) for _ in range(n_slots)]
+    slot_out = [(torch.empty(Q, dtype=torch.float64, device=dev), torch.empty(Q, dtype=torch.int64, device=dev),
+                 torch.empty(Q, dtype=torch.int32, device=dev)) for _ in range(n_slots)]
+    ws, (mant, ex, fl) = slot_ws[0], slot_out[0]
     n_waves = POOL // Q
 
     def wave(i):
         off = wave_offset(i, rank, world, n_waves, Q)
-        plan.execute_device(Q, d_wp[off:off + Q], d_wn[off:off + Q], ws, mant, ex, fl, stream=sp)
+        k = i % n_slots
+        m, e, f = slot_out[k]
+        plan.execute_device(Q, d_wp[off:off + Q], d_wn[off:off + Q], slot_ws[k], m, e, f,
+                            stream=slot_streams[k].cuda_stream)
 
     for i in range(args.warmup):
         wave(i)
@@ -224,8 +232,12 @@ def run_ours(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(dev.index) as clk:
         ev0.record(stream)
+        for st_ in slot_streams:
+            st_.wait_event(ev0)
         for i in range(args.steps):
             wave(args.warmup + i)
+        for st_ in slot_streams:
+            stream.wait_stream(st_)
         ev1.record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -239,19 +251,35 @@ def run_ours(args, rank, world):
     t_max = max_over_ranks(ms, dist, dev)
     value = world * args.steps * Q / (t_max / 1e3)
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the public serving API with host buffers: the
+    # queries of `steps` waves submitted at once (wmc_submit), results
+    # collected (wmc_wait); the server copies each wave's weights in from
+    # pinned staging and its results back, with n_slots waves in flight
     host_wp, host_wn = np.ascontiguousarray(wq), np.ascontiguousarray(wnq)
-    plan.execute(host_wp[:Q], host_wn[:Q])  # warm the host-path workspace
+    srv = w.Server(plan, max_batch=Q, max_waves=n_slots)
+    for t in [srv.submit(host_wp[j], host_wn[j]) for j in range(Q * n_slots)]:
+        srv.wait(t)  # warm the server's graphs
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    e2e_res = []
+    tickets = []
     for i in range(args.steps):
         off = wave_offset(args.warmup + i, rank, world, n_waves, Q)
-        e2e_res = plan.execute(host_wp[off:off + Q], host_wn[off:off + Q])
+        tickets += [srv.submit(host_wp[off + j], host_wn[off + j]) for j in range(Q)]
+    e2e_res = [srv.wait(t) for t in tickets]
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    srv.close()
     e2e = {"value": world * args.steps * Q / e2e_s, "unit": "queries/s",
-           "h2d_bytes_per_step": 2 * Q * n * 8, "d2h_bytes_per_step": Q * (8 + 8 + 4)}
+           "h2d_bytes_per_step": 2 * Q * n * 8, "d2h_bytes_per_step": Q * (8 + 8 + 4),
+           "api": "wmc_submit / wmc_wait, all queries submitted at once"}
+    # the synchronous one-wave call (wmc_execute), for comparison
+    plan.execute(host_wp[:Q], host_wn[:Q])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        off = wave_offset(args.warmup + i, rank, world, n_waves, Q)
+        plan.execute(host_wp[off:off + Q], host_wn[off:off + Q])
+    sync_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_sync = {"value": world * args.steps * Q / sync_s, "unit": "queries/s", "api": "wmc_execute, one wave per call"}
 
     if rank != 0:
         return
@@ -355,7 +383,7 @@ def run_ours(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config(Q), "e2e": e2e,
+            "data": "synthetic", "config": config(Q, n_slots), "e2e": e2e, "e2e_sync": e2e_sync,
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "plain_fp64": {"value": plain_qps, "unit": "queries/s", "queries": n_plain,
@@ -505,6 +533,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--Q", type=int, default=256)
+    ap.add_argument("--slots", type=int, default=2, help="waves in flight (streams + workspaces)")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--n-queries", type=int, default=4096)
     ap.add_argument("--waves", type=int, default=2)
