@@ -293,6 +293,11 @@ int wmc_server_create(wmc_plan_t *plan, const wmc_server_opts *opts,
 /* Copies n_vars weights each (host); returns a ticket (never reused). */
 int wmc_submit(wmc_server_t *srv, const double *w_pos, const double *w_neg,
                uint64_t *ticket);
+/* n queries at once: w_pos / w_neg are [n][n_vars] (host, row-major);
+ * tickets[n] receives consecutive tickets.  One lock for the whole batch,
+ * so a client with many queries in hand does not pay a call per query. */
+int wmc_submit_many(wmc_server_t *srv, int64_t n, const double *w_pos,
+                    const double *w_neg, uint64_t *tickets);
 /* WMC_OK (result written, ticket retired), WMC_PENDING, or an error. */
 int wmc_poll(wmc_server_t *srv, uint64_t ticket, wmc_result *out);
 /* As wmc_poll; *done_ns (may be NULL) receives the CLOCK_MONOTONIC time in

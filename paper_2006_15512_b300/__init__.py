@@ -266,6 +266,18 @@ class Server:
                              ctypes.byref(t)), "wmc_submit")
         return int(t.value)
 
+    def submit_many(self, w_pos, w_neg):
+        """Queries as rows of [n][n_vars] arrays; returns their tickets."""
+        wp = np.ascontiguousarray(w_pos, dtype=np.float64)
+        wn = np.ascontiguousarray(w_neg, dtype=np.float64)
+        n = int(wp.shape[0])
+        if wp.shape != wn.shape or (self.n_vars and wp.shape[1] != self.n_vars):
+            raise ValueError("w_pos, w_neg must both be [n][n_vars]")
+        t = np.zeros(n, dtype=np.uint64)
+        check(lib.wmc_submit_many(self.handle, ctypes.c_int64(n), _ptr(wp, ctypes.c_double),
+                                  _ptr(wn, ctypes.c_double), _ptr(t, ctypes.c_uint64)), "wmc_submit_many")
+        return [int(x) for x in t]
+
     def poll(self, ticket: int) -> Optional[Result]:
         r = _abi.wmc_result()
         rc = check(lib.wmc_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r)), "wmc_poll")

@@ -118,6 +118,7 @@ EXPORTS = {
     "wmc_batch_destroy": (None, [c_vp]),
     "wmc_server_create": (c_i32, [c_vp, P(wmc_server_opts), P(c_vp)]),
     "wmc_submit": (c_i32, [c_vp, P(c_dbl), P(c_dbl), P(c_u64)]),
+    "wmc_submit_many": (c_i32, [c_vp, c_i64, P(c_dbl), P(c_dbl), P(c_u64)]),
     "wmc_poll": (c_i32, [c_vp, c_u64, P(wmc_result)]),
     "wmc_wait": (c_i32, [c_vp, c_u64, c_i64, P(wmc_result)]),
     "wmc_poll_ex": (c_i32, [c_vp, c_u64, P(wmc_result), P(c_i64)]),

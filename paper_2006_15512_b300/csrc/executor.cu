@@ -1670,6 +1670,13 @@ int exec_state(Plan &plan, int32_t Q, ExecState **out) {
   return get_state(plan, Q, out);
 }
 int64_t exec_ws_bytes(const ExecState *st) { return st->ws_bytes; }
+int exec_prepare(Plan &plan, ExecState *st, void *ws) {
+  int rc = ensure_dev(*st);
+  if (rc) return rc;
+  cudaGraphExec_t ge = nullptr;
+  std::lock_guard<std::mutex> lk(st->graph_mu);
+  return get_graph(plan, *st, (char *)ws, &ge);
+}
 int exec_run_device(Plan &plan, ExecState *st, const double *d_w_pos, const double *d_w_neg,
                     void *ws, double *d_mant, int64_t *d_exp2, uint32_t *d_flags, void *stream) {
   return run_device(plan, *st, d_w_pos, d_w_neg, (char *)ws, d_mant, d_exp2, d_flags,

@@ -88,6 +88,9 @@ int64_t plan_workspace_bytes(Plan &plan, int32_t Q, int64_t *arena_bytes);
 void destroy_exec_state(ExecState *st);
 // Lays out (once) and returns the execution state of batch size Q.
 int exec_state(Plan &plan, int32_t Q, ExecState **out);
+// Lays out the device tables and captures the walk's graph for workspace
+// `ws` without running it (the first wave of that size then starts at once).
+int exec_prepare(Plan &plan, ExecState *st, void *ws);
 int64_t exec_ws_bytes(const ExecState *st);
 // Enqueues one walk on `stream` (device pointers; weights [Q][n_vars]).
 int exec_run_device(Plan &plan, ExecState *st, const double *d_w_pos, const double *d_w_neg,

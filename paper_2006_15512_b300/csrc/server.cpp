@@ -71,6 +71,7 @@ struct wmc_server {
   Plan *plan = nullptr;
   wmc_server_opts opts{};
   int32_t n_vars = 0;
+  int64_t ws_bytes = 0;              // each slot's workspace
   std::vector<Slot> slots;
   std::mutex mu;
   std::condition_variable cv_work;   // batcher: queue or slot changes
@@ -113,6 +114,11 @@ static int launch_wave(wmc_server *srv, int si) {
   ExecState *st = nullptr;
   int rc = exec_state(*srv->plan, Q, &st);
   if (rc) return rc;
+  if (exec_ws_bytes(st) > srv->ws_bytes) {
+    set_error("wave of %d needs %lld workspace bytes, slots hold %lld", Q, (long long)exec_ws_bytes(st),
+              (long long)srv->ws_bytes);
+    return WMC_EPLAN_TOO_BIG;
+  }
   if (nv && cudaMemcpyAsync(sl.d_w, sl.h_w, sizeof(double) * 2 * (size_t)Q * nv,
                             cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
     return WMC_ECUDA;
@@ -263,6 +269,7 @@ extern "C" int wmc_server_create(wmc_plan_t *cplan, const wmc_server_opts *opts,
   if (!srv) { set_error("out of host memory"); return WMC_ENOMEM; }
   srv->plan = &plan;
   srv->opts = o;
+  srv->ws_bytes = ws;
   srv->n_vars = plan.n_vars;
   srv->slots.resize((size_t)n_slots);
   const size_t nv = std::max<size_t>((size_t)plan.n_vars, 1);
@@ -286,6 +293,18 @@ extern "C" int wmc_server_create(wmc_plan_t *cplan, const wmc_server_opts *opts,
       return WMC_ENOMEM;
     }
   }
+  // capture every slot's graph for every wave size (powers of two up to
+  // max_batch) now, so that no wave waits for a capture later; sizes whose
+  // workspace exceeds the slots' are left to fail at their first wave
+  for (int32_t Q = 1; Q <= o.max_batch; Q <<= 1) {
+    ExecState *st = nullptr;
+    if (exec_state(plan, Q, &st)) break;
+    if (exec_ws_bytes(st) > ws) continue;
+    for (auto &s : srv->slots)
+      if (exec_prepare(plan, st, s.ws)) break;
+    if (Q == o.max_batch) break;
+  }
+  (void)cudaGetLastError();
   srv->batcher = std::thread(batcher_loop, srv);
   srv->completer = std::thread(completer_loop, srv);
   *out = srv;
@@ -307,6 +326,37 @@ extern "C" int wmc_submit(wmc_server_t *srv, const double *w_pos, const double *
     srv->tickets[q.ticket] = TicketState();
     srv->queue.push_back(std::move(q));
     srv->stats.submitted++;
+  }
+  srv->cv_work.notify_one();
+  return WMC_OK;
+}
+
+extern "C" int wmc_submit_many(wmc_server_t *srv, int64_t n, const double *w_pos, const double *w_neg,
+                               uint64_t *tickets) {
+  if (!srv || n < 0 || (n > 0 && !tickets) || (n > 0 && srv->n_vars > 0 && (!w_pos || !w_neg))) {
+    set_error("NULL argument or n < 0");
+    return WMC_EINVAL;
+  }
+  const size_t nv = (size_t)srv->n_vars;
+  std::vector<Query> qs((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    Query &q = qs[(size_t)i];
+    q.wp.assign(w_pos + (size_t)i * nv, w_pos + (size_t)(i + 1) * nv);
+    q.wn.assign(w_neg + (size_t)i * nv, w_neg + (size_t)(i + 1) * nv);
+    q.negative = false;
+    for (size_t v = 0; v < nv; ++v) q.negative |= (q.wp[v] < 0) | (q.wn[v] < 0);
+  }
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop) { set_error("server is shutting down"); return WMC_ESHUTDOWN; }
+    for (int64_t i = 0; i < n; ++i) {
+      Query &q = qs[(size_t)i];
+      q.ticket = srv->next_ticket++;
+      tickets[i] = q.ticket;
+      srv->tickets[q.ticket] = TicketState();
+      srv->queue.push_back(std::move(q));
+      srv->stats.submitted++;
+    }
   }
   srv->cv_work.notify_one();
   return WMC_OK;

@@ -341,6 +341,26 @@ def test_server_continuous_batching(w):
     srv.close()
 
 
+def test_server_submit_many_matches_single_submits(w):
+    """A block of queries submitted in one call gets consecutive tickets and
+    the same results as the queries submitted one by one (and run alone)."""
+    cnf = wmcgen.grid_cnf(10, 60, 3)
+    plan = plan_for(w, cnf, None, None, FP32)
+    n = 80
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, n, seed=8, lo=0.05, hi=0.95)
+    alone = plan.execute(wq, wnq)
+    srv = w.Server(plan, max_batch=32, max_waves=2)
+    t_single = [srv.submit(wq[i], wnq[i]) for i in range(0, 20)]
+    t_block = srv.submit_many(wq[20:], wnq[20:])
+    assert t_block == list(range(t_block[0], t_block[0] + n - 20))
+    assert t_block[0] > t_single[-1]
+    for i, t in enumerate(t_single + t_block):
+        r = srv.wait(t, timeout_s=60)
+        assert (r.mant, r.exp2) == (alone[i].mant, alone[i].exp2), i
+    assert srv.submit_many(wq[:0], wnq[:0]) == []
+    srv.close()
+
+
 def test_alloc_failure_is_reported(w):
     cnf = wmcgen.random_kcnf(14, 40, seed=9)
     plan = plan_for(w, cnf, None, None, FP32)
