@@ -675,7 +675,7 @@ int64_t grid_for(uint64_t work) {
 }  // namespace
 
 // Builds the host-side layout for batch size Q (no device work).
-static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
+static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false) {
   st.Q = Q;
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
@@ -715,7 +715,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
   // at most 2^8 summed terms)
   std::vector<int32_t> sp_index(plan.nodes.size(), -1);
   std::vector<int64_t> sp_nodes;
-  if (g_small_phase.load()) {
+  if (g_small_phase.load() && !plain) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       const Node &nd = plan.nodes[ni];
       const TensorInfo &C = plan.tensors[(size_t)nd.c];
@@ -829,7 +829,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st) {
     }
     std::vector<int64_t> fuse_next(plan.nodes.size(), -1);
     std::vector<uint8_t> absorbed(plan.nodes.size(), 0);
-    const int fuse_level = g_fuse.load();
+    const int fuse_level = plain ? 0 : g_fuse.load();
     // frontier steps: one summed index; f added ones (1 in place, 2 growth,
     // 0 shrink); a chain starts with f >= 1 and ends at its first f = 0
     auto frontier_f = [&](const Launch &l) { return (l.kind == L_K2T && l.k2.k == 1) ? l.k2.f : -1; };
@@ -1374,16 +1374,17 @@ static int get_graph(Plan &plan, ExecState &st, char *ws, cudaGraphExec_t *out) 
   return WMC_OK;
 }
 
-static int get_state(Plan &plan, int32_t Q, ExecState **out) {
+static int get_state(Plan &plan, int32_t Q, ExecState **out, bool plain = false) {
   std::lock_guard<std::mutex> lk(plan.exec_mu);
-  auto it = plan.exec.find(Q);
-  if (it != plan.exec.end()) { *out = it->second.get(); return WMC_OK; }
+  auto &cache = plain ? plan.exec_plain : plan.exec;
+  auto it = cache.find(Q);
+  if (it != cache.end()) { *out = it->second.get(); return WMC_OK; }
   std::unique_ptr<ExecState> st(new (std::nothrow) ExecState());
   if (!st) { set_error("out of host memory"); return WMC_ENOMEM; }
-  int rc = build_exec(plan, Q, *st);
+  int rc = build_exec(plan, Q, *st, plain);
   if (rc) return rc;
   *out = st.get();
-  plan.exec[Q] = std::move(st);
+  cache[Q] = std::move(st);
   return WMC_OK;
 }
 
@@ -1635,7 +1636,7 @@ extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, c
 namespace wmc {
 int exec_layout(Plan &plan, int32_t Q, LayoutView *out) {
   ExecState *st = nullptr;
-  int rc = get_state(plan, Q, &st);
+  int rc = get_state(plan, Q, &st, true);
   if (rc) return rc;
   out->ws_bytes = st->ws_bytes;
   out->off_io = st->off_io;

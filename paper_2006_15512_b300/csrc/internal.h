@@ -71,6 +71,9 @@ struct Plan {
 
   std::mutex exec_mu;
   std::map<int32_t, std::unique_ptr<ExecState>> exec;  // keyed by Q
+  // one pass per node in post-order, every tensor its own offset (no chains,
+  // no small-node phase): the layout other executors reuse
+  std::map<int32_t, std::unique_ptr<ExecState>> exec_plain;
   ~Plan();
 };
 
@@ -99,7 +102,8 @@ void exec_fill_result(const ExecState *st, double mant, int64_t exp2, uint32_t f
                       bool unit, bool negative, wmc_result *out);
 Plan &plan_of(wmc_plan_t *p);
 
-// Host-side layout of a plan's walk at batch size Q (executor.cu).
+// Host-side layout of a plan's walk at batch size Q (executor.cu): one pass
+// per node in post-order, every node's output at its own offset.
 struct LayoutView {
   int64_t ws_bytes = 0, off_io = 0, off_flags = 0, off_err = 0, off_exp = 0, off_max = 0,
           off_min = 0, n_slots = 0;

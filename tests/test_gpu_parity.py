@@ -425,10 +425,42 @@ def test_uneven_batch_persistent(w, precision):
                 assert rel(res[i], want) <= TOL[precision], (i, rep)
 
 
+def test_uneven_batch_with_chain_sized_formulas(w):
+    """Formulas large enough that their own single-query walks fuse frontier
+    chains: the persistent batch (one pass per node, its own layout) still
+    gives each formula's result."""
+    cnfs = [wmcgen.grid_cnf(h, wd, seed) for h, wd, seed in ((48, 16, 2), (64, 16, 5), (30, 12, 3))]
+    plans = []
+    for cnf in cnfs:
+        wp, wn = wmcgen.weights_complementary(cnf.n_vars, 4, 0.05, 0.95)
+        plans.append(plan_for(w, cnf, wp, wn, FP32))
+    try:
+        w.wmc_set_fusion(0)  # (a plan is laid out at its first info/execute)
+        unfused = [plan_for(w, c, *wmcgen.weights_complementary(c.n_vars, 4, 0.05, 0.95), FP32) for c in cnfs]
+        n_unfused = [p.info(1).launches_per_walk for p in unfused]
+    finally:
+        w.wmc_set_fusion(4)
+    assert any(p.info(1).launches_per_walk < n for p, n in zip(plans, n_unfused))  # chains formed
+    batch = w.Batch(plans)
+    assert batch.n_admitted == len(plans)
+    res = batch.execute()
+    for i, p in enumerate(plans):
+        alone = p.execute()[0]
+        assert Big(res[i].mant, res[i].exp2).rel_diff(Big(alone.mant, alone.exp2)) <= TOL[FP32], i
+
+
 def test_uneven_batch_admission(w):
     """Admission by workspace bytes: only the prefix that fits is taken."""
-    plans, _, _ = _uneven(w, 10, FP32, seed=6, n3=(14, 30), grid_w=(3, 6), grid_h=(4, 20))
-    sizes = [p.info(1).workspace_bytes for p in plans]
+    # the batch lays each formula out with one pass per node (no chains, no
+    # small-node phase): the same workspace as a plan laid out with both off
+    try:
+        w.wmc_set_fusion(0)
+        w.wmc_set_small_phase(0)
+        plans, _, _ = _uneven(w, 10, FP32, seed=6, n3=(14, 30), grid_w=(3, 6), grid_h=(4, 20))
+        sizes = [p.info(1).workspace_bytes for p in plans]
+    finally:
+        w.wmc_set_fusion(4)
+        w.wmc_set_small_phase(1)
     budget = sum((s_ + 255) // 256 * 256 for s_ in sizes[:4])
     batch = w.Batch(plans, mem_budget_bytes=budget)
     assert batch.n_admitted == 4
@@ -437,9 +469,9 @@ def test_uneven_batch_admission(w):
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
 def test_fused_chains_match_unfused(w, precision):
-    """Consecutive frontier eliminations contracted in one pass (pairs by
-    k2_fused, chains of 2..4 by k2_chain) give the same values as one pass
-    per elimination (the intermediates' pow2 scales only move into the
+    """Consecutive frontier eliminations contracted in one pass (k2_chain,
+    chains of up to 2, 3, 4) give the same values as one pass per
+    elimination (the intermediates' pow2 scales only move into the
     exponent), and match the oracle; longer chains move fewer bytes."""
     H, W_ = 16, 100
     cnf = wmcgen.grid_cnf(H, W_, 1)
