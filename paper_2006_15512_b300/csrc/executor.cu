@@ -384,7 +384,8 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
 // indices above x_D move down one position).  Labels are full
 // (with query bits).  `allow_gs` admits growth and shrink steps.  `fast`
 // is set when the chain has the FAST layout (S_i depends on no chain index
-// but the two added last; contiguous lanes; P's scale folds into S_1).
+// but the two added last; contiguous or broadcast lanes; P's scale folds
+// into S_1).
 bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int32_t>> &LS,
                const std::vector<std::vector<int32_t>> &LC, bool f64, bool p_has_q, bool s1_has_q,
                int32_t Qp, bool allow_gs, wmc::dev::K2CParams &cp, int &v_out, bool &fast, int &grow,
@@ -467,6 +468,7 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   };
   auto label_of_bit = [&](int i, int j) { return j == D ? z : (j < i ? y[(size_t)j] : x[(size_t)j]); };
   const size_t es = f64 ? 8 : 4;
+  bool any_broadcast = false;
   for (int i = 0; i < D; ++i) {
     const std::vector<int32_t> &S = LS[(size_t)i];
     std::vector<std::pair<int, int>> bb;
@@ -505,7 +507,8 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
       broadcast &= (cp.dv[i][e] == 0u);
     }
     cp.b_vec[i] = contiguous ? 1 : (broadcast ? 2 : 0);
-    if (!contiguous) fast = false;
+    if (!contiguous && !broadcast) fast = false;
+    if (!contiguous && V > 1) any_broadcast = true;
     const int sx = pos_of(S, x[(size_t)i]);
     const int sy = y[(size_t)i] != INT32_MIN ? pos_of(S, y[(size_t)i]) : -1;
     const int sz = (i == 0 && grow) ? pos_of(S, z) : -1;
@@ -526,7 +529,8 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
       }
     cp.s_log2[i] = (int)S.size();
   }
-  if (!fast && (grow || shrink)) return false;  // growth and shrink steps: FAST variants only
+  // growth and shrink steps: FAST variants with contiguous lanes only
+  if ((grow || shrink) && (!fast || any_broadcast)) return false;
   // tiling of P over its kept indices: 2 work units per thread when 16
   // chain states would leave runs of only 2 KB (bulk copies that short
   // lower the read rate)
@@ -1116,11 +1120,11 @@ static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream
   }
 }
 
-template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(dev::k2_chain<T, V, D, FAST, GROW, SHRINK>,
+    cudaFuncSetAttribute(dev::k2_chain<T, V, D, FAST, BC, GROW, SHRINK>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
@@ -1137,21 +1141,30 @@ static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t sm
   attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, dev::k2_chain<T, V, D, FAST, GROW, SHRINK>, p);
+  cudaLaunchKernelEx(&cfg, dev::k2_chain<T, V, D, FAST, BC, GROW, SHRINK>, p);
 }
 
-// vector lanes: FAST plain chains, growth-first and shrink-last variants
+static bool chain_broadcast(const Launch &l) {
+  for (int i = 0; i < l.chain_d; ++i)
+    if (l.k2c.b_vec[i] == 2) return true;
+  return false;
+}
+
+// vector lanes: FAST plain chains (contiguous lanes, or some steps with
+// one value for all lanes), growth-first and shrink-last variants
 template <int V, int D>
 static void launch_k2c_vec(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
-  if (!l.chain_fast) launch_k2c_t<float, V, D, false, 0, 0>(p, l.blocks, l.smem, s);
-  else if (l.chain_grow) launch_k2c_t<float, V, D, true, 1, 0>(p, l.blocks, l.smem, s);
-  else if (l.chain_shrink) launch_k2c_t<float, V, D, true, 0, 1>(p, l.blocks, l.smem, s);
-  else launch_k2c_t<float, V, D, true, 0, 0>(p, l.blocks, l.smem, s);
+  if (!l.chain_fast) launch_k2c_t<float, V, D, false, 0, 0, 0>(p, l.blocks, l.smem, s);
+  else if (l.chain_grow) launch_k2c_t<float, V, D, true, 0, 1, 0>(p, l.blocks, l.smem, s);
+  else if (l.chain_shrink) launch_k2c_t<float, V, D, true, 0, 0, 1>(p, l.blocks, l.smem, s);
+  else if (chain_broadcast(l)) launch_k2c_t<float, V, D, true, 1, 0, 0>(p, l.blocks, l.smem, s);
+  else launch_k2c_t<float, V, D, true, 0, 0, 0>(p, l.blocks, l.smem, s);
 }
 template <typename T, int V, int D>
 static void launch_k2c_plain(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
-  if (l.chain_fast) launch_k2c_t<T, V, D, true, 0, 0>(p, l.blocks, l.smem, s);
-  else launch_k2c_t<T, V, D, false, 0, 0>(p, l.blocks, l.smem, s);
+  if (!l.chain_fast) launch_k2c_t<T, V, D, false, 0, 0, 0>(p, l.blocks, l.smem, s);
+  else if (V > 1 && chain_broadcast(l)) launch_k2c_t<T, V, D, true, 1, 0, 0>(p, l.blocks, l.smem, s);
+  else launch_k2c_t<T, V, D, true, 0, 0, 0>(p, l.blocks, l.smem, s);
 }
 
 // instantiated (T, V, D) as try_chain chooses them: V at its largest for

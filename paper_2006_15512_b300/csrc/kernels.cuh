@@ -751,7 +751,8 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
 // variants are compiled for the common layout: S_i depends on no chain
 // index but the two added last before y_i (so each block of S_i is loaded
 // once per dependency combination, not once per pair), every S_i holds
-// its query lanes contiguously, and P's scale folds into S_1.  The S_i
+// its lanes contiguously or one value for all of them, and P's scale
+// folds into S_1.  The S_i
 // arrive in shared memory by bulk async copies and are scaled there; P is
 // staged tile by tile by bulk async copies that the whole producer warp
 // issues, with NW consumer warps.
@@ -831,12 +832,14 @@ __host__ __device__ constexpr uint32_t chain_deps(int D, bool fast, int grow, in
   return fast ? (m & chain_others(D, grow, i)) : chain_others(D, grow, i);
 }
 
-// V lanes of a staged S_i at shared-memory byte address `a`
-template <typename T, int V, bool FAST>
+// V lanes of a staged S_i at shared-memory byte address `a`; LM is the lane
+// mode when known at compile time (1 contiguous, 2 one value for all
+// lanes), 0 to follow the runtime mode
+template <typename T, int V, int LM>
 __device__ __forceinline__ void ld_lanes(uint32_t a, int mode, const uint32_t *dv, T (&r)[V]) {
-  if (FAST || V == 1 || mode == 1) {
+  if (LM == 1 || (LM == 0 && (V == 1 || mode == 1))) {
     LdsV<T, V>::ld(a, r);
-  } else if (mode == 2) {
+  } else if (LM == 2 || mode == 2) {
     const T v = lds1(a, T());
 #pragma unroll
     for (int i = 0; i < V; ++i) r[i] = v;
@@ -879,9 +882,10 @@ __device__ __forceinline__ void fma2terms<float, 4>(const float (&x0)[4], const 
 }
 
 // step I of the chain on the register block a (compile-time indices);
-// KIND 1 in place, 2 growth (adds z at bit D), 0 shrink (adds nothing)
-template <typename T, int V, int D, bool FAST, int GROW, int KIND, int I>
-__device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&a)[1 << (D + GROW)][V]) {
+// KIND 1 in place, 2 growth (adds z at bit D), 0 shrink (adds nothing);
+// LM: S_I's lane mode (see ld_lanes)
+template <typename T, int V, int D, bool FAST, int GROW, int KIND, int I, int LM>
+__device__ __forceinline__ void chain_step_m(const K2CParams &cp, uint32_t g, T (&a)[1 << (D + GROW)][V]) {
   constexpr int NB = D + GROW;
   constexpr uint32_t G = chain_deps(D, FAST, GROW, I);
   constexpr uint32_t O = chain_others(D, GROW, I) & ~G;
@@ -897,7 +901,7 @@ __device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int av = 0; av < NA; ++av)
-        ld_lanes<T, V, FAST>(g + cp.d[I][(sg | (x ? XB : 0u)) | ((uint32_t)av << NB)], mode, cp.dv[I], b[x][av]);
+        ld_lanes<T, V, LM>(g + cp.d[I][(sg | (x ? XB : 0u)) | ((uint32_t)av << NB)], mode, cp.dv[I], b[x][av]);
 #pragma unroll
     for (uint32_t to = 0; to < (1u << nO); ++to) {
       const uint32_t s0 = sg | pdep_c(to, O), s1 = s0 | XB;
@@ -929,17 +933,29 @@ __device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&
   }
 }
 
-template <typename T, int V, int D, bool FAST, int GROW, int SHRINK, int I>
+// FAST chains have contiguous or broadcast lanes per step: one branch per
+// step picks the variant; the generic chains follow the runtime mode per load
+// FAST chains: every step's lanes contiguous (BC 0), or each step
+// contiguous or broadcast (BC 1: one branch per step picks the variant);
+// the generic chains follow the runtime mode per load
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int KIND, int I>
+__device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&a)[1 << (D + GROW)][V]) {
+  if (!FAST) chain_step_m<T, V, D, FAST, GROW, KIND, I, 0>(cp, g, a);
+  else if (BC && V > 1 && cp.b_vec[I] == 2) chain_step_m<T, V, D, FAST, GROW, KIND, I, 2>(cp, g, a);
+  else chain_step_m<T, V, D, FAST, GROW, KIND, I, 1>(cp, g, a);
+}
+
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK, int I>
 struct ChainSteps {
   static __device__ __forceinline__ void run(const K2CParams &cp, const uint32_t (&g)[D],
                                              T (&a)[1 << (D + GROW)][V]) {
     constexpr int KIND = (I == 0 && GROW) ? 2 : ((I == D - 1 && SHRINK) ? 0 : 1);
-    chain_step<T, V, D, FAST, GROW, KIND, I>(cp, g[I], a);
-    ChainSteps<T, V, D, FAST, GROW, SHRINK, I + 1>::run(cp, g, a);
+    chain_step<T, V, D, FAST, BC, GROW, KIND, I>(cp, g[I], a);
+    ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, I + 1>::run(cp, g, a);
   }
 };
-template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
-struct ChainSteps<T, V, D, FAST, GROW, SHRINK, D> {
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
+struct ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, D> {
   static __device__ __forceinline__ void run(const K2CParams &, const uint32_t (&)[D],
                                              T (&)[1 << (D + GROW)][V]) {}
 };
@@ -953,7 +969,7 @@ __device__ __forceinline__ unsigned long long min_m1(unsigned long long bits, un
   return m < cur ? m : cur;
 }
 
-template <typename T, int V, int D, bool FAST, int GROW, int SHRINK>
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) {
   typedef typename Bits<T>::t BT;
   constexpr int NW = kChainNW;
@@ -1163,7 +1179,7 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers
         }
-        ChainSteps<T, V, D, FAST, GROW, SHRINK, 0>::run(cp, g, a);
+        ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, 0>::run(cp, g, a);
 #pragma unroll
         for (int s = 0; s < (1 << NB); ++s) {
           if (SHRINK && ((s >> (D - 1)) & 1)) continue;  // summed away
