@@ -123,7 +123,12 @@ typedef struct {
   int32_t max_rank_cap;     /* reject plans whose largest tensor (in index
                                count, before the query index) exceeds this;
                                0 = 30                                       */
-  int32_t reserved;
+  int32_t slice_to_rank;    /* index slicing (Alg. 3): if > 0, fix variables
+                               one at a time until the largest tensor has at
+                               most this many indices (at most 24 variables,
+                               2^24 slices); every execution then runs the
+                               walk once per slice assignment and sums the
+                               results (Thm 4.2).  0 = no slicing           */
   int64_t mem_budget_bytes; /* reject plans whose workspace at Q = 1
                                exceeds this; 0 = no limit                   */
   const int32_t *order;     /* WMC_ORDER_GIVEN: n_vars 1-based ids (host,
@@ -153,7 +158,10 @@ typedef struct {
   int32_t precision;
   int32_t ordering_used;
   int32_t max_path_roundings; /* d of wmc_result.rel_err_bound            */
-  int32_t launches_per_walk;  /* kernel launches one execution enqueues   */
+  int32_t launches_per_walk;  /* kernel launches one walk enqueues        */
+  int32_t n_slice_vars;       /* index slicing: s sliced variables, 2^s
+                                 walks per execution (0: none)           */
+  int32_t slice_vars[24];     /* their 0-based ids; slice bit k = var k  */
 } wmc_plan_info_t;
 /* Q >= 1 is the number of queries batched along the extra query index. */
 int wmc_plan_info(const wmc_plan_t *plan, int32_t Q, wmc_plan_info_t *out);
@@ -179,6 +187,15 @@ int wmc_plan_leaf(const wmc_plan_t *plan, int64_t leaf, int32_t *kind,
  * Errors: WMC_EINVAL (Q < 1 or Q > 4096), WMC_ENOMEM, WMC_ECUDA. */
 int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q,
                 const double *w_neg_q, void *stream, wmc_result *out);
+
+/* Index slicing across processes: as wmc_execute, but only the slice
+ * assignments eta in [slice_lo, slice_hi) of a sliced plan (0 <= slice_lo
+ * <= slice_hi <= 2^n_slice_vars); out[q] is their partial sum.  Partial
+ * sums of disjoint ranges covering every slice add up (exponent-aligned)
+ * to the full result.  An unsliced plan has the single slice 0. */
+int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_pos_q,
+                       const double *w_neg_q, int64_t slice_lo, int64_t slice_hi,
+                       void *stream, wmc_result *out);
 
 /* Execution with device-resident inputs and outputs, asynchronous on
  * `stream`.  d_w_pos / d_w_neg: device [Q][n_vars] float64.  d_workspace:

@@ -25,7 +25,7 @@ from ._abi import *  # noqa: F401,F403  (the C names)
 from ._abi import check, lib
 
 __all__ = ["Network", "Plan", "Server", "Batch", "Result", "contract_pair", "to_scaled_fp32",
-           "launch_count"] + list(_abi.EXPORTS)
+           "launch_count", "slice_range", "combine_results"] + list(_abi.EXPORTS)
 
 P = ctypes.POINTER
 
@@ -53,6 +53,43 @@ class Result:
 
 def launch_count() -> int:
     return int(lib.wmc_kernel_launch_count())
+
+
+def slice_range(n_slices: int, rank: int, world: int):
+    """Index slicing across processes (Alg. 3 with one share of the slices
+    per process): the contiguous range [lo, hi) of slice assignments that
+    process `rank` of `world` runs; the ranges cover [0, n_slices) once."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank must lie in [0, world)")
+    return n_slices * rank // world, n_slices * (rank + 1) // world
+
+
+def combine_results(parts: Sequence[Result]) -> Result:
+    """Sum of partial results mant * 2**exp2 (e.g. the slice shares of
+    several processes), with the exponents aligned to the largest and the
+    sum kept in float64; flags are OR-ed and the error bounds add up (plus
+    one float64 rounding per addition)."""
+    total_m, total_e = 0.0, 0
+    flags, bound = 0, 0.0
+    for r in parts:
+        flags |= r.flags
+        bound = max(bound, r.rel_err_bound)
+        if r.mant == 0.0:
+            continue
+        m, e = math.frexp(r.mant)
+        e += r.exp2
+        if total_m == 0.0:
+            total_m, total_e = m, e
+            continue
+        if e > total_e:
+            total_m, total_e, m, e = m, e, total_m, total_e
+        d = total_e - e
+        total_m += math.ldexp(m, -d) if d <= 1100 else 0.0
+        fm, fe = math.frexp(total_m)
+        total_m, total_e = fm, total_e + fe
+    bound += max(len(parts) - 1, 0) * 2.0 ** -53
+    log10 = (math.log10(abs(total_m)) + total_e * math.log10(2.0)) if total_m != 0.0 else -math.inf
+    return Result(total_m, total_e if total_m != 0.0 else 0, log10, flags, bound)
 
 
 class Network:
@@ -99,11 +136,13 @@ class Plan:
 
     def __init__(self, net: Network, precision: int = _abi.WMC_SCALED_FP32,
                  ordering: int = _abi.WMC_ORDER_BEST, max_rank_cap: int = 0,
-                 mem_budget_bytes: int = 0, order: Optional[Sequence[int]] = None):
+                 mem_budget_bytes: int = 0, order: Optional[Sequence[int]] = None,
+                 slice_to_rank: int = 0):
         o = _abi.wmc_plan_opts()
         o.precision = precision
         o.ordering = ordering
         o.max_rank_cap = max_rank_cap
+        o.slice_to_rank = slice_to_rank
         o.mem_budget_bytes = mem_budget_bytes
         self._order = None
         if order is not None:
@@ -160,6 +199,30 @@ class Plan:
             pw = nw = None
         out = (_abi.wmc_result * Q)()
         check(lib.wmc_execute(self.handle, int(Q), pw, nw, ctypes.c_void_p(stream), out), "wmc_execute")
+        return [Result.from_c(out[i]) for i in range(Q)]
+
+    @property
+    def slice_vars(self) -> List[int]:
+        i = self.info(1)
+        return [int(i.slice_vars[k]) for k in range(i.n_slice_vars)]
+
+    def execute_slices(self, slice_lo: int, slice_hi: int, w_pos_q: Optional[np.ndarray] = None,
+                       w_neg_q: Optional[np.ndarray] = None, Q: Optional[int] = None,
+                       stream: int = 0) -> List[Result]:
+        """wmc_execute_slices: the partial sum over slice assignments
+        [slice_lo, slice_hi) of a sliced plan."""
+        if w_pos_q is not None:
+            wp = np.ascontiguousarray(w_pos_q, dtype=np.float64).reshape(-1, max(self.n_vars, 1))
+            wn = np.ascontiguousarray(w_neg_q, dtype=np.float64).reshape(wp.shape)
+            Q = wp.shape[0]
+            pw, nw = _ptr(wp, ctypes.c_double), _ptr(wn, ctypes.c_double)
+        else:
+            Q = Q or 1
+            pw = nw = None
+        out = (_abi.wmc_result * Q)()
+        check(lib.wmc_execute_slices(self.handle, int(Q), pw, nw, ctypes.c_int64(slice_lo),
+                                     ctypes.c_int64(slice_hi), ctypes.c_void_p(stream), out),
+              "wmc_execute_slices")
         return [Result.from_c(out[i]) for i in range(Q)]
 
     def execute_device(self, Q: int, d_w_pos, d_w_neg, workspace, d_mant, d_exp2, d_flags,

@@ -63,14 +63,15 @@ class wmc_network_info_t(ctypes.Structure):
 
 class wmc_plan_opts(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("ordering", c_i32), ("max_rank_cap", c_i32),
-                ("reserved", c_i32), ("mem_budget_bytes", c_i64), ("order", P(c_i32))]
+                ("slice_to_rank", c_i32), ("mem_budget_bytes", c_i64), ("order", P(c_i32))]
 
 
 class wmc_plan_info_t(ctypes.Structure):
     _fields_ = [("max_rank", c_i32), ("max_node_rank", c_i32), ("n_leaves", c_i64),
                 ("n_nodes", c_i64), ("workspace_bytes", c_i64), ("peak_tensor_bytes", c_i64),
                 ("algorithmic_bytes", c_dbl), ("flops", c_dbl), ("precision", c_i32),
-                ("ordering_used", c_i32), ("max_path_roundings", c_i32), ("launches_per_walk", c_i32)]
+                ("ordering_used", c_i32), ("max_path_roundings", c_i32), ("launches_per_walk", c_i32),
+                ("n_slice_vars", c_i32), ("slice_vars", c_i32 * 24)]
 
 
 class wmc_server_opts(ctypes.Structure):
@@ -107,6 +108,7 @@ EXPORTS = {
     "wmc_plan_node": (c_i32, [c_vp, c_i64, P(c_i64), P(c_i64), P(c_i32), P(c_i32)]),
     "wmc_plan_leaf": (c_i32, [c_vp, c_i64, P(c_i32), P(c_i32), P(c_i32), P(c_u64)]),
     "wmc_execute": (c_i32, [c_vp, c_i32, P(c_dbl), P(c_dbl), c_vp, P(wmc_result)]),
+    "wmc_execute_slices": (c_i32, [c_vp, c_i32, P(c_dbl), P(c_dbl), c_i64, c_i64, c_vp, P(wmc_result)]),
     "wmc_execute_device": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_size, c_vp, c_vp, c_vp, c_vp]),
     "wmc_execute_device_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_contract_pair": (c_i32, [c_i32, c_i32, P(c_i32), c_vp, c_i32, P(c_i32), c_vp, c_i32,

@@ -121,6 +121,7 @@ struct ExecState {
   int64_t arena_bytes = 0, ws_bytes = 0;
   double alg_bytes = 0, flops = 0;
   int32_t max_roundings = 0;
+  int32_t n_slice_vars = 0;   // index slicing: walks per execution = 2^n_slice_vars
   std::vector<Launch> launches;
   int64_t kernels_per_run = 0;
   // constant tables (device, owned)
@@ -743,6 +744,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false) 
   for (int64_t i = 0; i < plan.n_leaves; ++i) { st.t_off[(size_t)i] = off; off += align_up(bytes[(size_t)i]); }
   const int64_t arena0 = off;
   st.max_roundings = plan.tensors[(size_t)root].roundings;
+  st.n_slice_vars = (int32_t)plan.slice_vars.size();
 
   // ---- per-node kernel choice (offsets are filled in once laid out)
   std::vector<Launch> node_l(plan.nodes.size());
@@ -969,6 +971,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false) 
     L.meta = st.t_meta[(size_t)i];
     L.fals = t.fals;
     L.rank = (int32_t)t.labels.size();
+    L.smask = t.clause >= 0 ? plan.clauses[(size_t)t.clause].smask : 0u;
+    L.sfals = t.clause >= 0 ? plan.clauses[(size_t)t.clause].sfals : 0u;
     L.pad = 0;
     st.h_clause.push_back(L);
     st.h_first.push_back(entries);
@@ -979,8 +983,9 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false) 
     Launch l; l.kind = L_CLAUSES; l.blocks = grid_for((uint64_t)entries);
     st.launches.push_back(l);
   }
-  st.h_woff.assign((size_t)plan.n_vars, 0);
-  st.h_wmeta.assign((size_t)plan.n_vars, 0);
+  // -1: a variable without a weight leaf (a sliced one), skipped by the kernel
+  st.h_woff.assign((size_t)plan.n_vars, -1);
+  st.h_wmeta.assign((size_t)plan.n_vars, -1);
   bool have_w = false;
   for (int64_t i = 0; i < plan.n_leaves; ++i) {
     const TensorInfo &t = plan.tensors[(size_t)i];
@@ -1249,11 +1254,11 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         if (st.f64)
           dev::k_clause_leaves<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
               tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
-              (double *)ws, mexp, mmax, mmin);
+              (double *)ws, mexp, mmax, mmin, io);
         else
           dev::k_clause_leaves<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
               tb.clause, tb.first, (int64_t)st.h_clause.size(), st.n_clause_entries,
-              (float *)ws, mexp, mmax, mmin);
+              (float *)ws, mexp, mmax, mmin, io);
         break;
       case L_WEIGHTS:
         if (st.f64)
@@ -1351,7 +1356,7 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Qp : 1;
         dev::k_finalize<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
             io, (const double *)(ws + l.off_c), mexp + l.meta_c, root_qc, flags,
-            (const uint32_t *)(ws + st.off_err), st.Q);
+            (const uint32_t *)(ws + st.off_err), st.Q, plan.n_vars);
         break;
       }
     }
@@ -1415,10 +1420,30 @@ static int check_q(int32_t Q) {
   return WMC_OK;
 }
 
-// Runs the walk for a power-of-two batch Qp >= Q on device pointers.
+static IoDesc io_desc(const Plan &plan, const double *d_wp, const double *d_wn, double *d_mant,
+                      int64_t *d_exp, uint32_t *d_flags) {
+  IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.w_pos = d_wp; io.w_neg = d_wn; io.mant = d_mant; io.exp2 = d_exp; io.flags = d_flags;
+  io.n_slice = (int32_t)plan.slice_vars.size();
+  for (size_t k = 0; k < plan.slice_vars.size(); ++k) io.slice_var[k] = plan.slice_vars[k];
+  return io;
+}
+
+static int64_t n_slices(const Plan &plan) { return int64_t(1) << plan.slice_vars.size(); }
+
+// Runs the walk for a power-of-two batch Qp >= Q on device pointers, once
+// per slice assignment in [slice_lo, slice_hi) (index slicing: the results
+// accumulate in the outputs; an unsliced plan has the single slice 0).
 static int run_device(Plan &plan, ExecState &st, const double *d_wp, const double *d_wn,
                       char *ws, double *d_mant, int64_t *d_exp, uint32_t *d_flags,
-                      cudaStream_t s) {
+                      cudaStream_t s, int64_t slice_lo = 0, int64_t slice_hi = -1) {
+  if (slice_hi < 0) slice_hi = n_slices(plan);
+  if (slice_lo < 0 || slice_lo >= slice_hi || slice_hi > n_slices(plan)) {
+    set_error("slice range [%lld, %lld) outside [0, %lld)", (long long)slice_lo, (long long)slice_hi,
+              (long long)n_slices(plan));
+    return WMC_EINVAL;
+  }
   int rc = ensure_dev(st);
   if (rc) return rc;
   cudaGraphExec_t ge = nullptr;
@@ -1427,12 +1452,14 @@ static int run_device(Plan &plan, ExecState &st, const double *d_wp, const doubl
     rc = get_graph(plan, st, ws, &ge);
   }
   if (rc) return rc;
-  IoDesc io;
-  std::memset(&io, 0, sizeof(io));
-  io.w_pos = d_wp; io.w_neg = d_wn; io.mant = d_mant; io.exp2 = d_exp; io.flags = d_flags;
-  CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaGraphLaunch(ge, s));
-  g_launches.fetch_add(st.kernels_per_run);
+  IoDesc io = io_desc(plan, d_wp, d_wn, d_mant, d_exp, d_flags);
+  for (int64_t eta = slice_lo; eta < slice_hi; ++eta) {
+    io.slice = (uint64_t)eta;
+    io.accumulate = eta != slice_lo;
+    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(ge, s));
+    g_launches.fetch_add(st.kernels_per_run);
+  }
   return WMC_OK;
 }
 
@@ -1447,6 +1474,10 @@ static void fill_result(const ExecState &st, double mant, int64_t e,
   const double u = st.f64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
   const double d = (double)st.max_roundings;
   r->rel_err_bound = d * u / (1.0 - d * u);
+  if (st.n_slice_vars > 0) {  // float64 slice factors (s roundings) and the sum of 2^s slices
+    const double ds = (double)st.n_slice_vars + std::ldexp(1.0, st.n_slice_vars) - 1.0;
+    r->rel_err_bound += ds * std::ldexp(1.0, -53);
+  }
   if (negative) r->flags |= WMC_FLAG_NO_BOUND;
   if (unit && st.f64 && mant != 0.0 && r->exp2 <= 53 && std::ldexp(fr, (int)r->exp2) == std::floor(std::ldexp(fr, (int)r->exp2)))
     r->flags |= WMC_FLAG_EXACT_INT;
@@ -1502,6 +1533,8 @@ extern "C" int wmc_plan_info(const wmc_plan_t *cplan, int32_t Q, wmc_plan_info_t
   out->ordering_used = plan->ordering_used;
   out->max_path_roundings = st->max_roundings;
   out->launches_per_walk = (int32_t)st->kernels_per_run;
+  out->n_slice_vars = (int32_t)plan->slice_vars.size();
+  for (size_t k = 0; k < plan->slice_vars.size() && k < 24; ++k) out->slice_vars[k] = plan->slice_vars[k];
   return WMC_OK;
 }
 
@@ -1565,9 +1598,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
   const size_t nl = st->launches.size();
   std::vector<cudaEvent_t> ev(nl + 1, nullptr);
   for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
-  IoDesc io;
-  std::memset(&io, 0, sizeof(io));
-  io.w_pos = d_w_pos; io.w_neg = d_w_neg; io.mant = d_mant; io.exp2 = d_exp2; io.flags = d_flags;
+  const IoDesc io = io_desc(*plan, d_w_pos, d_w_neg, d_mant, d_exp2, d_flags);  // slice 0
   char *ws = (char *)d_workspace;
   CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaEventRecord(ev[0], s));
@@ -1587,8 +1618,38 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
   return WMC_OK;
 }
 
+static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                        int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out);
+
 extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
                            void *stream, wmc_result *out) {
+  if (!plan) { set_error("NULL argument"); return WMC_EINVAL; }
+  return execute_host(plan, Q, w_pos_q, w_neg_q, 0, n_slices(*plan), stream, out);
+}
+
+extern "C" int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_pos_q,
+                                  const double *w_neg_q, int64_t slice_lo, int64_t slice_hi,
+                                  void *stream, wmc_result *out) {
+  if (!plan) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (slice_lo < 0 || slice_lo > slice_hi || slice_hi > n_slices(*plan)) {
+    set_error("slice range [%lld, %lld) outside [0, %lld]", (long long)slice_lo, (long long)slice_hi,
+              (long long)n_slices(*plan));
+    return WMC_EINVAL;
+  }
+  if (slice_lo == slice_hi) {  // an empty range: the sum is 0
+    if (!out) { set_error("NULL argument"); return WMC_EINVAL; }
+    if (check_q(Q)) return WMC_EINVAL;
+    for (int32_t q = 0; q < Q; ++q) {
+      std::memset(out + q, 0, sizeof(wmc_result));
+      out[q].log10 = -INFINITY;
+    }
+    return WMC_OK;
+  }
+  return execute_host(plan, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
+}
+
+static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                        int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
   if (!plan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
   if (check_q(Q)) return WMC_EINVAL;
   if ((w_pos_q == nullptr) != (w_neg_q == nullptr)) { set_error("give both weight arrays or neither"); return WMC_EINVAL; }
@@ -1630,7 +1691,7 @@ extern "C" int wmc_execute(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, c
     }
   }
   rc = run_device(*plan, *st, st->d_w, st->d_w + (size_t)Q * nv, (char *)st->own_ws,
-                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s);
+                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s, slice_lo, slice_hi);
   if (rc) return rc;
   CUDA_TRY(cudaMemcpyAsync(st->h_res_mant, st->d_res_mant, sizeof(double) * (size_t)Q, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(st->h_res_exp, st->d_res_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
@@ -1899,16 +1960,19 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   if (b_sn) CUDA_TRY(cudaMemcpyAsync(base + o_sn, st->h_snodes.data(), b_sn, cudaMemcpyHostToDevice, s));
   if (b_stk) CUDA_TRY(cudaMemcpyAsync(base + o_stk, st->h_stasks.data(), b_stk, cudaMemcpyHostToDevice, s));
   char *ws = base + o_ws;
-  IoDesc io;
-  std::memset(&io, 0, sizeof(io));
-  io.w_pos = d_w_pos; io.w_neg = d_w_neg; io.mant = d_mant; io.exp2 = d_exp2; io.flags = d_flags;
-  CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+  IoDesc io = io_desc(*plan, d_w_pos, d_w_neg, d_mant, d_exp2, d_flags);
   const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
                           (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta),
                           (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk)};
-  // the walk's first launch zeroes the flags and metadata it accumulates into
-  enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
-  g_launches.fetch_add(st->kernels_per_run);
+  // the walk's first launch zeroes the flags and metadata it accumulates
+  // into; one walk per slice assignment (index slicing)
+  for (int64_t eta = 0; eta < n_slices(*plan); ++eta) {
+    io.slice = (uint64_t)eta;
+    io.accumulate = eta != 0;
+    CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
+    g_launches.fetch_add(st->kernels_per_run);
+  }
   CUDA_TRY(cudaGetLastError());
   return WMC_OK;
 }
@@ -1955,6 +2019,27 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
       return WMC_EINVAL;
     }
     if (sn.chunk_log2 > sn.rC || sn.k > 8 || sn.rC > 16) { set_error("small-phase node %zu: bad shape", i); return WMC_EINVAL; }
+    ++checked;
+  }
+  // weight leaves: every variable's table entry is its own leaf or -1
+  {
+    std::vector<uint8_t> has_leaf((size_t)plan->n_vars, 0);
+    for (int64_t i = 0; i < plan->n_leaves; ++i) {
+      const TensorInfo &t = plan->tensors[(size_t)i];
+      if (t.kind != LEAF_WEIGHT) continue;
+      const size_t v = (size_t)t.labels[0];
+      has_leaf[v] = 1;
+      const int64_t es = st->f64 ? 8 : 4;
+      if (st->h_woff[v] * es != st->t_off[(size_t)i] || 2 * st->Qp * es > st->t_bytes[(size_t)i]) {
+        set_error("weight leaf of variable %zu: table offset outside its tensor", v);
+        return WMC_EINVAL;
+      }
+    }
+    for (size_t v = 0; v < (size_t)plan->n_vars; ++v)
+      if (!has_leaf[v] && (st->h_woff[v] != -1 || st->h_wmeta[v] != -1)) {
+        set_error("variable %zu has no weight leaf but a table entry", v);
+        return WMC_EINVAL;
+      }
     ++checked;
   }
   size_t li = 0;

@@ -23,6 +23,13 @@ void set_error(const char *fmt, ...);
 struct Clause {
   std::vector<int32_t> vars;
   uint64_t fals = 0;
+  // index slicing (Alg. 3): literals on sliced variables, as bits over the
+  // slice index (variable slice_vars[k] is bit k): smask = the clause's
+  // sliced variables, sfals = their falsifying values.  Under the slice
+  // assignment eta the clause is satisfied outright iff some sliced literal
+  // is true, i.e. ((eta ^ sfals) & smask) != 0; otherwise it is the clause
+  // over its remaining variables.
+  uint32_t smask = 0, sfals = 0;
 };
 
 struct Network {
@@ -33,6 +40,7 @@ struct Network {
   bool has_empty = false;
   int64_t n_indices_strict = 0;
   int64_t max_clause_rank = 0;
+  std::vector<uint8_t> sliced;  // per variable: fixed by the slice (no weight leaf, in no clause)
 };
 
 enum LeafKind : int32_t { LEAF_CLAUSE = 0, LEAF_WEIGHT = 1, LEAF_ONE = 2, NOT_LEAF = -1 };
@@ -68,6 +76,9 @@ struct Plan {
   int32_t max_rank = 0;
   int32_t max_node_rank = 0;
   std::vector<Clause> clauses;       // for leaf materialisation
+  // index slicing: the sliced variables (slice bit k = slice_vars[k]); the
+  // walk runs once per slice assignment and the results are summed
+  std::vector<int32_t> slice_vars;
 
   std::mutex exec_mu;
   std::map<int32_t, std::unique_ptr<ExecState>> exec;  // keyed by Q

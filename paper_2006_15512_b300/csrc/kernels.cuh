@@ -1564,43 +1564,6 @@ __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
 
 // --------------------------------------------------------------- leaves
 
-struct ClauseLeaf {
-  int64_t off;      // element offset in the tensor arena
-  int64_t meta;     // metadata slot
-  uint64_t fals;    // falsifying assignment
-  int32_t rank;
-  int32_t pad;
-};
-
-// Clause tensors B_C (Thm 3.2): 1 everywhere except 0 at the falsifying
-// assignment.  One thread per entry of a flat list; `first` holds the
-// first flat entry of each leaf (sorted), n_leaves entries.
-template <typename T>
-__global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, int64_t n_leaves,
-                                int64_t n_entries, T *arena, int64_t *meta_exp,
-                                unsigned long long *meta_max, unsigned long long *meta_min) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_entries;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = 0, hi = n_leaves - 1;
-    while (lo < hi) {  // last leaf with first <= i
-      int64_t mid = (lo + hi + 1) >> 1;
-      if (first[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    const ClauseLeaf L = leaves[lo];
-    const uint64_t a = (uint64_t)(i - first[lo]);
-    arena[L.off + (int64_t)a] = (a == L.fals) ? (T)0 : (T)1;
-    if (a == 0) {
-      meta_exp[L.meta] = 0;
-      // max is 1 unless the tensor is the rank-0 empty clause (value 0)
-      meta_max[L.meta] = (L.rank == 0) ? 0ull : abs_bits((T)1);
-      meta_min[L.meta] = (L.rank == 0) ? kNoMin : abs_bits((T)1);
-    }
-  }
-}
-
-// Weight vectors [W(x,0), W(x,1)] per query, normalised so the larger
-// magnitude lies in [1, 2); the scale is an exact power of two.
-// Element [b * Q + q] of variable x's tensor.
 // Pointers that change from call to call; read from device memory so a
 // captured graph can be replayed with new inputs and outputs.
 struct IoDesc {
@@ -1609,9 +1572,58 @@ struct IoDesc {
   double *mant;
   int64_t *exp2;
   uint32_t *flags;
-  int64_t pad[3];
+  // index slicing (Alg. 3): this walk's slice assignment (bit k fixes
+  // slice_var[k]); accumulate != 0 adds the result to what the outputs hold
+  uint64_t slice;
+  int32_t accumulate;
+  int32_t n_slice;
+  int32_t slice_var[24];
 };
 
+struct ClauseLeaf {
+  int64_t off;      // element offset in the tensor arena
+  int64_t meta;     // metadata slot
+  uint64_t fals;    // falsifying assignment
+  int32_t rank;
+  uint32_t smask;   // index slicing: the clause's sliced variables (slice bits)
+  uint32_t sfals;   // ... and their falsifying values
+  uint32_t pad;
+};
+
+// Clause tensors B_C (Thm 3.2): 1 everywhere except 0 at the falsifying
+// assignment.  One thread per entry of a flat list; `first` holds the
+// first flat entry of each leaf (sorted), n_leaves entries.  Under index
+// slicing a clause that a sliced literal satisfies is 1 everywhere.
+template <typename T>
+__global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, int64_t n_leaves,
+                                int64_t n_entries, T *arena, int64_t *meta_exp,
+                                unsigned long long *meta_max, unsigned long long *meta_min,
+                                const IoDesc *io) {
+  const uint32_t eta = (uint32_t)io->slice;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_entries;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = n_leaves - 1;
+    while (lo < hi) {  // last leaf with first <= i
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const ClauseLeaf L = leaves[lo];
+    const bool sat = ((eta ^ L.sfals) & L.smask) != 0u;
+    const uint64_t a = (uint64_t)(i - first[lo]);
+    arena[L.off + (int64_t)a] = (a == L.fals && !sat) ? (T)0 : (T)1;
+    if (a == 0) {
+      meta_exp[L.meta] = 0;
+      // max is 1 unless the tensor is a rank-0 clause with value 0
+      const bool zero = L.rank == 0 && !sat;
+      meta_max[L.meta] = zero ? 0ull : abs_bits((T)1);
+      meta_min[L.meta] = zero ? kNoMin : abs_bits((T)1);
+    }
+  }
+}
+
+// Weight vectors [W(x,0), W(x,1)] per query, normalised so the larger
+// magnitude lies in [1, 2); the scale is an exact power of two.
+// Element [b * Q + q] of variable x's tensor.
 // Q queries fill the Qp = 2^m query lanes; padding lanes repeat the last
 // query (their results are never read).
 template <typename T>
@@ -1625,6 +1637,7 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t x = (int32_t)(i / Qp), q = (int32_t)(i % Qp);
+    if (off[x] < 0) continue;  // no weight leaf: a variable fixed by index slicing
     const int32_t qs = q < Q ? q : Q - 1;
     const double w1 = w_pos[(int64_t)qs * n_vars + x];
     const double w0 = w_neg[(int64_t)qs * n_vars + x];
@@ -1662,17 +1675,57 @@ __global__ void k_one_leaf(T *dst, int64_t meta, int64_t *meta_exp, unsigned lon
 
 // Root: value[q] = mant[q] * 2^exp[q] with the root tensor stored in
 // float64 (its exponents already account for its inputs' scales).
+// The root (float64 mantissa and int64 exponent per query) into the
+// outputs.  Under index slicing the value is multiplied by the sliced
+// variables' weights at the slice assignment (Thm 4.2: the slice's share of
+// W) and, after the first slice, added to the outputs with the exponents
+// aligned (all terms nonnegative for nonnegative weights).
 __global__ void k_finalize(const IoDesc *io, const double *root, const int64_t *root_exp,
                            int32_t root_qc, const uint32_t *flags, const uint32_t *err,
-                           int32_t Q) {
+                           int32_t Q, int32_t n_vars) {
   double *mant = io->mant;
   int64_t *exp2 = io->exp2;
   uint32_t *out_flags = io->flags;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
     const int qr = root_qc > 1 ? q : 0;
-    mant[q] = root[qr];
-    exp2[q] = root_exp[qr];
-    out_flags[q] = flags[q] | (*err ? 0x8u : 0u);
+    double m = root[qr];
+    int64_t e = root_exp[qr];
+    for (int k = 0; k < io->n_slice; ++k) {
+      const int64_t at = (int64_t)q * n_vars + io->slice_var[k];
+      m *= ((io->slice >> k) & 1ull) ? io->w_pos[at] : io->w_neg[at];
+      int fe = 0;
+      m = frexp(m, &fe);
+      e += fe;
+    }
+    const uint32_t f = flags[q] | (*err ? 0x8u : 0u);
+    if (io->accumulate) {
+      double om = mant[q];
+      int64_t oe = exp2[q];
+      if (om == 0.0) {
+        mant[q] = m;
+        exp2[q] = e;
+      } else if (m != 0.0) {
+        int fo = 0, fn = 0;
+        om = frexp(om, &fo);
+        m = frexp(m, &fn);
+        oe += fo;
+        e += fn;
+        if (oe >= e) {
+          const int64_t d = oe - e;
+          mant[q] = om + (d > 1100 ? 0.0 : ldexp(m, -(int)d));
+          exp2[q] = oe;
+        } else {
+          const int64_t d = e - oe;
+          mant[q] = m + (d > 1100 ? 0.0 : ldexp(om, -(int)d));
+          exp2[q] = e;
+        }
+      }
+      out_flags[q] |= f;
+    } else {
+      mant[q] = m;
+      exp2[q] = e;
+      out_flags[q] = f;
+    }
   }
 }
 

@@ -221,6 +221,7 @@ bool build_tree(const Network &net, const std::vector<int32_t> &order, int32_t r
     T.push_back(t);
   }
   for (int32_t x = 0; x < net.n_vars; ++x) {
+    if (!net.sliced.empty() && net.sliced[(size_t)x]) continue;  // a factor of the slice, not a leaf
     TensorInfo t;
     t.labels = {x};
     t.kind = LEAF_WEIGHT;
@@ -376,8 +377,85 @@ void assign_roundings(Candidate &c, int32_t precision) {
 }
 }  // namespace
 
+// Index slicing (Alg. 3): fixes variables one at a time until the best
+// plan's largest tensor has at most `target` indices.  Each round picks the
+// variable whose tensors in the current best tree weigh most (the sum of
+// 2^rank over the tensors holding it: what fixing it halves), removes it
+// from every clause (recording the literal in the clause's slice bits) and
+// plans again.  At most kMaxSliceVars variables.
+static constexpr int kMaxSliceVars = 24;
+
+static int best_candidate(const Network &net, const wmc_plan_opts &opts, int32_t cap, Candidate &best);
+static int plan_unsliced(const Network &net, const wmc_plan_opts &opts, int32_t cap, Plan &plan);
+
+static int choose_slices(const Network &net, const wmc_plan_opts &opts, int32_t target, Network &work,
+                         std::vector<int32_t> &slice_vars) {
+  work = net;
+  work.sliced.assign((size_t)net.n_vars, 0);
+  slice_vars.clear();
+  for (;;) {
+    Candidate probe;
+    int rc = best_candidate(work, opts, 62, probe);
+    if (rc) return rc;
+    if (probe.max_rank <= target) return WMC_OK;
+    if ((int)slice_vars.size() >= kMaxSliceVars) {
+      set_error("slicing %d variables leaves a tensor of rank %d (target %d)", kMaxSliceVars, probe.max_rank, target);
+      return WMC_EPLAN_TOO_BIG;
+    }
+    std::vector<double> score((size_t)net.n_vars, 0.0);
+    for (const TensorInfo &t : probe.tensors)
+      for (int32_t v : t.labels) score[(size_t)v] += std::ldexp(1.0, (int)t.labels.size());
+    int32_t best = -1;
+    for (int32_t v = 0; v < net.n_vars; ++v)
+      if (!work.sliced[(size_t)v] && score[(size_t)v] > 0 && (best < 0 || score[(size_t)v] > score[(size_t)best]))
+        best = v;
+    if (best < 0) {
+      set_error("no variable left to slice (largest tensor rank %d, target %d)", probe.max_rank, target);
+      return WMC_EPLAN_TOO_BIG;
+    }
+    const uint32_t kbit = 1u << slice_vars.size();
+    for (Clause &c : work.clauses) {
+      auto it = std::find(c.vars.begin(), c.vars.end(), best);
+      if (it == c.vars.end()) continue;
+      const size_t j = (size_t)(it - c.vars.begin());
+      const uint64_t fv = (c.fals >> j) & 1ull;
+      const uint64_t low = c.fals & ((1ull << j) - 1ull);
+      c.fals = low | ((c.fals >> (j + 1)) << j);
+      c.vars.erase(it);
+      c.smask |= kbit;
+      if (fv) c.sfals |= kbit;
+    }
+    work.sliced[(size_t)best] = 1;
+    slice_vars.push_back(best);
+  }
+}
+
 int build_plan(const Network &net, const wmc_plan_opts &opts, Plan &plan) {
   const int32_t cap = opts.max_rank_cap > 0 ? opts.max_rank_cap : 30;
+  if (opts.slice_to_rank > 0) {
+    Network work;
+    std::vector<int32_t> slice_vars;
+    int rc;
+    try {
+      rc = choose_slices(net, opts, std::min(opts.slice_to_rank, cap), work, slice_vars);
+    } catch (const std::bad_alloc &) {
+      set_error("out of host memory while slicing");
+      return WMC_ENOMEM;
+    }
+    if (rc) return rc;
+    rc = plan_unsliced(work, opts, cap, plan);
+    if (rc) return rc;
+    plan.slice_vars = slice_vars;
+    plan.w_pos = net.w_pos;  // the sliced variables' weights enter as factors
+    plan.w_neg = net.w_neg;
+    return WMC_OK;
+  }
+  return plan_unsliced(net, opts, cap, plan);
+}
+
+// The best tree over the portfolio of elimination orders (lowest max rank,
+// then lowest cost) whose tensors stay within `cap` indices.
+static int best_candidate(const Network &net, const wmc_plan_opts &opts, int32_t cap, Candidate &best) {
   std::vector<std::pair<int32_t, std::vector<int32_t>>> orders;
   try {
     if (opts.ordering == WMC_ORDER_GIVEN) {
@@ -405,7 +483,6 @@ int build_plan(const Network &net, const wmc_plan_opts &opts, Plan &plan) {
         orders.push_back({WMC_ORDER_MINDEGREE, order_min_degree(n, adj)});
       if (orders.empty()) { set_error("unknown ordering %d", opts.ordering); return WMC_EINVAL; }
     }
-    Candidate best;
     bool have = false;
     for (auto &o : orders) {
       Candidate c;
@@ -420,6 +497,18 @@ int build_plan(const Network &net, const wmc_plan_opts &opts, Plan &plan) {
       set_error("no elimination order keeps every tensor within rank %d", cap);
       return WMC_EPLAN_TOO_BIG;
     }
+  } catch (const std::bad_alloc &) {
+    set_error("out of host memory while planning");
+    return WMC_ENOMEM;
+  }
+  return WMC_OK;
+}
+
+static int plan_unsliced(const Network &net, const wmc_plan_opts &opts, int32_t cap, Plan &plan) {
+  try {
+    Candidate best;
+    int rc = best_candidate(net, opts, cap, best);
+    if (rc) return rc;
     normalise_ids(best);
     assign_layouts(best);
     assign_roundings(best, opts.precision);

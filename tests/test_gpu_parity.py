@@ -527,3 +527,112 @@ def test_small_phase_matches_per_node_launches(w, precision, case):
     for q in (0, Q - 1):
         want = oracle.bucket_elim(cnf, wq[q], wnq[q], order=order)
         assert rel(b[q], want) <= TOL[precision]
+
+
+# ------------------------------------------------------ index slicing (Alg. 3)
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_sliced_walk_matches_unsliced(w, precision):
+    """Index slicing: the walk runs once per slice assignment with the sliced
+    variables fixed (clauses their literals satisfy become ones, their
+    weights multiply the root) and the results are summed (Thm 4.2); the sum
+    equals the unsliced walk and the oracle for several queries."""
+    cnf = wmcgen.random_kcnf(20, 60, seed=2)
+    Q = 3
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=13, lo=0.1, hi=0.9)
+    full = plan_for(w, cnf, None, None, precision).execute(wq, wnq)
+    r0 = plan_for(w, cnf, None, None, precision).info(1).max_rank
+    sliced = plan_for(w, cnf, None, None, precision, slice_to_rank=r0 - 4)
+    assert sliced.info(1).n_slice_vars >= 2
+    got = sliced.execute(wq, wnq)
+    for q in range(Q):
+        want = oracle.brute_force(cnf, wq[q], wnq[q])[0]
+        assert rel(got[q], want) <= TOL[precision], q
+        assert Big(got[q].mant, got[q].exp2).rel_diff(Big(full[q].mant, full[q].exp2)) <= 2 * TOL[precision]
+        assert rel(got[q], want) <= got[q].rel_err_bound  # the stated bound holds
+
+
+def test_sliced_unweighted_count_is_exact(w):
+    """Unit weights in FP64: the sliced count is the exact model count."""
+    cnf = wmcgen.random_kcnf(20, 60, seed=5)
+    exact = oracle.count_exact(cnf)
+    r0 = w.Plan(w.Network.from_cnf(cnf), precision=FP64).info(1).max_rank
+    plan = w.Plan(w.Network.from_cnf(cnf), precision=FP64, slice_to_rank=r0 - 3)
+    assert plan.info(1).n_slice_vars >= 2
+    r = plan.execute()[0]
+    assert r.to_float() == float(exact)
+    assert r.flags & w.WMC_FLAG_EXACT_INT
+
+
+def test_slice_ranges_sum_to_the_whole(w):
+    """Partial sums over disjoint slice ranges (one per process in a sharded
+    run) combine to the full result; an empty range is zero."""
+    cnf = wmcgen.random_kcnf(30, 90, seed=1)
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, 2, seed=3, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, FP32, slice_to_rank=16)
+    n = 1 << plan.info(1).n_slice_vars
+    assert n >= 4
+    whole = plan.execute(wq, wnq)
+    cuts = [0, 1, n // 2, n]
+    parts = [plan.execute_slices(cuts[i], cuts[i + 1], wq, wnq) for i in range(3)]
+    assert plan.execute_slices(2, 2, wq, wnq)[0].mant == 0.0
+    for q in range(2):
+        tot = w.combine_results([p[q] for p in parts])
+        assert Big(tot.mant, tot.exp2).rel_diff(Big(whole[q].mant, whole[q].exp2)) <= 1e-12
+    with pytest.raises(w._abi.WmcError) as e:
+        plan.execute_slices(0, n + 1, wq, wnq)
+    assert e.value.status == w.WMC_EINVAL
+
+
+def test_sliced_psi_beyond_the_rank_cap(w):
+    """psi(34) has no plan within rank 30; sliced to 28 it runs and gives
+    the closed form prod(w0 + w1) - prod(w1) - prod(w0)."""
+    from fractions import Fraction
+    n = 34
+    cnf = wmcgen.psi_family(n)
+    wp, wn = wmcgen.weights_complementary(n, 7, 0.2, 0.8)
+    plan = plan_for(w, cnf, wp, wn, FP64, slice_to_rank=28)
+    r = plan.execute()[0]
+    fp = [Fraction(float(x)) for x in wp]
+    fn = [Fraction(float(x)) for x in wn]
+    pa, p1, p0 = Fraction(1), Fraction(1), Fraction(1)
+    for a, b in zip(fp, fn):
+        pa *= a + b
+        p1 *= a
+        p0 *= b
+    want = pa - p1 - p0
+    import math
+    e = want.numerator.bit_length() - want.denominator.bit_length()
+    mant = float(want / Fraction(2) ** e) if e >= 0 else float(want * Fraction(2) ** (-e))
+    m, fe = math.frexp(mant)
+    assert Big(r.mant, r.exp2).rel_diff(Big(m, e + fe)) <= TOL[FP64]
+
+
+def test_sliced_device_path_and_server(w):
+    """The device entry and the server run every slice too."""
+    cnf = wmcgen.random_kcnf(30, 90, seed=1)
+    Q = 4
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=5, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, FP32, slice_to_rank=16)
+    host = plan.execute(wq, wnq)
+    info = plan.info(Q)
+    dwp = torch.from_numpy(wq).cuda(); dwn = torch.from_numpy(wnq).cuda()
+    ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device="cuda")
+    m = torch.empty(Q, dtype=torch.float64, device="cuda"); e = torch.empty(Q, dtype=torch.int64, device="cuda")
+    f = torch.empty(Q, dtype=torch.int32, device="cuda")
+    plan.execute_device(Q, dwp, dwn, ws, m, e, f, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for q in range(Q):
+        assert Big(*_norm_pair(float(m[q]), int(e[q]))).rel_diff(Big(host[q].mant, host[q].exp2)) == 0.0
+    srv = w.Server(plan, max_batch=4, max_waves=2)
+    ts = srv.submit_many(wq, wnq)
+    for q, t in enumerate(ts):
+        r = srv.wait(t, timeout_s=60)
+        assert (r.mant, r.exp2) == (host[q].mant, host[q].exp2)
+    srv.close()
+
+
+def _norm_pair(mant, e):
+    import math
+    fm, fe = math.frexp(mant)
+    return fm, (e + fe) if mant != 0.0 else 0

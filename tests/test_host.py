@@ -3,6 +3,8 @@ symbol is exported, the reduction matches Thm 3.2's structure, the planner's
 contraction tree is a valid tree whose evaluation (done here in numpy, from
 the tree the library reports) equals the oracle, and malformed input is
 rejected with the documented status codes."""
+import ctypes
+import math
 import os
 import re
 import subprocess
@@ -212,3 +214,59 @@ def test_bounds_check_of_every_launch(Q):
             rc = w.wmc_debug_check_bounds(plan.handle, Q, ctypes.byref(n))
             assert rc == 0, w.wmc_last_error()
             assert n.value > 0
+
+
+def test_slicing_plan_meets_its_target():
+    """Index slicing (Alg. 3): the planner fixes variables until the largest
+    tensor fits the target; the sliced variables are distinct, appear in no
+    leaf, and every launch of the sliced walk stays in bounds."""
+    w = _lib()
+    cnf = wmcgen.random_kcnf(20, 60, seed=0)
+    base = w.Plan(w.Network.from_cnf(cnf), precision=w.WMC_FP64)
+    r0 = base.info(1).max_rank
+    assert base.info(1).n_slice_vars == 0
+    same = w.Plan(w.Network.from_cnf(cnf), precision=w.WMC_FP64, slice_to_rank=r0)
+    assert same.info(1).n_slice_vars == 0  # already within the target
+    for target in (r0 - 2, r0 - 5):
+        p = w.Plan(w.Network.from_cnf(cnf), precision=w.WMC_FP64, slice_to_rank=target)
+        info = p.info(1)
+        sv = p.slice_vars
+        assert info.max_rank <= target and 0 < len(sv) == info.n_slice_vars
+        assert len(set(sv)) == len(sv) and all(0 <= v < 20 for v in sv)
+        for kind, labels, _ in p.leaves():
+            assert not set(labels) & set(sv)
+        for Q in (1, 4):
+            n = ctypes.c_int64()
+            assert w.wmc_debug_check_bounds(p.handle, Q, ctypes.byref(n)) == w.WMC_OK, w.wmc_last_error()
+
+
+def test_slicing_makes_a_too_wide_formula_plannable():
+    """psi with 34 literals per clause has rank-34 clause tensors: no plan
+    within rank 30; slicing to 28 fixes 6 variables (64 slices)."""
+    w = _lib()
+    net = w.Network.from_cnf(wmcgen.psi_family(34))
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net)
+    assert e.value.status == w.WMC_EPLAN_TOO_BIG
+    p = w.Plan(net, slice_to_rank=28)
+    assert p.info(1).max_rank <= 28 and p.info(1).n_slice_vars == 6
+
+
+def test_slice_ranges_and_combination():
+    """slice_range splits [0, n) into contiguous per-process ranges that
+    cover it once; combine_results sums exponent-aligned values."""
+    w = _lib()
+    for n in (1, 2, 7, 64):
+        for world in (1, 2, 3, 8):
+            rs = [w.slice_range(n, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+    R = w.Result
+    parts = [R(0.75, 10, 0, 0, 0.0), R(0.5, -3, 0, 2, 1e-9), R(0.0, 0, 0, 0, 0.0), R(0.625, 12, 0, 0, 0.0)]
+    tot = w.combine_results(parts)
+    want = 0.75 * 2 ** 10 + 0.5 * 2 ** -3 + 0.625 * 2 ** 12
+    assert math.isclose(tot.to_float(), want, rel_tol=1e-15)
+    assert tot.flags == 2 and tot.rel_err_bound >= 1e-9
+    tiny = w.combine_results([R(0.5, -5000, 0, 0, 0.0), R(0.5, -5001, 0, 0, 0.0)])
+    assert (tiny.mant, tiny.exp2) == (0.75, -5000)
+    assert w.combine_results([]).mant == 0.0

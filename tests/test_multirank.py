@@ -49,3 +49,66 @@ def test_two_cpu_ranks_shard_the_pool():
         assert len(first) == 16
         assert all(x % 256 == 0 for x in a + b)
         assert set(a[:8]).isdisjoint(set(b[:8]))
+
+
+def _slice_rank(rank, world, port, q):
+    """One CPU rank of the sliced count: its share of the slice assignments
+    (product code: slice_range), the share's value from the oracle on the
+    conditioned formulas (test side), the shares gathered and summed with
+    the product's combine_results."""
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    import wmcgen
+    from paper_2006_15512_b300 import Result, combine_results, slice_range
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cnf = wmcgen.random_kcnf(14, 40, seed=4)
+    wp, wn = wmcgen.weights_complementary(14, 4, 0.1, 0.9)
+    sliced = [2, 5, 9]  # 0-based variables; slice bit k fixes sliced[k]
+    lo, hi = slice_range(1 << len(sliced), rank, world)
+    parts = []
+    for eta in range(lo, hi):
+        # conditioning (Thm 4.2): the weight of the other value is zero
+        cwp, cwn = wp.copy(), wn.copy()
+        for k, v in enumerate(sliced):
+            if (eta >> k) & 1:
+                cwn[v] = 0.0
+            else:
+                cwp[v] = 0.0
+        b = oracle.brute_force(cnf, cwp, cwn)[0]
+        parts.append(Result(b.mant, b.exp2, 0.0, 0, 0.0))
+    share = combine_results(parts)
+    got = [None] * world
+    dist.all_gather_object(got, (lo, hi, share.mant, share.exp2))
+    total = combine_results([Result(m, e, 0.0, 0, 0.0) for (_, _, m, e) in got])
+    full = oracle.brute_force(cnf, wp, wn)[0]
+    q.put((rank, [(a, b) for (a, b, _, _) in got], total.mant, total.exp2, full.mant, full.exp2))
+    dist.destroy_process_group()
+
+
+def test_two_cpu_ranks_shard_the_slices():
+    """Index slicing across processes (Alg. 3, Thm 4.2): two gloo ranks take
+    disjoint halves of the 2^3 slice assignments and the exponent-aligned
+    sum of their shares equals the unsliced count."""
+    import socket
+    import torch.multiprocessing as mp
+    from oracle import Big
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slice_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ranges, m, e, fm, fe in out:
+        assert ranges == [(0, 4), (4, 8)]
+        assert Big(m, e).rel_diff(Big(fm, fe)) <= 1e-14
