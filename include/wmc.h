@@ -363,6 +363,11 @@ void wmc_set_small_phase(int32_t on);
  * dependent launches, so that each one's set-up overlaps the tail of the
  * launch before it.  Affects graphs captured after the call. */
 void wmc_set_dependent_launch(int32_t on);
+/* Execution option (default on): wmc_contract_pair runs float32 dense
+ * products with at least 2^7 rows, 2^7 columns and 2^5 summed terms on the
+ * tensor cores (tcgen05, 3xTF32, float32 accumulation); off, on the
+ * scalar tiled kernel.  The two agree within float32 rounding. */
+void wmc_set_tensor_cores(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,

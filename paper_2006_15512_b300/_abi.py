@@ -136,6 +136,7 @@ EXPORTS = {
     "wmc_set_fusion": (None, [c_i32]),
     "wmc_set_small_phase": (None, [c_i32]),
     "wmc_set_dependent_launch": (None, [c_i32]),
+    "wmc_set_tensor_cores": (None, [c_i32]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

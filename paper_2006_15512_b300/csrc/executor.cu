@@ -38,6 +38,7 @@ static std::atomic<int32_t> g_debug_stall{0};
 static std::atomic<int32_t> g_fuse{4};
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
+static std::atomic<int32_t> g_tensor_cores{1};  // dense float32 pair contractions on tcgen05
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
@@ -45,6 +46,7 @@ extern "C" void wmc_debug_stall_copies(int32_t on) { g_debug_stall.store(on); }
 extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
 extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
+extern "C" void wmc_set_tensor_cores(int32_t on) { g_tensor_cores.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -1807,6 +1809,19 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
   dev::K4Params p4;
   if (!k2 && try_k4(LA, LB, LC, f64, p4)) {
     p4.A = a; p4.B = b; p4.C = c; p4.ma = ma; p4.mb = mb; p4.mc = mc;
+    // float32 with 128 x 128 output tiles and 32-term chunks: the tensor cores
+    if (!f64 && g_tensor_cores.load() && p4.ni >= 7 && p4.nj >= 7 && p4.ns >= 5) {
+      static bool attr = false;
+      if (!attr) {
+        CUDA_TRY(cudaFuncSetAttribute(dev::k4_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kTcSmem));
+        attr = true;
+      }
+      const unsigned tiles = 1u << (p4.ni - 7 + p4.nj - 7 + p4.nb);
+      dev::k4_tc<<<tiles, dev::kTcThreads, dev::kTcSmem, s>>>(p4, nullptr);
+      g_launches.fetch_add(1);
+      CUDA_TRY(cudaGetLastError());
+      return WMC_OK;
+    }
     const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
     // few output tiles and a long summed range: split the range into
     // groups of whole 256-term blocks, each group's partials in stream-

@@ -1405,6 +1405,228 @@ __global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
+// ------------------------------------------------ K4 on the tensor cores
+//
+// The dense batched product of K4 in float32 on the 5th-generation tensor
+// cores (tcgen05, kind::tf32) with the 3xTF32 split: every operand value x
+// is staged as hi = x with the low 13 mantissa bits cleared (exactly a
+// TF32 value) and lo = x - hi (exact in float32, TF32 to within a few
+// bits), and C += A_hi.B_hi + A_hi.B_lo + A_lo.B_hi accumulates in float32
+// in tensor memory: about float32 accuracy for a tensor-core rate.
+//
+// A block owns a 128 x 128 output tile (128 values of i, 128 of j, one
+// batch assignment).  Its 128 threads gather each 32-term chunk of the
+// summed range from the operands' bit-scattered layouts into shared
+// memory, already split, in the canonical K-major layout without swizzle
+// (8 x 16-byte core matrices: 128 bytes between neighbours along K, 1024
+// between 8-row groups); one elected thread issues the 12 MMAs of the
+// chunk (4 steps of K = 8, 3 products each) and commits them to the
+// stage's mbarrier, so the next chunk's gather overlaps the MMAs (two
+// stages).  The accumulator (128 lanes x 128 columns of tensor memory) is
+// read back with tcgen05.ld, staged through shared memory and written
+// with C's fast index along the threads.  Waits are bounded by
+// %globaltimer; on timeout the block records the error, waits (bounded)
+// for its own MMAs and frees its tensor memory.  The summation order
+// differs from the scalar kernels: results agree within float32 rounding,
+// not bit for bit.
+
+constexpr int kTcM = 128, kTcN = 128, kTcK = 32, kTcThreads = 256;
+constexpr uint32_t kTcTile = (uint32_t)kTcM * kTcK * 4;  // bytes of one operand tile (16 KB)
+constexpr uint32_t kTcStage = 4 * kTcTile;               // A_hi, A_lo, B_hi, B_lo
+constexpr uint32_t kTcSmem = 2 * kTcStage;               // two stages (128 KB), reused for C
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
+  // start address, leading byte offset (neighbour core matrix along K),
+  // stride byte offset (next 8-row group), descriptor version 1, no swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((128u >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((1024u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// kind::tf32 instruction descriptor: float32 accumulator, TF32 A and B,
+// both K-major, N = 128, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// byte offset of element (row m, k) of a 128 x 32 operand tile
+__device__ __forceinline__ uint32_t tc_off(uint32_t m, uint32_t k) {
+  return (m >> 3) * 1024u + (k >> 2) * 128u + (m & 7u) * 16u + (k & 3u) * 4u;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k4_tc(K4Params p, uint32_t *err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long mma_done[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ uint32_t offA_i[kTcM], offB_j[kTcN], offC_i[kTcM], offC_j[kTcN];
+  __shared__ uint32_t offA_s[kTcK], offB_s[kTcK];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  __shared__ int s_fail;
+  const float *A = (const float *)p.A;
+  const float *B = (const float *)p.B;
+  float *C = (float *)p.C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t i_tiles = 1u << (p.ni - 7), j_tiles = 1u << (p.nj - 7);
+  const uint32_t tile = blockIdx.x;
+  const uint32_t it = tile % i_tiles, jt = (tile / i_tiles) % j_tiles, bb = tile / (i_tiles * j_tiles);
+  for (int x = threadIdx.x; x < kTcM; x += blockDim.x) {
+    offA_i[x] = scatter_bits((uint32_t)x, p.iA, 7);
+    offC_i[x] = scatter_bits((uint32_t)x, p.iC, 7);
+    offB_j[x] = scatter_bits((uint32_t)x, p.jB, 7);
+    offC_j[x] = scatter_bits((uint32_t)x, p.jC, 7);
+  }
+  for (int x = threadIdx.x; x < kTcK; x += blockDim.x) {
+    offA_s[x] = scatter_bits((uint32_t)x, p.sA, 5);
+    offB_s[x] = scatter_bits((uint32_t)x, p.sB, 5);
+  }
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  if (threadIdx.x == 0) {
+    mbar_init(&mma_done[0], 1);
+    mbar_init(&mma_done[1], 1);
+    mbar_fence_init();
+    s_fail = 0;
+  }
+  if (warp == 0) {  // 128 columns of tensor memory: the 128 x 128 float32 accumulator
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                 "r"((uint32_t)kTcN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t baseA = scatter_bits(it, p.iA + 7, p.ni - 7) | scatter_bits(bb, p.bA, p.nb);
+  const uint32_t baseB = scatter_bits(jt, p.jB + 7, p.nj - 7) | scatter_bits(bb, p.bB, p.nb);
+  const uint32_t baseC = scatter_bits(it, p.iC + 7, p.ni - 7) | scatter_bits(jt, p.jC + 7, p.nj - 7) |
+                         scatter_bits(bb, p.bC, p.nb);
+  const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
+  const float sa = operand_scale<float>(p.ma, q, p.mc.scale_inputs);
+  const float sb = operand_scale<float>(p.mb, q, p.mc.scale_inputs);
+  const uint32_t smem0 = smem_addr(tc_smem);
+  const uint32_t n_chunks = 1u << (p.ns - 5);
+  bool ok = true;
+  uint32_t issued = 0;  // chunks whose MMAs were committed
+  for (uint32_t c = 0; c < n_chunks; ++c) {
+    const uint32_t st = c & 1u;
+    if (c >= 2 && !__syncthreads_and(mbar_wait(&mma_done[st], ((c >> 1) - 1) & 1) ? 1 : 0)) { ok = false; break; }
+    unsigned char *stage = tc_smem + st * kTcStage;
+    const uint32_t hiA = scatter_bits(c, p.sA + 5, p.ns - 5), hiB = scatter_bits(c, p.sB + 5, p.ns - 5);
+    // gather, scale, split: each thread's 16 values of A and 16 of B are
+    // all requested before any is used (the loads overlap in flight)
+    constexpr int kPer = kTcM * kTcK / kTcThreads;
+    float va[kPer], vb[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const uint32_t x = threadIdx.x + (uint32_t)t * kTcThreads;
+      const uint32_t m = p.a_i_fast ? x % kTcM : x / kTcK, k = p.a_i_fast ? x / kTcM : x % kTcK;
+      va[t] = __ldg(A + (baseA | hiA | offA_i[m] | offA_s[k]));
+      const uint32_t n = p.b_j_fast ? x % kTcN : x / kTcK, k2 = p.b_j_fast ? x / kTcN : x % kTcK;
+      vb[t] = __ldg(B + (baseB | hiB | offB_j[n] | offB_s[k2]));
+    }
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+      const uint32_t x = threadIdx.x + (uint32_t)t * kTcThreads;
+      {
+        const uint32_t m = p.a_i_fast ? x % kTcM : x / kTcK, k = p.a_i_fast ? x / kTcM : x % kTcK;
+        const float v = va[t] * sa;
+        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        const uint32_t o = tc_off(m, k);
+        *reinterpret_cast<float *>(stage + o) = h;
+        *reinterpret_cast<float *>(stage + kTcTile + o) = v - h;
+      }
+      {
+        const uint32_t n = p.b_j_fast ? x % kTcN : x / kTcK, k = p.b_j_fast ? x / kTcN : x % kTcK;
+        const float v = vb[t] * sb;
+        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        const uint32_t o = tc_off(n, k);
+        *reinterpret_cast<float *>(stage + 2 * kTcTile + o) = h;
+        *reinterpret_cast<float *>(stage + 3 * kTcTile + o) = v - h;
+      }
+    }
+    fence_proxy_async_smem();  // the staged tiles, visible to the tensor cores
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem0 + st * kTcStage;
+#pragma unroll
+      for (uint32_t kk = 0; kk < (uint32_t)(kTcK / 8); ++kk) {
+        const uint64_t ahi = tc_smem_desc(a0 + kk * 256u), alo = tc_smem_desc(a0 + kTcTile + kk * 256u);
+        const uint64_t bhi = tc_smem_desc(a0 + 2 * kTcTile + kk * 256u);
+        const uint64_t blo = tc_smem_desc(a0 + 3 * kTcTile + kk * 256u);
+        tc_mma(tmem, alo, bhi, (c | kk) != 0u);
+        tc_mma(tmem, ahi, blo, 1u);
+        tc_mma(tmem, ahi, bhi, 1u);
+      }
+      tc_commit(&mma_done[st]);
+    }
+    issued = c + 1;
+  }
+  if (!ok && threadIdx.x == 0 && err) atomicOr(err, 1u);
+  // the last commit covers every MMA issued before it
+  bool done = true;
+  if (issued) {
+    const uint32_t last = issued - 1;
+    done = __syncthreads_and(mbar_wait(&mma_done[last & 1u], (last >> 1) & 1) ? 1 : 0) != 0;
+  }
+  if (!done && threadIdx.x == 0) {
+    if (err) atomicOr(err, 1u);
+    s_fail = 1;
+  }
+  tc_fence_after();
+  if (ok && done) {
+    // accumulator rows (lanes 32 w .. 32 w + 31) to shared memory, 32 columns at a time
+    float *Cs = reinterpret_cast<float *>(tc_smem);  // [128][129]
+    // warp w reads its lane quarter (w mod 4) of the accumulator, half the columns
+    const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
+    const uint32_t row = quarter * 32u + (uint32_t)lane;
+#pragma unroll 1
+    for (uint32_t col = half * (kTcN / 2); col < (half + 1) * (kTcN / 2); col += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((quarter * 32u) << 16) + col;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+          "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 32; ++k) Cs[row * (kTcN + 1) + col + (uint32_t)k] = __uint_as_float(r[k]);
+    }
+    __syncthreads();
+    float tmax = 0.f, tmin = INFINITY;
+    for (uint32_t x = threadIdx.x; x < (uint32_t)(kTcM * kTcN); x += blockDim.x) {
+      const uint32_t m = p.c_i_fast ? x % kTcM : x / kTcN, n = p.c_i_fast ? x / kTcM : x % kTcN;
+      const float v = Cs[m * (kTcN + 1) + n];
+      C[baseC | offC_i[m] | offC_j[n]] = v;
+      track(v, tmax, tmin);
+    }
+    publish(smax, smin, q, tmax, tmin);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTcN)
+                 : "memory");
+  if (!s_fail) finish_meta<float>(p.ma, p.mb, p.mc, smax, smin);
+}
+
 // ------------------------------------------------------ small-node phase
 //
 // Every node whose whole subtree is small (bucket products of clause

@@ -636,3 +636,27 @@ def _norm_pair(mant, e):
     import math
     fm, fe = math.frexp(mant)
     return fm, (e + fe) if mant != 0.0 else 0
+
+
+# dense float32 products with 2^7 x 2^7 output tiles: the tcgen05 kernel
+SWEEP_TC = [(13, 13, 1, 5), (16, 15, 0, 8), (17, 17, 2, 6), (15, 16, 1, 7)]
+
+
+@pytest.mark.parametrize("ra,rb,b,k", SWEEP_TC)
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_pair_tensor_cores(w, ra, rb, b, k, shuffle):
+    """Dense float32 products on the tensor cores (tcgen05, 3xTF32): every
+    output against direct long-double summation, and against the scalar
+    tiled kernel, within float32 rounding of the two summation orders."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=ra * 100 + rb + 31 * k, shuffle=shuffle)
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c)
+    got = _run_pair(w, case, FP32)
+    try:
+        w.wmc_set_tensor_cores(0)
+        scalar = _run_pair(w, case, FP32)
+    finally:
+        w.wmc_set_tensor_cores(1)
+    # 3 MMAs per 8-term step into a float32 accumulator, 2^-21 per product
+    tol = (3 * (2 ** k) / 8 + 8) * 2.0 ** -24 + 2.0 ** -21
+    assert (np.abs(got - want) / np.abs(want)).max() <= tol
+    assert (np.abs(got - scalar) / np.abs(scalar)).max() <= tol + _pair_tol(k, FP32)
