@@ -76,6 +76,16 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def tf32_peak():
+    """Dense TF32 tensor peak (TFLOP/s): the measured bf16 burst GEMM rate
+    times the nominal TF32/bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal TF32/bf16"
+    except Exception:
+        return 1800.0 * 1.1 / 2.25, "fallback bf16 x nominal TF32/bf16"
+
+
 def workload():
     cnf = wmcgen.grid_cnf(GRID_H, GRID_W, GRID_SEED)
     wq, wnq = wmcgen.query_weights(cnf.n_vars, POOL, seed=1, lo=0.05, hi=0.95)
@@ -452,7 +462,8 @@ def run_other(args):
                          "log10": r.log10, "max_rank": info.max_rank, "stated_bound": r.rel_err_bound}
     elif args.workload == "sweep":
         rows = []
-        for (ra, rb, b, k) in [(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)]:
+        tf32 = tf32_peak()
+        for (ra, rb, b, k) in args.sweep_rows:
             case = wmcgen.pair_case(ra, rb, b, k, seed=7 + ra + rb + k, shuffle=False)
             rc = len(case.labels_c)
             A = torch.from_numpy(case.a).cuda(); B = torch.from_numpy(case.b).cuda()
@@ -472,9 +483,17 @@ def run_other(args):
             t32 = _timed(f32, 3)
             n_el = (1 << ra) + (1 << rb) + (1 << rc)
             flops = 2.0 * (1 << (rc + k))
-            rows.append({"rank_a": ra, "rank_b": rb, "batch": b, "summed": k,
-                         "fp64_ms": t64 * 1e3, "fp64_GBs": 8 * n_el / t64 / 1e9, "fp64_GFLOPs": flops / t64 / 1e9,
-                         "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9})
+            row = {"rank_a": ra, "rank_b": rb, "batch": b, "summed": k,
+                   "fp64_ms": t64 * 1e3, "fp64_GBs": 8 * n_el / t64 / 1e9, "fp64_GFLOPs": flops / t64 / 1e9,
+                   "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9}
+            n_free_a, n_free_b = ra - b - k, rb - b - k
+            if n_free_a >= 7 and n_free_b >= 7 and k >= 4:
+                # tensor-core path: three TF32 products per float32 product
+                row["fp32_kernel"] = "k4_tc (tcgen05, 3xTF32)"
+                row["tensor_frac_of_tf32_peak"] = 3 * flops / t32 / 1e12 / tf32[0]
+                row["tf32_peak_tflops"] = tf32[0]
+                row["tf32_peak_source"] = tf32[1]
+            rows.append(row)
             del A, B, A32, B32, C32
             torch.cuda.empty_cache()
         out["rows"] = rows
@@ -543,6 +562,9 @@ def main():
     ap.add_argument("--workload", default="serving",
                     choices=["serving", "random3cnf", "grid", "sweep", "uneven"])
     ap.add_argument("--n-formulas", type=int, default=512)
+    ap.add_argument("--sweep-rows", type=lambda x: [tuple(int(v) for v in r.split(",")) for r in x.split(";")],
+                    default=[(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)],
+                    help="sweep cases 'rank_a,rank_b,batch,summed;...'")
     ap.add_argument("--only-waves", action="store_true",
                     help="run the warm-up and timed waves only (profiling driver)")
     args = ap.parse_args()

@@ -235,11 +235,14 @@ int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q,
 /* One pairwise contraction C = A . B (Eq. (1) on the network {A, B}; the
  * matrix-multiplication view of Sec. 4.2), on device memory, asynchronous on
  * `stream`.  Kernel choice: the streaming kernel when one operand is small,
- * a tiled dense kernel when the node is a batched matrix product with at
- * least 2^6 values on each free side and 2^5 summed values (its summed
- * range is split across blocks when there are few output tiles; the
- * partials then live in stream-ordered scratch, cudaMallocAsync), the
- * generic kernel otherwise.  Bit j of a tensor's linear offset is index labels_x[j];
+ * a dense kernel when the node is a batched matrix product with at least
+ * 2^6 values on each free side and 2^5 summed values (float32 with at least
+ * 2^7 per free side and 2^4 summed values: the tensor-core kernel, see
+ * wmc_set_tensor_cores; otherwise a tiled scalar kernel whose summed range
+ * is split across blocks when there are few output tiles), the generic
+ * kernel otherwise.  The tensor-core kernel's packed operands (8 bytes per
+ * operand entry) and the split partial sums live in stream-ordered scratch
+ * from a memory pool of the library's own, which keeps up to 8 GiB cached.  Bit j of a tensor's linear offset is index labels_x[j];
  * every index has extent 2.  Indices of C must appear in A or B; indices of
  * A or B absent from C are summed; an index in A, B and C is a batch index.
  * precision WMC_FP64: a, b, c are float64.  WMC_SCALED_FP32: a, b, c are
@@ -364,9 +367,12 @@ void wmc_set_small_phase(int32_t on);
  * launch before it.  Affects graphs captured after the call. */
 void wmc_set_dependent_launch(int32_t on);
 /* Execution option (default on): wmc_contract_pair runs float32 dense
- * products with at least 2^7 rows, 2^7 columns and 2^5 summed terms on the
- * tensor cores (tcgen05, 3xTF32, float32 accumulation); off, on the
- * scalar tiled kernel.  The two agree within float32 rounding. */
+ * products with at least 2^7 rows, 2^7 columns and 2^4 summed terms on the
+ * tensor cores (tcgen05, 3xTF32 with float32 accumulation: each operand is
+ * packed once, scaled and split into TF32 hi and lo parts, then a
+ * persistent kernel multiplies 128 x 256 (or 128 x 128) output tiles);
+ * off, on the scalar tiled kernel.  The two agree within float32 rounding,
+ * not bit for bit. */
 void wmc_set_tensor_cores(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index

@@ -247,7 +247,7 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   // one summation order for every kernel and batch size: ascending label
   std::sort(summed.begin(), summed.end());
   const int k = (int)summed.size(), f = (int)freeS.size();
-  if (k > 3 || f > 3 || LS.size() > 16) return false;
+  if (k > 4 || f > 4 || LS.size() > 16) return false;
   std::memset(&p, 0, sizeof(p));
   p.k = k;
   p.f = f;
@@ -256,7 +256,8 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   for (int32_t l : freeS) insC.push_back(pos_of(LC, l));
   std::sort(insA.begin(), insA.end());
   std::sort(insC.begin(), insC.end());
-  const int want_v = f64 ? 1 : 2;
+  // four summed or four S-free bits: one lane per thread (registers)
+  const int want_v = std::max(k, f) == 4 ? 0 : (f64 ? 1 : 2);
   int vbits = want_v;
   const int rC = (int)LC.size();
   if (rC - f < vbits) vbits = 0;
@@ -324,7 +325,7 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
     p.dC[ff] = dc;
   }
   vmax = 1 << vbits;
-  kmax = std::max(k, f) <= 1 ? 1 : (std::max(k, f) <= 2 ? 2 : 3);
+  kmax = std::max(k, f) <= 1 ? 1 : (std::max(k, f) <= 2 ? 2 : (std::max(k, f) == 3 ? 3 : 4));
   fmax = kmax;
   return true;
 }
@@ -334,6 +335,7 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
 bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
                 bool f64, bool p_has_q, bool s_has_q, int32_t Qp, wmc::dev::K2TParams &tp,
                 size_t &smem) {
+  if (p2.k > 3 || p2.f > 3) return false;  // the staged variant's tables hold 8 summed assignments
   const int V = 1 << p2.vbits;
   const int J = V == 1 ? 4 : 2;  // work units per thread per tile (<= kMaxJ)
   int tb = 0;
@@ -1078,7 +1080,8 @@ template <typename T, int V>
 static void launch_k2_v(const K2Params &p, int kmax, int64_t blocks, cudaStream_t s) {
   if (kmax <= 1) launch_k2_t<T, V, 1>(p, blocks, s);
   else if (kmax == 2) launch_k2_t<T, V, 2>(p, blocks, s);
-  else launch_k2_t<T, V, 3>(p, blocks, s);
+  else if (kmax == 3) launch_k2_t<T, V, 3>(p, blocks, s);
+  else if constexpr (V == 1) launch_k2_t<T, 1, 4>(p, blocks, s);  // try_k2 gives V = 1 here
 }
 
 static void launch_k2(const Launch &l, const K2Params &p, cudaStream_t s) {
@@ -1768,6 +1771,107 @@ Plan &plan_of(wmc_plan_t *p) { return *p; }
 
 // ------------------------------------------------------------ pairwise
 
+namespace {
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 148;
+  return n;
+}
+
+// Stream-ordered scratch of pair contractions: a memory pool of the
+// library's own per device that keeps up to 8 GiB cached across
+// synchronisations (the default pool returns its memory at every one).
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it == pools.end()) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = 8ull << 30;
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+      pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// Packs one K4 operand for k4_tc: rows = its free bits (i of A, j of B).
+dev::TcPackParams tc_pack_params(const void *x, float *xp, const dev::Meta &m, const dev::OutMeta &mc,
+                                 const dev::K4Params &p4, bool is_a, int rows_log2) {
+  dev::TcPackParams q;
+  std::memset(&q, 0, sizeof(q));
+  q.X = (const float *)x;
+  q.Xp = xp;
+  q.m = m;
+  q.scale_inputs = mc.scale_inputs;
+  q.rows_log2 = rows_log2;
+  q.nr = is_a ? p4.ni : p4.nj;
+  q.ns = p4.ns;
+  q.nb = p4.nb;
+  std::memcpy(q.r_pos, is_a ? p4.iA : p4.jB, 32);
+  std::memcpy(q.s_pos, is_a ? p4.sA : p4.sB, 32);
+  std::memcpy(q.b_pos, is_a ? p4.bA : p4.bB, 32);
+  std::memcpy(q.bC, p4.bC, 32);
+  q.Qc = mc.Qc;
+  q.row_fast = is_a ? p4.a_i_fast : p4.b_j_fast;
+  return q;
+}
+
+template <int N>
+cudaError_t launch_k4_tc_n(const dev::K4Params &p4, const float *ap, const float *bp, cudaStream_t s) {
+  static bool attr = false;  // opt in to the large dynamic shared memory once
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(dev::k4_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dev::TcShape<N>::smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nlog = N == 256 ? 8 : 7;
+  const uint64_t tiles = ((uint64_t)1 << (p4.ni - 7 + p4.nj - nlog)) << p4.nb;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)num_sms());
+  dev::k4_tc<N><<<grid, dev::kTcThreads, dev::TcShape<N>::smem, s>>>(p4, ap, bp, nullptr);
+  return cudaGetLastError();
+}
+
+// C = A.B on the tensor cores: both operands packed (scaled, split into
+// TF32 hi and lo) into stream-ordered scratch, then the persistent product.
+cudaError_t launch_k4_tc(const dev::K4Params &p4, cudaStream_t s) {
+  const int nlog = p4.nj >= 8 ? 8 : 7;
+  const size_t a_elems = (size_t)1 << (p4.ni + p4.ns + p4.nb), b_elems = (size_t)1 << (p4.nj + p4.ns + p4.nb);
+  float *scratch = nullptr;
+  cudaError_t e = scratch_alloc((void **)&scratch, (a_elems + b_elems) * 2 * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  float *ap = scratch, *bp = scratch + 2 * a_elems;
+  const dev::TcPackParams pa = tc_pack_params(p4.A, ap, p4.ma, p4.mc, p4, true, 7);
+  const dev::TcPackParams pb = tc_pack_params(p4.B, bp, p4.mb, p4.mc, p4, false, nlog);
+  dev::k4_tc_pack<<<(unsigned)(a_elems / (128 * dev::kTcKC)), 256, 0, s>>>(pa);
+  dev::k4_tc_pack<<<(unsigned)(b_elems / ((size_t)(1 << nlog) * dev::kTcKC)), 256, 0, s>>>(pb);
+  g_launches.fetch_add(3);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = nlog == 8 ? launch_k4_tc_n<256>(p4, ap, bp, s) : launch_k4_tc_n<128>(p4, ap, bp, s);
+  const cudaError_t f = cudaFreeAsync(scratch, s);
+  return e != cudaSuccess ? e : f;
+}
+}  // namespace
+
+
 extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_t *labels_a,
                                  const void *a, int32_t rank_b, const int32_t *labels_b,
                                  const void *b, int32_t rank_c, const int32_t *labels_c, void *c,
@@ -1809,17 +1913,10 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
   dev::K4Params p4;
   if (!k2 && try_k4(LA, LB, LC, f64, p4)) {
     p4.A = a; p4.B = b; p4.C = c; p4.ma = ma; p4.mb = mb; p4.mc = mc;
-    // float32 with 128 x 128 output tiles and 32-term chunks: the tensor cores
-    if (!f64 && g_tensor_cores.load() && p4.ni >= 7 && p4.nj >= 7 && p4.ns >= 5) {
-      static bool attr = false;
-      if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(dev::k4_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kTcSmem));
-        attr = true;
-      }
-      const unsigned tiles = 1u << (p4.ni - 7 + p4.nj - 7 + p4.nb);
-      dev::k4_tc<<<tiles, dev::kTcThreads, dev::kTcSmem, s>>>(p4, nullptr);
-      g_launches.fetch_add(1);
-      CUDA_TRY(cudaGetLastError());
+    // float32 with at least 2^7 rows, 2^7 columns and 2^4 summed terms:
+    // the tensor cores (operands packed once, then a persistent pipeline)
+    if (!f64 && g_tensor_cores.load() && p4.ni >= 7 && p4.nj >= 7 && p4.ns >= 4) {
+      CUDA_TRY(launch_k4_tc(p4, s));
       return WMC_OK;
     }
     const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
@@ -1833,15 +1930,15 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
     void *scratch = nullptr;
     if (g) {
       const size_t bytes = ((size_t)tiles << g) * 4096 * (f64 ? 8 : 4);
-      CUDA_TRY(cudaMallocAsync(&scratch, bytes, s));
+      CUDA_TRY(scratch_alloc(&scratch, bytes, s));
       p4.partial = scratch;
     }
     if (f64) dev::k4_dense<double><<<tiles << g, 256, 0, s>>>(p4);
     else dev::k4_dense<float><<<tiles << g, 256, 0, s>>>(p4);
     g_launches.fetch_add(1);
     if (g) {
-      if (f64) dev::k4_reduce<double><<<tiles, 256, 0, s>>>(p4);
-      else dev::k4_reduce<float><<<tiles, 256, 0, s>>>(p4);
+      if (f64) dev::k4_reduce<double><<<tiles * 16, 256, 0, s>>>(p4);
+      else dev::k4_reduce<float><<<tiles * 16, 256, 0, s>>>(p4);
       g_launches.fetch_add(1);
       CUDA_TRY(cudaFreeAsync(scratch, s));
     }

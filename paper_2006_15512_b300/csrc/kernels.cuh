@@ -225,10 +225,10 @@ struct K2Params {
   int8_t seg_c[16];   // S batch bits as runs: C position of the run's low bit,
   int8_t seg_b[16];   //   S position of the run's low bit,
   int8_t seg_len[16]; //   run length (C vector lanes excluded)
-  uint32_t dA[8];   // offset of summed assignment s in P
-  uint32_t dBs[8];  // ... in S
-  uint32_t dBf[8];  // offset of S-free assignment f in S
-  uint32_t dC[8];   // ... in C
+  uint32_t dA[16];   // offset of summed assignment s in P
+  uint32_t dBs[16];  // ... in S
+  uint32_t dBf[16];  // offset of S-free assignment f in S
+  uint32_t dC[16];   // ... in C
   uint32_t dBv[4];  // offset in S of vector lane e
 };
 
@@ -258,9 +258,11 @@ __device__ __forceinline__ void vstore(T *p, const T (&r)[V]) {
 }
 
 // K (summed bits) and F (S-free bits) are compile-time upper bounds; the
-// runtime p.k / p.f select the active terms.
+// runtime p.k / p.f select the active terms.  K = F = 4 runs with one lane
+// per thread (V = 1): 16 P values, 16 scales and 16 max/min pairs.
 template <typename T, int V, int K, int F>
-__global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 ? 2 : 1))) k2_stream(K2Params p) {
+__global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && sizeof(T) == 4) ? 2 : 1)))
+    k2_stream(K2Params p) {
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
   __syncthreads();
@@ -327,7 +329,9 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 ? 2 : 1))) k2_
           if (s < ns) {
             T b[V];
             const uint32_t ob = gb + p.dBs[s] + p.dBf[f];
-            if (V > 1 && p.b_vec == 1) {
+            if constexpr (V == 1) {
+              b[0] = __ldg(B + ob);  // one lane: every S mode is this load
+            } else if (p.b_vec == 1) {
               vload<T, V>(B + ob, b);
             } else if (p.b_vec == 2) {
               const T v = __ldg(B + ob);
@@ -1272,8 +1276,12 @@ __device__ __forceinline__ uint32_t scatter_bits(uint32_t v, const int8_t *pos, 
 template <typename T>
 __global__ void __launch_bounds__(256) k4_dense(K4Params p) {
   constexpr int TI = 64, TJ = 64, TK = 32, RI = 4, RJ = 4;
-  __shared__ T As[TK][TI + 1];
-  __shared__ T Bs[TK][TJ + 1];
+  // the operand chunks, and at the end the 64 x 64 output tile
+  // (2 x 32 x 65 = 64 x 65 elements)
+  __shared__ T AB[2][TK][TI + 1];
+  T (*As)[TI + 1] = AB[0];
+  T (*Bs)[TJ + 1] = AB[1];
+  T (*Cs)[TJ + 1] = reinterpret_cast<T (*)[TJ + 1]>(&AB[0][0][0]);
   __shared__ uint32_t offA_i[TI], offB_j[TJ], offC_i[TI], offC_j[TJ];
   __shared__ uint32_t offA_s[TK], offB_s[TK];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
@@ -1364,42 +1372,57 @@ __global__ void __launch_bounds__(256) k4_dense(K4Params p) {
       for (int c = 0; c < RJ; ++c) P[(ty * RI + r) * TJ + tx * RJ + c] = acc[r][c];
     return;
   }
-  T tmax = (T)0, tmin = (T)INFINITY;
+  // the tile through shared memory, then stored with C's fast index along
+  // consecutive threads (the chunk loop ended with a barrier)
 #pragma unroll
   for (int r = 0; r < RI; ++r)
 #pragma unroll
-    for (int c = 0; c < RJ; ++c) {
-      const T v = blocked ? acc[r][c] : part[r][c];
-      C[baseC | offC_i[ty * RI + r] | offC_j[tx * RJ + c]] = v;
-      track(v, tmax, tmin);
-    }
+    for (int c = 0; c < RJ; ++c) Cs[ty * RI + r][tx * RJ + c] = blocked ? acc[r][c] : part[r][c];
+  __syncthreads();
+  T tmax = (T)0, tmin = (T)INFINITY;
+  for (int x = threadIdx.x; x < TI * TJ; x += blockDim.x) {
+    const int ii = p.c_i_fast ? x % TI : x / TJ, jj = p.c_i_fast ? x / TI : x % TJ;
+    const T v = Cs[ii][jj];
+    C[baseC | offC_i[ii] | offC_j[jj]] = v;
+    track(v, tmax, tmin);
+  }
   publish(smax, smin, q, tmax, tmin);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
 // Split summed range: C = sum over groups (in group order) of the partials.
+// 16 blocks per 64 x 64 tile, one output per thread; each thread requests
+// eight groups' partials at a time and adds them in group order.
 template <typename T>
 __global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   const uint32_t i_tiles = 1u << (p.ni - 6), j_tiles = 1u << (p.nj - 6);
   const uint32_t n_tiles = i_tiles * j_tiles << p.nb;
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = blockIdx.x >> 4;
   const uint32_t it = tile % i_tiles, jt = (tile / i_tiles) % j_tiles, bb = tile / (i_tiles * j_tiles);
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
   const uint32_t baseC = scatter_bits(it, p.iC + 6, p.ni - 6) | scatter_bits(jt, p.jC + 6, p.nj - 6) |
                          scatter_bits(bb, p.bC, p.nb);
   __syncthreads();
   const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
-  const T *P = (const T *)p.partial;
-  T tmax = (T)0, tmin = (T)INFINITY;
-  for (int x = threadIdx.x; x < 64 * 64; x += blockDim.x) {
-    const int ii = x / 64, jj = x % 64;
-    T v = (T)0;
-    for (uint32_t g = 0; g < (1u << p.groups_log2); ++g) v += P[((size_t)g * n_tiles + tile) * 4096 + x];
-    ((T *)p.C)[baseC | scatter_bits(ii, p.iC, 6) | scatter_bits(jj, p.jC, 6)] = v;
-    track(v, tmax, tmin);
+  const uint32_t x = ((blockIdx.x & 15u) << 8) | threadIdx.x;  // output within the tile
+  const uint32_t ii = x / 64, jj = x % 64;
+  const uint32_t G = 1u << p.groups_log2;
+  const T *P = (const T *)p.partial + (size_t)tile * 4096 + x;
+  const size_t gstride = (size_t)n_tiles * 4096;
+  T v = (T)0;
+  for (uint32_t g = 0; g < G; g += 8) {
+    T t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = g + u < G ? P[(size_t)(g + u) * gstride] : (T)0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (g + u < G) v += t[u];
   }
+  ((T *)p.C)[baseC | scatter_bits(ii, p.iC, 6) | scatter_bits(jj, p.jC, 6)] = v;
+  T tmax = (T)0, tmin = (T)INFINITY;
+  track(v, tmax, tmin);
   publish(smax, smin, q, tmax, tmin);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
@@ -1409,48 +1432,100 @@ __global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
 //
 // The dense batched product of K4 in float32 on the 5th-generation tensor
 // cores (tcgen05, kind::tf32) with the 3xTF32 split: every operand value x
-// is staged as hi = x with the low 13 mantissa bits cleared (exactly a
+// is stored as hi = x with the low 13 mantissa bits cleared (exactly a
 // TF32 value) and lo = x - hi (exact in float32, TF32 to within a few
 // bits), and C += A_hi.B_hi + A_hi.B_lo + A_lo.B_hi accumulates in float32
-// in tensor memory: about float32 accuracy for a tensor-core rate.
+// in tensor memory: about float32 accuracy at a tensor-core rate.
 //
-// A block owns a 128 x 128 output tile (128 values of i, 128 of j, one
-// batch assignment).  Its 128 threads gather each 32-term chunk of the
-// summed range from the operands' bit-scattered layouts into shared
-// memory, already split, in the canonical K-major layout without swizzle
-// (8 x 16-byte core matrices: 128 bytes between neighbours along K, 1024
-// between 8-row groups); one elected thread issues the 12 MMAs of the
-// chunk (4 steps of K = 8, 3 products each) and commits them to the
-// stage's mbarrier, so the next chunk's gather overlaps the MMAs (two
-// stages).  The accumulator (128 lanes x 128 columns of tensor memory) is
-// read back with tcgen05.ld, staged through shared memory and written
-// with C's fast index along the threads.  Waits are bounded by
-// %globaltimer; on timeout the block records the error, waits (bounded)
-// for its own MMAs and frees its tensor memory.  The summation order
-// differs from the scalar kernels: results agree within float32 rounding,
-// not bit for bit.
+// Two launches.  k4_tc_pack rewrites each operand once, scaled and split,
+// into blocks of (batch assignment, 128 or N rows, 16 summed terms) in the
+// canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices: 128 bytes between neighbours along K, 512 between 8-row
+// groups), hi block then lo block.  k4_tc is persistent (one block per
+// SM) and warp-specialised: warp 0 moves each chunk's A and B blocks into
+// a ring of shared-memory stages with two bulk async copies (full/empty
+// mbarriers), warp 1 owns 2 x N columns of tensor memory and issues the
+// six MMAs of a chunk (two steps of K = 8, three products each), warps
+// 2..5 read a finished 128 x N accumulator back with tcgen05.ld and write
+// C while the MMAs of the next tile go to the other accumulator.  Waits are
+// bounded by %globaltimer; on timeout the block records the error, lets
+// its copies and MMAs in flight finish (bounded) and frees its tensor
+// memory.  The summation order differs from the scalar kernels: results
+// agree within float32 rounding, not bit for bit.
 
-constexpr int kTcM = 128, kTcN = 128, kTcK = 32, kTcThreads = 256;
-constexpr uint32_t kTcTile = (uint32_t)kTcM * kTcK * 4;  // bytes of one operand tile (16 KB)
-constexpr uint32_t kTcStage = 4 * kTcTile;               // A_hi, A_lo, B_hi, B_lo
-constexpr uint32_t kTcSmem = 2 * kTcStage;               // two stages (128 KB), reused for C
+constexpr int kTcM = 128, kTcKC = 16, kTcStages = 4, kTcThreads = 192;
+constexpr uint32_t kTcRowGroup = 8u * kTcKC * 4u;  // bytes between 8-row groups (512)
+
+struct TcPackParams {
+  const float *X;           // operand (bit-scattered layout)
+  float *Xp;                // packed: [batch][row tile][chunk][hi, lo][rows x 16]
+  Meta m;                   // the operand's metadata (scale on load)
+  int32_t scale_inputs;
+  int32_t rows_log2;        // log2 rows per block (7 or 8)
+  int32_t nr, ns, nb;       // row, summed and batch bits of the operand
+  int8_t r_pos[32], s_pos[32], b_pos[32];  // bit -> position in X
+  int8_t bC[32];            // batch bit -> position in C (query lane of the block)
+  int32_t Qc;
+  int32_t row_fast;         // X's lowest (row, summed) bit is a row bit
+};
+
+// byte offset of element (row m, summed k) inside a packed rows x 16 block
+__device__ __forceinline__ uint32_t tc_off(uint32_t m, uint32_t k) {
+  return (m >> 3) * kTcRowGroup + (k >> 2) * 128u + (m & 7u) * 16u + (k & 3u) * 4u;
+}
+
+// One block per packed (batch, row tile, chunk): each thread loads four
+// consecutive summed terms of one row and stores them as one 16-byte hi
+// and one 16-byte lo vector.
+__global__ void __launch_bounds__(256) k4_tc_pack(TcPackParams p) {
+  __shared__ uint32_t off_r[256], off_s[kTcKC];
+  const uint32_t R = 1u << p.rows_log2;
+  const uint32_t n_chunks = 1u << (p.ns - 4), n_rt = 1u << (p.nr - p.rows_log2);
+  const uint32_t c = blockIdx.x % n_chunks, rt = (blockIdx.x / n_chunks) % n_rt;
+  const uint32_t bb = blockIdx.x / (n_chunks * n_rt);
+  for (uint32_t x = threadIdx.x; x < R; x += blockDim.x) off_r[x] = scatter_bits(x, p.r_pos, p.rows_log2);
+  if (threadIdx.x < kTcKC) off_s[threadIdx.x] = scatter_bits(threadIdx.x, p.s_pos, 4);
+  __syncthreads();
+  const uint32_t base = scatter_bits(rt, p.r_pos + p.rows_log2, p.nr - p.rows_log2) |
+                        scatter_bits(c, p.s_pos + 4, p.ns - 4) | scatter_bits(bb, p.b_pos, p.nb);
+  const int q = (int)(scatter_bits(bb, p.bC, p.nb) & (uint32_t)(p.Qc - 1));
+  const float sc = operand_scale<float>(p.m, q, p.scale_inputs);
+  unsigned char *dst = reinterpret_cast<unsigned char *>(p.Xp) + (size_t)blockIdx.x * 2u * R * kTcKC * 4u;
+  for (uint32_t x = threadIdx.x; x < R * (kTcKC / 4); x += blockDim.x) {
+    const uint32_t m = p.row_fast ? x % R : x / (kTcKC / 4), kq = p.row_fast ? x / R : x % (kTcKC / 4);
+    float h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float v = __ldg(p.X + (base | off_r[m] | off_s[kq * 4 + t])) * sc;
+      h[t] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+      l[t] = v - h[t];
+    }
+    const uint32_t o = tc_off(m, kq * 4);
+    *reinterpret_cast<float4 *>(dst + o) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(dst + R * kTcKC * 4u + o) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
 
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
   // start address, leading byte offset (neighbour core matrix along K),
   // stride byte offset (next 8-row group), descriptor version 1, no swizzle
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((128u >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((1024u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+         ((uint64_t)((kTcRowGroup >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 // kind::tf32 instruction descriptor: float32 accumulator, TF32 A and B,
-// both K-major, N = 128, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
+// both K-major, N columns, M = 128 rows
+template <int N>
+struct TcIdesc {
+  static constexpr uint32_t value = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                    ((uint32_t)(kTcM >> 4) << 24);
+};
 
+template <int N>
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(acc)
+      "l"(adesc), "l"(bdesc), "r"(TcIdesc<N>::value), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(unsigned long long *bar) {
@@ -1461,46 +1536,57 @@ __device__ __forceinline__ void tc_commit(unsigned long long *bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// byte offset of element (row m, k) of a 128 x 32 operand tile
-__device__ __forceinline__ uint32_t tc_off(uint32_t m, uint32_t k) {
-  return (m >> 3) * 1024u + (k >> 2) * 128u + (m & 7u) * 16u + (k & 3u) * 4u;
+// bounded wait that also gives up once another role of the block failed
+__device__ __forceinline__ bool tc_wait(unsigned long long *bar, uint32_t parity, volatile int *fail) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (*fail) return false;
+    if (globaltimer_ns() - t0 > kWaitNs) return false;
+  }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k4_tc(K4Params p, uint32_t *err) {
+template <int N>
+struct TcShape {
+  static constexpr uint32_t a_bytes = 2u * kTcM * kTcKC * 4u;  // hi + lo block of A (16 KB)
+  static constexpr uint32_t b_bytes = 2u * N * kTcKC * 4u;     // hi + lo block of B
+  static constexpr uint32_t stage = a_bytes + b_bytes;
+  static constexpr uint32_t smem = kTcStages * stage + 4u * 32u * 33u * 4u;  // ring + epilogue transposes
+  static constexpr uint32_t tmem_cols = 2u * N;                              // two accumulators
+};
+
+template <int N>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k4_tc(K4Params p, const float *__restrict__ Ap, const float *__restrict__ Bp, uint32_t *err) {
+  using S = TcShape<N>;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long mma_done[2];
+  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base;
-  __shared__ uint32_t offA_i[kTcM], offB_j[kTcN], offC_i[kTcM], offC_j[kTcN];
-  __shared__ uint32_t offA_s[kTcK], offB_s[kTcK];
+  __shared__ uint32_t offC_i[kTcM], offC_j[N];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   __shared__ int s_fail;
-  const float *A = (const float *)p.A;
-  const float *B = (const float *)p.B;
+  volatile int *fail = &s_fail;
   float *C = (float *)p.C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t i_tiles = 1u << (p.ni - 7), j_tiles = 1u << (p.nj - 7);
-  const uint32_t tile = blockIdx.x;
-  const uint32_t it = tile % i_tiles, jt = (tile / i_tiles) % j_tiles, bb = tile / (i_tiles * j_tiles);
-  for (int x = threadIdx.x; x < kTcM; x += blockDim.x) {
-    offA_i[x] = scatter_bits((uint32_t)x, p.iA, 7);
-    offC_i[x] = scatter_bits((uint32_t)x, p.iC, 7);
-    offB_j[x] = scatter_bits((uint32_t)x, p.jB, 7);
-    offC_j[x] = scatter_bits((uint32_t)x, p.jC, 7);
-  }
-  for (int x = threadIdx.x; x < kTcK; x += blockDim.x) {
-    offA_s[x] = scatter_bits((uint32_t)x, p.sA, 5);
-    offB_s[x] = scatter_bits((uint32_t)x, p.sB, 5);
-  }
+  constexpr int nlog = N == 256 ? 8 : 7;
+  const uint32_t i_tiles = 1u << (p.ni - 7), j_tiles = 1u << (p.nj - nlog);
+  const uint32_t n_tiles = (i_tiles * j_tiles) << p.nb;
+  const uint32_t n_chunks = 1u << (p.ns - 4);
+  for (int x = threadIdx.x; x < kTcM; x += blockDim.x) offC_i[x] = scatter_bits((uint32_t)x, p.iC, 7);
+  for (int x = threadIdx.x; x < N; x += blockDim.x) offC_j[x] = scatter_bits((uint32_t)x, p.jC, nlog);
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
   if (threadIdx.x == 0) {
-    mbar_init(&mma_done[0], 1);
-    mbar_init(&mma_done[1], 1);
+    for (int s = 0; s < kTcStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+    mbar_init(&drain, 1);
     mbar_fence_init();
     s_fail = 0;
   }
-  if (warp == 0) {  // 128 columns of tensor memory: the 128 x 128 float32 accumulator
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                 "r"((uint32_t)kTcN)
+                 "r"(S::tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1508,121 +1594,135 @@ __global__ void __launch_bounds__(kTcThreads, 1) k4_tc(K4Params p, uint32_t *err
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t baseA = scatter_bits(it, p.iA + 7, p.ni - 7) | scatter_bits(bb, p.bA, p.nb);
-  const uint32_t baseB = scatter_bits(jt, p.jB + 7, p.nj - 7) | scatter_bits(bb, p.bB, p.nb);
-  const uint32_t baseC = scatter_bits(it, p.iC + 7, p.ni - 7) | scatter_bits(jt, p.jC + 7, p.nj - 7) |
-                         scatter_bits(bb, p.bC, p.nb);
-  const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
-  const float sa = operand_scale<float>(p.ma, q, p.mc.scale_inputs);
-  const float sb = operand_scale<float>(p.mb, q, p.mc.scale_inputs);
-  const uint32_t smem0 = smem_addr(tc_smem);
-  const uint32_t n_chunks = 1u << (p.ns - 5);
-  bool ok = true;
-  uint32_t issued = 0;  // chunks whose MMAs were committed
-  for (uint32_t c = 0; c < n_chunks; ++c) {
-    const uint32_t st = c & 1u;
-    if (c >= 2 && !__syncthreads_and(mbar_wait(&mma_done[st], ((c >> 1) - 1) & 1) ? 1 : 0)) { ok = false; break; }
-    unsigned char *stage = tc_smem + st * kTcStage;
-    const uint32_t hiA = scatter_bits(c, p.sA + 5, p.ns - 5), hiB = scatter_bits(c, p.sB + 5, p.ns - 5);
-    // gather, scale, split: each thread's 16 values of A and 16 of B are
-    // all requested before any is used (the loads overlap in flight)
-    constexpr int kPer = kTcM * kTcK / kTcThreads;
-    float va[kPer], vb[kPer];
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-      const uint32_t x = threadIdx.x + (uint32_t)t * kTcThreads;
-      const uint32_t m = p.a_i_fast ? x % kTcM : x / kTcK, k = p.a_i_fast ? x / kTcM : x % kTcK;
-      va[t] = __ldg(A + (baseA | hiA | offA_i[m] | offA_s[k]));
-      const uint32_t n = p.b_j_fast ? x % kTcN : x / kTcK, k2 = p.b_j_fast ? x / kTcN : x % kTcK;
-      vb[t] = __ldg(B + (baseB | hiB | offB_j[n] | offB_s[k2]));
-    }
-#pragma unroll
-    for (int t = 0; t < kPer; ++t) {
-      const uint32_t x = threadIdx.x + (uint32_t)t * kTcThreads;
-      {
-        const uint32_t m = p.a_i_fast ? x % kTcM : x / kTcK, k = p.a_i_fast ? x / kTcM : x % kTcK;
-        const float v = va[t] * sa;
-        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        const uint32_t o = tc_off(m, k);
-        *reinterpret_cast<float *>(stage + o) = h;
-        *reinterpret_cast<float *>(stage + kTcTile + o) = v - h;
+  const uint32_t ring = smem_addr(tc_smem);
+
+  if (warp == 0) {
+    // ---- producer: one elected lane moves each chunk's two packed blocks
+    if (lane == 0) {
+      uint32_t fill = 0;
+      for (uint32_t t = blockIdx.x; t < n_tiles && !*fail; t += gridDim.x) {
+        const uint32_t jt = t % j_tiles, it = (t / j_tiles) % i_tiles, bb = t / (i_tiles * j_tiles);
+        const unsigned char *a = reinterpret_cast<const unsigned char *>(Ap) +
+                                 (size_t)((bb * i_tiles + it) * n_chunks) * S::a_bytes;
+        const unsigned char *b = reinterpret_cast<const unsigned char *>(Bp) +
+                                 (size_t)((bb * j_tiles + jt) * n_chunks) * S::b_bytes;
+        for (uint32_t c = 0; c < n_chunks; ++c, ++fill) {
+          const uint32_t s = fill % kTcStages;
+          if (fill >= (uint32_t)kTcStages && !tc_wait(&empty[s], ((fill / kTcStages) - 1) & 1, fail)) {
+            *fail = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], S::stage);
+          bulk_g2s(tc_smem + s * S::stage, a + (size_t)c * S::a_bytes, S::a_bytes, &full[s]);
+          bulk_g2s(tc_smem + s * S::stage + S::a_bytes, b + (size_t)c * S::b_bytes, S::b_bytes, &full[s]);
+        }
+        if (*fail) break;
       }
-      {
-        const uint32_t n = p.b_j_fast ? x % kTcN : x / kTcK, k = p.b_j_fast ? x / kTcN : x % kTcK;
-        const float v = vb[t] * sb;
-        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        const uint32_t o = tc_off(n, k);
-        *reinterpret_cast<float *>(stage + 2 * kTcTile + o) = h;
-        *reinterpret_cast<float *>(stage + 3 * kTcTile + o) = v - h;
-      }
+      // every copy issued has landed before the block may exit
+      const uint32_t first = fill > (uint32_t)kTcStages ? fill - kTcStages : 0;
+      for (uint32_t f = first; f < fill; ++f)
+        if (!mbar_wait(&full[f % kTcStages], (f / kTcStages) & 1)) *fail = 1;
     }
-    fence_proxy_async_smem();  // the staged tiles, visible to the tensor cores
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem0 + st * kTcStage;
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      uint32_t fill = 0, lt = 0;
+      bool issued = false;
+      for (uint32_t t = blockIdx.x; t < n_tiles && !*fail; t += gridDim.x, ++lt) {
+        const uint32_t acc = lt & 1u;
+        if (lt >= 2 && !tc_wait(&tempty[acc], ((lt >> 1) - 1) & 1, fail)) { *fail = 1; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + acc * (uint32_t)N;
+        for (uint32_t c = 0; c < n_chunks; ++c, ++fill) {
+          const uint32_t s = fill % kTcStages;
+          if (!tc_wait(&full[s], (fill / kTcStages) & 1, fail)) { *fail = 1; break; }
+          tc_fence_after();
+          const uint32_t a0 = ring + s * S::stage, b0 = a0 + S::a_bytes;
 #pragma unroll
-      for (uint32_t kk = 0; kk < (uint32_t)(kTcK / 8); ++kk) {
-        const uint64_t ahi = tc_smem_desc(a0 + kk * 256u), alo = tc_smem_desc(a0 + kTcTile + kk * 256u);
-        const uint64_t bhi = tc_smem_desc(a0 + 2 * kTcTile + kk * 256u);
-        const uint64_t blo = tc_smem_desc(a0 + 3 * kTcTile + kk * 256u);
-        tc_mma(tmem, alo, bhi, (c | kk) != 0u);
-        tc_mma(tmem, ahi, blo, 1u);
-        tc_mma(tmem, ahi, bhi, 1u);
+          for (uint32_t kk = 0; kk < (uint32_t)(kTcKC / 8); ++kk) {
+            const uint64_t ahi = tc_smem_desc(a0 + kk * 256u), alo = tc_smem_desc(a0 + S::a_bytes / 2 + kk * 256u);
+            const uint64_t bhi = tc_smem_desc(b0 + kk * 256u), blo = tc_smem_desc(b0 + S::b_bytes / 2 + kk * 256u);
+            tc_mma<N>(d, alo, bhi, (c | kk) != 0u);
+            tc_mma<N>(d, ahi, blo, 1u);
+            tc_mma<N>(d, ahi, bhi, 1u);
+          }
+          issued = true;
+          tc_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        }
+        if (*fail) break;
+        tc_commit(&tfull[acc]);  // the accumulator is complete
       }
-      tc_commit(&mma_done[st]);
+      // every MMA issued has finished before tensor memory is freed
+      if (issued) {
+        tc_commit(&drain);
+        if (!mbar_wait(&drain, 0)) *fail = 1;
+      }
     }
-    issued = c + 1;
-  }
-  if (!ok && threadIdx.x == 0 && err) atomicOr(err, 1u);
-  // the last commit covers every MMA issued before it
-  bool done = true;
-  if (issued) {
-    const uint32_t last = issued - 1;
-    done = __syncthreads_and(mbar_wait(&mma_done[last & 1u], (last >> 1) & 1) ? 1 : 0) != 0;
-  }
-  if (!done && threadIdx.x == 0) {
-    if (err) atomicOr(err, 1u);
-    s_fail = 1;
-  }
-  tc_fence_after();
-  if (ok && done) {
-    // accumulator rows (lanes 32 w .. 32 w + 31) to shared memory, 32 columns at a time
-    float *Cs = reinterpret_cast<float *>(tc_smem);  // [128][129]
-    // warp w reads its lane quarter (w mod 4) of the accumulator, half the columns
-    const uint32_t quarter = (uint32_t)warp & 3u, half = (uint32_t)warp >> 2;
+  } else {
+    // ---- epilogue: warp w reads lanes 32 (w mod 4) .. + 31 of the accumulator
+    const uint32_t quarter = (uint32_t)warp & 3u;
     const uint32_t row = quarter * 32u + (uint32_t)lane;
+    float *tr = reinterpret_cast<float *>(tc_smem + kTcStages * S::stage) + (warp - 2) * 32 * 33;
+    uint32_t lt = 0;
+    for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u;
+      const bool ok = tc_wait(&tfull[acc], (lt >> 1) & 1, fail);
+      if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) *fail = 1; break; }
+      tc_fence_after();
+      const uint32_t jt = t % j_tiles, it = (t / j_tiles) % i_tiles, bb = t / (i_tiles * j_tiles);
+      const uint32_t baseC = scatter_bits(it, p.iC + 7, p.ni - 7) | scatter_bits(jt, p.jC + nlog, p.nj - nlog) |
+                             scatter_bits(bb, p.bC, p.nb);
+      const int q = (int)(baseC & (uint32_t)(p.mc.Qc - 1));
+      float tmax = 0.f, tmin = INFINITY;
 #pragma unroll 1
-    for (uint32_t col = half * (kTcN / 2); col < (half + 1) * (kTcN / 2); col += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((quarter * 32u) << 16) + col;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-          "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (uint32_t col = 0; col < (uint32_t)N; col += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((quarter * 32u) << 16) + acc * (uint32_t)N + col;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (p.c_i_fast) {
+          // lanes are consecutive rows: each column is one coalesced store
+          const uint32_t ci = baseC | offC_i[row];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) Cs[row * (kTcN + 1) + col + (uint32_t)k] = __uint_as_float(r[k]);
+          for (int k = 0; k < 32; ++k) {
+            const float v = __uint_as_float(r[k]);
+            C[ci | offC_j[col + (uint32_t)k]] = v;
+            track(v, tmax, tmin);
+          }
+        } else {
+          // transpose 32 x 32 through shared memory: lanes along the columns
+#pragma unroll
+          for (int k = 0; k < 32; ++k) tr[lane * 33 + k] = __uint_as_float(r[k]);
+          __syncwarp();
+          const uint32_t cj = baseC | offC_j[col + (uint32_t)lane];
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            const float v = tr[rr * 33 + lane];
+            C[cj | offC_i[quarter * 32u + (uint32_t)rr]] = v;
+            track(v, tmax, tmin);
+          }
+          __syncwarp();
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);  // the accumulator may be overwritten
+      publish(smax, smin, q, tmax, tmin);
     }
-    __syncthreads();
-    float tmax = 0.f, tmin = INFINITY;
-    for (uint32_t x = threadIdx.x; x < (uint32_t)(kTcM * kTcN); x += blockDim.x) {
-      const uint32_t m = p.c_i_fast ? x % kTcM : x / kTcN, n = p.c_i_fast ? x / kTcM : x % kTcN;
-      const float v = Cs[m * (kTcN + 1) + n];
-      C[baseC | offC_i[m] | offC_j[n]] = v;
-      track(v, tmax, tmin);
-    }
-    publish(smax, smin, q, tmax, tmin);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTcN)
+  if (s_fail && threadIdx.x == 0 && err) atomicOr(err, 1u);
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::tmem_cols)
                  : "memory");
   if (!s_fail) finish_meta<float>(p.ma, p.mb, p.mc, smax, smin);
 }

@@ -195,6 +195,8 @@ SWEEP_SMALL = [(ra, rb, b, k) for (b, k) in [(0, 1), (2, 1), (4, 1), (0, 4), (2,
                for (ra, rb) in [(b + k + 3, b + k + 2), (b + k + 9, b + k + 1)]]
 # dense batched products (at least 2^6 free values on each side): the tiled kernel
 SWEEP_SMALL += [(13, 14, 2, 5), (15, 14, 0, 8), (16, 16, 4, 6), (14, 14, 0, 8)]
+# streaming products with four summed and/or four S-free indices (one lane per thread)
+SWEEP_SMALL += [(10, 8, 0, 4), (12, 10, 2, 4), (9, 7, 0, 3), (13, 9, 2, 4), (14, 8, 4, 4)]
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
@@ -639,7 +641,10 @@ def _norm_pair(mant, e):
 
 
 # dense float32 products with 2^7 x 2^7 output tiles: the tcgen05 kernel
-SWEEP_TC = [(13, 13, 1, 5), (16, 15, 0, 8), (17, 17, 2, 6), (15, 16, 1, 7)]
+# (rank A, rank B, batch, summed): 128- and 256-column accumulators, one
+# 16-term chunk, a ring of stages that wraps within a tile (16 chunks), and
+# more tiles than blocks (both accumulators reused, 512 tiles)
+SWEEP_TC = [(13, 13, 1, 5), (16, 15, 0, 8), (17, 17, 2, 6), (15, 16, 1, 7), (12, 13, 0, 4), (18, 17, 1, 5)]
 
 
 @pytest.mark.parametrize("ra,rb,b,k", SWEEP_TC)
