@@ -72,6 +72,11 @@ extern "C" {
 #define WMC_FLAG_DEVICE_TIMEOUT 0x8u /* a bounded wait inside a kernel gave up;
                                         the value is invalid (wmc_execute and
                                         the server report WMC_ETIMEOUT)       */
+#define WMC_FLAG_FELL_BACK_FP64 0x10u /* the query's scaled-FP32 walk may have
+                                        flushed (WMC_FLAG_FP32_FLUSH), so
+                                        wmc_execute / wmc_execute_slices ran
+                                        it again on the same tree in FP64;
+                                        the value and bound are FP64's        */
 
 typedef struct wmc_network wmc_network_t;
 typedef struct wmc_plan wmc_plan_t;
@@ -99,6 +104,9 @@ typedef struct {
  * weights; they may be NULL (all weights 1).  The COPY tensors A_x are kept
  * in hyperedge form: each variable is one index shared by every tensor that
  * mentions it, and A_x becomes the weight vector [W(x,0), W(x,1)].
+ * A clause may have any number of literals; one over more than 62
+ * variables is planned only with clause factoring
+ * (wmc_plan_opts.factor_clauses_above).
  * Errors: WMC_EINVAL for a literal 0 or |lit| > n_vars, negative sizes or a
  * non-monotone clause_off; WMC_ENOMEM. */
 int wmc_network_create(int32_t n_vars, int64_t n_clauses, const int32_t *lits,
@@ -133,6 +141,18 @@ typedef struct {
                                exceeds this; 0 = no limit                   */
   const int32_t *order;     /* WMC_ORDER_GIVEN: n_vars 1-based ids (host,
                                copied)                                      */
+  int32_t factor_clauses_above; /* clause factoring (FactorTree, Def. 3.4 and
+                               Thm 3.3): if > 0 (at least 3), every clause
+                               with more literals than this becomes a chain
+                               of OR gates y_1 = l_1 | l_2, y_k = y_{k-1} |
+                               l_{k+1}, closed by (y_{r-2} | l_r), each gate
+                               the three clause tensors (~a | y), (~b | y),
+                               (a | b | ~y); the gate outputs are auxiliary
+                               indices with weight 1 for both values (no
+                               weight leaf, labels n_vars, n_vars + 1, ...),
+                               so W is unchanged.  Not combinable with
+                               WMC_ORDER_GIVEN.  0 = off                   */
+  int32_t reserved;
 } wmc_plan_opts;
 
 /* Planning: Sec. 3.3.  Builds a contraction tree by bucket elimination
@@ -162,6 +182,8 @@ typedef struct {
   int32_t n_slice_vars;       /* index slicing: s sliced variables, 2^s
                                  walks per execution (0: none)           */
   int32_t slice_vars[24];     /* their 0-based ids; slice bit k = var k  */
+  int32_t n_aux_vars;         /* clause factoring: auxiliary indices      */
+  int32_t reserved;
 } wmc_plan_info_t;
 /* Q >= 1 is the number of queries batched along the extra query index. */
 int wmc_plan_info(const wmc_plan_t *plan, int32_t Q, wmc_plan_info_t *out);
@@ -374,6 +396,13 @@ void wmc_set_dependent_launch(int32_t on);
  * off, on the scalar tiled kernel.  The two agree within float32 rounding,
  * not bit for bit. */
 void wmc_set_tensor_cores(int32_t on);
+/* Execution option (default on): wmc_execute and wmc_execute_slices run the
+ * queries of a scaled-FP32 plan whose results carry WMC_FLAG_FP32_FLUSH
+ * again in FP64 on the same contraction tree (one extra walk over those
+ * queries) and return the FP64 values with WMC_FLAG_FELL_BACK_FP64.  The
+ * device entries and the server report the flush flag and leave the choice
+ * to the caller. */
+void wmc_set_fp64_fallback(int32_t on);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,

@@ -39,6 +39,7 @@ WMC_FLAG_EXACT_INT = 0x1
 WMC_FLAG_FP32_FLUSH = 0x2
 WMC_FLAG_NO_BOUND = 0x4
 WMC_FLAG_DEVICE_TIMEOUT = 0x8
+WMC_FLAG_FELL_BACK_FP64 = 0x10
 
 c_i32 = ctypes.c_int32
 c_i64 = ctypes.c_int64
@@ -63,7 +64,8 @@ class wmc_network_info_t(ctypes.Structure):
 
 class wmc_plan_opts(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("ordering", c_i32), ("max_rank_cap", c_i32),
-                ("slice_to_rank", c_i32), ("mem_budget_bytes", c_i64), ("order", P(c_i32))]
+                ("slice_to_rank", c_i32), ("mem_budget_bytes", c_i64), ("order", P(c_i32)),
+                ("factor_clauses_above", c_i32), ("reserved", c_i32)]
 
 
 class wmc_plan_info_t(ctypes.Structure):
@@ -71,7 +73,8 @@ class wmc_plan_info_t(ctypes.Structure):
                 ("n_nodes", c_i64), ("workspace_bytes", c_i64), ("peak_tensor_bytes", c_i64),
                 ("algorithmic_bytes", c_dbl), ("flops", c_dbl), ("precision", c_i32),
                 ("ordering_used", c_i32), ("max_path_roundings", c_i32), ("launches_per_walk", c_i32),
-                ("n_slice_vars", c_i32), ("slice_vars", c_i32 * 24)]
+                ("n_slice_vars", c_i32), ("slice_vars", c_i32 * 24), ("n_aux_vars", c_i32),
+                ("reserved", c_i32)]
 
 
 class wmc_server_opts(ctypes.Structure):
@@ -137,6 +140,7 @@ EXPORTS = {
     "wmc_set_small_phase": (None, [c_i32]),
     "wmc_set_dependent_launch": (None, [c_i32]),
     "wmc_set_tensor_cores": (None, [c_i32]),
+    "wmc_set_fp64_fallback": (None, [c_i32]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

@@ -39,6 +39,7 @@ static std::atomic<int32_t> g_fuse{4};
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
 static std::atomic<int32_t> g_tensor_cores{1};  // dense float32 pair contractions on tcgen05
+static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run again in float64
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
@@ -47,6 +48,7 @@ extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
 extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
 extern "C" void wmc_set_tensor_cores(int32_t on) { g_tensor_cores.store(on); }
+extern "C" void wmc_set_fp64_fallback(int32_t on) { g_fp64_fallback.store(on); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -538,8 +540,9 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   if ((grow || shrink) && (!fast || any_broadcast)) return false;
   // tiling of P over its kept indices: 2 work units per thread when 16
   // chain states would leave runs of only 2 KB (bulk copies that short
-  // lower the read rate)
-  cp.units = (D == 4 && !f64) ? 2 : 1;
+  // lower the read rate); a growth chain's 32 states per unit already
+  // fill the registers (one unit measured ~1% faster)
+  cp.units = (D == 4 && !f64 && !grow) ? 2 : 1;  // growth chains hold 32 states: one unit
   int tb = 0;
   while ((1 << tb) < nthr * V * cp.units) ++tb;
   if (cp.units == 2 && cp.log2_nu + vbits < tb + 3) { cp.units = 1; --tb; }
@@ -684,14 +687,14 @@ int64_t grid_for(uint64_t work) {
 }  // namespace
 
 // Builds the host-side layout for batch size Q (no device work).
-static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false) {
+static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, bool force_f64 = false) {
   st.Q = Q;
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
   st.m = m;
   const int32_t Qp = 1 << m;
   st.Qp = Qp;
-  st.f64 = plan.precision == WMC_FP64;
+  st.f64 = plan.precision == WMC_FP64 || force_f64;
   const size_t nt = plan.tensors.size();
   const int64_t root = plan.nodes.back().c;
   st.t_off.assign(nt, 0);
@@ -1397,14 +1400,14 @@ static int get_graph(Plan &plan, ExecState &st, char *ws, cudaGraphExec_t *out) 
   return WMC_OK;
 }
 
-static int get_state(Plan &plan, int32_t Q, ExecState **out, bool plain = false) {
+static int get_state(Plan &plan, int32_t Q, ExecState **out, bool plain = false, bool f64 = false) {
   std::lock_guard<std::mutex> lk(plan.exec_mu);
-  auto &cache = plain ? plan.exec_plain : plan.exec;
+  auto &cache = f64 ? plan.exec_f64 : (plain ? plan.exec_plain : plan.exec);
   auto it = cache.find(Q);
   if (it != cache.end()) { *out = it->second.get(); return WMC_OK; }
   std::unique_ptr<ExecState> st(new (std::nothrow) ExecState());
   if (!st) { set_error("out of host memory"); return WMC_ENOMEM; }
-  int rc = build_exec(plan, Q, *st, plain);
+  int rc = build_exec(plan, Q, *st, plain, f64);
   if (rc) return rc;
   *out = st.get();
   cache[Q] = std::move(st);
@@ -1540,6 +1543,7 @@ extern "C" int wmc_plan_info(const wmc_plan_t *cplan, int32_t Q, wmc_plan_info_t
   out->launches_per_walk = (int32_t)st->kernels_per_run;
   out->n_slice_vars = (int32_t)plan->slice_vars.size();
   for (size_t k = 0; k < plan->slice_vars.size() && k < 24; ++k) out->slice_vars[k] = plan->slice_vars[k];
+  out->n_aux_vars = plan->n_aux;
   return WMC_OK;
 }
 
@@ -1653,14 +1657,10 @@ extern "C" int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_p
   return execute_host(plan, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
 }
 
-static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
-                        int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
-  if (!plan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
-  if (check_q(Q)) return WMC_EINVAL;
-  if ((w_pos_q == nullptr) != (w_neg_q == nullptr)) { set_error("give both weight arrays or neither"); return WMC_EINVAL; }
-  ExecState *st = nullptr;
-  int rc = get_state(*plan, Q, &st);
-  if (rc) return rc;
+// One walk of state `st` with host weights, results filled into out[Q].
+static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                    int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
+  int rc = WMC_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nv = (size_t)plan->n_vars;
   std::lock_guard<std::mutex> run(st->run_mu);  // the owned workspace is single-use at a time
@@ -1709,6 +1709,45 @@ static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, cons
     }
   for (int32_t q = 0; q < Q; ++q)
     fill_result(*st, st->h_res_mant[q], st->h_res_exp[q], st->h_res_flags[q], unit, negative, out + q);
+  return WMC_OK;
+}
+
+static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                        int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
+  if (!plan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  if ((w_pos_q == nullptr) != (w_neg_q == nullptr)) { set_error("give both weight arrays or neither"); return WMC_EINVAL; }
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Q, &st);
+  if (rc) return rc;
+  rc = run_host(plan, st, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
+  if (rc || st->f64 || !g_fp64_fallback.load()) return rc;
+  // queries whose float32 walk may have flushed run again in float64
+  std::vector<int32_t> redo;
+  for (int32_t q = 0; q < Q; ++q)
+    if (out[q].flags & WMC_FLAG_FP32_FLUSH) redo.push_back(q);
+  if (redo.empty()) return WMC_OK;
+  const int32_t R = (int32_t)redo.size();
+  const size_t nv = (size_t)plan->n_vars;
+  std::vector<double> wp, wn;
+  if (w_pos_q) {
+    wp.resize((size_t)R * nv);
+    wn.resize((size_t)R * nv);
+    for (int32_t i = 0; i < R; ++i) {
+      std::memcpy(wp.data() + (size_t)i * nv, w_pos_q + (size_t)redo[(size_t)i] * nv, sizeof(double) * nv);
+      std::memcpy(wn.data() + (size_t)i * nv, w_neg_q + (size_t)redo[(size_t)i] * nv, sizeof(double) * nv);
+    }
+  }
+  ExecState *st64 = nullptr;
+  if ((rc = get_state(*plan, R, &st64, false, true))) return rc;
+  std::vector<wmc_result> r64((size_t)R);
+  rc = run_host(plan, st64, R, w_pos_q ? wp.data() : nullptr, w_neg_q ? wn.data() : nullptr, slice_lo, slice_hi,
+                stream, r64.data());
+  if (rc) return rc;
+  for (int32_t i = 0; i < R; ++i) {
+    out[redo[(size_t)i]] = r64[(size_t)i];
+    out[redo[(size_t)i]].flags |= WMC_FLAG_FELL_BACK_FP64;
+  }
   return WMC_OK;
 }
 

@@ -30,6 +30,9 @@ struct Clause {
   // is true, i.e. ((eta ^ sfals) & smask) != 0; otherwise it is the clause
   // over its remaining variables.
   uint32_t smask = 0, sfals = 0;
+  // clauses over more than 62 variables (plannable only when factored):
+  // the falsifying value of vars[j] is fvals[j], and `fals` is unused
+  std::vector<uint8_t> fvals;
 };
 
 struct Network {
@@ -41,6 +44,11 @@ struct Network {
   int64_t n_indices_strict = 0;
   int64_t max_clause_rank = 0;
   std::vector<uint8_t> sliced;  // per variable: fixed by the slice (no weight leaf, in no clause)
+  // clause factoring (Def. 3.4, Thm 3.3): auxiliary indices n_vars ..
+  // n_vars + n_aux - 1, the OR-gate outputs of factored clauses; weight 1
+  // for both values (no weight leaf)
+  int32_t n_aux = 0;
+  int32_t n_all() const { return n_vars + n_aux; }
 };
 
 enum LeafKind : int32_t { LEAF_CLAUSE = 0, LEAF_WEIGHT = 1, LEAF_ONE = 2, NOT_LEAF = -1 };
@@ -79,12 +87,16 @@ struct Plan {
   // index slicing: the sliced variables (slice bit k = slice_vars[k]); the
   // walk runs once per slice assignment and the results are summed
   std::vector<int32_t> slice_vars;
+  int32_t n_aux = 0;  // auxiliary indices of factored clauses (labels n_vars ..)
 
   std::mutex exec_mu;
   std::map<int32_t, std::unique_ptr<ExecState>> exec;  // keyed by Q
   // one pass per node in post-order, every tensor its own offset (no chains,
   // no small-node phase): the layout other executors reuse
   std::map<int32_t, std::unique_ptr<ExecState>> exec_plain;
+  // the same tree in float64 for queries whose scaled-FP32 walk may have
+  // flushed (WMC_FLAG_FELL_BACK_FP64)
+  std::map<int32_t, std::unique_ptr<ExecState>> exec_f64;
   ~Plan();
 };
 

@@ -99,6 +99,21 @@ __device__ __forceinline__ void publish(unsigned long long *smax, unsigned long 
   if (tmin != (T)INFINITY) atomicMin(smin + q, abs_bits(tmin));
 }
 
+// publish() after folding the max/min of the warp's lanes that share a
+// query lane: lanes l and l ^ o hold the same q for every o that is a
+// multiple of `period` (1: the whole warp shares one q; Qc <= 32 when
+// q = lane mod Qc; >= 32: every lane its own).  Max and min are exact, so
+// the result does not depend on the grouping.  All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ void publish_warp(unsigned long long *smax, unsigned long long *smin, int q,
+                                             T tmax, T tmin, int period) {
+  for (int o = 16; o >= period; o >>= 1) {
+    tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+  }
+  if ((int)(threadIdx.x & 31u) < period) publish(smax, smin, q, tmax, tmin);
+}
+
 // ------------------------------------------------------------ K1 generic
 
 struct K1Params {
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k1_generic(K1Params p) {
     C[o] = c;
     track(c, tmax, tmin);
   }
-  publish(smax, smin, qc, tmax, tmin);
+  publish_warp(smax, smin, qc, tmax, tmin, p.mc.Qc);
   __syncthreads();
   finish_meta<TI>(p.ma, p.mb, p.mc, smax, smin);
 }
@@ -1386,7 +1401,7 @@ __global__ void __launch_bounds__(256) k4_dense(K4Params p) {
     C[baseC | offC_i[ii] | offC_j[jj]] = v;
     track(v, tmax, tmin);
   }
-  publish(smax, smin, q, tmax, tmin);
+  publish_warp(smax, smin, q, tmax, tmin, 1);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
@@ -1423,7 +1438,7 @@ __global__ void __launch_bounds__(256) k4_reduce(K4Params p) {
   ((T *)p.C)[baseC | scatter_bits(ii, p.iC, 6) | scatter_bits(jj, p.jC, 6)] = v;
   T tmax = (T)0, tmin = (T)INFINITY;
   track(v, tmax, tmin);
-  publish(smax, smin, q, tmax, tmin);
+  publish_warp(smax, smin, q, tmax, tmin, 1);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
@@ -1715,7 +1730,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);  // the accumulator may be overwritten
-      publish(smax, smin, q, tmax, tmin);
+      publish_warp(smax, smin, q, tmax, tmin, 1);
     }
   }
   tc_fence_before();

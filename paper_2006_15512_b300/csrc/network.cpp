@@ -83,14 +83,11 @@ extern "C" int wmc_network_create(int32_t n_vars, int64_t n_clauses, const int32
         if (!seen) vs.push_back({v, (int8_t)(l > 0 ? 0 : 1)});
       }
       std::sort(vs.begin(), vs.end());
-      if (vs.size() > 62) {
-        delete net;
-        set_error("clause %lld has %zu distinct variables (max 62)", (long long)c, vs.size());
-        return WMC_EINVAL;
-      }
+      const bool wide = vs.size() > 62;  // kept as per-literal values (factoring only)
       for (size_t j = 0; j < vs.size(); ++j) {
         cl.vars.push_back(vs[j].first);
-        if (vs[j].second) cl.fals |= (1ull << j);
+        if (wide) cl.fvals.push_back((uint8_t)vs[j].second);
+        else if (vs[j].second) cl.fals |= (1ull << j);
       }
       if (cl.vars.empty()) net->has_empty = true;
       net->n_indices_strict += (int64_t)cl.vars.size();

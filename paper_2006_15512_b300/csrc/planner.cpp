@@ -9,6 +9,7 @@
 // order (its memory layout) is then chosen from its larger operand so that
 // the streaming contraction keeps most bit positions in place.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -21,7 +22,7 @@
 namespace wmc {
 
 static std::vector<std::vector<int32_t>> primal_graph(const Network &net) {
-  std::vector<std::vector<int32_t>> adj((size_t)net.n_vars);
+  std::vector<std::vector<int32_t>> adj((size_t)net.n_all());
   for (const Clause &c : net.clauses)
     for (int32_t a : c.vars)
       for (int32_t b : c.vars)
@@ -234,8 +235,8 @@ bool build_tree(const Network &net, const std::vector<int32_t> &order, int32_t r
   int32_t max_rank = 0;
   for (auto &t : T) max_rank = std::max(max_rank, (int32_t)t.labels.size());
   const size_t n_leaves = T.size();
-  std::vector<int32_t> cnt((size_t)net.n_vars, 0);         // live tensors per var
-  std::vector<std::vector<int64_t>> holders((size_t)net.n_vars);
+  std::vector<int32_t> cnt((size_t)net.n_all(), 0);         // live tensors per var
+  std::vector<std::vector<int64_t>> holders((size_t)net.n_all());
   std::vector<uint8_t> live(n_leaves, 1);
   for (size_t i = 0; i < n_leaves; ++i)
     for (int32_t v : T[i].labels) { cnt[(size_t)v]++; holders[(size_t)v].push_back((int64_t)i); }
@@ -402,7 +403,7 @@ static int choose_slices(const Network &net, const wmc_plan_opts &opts, int32_t 
       set_error("slicing %d variables leaves a tensor of rank %d (target %d)", kMaxSliceVars, probe.max_rank, target);
       return WMC_EPLAN_TOO_BIG;
     }
-    std::vector<double> score((size_t)net.n_vars, 0.0);
+    std::vector<double> score((size_t)net.n_all(), 0.0);
     for (const TensorInfo &t : probe.tensors)
       for (int32_t v : t.labels) score[(size_t)v] += std::ldexp(1.0, (int)t.labels.size());
     int32_t best = -1;
@@ -430,8 +431,89 @@ static int choose_slices(const Network &net, const wmc_plan_opts &opts, int32_t 
   }
 }
 
+// Clause factoring (FactorTree of Sec. 3.3 for clause tensors: Def. 3.4,
+// Thm 3.3).  A clause tensor is tree-factorable: a clause with r > `above`
+// literals l_1 .. l_r (ascending variable order) becomes a chain of OR
+// gates over new indices y_1 .. y_{r-2}, y_1 = l_1 | l_2 and
+// y_k = y_{k-1} | l_{k+1}, closed by the clause (y_{r-2} | l_r).  A gate
+// y = a | b is the product of the clause tensors (~a | y), (~b | y) and
+// (a | b | ~y), so every tensor has rank <= 3.  For each assignment of the
+// formula's variables exactly one assignment of the y's satisfies every
+// gate, so with weight 1 for both values of each y the count is unchanged.
+namespace {
+struct Lit {
+  int32_t v;
+  uint32_t f;  // the value of v that falsifies the literal
+};
+Clause clause_of(std::vector<Lit> lits) {
+  std::sort(lits.begin(), lits.end(), [](const Lit &a, const Lit &b) { return a.v < b.v; });
+  Clause c;
+  for (size_t j = 0; j < lits.size(); ++j) {
+    c.vars.push_back(lits[j].v);
+    if (lits[j].f) c.fals |= 1ull << j;
+  }
+  return c;
+}
+void factor_clauses(const Network &net, int32_t above, Network &out) {
+  out = net;
+  out.clauses.clear();
+  out.n_aux = 0;
+  out.n_indices_strict = 0;
+  out.max_clause_rank = 0;
+  auto push = [&](Clause c) {
+    out.n_indices_strict += (int64_t)c.vars.size();
+    out.max_clause_rank = std::max(out.max_clause_rank, (int64_t)c.vars.size());
+    out.clauses.push_back(std::move(c));
+  };
+  for (const Clause &c : net.clauses) {
+    const size_t r = c.vars.size();
+    if ((int32_t)r <= above) { push(c); continue; }
+    std::vector<Lit> l(r);
+    for (size_t j = 0; j < r; ++j)
+      l[j] = {c.vars[j], c.fvals.empty() ? (uint32_t)((c.fals >> j) & 1ull) : (uint32_t)c.fvals[j]};
+    Lit prev = l[0];
+    for (size_t k = 1; k + 1 < r; ++k) {
+      const Lit y{net.n_vars + out.n_aux++, 0u};  // y = prev | l[k]
+      const Lit a = prev, b = l[k];
+      push(clause_of({{a.v, 1u - a.f}, y}));
+      push(clause_of({{b.v, 1u - b.f}, y}));
+      push(clause_of({a, b, {y.v, 1u}}));
+      prev = y;
+    }
+    push(clause_of({prev, l[r - 1]}));
+  }
+}
+}  // namespace
+
+static int build_plan_on(const Network &net, const wmc_plan_opts &opts, Plan &plan);
+
 int build_plan(const Network &net, const wmc_plan_opts &opts, Plan &plan) {
+  if (opts.factor_clauses_above == 0) return build_plan_on(net, opts, plan);
+  if (opts.factor_clauses_above < 3) {
+    set_error("factor_clauses_above must be 0 (off) or at least 3 (got %d)", opts.factor_clauses_above);
+    return WMC_EINVAL;
+  }
+  Network factored;
+  try {
+    factor_clauses(net, opts.factor_clauses_above, factored);
+  } catch (const std::bad_alloc &) {
+    set_error("out of host memory while factoring clauses");
+    return WMC_ENOMEM;
+  }
+  if ((int64_t)net.n_vars + factored.n_aux > INT32_MAX / 2) { set_error("too many auxiliary indices"); return WMC_EINVAL; }
+  const int rc = build_plan_on(factored, opts, plan);
+  if (rc == WMC_OK) plan.n_aux = factored.n_aux;
+  return rc;
+}
+
+static int build_plan_on(const Network &net, const wmc_plan_opts &opts, Plan &plan) {
   const int32_t cap = opts.max_rank_cap > 0 ? opts.max_rank_cap : 30;
+  for (size_t c = 0; c < net.clauses.size(); ++c)
+    if (!net.clauses[c].fvals.empty()) {
+      set_error("clause %zu has %zu literals (a rank-%zu tensor): plan with factor_clauses_above", c,
+                net.clauses[c].vars.size(), net.clauses[c].vars.size());
+      return WMC_EPLAN_TOO_BIG;
+    }
   if (opts.slice_to_rank > 0) {
     Network work;
     std::vector<int32_t> slice_vars;
@@ -460,6 +542,7 @@ static int best_candidate(const Network &net, const wmc_plan_opts &opts, int32_t
   try {
     if (opts.ordering == WMC_ORDER_GIVEN) {
       if (!opts.order) { set_error("WMC_ORDER_GIVEN without an order"); return WMC_EINVAL; }
+      if (net.n_aux) { set_error("a given order cannot be combined with clause factoring"); return WMC_EINVAL; }
       std::vector<int32_t> o((size_t)net.n_vars);
       std::vector<uint8_t> seen((size_t)net.n_vars, 0);
       for (int32_t i = 0; i < net.n_vars; ++i) {
@@ -471,7 +554,7 @@ static int best_candidate(const Network &net, const wmc_plan_opts &opts, int32_t
       orders.push_back({WMC_ORDER_GIVEN, o});
     } else {
       auto adj = primal_graph(net);
-      const int32_t n = net.n_vars;
+      const int32_t n = net.n_all();
       bool all = opts.ordering == WMC_ORDER_BEST;
       if (all || opts.ordering == WMC_ORDER_SWEEP) {
         orders.push_back({WMC_ORDER_SWEEP, order_sweep(n, adj, false)});

@@ -135,16 +135,53 @@ def test_evidence_zero_weight(w):
 
 
 def test_fp32_flush_is_flagged(w):
-    """A weight ratio beyond float32's range underflows a mantissa: the
-    result carries WMC_FLAG_FP32_FLUSH, FP64 stays exact-to-tolerance."""
+    """A weight ratio beyond float32's range underflows a mantissa: without
+    the fallback the result carries WMC_FLAG_FP32_FLUSH; FP64 stays
+    exact-to-tolerance."""
     cnf = wmcgen.random_kcnf(12, 30, seed=4)
     wp, wn = wmcgen.weights_complementary(12, 4, 0.2, 0.8)
     wn[2] = 1e-60
     want = oracle.bucket_elim(cnf, wp, wn)
-    r32 = plan_for(w, cnf, wp, wn, FP32).execute()[0]
+    try:
+        w.wmc_set_fp64_fallback(0)
+        r32 = plan_for(w, cnf, wp, wn, FP32).execute()[0]
+    finally:
+        w.wmc_set_fp64_fallback(1)
     assert r32.flags & w.WMC_FLAG_FP32_FLUSH
+    assert not r32.flags & w.WMC_FLAG_FELL_BACK_FP64
     r64 = plan_for(w, cnf, wp, wn, FP64).execute()[0]
     assert rel(r64, want) <= TOL[FP64]
+
+
+def test_fp32_flush_falls_back_to_fp64(w):
+    """With the fallback (default), the flushed queries of a scaled-FP32
+    batch run again in FP64 on the same tree: they carry
+    WMC_FLAG_FELL_BACK_FP64 and FP64's accuracy; the other queries keep
+    their FP32 values, bit for bit."""
+    n = 14
+    cnf = wmcgen.random_kcnf(n, 36, seed=6)
+    cnf = wmcgen.Cnf(n, cnf.clauses + [[3]])  # x_3 forced true: a tiny w(x_3) survives
+    Q = 8
+    wq, wnq = wmcgen.query_weights(n, Q, seed=9, lo=0.1, hi=0.9)
+    for q in (1, 4, 5):
+        wq[q, 2] = 1e-41  # below float32's smallest normal
+    plan = plan_for(w, cnf, None, None, FP32)
+    res = plan.execute(wq, wnq)
+    try:
+        w.wmc_set_fp64_fallback(0)
+        raw = plan.execute(wq, wnq)
+    finally:
+        w.wmc_set_fp64_fallback(1)
+    for q in range(Q):
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q])
+        if q in (1, 4, 5):
+            assert raw[q].flags & w.WMC_FLAG_FP32_FLUSH
+            assert res[q].flags & w.WMC_FLAG_FELL_BACK_FP64 and not res[q].flags & w.WMC_FLAG_FP32_FLUSH
+            assert rel(res[q], want) <= TOL[FP64]
+        else:
+            assert not res[q].flags & (w.WMC_FLAG_FELL_BACK_FP64 | w.WMC_FLAG_FP32_FLUSH)
+            assert (res[q].mant, res[q].exp2) == (raw[q].mant, raw[q].exp2)
+            assert rel(res[q], want) <= TOL[FP32]
 
 
 # ------------------------------------------------------------ grids
@@ -589,25 +626,12 @@ def test_slice_ranges_sum_to_the_whole(w):
 def test_sliced_psi_beyond_the_rank_cap(w):
     """psi(34) has no plan within rank 30; sliced to 28 it runs and gives
     the closed form prod(w0 + w1) - prod(w1) - prod(w0)."""
-    from fractions import Fraction
     n = 34
     cnf = wmcgen.psi_family(n)
     wp, wn = wmcgen.weights_complementary(n, 7, 0.2, 0.8)
     plan = plan_for(w, cnf, wp, wn, FP64, slice_to_rank=28)
     r = plan.execute()[0]
-    fp = [Fraction(float(x)) for x in wp]
-    fn = [Fraction(float(x)) for x in wn]
-    pa, p1, p0 = Fraction(1), Fraction(1), Fraction(1)
-    for a, b in zip(fp, fn):
-        pa *= a + b
-        p1 *= a
-        p0 *= b
-    want = pa - p1 - p0
-    import math
-    e = want.numerator.bit_length() - want.denominator.bit_length()
-    mant = float(want / Fraction(2) ** e) if e >= 0 else float(want * Fraction(2) ** (-e))
-    m, fe = math.frexp(mant)
-    assert Big(r.mant, r.exp2).rel_diff(Big(m, e + fe)) <= TOL[FP64]
+    assert Big(r.mant, r.exp2).rel_diff(_psi_closed_form(wp, wn)) <= TOL[FP64]
 
 
 def test_sliced_device_path_and_server(w):
@@ -665,3 +689,79 @@ def test_pair_tensor_cores(w, ra, rb, b, k, shuffle):
     tol = (3 * (2 ** k) / 8 + 8) * 2.0 ** -24 + 2.0 ** -21
     assert (np.abs(got - want) / np.abs(want)).max() <= tol
     assert (np.abs(got - scalar) / np.abs(scalar)).max() <= tol + _pair_tol(k, FP32)
+
+
+# ------------------------------------------------------ clause factoring
+
+def _psi_closed_form(wp, wn):
+    """W(psi_n) = prod(w0 + w1) - prod(w1) - prod(w0), exactly (Sec. 3.3's
+    example: every assignment but all-true and all-false satisfies psi)."""
+    import math
+    from fractions import Fraction
+    pa, p1, p0 = Fraction(1), Fraction(1), Fraction(1)
+    for a, b in zip(wp, wn):
+        fa, fb = Fraction(float(a)), Fraction(float(b))
+        pa *= fa + fb
+        p1 *= fa
+        p0 *= fb
+    want = pa - p1 - p0
+    e = want.numerator.bit_length() - want.denominator.bit_length()
+    mant = float(want / Fraction(2) ** e) if e >= 0 else float(want * Fraction(2) ** (-e))
+    m, fe = math.frexp(mant)
+    return Big(m, e + fe)
+
+
+def _long_clause_cnf(n, n_short, n_long, k_long, seed):
+    short = wmcgen.random_kcnf(n, n_short, seed=seed)
+    long_ = wmcgen.random_kcnf(n, n_long, seed=seed + 1000, k=k_long)
+    return wmcgen.Cnf(n, short.clauses + long_.clauses)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("seed", range(3))
+def test_factored_long_clauses_match_oracle(w, precision, seed):
+    """Clause factoring (Def. 3.4, Thm 3.3): formulas with 12-literal
+    clauses, factored into rank-3 gate clauses, against brute force and
+    against the unfactored plan."""
+    n = 22
+    cnf = _long_clause_cnf(n, 40, 4, 12, seed)
+    wp, wn = wmcgen.weights_complementary(n, seed, 0.05, 0.95)
+    want = oracle.brute_force(cnf, wp, wn)[0]
+    fac = plan_for(w, cnf, wp, wn, precision, factor_clauses_above=3)
+    assert fac.info(1).n_aux_vars == 4 * 10
+    got = fac.execute()[0]
+    assert rel(got, want) <= TOL[precision]
+    assert rel(plan_for(w, cnf, wp, wn, precision).execute()[0], want) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("n", [64, 1000])
+def test_factored_psi_closed_form(w, precision, n):
+    """psi_n with rank-n clauses (no plan within rank 30 unfactored; n = 1000
+    is beyond the network's 62-literal clause masks) against its closed
+    form; unit weights give 2^n - 2."""
+    cnf = wmcgen.psi_family(n)
+    wp, wn = wmcgen.weights_independent(n, 11, 0.3, 1.2)
+    r = plan_for(w, cnf, wp, wn, precision, factor_clauses_above=3).execute()[0]
+    assert Big(r.mant, r.exp2).rel_diff(_psi_closed_form(wp, wn)) <= TOL[precision]
+    u = plan_for(w, cnf, None, None, precision, factor_clauses_above=3).execute()[0]
+    assert Big(u.mant, u.exp2).rel_diff(_psi_closed_form([1.0] * n, [1.0] * n)) <= TOL[precision]
+
+
+def test_factored_query_batch_and_slicing(w):
+    """A factored plan batches queries (each against the oracle) and slices
+    (the sliced factored walk equals the unsliced one)."""
+    n = 26
+    cnf = _long_clause_cnf(n, 60, 5, 10, 5)
+    Q = 16
+    wq, wnq = wmcgen.query_weights(n, Q, seed=6, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, FP32, factor_clauses_above=3)
+    got = plan.execute(wq, wnq)
+    for i in range(Q):
+        assert rel(got[i], oracle.bucket_elim(cnf, wq[i], wnq[i])) <= TOL[FP32]
+    r0 = plan.info(1).max_rank
+    sliced = plan_for(w, cnf, None, None, FP64, factor_clauses_above=3, slice_to_rank=r0 - 2)
+    assert sliced.info(1).n_slice_vars > 0
+    s = sliced.execute(wq, wnq)
+    for i in range(Q):
+        assert rel(s[i], oracle.bucket_elim(cnf, wq[i], wnq[i])) <= TOL[FP64]

@@ -270,3 +270,78 @@ def test_slice_ranges_and_combination():
     tiny = w.combine_results([R(0.5, -5000, 0, 0, 0.0), R(0.5, -5001, 0, 0, 0.0)])
     assert (tiny.mant, tiny.exp2) == (0.75, -5000)
     assert w.combine_results([]).mant == 0.0
+
+
+# ------------------------------------------------------ clause factoring
+
+def _long_clause_cnf(n, n_short, n_long, k_long, seed):
+    """Random 3-CNF clauses plus a few long clauses (k_long literals)."""
+    short = wmcgen.random_kcnf(n, n_short, seed=seed)
+    long_ = wmcgen.random_kcnf(n, n_long, seed=seed + 1000, k=k_long)
+    return wmcgen.Cnf(n, short.clauses + long_.clauses)
+
+
+def _leaves_as_cnf(plan, n_vars):
+    """The plan's clause leaves read back as a CNF over the formula's and the
+    auxiliary variables (bit j of fals = the falsifying value of labels[j])."""
+    n_aux = plan.info(1).n_aux_vars
+    clauses = []
+    for kind, labels, fals in plan.leaves():
+        if kind == 0:
+            clauses.append([-(v + 1) if (fals >> j) & 1 else v + 1 for j, v in enumerate(labels)])
+    return wmcgen.Cnf(n_vars + n_aux, clauses), n_aux
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_factored_network_keeps_the_count(seed):
+    """Clause factoring (Def. 3.4, Thm 3.3): every factored clause leaf has
+    rank <= 3, and the factored network, read back through the ABI, has the
+    oracle's weighted count of the original formula when the auxiliary
+    variables weigh 1 for both values; the factored tree evaluated with
+    numpy gives the same value."""
+    w = _lib()
+    n = 14
+    cnf = _long_clause_cnf(n, 18, 3, 9, seed)
+    wp, wn = wmcgen.weights_independent(n, seed, 0.1, 1.0)
+    plan = w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=w.WMC_FP64, factor_clauses_above=3)
+    fcnf, n_aux = _leaves_as_cnf(plan, n)
+    assert n_aux == 3 * (9 - 2)
+    assert max(len(c) for c in fcnf.clauses) <= 3
+    want = oracle.brute_force(cnf, wp, wn)[0]
+    got = oracle.bucket_elim(fcnf, np.concatenate([wp, np.ones(n_aux)]), np.concatenate([wn, np.ones(n_aux)]))
+    assert want.rel_diff(got) <= 1e-15
+    assert abs(evaluate_plan_numpy(plan, wp, wn) - want.to_float()) <= 1e-13 * want.to_float()
+    # clauses at or below the threshold are kept as they are
+    same = w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=w.WMC_FP64, factor_clauses_above=9)
+    assert same.info(1).n_aux_vars == 0
+
+
+def test_factoring_makes_psi_plannable():
+    """psi(300): two rank-300 clause tensors, no plan within rank 30;
+    factored, 2 x 298 auxiliary indices, every leaf of rank <= 3 and a
+    small largest tensor; every launch of the walk stays in bounds."""
+    w = _lib()
+    net = w.Network.from_cnf(wmcgen.psi_family(300))
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net, precision=w.WMC_FP64)
+    assert e.value.status == w.WMC_EPLAN_TOO_BIG
+    p = w.Plan(net, precision=w.WMC_FP64, factor_clauses_above=3)
+    info = p.info(1)
+    assert info.n_aux_vars == 2 * 298
+    assert info.max_rank <= 6
+    assert all(len(labels) <= 3 for _, labels, _ in p.leaves())
+    for Q in (1, 4):
+        n = ctypes.c_int64()
+        assert w.wmc_debug_check_bounds(p.handle, Q, ctypes.byref(n)) == w.WMC_OK, w.wmc_last_error()
+
+
+def test_factoring_option_errors():
+    w = _lib()
+    net = w.Network.from_cnf(wmcgen.psi_family(8))
+    for bad in (1, 2, -1):
+        with pytest.raises(w._abi.WmcError) as e:
+            w.Plan(net, factor_clauses_above=bad)
+        assert e.value.status == w.WMC_EINVAL
+    with pytest.raises(w._abi.WmcError) as e:
+        w.Plan(net, factor_clauses_above=3, order=list(range(1, 9)))
+    assert e.value.status == w.WMC_EINVAL
