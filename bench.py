@@ -312,7 +312,7 @@ def run_ours(args, rank, world):
     k_kind = np.array([kinds[i] for i in range(L)])
     k_bytes = np.array([nbytes[i] for i in range(L)])
     hbm, src = peaks()
-    sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 6) | (k_kind == 8)
+    sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 8) | (k_kind == 9)
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
     # DRAM bytes from one ncu capture of a full-size k2_chain launch (profiles/

@@ -403,6 +403,14 @@ void wmc_set_tensor_cores(int32_t on);
  * device entries and the server report the flush flag and leave the choice
  * to the caller. */
 void wmc_set_fp64_fallback(int32_t on);
+/* Execution option (default 0 = off): consecutive four-step float32
+ * chains of the walk whose every chain has at most max_tiles tiles run as
+ * one launch (k2_chain_seq: tiles handed out in chain order from per-chain
+ * counters, each block waiting, bounded, for the previous chain's
+ * completion count), which replaces a launch and a grid completion per
+ * chain by counter waits.  Results are bit-identical either way.  Affects
+ * plans laid out after the call. */
+void wmc_set_chain_runs(int32_t max_tiles);
 
 /* Host-side bounds check of the walk for batch size Q: replays the index
  * arithmetic of every contraction launch (all bulk copies of every tile,
@@ -417,10 +425,13 @@ const char *wmc_last_error(void);
 int64_t wmc_kernel_launch_count(void);
 /* Test hook: make the next n device allocations fail with WMC_ENOMEM. */
 void wmc_debug_fail_next_allocs(int32_t n);
-/* Test hook: while on != 0, the TMA-staged contraction kernel never issues
- * its first tile's copy, so its bounded mbarrier wait runs out (about a
- * second) and the call reports WMC_ETIMEOUT; no fault, trap or hang.
- * Affects graphs captured while it is set. */
+/* Test hook: while on == 1, the walk's first launch that stages tiles with
+ * bulk copies never issues its first tile's copy; while on == 2, the first
+ * run of chains (k2_chain_seq) never issues the copies of its first chain's
+ * tile 0.  The bounded mbarrier wait runs out (about a second), the other
+ * blocks' bounded waits see the error word, and the call reports
+ * WMC_ETIMEOUT; no fault, trap or hang.  Affects graphs captured while it
+ * is set. */
 void wmc_debug_stall_copies(int32_t on);
 
 #ifdef __cplusplus

@@ -40,6 +40,10 @@ static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent 
 static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
 static std::atomic<int32_t> g_tensor_cores{1};  // dense float32 pair contractions on tcgen05
 static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run again in float64
+// runs of consecutive chains whose every chain has at most this many tiles
+// execute as one k2_chain_seq launch (0, the default: every chain its own
+// launch, which measured faster at every batch size on the grid walks)
+static std::atomic<int32_t> g_chain_runs{0};
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
@@ -49,6 +53,7 @@ extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
 extern "C" void wmc_set_tensor_cores(int32_t on) { g_tensor_cores.store(on); }
 extern "C" void wmc_set_fp64_fallback(int32_t on) { g_fp64_fallback.store(on); }
+extern "C" void wmc_set_chain_runs(int32_t max_tiles) { g_chain_runs.store(max_tiles < 0 ? 0 : max_tiles); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -80,7 +85,7 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -106,6 +111,10 @@ struct Launch {
   int64_t memset_off = 0, memset_bytes = 0;
   int memset_value = 0;
   double alg_bytes = 0;  // contraction: |A| + |B| + |C| bytes
+  // run of chains in one launch (L_K2CSEQ): the chain launches it replaces,
+  // its first entry in the state's parameter table, its counters' offset
+  std::vector<Launch> chains;
+  int64_t seq_first = 0, seq_ctr_off = 0;
 };
 
 }  // namespace
@@ -136,6 +145,11 @@ struct ExecState {
   wmc::dev::SNode *d_snodes = nullptr;
   wmc::dev::STask *d_stasks = nullptr;
   int64_t off_sp = 0;                      // task counter + per-node completion counters
+  // runs of chains (k2_chain_seq): parameters with workspace offsets for
+  // pointers, and two counters per chain (zeroed with the flags)
+  std::vector<wmc::dev::K2CParams> h_seq;
+  wmc::dev::K2CParams *d_seq = nullptr;
+  int64_t off_seqctr = 0;
   int64_t n_clause_entries = 0;
   ClauseLeaf *d_clause = nullptr;
   int64_t *d_first = nullptr, *d_woff = nullptr, *d_wmeta = nullptr;
@@ -158,7 +172,7 @@ struct ExecState {
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     cudaFree(d_clause); cudaFree(d_first); cudaFree(d_woff); cudaFree(d_wmeta);
-    cudaFree(d_snodes); cudaFree(d_stasks);
+    cudaFree(d_snodes); cudaFree(d_stasks); cudaFree(d_seq);
     cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant); cudaFree(d_res_exp); cudaFree(d_res_flags);
     cudaFreeHost(h_res_mant); cudaFreeHost(h_res_exp); cudaFreeHost(h_res_flags);
   }
@@ -722,6 +736,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   st.off_io = off; off += align_up(sizeof(IoDesc));
   st.off_flags = off; off += align_up(4 * (int64_t)Qp);
   st.off_err = off; off += align_up(4);
+  st.off_seqctr = off; off += align_up(8 * (int64_t)plan.nodes.size());  // at most one chain per node
   // small-node phase: which nodes run inside the persistent launch (every
   // node whose subtree is small: at most 2^16 outputs with the query bits,
   // at most 2^8 summed terms)
@@ -1061,6 +1076,71 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       }
     st.launches.push_back(l);
   }
+  // runs of consecutive chains with small tile counts: one k2_chain_seq
+  // launch each (float32, four eliminations, contiguous lanes)
+  if (g_chain_runs.load() > 0 && !st.f64) {
+    auto eligible = [&](const Launch &l) {
+      if (l.kind != L_K2C || l.ti != TF || l.chain_d != 4 || !l.chain_fast || (l.v != 1 && l.v != 2)) return false;
+      for (int i = 0; i < l.chain_d; ++i)
+        if (l.k2c.b_vec[i] == 2) return false;
+      const int64_t tiles = int64_t(1) << (l.k2c.log2_nu + l.k2c.vbits - l.k2c.tb);
+      return tiles <= (int64_t)g_chain_runs.load();
+    };
+    std::vector<Launch> out;
+    int64_t n_seq_chains = 0;
+    for (size_t i = 0; i < st.launches.size();) {
+      size_t j = i;
+      while (j < st.launches.size() && eligible(st.launches[j]) && st.launches[j].v == st.launches[i].v) ++j;
+      if (j - i < 2) {
+        out.push_back(st.launches[i]);
+        ++i;
+        continue;
+      }
+      Launch r;
+      r.kind = L_K2CSEQ;
+      r.ti = TF;
+      r.v = st.launches[i].v;
+      r.chain_d = 4;
+      r.chain_fast = 1;
+      r.seq_first = (int64_t)st.h_seq.size();
+      r.seq_ctr_off = st.off_seqctr + 8 * n_seq_chains;
+      for (size_t k = i; k < j; ++k) {
+        const Launch &l = st.launches[k];
+        wmc::dev::K2CParams cp = l.k2c;
+        // pointers as workspace offsets (the kernel adds the workspace base)
+        auto at = [](int64_t off) { return reinterpret_cast<void *>((uintptr_t)off); };
+        auto meta = [&](int64_t base, int64_t slot) { return at(base + 8 * slot); };
+        cp.P = at(l.off_a);
+        cp.C = at(l.off_c);
+        cp.mp.exp = (const int64_t *)meta(st.off_exp, l.meta_a);
+        cp.mp.maxb = (const unsigned long long *)meta(st.off_max, l.meta_a);
+        cp.mp.minb = (const unsigned long long *)meta(st.off_min, l.meta_a);
+        for (int d = 0; d < l.chain_d; ++d) {
+          cp.S[d] = at(l.off_sc[d]);
+          cp.ms[d].exp = (const int64_t *)meta(st.off_exp, l.meta_sc[d]);
+          cp.ms[d].maxb = (const unsigned long long *)meta(st.off_max, l.meta_sc[d]);
+          cp.ms[d].minb = (const unsigned long long *)meta(st.off_min, l.meta_sc[d]);
+        }
+        cp.mc.exp = (int64_t *)meta(st.off_exp, l.meta_c);
+        cp.mc.maxb = (unsigned long long *)meta(st.off_max, l.meta_c);
+        cp.mc.minb = (unsigned long long *)meta(st.off_min, l.meta_c);
+        cp.mc.flags = (uint32_t *)at(st.off_flags);
+        cp.err = (uint32_t *)at(st.off_err);
+        cp.debug_stall = 0;
+        cp.variant = l.chain_grow ? 1 : (l.chain_shrink ? 2 : 0);
+        st.h_seq.push_back(cp);
+        r.smem = std::max(r.smem, l.smem);
+        r.blocks = std::max(r.blocks, l.blocks);
+        r.alg_bytes += l.alg_bytes;
+        r.chains.push_back(l);
+      }
+      n_seq_chains += (int64_t)(j - i);
+      r.blocks = std::min<int64_t>(r.blocks, 148);
+      out.push_back(std::move(r));
+      i = j;
+    }
+    st.launches.swap(out);
+  }
   Launch fin;
   fin.kind = L_FINAL;
   fin.off_c = st.t_off[(size_t)root];
@@ -1205,6 +1285,22 @@ static void launch_k2c(const Launch &l, const wmc::dev::K2CParams &p, cudaStream
   }
 }
 
+template <int V>
+static void launch_k2cseq_t(const Launch &l, const wmc::dev::K2CParams *seq, char *ws, int stall, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(dev::k2_chain_seq<float, V, 4, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+    attr_set = true;
+  }
+  dev::k2_chain_seq<float, V, 4, true, 0><<<(unsigned)l.blocks, dev::kChainNW * 32 + 32, l.smem, s>>>(
+      seq + l.seq_first, (int32_t)l.chains.size(), (uint32_t *)(ws + l.seq_ctr_off), ws, stall);
+}
+static void launch_k2cseq(const Launch &l, const wmc::dev::K2CParams *seq, char *ws, int stall, cudaStream_t s) {
+  if (l.v == 2) launch_k2cseq_t<2>(l, seq, ws, stall, s);
+  else launch_k2cseq_t<1>(l, seq, ws, stall, s);
+}
+
 static void launch_k1(const Launch &l, const K1Params &p, cudaStream_t s) {
   const unsigned g = (unsigned)l.blocks;
   if (l.ti == TD) dev::k1_generic<double, double, double><<<g, dev::kThreads, 0, s>>>(p);
@@ -1228,6 +1324,7 @@ static int ensure_dev(ExecState &st) {
   if ((rc = up((void **)&st.d_wmeta, st.h_wmeta.data(), sizeof(int64_t) * st.h_wmeta.size()))) return rc;
   if ((rc = up((void **)&st.d_snodes, st.h_snodes.data(), sizeof(wmc::dev::SNode) * st.h_snodes.size()))) return rc;
   if ((rc = up((void **)&st.d_stasks, st.h_stasks.data(), sizeof(wmc::dev::STask) * st.h_stasks.size()))) return rc;
+  if ((rc = up((void **)&st.d_seq, st.h_seq.data(), sizeof(wmc::dev::K2CParams) * st.h_seq.size()))) return rc;
   CUDA_TRY(cudaStreamCreateWithFlags(&st.capture_stream, cudaStreamNonBlocking));
   st.dev_ready = true;
   return WMC_OK;
@@ -1240,18 +1337,22 @@ struct LeafTables {
   const int64_t *first, *woff, *wmeta;
   const wmc::dev::SNode *snodes;
   const wmc::dev::STask *stasks;
+  const wmc::dev::K2CParams *seq;
 };
 
 static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
                          cudaEvent_t *events = nullptr, const LeafTables *tables = nullptr) {
-  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta, st.d_snodes, st.d_stasks};
+  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta, st.d_snodes, st.d_stasks, st.d_seq};
   const LeafTables &tb = tables ? *tables : own;
   int64_t *mexp = (int64_t *)(ws + st.off_exp);
   unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
   unsigned long long *mmin = (unsigned long long *)(ws + st.off_min);
   uint32_t *flags = (uint32_t *)(ws + st.off_flags);
   const IoDesc *io = (const IoDesc *)(ws + st.off_io);
-  bool stall_armed = g_debug_stall.load() != 0;  // test hook: first staged launch only
+  // test hook: 1 = the first staged launch (bulk copies), 2 = the first run of chains
+  const int stall_mode = g_debug_stall.load();
+  bool stall_armed = stall_mode == 1;
+  bool stall_run_armed = stall_mode == 2;
   for (size_t li = 0; li < st.launches.size(); ++li) {
     const Launch &l = st.launches[li];
     switch (l.kind) {
@@ -1339,6 +1440,10 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         launch_k2c(l, cp, s);
         break;
       }
+      case L_K2CSEQ:
+        launch_k2cseq(l, tb.seq, ws, (stall_armed || stall_run_armed) ? 1 : 0, s);
+        stall_armed = stall_run_armed = false;
+        break;
       case L_K4: {
         wmc::dev::K4Params p = l.k4;
         p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
@@ -1619,7 +1724,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -2089,12 +2194,14 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   const size_t b_wmeta = sizeof(int64_t) * st->h_wmeta.size();
   const size_t b_sn = sizeof(wmc::dev::SNode) * st->h_snodes.size();
   const size_t b_stk = sizeof(wmc::dev::STask) * st->h_stasks.size();
+  const size_t b_seq = sizeof(wmc::dev::K2CParams) * st->h_seq.size();
   const size_t o_first = (size_t)align_up((int64_t)b_clause);
   const size_t o_woff = o_first + (size_t)align_up((int64_t)b_first);
   const size_t o_wmeta = o_woff + (size_t)align_up((int64_t)b_woff);
   const size_t o_sn = o_wmeta + (size_t)align_up((int64_t)b_wmeta);
   const size_t o_stk = o_sn + (size_t)align_up((int64_t)b_sn);
-  const size_t o_ws = o_stk + (size_t)align_up((int64_t)b_stk);
+  const size_t o_seq = o_stk + (size_t)align_up((int64_t)b_stk);
+  const size_t o_ws = o_seq + (size_t)align_up((int64_t)b_seq);
   const size_t need = o_ws + (size_t)st->ws_bytes;
   if (need > kNoAllocScratchBytes) {
     set_error("this plan needs %zu bytes of scratch at Q = %d; the static scratch holds %zu",
@@ -2110,11 +2217,13 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   if (b_wmeta) CUDA_TRY(cudaMemcpyAsync(base + o_wmeta, st->h_wmeta.data(), b_wmeta, cudaMemcpyHostToDevice, s));
   if (b_sn) CUDA_TRY(cudaMemcpyAsync(base + o_sn, st->h_snodes.data(), b_sn, cudaMemcpyHostToDevice, s));
   if (b_stk) CUDA_TRY(cudaMemcpyAsync(base + o_stk, st->h_stasks.data(), b_stk, cudaMemcpyHostToDevice, s));
+  if (b_seq) CUDA_TRY(cudaMemcpyAsync(base + o_seq, st->h_seq.data(), b_seq, cudaMemcpyHostToDevice, s));
   char *ws = base + o_ws;
   IoDesc io = io_desc(*plan, d_w_pos, d_w_neg, d_mant, d_exp2, d_flags);
   const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
                           (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta),
-                          (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk)};
+                          (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk),
+                          (const wmc::dev::K2CParams *)(base + o_seq)};
   // the walk's first launch zeroes the flags and metadata it accumulates
   // into; one walk per slice assignment (index slicing)
   for (int64_t eta = 0; eta < n_slices(*plan); ++eta) {
@@ -2194,7 +2303,19 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     ++checked;
   }
   size_t li = 0;
+  std::vector<const Launch *> flat;  // runs of chains checked chain by chain
   for (const Launch &l : st->launches) {
+    if (l.kind != L_K2CSEQ) { flat.push_back(&l); continue; }
+    if (l.seq_ctr_off + 8 * (int64_t)l.chains.size() > st->off_seqctr + 8 * (int64_t)plan->nodes.size() ||
+        l.seq_first + (int64_t)l.chains.size() > (int64_t)st->h_seq.size() || l.smem > 220 * 1024 ||
+        l.blocks < 1 || l.blocks > 148) {
+      set_error("run of chains: counters, parameter table, shared memory or grid out of range");
+      return WMC_EINVAL;
+    }
+    for (const Launch &c : l.chains) flat.push_back(&c);
+  }
+  for (const Launch *lp : flat) {
+    const Launch &l = *lp;
     ++li;
     // k4 offsets are bit scatters onto each tensor's own positions: in
     // bounds by construction

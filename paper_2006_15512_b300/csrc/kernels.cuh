@@ -815,6 +815,7 @@ struct K2CParams {
   uint32_t *err;
   int32_t debug_stall;
   int32_t units;                  // work units per consumer thread per tile (1, 2)
+  int32_t variant;                // 0 plain, 1 growth (first step adds two indices), 2 shrink
 };
 
 __host__ __device__ constexpr uint32_t pdep_c(uint32_t t, uint32_t mask) {
@@ -1250,6 +1251,361 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
     if (smin[q] != kNoMin) atomicMin(cp.mc.minb + q, smin[q]);
   }
 }
+
+// ------------------------------------------ runs of chains in one launch
+//
+// At small batches a chain launch is bound by latency (the launch, the
+// previous grid's completion, one tile's copy-in and write-out), not by
+// HBM.  k2_chain_seq executes a run of consecutive chains of the walk (one
+// T, V, D, FAST, BC; each chain plain, growth or shrink) in one launch.
+// Work is handed out in chain order from per-chain atomic tile counters
+// (next[c]); a block that took tiles of chain c adds their number to
+// done[c] after its stores and its max/min are published (release), and
+// block 0 adds one more after writing C's exponents.  Before chain c's
+// tiles, a block waits (acquire, bounded by %globaltimer) until done[c-1]
+// is complete.  Every tile of chain c-1 was taken by a running block
+// before any tile of chain c is handed out, so the waits end without any
+// assumption about which blocks are resident.  The chain parameters live
+// in global memory with workspace offsets in place of pointers, and are
+// copied to shared memory per chain.
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// waits until *cnt >= target or the walk's error word is set (bounded)
+__device__ __forceinline__ bool seq_wait_count(const uint32_t *cnt, uint32_t target, const uint32_t *err) {
+  if (ld_acquire_u32(cnt) >= target) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 32; ++i)
+      if (ld_acquire_u32(cnt) >= target) return true;
+    if (err && *(volatile const uint32_t *)err) return false;
+    if (globaltimer_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// a pointer stored as an offset into the workspace, made absolute
+template <typename P>
+__device__ __forceinline__ void rebase(P *&p, char *ws) {
+  p = reinterpret_cast<P *>(ws + reinterpret_cast<uintptr_t>(p));
+}
+
+struct ChainSeqShared {
+  unsigned long long full[kMaxStagesC], empty[kMaxStagesC], sbar;
+  uint32_t tile_oc[kMaxStagesC], tile_gb[kMaxChain][kMaxStagesC];
+  int32_t tile_id[kMaxStagesC];
+  int skip;
+  int owns_first;  // this block took tile 0: C's exponent and the extra count are its
+};
+
+// One chain of a run, by this block: tiles taken from next[c] until none
+// are left.
+template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
+__device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShared &sh, unsigned char *dyn_smem,
+                                               uint32_t *next, uint32_t *done, const uint32_t *prev_done,
+                                               uint32_t prev_total, bool reinit, bool stall) {
+  typedef typename Bits<T>::t BT;
+  constexpr int NW = kChainNW;
+  constexpr int NB = D + GROW;
+  const int n_stages = cp.n_stages;
+  const uint32_t run_len = 1u << cp.run_log2;
+  const uint32_t tile_elems = (uint32_t)cp.nruns * run_len;
+  const uint32_t tile_bytes = tile_elems * (uint32_t)sizeof(T);
+  const uint32_t n_tiles = 1u << (cp.log2_nu + cp.vbits - cp.tb);
+  T *stage_buf = reinterpret_cast<T *>(dyn_smem);
+  unsigned char *s_area = dyn_smem + (size_t)n_stages * tile_bytes;
+  unsigned long long *smax = reinterpret_cast<unsigned long long *>(s_area + cp.s_bytes_off[D]);
+  unsigned long long *smin = smax + cp.mc.Qc;
+  T *sscale = reinterpret_cast<T *>(smin + cp.mc.Qc);  // [D][Qc]
+  const T *P = (const T *)cp.P;
+  T *C = (T *)cp.C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // barriers (re-initialised per chain: every phase of the previous chain
+  // has completed) and the S_i copies (the S_i come from earlier launches)
+  if (warp == NW && lane == 0) {
+    if (reinit) {
+      for (int i = 0; i < kMaxStagesC; ++i) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&sh.full[i])) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&sh.empty[i])) : "memory");
+      }
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&sh.sbar)) : "memory");
+    }
+    for (int i = 0; i < kMaxStagesC; ++i) {
+      mbar_init(&sh.full[i], 1);
+      mbar_init(&sh.empty[i], NW);
+    }
+    mbar_init(&sh.sbar, 1);
+    mbar_fence_init();
+    mbar_expect_tx(&sh.sbar, cp.s_copy_bytes);
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+      bulk_g2s(s_area + cp.s_bytes_off[s], cp.S[s], (uint32_t)sizeof(T) << cp.s_log2[s], &sh.sbar);
+  }
+  // the previous chain's outputs and metadata, complete
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    if (prev_done) ok = seq_wait_count(prev_done, prev_total, cp.err);
+    if (!ok && cp.err) atomicOr(cp.err, 1u);
+    sh.skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
+    sh.owns_first = 0;
+  }
+  __syncthreads();
+  const bool skip = sh.skip != 0;
+  for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+    smax[q] = 0;
+    smin[q] = kNoMin;
+    if (!skip) {
+#pragma unroll
+      for (int s = 0; s < D; ++s) {
+        T v = operand_scale<T>(cp.ms[s], q, 1);
+        if (s == 0 && cp.fold_sp) v *= operand_scale<T>(cp.mp, q, 1);
+        sscale[s * cp.mc.Qc + q] = v;
+      }
+    }
+  }
+  __syncthreads();
+  const bool s_landed = __syncthreads_and(mbar_wait(&sh.sbar, 0) ? 1 : 0) != 0;
+  if (!skip && s_landed) {
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      T *dst = reinterpret_cast<T *>(s_area + cp.s_bytes_off[s]);
+      const uint32_t n = 1u << cp.s_log2[s];
+      const T *sc = sscale + s * cp.mc.Qc;
+      const uint32_t qm = (uint32_t)cp.ms[s].qmask;
+#pragma unroll 4
+      for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) dst[j] *= sc[j & qm];
+    }
+  } else if (!s_landed && threadIdx.x == 0 && cp.err) {
+    atomicOr(cp.err, 1u);
+  }
+  __syncthreads();
+  const bool run = !skip && s_landed;
+  uint32_t my_tiles = 0;
+  if (warp == NW) {
+    // ---- producer: tiles from the chain's counter, a sentinel at the end
+    if (run) {
+      const uint32_t run_src = lane < cp.nruns ? cp.run_off[lane] : 0u;
+      const uint32_t run_dst = (uint32_t)lane * run_len;
+      fence_proxy_async_global();  // generic-proxy writes of the previous chain, seen by the bulk copies
+      bool ok = true;
+      uint32_t n_issued = 0;  // tiles whose copies were issued
+      for (uint32_t i = 0;; ++i) {
+        const int st = (int)(i % (uint32_t)n_stages);
+        if (i >= (uint32_t)n_stages &&
+            !__all_sync(0xffffffffu, mbar_wait(&sh.empty[st], ((i / n_stages) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= n_tiles) {
+          if (lane == 0) {
+            sh.tile_id[st] = -1;
+            mbar_arrive(&sh.full[st]);  // the sentinel: no copies
+          }
+          __syncwarp();
+          break;
+        }
+        uint32_t base = t << cp.tb, oc = base;
+        for (int j = 0; j < cp.n_ins; ++j) base = insert0(base, cp.ins[j]);
+        for (int j = 0; j < cp.n_insc; ++j) oc = insert0(oc, cp.insc[j]);
+        if (t == 0 && lane == 0) sh.owns_first = 1;
+        if (lane < D) {
+          uint32_t gb = 0;
+          for (int j = 0; j < cp.n_seg[lane]; ++j)
+            gb |= ((oc >> cp.seg_c[lane][j]) & ((1u << cp.seg_len[lane][j]) - 1u)) << cp.seg_b[lane][j];
+          sh.tile_gb[lane][st] = gb;
+        }
+        if (lane == 0) {
+          sh.tile_oc[st] = oc;
+          sh.tile_id[st] = (int32_t)t;
+          mbar_expect_tx(&sh.full[st], tile_bytes);
+        }
+        __syncwarp();
+        if (!(stall && t == 0) && lane < cp.nruns)  // test hook: tile 0's copies never issued
+          bulk_g2s(stage_buf + (size_t)st * tile_elems + run_dst, P + base + run_src,
+                   run_len * (uint32_t)sizeof(T), &sh.full[st]);
+        n_issued = i + 1;
+      }
+      if (!ok && lane == 0) {
+        if (cp.err) atomicOr(cp.err, 1u);
+        // a wait gave up: copies of the last issued tiles may be in flight
+        for (uint32_t j = n_issued > (uint32_t)n_stages ? n_issued - n_stages : 0; j < n_issued; ++j)
+          mbar_wait(&sh.full[j % n_stages], (j / n_stages) & 1);
+      }
+    }
+    __syncwarp();
+  } else if (run) {
+    // ---- consumers, as in k2_chain (tiles in the order the producer took them)
+    constexpr uint32_t es = (uint32_t)sizeof(T);
+    const int J = cp.units;
+    uint32_t la_0 = 0, la_1 = 0, ocl_0 = 0, ocl_1 = 0, gl_0[D], gl_1[D];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t wl = (threadIdx.x + (uint32_t)j * NW * 32) * V;
+      uint32_t la = wl, ocl = wl;
+      for (int i = 0; i < cp.n_low; ++i) la = insert0(la, cp.low[i]);
+      for (int i = 0; i < cp.n_insc; ++i) ocl = insert0(ocl, cp.insc[i]);
+      (j ? la_1 : la_0) = la * es;
+      (j ? ocl_1 : ocl_0) = ocl;
+#pragma unroll
+      for (int s = 0; s < D; ++s) {
+        uint32_t g = 0;
+        for (int jj = 0; jj < cp.n_seg[s]; ++jj)
+          g |= ((ocl >> cp.seg_c[s][jj]) & ((1u << cp.seg_len[s][jj]) - 1u)) << cp.seg_b[s][jj];
+        (j ? gl_1[s] : gl_0[s]) = g * es + cp.s_bytes_off[s];
+      }
+    }
+    const uint32_t wl0 = threadIdx.x * V, ocl = ocl_0;
+    const uint32_t stage0 = smem_addr(dyn_smem), s_area0 = smem_addr(s_area);
+    T sp[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      sp[e] = (FAST || cp.fold_sp) ? (T)1 : operand_scale<T>(cp.mp, (int)(wl0 + e), 1);
+    T tmax[V];
+    BT tminm1[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) { tmax[e] = (T)0; tminm1[e] = (BT)~(BT)0; }
+    for (uint32_t i = 0;; ++i) {
+      const int st = (int)(i % (uint32_t)n_stages);
+      const bool landed = __all_sync(0xffffffffu, mbar_wait(&sh.full[st], (i / n_stages) & 1));
+      if (!landed) {
+        if (lane == 0 && cp.err) atomicOr(cp.err, 1u);
+        break;
+      }
+      if (sh.tile_id[st] < 0) break;  // no more tiles of this chain
+      ++my_tiles;
+      for (int j = 0; j < J; ++j) {
+        const uint32_t tile = stage0 + (uint32_t)st * tile_bytes + (j ? la_1 : la_0);
+        T *cbase = C + (sh.tile_oc[st] | (j ? ocl_1 : ocl_0));
+        uint32_t g[D];
+#pragma unroll
+        for (int s = 0; s < D; ++s) g[s] = s_area0 + (j ? gl_1[s] : gl_0[s]) + sh.tile_gb[s][st] * es;
+        T a[1 << NB][V];
+#pragma unroll
+        for (int s = 0; s < (1 << D); ++s) {
+          LdsV<T, V>::ld(tile + cp.pA[s], a[s]);
+          if (!FAST) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) a[s][e] *= sp[e];
+          }
+        }
+        if (j == J - 1) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.empty[st]);
+        }
+        ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, 0>::run(cp, g, a);
+#pragma unroll
+        for (int s = 0; s < (1 << NB); ++s) {
+          if (SHRINK && ((s >> (D - 1)) & 1)) continue;
+          vstore<T, V>(cbase + cp.dC[s], a[s]);
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            tmax[e] = fmax(tmax[e], fabs(a[s][e]));
+            tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
+          }
+        }
+      }
+    }
+    const uint32_t qmask_c = (uint32_t)(cp.mc.Qc - 1);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const int q = (int)((ocl + e) & qmask_c);
+      if (tmax[e] != (T)0) atomicMax(smax + q, abs_bits(tmax[e]));
+      if (tminm1[e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[e] + (BT)1));
+    }
+  }
+  __syncthreads();
+  // C's exponent and flush test (the block that took tile 0), then this
+  // block's max/min
+  const bool first = sh.owns_first != 0;
+  if (first && run) {
+    for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+      const int qp = q & cp.mp.qmask;
+      int64_t e = cp.mp.exp[qp] + pow2_exp_of(cp.mp.maxb[qp], T());
+      bool any_zero = cp.mp.minb[qp] == kNoMin;
+      T lo = any_zero ? (T)0 : from_bits<T>(cp.mp.minb[qp]) * operand_scale<T>(cp.mp, qp, 1);
+#pragma unroll
+      for (int s = 0; s < D; ++s) {
+        const int qs = q & cp.ms[s].qmask;
+        e += cp.ms[s].exp[qs] + pow2_exp_of(cp.ms[s].maxb[qs], T());
+        if (cp.ms[s].minb[qs] == kNoMin) any_zero = true;
+        else lo *= from_bits<T>(cp.ms[s].minb[qs]) * operand_scale<T>(cp.ms[s], qs, 1);
+      }
+      cp.mc.exp[q] = e;
+      if (cp.mc.flags && !any_zero && below_normal(lo)) {
+        if (cp.mc.Qc > 1) atomicOr(cp.mc.flags + q, 2u);
+        else
+          for (int qq = 0; qq < cp.mc.Q; ++qq) atomicOr(cp.mc.flags + qq, 2u);
+      }
+    }
+  }
+  if (run)
+    for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+      if (smax[q]) atomicMax(cp.mc.maxb + q, smax[q]);
+      if (smin[q] != kNoMin) atomicMin(cp.mc.minb + q, smin[q]);
+    }
+  // every consumer thread counted the same tiles; one count per block
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();
+    __threadfence();
+    red_release_add_u32(done, my_tiles + (first ? 1u : 0u));
+  }
+  __syncthreads();
+}
+
+// seq: the run's chain parameters with workspace offsets for pointers;
+// ctr: 2 counters per chain (next, done), zero at the start of the walk
+template <typename T, int V, int D, bool FAST, int BC>
+__global__ void __launch_bounds__(kChainNW * 32 + 32, 1)
+    k2_chain_seq(const K2CParams *__restrict__ seq, int32_t n_chains, uint32_t *ctr, char *ws, int32_t debug_stall) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  __shared__ K2CParams cp;
+  __shared__ ChainSeqShared sh;
+  for (int32_t c = 0; c < n_chains; ++c) {
+    {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(seq + c);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&cp);
+      for (uint32_t i = threadIdx.x; i < sizeof(K2CParams) / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      rebase(cp.P, ws); rebase(cp.C, ws);
+      rebase(cp.mp.exp, ws); rebase(cp.mp.maxb, ws); rebase(cp.mp.minb, ws);
+      rebase(cp.mc.exp, ws); rebase(cp.mc.maxb, ws); rebase(cp.mc.minb, ws); rebase(cp.mc.flags, ws);
+      rebase(cp.err, ws);
+      for (int s = 0; s < D; ++s) {
+        rebase(cp.S[s], ws);
+        rebase(cp.ms[s].exp, ws); rebase(cp.ms[s].maxb, ws); rebase(cp.ms[s].minb, ws);
+      }
+    }
+    __syncthreads();
+    uint32_t *next = ctr + 2 * c, *done = next + 1;
+    const uint32_t *prev_done = c ? ctr + 2 * (c - 1) + 1 : nullptr;
+    const uint32_t prev_total =
+        c ? (1u << (__ldg(&seq[c - 1].log2_nu) + __ldg(&seq[c - 1].vbits) - __ldg(&seq[c - 1].tb))) + 1u : 0u;
+    if (cp.variant == 1)
+      chain_seq_pass<T, V, D, FAST, BC, 1, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
+                                                debug_stall && c == 0);
+    else if (cp.variant == 2)
+      chain_seq_pass<T, V, D, FAST, BC, 0, 1>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
+                                                debug_stall && c == 0);
+    else
+      chain_seq_pass<T, V, D, FAST, BC, 0, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
+                                                debug_stall && c == 0);
+  }
+}
+
 
 // ------------------------------------------------------------ K4 dense
 //

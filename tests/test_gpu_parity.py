@@ -765,3 +765,120 @@ def test_factored_query_batch_and_slicing(w):
     s = sliced.execute(wq, wnq)
     for i in range(Q):
         assert rel(s[i], oracle.bucket_elim(cnf, wq[i], wnq[i])) <= TOL[FP64]
+
+
+# ------------------------------------------------------ runs of chains
+
+def _launch_kinds(w, plan, Q, wq, wnq):
+    """Kinds of the walk's launches (wmc_profile_walk: 8 chain, 9 run of chains)."""
+    import ctypes
+    info = plan.info(Q)
+    dev = torch.device("cuda", 0)
+    d_wp = torch.from_numpy(np.ascontiguousarray(wq[:Q])).to(dev)
+    d_wn = torch.from_numpy(np.ascontiguousarray(wnq[:Q])).to(dev)
+    ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev)
+    mant = torch.empty(Q, dtype=torch.float64, device=dev)
+    ex = torch.empty(Q, dtype=torch.int64, device=dev)
+    fl = torch.empty(Q, dtype=torch.int32, device=dev)
+    nmax = 8192
+    node_ms = (ctypes.c_float * nmax)()
+    kinds = (ctypes.c_int32 * nmax)()
+    nbytes = (ctypes.c_double * nmax)()
+    nl = ctypes.c_int64()
+    w.check(w.wmc_profile_walk(plan.handle, Q, ctypes.c_void_p(d_wp.data_ptr()), ctypes.c_void_p(d_wn.data_ptr()),
+                               ctypes.c_void_p(ws.data_ptr()), info.workspace_bytes, ctypes.c_void_p(mant.data_ptr()),
+                               ctypes.c_void_p(ex.data_ptr()), ctypes.c_void_p(fl.data_ptr()),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), nmax, node_ms, kinds, nbytes,
+                               ctypes.byref(nl)), "wmc_profile_walk")
+    return [kinds[i] for i in range(min(nl.value, nmax))]
+
+
+@pytest.mark.parametrize("Q", [4, 16, 64])
+def test_chain_runs_match_single_launches(w, Q):
+    """Runs of consecutive chains in one launch (k2_chain_seq: tiles handed
+    out in chain order, each block waiting for the previous chain's
+    completion count) give the bits of one launch per chain, and the
+    oracle's values."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=12, lo=0.05, hi=0.95)
+    single = plan_for(w, cnf, None, None, FP32)
+    n1 = single.info(Q).launches_per_walk
+    r1 = single.execute(wq, wnq)
+    try:
+        w.wmc_set_chain_runs(512)
+        runs = plan_for(w, cnf, None, None, FP32)
+        n2 = runs.info(Q).launches_per_walk
+        assert 9 in _launch_kinds(w, runs, Q, wq, wnq)
+        r2 = runs.execute(wq, wnq)
+    finally:
+        w.wmc_set_chain_runs(0)
+    assert n2 * 4 < n1
+    for q in range(Q):
+        assert (r1[q].mant, r1[q].exp2, r1[q].flags) == (r2[q].mant, r2[q].exp2, r2[q].flags)
+    col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
+    for q in (0, Q - 1):
+        assert rel(r2[q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[FP32]
+
+
+def test_chain_runs_on_two_streams(w):
+    """Two walks whose runs of chains execute at the same time on two
+    streams (no block waits on work that a non-running block holds) give
+    the results of the walks one at a time."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    Q = 8
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, 2 * Q, seed=13, lo=0.05, hi=0.95)
+    try:
+        w.wmc_set_chain_runs(512)
+        plan = plan_for(w, cnf, None, None, FP32)
+        info = plan.info(Q)
+    finally:
+        w.wmc_set_chain_runs(0)
+    ref = [plan.execute(wq[k * Q:(k + 1) * Q], wnq[k * Q:(k + 1) * Q]) for k in range(2)]
+    dev = torch.device("cuda", 0)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    bufs = []
+    for k in range(2):
+        d_wp = torch.from_numpy(np.ascontiguousarray(wq[k * Q:(k + 1) * Q])).to(dev)
+        d_wn = torch.from_numpy(np.ascontiguousarray(wnq[k * Q:(k + 1) * Q])).to(dev)
+        ws = torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev)
+        bufs.append((d_wp, d_wn, ws, torch.empty(Q, dtype=torch.float64, device=dev),
+                     torch.empty(Q, dtype=torch.int64, device=dev), torch.empty(Q, dtype=torch.int32, device=dev)))
+    torch.cuda.synchronize()
+    for rep in range(6):
+        for k in range(2):
+            d_wp, d_wn, ws, m, e, f = bufs[k]
+            plan.execute_device(Q, d_wp, d_wn, ws, m, e, f, stream=streams[k].cuda_stream)
+    torch.cuda.synchronize()
+    for k in range(2):
+        m, e = bufs[k][3].cpu().numpy(), bufs[k][4].cpu().numpy()
+        for q in range(Q):
+            r = ref[k][q]
+            got = Big(float(m[q]), int(e[q]))
+            assert got.rel_diff(Big(r.mant, r.exp2)) <= 1e-15
+
+
+def test_chain_run_bounded_wait_times_out_cleanly(w):
+    """Failure detection inside a run of chains without a GPU fault: the
+    test hook keeps the first tile of the run's first chain from being
+    copied; the block's bounded wait runs out, the others' waits for that
+    chain see the error word, the call returns WMC_ETIMEOUT and the context
+    stays usable."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    Q = 8
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=14, lo=0.05, hi=0.95)
+    w.wmc_set_chain_runs(512)
+    try:
+        probe = plan_for(w, cnf, None, None, FP32)
+        assert 9 in _launch_kinds(w, probe, Q, wq, wnq)  # the walk has runs of chains
+        w.wmc_debug_stall_copies(2)
+        plan = plan_for(w, cnf, None, None, FP32)
+        with pytest.raises(w._abi.WmcError) as e:
+            plan.execute(wq, wnq)
+        assert e.value.status == w.WMC_ETIMEOUT
+    finally:
+        w.wmc_debug_stall_copies(0)
+        w.wmc_set_chain_runs(0)
+    plan2 = plan_for(w, cnf, None, None, FP32)
+    res = plan2.execute(wq, wnq)
+    col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
+    assert rel(res[0], oracle.bucket_elim(cnf, wq[0], wnq[0], order=col)) <= TOL[FP32]
