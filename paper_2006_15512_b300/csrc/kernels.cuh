@@ -1303,15 +1303,30 @@ struct ChainSeqShared {
   uint32_t tile_oc[kMaxStagesC], tile_gb[kMaxChain][kMaxStagesC];
   int32_t tile_id[kMaxStagesC];
   int skip;
-  int owns_first;  // this block took tile 0: C's exponent and the extra count are its
+  int owns_first;     // this block took tile 0: C's exponent and the extra count are its
+  uint32_t pre_tile;  // the next chain's first tile, taken at the end of this one
 };
+constexpr uint32_t kNoTile = 0xffffffffu;
+
+__device__ __forceinline__ void chain_seq_rebase(K2CParams &cp, char *ws) {
+  rebase(cp.P, ws); rebase(cp.C, ws);
+  rebase(cp.mp.exp, ws); rebase(cp.mp.maxb, ws); rebase(cp.mp.minb, ws);
+  rebase(cp.mc.exp, ws); rebase(cp.mc.maxb, ws); rebase(cp.mc.minb, ws); rebase(cp.mc.flags, ws);
+  rebase(cp.err, ws);
+  for (int s = 0; s < kMaxChain; ++s) {
+    rebase(cp.S[s], ws);
+    rebase(cp.ms[s].exp, ws); rebase(cp.ms[s].maxb, ws); rebase(cp.ms[s].minb, ws);
+  }
+}
 
 // One chain of a run, by this block: tiles taken from next[c] until none
 // are left.
 template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShared &sh, unsigned char *dyn_smem,
                                                uint32_t *next, uint32_t *done, const uint32_t *prev_done,
-                                               uint32_t prev_total, bool reinit, bool stall) {
+                                               uint32_t prev_total, bool reinit, bool stall,
+                                               const K2CParams *next_src, K2CParams *next_dst, char *ws,
+                                               uint32_t *next_ctr) {
   typedef typename Bits<T>::t BT;
   constexpr int NW = kChainNW;
   constexpr int NB = D + GROW;
@@ -1355,7 +1370,6 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
     if (prev_done) ok = seq_wait_count(prev_done, prev_total, cp.err);
     if (!ok && cp.err) atomicOr(cp.err, 1u);
     sh.skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
-    sh.owns_first = 0;
   }
   __syncthreads();
   const bool skip = sh.skip != 0;
@@ -1405,7 +1419,7 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
           break;
         }
         uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(next, 1u);
+        if (lane == 0) t = (i == 0 && sh.pre_tile != kNoTile) ? sh.pre_tile : atomicAdd(next, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= n_tiles) {
           if (lane == 0) {
@@ -1415,10 +1429,11 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
           __syncwarp();
           break;
         }
+        if (t == 0 && lane == 0) sh.owns_first = 1;
         uint32_t base = t << cp.tb, oc = base;
         for (int j = 0; j < cp.n_ins; ++j) base = insert0(base, cp.ins[j]);
         for (int j = 0; j < cp.n_insc; ++j) oc = insert0(oc, cp.insc[j]);
-        if (t == 0 && lane == 0) sh.owns_first = 1;
+
         if (lane < D) {
           uint32_t gb = 0;
           for (int j = 0; j < cp.n_seg[lane]; ++j)
@@ -1444,6 +1459,20 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
       }
     }
     __syncwarp();
+    // while the consumers finish: the next chain's parameters, and its first
+    // tile (every tile of this chain has been taken, so holding one of the
+    // next chain cannot keep this chain from completing)
+    if (next_src) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(next_src);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(next_dst);
+      for (uint32_t k = lane; k < sizeof(K2CParams) / 4; k += 32) dst[k] = __ldg(src + k);
+      __syncwarp();
+      if (lane == 0) {
+        chain_seq_rebase(*next_dst, ws);
+        sh.pre_tile = atomicAdd(next_ctr, 1u);
+      }
+      __syncwarp();
+    }
   } else if (run) {
     // ---- consumers, as in k2_chain (tiles in the order the producer took them)
     constexpr uint32_t es = (uint32_t)sizeof(T);
@@ -1560,6 +1589,8 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
     fence_proxy_async_global();
     __threadfence();
     red_release_add_u32(done, my_tiles + (first ? 1u : 0u));
+    sh.owns_first = (next_src && sh.pre_tile == 0) ? 1 : 0;  // the next chain's tile 0, taken early
+    if (!next_src) sh.pre_tile = kNoTile;
   }
   __syncthreads();
 }
@@ -1570,39 +1601,40 @@ template <typename T, int V, int D, bool FAST, int BC>
 __global__ void __launch_bounds__(kChainNW * 32 + 32, 1)
     k2_chain_seq(const K2CParams *__restrict__ seq, int32_t n_chains, uint32_t *ctr, char *ws, int32_t debug_stall) {
   extern __shared__ __align__(128) unsigned char dyn_smem[];
-  __shared__ K2CParams cp;
+  __shared__ K2CParams cpb[2];  // this chain's parameters and the next one's
   __shared__ ChainSeqShared sh;
+  {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(seq);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&cpb[0]);
+    for (uint32_t i = threadIdx.x; i < sizeof(K2CParams) / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    chain_seq_rebase(cpb[0], ws);
+    sh.pre_tile = kNoTile;
+    sh.owns_first = 0;
+  }
+  __syncthreads();
   for (int32_t c = 0; c < n_chains; ++c) {
-    {
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(seq + c);
-      uint32_t *dst = reinterpret_cast<uint32_t *>(&cp);
-      for (uint32_t i = threadIdx.x; i < sizeof(K2CParams) / 4; i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      rebase(cp.P, ws); rebase(cp.C, ws);
-      rebase(cp.mp.exp, ws); rebase(cp.mp.maxb, ws); rebase(cp.mp.minb, ws);
-      rebase(cp.mc.exp, ws); rebase(cp.mc.maxb, ws); rebase(cp.mc.minb, ws); rebase(cp.mc.flags, ws);
-      rebase(cp.err, ws);
-      for (int s = 0; s < D; ++s) {
-        rebase(cp.S[s], ws);
-        rebase(cp.ms[s].exp, ws); rebase(cp.ms[s].maxb, ws); rebase(cp.ms[s].minb, ws);
-      }
-    }
-    __syncthreads();
+    const K2CParams &cp = cpb[c & 1];
     uint32_t *next = ctr + 2 * c, *done = next + 1;
     const uint32_t *prev_done = c ? ctr + 2 * (c - 1) + 1 : nullptr;
-    const uint32_t prev_total =
-        c ? (1u << (__ldg(&seq[c - 1].log2_nu) + __ldg(&seq[c - 1].vbits) - __ldg(&seq[c - 1].tb))) + 1u : 0u;
+    const K2CParams &pp = cpb[(c + 1) & 1];  // the previous chain's (until the prefetch overwrites it)
+    const uint32_t prev_total = c ? (1u << (pp.log2_nu + pp.vbits - pp.tb)) + 1u : 0u;
+    const bool more = c + 1 < n_chains;
+    const K2CParams *nsrc = more ? seq + c + 1 : nullptr;
+    K2CParams *ndst = &cpb[(c + 1) & 1];
+    uint32_t *nctr = more ? ctr + 2 * (c + 1) : nullptr;
+    const bool stall = debug_stall && c == 0;
     if (cp.variant == 1)
-      chain_seq_pass<T, V, D, FAST, BC, 1, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
-                                                debug_stall && c == 0);
+      chain_seq_pass<T, V, D, FAST, BC, 1, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0, stall,
+                                               nsrc, ndst, ws, nctr);
     else if (cp.variant == 2)
-      chain_seq_pass<T, V, D, FAST, BC, 0, 1>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
-                                                debug_stall && c == 0);
+      chain_seq_pass<T, V, D, FAST, BC, 0, 1>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0, stall,
+                                               nsrc, ndst, ws, nctr);
     else
-      chain_seq_pass<T, V, D, FAST, BC, 0, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0,
-                                                debug_stall && c == 0);
+      chain_seq_pass<T, V, D, FAST, BC, 0, 0>(cp, sh, dyn_smem, next, done, prev_done, prev_total, c > 0, stall,
+                                               nsrc, ndst, ws, nctr);
   }
 }
 
