@@ -882,3 +882,37 @@ def test_chain_run_bounded_wait_times_out_cleanly(w):
     res = plan2.execute(wq, wnq)
     col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
     assert rel(res[0], oracle.bucket_elim(cnf, wq[0], wnq[0], order=col)) <= TOL[FP32]
+
+
+def test_serving_config_as_benchmarked(w):
+    """The timed configuration itself: the 16x100 grid network, waves of
+    Q = 256 queries from the pool w ~ U(0.05, 0.95) (seed 1), two waves in
+    flight on two streams with their own workspaces (graph replays); sampled
+    queries of each wave against the oracle, one by one."""
+    H, W_, Q = 16, 100, 256
+    cnf = wmcgen.grid_cnf(H, W_, 1)
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, 4096, seed=1, lo=0.05, hi=0.95)  # the pool
+    plan = plan_for(w, cnf, None, None, FP32)
+    info = plan.info(Q)
+    dev = torch.device("cuda", 0)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    slots = []
+    for k in range(2):
+        slots.append((torch.from_numpy(np.ascontiguousarray(wq[k * Q:(k + 1) * Q])).to(dev),
+                      torch.from_numpy(np.ascontiguousarray(wnq[k * Q:(k + 1) * Q])).to(dev),
+                      torch.empty(info.workspace_bytes, dtype=torch.uint8, device=dev),
+                      torch.empty(Q, dtype=torch.float64, device=dev), torch.empty(Q, dtype=torch.int64, device=dev),
+                      torch.empty(Q, dtype=torch.int32, device=dev)))
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for k in range(2):
+            d_wp, d_wn, ws, m, e, f = slots[k]
+            plan.execute_device(Q, d_wp, d_wn, ws, m, e, f, stream=streams[k].cuda_stream)
+    torch.cuda.synchronize()
+    col = [i * W_ + j + 1 for j in range(W_) for i in range(H)]
+    for k in range(2):
+        m, e, f = (slots[k][3].cpu().numpy(), slots[k][4].cpu().numpy(), slots[k][5].cpu().numpy())
+        for q in (0, 37, 128, Q - 1):
+            assert int(f[q]) & 0x8 == 0
+            want = oracle.bucket_elim(cnf, wq[k * Q + q], wnq[k * Q + q], order=col)
+            assert Big(float(m[q]), int(e[q])).rel_diff(want) <= TOL[FP32]
