@@ -359,7 +359,7 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
   const int total_w_log2 = p2.log2_nu + p2.vbits;
   if (total_w_log2 < tb + 3) return false;
   if (p_has_q && (dev::kThreads * V) % Qp != 0) return false;
-  if (LS.size() > 12) return false;  // S is staged in shared memory
+  if (LS.size() > 13) return false;  // S is staged in shared memory
   std::vector<int> ins(p2.insA, p2.insA + p2.n_insA);
   std::vector<int> kept;
   for (int q = 0; q < (int)LP.size(); ++q)
@@ -426,7 +426,7 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
     for (int32_t l : cur) if (pos_of(C, l) < 0) summed.push_back(l);
     for (int32_t l : S) if (pos_of(C, l) < 0 && pos_of(cur, l) < 0) summed.push_back(l);
     for (int32_t l : S) if (pos_of(C, l) >= 0 && pos_of(cur, l) < 0) added.push_back(l);
-    if (summed.size() != 1 || S.size() > 12) return false;
+    if (summed.size() != 1 || S.size() > 13) return false;
     x[(size_t)i] = summed[0];
     p[(size_t)i] = pos_of(LP, x[(size_t)i]);
     if (p[(size_t)i] < 0 || pos_of(cur, x[(size_t)i]) != p[(size_t)i] || pos_of(S, x[(size_t)i]) < 0) return false;
@@ -560,6 +560,13 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   int tb = 0;
   while ((1 << tb) < nthr * V * cp.units) ++tb;
   if (cp.units == 2 && cp.log2_nu + vbits < tb + 3) { cp.units = 1; --tb; }
+  {
+    // two stages of two-unit tiles must fit beside the staged S_i (large
+    // batches carry the query bits in every S_i: 2^13 entries at Q = 512)
+    size_t s_need = (16 + (size_t)D * es) * (size_t)Qp;
+    for (int i = 0; i < D; ++i) s_need += ((es << cp.s_log2[i]) + 15) & ~(size_t)15;
+    if (cp.units == 2 && 2 * ((size_t)es << (tb + D)) + s_need > 220 * 1024) { cp.units = 1; --tb; }
+  }
   if (cp.log2_nu + vbits < tb + 3) return false;
   std::vector<int> kept;
   for (int q = 0; q < rP; ++q)

@@ -916,3 +916,20 @@ def test_serving_config_as_benchmarked(w):
             assert int(f[q]) & 0x8 == 0
             want = oracle.bucket_elim(cnf, wq[k * Q + q], wnq[k * Q + q], order=col)
             assert Big(float(m[q]), int(e[q])).rel_diff(want) <= TOL[FP32]
+
+
+def test_large_batch_chains_are_batch_invariant(w):
+    """Waves of 512 queries (bucket tensors of 2^13 entries with the query
+    bits: one work unit per thread beside the staged S_i) still run as
+    chains, and give each query the bits it gets alone."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    Q = 512
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=15, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, FP32)
+    assert plan.info(Q).launches_per_walk < 500
+    res = plan.execute(wq, wnq)
+    for q in (0, 300, Q - 1):
+        alone = plan.execute(wq[q:q + 1], wnq[q:q + 1])[0]
+        assert (res[q].mant, res[q].exp2) == (alone.mant, alone.exp2)
+    col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
+    assert rel(res[300], oracle.bucket_elim(cnf, wq[300], wnq[300], order=col)) <= TOL[FP32]
