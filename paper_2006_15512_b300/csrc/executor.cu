@@ -342,6 +342,10 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   }
   vmax = 1 << vbits;
   kmax = std::max(k, f) <= 1 ? 1 : (std::max(k, f) <= 2 ? 2 : (std::max(k, f) == 3 ? 3 : 4));
+  // four summed or S-free bits: 16 x 16 S terms per unit, read from shared
+  // memory (S staged once per block, at most 2^12 entries)
+  p.s_log2 = (int32_t)LS.size();
+  p.s_staged = (kmax == 4 && vbits == 0 && LS.size() <= 12) ? 1 : 0;
   fmax = kmax;
   return true;
 }
@@ -1163,7 +1167,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
 
 template <typename T, int V, int K>
 static void launch_k2_t(const K2Params &p, int64_t blocks, cudaStream_t s) {
-  dev::k2_stream<T, V, K, K><<<(unsigned)blocks, dev::kThreads, 0, s>>>(p);
+  const size_t smem = p.s_staged ? sizeof(T) << p.s_log2 : 0;  // staged S (at most 32 KB)
+  dev::k2_stream<T, V, K, K><<<(unsigned)blocks, dev::kThreads, smem, s>>>(p);
 }
 
 template <typename T, int V>

@@ -245,6 +245,8 @@ struct K2Params {
   uint32_t dBf[16];  // offset of S-free assignment f in S
   uint32_t dC[16];   // ... in C
   uint32_t dBv[4];  // offset in S of vector lane e
+  int32_t s_staged;  // S (2^s_log2 entries) staged in shared memory, pre-scaled (k2_stream, K = 4)
+  int32_t s_log2;
 };
 
 template <typename T, int V> struct VecT;
@@ -278,8 +280,15 @@ __device__ __forceinline__ void vstore(T *p, const T (&r)[V]) {
 template <typename T, int V, int K, int F>
 __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && sizeof(T) == 4) ? 2 : 1)))
     k2_stream(K2Params p) {
+  extern __shared__ __align__(16) unsigned char k2s_smem[];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  if (K == 4 && V == 1 && p.s_staged) {
+    T *sS = reinterpret_cast<T *>(k2s_smem);
+    const T *Bg = (const T *)p.B;
+    for (uint32_t j = threadIdx.x; j < (1u << p.s_log2); j += blockDim.x)
+      sS[j] = p.mc.scale_inputs ? __ldg(Bg + j) * operand_scale<T>(p.mb, (int)j, 1) : __ldg(Bg + j);
+  }
   __syncthreads();
   constexpr int NS = 1 << K, NF = 1 << F;
   const int ns = 1 << p.k, nf = 1 << p.f;
@@ -298,6 +307,9 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
     for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tmin[f][e] = (T)INFINITY; sb[f][e] = (T)1; }
 #pragma unroll
   for (int e = 0; e < V; ++e) sa[e] = (T)1;
+  uint32_t bsv[NS];  // summed offsets of S (staged path)
+#pragma unroll
+  for (int s = 0; s < NS; ++s) bsv[s] = s < ns ? p.dBs[s] : 0u;
   bool first = true;
   for (uint64_t u = gtid; u < nu; u += stride) {
     const uint32_t w = (uint32_t)u << p.vbits;
@@ -333,6 +345,27 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
 #pragma unroll
         for (int e = 0; e < V; ++e) a[s][e] *= sa[e];
       }
+    if constexpr (K == 4 && V == 1) {
+      if (p.s_staged) {
+        // S from shared memory, already times its lane scale (the same
+        // products b * sb as below); the summed offsets in registers, the
+        // outer loop over the S-free assignments kept rolled.  Every output
+        // of the unit is in one query lane (the S-free bits sit above the
+        // query bits), so one max/min pair tracks them all.
+        const T *sS = reinterpret_cast<const T *>(k2s_smem);
+#pragma unroll 1
+        for (int f = 0; f < nf; ++f) {
+          const T *sf = sS + gb + p.dBf[f];
+          T c = (T)0;
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            if (s < ns) c = fma_t(a[s][0], sf[bsv[s]], c);
+          C[oc + p.dC[f]] = c;
+          track(c, tmax[0][0], tmin[0][0]);
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (f < nf) {
