@@ -716,6 +716,12 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   st.Q = Q;
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
+  // a lone float32 query on a small network runs as two lanes (the second
+  // repeats it, as padding lanes do): such walks are bound by launch
+  // latency, and vector lanes let the growth and shrink steps join chains
+  // (about 413 launches instead of 605 on the 16x100 grid); results are
+  // the same bits at every batch size
+  if (Q == 1 && plan.precision != WMC_FP64 && !force_f64 && plan.max_rank <= 20) m = 1;
   st.m = m;
   const int32_t Qp = 1 << m;
   st.Qp = Qp;
