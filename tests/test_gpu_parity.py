@@ -933,3 +933,22 @@ def test_large_batch_chains_are_batch_invariant(w):
         assert (res[q].mant, res[q].exp2) == (alone.mant, alone.exp2)
     col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
     assert rel(res[300], oracle.bucket_elim(cnf, wq[300], wnq[300], order=col)) <= TOL[FP32]
+
+
+def test_single_lane_chains_match_unfused(w):
+    """One query on the 24x200 grid (max rank 25: one lane per thread, the
+    chains' FAST variant whose bucket tensors hold one value for all lanes)
+    gives the bits of one pass per elimination."""
+    cnf = wmcgen.grid_cnf(24, 200, 1)
+    wp, wn = wmcgen.weights_complementary(4800, 1, 0.05, 0.95)
+    out = {}
+    try:
+        for fuse in (4, 0):
+            w.wmc_set_fusion(fuse)
+            plan = plan_for(w, cnf, wp, wn, FP32)
+            r = plan.execute()[0]
+            out[fuse] = (r.mant, r.exp2, plan.info(1).launches_per_walk)
+    finally:
+        w.wmc_set_fusion(4)
+    assert out[4][2] * 2 < out[0][2]
+    assert out[4][:2] == out[0][:2]
