@@ -47,7 +47,7 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 # DRAM traffic / algorithmic bytes of the dominant kernel, from its ncu
 # capture (None once the kernel changes until it is captured again)
-TRAFFIC_PER_ALG_BYTE = 737.8e6 / 939.7e6
+TRAFFIC_PER_ALG_BYTE = 737.5e6 / 939.7e6
 
 
 def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
@@ -316,7 +316,7 @@ def run_ours(args, rank, world):
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
     # DRAM bytes from one ncu capture of a full-size k2_chain launch (profiles/
-    # k2_chain_serving_grid16x100_q256.md: 737.8 MB for 939.7 MB algorithmic over
+    # k2_chain_serving_grid16x100_q256.md: 737.5 MB for 939.7 MB algorithmic over
     # a wave's mix of plain, growth and shrink chains),
     # scaled to this run's average streaming launch by its algorithmic bytes
     bpl = float(k_bytes[sel].mean()) if sel.any() else 0.0
