@@ -405,6 +405,12 @@ def run_ours(args, rank, world):
             "plan": {"max_rank": info.max_rank, "n_nodes": info.n_nodes,
                      "workspace_MiB": info.workspace_bytes / 2 ** 20,
                      "algorithmic_GB_per_wave": info.algorithmic_bytes / 1e9}}
+    # the whole wave over the timed region: algorithmic bytes per wave / time
+    # per wave (two waves in flight overlap, so this is the rate the step
+    # achieves, not a single kernel's)
+    wave_gbs = info.algorithmic_bytes / (t_max / args.steps / 1e3) / 1e9
+    line["roofline"]["wave_alg_GBs"] = wave_gbs
+    line["roofline"]["wave_frac"] = wave_gbs / hbm
     print(json.dumps(line), flush=True)
 
 
