@@ -42,7 +42,8 @@ struct BNode {
   int32_t n_tasks;
   int32_t chunk_log2;       // outputs per task = 2^chunk_log2
   int32_t rC, k;
-  int8_t ti, ta, to, pad;   // element types: 0 float, 1 double
+  int8_t ti, ta, to;        // element types: 0 float, 1 double
+  int8_t vec4;              // float32, C's two lowest bits are A's, B has neither: 4 outputs per thread
   int8_t posA[32], posB[32], sposA[24], sposB[24];
 };
 
@@ -121,6 +122,38 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
   const uint32_t ns = 1u << nd.k;
   TO tmax = (TO)0;
   unsigned long long tmin = kNoMin;
+  if constexpr (sizeof(TI) == 4 && sizeof(TA) == 4 && sizeof(TO) == 4) {
+    if (nd.vec4 && nd.k <= 8) {
+      // four consecutive outputs per thread: A's four values per summed
+      // term in one 16-byte load, one B value, the same sums in the same
+      // order as below
+      for (uint64_t o = o0 + 4 * threadIdx.x; o < o1; o += 4 * blockDim.x) {
+        const uint32_t oo = (uint32_t)o;
+        const uint32_t bA = lut[0][oo & 255] | lut[1][(oo >> 8) & 255] | lut[2][(oo >> 16) & 255] | lut[3][oo >> 24];
+        const uint32_t bB = lut[4][oo & 255] | lut[5][(oo >> 8) & 255] | lut[6][(oo >> 16) & 255] | lut[7][oo >> 24];
+        TA acc[4] = {(TA)0, (TA)0, (TA)0, (TA)0};
+        for (uint32_t s = 0; s < ns; ++s) {
+          const float4 a4 = __ldcg(reinterpret_cast<const float4 *>(A + (bA | lut[8][s])));
+          const TA b = (TA)ldcg(B + (bB | lut[11][s])) * sb;
+          acc[0] = dev::fma_t((TA)a4.x * sa, b, acc[0]);
+          acc[1] = dev::fma_t((TA)a4.y * sa, b, acc[1]);
+          acc[2] = dev::fma_t((TA)a4.z * sa, b, acc[2]);
+          acc[3] = dev::fma_t((TA)a4.w * sa, b, acc[3]);
+        }
+        *reinterpret_cast<float4 *>(C + o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const TO m = acc[e] < (TO)0 ? -acc[e] : acc[e];
+          tmax = m > tmax ? m : tmax;
+          if (m != (TO)0) {
+            const unsigned long long bits = dev::abs_bits(m);
+            tmin = bits < tmin ? bits : tmin;
+          }
+        }
+      }
+      goto reduce;
+    }
+  }
   for (uint64_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
     const uint32_t oo = (uint32_t)o;
     const uint32_t bA = lut[0][oo & 255] | lut[1][(oo >> 8) & 255] | lut[2][(oo >> 16) & 255] | lut[3][oo >> 24];
@@ -154,6 +187,7 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
       tmin = bits < tmin ? bits : tmin;
     }
   }
+reduce:
   // block reduction into red[0] (max) and red[1] (min), then one atomic each
   if (threadIdx.x == 0) { red[0] = 0; red[1] = kNoMin; }
   __syncthreads();
@@ -403,6 +437,12 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
       n.ti = prec == WMC_FP64 ? 1 : 0;
       n.to = (*lv.t_dbl)[(size_t)nd.c];
       n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
+      {
+        bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
+                   n.posB[0] < 0 && n.posB[1] < 0;
+        for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
+        n.vec4 = (low && !n.ti && !n.ta && !n.to) ? 1 : 0;
+      }
       n.prev = prev;
       prev = (int32_t)b->nodes.size();
       ids.push_back(prev);
