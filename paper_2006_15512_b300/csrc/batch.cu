@@ -96,25 +96,34 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
   const TI *A = (const TI *)(ws + nd.a);
   const TI *B = (const TI *)(ws + nd.b);
   TO *C = (TO *)(ws + nd.c);
-  // per-byte offset tables: rows 0-3 A, 4-7 B (output bits); 8-10 A, 11-13 B (summed bits)
-  for (int i = threadIdx.x; i < 14 * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255;
+  // per-byte offset tables: rows 0-3 A, 4-7 B (output bits); 8-10 A, 11-13 B (summed bits).
+  // Entry v of a row is the OR over v's set bits of that bit's offset: the
+  // single-bit offsets first, then entries [2^b, 2^(b+1)) = entries [0, 2^b)
+  // OR bit b's offset, for b = 0..7
+  if (threadIdx.x < 14 * 8) {
+    const int row = threadIdx.x >> 3, bit = threadIdx.x & 7;
     uint32_t o = 0;
-    for (int bit = 0; bit < 8; ++bit) {
-      if (!((v >> bit) & 1)) continue;
-      if (row < 8) {
-        const int j = (row & 3) * 8 + bit;
-        const int8_t pos = row < 4 ? nd.posA[j] : nd.posB[j];
-        if (j < nd.rC && pos >= 0) o |= 1u << pos;
-      } else {
-        const int j = ((row - 8) % 3) * 8 + bit;
-        const int8_t pos = row < 11 ? nd.sposA[j] : nd.sposB[j];
-        if (j < nd.k && pos >= 0) o |= 1u << pos;
-      }
+    if (row < 8) {
+      const int j = (row & 3) * 8 + bit;
+      const int8_t pos = row < 4 ? nd.posA[j] : nd.posB[j];
+      if (j < nd.rC && pos >= 0) o = 1u << pos;
+    } else {
+      const int j = ((row - 8) % 3) * 8 + bit;
+      const int8_t pos = row < 11 ? nd.sposA[j] : nd.sposB[j];
+      if (j < nd.k && pos >= 0) o = 1u << pos;
     }
-    lut[row][v] = o;
+    lut[row][1 << bit] = o;  // the single-bit entries
+    if (bit == 0) lut[row][0] = 0u;
   }
   __syncthreads();
+  for (int b = 1; b < 8; ++b) {
+    const int half = 1 << b;  // entries [half + 1, 2 half) from [1, half)
+    for (int i = threadIdx.x; i < 14 * (half - 1); i += blockDim.x) {
+      const int row = i / (half - 1), v = 1 + i % (half - 1);
+      lut[row][half + v] = lut[row][half] | lut[row][v];
+    }
+    __syncthreads();
+  }
   const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xa)), TI()), TI());
   const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xb)), TI()), TI());
   const uint64_t o0 = (uint64_t)chunk << nd.chunk_log2;
@@ -188,11 +197,22 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
     }
   }
 reduce:
-  // block reduction into red[0] (max) and red[1] (min), then one atomic each
+  // block reduction into red[0] (max) and red[1] (min): folded across each
+  // warp first (max and min are exact), one shared atomic per warp, then
+  // one global atomic each
   if (threadIdx.x == 0) { red[0] = 0; red[1] = kNoMin; }
   __syncthreads();
-  if (tmax != (TO)0) atomicMax(&red[0], dev::abs_bits(tmax));
-  if (tmin != kNoMin) atomicMin(&red[1], tmin);
+  unsigned long long bmax = tmax != (TO)0 ? dev::abs_bits(tmax) : 0ull, bmin = tmin;
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long xm = __shfl_xor_sync(0xffffffffu, bmax, o);
+    const unsigned long long xn = __shfl_xor_sync(0xffffffffu, bmin, o);
+    bmax = xm > bmax ? xm : bmax;
+    bmin = xn < bmin ? xn : bmin;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bmax) atomicMax(&red[0], bmax);
+    if (bmin != kNoMin) atomicMin(&red[1], bmin);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     if (red[0]) atomicMax((unsigned long long *)(ws + nd.xc), red[0]);
