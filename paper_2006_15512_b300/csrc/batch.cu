@@ -396,7 +396,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
   if (!b) { set_error("out of host memory"); return WMC_ENOMEM; }
   const int32_t prec = plan_of(plans[0]).precision;
   b->precision = prec;
-  constexpr int kChunkLog2 = 14;
+  constexpr int kChunkLog2 = 15;
   int64_t off = 0;
   std::vector<std::vector<int32_t>> node_ids;  // per formula: global node ids in post-order
   for (int32_t f = 0; f < n_plans; ++f) {
