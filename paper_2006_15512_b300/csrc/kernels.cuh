@@ -2218,22 +2218,31 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
   const TI *A = (const TI *)(ws + nd.a);
   const TI *B = (const TI *)(ws + nd.b);
   TO *C = (TO *)(ws + nd.c);
-  // lookup tables: rows 0-1 A, 2-3 B (output bits), 4 A, 5 B (summed bits)
-  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255;
+  // lookup tables: rows 0-1 A, 2-3 B (output bits), 4 A, 5 B (summed bits).
+  // Entry v is the OR over v's set bits of that bit's offset: the single-bit
+  // offsets first, then entries [2^b, 2^(b+1)) = entry 2^b OR entries [0, 2^b)
+  if (threadIdx.x < 6 * 8) {
+    const int row = threadIdx.x >> 3, bit = threadIdx.x & 7;
     uint32_t o = 0;
-    for (int bit = 0; bit < 8; ++bit) {
-      if (!((v >> bit) & 1)) continue;
-      if (row < 4) {
-        const int j = (row & 1) * 8 + bit;
-        const int8_t pos = row < 2 ? nd.posA[j] : nd.posB[j];
-        if (j < nd.rC && pos >= 0) o |= 1u << pos;
-      } else if (bit < nd.k) {
-        const int8_t pos = row == 4 ? nd.sposA[bit] : nd.sposB[bit];
-        if (pos >= 0) o |= 1u << pos;
-      }
+    if (row < 4) {
+      const int j = (row & 1) * 8 + bit;
+      const int8_t pos = row < 2 ? nd.posA[j] : nd.posB[j];
+      if (j < nd.rC && pos >= 0) o = 1u << pos;
+    } else if (bit < nd.k) {
+      const int8_t pos = row == 4 ? nd.sposA[bit] : nd.sposB[bit];
+      if (pos >= 0) o = 1u << pos;
     }
-    lut[row][v] = o;
+    lut[row][1 << bit] = o;
+    if (bit == 0) lut[row][0] = 0u;
+  }
+  __syncthreads();
+  for (int b = 1; b < 8; ++b) {
+    const int half = 1 << b;
+    for (int i = threadIdx.x; i < 6 * (half - 1); i += blockDim.x) {
+      const int row = i / (half - 1), v = 1 + i % (half - 1);
+      lut[row][half + v] = lut[row][half] | lut[row][v];
+    }
+    __syncthreads();
   }
   // per-lane operand scales (their max patterns are final: children done)
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
@@ -2245,6 +2254,12 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
   __syncthreads();
   const uint32_t o0 = (uint32_t)chunk << nd.chunk_log2, o1 = o0 + (1u << nd.chunk_log2);
   const uint32_t ns = 1u << nd.k;
+  // a thread's outputs share one query lane when the lanes divide the block
+  // size (o advances by blockDim): its max/min are then folded across the
+  // warp's lanes of that query before the shared atomics; otherwise every
+  // output publishes
+  const bool lane_fixed = nd.Qc <= (int)blockDim.x;
+  TO tmax = (TO)0, tmin = (TO)INFINITY;
   for (uint32_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
     const uint32_t bA = lut[0][o & 255] | lut[1][(o >> 8) & 255];
     const uint32_t bB = lut[2][o & 255] | lut[3][(o >> 8) & 255];
@@ -2258,12 +2273,19 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
     }
     const TO c = (TO)acc;
     C[o] = c;
-    const unsigned long long bits = abs_bits(c);
-    if (bits) {
-      atomicMax(smax + q, bits);
-      atomicMin(smin + q, bits);
+    if (lane_fixed) {
+      track(c, tmax, tmin);
+    } else {
+      const unsigned long long bits = abs_bits(c);
+      if (bits) {
+        atomicMax(smax + q, bits);
+        atomicMin(smin + q, bits);
+      }
     }
   }
+  if (lane_fixed)
+    publish_warp(smax, smin, (int)((o0 + threadIdx.x) & (uint32_t)(nd.Qc - 1)), tmax, tmin,
+                 nd.Qc < 32 ? nd.Qc : 32);
   __syncthreads();
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
     if (smax[q]) atomicMax(sa_.mmax + nd.mc + q, smax[q]);
