@@ -89,13 +89,9 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t target)
   }
 }
 
-template <typename TI, typename TA, typename TO>
-__device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
-                         unsigned long long *red) {
-  char *ws = ba.ws;
-  const TI *A = (const TI *)(ws + nd.a);
-  const TI *B = (const TI *)(ws + nd.b);
-  TO *C = (TO *)(ws + nd.c);
+// The node's per-byte lookup tables (they depend on the node alone, so they
+// are built before the previous node is waited for).
+__device__ __forceinline__ void batch_lut(const BNode &nd, uint32_t (*lut)[256]) {
   // per-byte offset tables: rows 0-3 A, 4-7 B (output bits); 8-10 A, 11-13 B (summed bits).
   // Entry v of a row is the OR over v's set bits of that bit's offset: the
   // single-bit offsets first, then entries [2^b, 2^(b+1)) = entries [0, 2^b)
@@ -124,6 +120,15 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
     }
     __syncthreads();
   }
+}
+
+template <typename TI, typename TA, typename TO>
+__device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
+                         unsigned long long *red) {
+  char *ws = ba.ws;
+  const TI *A = (const TI *)(ws + nd.a);
+  const TI *B = (const TI *)(ws + nd.b);
+  TO *C = (TO *)(ws + nd.c);
   const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xa)), TI()), TI());
   const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xb)), TI()), TI());
   const uint64_t o0 = (uint64_t)chunk << nd.chunk_log2;
@@ -245,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) k6_persistent(BatchArgs ba) {
     if (t >= ba.n_tasks) break;
     const BTask task = ba.tasks[t];
     const BNode &nd = ba.nodes[task.node];
+    batch_lut(nd, lut);  // overlaps the wait for the previous node
     if (threadIdx.x == 0) {
       bool ok = *(volatile uint32_t *)ba.err == 0;
       if (ok && nd.prev >= 0) ok = wait_count(ba.done + nd.prev, (uint32_t)ba.nodes[nd.prev].n_tasks);

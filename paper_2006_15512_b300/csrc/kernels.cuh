@@ -2211,13 +2211,9 @@ __device__ __forceinline__ bool wait_ctr(const uint32_t *ctr, uint32_t target) {
   }
 }
 
-template <typename TI, typename TA, typename TO>
-__device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uint32_t (*lut)[256],
-                           TA *scl, unsigned long long *smax, unsigned long long *smin) {
-  char *ws = sa_.ws;
-  const TI *A = (const TI *)(ws + nd.a);
-  const TI *B = (const TI *)(ws + nd.b);
-  TO *C = (TO *)(ws + nd.c);
+// The node's per-byte lookup tables (they depend on the node alone, so they
+// are built before its children are waited for).
+__device__ __forceinline__ void small_lut(const SNode &nd, uint32_t (*lut)[256]) {
   // lookup tables: rows 0-1 A, 2-3 B (output bits), 4 A, 5 B (summed bits).
   // Entry v is the OR over v's set bits of that bit's offset: the single-bit
   // offsets first, then entries [2^b, 2^(b+1)) = entry 2^b OR entries [0, 2^b)
@@ -2244,6 +2240,15 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
     }
     __syncthreads();
   }
+}
+
+template <typename TI, typename TA, typename TO>
+__device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uint32_t (*lut)[256],
+                           TA *scl, unsigned long long *smax, unsigned long long *smin) {
+  char *ws = sa_.ws;
+  const TI *A = (const TI *)(ws + nd.a);
+  const TI *B = (const TI *)(ws + nd.b);
+  TO *C = (TO *)(ws + nd.c);
   // per-lane operand scales (their max patterns are final: children done)
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
     scl[q] = (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + nd.ma + (q & nd.qmask_a)), TI()), TI());
@@ -2321,6 +2326,7 @@ __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
     if (t >= a.n_tasks) break;
     const STask task = a.tasks[t];
     const SNode &nd = a.nodes[task.node];
+    small_lut(nd, lut);  // overlaps the wait for the children
     if (threadIdx.x == 0) {
       bool ok = *(volatile uint32_t *)a.err == 0;
       if (ok && nd.dep_a >= 0) ok = wait_ctr(a.done + nd.dep_a, (uint32_t)a.nodes[nd.dep_a].n_chunks);
