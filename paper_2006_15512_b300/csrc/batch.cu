@@ -129,8 +129,23 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
   const TI *A = (const TI *)(ws + nd.a);
   const TI *B = (const TI *)(ws + nd.b);
   TO *C = (TO *)(ws + nd.c);
-  const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xa)), TI()), TI());
-  const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(ldcg((const unsigned long long *)(ws + nd.xb)), TI()), TI());
+  const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
+  const unsigned long long mb = ldcg((const unsigned long long *)(ws + nd.xb));
+  const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI());
+  const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI());
+  if (chunk == 0 && threadIdx.x == 32) {
+    // C's exponent and the float32 flush test (as in the single-plan
+    // kernels), from the operands' metadata alone, beside the outputs
+    *(int64_t *)(ws + nd.ec) = ldcg((const int64_t *)(ws + nd.ea)) + dev::pow2_exp_of(ma, TI()) +
+                               ldcg((const int64_t *)(ws + nd.eb)) + dev::pow2_exp_of(mb, TI());
+    const unsigned long long na = ldcg((const unsigned long long *)(ws + nd.na));
+    const unsigned long long nb = ldcg((const unsigned long long *)(ws + nd.nb));
+    if (na != kNoMin && nb != kNoMin) {
+      const TI lo = (dev::from_bits<TI>(na) * dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI())) *
+                    (dev::from_bits<TI>(nb) * dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI()));
+      if (dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
+    }
+  }
   const uint64_t o0 = (uint64_t)chunk << nd.chunk_log2;
   const uint64_t o1 = o0 + (1ull << nd.chunk_log2);
   const uint32_t ns = 1u << nd.k;
@@ -222,20 +237,6 @@ reduce:
   if (threadIdx.x == 0) {
     if (red[0]) atomicMax((unsigned long long *)(ws + nd.xc), red[0]);
     if (red[1] != kNoMin) atomicMin((unsigned long long *)(ws + nd.nc), red[1]);
-    if (chunk == 0) {
-      const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
-      const unsigned long long mb = ldcg((const unsigned long long *)(ws + nd.xb));
-      *(int64_t *)(ws + nd.ec) = ldcg((const int64_t *)(ws + nd.ea)) + dev::pow2_exp_of(ma, TI()) +
-                                 ldcg((const int64_t *)(ws + nd.eb)) + dev::pow2_exp_of(mb, TI());
-      // float32 flush test (as in the single-plan kernels)
-      const unsigned long long na = ldcg((const unsigned long long *)(ws + nd.na));
-      const unsigned long long nb = ldcg((const unsigned long long *)(ws + nd.nb));
-      if (na != kNoMin && nb != kNoMin) {
-        const TI lo = (dev::from_bits<TI>(na) * dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI())) *
-                      (dev::from_bits<TI>(nb) * dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI()));
-        if (dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
-      }
-    }
   }
 }
 

@@ -2249,12 +2249,30 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
   const TI *A = (const TI *)(ws + nd.a);
   const TI *B = (const TI *)(ws + nd.b);
   TO *C = (TO *)(ws + nd.c);
-  // per-lane operand scales (their max patterns are final: children done)
+  // per-lane operand scales (their max patterns are final: children done);
+  // chunk 0 also writes C's exponents and runs the flush test now, from the
+  // children's metadata alone (off the path that waits for the outputs)
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
-    scl[q] = (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + nd.ma + (q & nd.qmask_a)), TI()), TI());
-    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + nd.mb + (q & nd.qmask_b)), TI()), TI());
+    const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+    const unsigned long long xa = __ldcg(sa_.mmax + nd.ma + qa), xb = __ldcg(sa_.mmax + nd.mb + qb);
+    scl[q] = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
+    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
     smax[q] = 0;
     smin[q] = kNoMin;
+    if (chunk == 0) {
+      sa_.mexp[nd.mc + q] = __ldcg(sa_.mexp + nd.ma + qa) + pow2_exp_of(xa, TI()) +
+                            __ldcg(sa_.mexp + nd.mb + qb) + pow2_exp_of(xb, TI());
+      const unsigned long long na = __ldcg(sa_.mmin + nd.ma + qa), nb = __ldcg(sa_.mmin + nd.mb + qb);
+      if (na != kNoMin && nb != kNoMin) {
+        const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
+                      (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
+        if (below_normal(lo)) {
+          if (nd.Qc > 1) atomicOr(sa_.flags + q, 2u);
+          else
+            for (int qq = 0; qq < sa_.Q; ++qq) atomicOr(sa_.flags + qq, 2u);
+        }
+      }
+    }
   }
   __syncthreads();
   const uint32_t o0 = (uint32_t)chunk << nd.chunk_log2, o1 = o0 + (1u << nd.chunk_log2);
@@ -2295,22 +2313,6 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
     if (smax[q]) atomicMax(sa_.mmax + nd.mc + q, smax[q]);
     if (smin[q] != kNoMin) atomicMin(sa_.mmin + nd.mc + q, smin[q]);
-    if (chunk == 0) {
-      const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
-      const unsigned long long xa = __ldcg(sa_.mmax + nd.ma + qa), xb = __ldcg(sa_.mmax + nd.mb + qb);
-      sa_.mexp[nd.mc + q] = __ldcg(sa_.mexp + nd.ma + qa) + pow2_exp_of(xa, TI()) +
-                            __ldcg(sa_.mexp + nd.mb + qb) + pow2_exp_of(xb, TI());
-      const unsigned long long na = __ldcg(sa_.mmin + nd.ma + qa), nb = __ldcg(sa_.mmin + nd.mb + qb);
-      if (na != kNoMin && nb != kNoMin) {
-        const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
-                      (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
-        if (below_normal(lo)) {
-          if (nd.Qc > 1) atomicOr(sa_.flags + q, 2u);
-          else
-            for (int qq = 0; qq < sa_.Q; ++qq) atomicOr(sa_.flags + qq, 2u);
-        }
-      }
-    }
   }
 }
 
