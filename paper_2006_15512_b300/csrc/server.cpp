@@ -52,6 +52,12 @@ struct Slot {
   int32_t Q = 0;
   int status = WMC_OK;
   bool busy = false;
+  int64_t launched_ns = 0;
+  // a full wave staged in h_w2 while this slot's wave runs (throughput-
+  // bound serving: launched as soon as the slot frees)
+  double *h_w2 = nullptr;
+  std::vector<Query> next;
+  bool staged = false;
 };
 
 struct TicketState {
@@ -97,20 +103,33 @@ struct CbArg {
 };
 }  // namespace
 
-static int launch_wave(wmc_server *srv, int si) {
-  Slot &sl = srv->slots[(size_t)si];
-  const size_t nv = (size_t)srv->n_vars;
-  const int32_t n = (int32_t)sl.wave.size();
+// Weights of `wave` into pinned staging `h` ([2][Q][n_vars]); lanes past the
+// wave's queries (Q is the next power of two) repeat its last query.
+static int32_t stage_weights(const std::vector<Query> &wave, size_t nv, double *h) {
+  const int32_t n = (int32_t)wave.size();
   int32_t Q = 1;
   while (Q < n) Q <<= 1;
-  sl.Q = Q;
-  for (int32_t q = 0; q < Q; ++q) {
-    const Query &src = sl.wave[(size_t)std::min(q, n - 1)];
-    if (nv) {
-      std::memcpy(sl.h_w + (size_t)q * nv, src.wp.data(), sizeof(double) * nv);
-      std::memcpy(sl.h_w + (size_t)Q * nv + (size_t)q * nv, src.wn.data(), sizeof(double) * nv);
-    }
+  for (int32_t q = 0; q < Q && nv; ++q) {
+    const Query &src = wave[(size_t)std::min(q, n - 1)];
+    std::memcpy(h + (size_t)q * nv, src.wp.data(), sizeof(double) * nv);
+    std::memcpy(h + (size_t)Q * nv + (size_t)q * nv, src.wn.data(), sizeof(double) * nv);
   }
+  return Q;
+}
+
+// Enqueues the slot's wave (its weights already staged in h_w for sl.Q lanes).
+static int submit_wave(wmc_server *srv, int si);
+
+static int launch_wave(wmc_server *srv, int si) {
+  Slot &sl = srv->slots[(size_t)si];
+  sl.Q = stage_weights(sl.wave, (size_t)srv->n_vars, sl.h_w);
+  return submit_wave(srv, si);
+}
+
+static int submit_wave(wmc_server *srv, int si) {
+  Slot &sl = srv->slots[(size_t)si];
+  const size_t nv = (size_t)srv->n_vars;
+  const int32_t Q = sl.Q;
   ExecState *st = nullptr;
   int rc = exec_state(*srv->plan, Q, &st);
   if (rc) return rc;
@@ -154,11 +173,62 @@ static void batcher_loop(wmc_server *srv) {
   for (;;) {
     srv->cv_work.wait(lk, [&] {
       if (srv->stop) return true;
-      if (srv->queue.empty()) return false;
-      for (auto &s : srv->slots) if (!s.busy) return true;
+      for (auto &s : srv->slots)
+        if (!s.busy && (s.staged || !srv->queue.empty())) return true;
+      if (srv->queue.size() >= max_b)
+        for (auto &s : srv->slots)
+          if (s.busy && !s.staged) return true;
       return false;
     });
     if (srv->stop) return;
+    // a free slot with a staged wave: launch it at once
+    int sj = -1;
+    for (size_t i = 0; i < srv->slots.size(); ++i)
+      if (!srv->slots[i].busy && srv->slots[i].staged) { sj = (int)i; break; }
+    if (sj >= 0) {
+      Slot &sl = srv->slots[(size_t)sj];
+      sl.wave = std::move(sl.next);
+      sl.next.clear();
+      std::swap(sl.h_w, sl.h_w2);
+      sl.Q = (int32_t)max_b;
+      sl.staged = false;
+      sl.busy = true;
+      sl.status = WMC_OK;
+      sl.launched_ns = mono_ns();
+      srv->in_flight++;
+      lk.unlock();
+      int rc = submit_wave(srv, sj);
+      lk.lock();
+      if (rc) {
+        sl.status = rc;
+        srv->finished.push_back(sj);
+        srv->cv_comp.notify_one();
+      }
+      continue;
+    }
+    bool any_free = false;
+    for (auto &s : srv->slots) any_free |= !s.busy;
+    if (!any_free) {
+      // every slot busy and a full wave queued: stage it for the slot that
+      // was launched first (the one expected to free first)
+      int sk = -1;
+      for (size_t i = 0; i < srv->slots.size(); ++i)
+        if (srv->slots[i].busy && !srv->slots[i].staged &&
+            (sk < 0 || srv->slots[i].launched_ns < srv->slots[(size_t)sk].launched_ns))
+          sk = (int)i;
+      if (sk < 0 || srv->queue.size() < max_b) continue;
+      Slot &sl = srv->slots[(size_t)sk];
+      sl.next.clear();
+      for (size_t k = 0; k < max_b; ++k) {
+        sl.next.push_back(std::move(srv->queue.front()));
+        srv->queue.pop_front();
+      }
+      lk.unlock();
+      stage_weights(sl.next, (size_t)srv->n_vars, sl.h_w2);
+      lk.lock();
+      sl.staged = true;
+      continue;
+    }
     // optional short wait for a fuller wave while other waves run
     if (srv->opts.max_wave_wait_us > 0 && srv->queue.size() < max_b && srv->in_flight > 0) {
       srv->cv_work.wait_for(lk, std::chrono::microseconds(srv->opts.max_wave_wait_us),
@@ -177,6 +247,7 @@ static void batcher_loop(wmc_server *srv) {
     }
     sl.busy = true;
     sl.status = WMC_OK;
+    sl.launched_ns = mono_ns();
     srv->in_flight++;
     lk.unlock();
     int rc = launch_wave(srv, si);
@@ -235,7 +306,7 @@ static void completer_loop(wmc_server *srv) {
 static void free_slot(Slot &s) {
   if (s.stream) cudaStreamSynchronize(s.stream);
   cudaFree(s.ws); cudaFree(s.d_w); cudaFree(s.d_mant); cudaFree(s.d_exp); cudaFree(s.d_flags);
-  cudaFreeHost(s.h_w); cudaFreeHost(s.h_mant); cudaFreeHost(s.h_exp); cudaFreeHost(s.h_flags);
+  cudaFreeHost(s.h_w); cudaFreeHost(s.h_w2); cudaFreeHost(s.h_mant); cudaFreeHost(s.h_exp); cudaFreeHost(s.h_flags);
   if (s.stream) cudaStreamDestroy(s.stream);
   s = Slot();
 }
@@ -282,6 +353,7 @@ extern "C" int wmc_server_create(wmc_plan_t *cplan, const wmc_server_opts *opts,
               cudaMalloc((void **)&s.d_exp, sizeof(int64_t) * B) == cudaSuccess &&
               cudaMalloc((void **)&s.d_flags, sizeof(uint32_t) * B) == cudaSuccess &&
               cudaMallocHost((void **)&s.h_w, sizeof(double) * 2 * B * nv) == cudaSuccess &&
+              cudaMallocHost((void **)&s.h_w2, sizeof(double) * 2 * B * nv) == cudaSuccess &&
               cudaMallocHost((void **)&s.h_mant, sizeof(double) * B) == cudaSuccess &&
               cudaMallocHost((void **)&s.h_exp, sizeof(int64_t) * B) == cudaSuccess &&
               cudaMallocHost((void **)&s.h_flags, sizeof(uint32_t) * B) == cudaSuccess;
