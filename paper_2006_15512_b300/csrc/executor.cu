@@ -532,7 +532,6 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
       broadcast &= (cp.dv[i][e] == 0u);
     }
     cp.b_vec[i] = contiguous ? 1 : (broadcast ? 2 : 0);
-    if (!contiguous && !broadcast) fast = false;
     if (!contiguous && V > 1) any_broadcast = true;
     const int sx = pos_of(S, x[(size_t)i]);
     const int sy = y[(size_t)i] != INT32_MIN ? pos_of(S, y[(size_t)i]) : -1;
@@ -1099,7 +1098,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     auto eligible = [&](const Launch &l) {
       if (l.kind != L_K2C || l.ti != TF || l.chain_d != 4 || !l.chain_fast || (l.v != 1 && l.v != 2)) return false;
       for (int i = 0; i < l.chain_d; ++i)
-        if (l.k2c.b_vec[i] == 2) return false;
+        if (l.v > 1 && l.k2c.b_vec[i] != 1) return false;
       const int64_t tiles = int64_t(1) << (l.k2c.log2_nu + l.k2c.vbits - l.k2c.tb);
       return tiles <= (int64_t)g_chain_runs.load();
     };
@@ -1257,12 +1256,13 @@ static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t sm
 
 static bool chain_broadcast(const Launch &l) {
   for (int i = 0; i < l.chain_d; ++i)
-    if (l.k2c.b_vec[i] == 2) return true;
+    if (l.k2c.b_vec[i] != 1) return true;
   return false;
 }
 
 // vector lanes: FAST plain chains (contiguous lanes, or some steps with
-// one value for all lanes), growth-first and shrink-last variants
+// one value for all lanes or one load per lane), growth-first and
+// shrink-last variants
 template <int V, int D>
 static void launch_k2c_vec(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
   if (!l.chain_fast) launch_k2c_t<float, V, D, false, 0, 0, 0>(p, l.blocks, l.smem, s);

@@ -887,12 +887,12 @@ __host__ __device__ constexpr uint32_t chain_deps(int D, bool fast, int grow, in
 
 // V lanes of a staged S_i at shared-memory byte address `a`; LM is the lane
 // mode when known at compile time (1 contiguous, 2 one value for all
-// lanes), 0 to follow the runtime mode
+// lanes, 3 one load per lane at its own offset), 0 to follow the runtime mode
 template <typename T, int V, int LM>
 __device__ __forceinline__ void ld_lanes(uint32_t a, int mode, const uint32_t *dv, T (&r)[V]) {
   if (LM == 1 || (LM == 0 && (V == 1 || mode == 1))) {
     LdsV<T, V>::ld(a, r);
-  } else if (LM == 2 || mode == 2) {
+  } else if (LM == 2 || (LM == 0 && mode == 2)) {
     const T v = lds1(a, T());
 #pragma unroll
     for (int i = 0; i < V; ++i) r[i] = v;
@@ -986,15 +986,14 @@ __device__ __forceinline__ void chain_step_m(const K2CParams &cp, uint32_t g, T 
   }
 }
 
-// FAST chains have contiguous or broadcast lanes per step: one branch per
-// step picks the variant; the generic chains follow the runtime mode per load
 // FAST chains: every step's lanes contiguous (BC 0), or each step
-// contiguous or broadcast (BC 1: one branch per step picks the variant);
-// the generic chains follow the runtime mode per load
+// contiguous, broadcast or per lane (BC 1: one branch per step picks the
+// variant); the generic chains follow the runtime mode per load
 template <typename T, int V, int D, bool FAST, int BC, int GROW, int KIND, int I>
 __device__ __forceinline__ void chain_step(const K2CParams &cp, uint32_t g, T (&a)[1 << (D + GROW)][V]) {
   if (!FAST) chain_step_m<T, V, D, FAST, GROW, KIND, I, 0>(cp, g, a);
   else if (BC && V > 1 && cp.b_vec[I] == 2) chain_step_m<T, V, D, FAST, GROW, KIND, I, 2>(cp, g, a);
+  else if (BC && V > 1 && cp.b_vec[I] == 0) chain_step_m<T, V, D, FAST, GROW, KIND, I, 3>(cp, g, a);
   else chain_step_m<T, V, D, FAST, GROW, KIND, I, 1>(cp, g, a);
 }
 
