@@ -258,11 +258,13 @@ int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q,
  * matrix-multiplication view of Sec. 4.2), on device memory, asynchronous on
  * `stream`.  Kernel choice: the streaming kernel when one operand is small,
  * a dense kernel when the node is a batched matrix product with at least
- * 2^6 values on each free side and 2^5 summed values (float32 with at least
- * 2^7 per free side and 2^4 summed values: the tensor-core kernel, see
- * wmc_set_tensor_cores; otherwise a tiled scalar kernel whose summed range
- * is split across blocks when there are few output tiles), the generic
- * kernel otherwise.  The tensor-core kernel's packed operands (8 bytes per
+ * 2^6 values on each free side (float32 with at least 2^7 per free side and
+ * 2^4 summed values: the tensor-core kernel, see wmc_set_tensor_cores; at
+ * most 4 summed values, one operand's first 10 free indices at C's lowest
+ * 10 bits and at least 2^24 outputs: a streaming outer-product kernel, see
+ * wmc_set_outer_products; otherwise a tiled scalar kernel whose summed
+ * range is split across blocks when there are few output tiles), the
+ * generic kernel otherwise.  The tensor-core kernel's packed operands (8 bytes per
  * operand entry) and the split partial sums live in stream-ordered scratch
  * from a memory pool of the library's own, which keeps up to 8 GiB cached.  Bit j of a tensor's linear offset is index labels_x[j];
  * every index has extent 2.  Indices of C must appear in A or B; indices of
@@ -396,6 +398,16 @@ void wmc_set_dependent_launch(int32_t on);
  * off, on the scalar tiled kernel.  The two agree within float32 rounding,
  * not bit for bit. */
 void wmc_set_tensor_cores(int32_t on);
+/* Execution option (default on): dense products with at most 4 summed
+ * values whose C has one operand's first 10 free indices as its lowest 10
+ * bits, at one query lane and at least 2^24 outputs, run on a streaming
+ * outer-product kernel (each thread keeps 4 consecutive entries of that
+ * operand in registers and writes 4 consecutive outputs per value of the
+ * other side); off, on the tiled scalar kernel.  Both add the summed terms
+ * in the same order, so the results are the same bits.  Read by
+ * wmc_contract_pair at each call and by a plan's execution state when it
+ * is built. */
+void wmc_set_outer_products(int32_t on);
 /* Execution option (default on): wmc_execute and wmc_execute_slices run the
  * queries of a scaled-FP32 plan whose results carry WMC_FLAG_FP32_FLUSH
  * again in FP64 on the same contraction tree (one extra walk over those

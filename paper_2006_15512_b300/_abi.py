@@ -140,6 +140,7 @@ EXPORTS = {
     "wmc_set_small_phase": (None, [c_i32]),
     "wmc_set_dependent_launch": (None, [c_i32]),
     "wmc_set_tensor_cores": (None, [c_i32]),
+    "wmc_set_outer_products": (None, [c_i32]),
     "wmc_set_fp64_fallback": (None, [c_i32]),
     "wmc_set_chain_runs": (None, [c_i32]),
 }

@@ -52,6 +52,8 @@ extern "C" void wmc_set_fusion(int32_t on) { g_fuse.store(on); }
 extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
 extern "C" void wmc_set_tensor_cores(int32_t on) { g_tensor_cores.store(on); }
+static std::atomic<int32_t> g_outer{1};  // short summed ranges: k4_outer in place of k4_dense
+extern "C" void wmc_set_outer_products(int32_t on) { g_outer.store(on); }
 extern "C" void wmc_set_fp64_fallback(int32_t on) { g_fp64_fallback.store(on); }
 extern "C" void wmc_set_chain_runs(int32_t max_tiles) { g_chain_runs.store(max_tiles < 0 ? 0 : max_tiles); }
 
@@ -680,6 +682,28 @@ bool try_k4(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
   return true;
 }
 
+// k4_outer in place of k4_dense: at most 2 summed bits, one query lane, C's
+// low 10 bits the first 10 free bits of A (u = i) or of B (u = j), and at
+// least 2^8 blocks of 1024 x 64 outputs.  Sets p.outer_u; returns the
+// block count, or 0 to keep k4_dense.
+int64_t k4_outer_pick(wmc::dev::K4Params &p) {
+  p.outer_u = 0;
+  if (p.ns > 2 || p.mc.Qc != 1) return 0;
+  auto low10 = [](const int8_t *pos, int n) {
+    if (n < 10) return false;
+    for (int t = 0; t < 10; ++t)
+      if (pos[t] != t) return false;
+    return true;
+  };
+  int nu = 0, nv = 0;
+  if (low10(p.iC, p.ni)) { p.outer_u = 1; nu = p.ni; nv = p.nj; }
+  else if (low10(p.jC, p.nj)) { p.outer_u = 2; nu = p.nj; nv = p.ni; }
+  else return 0;
+  const int blog2 = nu - 10 + nv - 6 + p.nb;
+  if (nv < 6 || blog2 < 8 || blog2 > 30) { p.outer_u = 0; return 0; }
+  return (int64_t)1 << blog2;
+}
+
 void fill_k1(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
              const std::vector<int32_t> &LC, K1Params &p) {
   std::memset(&p, 0, sizeof(p));
@@ -858,6 +882,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     mc.Qc = C.has_q ? Qp : 1;
     mc.Q = Qp;
     mc.scale_inputs = 1;
+    if (l.kind == L_K4 && g_outer.load()) {
+      const int64_t ob = k4_outer_pick(l.k4);
+      if (ob) l.blocks = ob;
+    }
   }
 
   // ---- fuse consecutive frontier eliminations (i, j): node j's large
@@ -1469,8 +1497,14 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
         p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
         p.mc.flags = flags;
-        if (l.ti == TD) dev::k4_dense<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
-        else dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        if (p.outer_u) {
+          if (l.ti == TD) dev::k4_outer<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+          else dev::k4_outer<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        } else if (l.ti == TD) {
+          dev::k4_dense<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        } else {
+          dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        }
         break;
       }
       case L_K2: {
@@ -2080,6 +2114,15 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
     if (!f64 && g_tensor_cores.load() && p4.ni >= 7 && p4.nj >= 7 && p4.ns >= 4) {
       CUDA_TRY(launch_k4_tc(p4, s));
       return WMC_OK;
+    }
+    if (g_outer.load() && ((uintptr_t)c & 15u) == 0) {  // its vector stores need a 16-byte aligned C
+      if (const int64_t ob = k4_outer_pick(p4)) {
+        if (f64) dev::k4_outer<double><<<(unsigned)ob, 256, 0, s>>>(p4);
+        else dev::k4_outer<float><<<(unsigned)ob, 256, 0, s>>>(p4);
+        g_launches.fetch_add(1);
+        CUDA_TRY(cudaGetLastError());
+        return WMC_OK;
+      }
     }
     const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
     // few output tiles and a long summed range: split the range into

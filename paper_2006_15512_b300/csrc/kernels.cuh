@@ -91,6 +91,18 @@ __device__ __forceinline__ void track(T c, T &tmax, T &tmin) {
   tmax = a > tmax ? a : tmax;
   tmin = (a != (T)0 && a < tmin) ? a : tmin;
 }
+// float64: the same max and min from the bit patterns on the integer units
+// (nonnegative IEEE values order as their bits; NaNs are skipped), leaving
+// B300's few FP64 units to the products
+template <>
+__device__ __forceinline__ void track<double>(double c, double &tmax, double &tmin) {
+  constexpr unsigned long long kInf = 0x7ff0000000000000ull;
+  const unsigned long long a = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
+  const unsigned long long mx = (unsigned long long)__double_as_longlong(tmax);
+  const unsigned long long mn = (unsigned long long)__double_as_longlong(tmin);
+  tmax = __longlong_as_double((long long)((a > mx && a <= kInf) ? a : mx));
+  tmin = __longlong_as_double((long long)((a != 0ull && a < mn) ? a : mn));
+}
 
 template <typename T>
 __device__ __forceinline__ void publish(unsigned long long *smax, unsigned long long *smin, int q,
@@ -507,11 +519,25 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
   }
 }
 
+// max(m, |x|); float64 on the integer units as in track<double>
+template <typename T>
+__device__ __forceinline__ T max_abs(T m, T x) { return fmax(m, fabs(x)); }
+template <>
+__device__ __forceinline__ double max_abs<double>(double m, double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const unsigned long long mb = (unsigned long long)__double_as_longlong(m);
+  return __longlong_as_double((long long)((a > mb && a <= 0x7ff0000000000000ull) ? a : mb));
+}
+
 template <typename T>
 __device__ __forceinline__ void track_fast(T c, T &tmax, T &tmin) {
-  const T a = fabs(c);
-  tmax = fmax(tmax, a);
-  tmin = fmin(tmin, a != (T)0 ? a : (T)INFINITY);
+  if constexpr (sizeof(T) == 8) {
+    track<double>(c, tmax, tmin);
+  } else {
+    const T a = fabs(c);
+    tmax = fmax(tmax, a);
+    tmin = fmin(tmin, a != (T)0 ? a : (T)INFINITY);
+  }
 }
 
 constexpr int kConsumerWarps = kThreads / 32;
@@ -756,7 +782,7 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
             vstore<T, V>(cptr + dCf[f], c);
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-              tmax[f][e] = fmax(tmax[f][e], fabs(c[e]));
+              tmax[f][e] = max_abs(tmax[f][e], c[e]);
               const BT bm1 = to_bits(c[e]) - (BT)1;
               tminm1[f][e] = bm1 < tminm1[f][e] ? bm1 : tminm1[f][e];
             }
@@ -1238,7 +1264,7 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
           vstore<T, V>(cbase + cp.dC[s], a[s]);
 #pragma unroll
           for (int e = 0; e < V; ++e) {
-            tmax[e] = fmax(tmax[e], fabs(a[s][e]));
+            tmax[e] = max_abs(tmax[e], a[s][e]);
             tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
           }
         }
@@ -1571,7 +1597,7 @@ __device__ __forceinline__ void chain_seq_pass(const K2CParams &cp, ChainSeqShar
           vstore<T, V>(cbase + cp.dC[s], a[s]);
 #pragma unroll
           for (int e = 0; e < V; ++e) {
-            tmax[e] = fmax(tmax[e], fabs(a[s][e]));
+            tmax[e] = max_abs(tmax[e], a[s][e]);
             tminm1[e] = min_m1(to_bits(a[s][e]), tminm1[e]);
           }
         }
@@ -1699,6 +1725,7 @@ struct K4Params {
   int32_t a_i_fast;   // A's lowest (i, s) bit is an i bit: load A along i
   int32_t b_j_fast;   // B's lowest (s, j) bit is a j bit: load B along j
   int32_t c_i_fast;   // C's lowest (i, j) bit is an i bit: threads along i
+  int32_t outer_u;    // k4_outer: 1 when C's low 10 bits are i's first 10, 2 when j's
 };
 
 __device__ __forceinline__ uint32_t scatter_bits(uint32_t v, const int8_t *pos, int n) {
@@ -1822,6 +1849,81 @@ __global__ void __launch_bounds__(256) k4_dense(K4Params p) {
     track(v, tmax, tmin);
   }
   publish_warp(smax, smin, q, tmax, tmin, 1);
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
+// Outer products with a short summed range (at most 2 summed bits, one
+// query lane): C's lowest 10 bits are the first 10 free bits u of one
+// operand U, in order; v are the other operand's free bits.  A block owns
+// 1024 consecutive u (4 per thread, one vector store each) and 64 values of
+// v, for one value of u's and v's high bits and of the batch bits.  Each
+// thread keeps its U entries in registers and loops over the 64 v, whose
+// entries are staged in shared memory; every output is written once.  The
+// summed terms are added as k4_dense adds them (fma chain over s in order
+// from 0, operands scaled first), so the values are the same bits.
+template <typename T>
+__global__ void __launch_bounds__(256) k4_outer(K4Params p) {
+  constexpr int LU = 10, LV = 6, NV = 1 << LV;
+  __shared__ T Vs[NV][4];
+  __shared__ uint32_t offC_v[NV];
+  __shared__ unsigned long long smax[1], smin[1];
+  const bool ui = p.outer_u == 1;
+  const int nu = ui ? p.ni : p.nj, nv = ui ? p.nj : p.ni, ns = p.ns;
+  const int8_t *uU = ui ? p.iA : p.jB, *uC = ui ? p.iC : p.jC;
+  const int8_t *vV = ui ? p.jB : p.iA, *vC = ui ? p.jC : p.iC;
+  const int8_t *sU = ui ? p.sA : p.sB, *sV = ui ? p.sB : p.sA;
+  const int8_t *bU = ui ? p.bA : p.bB, *bV = ui ? p.bB : p.bA;
+  const T *U = (const T *)(ui ? p.A : p.B);
+  const T *Vop = (const T *)(ui ? p.B : p.A);
+  const T su = operand_scale<T>(ui ? p.ma : p.mb, 0, p.mc.scale_inputs);
+  const T sv = operand_scale<T>(ui ? p.mb : p.ma, 0, p.mc.scale_inputs);
+  const uint32_t u_tiles = 1u << (nu - LU), v_tiles = 1u << (nv - LV);
+  const uint32_t ut = blockIdx.x % u_tiles, vt = (blockIdx.x / u_tiles) % v_tiles;
+  const uint32_t bb = blockIdx.x / (u_tiles * v_tiles);
+  const int NS = 1 << ns;
+  if (threadIdx.x == 0) { smax[0] = 0; smin[0] = kNoMin; }
+  const uint32_t baseV = scatter_bits(vt, vV + LV, nv - LV) | scatter_bits(bb, bV, p.nb);
+  for (int x = threadIdx.x; x < NV * NS; x += blockDim.x) {
+    const int vv = x >> ns, k = x & (NS - 1);
+    Vs[vv][k] = __ldg(Vop + (baseV | scatter_bits(vv, vV, LV) | scatter_bits(k, sV, ns))) * sv;
+  }
+  for (int x = threadIdx.x; x < NV; x += blockDim.x) offC_v[x] = scatter_bits(x, vC, LV);
+  // this thread's 4 values of u and their entries of U, scaled
+  const uint32_t baseU = scatter_bits(ut, uU + LU, nu - LU) | scatter_bits(bb, bU, p.nb);
+  T a[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t o = baseU | scatter_bits(threadIdx.x * 4u + e, uU, LU);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[e][k] = k < NS ? __ldg(U + (o | scatter_bits(k, sU, ns))) * su : (T)0;
+  }
+  const uint32_t baseC = scatter_bits(ut, uC + LU, nu - LU) | scatter_bits(vt, vC + LV, nv - LV) |
+                         scatter_bits(bb, p.bC, p.nb);
+  T *C = (T *)p.C + baseC + threadIdx.x * 4u;
+  __syncthreads();
+  T tmax = (T)0, tmin = (T)INFINITY;
+#pragma unroll 4
+  for (int vv = 0; vv < NV; ++vv) {
+    T c[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      T acc = (T)0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < NS) acc = fma_t(a[e][k], Vs[vv][k], acc);
+      c[e] = acc;
+      track_fast(acc, tmax, tmin);
+    }
+    T *dst = C + offC_v[vv];
+    if constexpr (sizeof(T) == 4) {
+      __stcs(reinterpret_cast<float4 *>(dst), make_float4(c[0], c[1], c[2], c[3]));
+    } else {
+      __stcs(reinterpret_cast<double2 *>(dst), make_double2(c[0], c[1]));
+      __stcs(reinterpret_cast<double2 *>(dst) + 1, make_double2(c[2], c[3]));
+    }
+  }
+  publish_warp(smax, smin, 0, tmax, tmin, 1);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }

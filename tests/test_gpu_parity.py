@@ -691,6 +691,53 @@ def test_pair_tensor_cores(w, ra, rb, b, k, shuffle):
     assert (np.abs(got - scalar) / np.abs(scalar)).max() <= tol + _pair_tol(k, FP32)
 
 
+# dense products with one or two summed bits and 2^24 or more outputs: the
+# streaming outer-product kernel; (rank A, rank B, batch, summed, swap): with
+# swap the operands are passed as (B, A), so C's low bits are the second
+# operand's free indices
+SWEEP_OUTER = [(13, 13, 0, 1, False), (15, 14, 1, 2, False), (15, 14, 1, 2, True), (14, 15, 2, 1, True)]
+
+
+@pytest.mark.parametrize("ra,rb,b,k,swap", SWEEP_OUTER)
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_pair_outer_products(w, ra, rb, b, k, swap, precision):
+    """Short summed ranges with a large output: every output against the
+    oracle, and the same bits as the tiled kernel (same summation order)."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=ra * 7 + rb + 13 * k, shuffle=False)
+    if swap:
+        case = wmcgen.PairCase(case.labels_b, case.labels_a, case.labels_c, case.b, case.a)
+    assert len(case.labels_c) >= 24
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c)
+    got = _run_pair(w, case, precision)
+    try:
+        w.wmc_set_outer_products(0)
+        tiled = _run_pair(w, case, precision)
+    finally:
+        w.wmc_set_outer_products(1)
+    assert np.array_equal(got, tiled)
+    assert (np.abs(got - want) / np.abs(want)).max() <= _pair_tol(k, precision)
+
+
+def test_pair_outer_products_full_size(w):
+    """The sweep's (17, 17, b2, k1) row, 2^30 outputs: the same bits as the
+    tiled kernel on sampled outputs, and those outputs against the oracle's
+    sum over the two summed values."""
+    case = wmcgen.pair_case(17, 17, 2, 1, seed=7 + 17 + 17 + 1, shuffle=False)
+    rng = np.random.default_rng(3)
+    offs = np.concatenate([np.arange(4096), rng.integers(0, 1 << 30, 60000), (1 << 30) - 1 - np.arange(64)])
+    got = _run_pair(w, case, FP32, out_offsets=offs)
+    try:
+        w.wmc_set_outer_products(0)
+        tiled = _run_pair(w, case, FP32, out_offsets=offs)
+    finally:
+        w.wmc_set_outer_products(1)
+    assert np.array_equal(got, tiled)
+    # C = [fa (14 bits), batch (2), fb (14)]; A = [fa, batch, s]; B = [s, batch, fb]
+    i = offs & ((1 << 14) - 1); bb = (offs >> 14) & 3; j = offs >> 16
+    want = sum(case.a[i + (bb << 14) + (s << 16)] * case.b[s + (bb << 1) + (j << 3)] for s in (0, 1))
+    assert (np.abs(got - want) / np.abs(want)).max() <= _pair_tol(1, FP32)
+
+
 # ------------------------------------------------------ clause factoring
 
 def _psi_closed_form(wp, wn):
