@@ -348,6 +348,11 @@ bool try_k2(const std::vector<int32_t> &LP, const std::vector<int32_t> &LS,
   // memory (S staged once per block, at most 2^12 entries)
   p.s_log2 = (int32_t)LS.size();
   p.s_staged = (kmax == 4 && vbits == 0 && LS.size() <= 12) ? 1 : 0;
+  p.s_contig = 0;
+  if (p.s_staged && k == 4) {
+    p.s_contig = 1;
+    for (int s = 0; s < 16; ++s) p.s_contig &= p.dBs[s] == (uint32_t)s;
+  }
   fmax = kmax;
   return true;
 }
@@ -1200,8 +1205,15 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
 
 template <typename T, int V, int K>
 static void launch_k2_t(const K2Params &p, int64_t blocks, cudaStream_t s) {
-  const size_t smem = p.s_staged ? sizeof(T) << p.s_log2 : 0;  // staged S (at most 32 KB)
-  dev::k2_stream<T, V, K, K><<<(unsigned)blocks, dev::kThreads, smem, s>>>(p);
+  if constexpr (K == 4 && V == 1) {
+    if (p.s_staged) {  // S staged in shared memory (at most 32 KB)
+      // grid-stride over the units: one wave of three blocks per SM
+      const unsigned b3 = (unsigned)std::min<int64_t>(blocks, 148 * 3);
+      dev::k2_stream_s16<T><<<b3, dev::kThreads, sizeof(T) << p.s_log2, s>>>(p);
+      return;
+    }
+  }
+  dev::k2_stream<T, V, K, K><<<(unsigned)blocks, dev::kThreads, 0, s>>>(p);
 }
 
 template <typename T, int V>

@@ -258,6 +258,7 @@ struct K2Params {
   uint32_t dC[16];   // ... in C
   uint32_t dBv[4];  // offset in S of vector lane e
   int32_t s_staged;  // S (2^s_log2 entries) staged in shared memory, pre-scaled (k2_stream, K = 4)
+  int32_t s_contig;  // staged, 4 summed bits at S's lowest 4 positions: 16-byte loads of S
   int32_t s_log2;
 };
 
@@ -286,21 +287,27 @@ __device__ __forceinline__ void vstore(T *p, const T (&r)[V]) {
   *reinterpret_cast<VT *>(p) = v;
 }
 
+// four consecutive entries from a 16-byte aligned shared-memory address
+template <typename T>
+__device__ __forceinline__ void lds4(const T *ptr, T (&r)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(ptr);
+    r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+  } else {
+    const double2 v0 = reinterpret_cast<const double2 *>(ptr)[0];
+    const double2 v1 = reinterpret_cast<const double2 *>(ptr)[1];
+    r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+  }
+}
+
 // K (summed bits) and F (S-free bits) are compile-time upper bounds; the
 // runtime p.k / p.f select the active terms.  K = F = 4 runs with one lane
 // per thread (V = 1): 16 P values, 16 scales and 16 max/min pairs.
 template <typename T, int V, int K, int F>
 __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && sizeof(T) == 4) ? 2 : 1)))
     k2_stream(K2Params p) {
-  extern __shared__ __align__(16) unsigned char k2s_smem[];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
-  if (K == 4 && V == 1 && p.s_staged) {
-    T *sS = reinterpret_cast<T *>(k2s_smem);
-    const T *Bg = (const T *)p.B;
-    for (uint32_t j = threadIdx.x; j < (1u << p.s_log2); j += blockDim.x)
-      sS[j] = p.mc.scale_inputs ? __ldg(Bg + j) * operand_scale<T>(p.mb, (int)j, 1) : __ldg(Bg + j);
-  }
   __syncthreads();
   constexpr int NS = 1 << K, NF = 1 << F;
   const int ns = 1 << p.k, nf = 1 << p.f;
@@ -319,9 +326,6 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
     for (int e = 0; e < V; ++e) { tmax[f][e] = (T)0; tmin[f][e] = (T)INFINITY; sb[f][e] = (T)1; }
 #pragma unroll
   for (int e = 0; e < V; ++e) sa[e] = (T)1;
-  uint32_t bsv[NS];  // summed offsets of S (staged path)
-#pragma unroll
-  for (int s = 0; s < NS; ++s) bsv[s] = s < ns ? p.dBs[s] : 0u;
   bool first = true;
   for (uint64_t u = gtid; u < nu; u += stride) {
     const uint32_t w = (uint32_t)u << p.vbits;
@@ -357,27 +361,6 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
 #pragma unroll
         for (int e = 0; e < V; ++e) a[s][e] *= sa[e];
       }
-    if constexpr (K == 4 && V == 1) {
-      if (p.s_staged) {
-        // S from shared memory, already times its lane scale (the same
-        // products b * sb as below); the summed offsets in registers, the
-        // outer loop over the S-free assignments kept rolled.  Every output
-        // of the unit is in one query lane (the S-free bits sit above the
-        // query bits), so one max/min pair tracks them all.
-        const T *sS = reinterpret_cast<const T *>(k2s_smem);
-#pragma unroll 1
-        for (int f = 0; f < nf; ++f) {
-          const T *sf = sS + gb + p.dBf[f];
-          T c = (T)0;
-#pragma unroll
-          for (int s = 0; s < NS; ++s)
-            if (s < ns) c = fma_t(a[s][0], sf[bsv[s]], c);
-          C[oc + p.dC[f]] = c;
-          track(c, tmax[0][0], tmin[0][0]);
-        }
-        continue;
-      }
-    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (f < nf) {
@@ -418,6 +401,119 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
       for (int e = 0; e < V; ++e)
         if (f < nf) publish(smax, smin, (int)((qbase + p.dC[f] + e) & qmask_c), tmax[f][e], tmin[f][e]);
   }
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
+// k2_stream for four summed or S-free bits at one lane per thread with S
+// staged in shared memory (K2Params.s_staged), in a kernel of its own so
+// that it holds only what this path needs (three blocks per SM).  S is
+// staged once per block, already times its lane scale (the products b * sb
+// of k2_stream); the summed offsets sit in registers.  Every output of a
+// unit is in one query lane (the S-free bits sit above the query bits), so
+// one max/min pair tracks them all.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k2_stream_s16(K2Params p) {
+  extern __shared__ __align__(16) unsigned char k2s_smem[];
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  T *sS = reinterpret_cast<T *>(k2s_smem);
+  {
+    const T *Bg = (const T *)p.B;
+    for (uint32_t j = threadIdx.x; j < (1u << p.s_log2); j += blockDim.x)
+      sS[j] = p.mc.scale_inputs ? __ldg(Bg + j) * operand_scale<T>(p.mb, (int)j, 1) : __ldg(Bg + j);
+  }
+  __syncthreads();
+  constexpr int K = 4, NS = 16;
+  const int ns = 1 << p.k, nf = 1 << p.f;
+  const T *A = (const T *)p.A;
+  T *C = (T *)p.C;
+  const uint64_t nu = 1ull << p.log2_nu;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
+  T sa = (T)1, tmax = (T)0, tmin = (T)INFINITY;
+  uint32_t qbase = 0;
+  uint32_t bsv[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) bsv[s] = s < ns ? p.dBs[s] : 0u;
+  bool first = true;
+  for (uint64_t u = gtid; u < nu; u += stride) {
+    uint32_t oa = (uint32_t)u, oc = (uint32_t)u, gb = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < p.n_insA) oa = insert0(oa, p.insA[i]);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < p.n_insC) oc = insert0(oc, p.insC[i]);
+    for (int i = 0; i < p.n_seg; ++i)
+      gb |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+    if (first) {
+      first = false;
+      qbase = oc;
+      if (p.mc.scale_inputs) sa = operand_scale<T>(p.ma, (int)oa, 1);
+    }
+    T a[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (s < ns) a[s] = __ldg(A + oa + p.dA[s]) * sa;
+    // Four outputs at a time (nf is a power of two): four independent
+    // FMA chains hide the shared-memory and FMA latencies; each output
+    // still adds its terms in order.
+    const T *sS = reinterpret_cast<const T *>(k2s_smem);
+    if (nf >= 4) {
+#pragma unroll 1
+      for (int f = 0; f < nf; f += 4) {
+        const T *s0 = sS + gb + p.dBf[f], *s1 = sS + gb + p.dBf[f + 1];
+        const T *s2 = sS + gb + p.dBf[f + 2], *s3 = sS + gb + p.dBf[f + 3];
+        T c0 = (T)0, c1 = (T)0, c2 = (T)0, c3 = (T)0;
+        if (p.s_contig) {
+          // the 16 summed entries of each output are consecutive in S
+#pragma unroll
+          for (int g4 = 0; g4 < NS; g4 += 4) {
+            T v0[4], v1[4], v2[4], v3[4];
+            lds4(s0 + g4, v0); lds4(s1 + g4, v1); lds4(s2 + g4, v2); lds4(s3 + g4, v3);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              c0 = fma_t(a[g4 + r], v0[r], c0);
+              c1 = fma_t(a[g4 + r], v1[r], c1);
+              c2 = fma_t(a[g4 + r], v2[r], c2);
+              c3 = fma_t(a[g4 + r], v3[r], c3);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            if (s < ns) {
+              c0 = fma_t(a[s], s0[bsv[s]], c0);
+              c1 = fma_t(a[s], s1[bsv[s]], c1);
+              c2 = fma_t(a[s], s2[bsv[s]], c2);
+              c3 = fma_t(a[s], s3[bsv[s]], c3);
+            }
+        }
+        C[oc + p.dC[f]] = c0;
+        C[oc + p.dC[f + 1]] = c1;
+        C[oc + p.dC[f + 2]] = c2;
+        C[oc + p.dC[f + 3]] = c3;
+        track(c0, tmax, tmin);
+        track(c1, tmax, tmin);
+        track(c2, tmax, tmin);
+        track(c3, tmax, tmin);
+      }
+    } else {
+#pragma unroll 1
+      for (int f = 0; f < nf; ++f) {
+        const T *sf = sS + gb + p.dBf[f];
+        T c = (T)0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if (s < ns) c = fma_t(a[s], sf[bsv[s]], c);
+        C[oc + p.dC[f]] = c;
+        track(c, tmax, tmin);
+      }
+    }
+  }
+  if (!first) publish(smax, smin, (int)(qbase & qmask_c), tmax, tmin);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
