@@ -47,7 +47,7 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 # DRAM traffic / algorithmic bytes of the dominant kernel, from its ncu
 # capture (None once the kernel changes until it is captured again)
-TRAFFIC_PER_ALG_BYTE = 737.5e6 / 939.7e6
+TRAFFIC_PER_ALG_BYTE = 737.2e6 / 939.7e6
 
 
 def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
