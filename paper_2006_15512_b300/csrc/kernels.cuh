@@ -407,13 +407,14 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
 
 // k2_stream for four summed or S-free bits at one lane per thread with S
 // staged in shared memory (K2Params.s_staged), in a kernel of its own so
-// that it holds only what this path needs (three blocks per SM).  S is
+// that it holds only what this path needs (64 registers: four blocks per SM).  S is
 // staged once per block, already times its lane scale (the products b * sb
 // of k2_stream); the summed offsets sit in registers.  Every output of a
 // unit is in one query lane (the S-free bits sit above the query bits), so
-// one max/min pair tracks them all.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) k2_stream_s16(K2Params p) {
+// one max/min pair tracks them all.  CONTIG: S's 4 summed indices are its
+// lowest bits (K2Params.s_contig), read with 16-byte loads.
+template <typename T, bool CONTIG>
+__global__ void __launch_bounds__(kThreads, 4) k2_stream_s16(K2Params p) {
   extern __shared__ __align__(16) unsigned char k2s_smem[];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
@@ -434,9 +435,9 @@ __global__ void __launch_bounds__(kThreads, 3) k2_stream_s16(K2Params p) {
   const uint32_t qmask_c = (uint32_t)(p.mc.Qc - 1);
   T sa = (T)1, tmax = (T)0, tmin = (T)INFINITY;
   uint32_t qbase = 0;
-  uint32_t bsv[NS];
+  uint32_t bsv[NS];  // summed offsets of S (unused when CONTIG)
 #pragma unroll
-  for (int s = 0; s < NS; ++s) bsv[s] = s < ns ? p.dBs[s] : 0u;
+  for (int s = 0; s < NS; ++s) bsv[s] = (!CONTIG && s < ns) ? p.dBs[s] : 0u;
   bool first = true;
   for (uint64_t u = gtid; u < nu; u += stride) {
     uint32_t oa = (uint32_t)u, oc = (uint32_t)u, gb = 0;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 3) k2_stream_s16(K2Params p) {
         const T *s0 = sS + gb + p.dBf[f], *s1 = sS + gb + p.dBf[f + 1];
         const T *s2 = sS + gb + p.dBf[f + 2], *s3 = sS + gb + p.dBf[f + 3];
         T c0 = (T)0, c1 = (T)0, c2 = (T)0, c3 = (T)0;
-        if (p.s_contig) {
+        if constexpr (CONTIG) {
           // the 16 summed entries of each output are consecutive in S
 #pragma unroll
           for (int g4 = 0; g4 < NS; g4 += 4) {
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 3) k2_stream_s16(K2Params p) {
         T c = (T)0;
 #pragma unroll
         for (int s = 0; s < NS; ++s)
-          if (s < ns) c = fma_t(a[s], sf[bsv[s]], c);
+          if (s < ns) c = fma_t(a[s], sf[CONTIG ? (uint32_t)s : bsv[s]], c);
         C[oc + p.dC[f]] = c;
         track(c, tmax, tmin);
       }
