@@ -1207,9 +1207,9 @@ template <typename T, int V, int K>
 static void launch_k2_t(const K2Params &p, int64_t blocks, cudaStream_t s) {
   if constexpr (K == 4 && V == 1) {
     if (p.s_staged) {  // S staged in shared memory (at most 32 KB)
-      // grid-stride over the units: one wave of four blocks per SM
+      // grid-stride over the units: one wave of three (float64: two) blocks per SM
       const size_t smem = sizeof(T) << p.s_log2;
-      const unsigned b4 = (unsigned)std::min<int64_t>(blocks, 148 * 4);
+      const unsigned b4 = (unsigned)std::min<int64_t>(blocks, 148 * (sizeof(T) == 4 ? 3 : 2));
       if (p.s_contig) dev::k2_stream_s16<T, true><<<b4, dev::kThreads, smem, s>>>(p);
       else dev::k2_stream_s16<T, false><<<b4, dev::kThreads, smem, s>>>(p);
       return;

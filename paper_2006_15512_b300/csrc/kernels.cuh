@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, (K <= 1 ? 4 : (K == 2 || (K == 4 && 
 // one max/min pair tracks them all.  CONTIG: S's 4 summed indices are its
 // lowest bits (K2Params.s_contig), read with 16-byte loads.
 template <typename T, bool CONTIG>
-__global__ void __launch_bounds__(kThreads, 4) k2_stream_s16(K2Params p) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k2_stream_s16(K2Params p) {
   extern __shared__ __align__(16) unsigned char k2s_smem[];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
@@ -439,11 +439,26 @@ __global__ void __launch_bounds__(kThreads, 4) k2_stream_s16(K2Params p) {
 #pragma unroll
   for (int s = 0; s < NS; ++s) bsv[s] = (!CONTIG && s < ns) ? p.dBs[s] : 0u;
   bool first = true;
-  for (uint64_t u = gtid; u < nu; u += stride) {
-    uint32_t oa = (uint32_t)u, oc = (uint32_t)u, gb = 0;
+  auto p_offset = [&](uint64_t uu) {
+    uint32_t o = (uint32_t)uu;
 #pragma unroll
     for (int i = 0; i < K; ++i)
-      if (i < p.n_insA) oa = insert0(oa, p.insA[i]);
+      if (i < p.n_insA) o = insert0(o, p.insA[i]);
+    return o;
+  };
+  // P entries of the next unit, requested before this unit's products
+  T an[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) an[s] = (T)0;
+  if (gtid < nu) {
+    const uint32_t o = p_offset(gtid);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (s < ns) an[s] = __ldg(A + o + p.dA[s]);
+  }
+  for (uint64_t u = gtid; u < nu; u += stride) {
+    const uint32_t oa = p_offset(u);
+    uint32_t oc = (uint32_t)u, gb = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i)
       if (i < p.n_insC) oc = insert0(oc, p.insC[i]);
@@ -456,8 +471,13 @@ __global__ void __launch_bounds__(kThreads, 4) k2_stream_s16(K2Params p) {
     }
     T a[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if (s < ns) a[s] = __ldg(A + oa + p.dA[s]) * sa;
+    for (int s = 0; s < NS; ++s) a[s] = an[s] * sa;
+    if (u + stride < nu) {
+      const uint32_t o = p_offset(u + stride);
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (s < ns) an[s] = __ldg(A + o + p.dA[s]);
+    }
     // Four outputs at a time (nf is a power of two): four independent
     // FMA chains hide the shared-memory and FMA latencies; each output
     // still adds its terms in order.
