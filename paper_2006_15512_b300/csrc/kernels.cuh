@@ -94,14 +94,18 @@ __device__ __forceinline__ void track(T c, T &tmax, T &tmin) {
 // float64: the same max and min from the bit patterns on the integer units
 // (nonnegative IEEE values order as their bits; NaNs are skipped), leaving
 // B300's few FP64 units to the products
+// (compared as 32-bit halves: high words first, low words on a tie)
 template <>
 __device__ __forceinline__ void track<double>(double c, double &tmax, double &tmin) {
-  constexpr unsigned long long kInf = 0x7ff0000000000000ull;
-  const unsigned long long a = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffull;
-  const unsigned long long mx = (unsigned long long)__double_as_longlong(tmax);
-  const unsigned long long mn = (unsigned long long)__double_as_longlong(tmin);
-  tmax = __longlong_as_double((long long)((a > mx && a <= kInf) ? a : mx));
-  tmin = __longlong_as_double((long long)((a != 0ull && a < mn) ? a : mn));
+  const uint32_t ah = (uint32_t)__double2hiint(c) & 0x7fffffffu, al = (uint32_t)__double2loint(c);
+  const uint32_t xh = (uint32_t)__double2hiint(tmax), xl = (uint32_t)__double2loint(tmax);
+  const uint32_t nh = (uint32_t)__double2hiint(tmin), nl = (uint32_t)__double2loint(tmin);
+  const bool finite_or_inf = ah < 0x7ff00000u || (ah == 0x7ff00000u && al == 0u);
+  const bool gt = ah > xh || (ah == xh && al > xl);
+  const bool lt = ah < nh || (ah == nh && al < nl);
+  const bool nz = (ah | al) != 0u;
+  if (gt && finite_or_inf) tmax = __hiloint2double((int)ah, (int)al);
+  if (lt && nz) tmin = __hiloint2double((int)ah, (int)al);
 }
 
 template <typename T>
@@ -641,9 +645,26 @@ template <typename T>
 __device__ __forceinline__ T max_abs(T m, T x) { return fmax(m, fabs(x)); }
 template <>
 __device__ __forceinline__ double max_abs<double>(double m, double x) {
-  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  const unsigned long long mb = (unsigned long long)__double_as_longlong(m);
-  return __longlong_as_double((long long)((a > mb && a <= 0x7ff0000000000000ull) ? a : mb));
+  const uint32_t ah = (uint32_t)__double2hiint(x) & 0x7fffffffu, al = (uint32_t)__double2loint(x);
+  const uint32_t mh = (uint32_t)__double2hiint(m), ml = (uint32_t)__double2loint(m);
+  const bool finite_or_inf = ah < 0x7ff00000u || (ah == 0x7ff00000u && al == 0u);
+  const bool gt = ah > mh || (ah == mh && al > ml);
+  return (gt && finite_or_inf) ? __hiloint2double((int)ah, (int)al) : m;
+}
+
+// min(bits - 1, cur) on IEEE bit patterns: zero maps to the largest value,
+// so the running minimum is the smallest nonzero magnitude minus one
+__device__ __forceinline__ uint32_t min_m1(uint32_t bits, uint32_t cur) {
+  return __viaddmin_u32(bits, 0xffffffffu, cur);
+}
+// float64: the same in 32-bit halves (subtract with borrow, compare high
+// words first), off the slower 64-bit integer path
+__device__ __forceinline__ unsigned long long min_m1(unsigned long long bits, unsigned long long cur) {
+  const uint32_t lo = (uint32_t)bits, hi = (uint32_t)(bits >> 32);
+  const uint32_t mlo = lo - 1u, mhi = hi - (lo == 0u ? 1u : 0u);
+  const uint32_t clo = (uint32_t)cur, chi = (uint32_t)(cur >> 32);
+  const bool lt = mhi < chi || (mhi == chi && mlo < clo);
+  return lt ? (((unsigned long long)mhi << 32) | mlo) : cur;
 }
 
 template <typename T>
@@ -900,8 +921,7 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
 #pragma unroll
             for (int e = 0; e < V; ++e) {
               tmax[f][e] = max_abs(tmax[f][e], c[e]);
-              const BT bm1 = to_bits(c[e]) - (BT)1;
-              tminm1[f][e] = bm1 < tminm1[f][e] ? bm1 : tminm1[f][e];
+              tminm1[f][e] = min_m1(to_bits(c[e]), tminm1[f][e]);
             }
           }
         }
@@ -1156,13 +1176,6 @@ struct ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, D> {
 };
 
 // min over nonzero bit patterns, tracked as (bits - 1) with zero wrapping
-__device__ __forceinline__ uint32_t min_m1(uint32_t bits, uint32_t cur) {
-  return __viaddmin_u32(bits, 0xffffffffu, cur);
-}
-__device__ __forceinline__ unsigned long long min_m1(unsigned long long bits, unsigned long long cur) {
-  const unsigned long long m = bits - 1ull;
-  return m < cur ? m : cur;
-}
 
 template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) {
