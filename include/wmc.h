@@ -398,15 +398,15 @@ void wmc_set_dependent_launch(int32_t on);
  * off, on the scalar tiled kernel.  The two agree within float32 rounding,
  * not bit for bit. */
 void wmc_set_tensor_cores(int32_t on);
-/* Execution option (default on): dense products with at most 4 summed
- * values whose C has one operand's first 10 free indices as its lowest 10
- * bits, at one query lane and at least 2^24 outputs, run on a streaming
- * outer-product kernel (each thread keeps 4 consecutive entries of that
- * operand in registers and writes 4 consecutive outputs per value of the
- * other side); off, on the tiled scalar kernel.  Both add the summed terms
- * in the same order, so the results are the same bits.  Read by
- * wmc_contract_pair at each call and by a plan's execution state when it
- * is built. */
+/* Execution option (default on): wmc_contract_pair runs dense products
+ * with at most 4 summed values whose C has one operand's first 10 free
+ * indices as its lowest 10 bits, at least 2^24 outputs and a 16-byte
+ * aligned c, on a streaming outer-product kernel (each thread keeps 4
+ * consecutive entries of that operand in registers and writes 4
+ * consecutive outputs per value of the other side); off, on the tiled
+ * scalar kernel.  Both add the summed terms in the same order, so the
+ * results are the same bits.  Read at each call; walks keep the tiled
+ * kernel. */
 void wmc_set_outer_products(int32_t on);
 /* Execution option (default on): wmc_execute and wmc_execute_slices run the
  * queries of a scaled-FP32 plan whose results carry WMC_FLAG_FP32_FLUSH

@@ -687,10 +687,10 @@ bool try_k4(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
   return true;
 }
 
-// k4_outer in place of k4_dense: at most 2 summed bits, one query lane, C's
-// low 10 bits the first 10 free bits of A (u = i) or of B (u = j), and at
-// least 2^8 blocks of 1024 x 64 outputs.  Sets p.outer_u; returns the
-// block count, or 0 to keep k4_dense.
+// k4_outer in place of k4_dense (wmc_contract_pair): at most 2 summed bits,
+// one query lane, C's low 10 bits the first 10 free bits of A (u = i) or of
+// B (u = j), and at least 2^8 blocks of 1024 x 64 outputs.  Sets p.outer_u;
+// returns the block count, or 0 to keep k4_dense.
 int64_t k4_outer_pick(wmc::dev::K4Params &p) {
   p.outer_u = 0;
   if (p.ns > 2 || p.mc.Qc != 1) return 0;
@@ -887,10 +887,6 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     mc.Qc = C.has_q ? Qp : 1;
     mc.Q = Qp;
     mc.scale_inputs = 1;
-    if (l.kind == L_K4 && g_outer.load()) {
-      const int64_t ob = k4_outer_pick(l.k4);
-      if (ob) l.blocks = ob;
-    }
   }
 
   // ---- fuse consecutive frontier eliminations (i, j): node j's large
@@ -1511,14 +1507,8 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
         p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
         p.mc.flags = flags;
-        if (p.outer_u) {
-          if (l.ti == TD) dev::k4_outer<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
-          else dev::k4_outer<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
-        } else if (l.ti == TD) {
-          dev::k4_dense<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
-        } else {
-          dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
-        }
+        if (l.ti == TD) dev::k4_dense<double><<<(unsigned)l.blocks, 256, 0, s>>>(p);
+        else dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
         break;
       }
       case L_K2: {
