@@ -219,6 +219,20 @@ int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_pos_q,
                        const double *w_neg_q, int64_t slice_lo, int64_t slice_hi,
                        void *stream, wmc_result *out);
 
+/* Sum of partial results (Thm 4.2: the count is the sum over the slice
+ * assignments eta of the counts conditioned on eta), e.g. the shares that
+ * several processes computed with wmc_execute_slices over disjoint slice
+ * ranges (Alg. 3, one share per process).  parts: host, n records (n >= 0;
+ * may be NULL when n = 0); out: host, one record.  The parts are brought to
+ * the largest part's binary exponent and added in order in float64, so
+ * counts far outside the float64 range combine without overflow.  flags:
+ * the OR of the parts' flags, except WMC_FLAG_EXACT_INT, which is kept only
+ * if every part carries it and the sum is below 2^53.  rel_err_bound: the
+ * largest part bound plus (n - 1) * 2^-53 (nonnegative parts).  Host only,
+ * allocates nothing.  Errors: WMC_EINVAL (NULL out, negative n, a part
+ * that is not finite). */
+int wmc_combine_results(const wmc_result *parts, int64_t n, wmc_result *out);
+
 /* Execution with device-resident inputs and outputs, asynchronous on
  * `stream`.  d_w_pos / d_w_neg: device [Q][n_vars] float64.  d_workspace:
  * device memory of at least wmc_plan_info(Q).workspace_bytes, 256-byte
@@ -232,23 +246,30 @@ int wmc_execute_device(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                        size_t workspace_bytes, double *d_mant,
                        int64_t *d_exp2, uint32_t *d_flags, void *stream);
 
-/* Allocation-free variant of wmc_execute_device (the paper has no
- * counterpart; this serves callers that cannot allocate device memory:
- * code enqueuing work while a stream is being captured into a CUDA graph,
- * serving loops that cannot afford the synchronisation or latency of
- * cudaMalloc/cudaFree, and hosts whose device memory belongs to another
- * allocator).  Same walk, kernels and results as wmc_execute_device, but
- * the leaf tables and the workspace live in a fixed 32 MiB scratch array
- * that is part of the library's device image (every GPU that loads the
- * library holds it until exit).  Calls no cudaMalloc, cudaFree or other
- * allocating routine.  Plans whose tables plus workspace at this Q exceed
- * 32 MiB are rejected with WMC_EINVAL (wmc_last_error gives the size).
- * The first call on each device looks up the scratch's device address with
- * that device current; make that first call before any stream capture.
- * Every call shares the one scratch array and the walk clears what it
- * accumulates into, but calls whose work overlaps on the GPU (different
- * streams, or different host threads) race on it: serialise them.
- * Inputs and outputs as for wmc_execute_device. */
+/* Allocation-free variant of wmc_execute_device.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory when
+ * they run a count -- a library embedded in a host process whose device
+ * memory is entirely owned by another allocator (a framework's caching
+ * allocator, a pool reserved up front), or code that must not call
+ * cudaMalloc/cudaFree once it is running, since both can synchronise the
+ * device.  Same walk, kernels and results (bit for bit) as
+ * wmc_execute_device, but the leaf tables and the workspace live in a
+ * fixed 32 MiB scratch array that is part of the library's device image
+ * (every GPU that loads the library holds it until exit).  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Plans whose tables
+ * plus workspace at this Q exceed 32 MiB are rejected with WMC_EINVAL
+ * (wmc_last_error gives the size).  The first call on each device looks up
+ * the scratch's device address, with that device current, and keeps it
+ * for the life of the process (a cudaDeviceReset of that device
+ * invalidates it, as it invalidates every plan's device state).  The leaf
+ * tables are copied from host memory only when the scratch holds another
+ * plan's (or another Q's); the call descriptor travels as a kernel
+ * argument.  Every call shares the one scratch array, which keeps the last
+ * call's contents; the walk clears what it accumulates into, but calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads without ordering between their streams) race on it: serialise
+ * them.  Inputs and outputs as for wmc_execute_device (asynchronous on
+ * `stream`).  Errors: WMC_EINVAL (bad argument, plan too large), WMC_ECUDA. */
 int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q,
                                const double *d_w_pos, const double *d_w_neg,
                                double *d_mant, int64_t *d_exp2,
@@ -312,6 +333,13 @@ typedef struct {
 int wmc_batch_info(const wmc_batch_t *batch, wmc_batch_info_t *out);
 /* Synchronous on `stream`; out[i] is the result of admitted formula i. */
 int wmc_batch_execute(wmc_batch_t *batch, void *stream, wmc_result *out);
+/* Layout of admitted formula i (0 <= i < n_formulas), for inspection: the
+ * byte offset of its workspace inside the batch workspace, its largest
+ * tensor rank and its number of pairwise contractions.  Any output pointer
+ * may be NULL.  Errors: WMC_EINVAL (bad handle or index). */
+int wmc_batch_formula_info(const wmc_batch_t *batch, int32_t i,
+                           int64_t *ws_offset, int32_t *max_rank,
+                           int64_t *n_nodes);
 void wmc_batch_destroy(wmc_batch_t *batch);
 
 /* ------------------------------------------------------------- serving */

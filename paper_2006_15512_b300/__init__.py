@@ -65,31 +65,17 @@ def slice_range(n_slices: int, rank: int, world: int):
 
 
 def combine_results(parts: Sequence[Result]) -> Result:
-    """Sum of partial results mant * 2**exp2 (e.g. the slice shares of
-    several processes), with the exponents aligned to the largest and the
-    sum kept in float64; flags are OR-ed and the error bounds add up (plus
-    one float64 rounding per addition)."""
-    total_m, total_e = 0.0, 0
-    flags, bound = 0, 0.0
-    for r in parts:
-        flags |= r.flags
-        bound = max(bound, r.rel_err_bound)
-        if r.mant == 0.0:
-            continue
-        m, e = math.frexp(r.mant)
-        e += r.exp2
-        if total_m == 0.0:
-            total_m, total_e = m, e
-            continue
-        if e > total_e:
-            total_m, total_e, m, e = m, e, total_m, total_e
-        d = total_e - e
-        total_m += math.ldexp(m, -d) if d <= 1100 else 0.0
-        fm, fe = math.frexp(total_m)
-        total_m, total_e = fm, total_e + fe
-    bound += max(len(parts) - 1, 0) * 2.0 ** -53
-    log10 = (math.log10(abs(total_m)) + total_e * math.log10(2.0)) if total_m != 0.0 else -math.inf
-    return Result(total_m, total_e if total_m != 0.0 else 0, log10, flags, bound)
+    """wmc_combine_results: the sum of partial results mant * 2**exp2 (e.g.
+    the slice shares of several processes, Thm 4.2), computed in the C
+    library."""
+    parts = list(parts)
+    arr = (_abi.wmc_result * max(len(parts), 1))()
+    for i, r in enumerate(parts):
+        arr[i].mant, arr[i].exp2, arr[i].log10 = r.mant, r.exp2, r.log10
+        arr[i].flags, arr[i].rel_err_bound = r.flags, r.rel_err_bound
+    out = _abi.wmc_result()
+    check(lib.wmc_combine_results(arr, len(parts), ctypes.byref(out)), "wmc_combine_results")
+    return Result.from_c(out)
 
 
 class Network:
@@ -290,6 +276,13 @@ class Batch:
         out = _abi.wmc_batch_info_t()
         check(lib.wmc_batch_info(self.handle, ctypes.byref(out)), "wmc_batch_info")
         return out
+
+    def formula_info(self, i: int):
+        """(workspace byte offset, max rank, node count) of admitted formula i."""
+        off = ctypes.c_int64(); r = ctypes.c_int32(); n = ctypes.c_int64()
+        check(lib.wmc_batch_formula_info(self.handle, int(i), ctypes.byref(off), ctypes.byref(r),
+                                         ctypes.byref(n)), "wmc_batch_formula_info")
+        return int(off.value), int(r.value), int(n.value)
 
     def execute(self, stream: int = 0) -> List[Result]:
         out = (_abi.wmc_result * self.n_admitted)()

@@ -112,6 +112,7 @@ EXPORTS = {
     "wmc_plan_leaf": (c_i32, [c_vp, c_i64, P(c_i32), P(c_i32), P(c_i32), P(c_u64)]),
     "wmc_execute": (c_i32, [c_vp, c_i32, P(c_dbl), P(c_dbl), c_vp, P(wmc_result)]),
     "wmc_execute_slices": (c_i32, [c_vp, c_i32, P(c_dbl), P(c_dbl), c_i64, c_i64, c_vp, P(wmc_result)]),
+    "wmc_combine_results": (c_i32, [P(wmc_result), c_i64, P(wmc_result)]),
     "wmc_execute_device": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_size, c_vp, c_vp, c_vp, c_vp]),
     "wmc_execute_device_noalloc": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_contract_pair": (c_i32, [c_i32, c_i32, P(c_i32), c_vp, c_i32, P(c_i32), c_vp, c_i32,
@@ -120,6 +121,7 @@ EXPORTS = {
     "wmc_batch_create": (c_i32, [P(c_vp), c_i32, c_i64, P(c_vp), P(c_i32)]),
     "wmc_batch_info": (c_i32, [c_vp, P(wmc_batch_info_t)]),
     "wmc_batch_execute": (c_i32, [c_vp, c_vp, P(wmc_result)]),
+    "wmc_batch_formula_info": (c_i32, [c_vp, c_i32, P(c_i64), P(c_i32), P(c_i64)]),
     "wmc_batch_destroy": (None, [c_vp]),
     "wmc_server_create": (c_i32, [c_vp, P(wmc_server_opts), P(c_vp)]),
     "wmc_submit": (c_i32, [c_vp, P(c_dbl), P(c_dbl), P(c_u64)]),

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libwmc_b300.so")
 
-SOURCES = ["network.cpp", "planner.cpp", "executor.cu", "batch.cu", "server.cpp"]
+SOURCES = ["network.cpp", "planner.cpp", "executor.cu", "batch.cu", "server.cpp", "combine.cpp"]
 HEADERS = ["internal.h", "kernels.cuh", "dev_common.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -635,4 +635,13 @@ extern "C" int wmc_batch_info(const wmc_batch_t *b, wmc_batch_info_t *out) {
   return WMC_OK;
 }
 
+extern "C" int wmc_batch_formula_info(const wmc_batch_t *b, int32_t i, int64_t *ws_offset,
+                                      int32_t *max_rank, int64_t *n_nodes) {
+  if (!b || i < 0 || (size_t)i >= b->plans.size()) { set_error("bad batch or formula index"); return WMC_EINVAL; }
+  if (ws_offset) *ws_offset = b->base[(size_t)i];
+  if (max_rank) *max_rank = b->plans[(size_t)i]->max_rank;
+  if (n_nodes) *n_nodes = (int64_t)b->plans[(size_t)i]->nodes.size();
+  return WMC_OK;
+}
+
 extern "C" void wmc_batch_destroy(wmc_batch_t *b) { delete b; }

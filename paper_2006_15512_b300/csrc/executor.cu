@@ -123,7 +123,10 @@ struct Launch {
 
 namespace wmc {
 
+static std::atomic<uint64_t> g_state_serial{0};
+
 struct ExecState {
+  uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
   int32_t Qp = 1;  // Q padded to 2^m: the query index is m bits
   bool f64 = false;
@@ -2207,11 +2210,11 @@ extern "C" int wmc_to_scaled_fp32(const double *x, int64_t n, float *out, int64_
 
 // ------------------------------------------------- allocation-free variant
 //
-// Some callers cannot call cudaMalloc: code that enqueues work while a
-// stream is being captured into a CUDA graph (allocation is not a
-// capturable operation), serving loops that must not take the device-wide
-// synchronisation of a cudaMalloc/cudaFree or its latency spikes, and hosts
-// whose device memory is entirely owned by another allocator.  For them,
+// Some callers cannot allocate device memory at the time they run a count:
+// a library embedded in a host process whose device memory is entirely
+// owned by another allocator (a framework's caching allocator, or a pool
+// reserved up front), and code that must not call cudaMalloc/cudaFree once
+// it is running (both can synchronise the device).  For them,
 // wmc_execute_device_noalloc runs the same walk on a fixed scratch array
 // that is part of this library's device image instead of on caller- or
 // library-allocated memory.
@@ -2223,13 +2226,14 @@ static constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[256];  // device address of the scratch, per device
+static void *g_noalloc_ptr[256];         // device address of the scratch, per device
+static uint64_t g_noalloc_tables[256];   // serial of the state whose tables it holds (0: none)
 
-static int noalloc_scratch(void **out) {
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
+// Looked up once per device, by the first call on that device, with that
+// device current.  A cudaDeviceReset of the device invalidates it (as it
+// invalidates every plan's cached device state).
+static int noalloc_scratch(int dev, void **out) {
   if (dev < 0 || dev >= 256) { set_error("device id %d out of range", dev); return WMC_EINVAL; }
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -2242,6 +2246,10 @@ static int noalloc_scratch(void **out) {
   *out = g_noalloc_ptr[dev];
   return WMC_OK;
 }
+
+// The call descriptor travels as a kernel argument (copied at launch), so
+// nothing reads host memory after the call returns.
+__global__ void k_store_io(IoDesc io, IoDesc *dst) { *dst = io; }
 
 extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                                           const double *d_w_neg, double *d_mant, int64_t *d_exp2,
@@ -2273,16 +2281,29 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
               need, Q, kNoAllocScratchBytes);
     return WMC_EINVAL;
   }
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   char *base = nullptr;
-  if ((rc = noalloc_scratch((void **)&base))) return rc;
+  if ((rc = noalloc_scratch(dev, (void **)&base))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  if (b_clause) CUDA_TRY(cudaMemcpyAsync(base, st->h_clause.data(), b_clause, cudaMemcpyHostToDevice, s));
-  if (b_first) CUDA_TRY(cudaMemcpyAsync(base + o_first, st->h_first.data(), b_first, cudaMemcpyHostToDevice, s));
-  if (b_woff) CUDA_TRY(cudaMemcpyAsync(base + o_woff, st->h_woff.data(), b_woff, cudaMemcpyHostToDevice, s));
-  if (b_wmeta) CUDA_TRY(cudaMemcpyAsync(base + o_wmeta, st->h_wmeta.data(), b_wmeta, cudaMemcpyHostToDevice, s));
-  if (b_sn) CUDA_TRY(cudaMemcpyAsync(base + o_sn, st->h_snodes.data(), b_sn, cudaMemcpyHostToDevice, s));
-  if (b_stk) CUDA_TRY(cudaMemcpyAsync(base + o_stk, st->h_stasks.data(), b_stk, cudaMemcpyHostToDevice, s));
-  if (b_seq) CUDA_TRY(cudaMemcpyAsync(base + o_seq, st->h_seq.data(), b_seq, cudaMemcpyHostToDevice, s));
+  // The tables depend on the plan and Q alone and the walk never writes
+  // them: they are copied only when the scratch holds another state's.
+  if (g_noalloc_tables[dev] != st->serial) {
+    g_noalloc_tables[dev] = 0;
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+      return bytes ? cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    if (up(0, st->h_clause.data(), b_clause) || up(o_first, st->h_first.data(), b_first) ||
+        up(o_woff, st->h_woff.data(), b_woff) || up(o_wmeta, st->h_wmeta.data(), b_wmeta) ||
+        up(o_sn, st->h_snodes.data(), b_sn) || up(o_stk, st->h_stasks.data(), b_stk) ||
+        up(o_seq, st->h_seq.data(), b_seq)) {
+      set_error("copying the leaf tables into the static scratch failed: %s",
+                cudaGetErrorString(cudaGetLastError()));
+      return WMC_ECUDA;
+    }
+    g_noalloc_tables[dev] = st->serial;
+  }
   char *ws = base + o_ws;
   IoDesc io = io_desc(*plan, d_w_pos, d_w_neg, d_mant, d_exp2, d_flags);
   const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
@@ -2290,13 +2311,14 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
                           (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk),
                           (const wmc::dev::K2CParams *)(base + o_seq)};
   // the walk's first launch zeroes the flags and metadata it accumulates
-  // into; one walk per slice assignment (index slicing)
+  // into; one walk per slice assignment (index slicing), the later ones
+  // adding into the outputs
   for (int64_t eta = 0; eta < n_slices(*plan); ++eta) {
     io.slice = (uint64_t)eta;
     io.accumulate = eta != 0;
-    CUDA_TRY(cudaMemcpyAsync(ws + st->off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    k_store_io<<<1, 1, 0, s>>>(io, (IoDesc *)(ws + st->off_io));
     enqueue_walk(*plan, *st, ws, s, nullptr, &tables);
-    g_launches.fetch_add(st->kernels_per_run);
+    g_launches.fetch_add(st->kernels_per_run + 1);
   }
   CUDA_TRY(cudaGetLastError());
   return WMC_OK;

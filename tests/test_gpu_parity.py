@@ -304,6 +304,31 @@ def test_pair_full_size_sampled(w, precision, ra, rb, b, k):
     torch.cuda.empty_cache()
 
 
+# nodes summing more than 2^16 terms (Eq. (1) with 17..20 summed indices):
+# (rank A, rank B, batch, summed); the last one would be a dense batched
+# product (2^6 x 2^6 free values) if its summed range were short
+SWEEP_LONG_SUM = [(24, 22, 0, 18), (22, 21, 2, 17), (21, 21, 1, 20), (23, 23, 0, 17)]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("ra,rb,b,k", SWEEP_LONG_SUM)
+def test_pair_long_summed_range_accumulates_in_fp64(w, precision, ra, rb, b, k):
+    """A node whose summed extent exceeds 2^16 accumulates in float64 even
+    on the scaled-FP32 path.  The float32 result then differs from the
+    exact sum only by the rounding of the float32 inputs (2 u per product)
+    and of the output (u), u = 2^-24: a tolerance of 4 u.  Summing 2^17 or
+    more terms in float32 (even in 256-term blocks) drifts well past it."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=300 + ra + rb + k, shuffle=True)
+    rc = len(case.labels_c)
+    offs = np.random.default_rng(k).integers(0, 1 << rc, size=min(48, 1 << rc))
+    offs[0], offs[-1] = 0, (1 << rc) - 1
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c, offs)
+    got = _run_pair(w, case, precision, offs)
+    err = np.abs(got - want) / np.abs(want)
+    tol = 1e-12 if precision == FP64 else 4 * 2.0 ** -24
+    assert err.max() <= tol, err.max()
+
+
 def test_pair_edge_cases(w):
     """Rank-0 output (full inner product), no summed index (outer product),
     a summed index present in one operand only."""
@@ -504,6 +529,86 @@ def test_uneven_batch_admission(w):
     batch = w.Batch(plans, mem_budget_bytes=budget)
     assert batch.n_admitted == 4
     assert len(batch.execute()) == 4
+
+
+_C5_CACHE = {}
+
+
+def _c5_formulas(w, precision):
+    """The uneven-batch configuration at full scale: the first 512 candidates
+    (random 3-CNF n in [40, 120], clause ratio [2.0, 3.5]; grids of width
+    6..20 and height 20..150; seed 3) whose plans have max-rank <= 26,
+    planned on host threads (the planner releases the GIL)."""
+    if precision in _C5_CACHE:
+        return _C5_CACHE[precision]
+    from concurrent.futures import ThreadPoolExecutor
+    cands = []
+    gen = wmcgen.uneven_candidates(3)
+    plans = []
+    with ThreadPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2))) as ex:
+        while len(plans) < 512:
+            chunk = [next(gen) for _ in range(64)]
+
+            def one(c):
+                kind, cnf, wp, wn, sub = c
+                try:
+                    return w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=precision, max_rank_cap=26)
+                except w._abi.WmcError:
+                    return None
+            for c, p in zip(chunk, ex.map(one, chunk)):
+                if p is not None and len(plans) < 512:
+                    plans.append(p)
+                    cands.append(c)
+    _C5_CACHE[precision] = (plans, cands)
+    return plans, cands
+
+
+_C5_ORACLE = {}
+
+
+def _c5_want(i, cand):
+    if i not in _C5_ORACLE:
+        kind, cnf, wp, wn, sub = cand
+        if kind.startswith("grid"):  # row by row or column by column
+            h_, w_ = (int(v) for v in kind[4:].split("x"))
+            orders = (list(range(1, cnf.n_vars + 1)), wmcgen.grid_column_order(h_, w_))
+        else:  # the oracle's two greedy orders
+            orders = (oracle.min_degree_order(cnf), oracle.min_fill_order(cnf))
+        order = min(orders, key=lambda o: oracle.induced_width(cnf, o))
+        _C5_ORACLE[i] = oracle.bucket_elim(cnf, wp, wn, order=order, max_width=30)
+    return _C5_ORACLE[i]
+
+
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_uneven_batch_full_scale(w, precision):
+    """The uneven-batch configuration as benchmarked: 512 formulas in one
+    persistent launch, a workspace of many GiB.  Compared with the oracle
+    (bucket elimination, long double): every formula of max-rank 26, and
+    formulas laid out past byte 2^32 of the batch workspace, one of each
+    kind per GiB beyond it."""
+    plans, cands = _c5_formulas(w, precision)
+    batch = w.Batch(plans)
+    assert batch.n_admitted == 512
+    assert batch.info().workspace_bytes > 2 ** 32
+    layout = [batch.formula_info(i) for i in range(512)]
+    sample = [i for i, (off, r, n) in enumerate(layout) if r == 26]
+    assert len(sample) >= 8
+    seen = set()
+    for i, (off, r, n) in enumerate(layout):
+        key = (off >> 30, cands[i][0][:4])
+        if off >= 2 ** 32 and r <= 17 and key not in seen:
+            seen.add(key)
+            sample.append(i)
+    assert any(layout[i][0] >= 2 ** 32 and layout[i][1] == 26 for i in sample)
+    assert layout[-1][0] >= 2 ** 32
+    sample.append(511)
+    for rep in range(2):
+        res = batch.execute()
+        for i in sorted(set(sample)):
+            r = rel(res[i], _c5_want(i, cands[i]))
+            assert r <= TOL[precision], (i, cands[i][0], layout[i], r)
+            assert r <= res[i].rel_err_bound + 1e-16, (i, r, res[i].rel_err_bound)
+    del batch
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])

@@ -275,6 +275,28 @@ def test_slice_ranges_and_combination():
     tiny = w.combine_results([R(0.5, -5000, 0, 0, 0.0), R(0.5, -5001, 0, 0, 0.0)])
     assert (tiny.mant, tiny.exp2) == (0.75, -5000)
     assert w.combine_results([]).mant == 0.0
+    # exact integer shares stay flagged exact while the total is below 2^53
+    E = w.WMC_FLAG_EXACT_INT
+    ex = w.combine_results([R(0.5, 52, 0, E, 0.0), R(0.75, 2, 0, E, 0.0)])
+    assert ex.to_float() == 2.0 ** 51 + 3 and ex.flags == E
+    big = w.combine_results([R(0.5, 53, 0, E, 0.0), R(0.5, 53, 0, E, 0.0)])
+    assert big.to_float() == 2.0 ** 53 and not big.flags & E
+    assert not w.combine_results([R(0.5, 2, 0, E, 0.0), R(0.5, 2, 0, 0, 0.0)]).flags & E
+    # exponents far apart: the small part is below the sum's last bit
+    far = w.combine_results([R(0.5, 5000, 0, 0, 0.0), R(0.5, -5000, 0, 0, 0.0)])
+    assert (far.mant, far.exp2) == (0.5, 5000)
+    # unnormalised mantissas are accepted (value = mant * 2^exp2)
+    un = w.combine_results([R(3.0, 4, 0, 0, 0.0), R(-1.0, 4, 0, 0, 0.0)])
+    assert un.to_float() == 32.0
+    assert math.isclose(un.log10, math.log10(32.0), rel_tol=1e-15)
+    # error bound: the largest part bound plus one rounding per addition
+    b3 = w.combine_results([R(0.5, 1, 0, 0, 1e-7), R(0.5, 1, 0, 0, 3e-7), R(0.5, 1, 0, 0, 0.0)])
+    assert b3.rel_err_bound == 3e-7 + 2 * 2.0 ** -53
+    out = w._abi.wmc_result()
+    assert w.wmc_combine_results(None, -1, ctypes.byref(out)) == w.WMC_EINVAL
+    nan = (w._abi.wmc_result * 1)()
+    nan[0].mant = float("nan")
+    assert w.wmc_combine_results(nan, 1, ctypes.byref(out)) == w.WMC_EINVAL
 
 
 # ------------------------------------------------------ clause factoring

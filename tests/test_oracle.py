@@ -260,6 +260,27 @@ def test_implication_chain(n):
         assert oracle.brute_force(cnf, *wmcgen.weights_unit(n))[1] == n + 1
 
 
+@pytest.mark.parametrize("n", [64, 65, 100, 127])
+def test_exact_count_beyond_64_bits_free_variables(n):
+    """Unweighted count of n free variables is 2^n (Def. 2.1 with unit
+    weights): counts at and beyond 2^64 exercise the upper half of the
+    128-bit result."""
+    assert oracle.count_exact(wmcgen.Cnf(n, [])) == 2 ** n
+
+
+@pytest.mark.parametrize("n", [92, 100, 180])
+def test_exact_count_beyond_64_bits_or_chain(n):
+    """(x1|x2)&...&(x_{n-1}|x_n) has F(n+2) models; F(94) > 2^64, F(182)
+    is just below 2^125."""
+    assert _fib(n + 2) >= 2 ** 64
+    assert oracle.count_exact(wmcgen.chain_or(n)) == _fib(n + 2)
+
+
+def test_exact_count_beyond_64_bits_independent_clauses():
+    """40 disjoint 3-literal clauses: 7^40 (about 2^112) models."""
+    assert oracle.count_exact(wmcgen.independent_clauses(40, 3, seed=2)) == 7 ** 40
+
+
 # ------------------------------------------ theorems used as invariants
 
 @pytest.mark.parametrize("seed", range(8))
@@ -289,6 +310,27 @@ def test_order_independence(seed):
         order = list(rng.permutation(16) + 1)
         assert rel(oracle.bucket_elim(cnf, wp, wn, order=order), ref) < 1e-15
         assert oracle.count_exact(cnf, order=order) == cref
+
+
+def test_min_fill_order_and_induced_width():
+    """The second elimination order is a permutation and gives brute
+    force's value (Thm 3.1); induced_width equals the bucket size the
+    elimination reports, and known widths: an or-chain eliminated in
+    order has buckets of 2 variables, one clause over k variables a bucket
+    of k, an H x W grid eliminated column by column buckets of H + 2."""
+    for seed in range(4):
+        cnf = wmcgen.random_kcnf(18, 60, seed=90 + seed)
+        wp, wn = wmcgen.weights_complementary(18, seed, 0.1, 0.9)
+        o = oracle.min_fill_order(cnf)
+        assert sorted(o) == list(range(1, 19))
+        v, wd = oracle.bucket_elim(cnf, wp, wn, order=o, return_width=True)
+        assert rel(v, oracle.brute_force(cnf, wp, wn)[0]) < 1e-15
+        assert oracle.induced_width(cnf, o) == wd
+    assert oracle.induced_width(wmcgen.chain_or(30), list(range(1, 31))) == 2
+    assert oracle.induced_width(wmcgen.Cnf(9, [list(range(1, 10))]), list(range(1, 10))) == 9
+    assert oracle.induced_width(wmcgen.grid_cnf(6, 10, 1), wmcgen.grid_column_order(6, 10)) == 8
+    assert oracle.bucket_elim(wmcgen.grid_cnf(6, 10, 1), *wmcgen.weights_unit(60),
+                              order=wmcgen.grid_column_order(6, 10), return_width=True)[1] == 8
 
 
 @pytest.mark.parametrize("seed", range(3))
