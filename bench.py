@@ -45,9 +45,26 @@ import wmcgen  # noqa: E402
 METRIC = "WMC queries/s and p50/p99 latency vs plain FP64 path; % of HBM roofline"
 GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
-# DRAM traffic / algorithmic bytes of the dominant kernel, from its ncu
-# capture (None once the kernel changes until it is captured again)
-TRAFFIC_PER_ALG_BYTE = 737.2e6 / 939.7e6
+# DRAM traffic / algorithmic bytes of the dominant kernel (k2_chain) over a
+# serving wave's mix of chains, from one ncu capture, and the SHA-256 of the
+# kernel source it was taken on: when the source differs, the ratio no
+# longer describes the kernel and `roofline.traffic` is null.
+TRAFFIC_CAPTURE = {"ratio": None, "kernels_cuh_sha256": None}
+
+
+def _kernel_source_sha256() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2006_15512_b300", "csrc", "kernels.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def traffic_ratio():
+    """(ratio or None, note)."""
+    if TRAFFIC_CAPTURE["ratio"] is None:
+        return None, "no ncu capture of the current kernel source"
+    if TRAFFIC_CAPTURE["kernels_cuh_sha256"] != _kernel_source_sha256():
+        return None, "kernel source changed since the ncu capture"
+    return TRAFFIC_CAPTURE["ratio"], "ncu capture of k2_chain on this kernel source (serving wave mix)"
 
 
 def wave_offset(step: int, rank: int, world: int, n_waves: int, Q: int) -> int:
@@ -150,21 +167,26 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
-def cpu_baseline(cnf, wq, wnq, budget_s=15.0):
-    """The oracle (bucket elimination, long double) per query on the host
-    cores, for as many pool queries as fit in budget_s (at least one)."""
+def cpu_baseline(cnf, wq, wnq, gpu_results, budget_s=15.0):
+    """The CPU baseline leg: the oracle (bucket elimination, long double)
+    per query on the host cores, for as many pool queries as fit in
+    budget_s (at least one); the same oracle values give the accuracy of
+    the GPU results for those queries (gpu_results: (mant, exp2) pairs of
+    the first pool queries)."""
     import oracle
+    from oracle import Big
     col = [i * GRID_W + j + 1 for j in range(GRID_W) for i in range(GRID_H)]
     vals = []
     t0 = time.perf_counter()
     i = 0
-    while i == 0 or (time.perf_counter() - t0 < budget_s and i < 64):
+    while i == 0 or (time.perf_counter() - t0 < budget_s and i < min(64, len(gpu_results))):
         vals.append(oracle.bucket_elim(cnf, wq[i], wnq[i], order=col))
         i += 1
     dt = time.perf_counter() - t0
-    return {"value": i / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{i} pool queries of the 16x100 grid, long-double bucket elimination, "
-                      f"{dt:.1f} s"}, vals
+    cpu = {"value": i / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{i} pool queries of the 16x100 grid, long-double bucket elimination, {dt:.1f} s"}
+    err = max(Big(*gpu_results[j]).rel_diff(vals[j]) for j in range(i))
+    return cpu, {"max_rel_err_vs_oracle": err, "n": i}
 
 
 def run_reference(args, rank, world):
@@ -192,10 +214,44 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def poisson_run(srv, wq, wnq, rate, n):
+    """n queries arriving as a Poisson stream at `rate` per second (seed 2),
+    open loop: every arrival that is due is submitted at once (one
+    wmc_submit_many call for all of them), so the client keeps up at high
+    rates.  Latency = server-stamped completion - scheduled arrival."""
+    arr = wmcgen.poisson_arrivals(n, rate, seed=2)
+    pool = wq.shape[0]
+    tickets = []
+    st0 = srv.stats()
+    t0 = time.monotonic()
+    j = 0
+    while j < n:
+        now = time.monotonic() - t0
+        if arr[j] > now:
+            time.sleep(min(arr[j] - now, 0.001))
+            continue
+        k = j
+        while k < n and arr[k] <= now:
+            k += 1
+        idx = np.arange(j, k) % pool
+        tickets += srv.submit_many(wq[idx], wnq[idx])
+        j = k
+    done = srv.collect_done_ns(tickets, timeout_s=600)
+    st = srv.stats()
+    lat_ms = np.array([(done[i] / 1e9 - (t0 + arr[i])) * 1e3 for i in range(n)])
+    span = max(done) / 1e9 - t0
+    served = n / span
+    waves = int(st.waves - st0.waves)
+    return {"rate_qps": rate, "n_queries": n, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+            "served_qps": served, "waves": waves,
+            "mean_wave_q": (st.completed - st0.completed) / max(waves, 1),
+            "saturated": bool(served < 0.95 * rate)}
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2006_15512_b300 as w
-    from oracle import Big
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
@@ -315,14 +371,16 @@ def run_ours(args, rank, world):
     sel = (k_kind == 1) | (k_kind == 4) | (k_kind == 8) | (k_kind == 9)
     walk_ms = float(k_ms.sum())
     achieved = float(k_bytes[sel].sum() / (k_ms[sel].sum() / 1e3) / 1e9) if sel.any() else 0.0
-    # DRAM bytes from one ncu capture of a full-size k2_chain launch (profiles/
-    # k2_chain_serving_grid16x100_q256.md: 737.5 MB for 939.7 MB algorithmic over
-    # a wave's mix of plain, growth and shrink chains),
-    # scaled to this run's average streaming launch by its algorithmic bytes
+    # DRAM bytes per launch: the traffic / algorithmic-bytes ratio of one ncu
+    # capture of the chain kernel over a wave's mix of plain, growth and
+    # shrink chains, scaled to this run's average streaming launch
     bpl = float(k_bytes[sel].mean()) if sel.any() else 0.0
-    traffic = TRAFFIC_PER_ALG_BYTE * bpl if TRAFFIC_PER_ALG_BYTE else None
+    ratio, traffic_note = traffic_ratio()
+    traffic = ratio * bpl if ratio else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                "frac": achieved / hbm, "traffic": traffic, "traffic_note": traffic_note,
+                "peak_source": src, "timing": "each streaming launch of one eager walk, CUDA events, "
+                                              "launches serialised (no overlap between waves)",
                 "kernel": "k2_chain / k2_tma / k2_stream (streaming contractions)",
                 "tma_launches": int((k_kind == 4).sum()),
                 "chain_launches": int((k_kind == 8).sum()),
@@ -352,45 +410,25 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     plain_qps = n_plain / (e0.elapsed_time(e1) / 1e3)
 
-    # ---- Poisson serving run (continuous batching)
-    latency = None
+    # ---- Poisson serving runs (continuous batching), one per arrival rate
+    latency_by_rate = []
     if args.rate > 0:
         srv = w.Server(plan, max_batch=Q, max_waves=args.waves)
         # warm every power-of-two wave size's graph
         for q in [1 << k for k in range(int(math.log2(Q)) + 1)]:
-            ts = [srv.submit(wq[j], wnq[j]) for j in range(q)]
-            for t in ts:
+            for t in srv.submit_many(wq[:q], wnq[:q]):
                 srv.wait(t)
-        arr = wmcgen.poisson_arrivals(args.n_queries, args.rate, seed=2)
-        tickets = []
-        t0 = time.monotonic()
-        for j in range(args.n_queries):
-            target = t0 + arr[j]
-            d = target - time.monotonic()
-            if d > 0:
-                time.sleep(d)
-            tickets.append(srv.submit(wq[j % POOL], wnq[j % POOL]))
-        st0 = srv.stats()
-        # completion times are stamped by the server (CLOCK_MONOTONIC), so
-        # collecting them late does not change them
-        done = srv.collect_done_ns(tickets, timeout_s=300)
-        st = srv.stats()
-        st.waves -= st0.waves * 0  # stats are cumulative incl. warm-up
+        for rate in args.rates:
+            latency_by_rate.append(poisson_run(srv, wq, wnq, rate, max(args.n_queries, int(rate * 0.5))))
         srv.close()
-        lat_ms = np.array([(done[j] / 1e9 - (t0 + arr[j])) * 1e3 for j in range(len(tickets))])
-        span = max(done) / 1e9 - t0
-        latency = {"rate_qps": args.rate, "n_queries": args.n_queries,
-                   "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                   "mean_ms": float(lat_ms.mean()), "served_qps": args.n_queries / span,
-                   "waves": int(st.waves), "mean_wave_q": float(st.mean_wave_q)}
-    # ---- accuracy on the sampled queries + CPU baseline
-    cpu, oracle_vals = (None, [])
+    latency = latency_by_rate[0] if latency_by_rate else None
+    # ---- CPU baseline leg (and, from its oracle values, the accuracy of
+    # the GPU results for the same pool queries)
+    cpu, accuracy = None, {"max_rel_err_vs_oracle": None, "n": 0}
     if world == 1 and not args.no_cpu_baseline:
-        cpu, oracle_vals = cpu_baseline(cnf, wq, wnq)
-    max_err = None
-    if oracle_vals:
         res = plan.execute(host_wp[:Q], host_wn[:Q])
-        max_err = max(Big(res[i].mant, res[i].exp2).rel_diff(oracle_vals[i]) for i in range(len(oracle_vals)))
+        cpu, accuracy = cpu_baseline(cnf, wq, wnq, [(r.mant, r.exp2) for r in res])
+    accuracy["stated_bound"] = e2e_res[0].rel_err_bound if e2e_res else None
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -399,9 +437,8 @@ def run_ours(args, rank, world):
             "clocks": clk.summary(),
             "plain_fp64": {"value": plain_qps, "unit": "queries/s", "queries": n_plain,
                            "speedup_of_batched": value / world / plain_qps},
-            "latency": latency,
-            "accuracy": {"max_rel_err_vs_oracle": max_err, "n": len(oracle_vals),
-                         "stated_bound": e2e_res[0].rel_err_bound if e2e_res else None},
+            "latency": latency, "latency_by_rate": latency_by_rate,
+            "accuracy": accuracy,
             "plan": {"max_rank": info.max_rank, "n_nodes": info.n_nodes,
                      "workspace_MiB": info.workspace_bytes / 2 ** 20,
                      "algorithmic_GB_per_wave": info.algorithmic_bytes / 1e9}}
@@ -409,8 +446,11 @@ def run_ours(args, rank, world):
     # per wave (two waves in flight overlap, so this is the rate the step
     # achieves, not a single kernel's)
     wave_gbs = info.algorithmic_bytes / (t_max / args.steps / 1e3) / 1e9
-    line["roofline"]["wave_alg_GBs"] = wave_gbs
-    line["roofline"]["wave_frac"] = wave_gbs / hbm
+    line["roofline"]["in_context"] = {
+        "what": "the whole step in the timed region: algorithmic bytes per wave / ms_per_step "
+                "(two waves in flight; the chain kernel is ~96% of a wave's device time)",
+        "alg_GB_per_step": info.algorithmic_bytes / 1e9, "ms_per_step": t_max / args.steps,
+        "achieved_GBs": wave_gbs, "frac": wave_gbs / hbm}
     print(json.dumps(line), flush=True)
 
 
@@ -424,18 +464,82 @@ def _timed(fn, reps):
     return (time.perf_counter() - t0) / reps
 
 
+def _rel_diff(m1, e1, m2, e2):
+    """|a - b| / |b| for a = m1 * 2^e1, b = m2 * 2^e2, without leaving the
+    float64 range."""
+    if m2 == 0:
+        return 0.0 if m1 == 0 else float("inf")
+    return abs(math.ldexp(m1, e1 - e2) - m2) / abs(m2)
+
+
+def cpu_baseline_random3cnf(cases, gpu_results):
+    """CPU baseline leg of the random 3-CNF config: the oracle's brute force
+    (Def. 2.1 over 2^20 assignments) per formula on the host cores; its
+    values also give the accuracy of the GPU results."""
+    import oracle
+    t0 = time.perf_counter()
+    vals = [oracle.brute_force(cnf, wp, wn)[0] for (cnf, wp, wn) in cases]
+    dt = time.perf_counter() - t0
+    err = max(_rel_diff(m, e, v.mant, v.exp2) for (m, e), v in zip(gpu_results, vals))
+    return {"value": len(cases) / dt, "unit": "formulas/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{len(cases)} formulas, brute force over 2^20 assignments"}, err
+
+
+def cpu_baseline_uneven(sample, gpu_results, budget_s=20.0):
+    """CPU baseline leg of the uneven batch: the oracle (bucket elimination,
+    long double, along the narrowest of its orders) on formulas of the batch
+    until budget_s is spent; its values also give the accuracy of the GPU
+    results for those formulas."""
+    import oracle
+    t0 = time.perf_counter()
+    errs, n = [], 0
+    for (kind, cnf, wp, wn), (m, e) in zip(sample, gpu_results):
+        if n and time.perf_counter() - t0 > budget_s:
+            break
+        orders = [oracle.min_degree_order(cnf), list(range(1, cnf.n_vars + 1))]
+        if kind.startswith("grid"):
+            h_, w_ = (int(v) for v in kind[4:].split("x"))
+            orders.append(wmcgen.grid_column_order(h_, w_))
+        order = min(orders, key=lambda o: oracle.induced_width(cnf, o))
+        v = oracle.bucket_elim(cnf, wp, wn, order=order, max_width=30)
+        errs.append(_rel_diff(m, e, v.mant, v.exp2))
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "formulas/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} formulas of the batch (every 16th), long-double bucket elimination, {dt:.1f} s"}, errs
+
+
+def plan_many(w, cands, precision, cap, count):
+    """Plans of the first `count` candidates whose plans fit max-rank `cap`,
+    planned on host threads (the planner releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    out, rejected = [], 0
+
+    def one(c):
+        try:
+            return w.Plan(w.Network.from_cnf(c[1], c[2], c[3]), precision=precision, max_rank_cap=cap)
+        except w._abi.WmcError:
+            return None
+    with ThreadPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2))) as ex:
+        while len(out) < count:
+            chunk = [next(cands) for _ in range(64)]
+            for c, p in zip(chunk, ex.map(one, chunk)):
+                if p is None:
+                    rejected += 1
+                elif len(out) < count:
+                    out.append((p, c))
+    return out, rejected
+
+
 def run_other(args):
     """Measurements of the non-headline configs (one JSON line each)."""
-    import ctypes
     import torch
     import paper_2006_15512_b300 as w
-    import oracle
-    from oracle import Big
     hbm, src = peaks()
     out = {"workload": args.workload}
     if args.workload == "random3cnf":
         # n=20, m=60 random 3-CNF, FP64, one query per call (latency)
-        lat, errs = [], []
+        lat, res, cases = [], [], []
         for seed in range(10):
             cnf = wmcgen.random_kcnf(20, 60, seed=seed)
             wp, wn = wmcgen.weights_complementary(20, seed, 0.1, 0.9)
@@ -443,14 +547,14 @@ def run_other(args):
             plan.execute()
             lat.append(_timed(lambda: plan.execute(), 20))
             r = plan.execute()[0]
-            errs.append(Big(r.mant, r.exp2).rel_diff(oracle.brute_force(cnf, wp, wn)[0]))
-        t0 = time.perf_counter()
-        oracle.brute_force(wmcgen.random_kcnf(20, 60, seed=0), *wmcgen.weights_complementary(20, 0, 0.1, 0.9))
+            res.append((r.mant, r.exp2))
+            cases.append((cnf, wp, wn))
+        cpu, err = cpu_baseline_random3cnf(cases, res)
         out.update({"metric": "latency per query (host buffers, FP64)", "p50_us": float(np.median(lat) * 1e6),
-                    "max_us": float(max(lat) * 1e6), "max_rel_err": float(max(errs)),
-                    "oracle_brute_force_s": time.perf_counter() - t0, "oracle_threads": oracle.num_threads()})
+                    "max_us": float(max(lat) * 1e6), "max_rel_err": err, "cpu_baseline": cpu})
     elif args.workload == "grid":
-        # 24x200 grid, one query, scaled FP32 and FP64
+        # 24x200 grid, one query, scaled FP32 and FP64; the reference value
+        # is the stored golden (written by the oracle's own script)
         with open(os.path.join(ROOT, "tests", "golden", "grid_24x200.json")) as f:
             g = json.load(f)["values"][0]
         cnf = wmcgen.grid_cnf(24, 200, g["seed"])
@@ -464,7 +568,7 @@ def run_other(args):
             r = plan.execute()[0]
             out[name] = {"ms": t * 1e3, "alg_GB": info.algorithmic_bytes / 1e9,
                          "frac_hbm": info.algorithmic_bytes / t / 1e9 / hbm,
-                         "rel_err": Big(r.mant, r.exp2).rel_diff(Big(g["mant"], g["exp2"])),
+                         "rel_err": _rel_diff(r.mant, r.exp2, g["mant"], g["exp2"]),
                          "log10": r.log10, "max_rank": info.max_rank, "stated_bound": r.rel_err_bound}
     elif args.workload == "sweep":
         rows = []
@@ -493,10 +597,11 @@ def run_other(args):
                    "fp64_ms": t64 * 1e3, "fp64_GBs": 8 * n_el / t64 / 1e9, "fp64_GFLOPs": flops / t64 / 1e9,
                    "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9}
             n_free_a, n_free_b = ra - b - k, rb - b - k
-            if n_free_a >= 7 and n_free_b >= 7 and k >= 4:
+            if n_free_a >= 7 and n_free_b >= 7 and 4 <= k <= 16:
                 # tensor-core path: three TF32 products per float32 product
                 row["fp32_kernel"] = "k4_tc (tcgen05, 3xTF32)"
-                row["tensor_frac_of_tf32_peak"] = 3 * flops / t32 / 1e12 / tf32[0]
+                row["tensor_frac_of_tf32_peak_3x_products"] = 3 * flops / t32 / 1e12 / tf32[0]
+                row["tensor_frac_of_tf32_peak_method_flops"] = flops / t32 / 1e12 / tf32[0]
                 row["tf32_peak_tflops"] = tf32[0]
                 row["tf32_peak_source"] = tf32[1]
             rows.append(row)
@@ -505,51 +610,128 @@ def run_other(args):
         out["rows"] = rows
         out["hbm_peak_GBs"] = hbm
     elif args.workload == "uneven":
-        plans, rejected, kinds = [], 0, {}
         t0 = time.perf_counter()
-        for kind, cnf, wp, wn, sub in wmcgen.uneven_candidates(3):
-            try:
-                plans.append((w.Plan(w.Network.from_cnf(cnf, wp, wn), precision=w.WMC_SCALED_FP32,
-                                     max_rank_cap=26), cnf, wp, wn, kind))
-                kinds[kind[:4]] = kinds.get(kind[:4], 0) + 1
-            except w._abi.WmcError:
-                rejected += 1
-            if len(plans) == args.n_formulas:
-                break
+        planned, rejected = plan_many(w, wmcgen.uneven_candidates(3), w.WMC_SCALED_FP32, 26, args.n_formulas)
         plan_s = time.perf_counter() - t0
-        batch = w.Batch([x[0] for x in plans])
+        kinds = {}
+        for _, c in planned:
+            kinds[c[0][:4]] = kinds.get(c[0][:4], 0) + 1
+        t0 = time.perf_counter()
+        batch = w.Batch([p for p, _ in planned])
+        create_s = time.perf_counter() - t0
         info = batch.info()
-        batch.execute()
-        t = _timed(lambda: batch.execute(), max(1, args.steps // 10))
+        for _ in range(max(1, args.warmup)):
+            batch.execute()
+        reps = max(1, args.steps // 5)
+        with Clocks(0) as clk:
+            t = _timed(lambda: batch.execute(), reps)
         res = batch.execute()
         # per-formula graph loop on the same formulas
-        for x in plans:
-            x[0].execute()
-        t_loop = _timed(lambda: [x[0].execute() for x in plans], 1)
-        errs = []
-        for i in range(len(plans)):
-            p, cnf, wp, wn, kind = plans[i]
-            if p.info(1).max_rank > 18 or len(errs) >= 12:
-                continue
-            order = None
-            if kind.startswith("grid"):
-                h_, w_ = (int(v) for v in kind[4:].split("x"))
-                order = wmcgen.grid_column_order(h_, w_)
-            try:
-                want = oracle.bucket_elim(cnf, wp, wn, order=order, max_width=22)
-            except RuntimeError:
-                continue
-            errs.append(Big(res[i].mant, res[i].exp2).rel_diff(want))
-        out.update({"metric": "formulas/s", "value": len(plans) / t, "persistent_ms": t * 1e3,
-                    "graph_loop_ms": t_loop * 1e3, "speedup_vs_graph_loop": t_loop / t,
-                    "formulas": len(plans), "rejected": rejected, "mix": kinds,
-                    "nodes": info.n_nodes, "tasks": info.n_tasks,
+        for p, _ in planned:
+            p.execute()
+        t_loop = _timed(lambda: [p.execute() for p, _ in planned], 1)
+        achieved = info.algorithmic_bytes / t / 1e9
+        sample = [(c[0], c[1], c[2], c[3]) for _, c in planned][::16]
+        gres = [(r.mant, r.exp2) for r in res][::16]
+        cpu, errs = (None, [])
+        if not args.no_cpu_baseline:
+            cpu, errs = cpu_baseline_uneven(sample, gres)
+        out.update({"metric": "formulas/s", "value": len(planned) / t, "unit": "formulas/s",
+                    "persistent_ms": t * 1e3, "graph_loop_ms": t_loop * 1e3, "speedup_vs_graph_loop": t_loop / t,
+                    "formulas": len(planned), "rejected": rejected, "mix": kinds,
+                    "nodes": info.n_nodes, "tasks": info.n_tasks, "grid": info.grid,
                     "workspace_GiB": info.workspace_bytes / 2 ** 30,
-                    "alg_GB": info.algorithmic_bytes / 1e9,
-                    "frac_hbm": info.algorithmic_bytes / t / 1e9 / hbm,
+                    "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                 "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                                 "kernel": "k6_persistent (one launch; timed with the batch graph's "
+                                           "clear, leaf and result kernels)",
+                                 "alg_bytes": "one pass per node: |A| + |B| + |C| over the batch's nodes",
+                                 "alg_GB": info.algorithmic_bytes / 1e9},
+                    "clocks": clk.summary(), "cpu_baseline": cpu,
                     "max_rel_err_sampled": max(errs) if errs else None, "sampled": len(errs),
-                    "planning_s": plan_s})
+                    "planning_s": plan_s, "batch_create_s": create_s})
+    elif args.workload == "sliced":
+        line = run_sliced(args, w)
+        if not line:  # ranks other than 0 print nothing
+            return
+        out.update(line)
     print(json.dumps(out), flush=True)
+
+
+SLICED_FORMULA = (56, 196, 4)   # random 3-CNF n, m, seed: no plan within rank 31 unsliced
+SLICED_RANK = 24
+
+
+def gather_shares(parts, dist, device):
+    """All-gathers every rank's per-query partial results (mant, exp2) and
+    returns them as [rank][query] pairs (one collective per array)."""
+    import torch
+    m = torch.tensor([r.mant for r in parts], dtype=torch.float64, device=device)
+    e = torch.tensor([r.exp2 for r in parts], dtype=torch.int64, device=device)
+    world = dist.get_world_size()
+    ms = [torch.empty_like(m) for _ in range(world)]
+    es = [torch.empty_like(e) for _ in range(world)]
+    dist.all_gather(ms, m)
+    dist.all_gather(es, e)
+    return [[(float(a), int(b)) for a, b in zip(mm.tolist(), ee.tolist())] for mm, ee in zip(ms, es)]
+
+
+def sliced_count(w, plan, wq, wnq, rank, world, dist, device):
+    """Index slicing across processes (Alg. 3, Thm 4.2): this rank runs the
+    walks of its contiguous share of the slice assignments
+    (wmc_execute_slices), the ranks all-gather their per-query partial sums,
+    and wmc_combine_results adds them.  Returns the per-query totals."""
+    n_slices = 1 << plan.info(1).n_slice_vars
+    lo, hi = w.slice_range(n_slices, rank, world)
+    parts = plan.execute_slices(lo, hi, wq, wnq)
+    if dist is None:
+        return parts
+    shares = gather_shares(parts, dist, device)
+    Q = len(parts)
+    return [w.combine_results([w.Result(m, e, 0.0, 0, 0.0) for (m, e) in (sh[q] for sh in shares)])
+            for q in range(Q)]
+
+
+def run_sliced(args, w):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    n, m, seed = SLICED_FORMULA
+    cnf = wmcgen.random_kcnf(n, m, seed=seed)
+    Q = 1
+    wq, wnq = wmcgen.query_weights(n, Q, seed=5, lo=0.05, hi=0.95)
+    plan = w.Plan(w.Network.from_cnf(cnf), precision=w.WMC_SCALED_FP32, slice_to_rank=SLICED_RANK)
+    info = plan.info(Q)
+    n_slices = 1 << info.n_slice_vars
+    for _ in range(max(1, args.warmup)):
+        sliced_count(w, plan, wq, wnq, rank, world, dist, dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Clocks(dev.index) as clk:
+        for _ in range(args.steps):
+            tot = sliced_count(w, plan, wq, wnq, rank, world, dist, dev)
+    dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    if rank != 0:
+        return {}
+    hbm, src = peaks()
+    walks_per_s = args.steps * n_slices / dt
+    alg = info.algorithmic_bytes * n_slices * args.steps / dt / 1e9
+    return {"metric": "sliced counts/s (index slicing across processes, Alg. 3)",
+            "value": args.steps / dt, "unit": "counts/s", "n_gpus": world,
+            "slice_walks_per_s": walks_per_s, "slices": n_slices, "slice_vars": info.n_slice_vars,
+            "max_rank": info.max_rank, "formula": f"random 3-CNF n={n} m={m} seed={seed}",
+            "collective": "all_gather of per-query (mant, exp2) partial sums, then wmc_combine_results",
+            "roofline": {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s", "frac": alg / hbm,
+                         "peak_source": src, "alg_bytes": "per slice walk: sum over nodes of |A|+|B|+|C|"},
+            "result": {"mant": tot[0].mant, "exp2": tot[0].exp2, "rel_err_bound": tot[0].rel_err_bound},
+            "clocks": clk.summary()}
 
 
 def main():
@@ -560,13 +742,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--Q", type=int, default=256)
     ap.add_argument("--slots", type=int, default=2, help="waves in flight (streams + workspaces)")
-    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--rate", type=float, default=2000.0,
+                    help="the arrival rate of the headline latency (first of --rates)")
+    ap.add_argument("--rates", type=lambda x: [float(v) for v in x.split(",")], default=None,
+                    help="arrival rates of the serving runs (queries/s, comma-separated)")
     ap.add_argument("--n-queries", type=int, default=4096)
     ap.add_argument("--waves", type=int, default=2)
     ap.add_argument("--plain-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="serving",
-                    choices=["serving", "random3cnf", "grid", "sweep", "uneven"])
+                    choices=["serving", "random3cnf", "grid", "sweep", "uneven", "sliced"])
     ap.add_argument("--n-formulas", type=int, default=512)
     ap.add_argument("--sweep-rows", type=lambda x: [tuple(int(v) for v in r.split(",")) for r in x.split(";")],
                     default=[(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)],
@@ -574,12 +759,16 @@ def main():
     ap.add_argument("--only-waves", action="store_true",
                     help="run the warm-up and timed waves only (profiling driver)")
     args = ap.parse_args()
+    if args.rates is None:
+        args.rates = [args.rate] + [r for r in (5000.0, 10000.0, 20000.0, 50000.0) if r != args.rate]
     if args.impl == "ours" and not args.only_waves:
         args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":
+        import torch
         import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -315,14 +315,27 @@ int wmc_to_scaled_fp32(const double *x, int64_t n, float *out,
  * receives how many.  All plans must share a precision.  Each formula is
  * evaluated with its network's default weights.  Execution: one graph of
  * four kernels -- clear, leaves, a persistent task-queue contraction kernel
- * (tasks = chunks of 2^14 outputs of one node; within a formula the nodes
- * run in post-order, across formulas and within a node concurrently; every
- * dependency wait is bounded at one second), and the results.
+ * (tasks = chunks of 2^15 outputs of one node -- for the frontier-times-
+ * bucket nodes that carry almost all bytes, 2^15 assignments of the
+ * frontier's indices, each thread reading the frontier's entries once and
+ * writing every output that differs only in the bucket tensor's own
+ * indices; within a formula the nodes
+ * run in post-order, across formulas and within a node concurrently; the
+ * task list is built by list scheduling, the formulas with the longest
+ * remaining chains first; every dependency wait is bounded at one second),
+ * and the results.
  * Errors: WMC_EINVAL, WMC_EPLAN_TOO_BIG (nothing fits), WMC_ENOMEM,
  * WMC_ECUDA, WMC_ETIMEOUT. */
 int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans,
                      int64_t mem_budget_bytes, wmc_batch_t **out,
                      int32_t *n_admitted);
+/* Task size and order of batches created after the call: chunk_log2 = log2
+ * of the outputs per task, or of the assignments u per task for nodes in
+ * stream mode (8..16; 0 = the default 15), order 0 = list
+ * scheduling by the formulas' remaining chains (default), 1 = round-robin
+ * over the formulas in post-order.  Results are the same bits either way
+ * (a node's outputs do not depend on how they are split into tasks). */
+void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order);
 typedef struct {
   int64_t n_formulas, n_nodes, n_tasks;
   int64_t workspace_bytes;

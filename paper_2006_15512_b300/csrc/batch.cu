@@ -8,14 +8,25 @@
 // node's tasks wait until the previous node of the same formula has
 // completed, which also keeps the arena's first-fit reuse safe), while the
 // tasks of one node and the nodes of different formulas run concurrently.
-// Tasks are listed round-robin across formulas in post-order, so a task's
-// dependency was always handed out earlier; only running blocks take tasks,
-// so every wait ends.  Each wait is also bounded by %globaltimer (one
-// second); on timeout the block records an error word and stops.
+//
+// Task order.  Each formula is a chain of nodes, so the batch's length is at
+// least its longest formula's chain.  The list is built on the host by list
+// scheduling (Algorithm 2's post-order within each formula): a simulation
+// of the resident blocks, with a cost model of each task, repeatedly gives
+// the next free block a task of the ready node whose formula has the most
+// estimated work left on its chain (its bottom level), so the long chains
+// start at once and never queue behind the short formulas' large nodes.  A
+// node enters the simulation only after its predecessor's tasks have
+// finished there, so a task's dependency always comes earlier in the list;
+// only running blocks take tasks, so every wait ends.  Each wait is also
+// bounded by %globaltimer (one second); on timeout the block records an
+// error word and stops.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <queue>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -40,10 +51,14 @@ struct BNode {
   int64_t flags;            // byte offset of the formula's flag word
   int32_t prev;             // node that must complete first (-1: none)
   int32_t n_tasks;
-  int32_t chunk_log2;       // outputs per task = 2^chunk_log2
+  int32_t chunk_log2;       // outputs per task = 2^chunk_log2 (<= 16)
   int32_t rC, k;
   int8_t ti, ta, to;        // element types: 0 float, 1 double
   int8_t vec4;              // float32, C's two lowest bits are A's, B has neither: 4 outputs per thread
+  int8_t stream;            // stream mode (below); chunk_log2 then counts u, not outputs
+  int8_t f;                 // stream mode: output bits absent from A ("S-free", <= 4)
+  int8_t rB;                // rank of B
+  int8_t pad0;
   int8_t posA[32], posB[32], sposA[24], sposB[24];
 };
 
@@ -90,136 +105,80 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t target)
 }
 
 // The node's per-byte lookup tables (they depend on the node alone, so they
-// are built before the previous node is waited for).
+// are built before the previous node is waited for, and kept while a block
+// takes consecutive tasks of one node).  A task covers 2^chunk_log2
+// consecutive outputs, at most 2^16: rows 0-1 map the task-local output
+// bits to A's offset, rows 2-3 to B's, rows 4/6/8 the summed bits 0-7,
+// 8-15, 16-23 to A's, rows 5/7/9 to B's; only the rows the node uses are
+// built.  Entry v of a row is the OR of the single-bit offsets of v's set
+// bits.
+constexpr int kLutRows = 10;
+
 __device__ __forceinline__ void batch_lut(const BNode &nd, uint32_t (*lut)[256]) {
-  // per-byte offset tables: rows 0-3 A, 4-7 B (output bits); 8-10 A, 11-13 B (summed bits).
-  // Entry v of a row is the OR over v's set bits of that bit's offset: the
-  // single-bit offsets first, then entries [2^b, 2^(b+1)) = entries [0, 2^b)
-  // OR bit b's offset, for b = 0..7
-  if (threadIdx.x < 14 * 8) {
-    const int row = threadIdx.x >> 3, bit = threadIdx.x & 7;
-    uint32_t o = 0;
-    if (row < 8) {
-      const int j = (row & 3) * 8 + bit;
-      const int8_t pos = row < 4 ? nd.posA[j] : nd.posB[j];
-      if (j < nd.rC && pos >= 0) o = 1u << pos;
+  const int lbits = nd.chunk_log2;          // task-local output bits
+  const int rows_out = lbits > 8 ? 2 : 1;
+  const int rows_sum = (nd.k + 7) >> 3;     // 0..3
+  for (int i = threadIdx.x; i < kLutRows * 256; i += blockDim.x) {
+    const int row = i >> 8, v = i & 255;
+    int base, nb;
+    const int8_t *pos;
+    if (row < 4) {
+      const int half = row & 1;
+      if (half >= rows_out) continue;  // (entry 0 is cleared below)
+      base = half * 8;
+      nb = min(8, lbits - base);
+      pos = (row < 2 ? nd.posA : nd.posB) + base;
     } else {
-      const int j = ((row - 8) % 3) * 8 + bit;
-      const int8_t pos = row < 11 ? nd.sposA[j] : nd.sposB[j];
-      if (j < nd.k && pos >= 0) o = 1u << pos;
+      const int grp = (row - 4) >> 1;
+      if (grp >= rows_sum) continue;
+      base = grp * 8;
+      nb = min(8, nd.k - base);
+      pos = ((row & 1) == 0 ? nd.sposA : nd.sposB) + base;
     }
-    lut[row][1 << bit] = o;  // the single-bit entries
-    if (bit == 0) lut[row][0] = 0u;
+    uint32_t o = 0;
+    for (int b = 0; b < nb; ++b)
+      if (((v >> b) & 1) && pos[b] >= 0) o |= 1u << pos[b];
+    lut[row][v] = o;
   }
-  __syncthreads();
-  for (int b = 1; b < 8; ++b) {
-    const int half = 1 << b;  // entries [half + 1, 2 half) from [1, half)
-    for (int i = threadIdx.x; i < 14 * (half - 1); i += blockDim.x) {
-      const int row = i / (half - 1), v = 1 + i % (half - 1);
-      lut[row][half + v] = lut[row][half] | lut[row][v];
+  // entry 0 of every row is read even where the row is unused (a zero
+  // high byte): it is 0
+  if (threadIdx.x < kLutRows) lut[threadIdx.x][0] = 0u;
+}
+
+// A's and B's offsets of a task's first output (its bits above the task's
+// local bits).
+__device__ __forceinline__ void batch_base(const BNode &nd, uint64_t o0, uint32_t &bA, uint32_t &bB) {
+  bA = 0; bB = 0;
+  for (int j = nd.chunk_log2; j < nd.rC; ++j)
+    if ((o0 >> j) & 1) {
+      if (nd.posA[j] >= 0) bA |= 1u << nd.posA[j];
+      if (nd.posB[j] >= 0) bB |= 1u << nd.posB[j];
     }
-    __syncthreads();
+}
+
+// C's exponent and the float32 flush test (as in the single-plan
+// kernels), from the operands' metadata alone, by one thread of a node's
+// first task, beside the outputs.
+template <typename TI>
+__device__ __forceinline__ void node_exponent(char *ws, const BNode &nd, unsigned long long ma,
+                                              unsigned long long mb) {
+  *(int64_t *)(ws + nd.ec) = ldcg((const int64_t *)(ws + nd.ea)) + dev::pow2_exp_of(ma, TI()) +
+                             ldcg((const int64_t *)(ws + nd.eb)) + dev::pow2_exp_of(mb, TI());
+  const unsigned long long na = ldcg((const unsigned long long *)(ws + nd.na));
+  const unsigned long long nb = ldcg((const unsigned long long *)(ws + nd.nb));
+  if (na != kNoMin && nb != kNoMin) {
+    const TI lo = (dev::from_bits<TI>(na) * dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI())) *
+                  (dev::from_bits<TI>(nb) * dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI()));
+    if (dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
   }
 }
 
-template <typename TI, typename TA, typename TO>
-__device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
-                         unsigned long long *red) {
-  char *ws = ba.ws;
-  const TI *A = (const TI *)(ws + nd.a);
-  const TI *B = (const TI *)(ws + nd.b);
-  TO *C = (TO *)(ws + nd.c);
-  const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
-  const unsigned long long mb = ldcg((const unsigned long long *)(ws + nd.xb));
-  const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI());
-  const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI());
-  if (chunk == 0 && threadIdx.x == 32) {
-    // C's exponent and the float32 flush test (as in the single-plan
-    // kernels), from the operands' metadata alone, beside the outputs
-    *(int64_t *)(ws + nd.ec) = ldcg((const int64_t *)(ws + nd.ea)) + dev::pow2_exp_of(ma, TI()) +
-                               ldcg((const int64_t *)(ws + nd.eb)) + dev::pow2_exp_of(mb, TI());
-    const unsigned long long na = ldcg((const unsigned long long *)(ws + nd.na));
-    const unsigned long long nb = ldcg((const unsigned long long *)(ws + nd.nb));
-    if (na != kNoMin && nb != kNoMin) {
-      const TI lo = (dev::from_bits<TI>(na) * dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI())) *
-                    (dev::from_bits<TI>(nb) * dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI()));
-      if (dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
-    }
-  }
-  const uint64_t o0 = (uint64_t)chunk << nd.chunk_log2;
-  const uint64_t o1 = o0 + (1ull << nd.chunk_log2);
-  const uint32_t ns = 1u << nd.k;
-  TO tmax = (TO)0;
-  unsigned long long tmin = kNoMin;
-  if constexpr (sizeof(TI) == 4 && sizeof(TA) == 4 && sizeof(TO) == 4) {
-    if (nd.vec4 && nd.k <= 8) {
-      // four consecutive outputs per thread: A's four values per summed
-      // term in one 16-byte load, one B value, the same sums in the same
-      // order as below
-      for (uint64_t o = o0 + 4 * threadIdx.x; o < o1; o += 4 * blockDim.x) {
-        const uint32_t oo = (uint32_t)o;
-        const uint32_t bA = lut[0][oo & 255] | lut[1][(oo >> 8) & 255] | lut[2][(oo >> 16) & 255] | lut[3][oo >> 24];
-        const uint32_t bB = lut[4][oo & 255] | lut[5][(oo >> 8) & 255] | lut[6][(oo >> 16) & 255] | lut[7][oo >> 24];
-        TA acc[4] = {(TA)0, (TA)0, (TA)0, (TA)0};
-        for (uint32_t s = 0; s < ns; ++s) {
-          const float4 a4 = __ldcg(reinterpret_cast<const float4 *>(A + (bA | lut[8][s])));
-          const TA b = (TA)ldcg(B + (bB | lut[11][s])) * sb;
-          acc[0] = dev::fma_t((TA)a4.x * sa, b, acc[0]);
-          acc[1] = dev::fma_t((TA)a4.y * sa, b, acc[1]);
-          acc[2] = dev::fma_t((TA)a4.z * sa, b, acc[2]);
-          acc[3] = dev::fma_t((TA)a4.w * sa, b, acc[3]);
-        }
-        *reinterpret_cast<float4 *>(C + o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const TO m = acc[e] < (TO)0 ? -acc[e] : acc[e];
-          tmax = m > tmax ? m : tmax;
-          if (m != (TO)0) {
-            const unsigned long long bits = dev::abs_bits(m);
-            tmin = bits < tmin ? bits : tmin;
-          }
-        }
-      }
-      goto reduce;
-    }
-  }
-  for (uint64_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
-    const uint32_t oo = (uint32_t)o;
-    const uint32_t bA = lut[0][oo & 255] | lut[1][(oo >> 8) & 255] | lut[2][(oo >> 16) & 255] | lut[3][oo >> 24];
-    const uint32_t bB = lut[4][oo & 255] | lut[5][(oo >> 8) & 255] | lut[6][(oo >> 16) & 255] | lut[7][oo >> 24];
-    TA acc = (TA)0;
-    if (nd.k <= 8) {
-      for (uint32_t s = 0; s < ns; ++s) {
-        const TA a = (TA)ldcg(A + (bA | lut[8][s])) * sa;
-        const TA b = (TA)ldcg(B + (bB | lut[11][s])) * sb;
-        acc = dev::fma_t(a, b, acc);
-      }
-    } else {
-      for (uint32_t hi = 0; hi < (ns >> 8); ++hi) {
-        const uint32_t hA = bA | lut[9][hi & 255] | lut[10][hi >> 8];
-        const uint32_t hB = bB | lut[12][hi & 255] | lut[13][hi >> 8];
-        TA part = (TA)0;
-        for (uint32_t lo = 0; lo < 256; ++lo) {
-          const TA a = (TA)ldcg(A + (hA | lut[8][lo])) * sa;
-          const TA b = (TA)ldcg(B + (hB | lut[11][lo])) * sb;
-          part = dev::fma_t(a, b, part);
-        }
-        acc += part;
-      }
-    }
-    const TO c = (TO)acc;
-    C[o] = c;
-    const TO m = c < (TO)0 ? -c : c;
-    tmax = m > tmax ? m : tmax;
-    if (m != (TO)0) {
-      const unsigned long long bits = dev::abs_bits(m);
-      tmin = bits < tmin ? bits : tmin;
-    }
-  }
-reduce:
-  // block reduction into red[0] (max) and red[1] (min): folded across each
-  // warp first (max and min are exact), one shared atomic per warp, then
-  // one global atomic each
+// Block reduction of the task's max |C| and min nonzero |C| into red[0]
+// (max) and red[1] (min): folded across each warp first (max and min are
+// exact), one shared atomic per warp, then one global atomic each.
+template <typename TO>
+__device__ __forceinline__ void task_maxmin(char *ws, const BNode &nd, TO tmax, unsigned long long tmin,
+                                            unsigned long long *red) {
   if (threadIdx.x == 0) { red[0] = 0; red[1] = kNoMin; }
   __syncthreads();
   unsigned long long bmax = tmax != (TO)0 ? dev::abs_bits(tmax) : 0ull, bmin = tmin;
@@ -240,10 +199,269 @@ reduce:
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k6_persistent(BatchArgs ba) {
-  __shared__ uint32_t lut[14][256];
+template <typename T>
+__device__ __forceinline__ void track_out(T c, T &tmax, unsigned long long &tmin) {
+  const T m = c < (T)0 ? -c : c;
+  tmax = m > tmax ? m : tmax;
+  if (m != (T)0) {
+    const unsigned long long bits = dev::abs_bits(m);
+    tmin = bits < tmin ? bits : tmin;
+  }
+}
+
+// ---- stream mode
+//
+// The frontier-times-bucket shape that carries almost all of a batch's
+// bytes: A = P holds every output index except f <= 4 "S-free" ones, B = S
+// has at most 8 indices, k <= 2 indices are summed.  A task owns 2^cl
+// consecutive assignments u of C's indices that A holds; a thread loads
+// A's 2^k entries of its u once and writes the 2^f outputs that differ
+// only in the S-free indices (so A and C cross memory once each, as in the
+// single-plan streaming kernels), with S staged in shared memory,
+// pre-scaled.  The summed terms are added as in the generic path (operands
+// scaled first, one fused multiply-add per term in ascending summed
+// assignment, from zero), so the results are the same bits.
+struct StreamGeom {
+  uint32_t lut[6][256];          // u-local bits 0-7 / 8-15 -> C, A, S offsets
+  uint32_t cv[16], sv[16];       // S-free assignment v -> C offset, S offset
+  uint32_t as[4], ss[4];         // summed assignment s -> A offset, S offset
+  uint32_t sl[4];                // u's two lowest bits -> S offset (vector path)
+  int8_t uc[32], ua[32], us[32]; // u bit -> C bit, A bit, S bit (-1: none)
+};
+constexpr int kSMaxS = 256;      // S entries staged (B rank <= 8)
+
+__device__ __forceinline__ void stream_geom(const BNode &nd, StreamGeom &g) {
+  if (threadIdx.x == 0) {
+    int nu = 0, nv = 0;
+    int8_t vc[4] = {0, 0, 0, 0}, vs[4] = {0, 0, 0, 0};
+    for (int j = 0; j < nd.rC; ++j) {
+      if (nd.posA[j] >= 0) { g.uc[nu] = (int8_t)j; g.ua[nu] = nd.posA[j]; g.us[nu] = nd.posB[j]; ++nu; }
+      else if (nv < 4) { vc[nv] = (int8_t)j; vs[nv] = nd.posB[j]; ++nv; }
+    }
+    for (int v = 0; v < 16; ++v) {
+      uint32_t c = 0, sv = 0;
+      for (int i = 0; i < nv; ++i)
+        if ((v >> i) & 1) { c |= 1u << vc[i]; if (vs[i] >= 0) sv |= 1u << vs[i]; }
+      g.cv[v] = c; g.sv[v] = sv;
+    }
+    for (int sidx = 0; sidx < 4; ++sidx) {
+      uint32_t a = 0, sb = 0;
+      for (int i = 0; i < nd.k; ++i)
+        if ((sidx >> i) & 1) {
+          if (nd.sposA[i] >= 0) a |= 1u << nd.sposA[i];
+          if (nd.sposB[i] >= 0) sb |= 1u << nd.sposB[i];
+        }
+      g.as[sidx] = a; g.ss[sidx] = sb;
+    }
+    for (int e = 0; e < 4; ++e) {
+      uint32_t o = 0;
+      for (int i = 0; i < 2 && i < nu; ++i)
+        if (((e >> i) & 1) && g.us[i] >= 0) o |= 1u << g.us[i];
+      g.sl[e] = o;
+    }
+  }
+  __syncthreads();
+  const int cl = nd.chunk_log2;
+  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
+    const int row = i >> 8, v = i & 255, base = (row & 1) * 8;
+    const int8_t *pos = row < 2 ? g.uc : (row < 4 ? g.ua : g.us);
+    uint32_t o = 0;
+    for (int b = 0; b < 8 && base + b < cl; ++b)
+      if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
+    g.lut[row][v] = o;
+  }
+}
+
+template <typename T, int NS>
+__device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, const StreamGeom &g, T *sS,
+                           unsigned long long *red) {
+  char *ws = ba.ws;
+  const T *A = (const T *)(ws + nd.a);
+  const T *B = (const T *)(ws + nd.b);
+  T *C = (T *)(ws + nd.c);
+  const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
+  const unsigned long long mb = ldcg((const unsigned long long *)(ws + nd.xb));
+  const T sa = dev::pow2_scale(dev::pow2_exp_of(ma, T()), T());
+  const T sb = dev::pow2_scale(dev::pow2_exp_of(mb, T()), T());
+  if (chunk == 0 && threadIdx.x == 32) node_exponent<T>(ws, nd, ma, mb);
+  for (int i = threadIdx.x; i < (1 << nd.rB); i += blockDim.x) sS[i] = ldcg(B + i) * sb;
+  // offsets of the task's first u (its bits above the task's local bits)
+  const uint32_t u0 = (uint32_t)chunk << nd.chunk_log2;
+  uint32_t bC = 0, bA = 0, bS = 0;
+  for (int i = nd.chunk_log2; i < nd.rC - nd.f; ++i)
+    if ((u0 >> i) & 1) {
+      bC |= 1u << g.uc[i];
+      bA |= 1u << g.ua[i];
+      if (g.us[i] >= 0) bS |= 1u << g.us[i];
+    }
+  __syncthreads();  // sS
+  const uint32_t n_loc = 1u << nd.chunk_log2;
+  const int nv = 1 << nd.f;  // NS = 2^k summed assignments
+  T tmax = (T)0;
+  unsigned long long tmin = kNoMin;
+  if constexpr (sizeof(T) == 4) {
+    if (nd.vec4) {
+      // four consecutive u per group (C's and A's two lowest bits), two
+      // groups per step with their loads issued first
+      for (uint32_t l0 = 8 * threadIdx.x; l0 < n_loc; l0 += 8 * blockDim.x) {
+        float4 a4[2][NS];
+        uint32_t cb[2], sbx[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint32_t l = l0 + 4 * q;
+          const uint32_t ab = bA | g.lut[2][l & 255] | g.lut[3][l >> 8];
+          cb[q] = bC | g.lut[0][l & 255] | g.lut[1][l >> 8];
+          sbx[q] = bS | g.lut[4][l & 255] | g.lut[5][l >> 8];
+#pragma unroll
+          for (int sidx = 0; sidx < NS; ++sidx)
+            a4[q][sidx] = __ldcg(reinterpret_cast<const float4 *>(A + (ab | g.as[sidx])));
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float a[NS][4];
+#pragma unroll
+          for (int sidx = 0; sidx < NS; ++sidx) {
+              a[sidx][0] = a4[q][sidx].x * sa; a[sidx][1] = a4[q][sidx].y * sa;
+              a[sidx][2] = a4[q][sidx].z * sa; a[sidx][3] = a4[q][sidx].w * sa;
+            }
+          for (int v = 0; v < nv; ++v) {
+            float out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const uint32_t so = sbx[q] | g.sl[e] | g.sv[v];
+              float acc = 0.0f;
+#pragma unroll
+              for (int sidx = 0; sidx < NS; ++sidx)
+                acc = dev::fma_t(a[sidx][e], sS[so | g.ss[sidx]], acc);
+              out[e] = acc;
+              track_out(acc, tmax, tmin);
+            }
+            *reinterpret_cast<float4 *>(C + (cb[q] | g.cv[v])) = make_float4(out[0], out[1], out[2], out[3]);
+          }
+        }
+      }
+      task_maxmin<T>(ws, nd, tmax, tmin, red);
+      return;
+    }
+  }
+  for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
+    const uint32_t ab = bA | g.lut[2][l & 255] | g.lut[3][l >> 8];
+    const uint32_t cb = bC | g.lut[0][l & 255] | g.lut[1][l >> 8];
+    const uint32_t sbx = bS | g.lut[4][l & 255] | g.lut[5][l >> 8];
+    T a[NS];
+#pragma unroll
+    for (int sidx = 0; sidx < NS; ++sidx) a[sidx] = ldcg(A + (ab | g.as[sidx])) * sa;
+    for (int v = 0; v < nv; ++v) {
+      T acc = (T)0;
+#pragma unroll
+      for (int sidx = 0; sidx < NS; ++sidx) acc = dev::fma_t(a[sidx], sS[sbx | g.sv[v] | g.ss[sidx]], acc);
+      C[cb | g.cv[v]] = acc;
+      track_out(acc, tmax, tmin);
+    }
+  }
+  task_maxmin<T>(ws, nd, tmax, tmin, red);
+}
+
+template <typename TI, typename TA, typename TO>
+__device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
+                         unsigned long long *red) {
+  char *ws = ba.ws;
+  const TI *A = (const TI *)(ws + nd.a);
+  const TI *B = (const TI *)(ws + nd.b);
+  TO *C = (TO *)(ws + nd.c);
+  const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
+  const unsigned long long mb = ldcg((const unsigned long long *)(ws + nd.xb));
+  const TA sa = (TA)dev::pow2_scale(dev::pow2_exp_of(ma, TI()), TI());
+  const TA sb = (TA)dev::pow2_scale(dev::pow2_exp_of(mb, TI()), TI());
+  if (chunk == 0 && threadIdx.x == 32) node_exponent<TI>(ws, nd, ma, mb);
+  const uint64_t o0 = (uint64_t)chunk << nd.chunk_log2;
+  const uint32_t n_loc = 1u << nd.chunk_log2;  // outputs of this task
+  uint32_t baseA, baseB;
+  batch_base(nd, o0, baseA, baseB);
+  const uint32_t ns = 1u << nd.k;
+  TO tmax = (TO)0;
+  unsigned long long tmin = kNoMin;
+  if constexpr (sizeof(TI) == 4 && sizeof(TA) == 4 && sizeof(TO) == 4) {
+    if (nd.vec4 && nd.k <= 8) {
+      // four consecutive outputs per thread: A's four values per summed
+      // term in one 16-byte load, one B value, the same sums in the same
+      // order as below
+      for (uint32_t l = 4 * threadIdx.x; l < n_loc; l += 4 * blockDim.x) {
+        const uint64_t o = o0 + l;
+        const uint32_t bA = baseA | lut[0][l & 255] | lut[1][l >> 8];
+        const uint32_t bB = baseB | lut[2][l & 255] | lut[3][l >> 8];
+        TA acc[4] = {(TA)0, (TA)0, (TA)0, (TA)0};
+        for (uint32_t s = 0; s < ns; ++s) {
+          const float4 a4 = __ldcg(reinterpret_cast<const float4 *>(A + (bA | lut[4][s])));
+          const TA b = (TA)ldcg(B + (bB | lut[5][s])) * sb;
+          acc[0] = dev::fma_t((TA)a4.x * sa, b, acc[0]);
+          acc[1] = dev::fma_t((TA)a4.y * sa, b, acc[1]);
+          acc[2] = dev::fma_t((TA)a4.z * sa, b, acc[2]);
+          acc[3] = dev::fma_t((TA)a4.w * sa, b, acc[3]);
+        }
+        *reinterpret_cast<float4 *>(C + o) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const TO m = acc[e] < (TO)0 ? -acc[e] : acc[e];
+          tmax = m > tmax ? m : tmax;
+          if (m != (TO)0) {
+            const unsigned long long bits = dev::abs_bits(m);
+            tmin = bits < tmin ? bits : tmin;
+          }
+        }
+      }
+      task_maxmin<TO>(ws, nd, tmax, tmin, red);
+      return;
+    }
+  }
+  for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
+    const uint64_t o = o0 + l;
+    const uint32_t bA = baseA | lut[0][l & 255] | lut[1][l >> 8];
+    const uint32_t bB = baseB | lut[2][l & 255] | lut[3][l >> 8];
+    TA acc = (TA)0;
+    if (nd.k <= 8) {
+      for (uint32_t s = 0; s < ns; ++s) {
+        const TA a = (TA)ldcg(A + (bA | lut[4][s])) * sa;
+        const TA b = (TA)ldcg(B + (bB | lut[5][s])) * sb;
+        acc = dev::fma_t(a, b, acc);
+      }
+    } else {
+      for (uint32_t hi = 0; hi < (ns >> 8); ++hi) {
+        const uint32_t hA = bA | lut[6][hi & 255] | lut[8][hi >> 8];
+        const uint32_t hB = bB | lut[7][hi & 255] | lut[9][hi >> 8];
+        TA part = (TA)0;
+        for (uint32_t lo = 0; lo < 256; ++lo) {
+          const TA a = (TA)ldcg(A + (hA | lut[4][lo])) * sa;
+          const TA b = (TA)ldcg(B + (hB | lut[5][lo])) * sb;
+          part = dev::fma_t(a, b, part);
+        }
+        acc += part;
+      }
+    }
+    const TO c = (TO)acc;
+    C[o] = c;
+    const TO m = c < (TO)0 ? -c : c;
+    tmax = m > tmax ? m : tmax;
+    if (m != (TO)0) {
+      const unsigned long long bits = dev::abs_bits(m);
+      tmin = bits < tmin ? bits : tmin;
+    }
+  }
+  task_maxmin<TO>(ws, nd, tmax, tmin, red);
+}
+
+constexpr size_t kTabBytes = sizeof(StreamGeom) > kLutRows * 256 * 4 ? sizeof(StreamGeom) : kLutRows * 256 * 4;
+
+__global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
+  // a node's tables: the generic path's lookup rows or the stream mode's
+  // geometry, and the stream mode's staged S
+  __shared__ __align__(16) unsigned char s_tab[kTabBytes];
+  __shared__ __align__(16) double s_S[kSMaxS];
+  uint32_t (*lut)[256] = reinterpret_cast<uint32_t (*)[256]>(s_tab);
+  StreamGeom &geom = *reinterpret_cast<StreamGeom *>(s_tab);
   __shared__ unsigned long long red[2];
   __shared__ int s_task, s_ok;
+  int lut_node = -1;  // node whose tables the block holds
   for (;;) {
     if (threadIdx.x == 0) s_task = (int)atomicAdd(ba.next, 1u);
     __syncthreads();
@@ -251,7 +469,11 @@ __global__ void __launch_bounds__(kThreads) k6_persistent(BatchArgs ba) {
     if (t >= ba.n_tasks) break;
     const BTask task = ba.tasks[t];
     const BNode &nd = ba.nodes[task.node];
-    batch_lut(nd, lut);  // overlaps the wait for the previous node
+    if (task.node != lut_node) {  // overlaps the wait for the previous node
+      if (nd.stream) stream_geom(nd, geom);
+      else batch_lut(nd, lut);
+      lut_node = task.node;
+    }
     if (threadIdx.x == 0) {
       bool ok = *(volatile uint32_t *)ba.err == 0;
       if (ok && nd.prev >= 0) ok = wait_count(ba.done + nd.prev, (uint32_t)ba.nodes[nd.prev].n_tasks);
@@ -261,7 +483,17 @@ __global__ void __launch_bounds__(kThreads) k6_persistent(BatchArgs ba) {
     }
     __syncthreads();
     if (!s_ok) break;
-    if (nd.ti == 1) run_task<double, double, double>(ba, nd, task.chunk, lut, red);
+    float *s_Sf = reinterpret_cast<float *>(s_S);
+    if (nd.stream && nd.ti == 1) {
+      if (nd.k == 0) run_stream<double, 1>(ba, nd, task.chunk, geom, s_S, red);
+      else if (nd.k == 1) run_stream<double, 2>(ba, nd, task.chunk, geom, s_S, red);
+      else run_stream<double, 4>(ba, nd, task.chunk, geom, s_S, red);
+    } else if (nd.stream) {
+      if (nd.k == 0) run_stream<float, 1>(ba, nd, task.chunk, geom, s_Sf, red);
+      else if (nd.k == 1) run_stream<float, 2>(ba, nd, task.chunk, geom, s_Sf, red);
+      else run_stream<float, 4>(ba, nd, task.chunk, geom, s_Sf, red);
+    }
+    else if (nd.ti == 1) run_task<double, double, double>(ba, nd, task.chunk, lut, red);
     else if (nd.to == 1) run_task<float, double, double>(ba, nd, task.chunk, lut, red);
     else if (nd.ta == 1) run_task<float, double, float>(ba, nd, task.chunk, lut, red);
     else run_task<float, float, float>(ba, nd, task.chunk, lut, red);
@@ -395,6 +627,95 @@ struct wmc_batch {
 
 static std::vector<int32_t> qlabels(const TensorInfo &t) { return t.labels; }  // Q = 1
 
+// Task size and order of batches created after wmc_set_batch_schedule.
+static std::atomic<int32_t> g_batch_chunk{15};  // log2 outputs (stream mode: u) per task
+static std::atomic<int32_t> g_batch_order{0};   // 0 list scheduling, 1 round-robin
+
+extern "C" void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order) {
+  g_batch_chunk.store(chunk_log2 <= 0 ? 15 : std::min(16, std::max(8, chunk_log2)));
+  g_batch_order.store(order == 1 ? 1 : 0);
+}
+
+namespace {
+
+// Estimated microseconds of one task (cost model of the list scheduling):
+// a fixed part (counter, tables, epilogue) and, per output, one store plus
+// 2^k loads of the operand holding the summed indices, at the rate one
+// block of the persistent kernel reaches on the large frontier nodes.
+double task_us(const BNode &n) {
+  const double el = n.ti ? 2.0 : 1.0;  // element size in float32 units
+  if (n.stream)  // 2^cl u: 2^k loads and 2^f stores each
+    return 2.0 + 0.0009 * el * std::ldexp(1.0, n.chunk_log2) * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
+  const double outputs = std::ldexp(1.0, n.chunk_log2);
+  return 2.0 + outputs * 0.00091 * el * (1.0 + std::ldexp(1.0, n.k));
+}
+
+// List scheduling of the formulas' node chains onto `slots` resident
+// blocks: whenever a simulated block frees, it takes the next task of the
+// ready node whose formula has the largest bottom level (the estimated time
+// of its remaining chain); a node becomes ready `dep_us` after the last of
+// its predecessor's tasks finishes.  Tasks are listed in the order they are
+// taken.
+void list_schedule(const std::vector<BNode> &nodes, const std::vector<std::vector<int32_t>> &chains,
+                   int32_t slots, double dep_us, std::vector<BTask> &tasks) {
+  const size_t F = chains.size();
+  std::vector<std::vector<double>> bottom(F);
+  for (size_t f = 0; f < F; ++f) {
+    const auto &c = chains[f];
+    bottom[f].assign(c.size(), 0.0);
+    double acc = 0.0;
+    for (size_t j = c.size(); j-- > 0;) {
+      acc += task_us(nodes[(size_t)c[j]]) + dep_us;
+      bottom[f][j] = acc;
+    }
+  }
+  std::vector<size_t> cur(F, 0);
+  std::vector<int32_t> left(F, 0);
+  std::vector<double> fin(F, 0.0);
+  typedef std::pair<double, int64_t> Item;  // (key, formula)
+  std::priority_queue<Item> ready;           // largest bottom level first
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> waiting;  // earliest ready time
+  std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+  for (int32_t i = 0; i < slots; ++i) free_at.push(0.0);
+  for (size_t f = 0; f < F; ++f)
+    if (!chains[f].empty()) {
+      left[f] = nodes[(size_t)chains[f][0]].n_tasks;
+      ready.push({bottom[f][0], (int64_t)f});
+    }
+  while (!ready.empty() || !waiting.empty()) {
+    double t = free_at.top();
+    free_at.pop();
+    while (!waiting.empty() && waiting.top().first <= t) {
+      const int64_t f = waiting.top().second;
+      waiting.pop();
+      ready.push({bottom[(size_t)f][cur[(size_t)f]], f});
+    }
+    if (ready.empty()) {  // the block idles until the earliest node is ready
+      t = std::max(t, waiting.top().first);
+      const int64_t f = waiting.top().second;
+      waiting.pop();
+      ready.push({bottom[(size_t)f][cur[(size_t)f]], f});
+    }
+    const size_t f = (size_t)ready.top().second;
+    const int32_t node = chains[f][cur[f]];
+    const BNode &n = nodes[(size_t)node];
+    const double end = t + task_us(n);
+    tasks.push_back({node, n.n_tasks - left[f]});
+    free_at.push(end);
+    fin[f] = std::max(fin[f], end);
+    if (--left[f] == 0) {
+      ready.pop();
+      if (++cur[f] < chains[f].size()) {
+        left[f] = nodes[(size_t)chains[f][cur[f]]].n_tasks;
+        waiting.push({fin[f] + dep_us, (int64_t)f});
+        fin[f] = 0.0;
+      }
+    }
+  }
+}
+
+}  // namespace
+
 extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64_t mem_budget_bytes,
                                 wmc_batch_t **out, int32_t *n_admitted) {
   if (!plans || !out || n_plans < 1) { set_error("bad argument"); return WMC_EINVAL; }
@@ -403,7 +724,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
   if (!b) { set_error("out of host memory"); return WMC_ENOMEM; }
   const int32_t prec = plan_of(plans[0]).precision;
   b->precision = prec;
-  constexpr int kChunkLog2 = 15;
+  const int32_t chunk_log2 = g_batch_chunk.load();
   int64_t off = 0;
   std::vector<std::vector<int32_t>> node_ids;  // per formula: global node ids in post-order
   for (int32_t f = 0; f < n_plans; ++f) {
@@ -459,12 +780,30 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
       k1_bitmaps(qlabels(plan.tensors[(size_t)nd.a]), qlabels(plan.tensors[(size_t)nd.b]),
                  qlabels(plan.tensors[(size_t)nd.c]), &n.rC, &n.k, n.posA, n.posB, n.sposA, n.sposB);
       if (n.k > 24 || n.rC > 31) { delete b; set_error("node too large for the batch executor"); return WMC_EPLAN_TOO_BIG; }
-      n.chunk_log2 = std::min<int32_t>(n.rC, kChunkLog2);
-      n.n_tasks = 1 << (n.rC - n.chunk_log2);
+      int32_t ra = (int32_t)plan.tensors[(size_t)nd.a].labels.size();
+      int32_t rb = (int32_t)plan.tensors[(size_t)nd.b].labels.size();
+      if (rb > ra) {  // A = the operand with more indices (the product commutes, term by term)
+        std::swap(n.a, n.b); std::swap(n.ea, n.eb); std::swap(n.xa, n.xb); std::swap(n.na, n.nb);
+        for (int j = 0; j < 32; ++j) std::swap(n.posA[j], n.posB[j]);
+        for (int j = 0; j < 24; ++j) std::swap(n.sposA[j], n.sposB[j]);
+        std::swap(ra, rb);
+      }
+      n.rB = (int8_t)rb;
       n.ti = prec == WMC_FP64 ? 1 : 0;
       n.to = (*lv.t_dbl)[(size_t)nd.c];
       n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
-      {
+      int32_t f = 0;
+      for (int j = 0; j < n.rC; ++j) f += n.posA[j] < 0;
+      n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && f <= 4) ? 1 : 0;
+      if (n.stream) {
+        // tasks over u, the assignments of C's indices that A holds
+        n.f = (int8_t)f;
+        n.chunk_log2 = std::min<int32_t>(n.rC - f, chunk_log2);
+        n.n_tasks = 1 << (n.rC - f - n.chunk_log2);
+        n.vec4 = (!n.ti && n.chunk_log2 >= 3 && n.rC >= 2 && n.posA[0] == 0 && n.posA[1] == 1) ? 1 : 0;
+      } else {
+        n.chunk_log2 = std::min<int32_t>(n.rC, chunk_log2);
+        n.n_tasks = 1 << (n.rC - n.chunk_log2);
         bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
                    n.posB[0] < 0 && n.posB[1] < 0;
         for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
@@ -484,15 +823,25 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
   }
   if (b->plans.empty()) { delete b; set_error("no formula fits the memory budget"); return WMC_EPLAN_TOO_BIG; }
   b->ws_bytes = off;
-  // tasks: round-robin over formulas, each formula in post-order
-  size_t longest = 0;
-  for (auto &v : node_ids) longest = std::max(longest, v.size());
-  for (size_t r = 0; r < longest; ++r)
-    for (auto &v : node_ids)
-      if (r < v.size()) {
-        const BNode &n = b->nodes[(size_t)v[r]];
-        for (int32_t c = 0; c < n.n_tasks; ++c) b->tasks.push_back({v[r], c});
-      }
+  // tasks: list scheduling onto the resident blocks (8 per SM on 148 SMs;
+  // the order stays valid for any block count), or round-robin over the
+  // formulas, each formula in post-order
+  int64_t n_tasks = 0;
+  for (const BNode &n : b->nodes) n_tasks += n.n_tasks;
+  if (n_tasks > INT32_MAX) { delete b; set_error("batch has more than 2^31 tasks"); return WMC_EPLAN_TOO_BIG; }
+  b->tasks.reserve((size_t)n_tasks);
+  if (g_batch_order.load() == 0) {
+    list_schedule(b->nodes, node_ids, 148 * 8, 2.0, b->tasks);
+  } else {
+    size_t longest = 0;
+    for (auto &v : node_ids) longest = std::max(longest, v.size());
+    for (size_t r = 0; r < longest; ++r)
+      for (auto &v : node_ids)
+        if (r < v.size()) {
+          const BNode &n = b->nodes[(size_t)v[r]];
+          for (int32_t c = 0; c < n.n_tasks; ++c) b->tasks.push_back({v[r], c});
+        }
+  }
   if (n_admitted) *n_admitted = (int32_t)b->plans.size();
   *out = b;
   return WMC_OK;

@@ -1,9 +1,11 @@
 // Continuous-batching WMC server over one compiled plan.
 //
 // Queries (weight vectors) arrive through wmc_submit.  A batcher thread
-// forms a wave from whatever is queued as soon as a wave slot is free: the
-// wave's Q is the next power of two >= the queued count (capped at
-// max_batch; padding lanes repeat the last query and are discarded).  Each
+// forms a wave from what is queued as soon as a wave slot is free: the
+// wave's Q is the next power of two >= the count it takes (capped at
+// max_batch; padding lanes repeat the last query and are discarded), and it
+// takes fewer queries, a power of two of them, rather than pad more than a
+// quarter of the lanes (wave_take).  Each
 // slot owns a stream and a workspace sized for max_batch, so admission is
 // by the plan's workspace bytes: the number of slots is what fits in
 // arena_bytes.  Waves on different slots overlap on the device.  A host
@@ -167,6 +169,23 @@ static void CUDART_CB on_wave_done(void *p) {
   delete arg;
 }
 
+// How many of the n queued queries the next wave takes.  A wave runs on a
+// power-of-two batch, so n queries fill Q = the next power of two >= n
+// lanes and the rest repeat the last query.  When that would leave more
+// than a quarter of the lanes as padding, the wave takes the largest power
+// of two <= n instead and the others wait for the next slot: under load
+// the queue is long and every lane does real work; when the queue is short
+// (n below 8) the wave takes everything, which keeps the latency of light
+// traffic at one walk.
+static size_t wave_take(size_t n, size_t max_b) {
+  if (n >= max_b) return max_b;
+  if (n < 8) return n;
+  size_t up = 1, down = 1;
+  while (up < n) up <<= 1;
+  while (down * 2 <= n) down <<= 1;
+  return (up - n) * 4 > up ? down : n;
+}
+
 static void batcher_loop(wmc_server *srv) {
   std::unique_lock<std::mutex> lk(srv->mu);
   const size_t max_b = (size_t)srv->opts.max_batch;
@@ -241,7 +260,8 @@ static void batcher_loop(wmc_server *srv) {
     if (si < 0 || srv->queue.empty()) continue;
     Slot &sl = srv->slots[(size_t)si];
     sl.wave.clear();
-    while (!srv->queue.empty() && sl.wave.size() < max_b) {
+    const size_t take = wave_take(srv->queue.size(), max_b);
+    while (sl.wave.size() < take) {
       sl.wave.push_back(std::move(srv->queue.front()));
       srv->queue.pop_front();
     }

@@ -513,6 +513,42 @@ def test_uneven_batch_with_chain_sized_formulas(w):
         assert Big(res[i].mant, res[i].exp2).rel_diff(Big(alone.mant, alone.exp2)) <= TOL[FP32], i
 
 
+def _narrow_order(cnf):
+    """The narrowest of the oracle's elimination orders for this formula:
+    min-degree, variable-id order (row by row on the generator's grids) and,
+    for formulas of up to 200 variables, min-fill."""
+    orders = [oracle.min_degree_order(cnf), list(range(1, cnf.n_vars + 1))]
+    if cnf.n_vars <= 200:
+        orders.append(oracle.min_fill_order(cnf))
+    return min(orders, key=lambda o: oracle.induced_width(cnf, o))
+
+
+def test_uneven_batch_schedules_give_the_same_bits(w):
+    """Task size and order change only how a node's outputs are split and
+    when they run: the results are the same bits (round-robin over 2^15-
+    output tasks, list scheduling over 2^13 and over 2^9), in both
+    precisions, and each equals the formula's own walk and the oracle."""
+    for precision in (FP32, FP64):
+        plans, cnfs, _ = _uneven(w, 16, precision, seed=9, n3=(20, 44), grid_w=(4, 12), grid_h=(10, 60))
+        got = []
+        try:
+            for chunk, order in ((15, 1), (13, 0), (9, 0)):
+                w.wmc_set_batch_schedule(chunk, order)
+                b = w.Batch(plans)
+                got.append([(r.mant, r.exp2, r.flags) for r in b.execute()])
+                del b
+        finally:
+            w.wmc_set_batch_schedule(0, 0)
+        assert got[0] == got[1] == got[2]
+        for i, (p, (cnf, wp, wn)) in enumerate(zip(plans, cnfs)):
+            alone = p.execute()[0]
+            assert Big(got[0][i][0], got[0][i][1]).rel_diff(Big(alone.mant, alone.exp2)) <= TOL[precision]
+            if i % 4 == 0:
+                want = oracle.bucket_elim(cnf, wp, wn, order=_narrow_order(cnf), max_width=30)
+                r = Big(got[1][i][0], got[1][i][1]).rel_diff(want)
+                assert r <= TOL[precision], (i, r)
+
+
 def test_uneven_batch_admission(w):
     """Admission by workspace bytes: only the prefix that fits is taken."""
     # the batch lays each formula out with one pass per node (no chains, no
