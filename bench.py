@@ -49,7 +49,8 @@ POOL = 4096
 # serving wave's mix of chains, from one ncu capture, and the SHA-256 of the
 # kernel source it was taken on: when the source differs, the ratio no
 # longer describes the kernel and `roofline.traffic` is null.
-TRAFFIC_CAPTURE = {"ratio": None, "kernels_cuh_sha256": None}
+TRAFFIC_CAPTURE = {"ratio": 738.3e6 / 939.7e6,
+                   "kernels_cuh_sha256": "d23de3bcc1f2868743f9f8bb9e589350c1fe33581abe770595b46d1f033f24fe"}
 
 
 def _kernel_source_sha256() -> str:
@@ -611,7 +612,8 @@ def run_other(args):
         out["hbm_peak_GBs"] = hbm
     elif args.workload == "uneven":
         t0 = time.perf_counter()
-        planned, rejected = plan_many(w, wmcgen.uneven_candidates(3), w.WMC_SCALED_FP32, 26, args.n_formulas)
+        planned, rejected = plan_many(w, wmcgen.uneven_candidates(3), w.WMC_SCALED_FP32, args.rank_cap,
+                                      args.n_formulas)
         plan_s = time.perf_counter() - t0
         kinds = {}
         for _, c in planned:
@@ -753,6 +755,7 @@ def main():
     ap.add_argument("--workload", default="serving",
                     choices=["serving", "random3cnf", "grid", "sweep", "uneven", "sliced"])
     ap.add_argument("--n-formulas", type=int, default=512)
+    ap.add_argument("--rank-cap", type=int, default=26, help="uneven batch: largest plan rank admitted")
     ap.add_argument("--sweep-rows", type=lambda x: [tuple(int(v) for v in r.split(",")) for r in x.split(";")],
                     default=[(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)],
                     help="sweep cases 'rank_a,rank_b,batch,summed;...'")

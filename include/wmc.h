@@ -361,7 +361,12 @@ typedef struct {
   int32_t max_batch;        /* largest Q of one wave (power of 2, <= 1024) */
   int32_t max_waves;        /* waves in flight at once (each its own stream
                                and workspace)                               */
-  int32_t reserved;
+  int32_t partial_overlap;  /* 0 (default): a wave of fewer than max_batch
+                               queries starts only when no wave is running,
+                               so under load the next wave grows while the
+                               current one runs; full waves start in any
+                               free slot.  1: any free slot starts a wave
+                               from whatever is queued                     */
   int64_t arena_bytes;      /* device memory for all wave workspaces; a wave
                                of Q queries is admitted only while its
                                workspace fits; 0 = max_waves * ws(max_batch) */
@@ -395,6 +400,7 @@ int wmc_wait(wmc_server_t *srv, uint64_t ticket, int64_t timeout_us,
 typedef struct {
   int64_t submitted, completed, waves, failed_waves;
   double mean_wave_q;
+  int64_t max_in_flight;    /* most waves that were on the device at once */
 } wmc_server_stats_t;
 int wmc_server_stats(wmc_server_t *srv, wmc_server_stats_t *out);
 void wmc_server_destroy(wmc_server_t *srv);

@@ -300,11 +300,12 @@ class Server:
     wmc_poll / wmc_wait)."""
 
     def __init__(self, plan: Plan, max_batch: int = 256, max_waves: int = 2,
-                 arena_bytes: int = 0, max_wave_wait_us: int = 0):
+                 arena_bytes: int = 0, max_wave_wait_us: int = 0, partial_overlap: int = 0):
         o = _abi.wmc_server_opts()
         o.precision = plan.precision
         o.max_batch = max_batch
         o.max_waves = max_waves
+        o.partial_overlap = partial_overlap
         o.arena_bytes = arena_bytes
         o.max_wave_wait_us = max_wave_wait_us
         h = ctypes.c_void_p()

@@ -79,7 +79,7 @@ class wmc_plan_info_t(ctypes.Structure):
 
 class wmc_server_opts(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("max_batch", c_i32), ("max_waves", c_i32),
-                ("reserved", c_i32), ("arena_bytes", c_i64), ("max_wave_wait_us", c_i64)]
+                ("partial_overlap", c_i32), ("arena_bytes", c_i64), ("max_wave_wait_us", c_i64)]
 
 
 class wmc_batch_info_t(ctypes.Structure):
@@ -90,7 +90,7 @@ class wmc_batch_info_t(ctypes.Structure):
 
 class wmc_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_i64), ("completed", c_i64), ("waves", c_i64),
-                ("failed_waves", c_i64), ("mean_wave_q", c_dbl)]
+                ("failed_waves", c_i64), ("mean_wave_q", c_dbl), ("max_in_flight", c_i64)]
 
 
 def _decl(name, restype, argtypes):

@@ -5,7 +5,10 @@
 // wave's Q is the next power of two >= the count it takes (capped at
 // max_batch; padding lanes repeat the last query and are discarded), and it
 // takes fewer queries, a power of two of them, rather than pad more than a
-// quarter of the lanes (wave_take).  Each
+// quarter of the lanes (wave_take).  A partial wave starts only when no
+// wave is running: while one runs, arrivals accumulate into the next, so
+// the wave size grows with the load; a full wave starts in any free slot
+// (throughput-bound serving overlaps full waves).  Each
 // slot owns a stream and a workspace sized for max_batch, so admission is
 // by the plan's workspace bytes: the number of slots is what fits in
 // arena_bytes.  Waves on different slots overlap on the device.  A host
@@ -190,10 +193,16 @@ static void batcher_loop(wmc_server *srv) {
   std::unique_lock<std::mutex> lk(srv->mu);
   const size_t max_b = (size_t)srv->opts.max_batch;
   for (;;) {
+    // a partial wave starts only on an idle device (or with
+    // partial_overlap): while a wave runs, the queue grows into the next
+    // one; a full wave starts in any free slot
+    auto may_start = [&] {
+      return srv->in_flight == 0 || srv->opts.partial_overlap || srv->queue.size() >= max_b;
+    };
     srv->cv_work.wait(lk, [&] {
       if (srv->stop) return true;
       for (auto &s : srv->slots)
-        if (!s.busy && (s.staged || !srv->queue.empty())) return true;
+        if (!s.busy && (s.staged || (!srv->queue.empty() && may_start()))) return true;
       if (srv->queue.size() >= max_b)
         for (auto &s : srv->slots)
           if (s.busy && !s.staged) return true;
@@ -215,6 +224,7 @@ static void batcher_loop(wmc_server *srv) {
       sl.status = WMC_OK;
       sl.launched_ns = mono_ns();
       srv->in_flight++;
+    srv->stats.max_in_flight = std::max<int64_t>(srv->stats.max_in_flight, srv->in_flight);
       lk.unlock();
       int rc = submit_wave(srv, sj);
       lk.lock();
@@ -257,7 +267,7 @@ static void batcher_loop(wmc_server *srv) {
     int si = -1;
     for (size_t i = 0; i < srv->slots.size(); ++i)
       if (!srv->slots[i].busy) { si = (int)i; break; }
-    if (si < 0 || srv->queue.empty()) continue;
+    if (si < 0 || srv->queue.empty() || !may_start()) continue;
     Slot &sl = srv->slots[(size_t)si];
     sl.wave.clear();
     const size_t take = wave_take(srv->queue.size(), max_b);
@@ -269,6 +279,7 @@ static void batcher_loop(wmc_server *srv) {
     sl.status = WMC_OK;
     sl.launched_ns = mono_ns();
     srv->in_flight++;
+    srv->stats.max_in_flight = std::max<int64_t>(srv->stats.max_in_flight, srv->in_flight);
     lk.unlock();
     int rc = launch_wave(srv, si);
     lk.lock();

@@ -405,6 +405,32 @@ def test_server_continuous_batching(w):
     srv.close()
 
 
+@pytest.mark.parametrize("partial_overlap", [0, 1])
+def test_server_waves_overlap_under_load(w, partial_overlap):
+    """A burst of four full waves: full waves run in both slots at once
+    (their work overlaps on the device) under either wave-start policy, and
+    every result equals the query run alone; trickling queries afterwards
+    are admitted into later waves."""
+    import time
+    cnf = wmcgen.grid_cnf(10, 60, 3)
+    plan = plan_for(w, cnf, None, None, FP32)
+    n = 4 * 32 + 24
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, n, seed=16, lo=0.05, hi=0.95)
+    alone = plan.execute(wq, wnq)
+    srv = w.Server(plan, max_batch=32, max_waves=2, partial_overlap=partial_overlap)
+    tickets = srv.submit_many(wq[:128], wnq[:128])
+    for i in range(128, n):
+        tickets.append(srv.submit(wq[i], wnq[i]))
+        time.sleep(0.0005)
+    for i, t in enumerate(tickets):
+        r = srv.wait(t, timeout_s=60)
+        assert (r.mant, r.exp2) == (alone[i].mant, alone[i].exp2), i
+    st = srv.stats()
+    assert st.completed == n and st.failed_waves == 0
+    assert st.max_in_flight == 2
+    srv.close()
+
+
 def test_server_submit_many_matches_single_submits(w):
     """A block of queries submitted in one call gets consecutive tickets and
     the same results as the queries submitted one by one (and run alone)."""
