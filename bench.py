@@ -263,6 +263,9 @@ def run_ours(args, rank, world):
     cnf, wq, wnq = workload()
     net = w.Network.from_cnf(cnf)
     plan = w.Plan(net, precision=w.WMC_SCALED_FP32)
+    # the walk's layout for this Q: the autotuner's pick (every layout gives
+    # the same bits)
+    tune = plan.autotune(Q, stream=torch.cuda.current_stream().cuda_stream) if not args.no_tune else None
     info = plan.info(Q)
     n = cnf.n_vars
     stream = torch.cuda.current_stream()
@@ -438,7 +441,7 @@ def run_ours(args, rank, world):
             "clocks": clk.summary(),
             "plain_fp64": {"value": plain_qps, "unit": "queries/s", "queries": n_plain,
                            "speedup_of_batched": value / world / plain_qps},
-            "latency": latency, "latency_by_rate": latency_by_rate,
+            "latency": latency, "latency_by_rate": latency_by_rate, "walk_autotune": tune,
             "accuracy": accuracy,
             "plan": {"max_rank": info.max_rank, "n_nodes": info.n_nodes,
                      "workspace_MiB": info.workspace_bytes / 2 ** 20,
@@ -592,11 +595,24 @@ def run_other(args):
                                           e[0:1], e[1:2], e[2:3])
             f32()
             t32 = _timed(f32, 3)
+            # the autotuner's pick (same bits): first call measures, then timed
+            w.wmc_set_autotune(1)
+            try:
+                f64(); t64_tuned = _timed(f64, 3)
+                f32(); t32_tuned = _timed(f32, 3)
+            finally:
+                w.wmc_set_autotune(0)
+            picks = {}
+            for name, prec in (("fp64", 0), ("fp32", 1)):
+                v, ch = w.pair_variants(prec, case.labels_a, case.labels_b, case.labels_c)
+                picks[name] = {"fixed": [w.PAIR_KINDS[v[0][0]], v[0][1]], "tuned": [w.PAIR_KINDS[v[ch][0]], v[ch][1]],
+                               "variants": len(v)}
             n_el = (1 << ra) + (1 << rb) + (1 << rc)
             flops = 2.0 * (1 << (rc + k))
             row = {"rank_a": ra, "rank_b": rb, "batch": b, "summed": k,
                    "fp64_ms": t64 * 1e3, "fp64_GBs": 8 * n_el / t64 / 1e9, "fp64_GFLOPs": flops / t64 / 1e9,
-                   "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9}
+                   "fp32_ms": t32 * 1e3, "fp32_GBs": 4 * n_el / t32 / 1e9, "fp32_GFLOPs": flops / t32 / 1e9,
+                   "fp64_tuned_ms": t64_tuned * 1e3, "fp32_tuned_ms": t32_tuned * 1e3, "kernels": picks}
             n_free_a, n_free_b = ra - b - k, rb - b - k
             if n_free_a >= 7 and n_free_b >= 7 and 4 <= k <= 16:
                 # tensor-core path: three TF32 products per float32 product
@@ -752,6 +768,7 @@ def main():
     ap.add_argument("--waves", type=int, default=2)
     ap.add_argument("--plain-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the fixed walk layout (no autotuning)")
     ap.add_argument("--workload", default="serving",
                     choices=["serving", "random3cnf", "grid", "sweep", "uneven", "sliced"])
     ap.add_argument("--n-formulas", type=int, default=512)

@@ -302,6 +302,34 @@ int wmc_contract_pair(int32_t precision, int32_t rank_a,
                       const int32_t *labels_c, void *c, const int64_t *exp_a,
                       const int64_t *exp_b, int64_t *exp_c, void *stream);
 
+/* Autotuning of wmc_contract_pair (default off): when on, the first call
+ * of each node shape (precision, the three label lists, whether c is
+ * 16-byte aligned) times every legal kernel variant that adds the summed
+ * terms in the canonical order -- the generic kernel, the streaming kernel
+ * at several block counts, the TMA-staged streaming kernel at one to three
+ * blocks per SM, the tiled and the outer-product dense kernels -- on the
+ * call's own buffers (one warm-up and three timed runs each, synchronising
+ * `stream`), and later calls of that shape use the fastest.  All these
+ * variants give the same bits, so tuning changes times only.  Shapes whose
+ * fixed rule picks a variant with another summation order (the tensor-core
+ * product, the split summed range) are not tuned.  The choices are kept
+ * for the life of the process (the matrix-multiplication view of Sec. 4.2:
+ * kernel and launch shape against the batch / summed / free split). */
+void wmc_set_autotune(int32_t on);
+/* The variants of a node shape (labels as for wmc_contract_pair; c_aligned16
+ * nonzero when C will be 16-byte aligned): *n receives their number, the
+ * first min(*n, max_n) are written to kinds / blocks (kind 0 generic, 1
+ * streaming, 2 TMA-staged streaming, 3 tiled dense, 4 outer-product dense,
+ * 5 tensor-core dense, 6 tiled dense with a split summed range; blocks 0 =
+ * the kernel's own count, else the block count (kind 1) or blocks per SM
+ * (kind 2)); the fixed rule's variant is listed first; *chosen is the index
+ * of the one wmc_contract_pair uses now (the tuned one once measured).
+ * Host only.  Errors: WMC_EINVAL. */
+int wmc_pair_variants(int32_t precision, int32_t rank_a, const int32_t *labels_a,
+                      int32_t rank_b, const int32_t *labels_b, int32_t rank_c,
+                      const int32_t *labels_c, int32_t c_aligned16, int32_t max_n,
+                      int32_t *kinds, int64_t *blocks, int32_t *n, int32_t *chosen);
+
 /* Converts a float64 device tensor of n elements to a scaled float32 one:
  * out = x * 2^-E rounded to float32 and exp_out[0] = E, with E chosen so
  * that max|out| lies in [1, 2).  Asynchronous on `stream`. */
@@ -422,6 +450,30 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                      float *node_ms, int32_t *kind, double *alg_bytes,
                      int64_t *n_launches);
 
+/* Autotuning of a plan's walk (the benchmark spec's tuner of kernel shape against
+ * the index split, at the level of the whole walk): for batch size Q, times
+ * the walk under up to eight layouts -- chains of up to 4, 3 or 2
+ * consecutive frontier eliminations per pass or none, the small-node phase
+ * on or off, runs of chains in one launch (float32) -- on the network's
+ * default weights (median of five walks after two warm-up walks, on
+ * `stream`, synchronously), checks that every layout returns the first
+ * one's values bit for bit (a layout that does not is rejected, ms = -1),
+ * and installs the fastest as the plan's layout for Q: later calls with
+ * this Q (wmc_execute, wmc_execute_device, servers created afterwards) use
+ * it, and wmc_plan_info(Q) reports its workspace and launch count.
+ * Allocates its own device buffers while it runs.  Call it before sharing
+ * the plan with other threads.  Errors: WMC_EINVAL, WMC_ENOMEM, WMC_ECUDA. */
+typedef struct {
+  int32_t n_candidates;    /* layouts timed (<= 8)                          */
+  int32_t chosen;          /* index of the installed one                    */
+  int32_t fuse[8];         /* longest chain per pass (0: one pass per node) */
+  int32_t small_phase[8];  /* small-node phase on (1) or off (0)            */
+  int32_t chain_runs[8];   /* runs of chains in one launch: max tiles (0: off) */
+  int32_t launches[8];     /* kernel launches per walk                      */
+  float ms[8];             /* median walk time; -1: rejected                */
+} wmc_tune_report;
+int wmc_autotune_plan(wmc_plan_t *plan, int32_t Q, void *stream, wmc_tune_report *out);
+
 /* Execution option: the longest run of consecutive frontier eliminations
  * contracted in one pass over the frontier tensor (k2_chain; the
  * intermediates never reach memory), 2..4; 0 or 1 turns fusion off;
@@ -482,6 +534,10 @@ int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_checked);
 const char *wmc_last_error(void);
 /* Number of kernels this library launched since load (for accounting). */
 int64_t wmc_kernel_launch_count(void);
+/* Test hook: wmc_contract_pair runs the variant (kind, blocks) of
+ * wmc_pair_variants (WMC_EINVAL if the node has no such variant); kind < 0
+ * turns the hook off. */
+void wmc_debug_force_pair_variant(int32_t kind, int64_t blocks);
 /* Test hook: make the next n device allocations fail with WMC_ENOMEM. */
 void wmc_debug_fail_next_allocs(int32_t n);
 /* Test hook: while on == 1, the walk's first launch that stages tiles with

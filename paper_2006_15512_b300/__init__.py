@@ -25,7 +25,7 @@ from ._abi import *  # noqa: F401,F403  (the C names)
 from ._abi import check, lib
 
 __all__ = ["Network", "Plan", "Server", "Batch", "Result", "contract_pair", "to_scaled_fp32",
-           "launch_count", "slice_range", "combine_results"] + list(_abi.EXPORTS)
+           "launch_count", "slice_range", "combine_results", "pair_variants", "PAIR_KINDS"] + list(_abi.EXPORTS)
 
 P = ctypes.POINTER
 
@@ -212,6 +212,18 @@ class Plan:
               "wmc_execute_slices")
         return [Result.from_c(out[i]) for i in range(Q)]
 
+    def autotune(self, Q: int, stream: int = 0) -> dict:
+        """wmc_autotune_plan: time the walk's layouts for batch size Q and
+        install the fastest; returns the report as a dict."""
+        rep = _abi.wmc_tune_report()
+        check(lib.wmc_autotune_plan(self.handle, int(Q), ctypes.c_void_p(stream), ctypes.byref(rep)),
+              "wmc_autotune_plan")
+        n = rep.n_candidates
+        return {"chosen": rep.chosen,
+                "layouts": [{"fuse": rep.fuse[i], "small_phase": rep.small_phase[i],
+                             "chain_runs": rep.chain_runs[i], "launches": rep.launches[i],
+                             "ms": rep.ms[i]} for i in range(n)]}
+
     def execute_device(self, Q: int, d_w_pos, d_w_neg, workspace, d_mant, d_exp2, d_flags,
                        stream: int = 0) -> None:
         """wmc_execute_device on torch tensors (or raw integer pointers)."""
@@ -252,6 +264,27 @@ def contract_pair(precision: int, labels_a, a, labels_b, b, labels_c, c,
                                 lc.size, _ptr(lc_, ctypes.c_int32), _dptr(c),
                                 _dptr(exp_a), _dptr(exp_b), _dptr(exp_c),
                                 ctypes.c_void_p(stream)), "wmc_contract_pair")
+
+
+PAIR_KINDS = {0: "k1_generic", 1: "k2_stream", 2: "k2_tma", 3: "k4_dense", 4: "k4_outer", 5: "k4_tc",
+              6: "k4_dense split"}
+
+
+def pair_variants(precision: int, labels_a, labels_b, labels_c, c_aligned16: bool = True):
+    """wmc_pair_variants: ([(kind, blocks)], index of the current choice)."""
+    la = np.ascontiguousarray(labels_a, dtype=np.int32)
+    lb = np.ascontiguousarray(labels_b, dtype=np.int32)
+    lc = np.ascontiguousarray(labels_c, dtype=np.int32)
+    pad = lambda x: x if x.size else np.zeros(1, dtype=np.int32)
+    la_, lb_, lc_ = pad(la), pad(lb), pad(lc)
+    kinds = (ctypes.c_int32 * 32)()
+    blocks = (ctypes.c_int64 * 32)()
+    n = ctypes.c_int32(); chosen = ctypes.c_int32()
+    check(lib.wmc_pair_variants(int(precision), la.size, _ptr(la_, ctypes.c_int32), lb.size,
+                                _ptr(lb_, ctypes.c_int32), lc.size, _ptr(lc_, ctypes.c_int32),
+                                int(bool(c_aligned16)), 32, kinds, blocks, ctypes.byref(n),
+                                ctypes.byref(chosen)), "wmc_pair_variants")
+    return [(int(kinds[i]), int(blocks[i])) for i in range(min(n.value, 32))], int(chosen.value)
 
 
 def to_scaled_fp32(x, out, exp_out, stream: int = 0) -> None:

@@ -88,6 +88,11 @@ class wmc_batch_info_t(ctypes.Structure):
                 ("grid", c_i32)]
 
 
+class wmc_tune_report(ctypes.Structure):
+    _fields_ = [("n_candidates", c_i32), ("chosen", c_i32), ("fuse", c_i32 * 8), ("small_phase", c_i32 * 8),
+                ("chain_runs", c_i32 * 8), ("launches", c_i32 * 8), ("ms", ctypes.c_float * 8)]
+
+
 class wmc_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_i64), ("completed", c_i64), ("waves", c_i64),
                 ("failed_waves", c_i64), ("mean_wave_q", c_dbl), ("max_in_flight", c_i64)]
@@ -118,6 +123,11 @@ EXPORTS = {
     "wmc_contract_pair": (c_i32, [c_i32, c_i32, P(c_i32), c_vp, c_i32, P(c_i32), c_vp, c_i32,
                                   P(c_i32), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wmc_to_scaled_fp32": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "wmc_set_autotune": (None, [c_i32]),
+    "wmc_autotune_plan": (c_i32, [c_vp, c_i32, c_vp, P(wmc_tune_report)]),
+    "wmc_pair_variants": (c_i32, [c_i32, c_i32, P(c_i32), c_i32, P(c_i32), c_i32, P(c_i32), c_i32, c_i32,
+                                  P(c_i32), P(c_i64), P(c_i32), P(c_i32)]),
+    "wmc_debug_force_pair_variant": (None, [c_i32, c_i64]),
     "wmc_batch_create": (c_i32, [P(c_vp), c_i32, c_i64, P(c_vp), P(c_i32)]),
     "wmc_batch_info": (c_i32, [c_vp, P(wmc_batch_info_t)]),
     "wmc_batch_execute": (c_i32, [c_vp, c_vp, P(wmc_result)]),

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <string>
 #include <cstdio>
 #include <cstdlib>
 
@@ -44,6 +45,9 @@ static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run 
 // execute as one k2_chain_seq launch (0, the default: every chain its own
 // launch, which measured faster at every batch size on the grid walks)
 static std::atomic<int32_t> g_chain_runs{0};
+static std::atomic<int32_t> g_autotune{0};  // wmc_contract_pair: time same-order variants per shape
+static std::atomic<int32_t> g_force_kind{-1};  // test hook: force one variant (-1: off)
+static std::atomic<int64_t> g_force_blocks{0};
 
 extern "C" int64_t wmc_kernel_launch_count(void) { return g_launches.load(); }
 extern "C" void wmc_debug_fail_next_allocs(int32_t n) { g_fail_allocs.store(n); }
@@ -125,7 +129,16 @@ namespace wmc {
 
 static std::atomic<uint64_t> g_state_serial{0};
 
+// Walk options of one execution state (the process-wide defaults come from
+// the wmc_set_* calls; the plan tuner builds states with others).
+struct WalkOpts {
+  int32_t fuse = 4;         // longest chain of frontier eliminations per pass (0 or 1: none)
+  int32_t small_phase = 1;  // small-node phase
+  int32_t chain_runs = 0;   // runs of chains in one launch: max tiles (0: off)
+};
+
 struct ExecState {
+  WalkOpts wo;
   uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
   int32_t Qp = 1;  // Q padded to 2^m: the query index is m bits
@@ -742,8 +755,18 @@ int64_t grid_for(uint64_t work) {
 
 }  // namespace
 
+static WalkOpts walk_opts_now() {
+  WalkOpts wo;
+  wo.fuse = g_fuse.load();
+  wo.small_phase = g_small_phase.load();
+  wo.chain_runs = g_chain_runs.load();
+  return wo;
+}
+
 // Builds the host-side layout for batch size Q (no device work).
-static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, bool force_f64 = false) {
+static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, bool force_f64 = false,
+                      const WalkOpts *wo = nullptr) {
+  st.wo = wo ? *wo : walk_opts_now();
   st.Q = Q;
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
@@ -790,7 +813,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   // at most 2^8 summed terms)
   std::vector<int32_t> sp_index(plan.nodes.size(), -1);
   std::vector<int64_t> sp_nodes;
-  if (g_small_phase.load() && !plain) {
+  if (st.wo.small_phase && !plain) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       const Node &nd = plan.nodes[ni];
       const TensorInfo &C = plan.tensors[(size_t)nd.c];
@@ -905,7 +928,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     }
     std::vector<int64_t> fuse_next(plan.nodes.size(), -1);
     std::vector<uint8_t> absorbed(plan.nodes.size(), 0);
-    const int fuse_level = plain ? 0 : g_fuse.load();
+    const int fuse_level = plain ? 0 : st.wo.fuse;
     // frontier steps: one summed index; f added ones (1 in place, 2 growth,
     // 0 shrink); a chain starts with f >= 1 and ends at its first f = 0
     auto frontier_f = [&](const Launch &l) { return (l.kind == L_K2T && l.k2.k == 1) ? l.k2.f : -1; };
@@ -1126,13 +1149,13 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   }
   // runs of consecutive chains with small tile counts: one k2_chain_seq
   // launch each (float32, four eliminations, contiguous lanes)
-  if (g_chain_runs.load() > 0 && !st.f64) {
+  if (st.wo.chain_runs > 0 && !st.f64) {
     auto eligible = [&](const Launch &l) {
       if (l.kind != L_K2C || l.ti != TF || l.chain_d != 4 || !l.chain_fast || (l.v != 1 && l.v != 2)) return false;
       for (int i = 0; i < l.chain_d; ++i)
         if (l.v > 1 && l.k2c.b_vec[i] != 1) return false;
       const int64_t tiles = int64_t(1) << (l.k2c.log2_nu + l.k2c.vbits - l.k2c.tb);
-      return tiles <= (int64_t)g_chain_runs.load();
+      return tiles <= (int64_t)st.wo.chain_runs;
     };
     std::vector<Launch> out;
     int64_t n_seq_chains = 0;
@@ -1635,6 +1658,130 @@ static int run_device(Plan &plan, ExecState &st, const double *d_wp, const doubl
   return WMC_OK;
 }
 
+// ------------------------------------------------------ walk autotuning
+//
+// For one plan and batch size, times the walk under several layouts --
+// chains of up to 4, 3 or 2 frontier eliminations per pass or none, the
+// small-node phase on or off, runs of chains in one launch -- and installs
+// the fastest as the plan's state for that Q.  Every layout adds each
+// node's terms in the canonical order and differs from the others only by
+// power-of-two scales, so all give the same bits; a layout whose results
+// differ from the first one's is rejected.
+extern "C" int wmc_autotune_plan(wmc_plan_t *cplan, int32_t Q, void *stream, wmc_tune_report *rep) {
+  if (!cplan || !rep) { set_error("NULL argument"); return WMC_EINVAL; }
+  if (check_q(Q)) return WMC_EINVAL;
+  Plan &plan = *cplan;
+  std::memset(rep, 0, sizeof(*rep));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = plan.precision == WMC_FP64;
+  std::vector<WalkOpts> cands;
+  auto add = [&](int fuse, int sp, int runs) {
+    WalkOpts w; w.fuse = fuse; w.small_phase = sp; w.chain_runs = runs;
+    cands.push_back(w);
+  };
+  add(4, 1, 0); add(3, 1, 0); add(2, 1, 0); add(0, 1, 0); add(4, 0, 0);
+  if (!f64) add(4, 1, 512);
+  // inputs: the network's default weights for every query
+  const size_t nv = (size_t)plan.n_vars;
+  std::vector<double> hw(2 * (size_t)Q * std::max<size_t>(nv, 1), 1.0);
+  for (int32_t q = 0; q < Q; ++q)
+    for (size_t v = 0; v < nv; ++v) {
+      hw[(size_t)q * nv + v] = plan.w_pos[v];
+      hw[(size_t)Q * nv + (size_t)q * nv + v] = plan.w_neg[v];
+    }
+  char *dbuf = nullptr;
+  const size_t w_bytes = sizeof(double) * hw.size();
+  const size_t o_out = (w_bytes + 255) / 256 * 256;
+  int rc = device_alloc((void **)&dbuf, o_out + (size_t)Q * (8 + 8 + 4) + 64);
+  if (rc) return rc;
+  const double *d_wp = (const double *)dbuf, *d_wn = d_wp + (size_t)Q * nv;
+  double *d_mant = (double *)(dbuf + o_out);
+  int64_t *d_exp = (int64_t *)(d_mant + Q);
+  uint32_t *d_flags = (uint32_t *)(d_exp + Q);
+  std::vector<std::unique_ptr<ExecState>> states;
+  std::vector<double> ref_m;
+  std::vector<int64_t> ref_e;
+  std::vector<uint32_t> ref_f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto fail = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(dbuf);
+    return code;
+  };
+  if (cudaMemcpyAsync(dbuf, hw.data(), w_bytes, cudaMemcpyHostToDevice, s) || cudaEventCreate(&e0) ||
+      cudaEventCreate(&e1)) {
+    set_error("autotune set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(WMC_ECUDA);
+  }
+  int best = -1;
+  for (size_t i = 0; i < cands.size() && i < 8; ++i) {
+    std::unique_ptr<ExecState> st(new (std::nothrow) ExecState());
+    if (!st) { set_error("out of host memory"); return fail(WMC_ENOMEM); }
+    if ((rc = build_exec(plan, Q, *st, false, false, &cands[i]))) return fail(rc);
+    if ((rc = ensure_dev(*st))) return fail(rc);
+    char *ws = nullptr;
+    if ((rc = device_alloc((void **)&ws, (size_t)st->ws_bytes))) return fail(rc);
+    std::vector<float> times;
+    for (int r = 0; r < 7 && rc == WMC_OK; ++r) {
+      cudaEventRecord(e0, s);
+      rc = run_device(plan, *st, d_wp, d_wn, ws, d_mant, d_exp, d_flags, s);
+      cudaEventRecord(e1, s);
+      if (!rc && cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("autotune walk failed: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = WMC_ECUDA;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r >= 2) times.push_back(ms);  // two warm-up walks (graph capture)
+    }
+    std::vector<double> m((size_t)Q);
+    std::vector<int64_t> ex((size_t)Q);
+    std::vector<uint32_t> fl((size_t)Q);
+    if (!rc && (cudaMemcpy(m.data(), d_mant, 8 * (size_t)Q, cudaMemcpyDeviceToHost) ||
+                cudaMemcpy(ex.data(), d_exp, 8 * (size_t)Q, cudaMemcpyDeviceToHost) ||
+                cudaMemcpy(fl.data(), d_flags, 4 * (size_t)Q, cudaMemcpyDeviceToHost))) {
+      set_error("autotune read-back failed");
+      rc = WMC_ECUDA;
+    }
+    cudaFree(ws);
+    if (rc) return fail(rc);
+    std::sort(times.begin(), times.end());
+    float med = times[times.size() / 2];
+    if (i == 0) { ref_m = m; ref_e = ex; ref_f = fl; }
+    else {
+      // compare values as mant * 2^exp (the unnormalised mantissas of two
+      // layouts may differ by powers of two)
+      for (int32_t q = 0; q < Q && med >= 0; ++q) {
+        int fa = 0, fb = 0;
+        const double ma = std::frexp(m[(size_t)q], &fa), mb = std::frexp(ref_m[(size_t)q], &fb);
+        const bool same = ma == mb && (ma == 0.0 || ex[(size_t)q] + fa == ref_e[(size_t)q] + fb) &&
+                          fl[(size_t)q] == ref_f[(size_t)q];
+        if (!same) med = -1.0f;
+      }
+    }
+    rep->fuse[i] = cands[i].fuse;
+    rep->small_phase[i] = cands[i].small_phase;
+    rep->chain_runs[i] = cands[i].chain_runs;
+    rep->launches[i] = (int32_t)st->kernels_per_run;
+    rep->ms[i] = med;
+    rep->n_candidates = (int32_t)i + 1;
+    if (med >= 0 && (best < 0 || med < rep->ms[best])) best = (int)i;
+    states.push_back(std::move(st));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(dbuf);
+  if (best < 0) { set_error("no layout could be timed"); return WMC_ECUDA; }
+  rep->chosen = best;
+  std::lock_guard<std::mutex> lk(plan.exec_mu);
+  auto it = plan.exec.find(Q);
+  if (it != plan.exec.end()) plan.retired.push_back(std::move(it->second));  // may still be in use
+  plan.exec[Q] = std::move(states[(size_t)best]);
+  return WMC_OK;
+}
+
 static void fill_result(const ExecState &st, double mant, int64_t e,
                         uint32_t flags, bool unit, bool negative, wmc_result *r) {
   int fe = 0;
@@ -2075,6 +2222,307 @@ cudaError_t launch_k4_tc(const dev::K4Params &p4, cudaStream_t s) {
 }  // namespace
 
 
+// ------------------------------------------------- pairwise contraction
+//
+// wmc_contract_pair picks one of several kernels for a node.  The fixed
+// rule (pair_default) follows the node's shape; with autotuning on
+// (wmc_set_autotune), the first call of each shape times every legal
+// variant that adds the summed terms in the canonical order (so all give
+// the same bits: k1_generic, the streaming kernels at several block counts,
+// the TMA-staged streaming kernel at 1..3 blocks per SM, the tiled and the
+// outer-product dense kernels) on the call's own buffers and keeps the
+// fastest for later calls of that shape.  Variants with another order (the
+// tensor-core product, the split summed range) are never swapped in or out.
+
+namespace {
+
+enum PairKind { PK_K1 = 0, PK_K2 = 1, PK_K2T = 2, PK_K4D = 3, PK_K4O = 4, PK_K4TC = 5, PK_K4SPLIT = 6 };
+
+struct PairChoice {
+  int kind = PK_K1;
+  int64_t blocks = 0;  // 0: the kernel's own block count
+};
+
+struct PairSetup {
+  bool f64 = false;
+  const void *a = nullptr, *b = nullptr;
+  void *c = nullptr;
+  const int64_t *exp_a = nullptr, *exp_b = nullptr;
+  int64_t *exp_c = nullptr;
+  std::vector<int32_t> LA, LB, LC;
+  // streaming form: P (the larger operand, else the other) keeps its order
+  bool k2 = false, use_a = true;
+  K2Params p2;
+  int vmax = 1, kmax = 1, fmax = 1;
+  bool k2t = false;
+  wmc::dev::K2TParams k2tp;
+  size_t k2t_smem = 0;
+  int k2t_per_sm = 1;
+  uint64_t k2t_tiles = 0;
+  // dense form
+  bool k4 = false;
+  wmc::dev::K4Params p4;
+  int64_t outer_blocks = 0;
+  int split_g = 0;
+  int32_t k1_k = 0;
+};
+
+void pair_setup(PairSetup &ps) {
+  const bool a_first = ps.LA.size() >= ps.LB.size();
+  for (int attempt = 0; attempt < 2 && !ps.k2; ++attempt) {
+    ps.use_a = (attempt == 0) == a_first;
+    ps.k2 = try_k2(ps.use_a ? ps.LA : ps.LB, ps.use_a ? ps.LB : ps.LA, ps.LC, ps.f64, ps.p2, ps.vmax, ps.kmax,
+                   ps.fmax);
+  }
+  dev::Meta ma{ps.exp_a, nullptr, nullptr, 0}, mb{ps.exp_b, nullptr, nullptr, 0};
+  dev::OutMeta mc{ps.exp_c, nullptr, nullptr, nullptr, 1, 1, 0};
+  if (ps.k2) {
+    ps.p2.A = ps.use_a ? ps.a : ps.b; ps.p2.B = ps.use_a ? ps.b : ps.a; ps.p2.C = ps.c;
+    ps.p2.ma = ps.use_a ? ma : mb; ps.p2.mb = ps.use_a ? mb : ma; ps.p2.mc = mc;
+    ps.k2t = try_k2_tma(ps.p2, ps.use_a ? ps.LA : ps.LB, ps.use_a ? ps.LB : ps.LA, ps.f64, false, false, 1,
+                        ps.k2tp, ps.k2t_smem);
+    if (ps.k2t) {
+      ps.k2t_tiles = 1ull << (ps.p2.log2_nu + ps.p2.vbits - ps.k2tp.tb);
+      const int kf = ps.p2.k + ps.p2.f;
+      const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
+      ps.k2t_per_sm = std::min(per_sm_regs, ps.k2t_smem <= 72 * 1024 ? 3 : (ps.k2t_smem <= 108 * 1024 ? 2 : 1));
+      ps.k2tp.k = ps.p2;
+      ps.k2tp.err = nullptr;
+    }
+  }
+  ps.k4 = try_k4(ps.LA, ps.LB, ps.LC, ps.f64, ps.p4);
+  if (ps.k4) {
+    ps.p4.A = ps.a; ps.p4.B = ps.b; ps.p4.C = ps.c; ps.p4.ma = ma; ps.p4.mb = mb; ps.p4.mc = mc;
+    if (((uintptr_t)ps.c & 15u) == 0) ps.outer_blocks = k4_outer_pick(ps.p4);
+    const unsigned tiles = 1u << (ps.p4.ni - 6 + ps.p4.nj - 6 + ps.p4.nb);
+    int g = 0;
+    while (ps.p4.ns - 8 - g > 0 && (tiles << g) < 2 * 148 && g < 9) ++g;
+    if (ps.p4.ns <= 8) g = 0;
+    ps.split_g = g;
+  }
+  K1Params k1;
+  fill_k1(ps.LA, ps.LB, ps.LC, k1);
+  ps.k1_k = k1.k;
+}
+
+PairChoice pair_default(const PairSetup &ps) {
+  PairChoice ch;
+  if (!ps.k2 && ps.k4) {
+    if (!ps.f64 && g_tensor_cores.load() && ps.p4.ni >= 7 && ps.p4.nj >= 7 && ps.p4.ns >= 4) ch.kind = PK_K4TC;
+    else if (g_outer.load() && ps.outer_blocks) ch.kind = PK_K4O;
+    else ch.kind = ps.split_g ? PK_K4SPLIT : PK_K4D;
+  } else if (ps.k2) {
+    ch.kind = ps.k2t ? PK_K2T : PK_K2;
+  } else {
+    ch.kind = PK_K1;
+  }
+  return ch;
+}
+
+bool pair_canonical(const PairChoice &ch) { return ch.kind != PK_K4TC && ch.kind != PK_K4SPLIT; }
+
+int pair_enqueue(PairSetup &ps, const PairChoice &ch, cudaStream_t s) {
+  const bool f64 = ps.f64;
+  switch (ch.kind) {
+    case PK_K4TC:
+      CUDA_TRY(launch_k4_tc(ps.p4, s));
+      return WMC_OK;
+    case PK_K4O:
+      if (f64) dev::k4_outer<double><<<(unsigned)ps.outer_blocks, 256, 0, s>>>(ps.p4);
+      else dev::k4_outer<float><<<(unsigned)ps.outer_blocks, 256, 0, s>>>(ps.p4);
+      g_launches.fetch_add(1);
+      break;
+    case PK_K4D:
+    case PK_K4SPLIT: {
+      dev::K4Params p4 = ps.p4;
+      const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
+      const int g = ch.kind == PK_K4SPLIT ? ps.split_g : 0;
+      // a long summed range over few output tiles: split into groups of
+      // whole 256-term blocks, each group's partials in stream-ordered
+      // scratch, then the groups added in order
+      p4.groups_log2 = g;
+      void *scratch = nullptr;
+      if (g) {
+        const size_t bytes = ((size_t)tiles << g) * 4096 * (f64 ? 8 : 4);
+        CUDA_TRY(scratch_alloc(&scratch, bytes, s));
+        p4.partial = scratch;
+      }
+      if (f64) dev::k4_dense<double><<<tiles << g, 256, 0, s>>>(p4);
+      else dev::k4_dense<float><<<tiles << g, 256, 0, s>>>(p4);
+      g_launches.fetch_add(1);
+      if (g) {
+        if (f64) dev::k4_reduce<double><<<tiles * 16, 256, 0, s>>>(p4);
+        else dev::k4_reduce<float><<<tiles * 16, 256, 0, s>>>(p4);
+        g_launches.fetch_add(1);
+        CUDA_TRY(cudaFreeAsync(scratch, s));
+      }
+      break;
+    }
+    case PK_K2T: {
+      Launch l;
+      l.kind = L_K2T; l.ti = f64 ? TD : TF; l.v = ps.vmax; l.kmax = ps.kmax; l.fmax = ps.fmax;
+      l.smem = ps.k2t_smem;
+      const int per_sm = ch.blocks > 0 ? (int)ch.blocks : ps.k2t_per_sm;
+      l.blocks = (int64_t)std::min<uint64_t>(ps.k2t_tiles, (uint64_t)(148 * per_sm));
+      l.k2t = ps.k2tp;
+      launch_k2t(l, l.k2t, s);
+      g_launches.fetch_add(1);
+      break;
+    }
+    case PK_K2: {
+      Launch l;
+      l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = ps.vmax; l.kmax = ps.kmax; l.fmax = ps.fmax;
+      const int64_t dflt = grid_for(1ull << ps.p2.log2_nu);
+      l.blocks = ch.blocks > 0 ? std::min<int64_t>(dflt, ch.blocks) : dflt;
+      launch_k2(l, ps.p2, s);
+      g_launches.fetch_add(1);
+      break;
+    }
+    default: {
+      Launch l;
+      l.kind = L_K1;
+      fill_k1(ps.LA, ps.LB, ps.LC, l.k1);
+      if (l.k1.k > 24) { set_error("at most 24 summed indices"); return WMC_EINVAL; }
+      l.ti = f64 ? TD : TF;
+      l.ta = (f64 || l.k1.k > 16) ? TD : TF;
+      l.to = f64 ? TD : TF;
+      l.blocks = grid_for(1ull << l.k1.rC);
+      l.k1.A = ps.a; l.k1.B = ps.b; l.k1.C = ps.c;
+      l.k1.ma = dev::Meta{ps.exp_a, nullptr, nullptr, 0};
+      l.k1.mb = dev::Meta{ps.exp_b, nullptr, nullptr, 0};
+      l.k1.mc = dev::OutMeta{ps.exp_c, nullptr, nullptr, nullptr, 1, 1, 0};
+      launch_k1(l, l.k1, s);
+      g_launches.fetch_add(1);
+      break;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  return WMC_OK;
+}
+
+// the legal same-order variants of a node, the fixed rule's first
+std::vector<PairChoice> pair_candidates(const PairSetup &ps, const PairChoice &dflt) {
+  std::vector<PairChoice> v{dflt};
+  auto add = [&](int kind, int64_t blocks) {
+    for (const PairChoice &c : v)
+      if (c.kind == kind && c.blocks == blocks) return;
+    v.push_back(PairChoice{kind, blocks});
+  };
+  if (ps.k2) {
+    add(PK_K2, 0);
+    const int64_t g = grid_for(1ull << ps.p2.log2_nu);
+    for (int64_t m : {2, 4, 8})
+      if (148 * m < g) add(PK_K2, 148 * m);
+    if (ps.k2t)
+      for (int per_sm = 1; per_sm <= ps.k2t_per_sm; ++per_sm)
+        if (!(dflt.kind == PK_K2T && dflt.blocks == 0 && per_sm == ps.k2t_per_sm)) add(PK_K2T, per_sm);
+  }
+  if (ps.k4 && ps.split_g == 0) {
+    add(PK_K4D, 0);
+    if (ps.outer_blocks) add(PK_K4O, 0);
+  }
+  if (ps.k1_k <= 24) add(PK_K1, 0);
+  return v;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, PairChoice> g_tune_cache;
+
+std::string pair_key(const PairSetup &ps, int precision) {
+  std::string k = std::to_string(precision) + ":" + std::to_string(((uintptr_t)ps.c & 15u) == 0) + ":";
+  for (const auto *L : {&ps.LA, &ps.LB, &ps.LC}) {
+    for (int32_t x : *L) k += std::to_string(x) + ",";
+    k += "|";
+  }
+  return k;
+}
+
+// The tuned choice for this node's shape: cached, or measured now on the
+// call's own buffers (each variant once to warm, then three timed runs;
+// the fastest minimum wins).  Synchronises the stream while measuring.
+int pair_tuned(PairSetup &ps, int precision, PairChoice &ch, cudaStream_t s) {
+  const std::string key = pair_key(ps, precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { ch = it->second; return WMC_OK; }
+  }
+  const std::vector<PairChoice> cands = pair_candidates(ps, ch);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0.0f;
+  PairChoice pick = ch;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    int rc = pair_enqueue(ps, cands[i], s);
+    if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+    float t_min = 0.0f;
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, s);
+      rc = pair_enqueue(ps, cands[i], s);
+      cudaEventRecord(e1, s);
+      if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+        if (!rc) set_error("timing a variant failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return rc ? rc : WMC_ECUDA;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t_min = r == 0 ? ms : std::min(t_min, ms);
+    }
+    if (i == 0 || t_min < best) { best = t_min; pick = cands[i]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = pick;
+  ch = pick;
+  return WMC_OK;
+}
+
+}  // namespace
+
+extern "C" void wmc_set_autotune(int32_t on) { g_autotune.store(on ? 1 : 0); }
+
+extern "C" int wmc_pair_variants(int32_t precision, int32_t rank_a, const int32_t *labels_a, int32_t rank_b,
+                                 const int32_t *labels_b, int32_t rank_c, const int32_t *labels_c,
+                                 int32_t c_aligned16, int32_t max_n, int32_t *kinds, int64_t *blocks,
+                                 int32_t *n, int32_t *chosen) {
+  if (!n || !chosen || max_n < 0 || (max_n && (!kinds || !blocks)) || rank_a < 0 || rank_b < 0 || rank_c < 0 ||
+      rank_a > 31 || rank_b > 31 || rank_c > 31 || (rank_a && !labels_a) || (rank_b && !labels_b) ||
+      (rank_c && !labels_c)) {
+    set_error("bad argument");
+    return WMC_EINVAL;
+  }
+  PairSetup ps;
+  ps.f64 = precision == WMC_FP64;
+  ps.c = c_aligned16 ? (void *)(uintptr_t)256 : (void *)(uintptr_t)4;  // only its alignment is read
+  ps.LA.assign(labels_a, labels_a + rank_a);
+  ps.LB.assign(labels_b, labels_b + rank_b);
+  ps.LC.assign(labels_c, labels_c + rank_c);
+  pair_setup(ps);
+  const PairChoice dflt = pair_default(ps);
+  PairChoice cur = dflt;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(pair_key(ps, precision));
+    if (g_autotune.load() && it != g_tune_cache.end()) cur = it->second;
+  }
+  const std::vector<PairChoice> v = pair_canonical(dflt) ? pair_candidates(ps, dflt) : std::vector<PairChoice>{dflt};
+  *n = (int32_t)v.size();
+  *chosen = 0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    if (v[i].kind == cur.kind && v[i].blocks == cur.blocks) *chosen = (int32_t)i;
+    if ((int32_t)i < max_n) { kinds[i] = v[i].kind; blocks[i] = v[i].blocks; }
+  }
+  return WMC_OK;
+}
+
+extern "C" void wmc_debug_force_pair_variant(int32_t kind, int64_t blocks) {
+  g_force_kind.store(kind);
+  g_force_blocks.store(blocks);
+}
+
 extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_t *labels_a,
                                  const void *a, int32_t rank_b, const int32_t *labels_b,
                                  const void *b, int32_t rank_c, const int32_t *labels_c, void *c,
@@ -2100,95 +2548,27 @@ extern "C" int wmc_contract_pair(int32_t precision, int32_t rank_a, const int32_
   if (dup(LA) || dup(LB) || dup(LC)) { set_error("repeated label within a tensor"); return WMC_EINVAL; }
   for (int32_t l : LC)
     if (pos_of(LA, l) < 0 && pos_of(LB, l) < 0) { set_error("label %d of C is in neither A nor B", l); return WMC_EINVAL; }
+  PairSetup ps;
+  ps.f64 = f64; ps.a = a; ps.b = b; ps.c = c;
+  ps.exp_a = exp_a; ps.exp_b = exp_b; ps.exp_c = exp_c;
+  ps.LA = LA; ps.LB = LB; ps.LC = LC;
+  pair_setup(ps);
+  if (ps.k1_k > 24 && !ps.k2 && !ps.k4) { set_error("at most 24 summed indices"); return WMC_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
-  Launch l;
-  K2Params p2;
-  int vmax = 1, kmax = 1, fmax = 1;
-  bool k2 = false;
-  const bool a_first = LA.size() >= LB.size();
-  bool use_a = a_first;
-  for (int attempt = 0; attempt < 2 && !k2; ++attempt) {
-    use_a = (attempt == 0) == a_first;
-    k2 = try_k2(use_a ? LA : LB, use_a ? LB : LA, LC, f64, p2, vmax, kmax, fmax);
+  PairChoice ch = pair_default(ps);
+  if (g_force_kind.load() >= 0) {  // test hook: one listed variant
+    const std::vector<PairChoice> v = pair_canonical(ch) ? pair_candidates(ps, ch) : std::vector<PairChoice>{ch};
+    bool found = false;
+    for (const PairChoice &c : v)
+      if (c.kind == g_force_kind.load() && c.blocks == g_force_blocks.load()) { ch = c; found = true; }
+    if (!found) { set_error("the forced variant is not one of this node's variants"); return WMC_EINVAL; }
+    return pair_enqueue(ps, ch, s);
   }
-  dev::Meta ma{exp_a, nullptr, nullptr, 0}, mb{exp_b, nullptr, nullptr, 0};
-  dev::OutMeta mc{exp_c, nullptr, nullptr, nullptr, 1, 1, 0};
-  dev::K4Params p4;
-  if (!k2 && try_k4(LA, LB, LC, f64, p4)) {
-    p4.A = a; p4.B = b; p4.C = c; p4.ma = ma; p4.mb = mb; p4.mc = mc;
-    // float32 with at least 2^7 rows, 2^7 columns and 2^4 summed terms:
-    // the tensor cores (operands packed once, then a persistent pipeline)
-    if (!f64 && g_tensor_cores.load() && p4.ni >= 7 && p4.nj >= 7 && p4.ns >= 4) {
-      CUDA_TRY(launch_k4_tc(p4, s));
-      return WMC_OK;
-    }
-    if (g_outer.load() && ((uintptr_t)c & 15u) == 0) {  // its vector stores need a 16-byte aligned C
-      if (const int64_t ob = k4_outer_pick(p4)) {
-        if (f64) dev::k4_outer<double><<<(unsigned)ob, 256, 0, s>>>(p4);
-        else dev::k4_outer<float><<<(unsigned)ob, 256, 0, s>>>(p4);
-        g_launches.fetch_add(1);
-        CUDA_TRY(cudaGetLastError());
-        return WMC_OK;
-      }
-    }
-    const unsigned tiles = 1u << (p4.ni - 6 + p4.nj - 6 + p4.nb);
-    // few output tiles and a long summed range: split the range into
-    // groups of whole 256-term blocks, each group's partials in stream-
-    // ordered scratch, then add the groups in order
-    int g = 0;
-    while (p4.ns - 8 - g > 0 && (tiles << g) < 2 * 148 && g < 9) ++g;
-    if (p4.ns <= 8) g = 0;
-    p4.groups_log2 = g;
-    void *scratch = nullptr;
-    if (g) {
-      const size_t bytes = ((size_t)tiles << g) * 4096 * (f64 ? 8 : 4);
-      CUDA_TRY(scratch_alloc(&scratch, bytes, s));
-      p4.partial = scratch;
-    }
-    if (f64) dev::k4_dense<double><<<tiles << g, 256, 0, s>>>(p4);
-    else dev::k4_dense<float><<<tiles << g, 256, 0, s>>>(p4);
-    g_launches.fetch_add(1);
-    if (g) {
-      if (f64) dev::k4_reduce<double><<<tiles * 16, 256, 0, s>>>(p4);
-      else dev::k4_reduce<float><<<tiles * 16, 256, 0, s>>>(p4);
-      g_launches.fetch_add(1);
-      CUDA_TRY(cudaFreeAsync(scratch, s));
-    }
-    CUDA_TRY(cudaGetLastError());
-    return WMC_OK;
+  if (g_autotune.load() && pair_canonical(ch)) {
+    int rc = pair_tuned(ps, precision, ch, s);
+    if (rc) return rc;
   }
-  if (k2) {
-    l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = vmax; l.kmax = kmax; l.fmax = fmax;
-    l.blocks = grid_for(1ull << p2.log2_nu);
-    p2.A = use_a ? a : b; p2.B = use_a ? b : a; p2.C = c;
-    p2.ma = use_a ? ma : mb; p2.mb = use_a ? mb : ma; p2.mc = mc;
-    if (try_k2_tma(p2, use_a ? LA : LB, use_a ? LB : LA, f64, false, false, 1, l.k2t, l.smem)) {
-      const uint64_t n_tiles = 1ull << (p2.log2_nu + p2.vbits - l.k2t.tb);
-      const int kf = p2.k + p2.f;
-      const int per_sm_regs = kf <= 2 ? 3 : (kf <= 4 ? 2 : 1);
-      const int per_sm = std::min(per_sm_regs, l.smem <= 72 * 1024 ? 3 : (l.smem <= 108 * 1024 ? 2 : 1));
-      l.blocks = (int64_t)std::min<uint64_t>(n_tiles, (uint64_t)(148 * per_sm));
-      l.k2t.k = p2;
-      l.k2t.err = nullptr;
-      launch_k2t(l, l.k2t, s);
-    } else {
-      launch_k2(l, p2, s);
-    }
-  } else {
-    l.kind = L_K1;
-    fill_k1(LA, LB, LC, l.k1);
-    if (l.k1.k > 24) { set_error("at most 24 summed indices"); return WMC_EINVAL; }
-    l.ti = f64 ? TD : TF;
-    l.ta = (f64 || l.k1.k > 16) ? TD : TF;
-    l.to = f64 ? TD : TF;
-    l.blocks = grid_for(1ull << l.k1.rC);
-    l.k1.A = a; l.k1.B = b; l.k1.C = c;
-    l.k1.ma = ma; l.k1.mb = mb; l.k1.mc = mc;
-    launch_k1(l, l.k1, s);
-  }
-  g_launches.fetch_add(1);
-  CUDA_TRY(cudaGetLastError());
-  return WMC_OK;
+  return pair_enqueue(ps, ch, s);
 }
 
 extern "C" int wmc_to_scaled_fp32(const double *x, int64_t n, float *out, int64_t *exp_out,

@@ -97,6 +97,9 @@ struct Plan {
   // the same tree in float64 for queries whose scaled-FP32 walk may have
   // flushed (WMC_FLAG_FELL_BACK_FP64)
   std::map<int32_t, std::unique_ptr<ExecState>> exec_f64;
+  // states replaced by wmc_autotune_plan (kept until the plan is destroyed:
+  // a server or graph may still hold them)
+  std::vector<std::unique_ptr<ExecState>> retired;
   ~Plan();
 };
 

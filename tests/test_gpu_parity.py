@@ -329,6 +329,92 @@ def test_pair_long_summed_range_accumulates_in_fp64(w, precision, ra, rb, b, k):
     assert err.max() <= tol, err.max()
 
 
+# shapes with several same-order variants: streaming (and TMA-staged),
+# dense tiled / outer product, and the generic kernel
+SWEEP_VARIANTS = [(20, 3, 2, 1), (18, 6, 0, 2), (15, 14, 1, 2), (13, 14, 2, 5), (12, 10, 2, 4), (16, 8, 4, 4)]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("ra,rb,b,k", SWEEP_VARIANTS)
+def test_pair_variants_give_the_same_bits(w, precision, ra, rb, b, k):
+    """Every variant the autotuner may pick for a node (wmc_pair_variants)
+    adds the summed terms in the canonical order: forced one by one, each
+    returns the fixed rule's bits (and exponent), which match the oracle."""
+    case = wmcgen.pair_case(ra, rb, b, k, seed=500 + ra + rb + k, shuffle=False)
+    variants, chosen = w.pair_variants(precision, case.labels_a, case.labels_b, case.labels_c)
+    assert chosen == 0 and len(variants) >= 2
+    ref = None
+    try:
+        for kind, blocks in variants:
+            w.wmc_debug_force_pair_variant(kind, blocks)
+            got = _run_pair_raw(w, case, precision)
+            if ref is None:
+                ref = got
+            assert np.array_equal(got[0], ref[0]) and got[1] == ref[1], (w.PAIR_KINDS[kind], blocks)
+    finally:
+        w.wmc_debug_force_pair_variant(-1, 0)
+    want = oracle.contract_pair(case.labels_a, case.a, case.labels_b, case.b, case.labels_c)
+    err = np.abs(ref[0].astype(np.float64) * 2.0 ** ref[1] - want) / np.abs(want)
+    assert err.max() <= _pair_tol(k, precision)
+
+
+def _run_pair_raw(w, case, precision):
+    """(C as stored, C's exponent) of one wmc_contract_pair call."""
+    rc = len(case.labels_c)
+    A64, B64 = _dev(case.a, torch.float64), _dev(case.b, torch.float64)
+    if precision == FP64:
+        C = torch.empty(1 << rc, dtype=torch.float64, device="cuda")
+        w.contract_pair(FP64, case.labels_a, A64, case.labels_b, B64, case.labels_c, C)
+        torch.cuda.synchronize()
+        return C.cpu().numpy(), 0
+    A = torch.empty(A64.numel(), dtype=torch.float32, device="cuda")
+    B = torch.empty(B64.numel(), dtype=torch.float32, device="cuda")
+    e = torch.zeros(3, dtype=torch.int64, device="cuda")
+    w.to_scaled_fp32(A64, A, e[0:1])
+    w.to_scaled_fp32(B64, B, e[1:2])
+    C = torch.empty(1 << rc, dtype=torch.float32, device="cuda")
+    w.contract_pair(FP32, case.labels_a, A, case.labels_b, B, case.labels_c, C, e[0:1], e[1:2], e[2:3])
+    torch.cuda.synchronize()
+    return C.cpu().numpy(), int(e[2])
+
+
+def test_pair_autotune_keeps_the_bits(w):
+    """With autotuning on, the first call of a shape times its variants and
+    later calls use the fastest: the results stay the fixed rule's bits."""
+    cases = [wmcgen.pair_case(ra, rb, b, k, seed=600 + ra + k, shuffle=False) for (ra, rb, b, k) in SWEEP_VARIANTS]
+    fixed = [_run_pair_raw(w, c, FP32) for c in cases]
+    try:
+        w.wmc_set_autotune(1)
+        for c, ref in zip(cases, fixed):
+            for _ in range(2):  # the tuning call, then a tuned call
+                got = _run_pair_raw(w, c, FP32)
+                assert np.array_equal(got[0], ref[0]) and got[1] == ref[1]
+            variants, chosen = w.pair_variants(FP32, c.labels_a, c.labels_b, c.labels_c)
+            assert 0 <= chosen < len(variants)
+    finally:
+        w.wmc_set_autotune(0)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_plan_autotune_keeps_the_bits(w, precision):
+    """wmc_autotune_plan times the walk's layouts and installs the fastest:
+    no layout is rejected (all return the same bits), and the tuned plan's
+    results equal the untuned plan's bit for bit."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    Q = 16
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=23, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, precision)
+    before = plan.execute(wq, wnq)
+    rep = plan.autotune(Q)
+    ms = [l["ms"] for l in rep["layouts"]]
+    assert len(ms) >= 5 and min(ms) >= 0
+    assert ms[rep["chosen"]] == min(ms)
+    assert plan.info(Q).launches_per_walk == rep["layouts"][rep["chosen"]]["launches"]
+    after = plan.execute(wq, wnq)
+    for q in range(Q):
+        assert (after[q].mant, after[q].exp2, after[q].flags) == (before[q].mant, before[q].exp2, before[q].flags)
+
+
 def test_pair_edge_cases(w):
     """Rank-0 output (full inner product), no summed index (outer product),
     a summed index present in one operand only."""

@@ -299,6 +299,27 @@ def test_slice_ranges_and_combination():
     assert w.wmc_combine_results(nan, 1, ctypes.byref(out)) == w.WMC_EINVAL
 
 
+def test_pair_variants_listing():
+    """wmc_pair_variants lists the fixed rule's kernel first and, for
+    shapes in the canonical summation order, the other same-order kernels
+    the autotuner may pick; shapes whose rule picks another order (the
+    tensor-core product, the split summed range) list only that one."""
+    w = _lib()
+    K = {v: k for k, v in w.PAIR_KINDS.items()}
+    def kinds(ra, rb, b, k, prec):
+        pc = wmcgen.pair_case(ra, rb, b, k, seed=1, shuffle=False, with_data=False)
+        v, ch = w.pair_variants(prec, pc.labels_a, pc.labels_b, pc.labels_c)
+        assert ch == 0
+        return [x[0] for x in v]
+    assert kinds(29, 5, 2, 1, 1)[0] == K["k2_tma"] and K["k2_stream"] in kinds(29, 5, 2, 1, 1)
+    assert kinds(17, 17, 2, 1, 1)[:2] == [K["k4_outer"], K["k4_dense"]]
+    assert kinds(24, 22, 0, 8, 1) == [K["k4_tc"]]
+    assert kinds(24, 22, 0, 8, 0)[0] == K["k4_dense"]
+    assert kinds(22, 22, 0, 16, 1) == [K["k4_dense split"]]
+    for sh in [(29, 5, 2, 1), (17, 17, 2, 1), (13, 14, 2, 5), (12, 10, 2, 4)]:
+        assert kinds(*sh, 1)[-1] == K["k1_generic"]
+
+
 # ------------------------------------------------------ clause factoring
 
 def _long_clause_cnf(n, n_short, n_long, k_long, seed):
