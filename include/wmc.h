@@ -152,7 +152,21 @@ typedef struct {
                                weight leaf, labels n_vars, n_vars + 1, ...),
                                so W is unchanged.  Not combinable with
                                WMC_ORDER_GIVEN.  0 = off                   */
-  int32_t reserved;
+  int32_t block_fp;         /* block-floating-point float32 (scaled-FP32
+                               plans): if > 0, every tensor keeps one int32
+                               exponent per query lane for each block of
+                               2^(block_fp - 1) consecutive assignments of
+                               its non-query indices (weight vectors: one per
+                               entry), so entries of different blocks may
+                               differ by any factor and only entries of one
+                               block share float32's range; nodes add their
+                               float32 products in float64 and normalise
+                               each output block.  Every node runs on the
+                               block-floating-point kernel (no chains, no
+                               small-node phase).  At most 9; blocks of at
+                               most 2^11 outputs with the query bits (Q *
+                               2^(block_fp - 1) <= 2048); not combinable
+                               with index slicing.  0 = off                 */
 } wmc_plan_opts;
 
 /* Planning: Sec. 3.3.  Builds a contraction tree by bucket elimination

@@ -123,8 +123,9 @@ class Plan:
     def __init__(self, net: Network, precision: int = _abi.WMC_SCALED_FP32,
                  ordering: int = _abi.WMC_ORDER_BEST, max_rank_cap: int = 0,
                  mem_budget_bytes: int = 0, order: Optional[Sequence[int]] = None,
-                 slice_to_rank: int = 0, factor_clauses_above: int = 0):
+                 slice_to_rank: int = 0, factor_clauses_above: int = 0, block_fp: int = 0):
         o = _abi.wmc_plan_opts()
+        o.block_fp = block_fp
         o.precision = precision
         o.ordering = ordering
         o.max_rank_cap = max_rank_cap

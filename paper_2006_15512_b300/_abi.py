@@ -65,7 +65,7 @@ class wmc_network_info_t(ctypes.Structure):
 class wmc_plan_opts(ctypes.Structure):
     _fields_ = [("precision", c_i32), ("ordering", c_i32), ("max_rank_cap", c_i32),
                 ("slice_to_rank", c_i32), ("mem_budget_bytes", c_i64), ("order", P(c_i32)),
-                ("factor_clauses_above", c_i32), ("reserved", c_i32)]
+                ("factor_clauses_above", c_i32), ("block_fp", c_i32)]
 
 
 class wmc_plan_info_t(ctypes.Structure):

@@ -731,6 +731,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
     Plan &plan = plan_of(plans[f]);
     if (plan.precision != prec) { delete b; set_error("plans of one batch must share a precision"); return WMC_EINVAL; }
     if (!plan.slice_vars.empty()) { delete b; set_error("sliced plans run through wmc_execute, not a batch"); return WMC_EINVAL; }
+    if (plan.bfp_b >= 0) { delete b; set_error("block-floating-point plans run through wmc_execute, not a batch"); return WMC_EINVAL; }
     LayoutView lv;
     int rc = exec_layout(plan, 1, &lv);
     if (rc) { delete b; return rc; }

@@ -91,7 +91,8 @@ namespace {
 constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ };
+enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ,
+            L_BFP, L_BFPW };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -139,6 +140,11 @@ struct WalkOpts {
 
 struct ExecState {
   WalkOpts wo;
+  // block floating point: block bits (-1: off), per tensor the exponent
+  // array's byte offset (right after its mantissas) and block bits
+  int32_t bfp_b = -1;
+  std::vector<int64_t> t_eoff;
+  std::vector<int8_t> t_bb;
   uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
   int32_t Qp = 1;  // Q padded to 2^m: the query index is m bits
@@ -767,6 +773,8 @@ static WalkOpts walk_opts_now() {
 static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, bool force_f64 = false,
                       const WalkOpts *wo = nullptr) {
   st.wo = wo ? *wo : walk_opts_now();
+  st.bfp_b = (plan.bfp_b >= 0 && !plain && !force_f64) ? plan.bfp_b : -1;
+  if (st.bfp_b >= 0) { st.wo.fuse = 0; st.wo.small_phase = 0; st.wo.chain_runs = 0; }
   st.Q = Q;
   int32_t m = 0;
   while ((1 << m) < Q) ++m;
@@ -799,6 +807,18 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     }
     bytes[i] = (int64_t(1) << r) * (st.t_dbl[i] ? 8 : 4);
     st.t_qc[i] = t.has_q ? Qp : 1;
+    if (st.bfp_b >= 0) {
+      // the mantissas, then one int32 exponent per (block, lane)
+      const int32_t n = (int32_t)t.labels.size();
+      const int32_t bb = t.kind == LEAF_WEIGHT ? 0 : std::min(st.bfp_b, n);
+      if ((t.has_q ? m : 0) + bb > 11) {
+        set_error("block floating point: blocks of 2^%d outputs with the query bits (max 2^11)",
+                  (t.has_q ? m : 0) + bb);
+        return WMC_EINVAL;
+      }
+      st.t_bb.push_back((int8_t)bb);
+      bytes[i] = align_up(bytes[i]) + 4 * (int64_t)st.t_qc[i] * (int64_t(1) << (n - bb));
+    }
     st.t_meta[i] = slots;
     slots += st.t_qc[i];
   }
@@ -850,7 +870,19 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     Launch &l = node_l[ni];
     const bool is_root = nd.c == root;
     bool used_k2 = false;
-    if (!is_root) {
+    if (st.bfp_b >= 0) {  // block floating point: one kernel for every node
+      l.kind = L_BFP;
+      fill_k1(LA, LB, LC, l.k1);
+      if (l.k1.k > 24) { set_error("node sums %d indices (max 24)", l.k1.k); return WMC_EPLAN_TOO_BIG; }
+      l.ti = TF;
+      l.to = st.t_dbl[(size_t)nd.c] ? TD : TF;
+      l.id_a = nd.a;
+      l.id_b = nd.b;
+      const int64_t nb = int64_t(1) << ((int64_t)C.labels.size() - st.t_bb[(size_t)nd.c]);
+      l.blocks = std::min<int64_t>(nb, 148 * 8);
+      used_k2 = true;  // (no other kernel)
+    }
+    if (!is_root && !used_k2) {
       const bool a_first = LA.size() >= LB.size();
       int vmax = 1, kmax = 1, fmax = 1;
       K2Params p2;
@@ -1039,6 +1071,14 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   }
   st.arena_bytes = ff.top;
   st.ws_bytes = arena0 + align_up(ff.top);
+  if (st.bfp_b >= 0) {
+    st.t_eoff.assign(nt, 0);
+    for (size_t i = 0; i < nt; ++i) {
+      const TensorInfo &t = plan.tensors[i];
+      const int64_t r = (int64_t)t.labels.size() + (t.has_q ? m : 0);
+      st.t_eoff[i] = st.t_off[i] + align_up((int64_t(1) << r) * (st.t_dbl[i] ? 8 : 4));
+    }
+  }
 
   // ---- launches
   st.launches.clear();
@@ -1053,6 +1093,14 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   ms1.memset_bytes = align_up(8 * slots);
   ms1.memset_value = 0xff;
   st.launches.push_back(ms1);
+  if (st.bfp_b >= 0 && plan.n_leaves > 0) {
+    // block floating point: the leaves' exponents start at 0 (clause
+    // tensors and the scalar 1 keep them; weight vectors write their own)
+    Launch z = ms;
+    z.memset_off = st.t_off[0];
+    z.memset_bytes = arena0 - st.t_off[0];
+    st.launches.push_back(z);
+  }
   // clause leaves
   st.h_clause.clear(); st.h_first.clear();
   int64_t entries = 0;
@@ -1092,7 +1140,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     }
   }
   if (have_w) {
-    Launch l; l.kind = L_WEIGHTS; l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Qp);
+    Launch l; l.kind = st.bfp_b >= 0 ? L_BFPW : L_WEIGHTS;
+    l.blocks = grid_for((uint64_t)plan.n_vars * (uint64_t)Qp);
     st.launches.push_back(l);
   }
   st.h_snodes.clear();
@@ -1547,6 +1596,30 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         launch_k2(l, p, s);
         break;
       }
+      case L_BFPW:
+        dev::k_bfp_weights<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
+            io, plan.n_vars, st.Q, st.Qp, tb.woff, (float *)ws, align_up(8 * (int64_t)st.Qp), flags);
+        break;
+      case L_BFP: {
+        dev::BfpParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.k1 = l.k1;
+        p.k1.A = ws + l.off_a; p.k1.B = ws + l.off_b; p.k1.C = ws + l.off_c;
+        const TensorInfo &TA = plan.tensors[(size_t)l.id_a], &TB = plan.tensors[(size_t)l.id_b];
+        const TensorInfo &TC = plan.tensors[(size_t)l.id_c];
+        p.eA = (const int32_t *)(ws + st.t_eoff[(size_t)l.id_a]);
+        p.eB = (const int32_t *)(ws + st.t_eoff[(size_t)l.id_b]);
+        p.eC = (int32_t *)(ws + st.t_eoff[(size_t)l.id_c]);
+        p.mA = (int8_t)(TA.has_q ? st.m : 0); p.mB = (int8_t)(TB.has_q ? st.m : 0); p.mC = (int8_t)(TC.has_q ? st.m : 0);
+        p.bA = st.t_bb[(size_t)l.id_a]; p.bB = st.t_bb[(size_t)l.id_b]; p.bC = st.t_bb[(size_t)l.id_c];
+        p.c_double = l.to == TD ? 1 : 0;
+        p.root_exp = mexp + l.meta_c;
+        p.flags = flags;
+        p.n_blocks = int64_t(1) << ((int64_t)TC.labels.size() - p.bC);
+        if (l.to == TD) dev::k_bfp_node<double><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(p);
+        else dev::k_bfp_node<float><<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(p);
+        break;
+      }
       case L_FINAL: {
         const int32_t root_qc = plan.tensors[(size_t)plan.nodes.back().c].has_q ? st.Qp : 1;
         dev::k_finalize<<<(unsigned)l.blocks, dev::kThreads, 0, s>>>(
@@ -1813,10 +1886,16 @@ extern "C" int wmc_plan(const wmc_network_t *net, const wmc_plan_opts *opts, wmc
   o.precision = WMC_SCALED_FP32;
   if (opts) o = *opts;
   if (o.precision != WMC_FP64 && o.precision != WMC_SCALED_FP32) { set_error("bad precision %d", o.precision); return WMC_EINVAL; }
+  if (o.block_fp < 0 || o.block_fp > 9) { set_error("block_fp must be in [0, 9] (got %d)", o.block_fp); return WMC_EINVAL; }
+  if (o.block_fp && (o.precision != WMC_SCALED_FP32 || o.slice_to_rank > 0)) {
+    set_error("block floating point needs a scaled-FP32 plan without index slicing");
+    return WMC_EINVAL;
+  }
   wmc_plan_t *p = new (std::nothrow) wmc_plan_t();
   if (!p) { set_error("out of host memory"); return WMC_ENOMEM; }
   int rc = build_plan(network_of(net), o, *p);
   if (rc) { delete p; return rc; }
+  p->bfp_b = o.block_fp - 1;
   if (o.mem_budget_bytes > 0) {
     int64_t ws = plan_workspace_bytes(*p, 1, nullptr);
     if (ws < 0) { delete p; return WMC_EPLAN_TOO_BIG; }
@@ -1930,7 +2009,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_K1 ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = (l.kind == L_K1 || l.kind == L_BFP) ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -2860,6 +2939,38 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
           return badc("staged S", i, D);
       if (need > l.smem || l.smem > 220 * 1024 || cp.n_stages < 2 || cp.n_stages > wmc::dev::kMaxStagesC)
         return badc("shared memory", (int64_t)need, (int64_t)l.smem);
+      continue;
+    }
+    if (l.kind == L_BFP) {
+      // mantissas (all index bits set) and the exponent entry of the last
+      // block and lane of each tensor, inside the tensor's allocation
+      const K1Params &p = l.k1;
+      int64_t ma = 0, mb = 0;
+      for (int j = 0; j < p.rC; ++j) {
+        if (p.posA[j] >= 0) ma |= 1ll << p.posA[j];
+        if (p.posB[j] >= 0) mb |= 1ll << p.posB[j];
+      }
+      for (int j = 0; j < p.k; ++j) {
+        if (p.sposA[j] >= 0) ma |= 1ll << p.sposA[j];
+        if (p.sposB[j] >= 0) mb |= 1ll << p.sposB[j];
+      }
+      const int64_t ids[3] = {l.id_a, l.id_b, l.id_c};
+      const int64_t last[3] = {ma, mb, (1ll << p.rC) - 1};
+      for (int t = 0; t < 3; ++t) {
+        const size_t id = (size_t)ids[t];
+        const TensorInfo &T = plan->tensors[id];
+        const int mq = T.has_q ? st->m : 0;
+        const int64_t es = st->t_dbl[id] ? 8 : 4;
+        const int64_t n_el = int64_t(1) << ((int64_t)T.labels.size() + mq);
+        const int64_t e_last = ((last[t] >> (mq + st->t_bb[id])) << mq) | (last[t] & ((1ll << mq) - 1));
+        if (last[t] >= n_el || st->t_eoff[id] < st->t_off[id] + n_el * es ||
+            st->t_eoff[id] + 4 * (e_last + 1) > st->t_off[id] + st->t_bytes[id] ||
+            (t == 2 && (mq + st->t_bb[id] > 11))) {
+          set_error("launch %zu: block-floating-point tensor %d out of bounds", li, t);
+          return WMC_EINVAL;
+        }
+      }
+      ++checked;
       continue;
     }
     if (l.kind != L_K2 && l.kind != L_K2T && l.kind != L_K1) continue;

@@ -88,6 +88,7 @@ struct Plan {
   // walk runs once per slice assignment and the results are summed
   std::vector<int32_t> slice_vars;
   int32_t n_aux = 0;  // auxiliary indices of factored clauses (labels n_vars ..)
+  int32_t bfp_b = -1;  // block floating point: block bits b (-1: off)
 
   std::mutex exec_mu;
   std::map<int32_t, std::unique_ptr<ExecState>> exec;  // keyed by Q

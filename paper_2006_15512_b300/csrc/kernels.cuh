@@ -2681,6 +2681,167 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int
   }
 }
 
+// ------------------------------------------------ block floating point
+//
+// Block-floating-point float32 (a plan option): every tensor's entries are
+// float32 mantissas, and each block of 2^b consecutive assignments of its
+// non-query indices has its own int32 exponent per query lane (weight
+// vectors: one exponent per entry), so one tensor may span any range: only
+// entries of one block share float32's 2^126 range.  A node adds its
+// products in float64 (a product of two float32 mantissas is exact there),
+// each term brought to the largest exponent met so far, then each output
+// block is normalised so its largest |entry| lies in [1, 2) and its
+// exponent stored.  Value of entry o of a tensor with m query bits and b
+// block bits: mant[o] * 2^exp[(o >> (m + b)) * 2^m + (o & (2^m - 1))].
+
+struct BfpParams {
+  K1Params k1;                   // addressing (C bits -> A, B bits; summed bits)
+  const int32_t *eA, *eB;        // block exponents of the operands
+  int32_t *eC;
+  int8_t mA, mB, mC;             // query bits of each tensor (0 or m)
+  int8_t bA, bB, bC;             // block bits of each tensor
+  int8_t c_double;               // the root: float64 mantissas, exponent also to root_exp
+  int8_t pad;
+  int64_t *root_exp;             // per-lane exponent slots of the root (k_finalize)
+  uint32_t *flags;               // per-lane flags (WMC_FLAG_FP32_FLUSH)
+  int64_t n_blocks;              // output blocks: 2^(non-query bits of C - bC)
+};
+
+constexpr int kBfpMaxOut = 2048;  // outputs of one block (all lanes) held in shared memory
+constexpr int kNoExp = -2147483647 - 1;  // no nonzero term yet
+
+__device__ __forceinline__ double pow2_d(int e) {  // 2^e for e in [-1022, 1023], else 0 / inf-free clamp
+  if (e < -1022) return 0.0;
+  if (e > 1023) e = 1023;
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+__device__ __forceinline__ int ilogb_d(double x) {  // floor(log2 |x|) of a normal nonzero double
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(kThreads) k_bfp_node(BfpParams p) {
+  __shared__ uint32_t lutA[4][256], lutB[4][256];
+  __shared__ uint32_t slutA[3][256], slutB[3][256];
+  __shared__ double s_acc[kBfpMaxOut];
+  __shared__ int s_t[kBfpMaxOut];
+  __shared__ int s_emax[kMaxQ];
+  const K1Params &k = p.k1;
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const int byte = i >> 8, v = i & 255;
+    uint32_t oa = 0, ob = 0;
+    for (int b = 0; b < 8; ++b) {
+      const int j = byte * 8 + b;
+      if (((v >> b) & 1) && j < k.rC) {
+        if (k.posA[j] >= 0) oa |= 1u << k.posA[j];
+        if (k.posB[j] >= 0) ob |= 1u << k.posB[j];
+      }
+    }
+    lutA[byte][v] = oa;
+    lutB[byte][v] = ob;
+  }
+  for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
+    const int byte = i >> 8, v = i & 255;
+    uint32_t oa = 0, ob = 0;
+    for (int b = 0; b < 8; ++b) {
+      const int j = byte * 8 + b;
+      if (((v >> b) & 1) && j < k.k) {
+        if (k.sposA[j] >= 0) oa |= 1u << k.sposA[j];
+        if (k.sposB[j] >= 0) ob |= 1u << k.sposB[j];
+      }
+    }
+    slutA[byte][v] = oa;
+    slutB[byte][v] = ob;
+  }
+  __syncthreads();
+  const float *A = (const float *)k.A;
+  const float *B = (const float *)k.B;
+  const int qa = (1 << p.mA) - 1, qb = (1 << p.mB) - 1, qc = (1 << p.mC) - 1;
+  const int shA = p.mA + p.bA, shB = p.mB + p.bB;
+  const uint32_t n_out = 1u << (p.mC + p.bC);  // outputs of one block, all lanes
+  const uint32_t ns = 1u << k.k;
+  for (int64_t blk = blockIdx.x; blk < p.n_blocks; blk += gridDim.x) {
+    for (int q = threadIdx.x; q <= qc; q += blockDim.x) s_emax[q] = kNoExp;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_out; i += blockDim.x) {
+      const uint32_t o = ((uint32_t)blk << (p.mC + p.bC)) | i;
+      const uint32_t ba = lutA[0][o & 255] | lutA[1][(o >> 8) & 255] | lutA[2][(o >> 16) & 255] | lutA[3][o >> 24];
+      const uint32_t bb = lutB[0][o & 255] | lutB[1][(o >> 8) & 255] | lutB[2][(o >> 16) & 255] | lutB[3][o >> 24];
+      // terms in ascending summed assignment; the running sum is kept at
+      // the largest exponent met so far (a power-of-two rescale is exact)
+      double acc = 0.0;
+      int t = kNoExp;
+      for (uint32_t sidx = 0; sidx < ns; ++sidx) {
+        const uint32_t oa = ba | slutA[0][sidx & 255] | slutA[1][(sidx >> 8) & 255] | slutA[2][sidx >> 16];
+        const uint32_t ob = bb | slutB[0][sidx & 255] | slutB[1][(sidx >> 8) & 255] | slutB[2][sidx >> 16];
+        const float ma = A[oa], mb = B[ob];
+        if (ma == 0.0f || mb == 0.0f) continue;
+        const int e = p.eA[((oa >> shA) << p.mA) | (oa & qa)] + p.eB[((ob >> shB) << p.mB) | (ob & qb)];
+        const double prod = (double)ma * (double)mb;  // exact
+        if (t == kNoExp) { acc = prod; t = e; }
+        else if (e > t) { acc = acc * pow2_d(t - e) + prod; t = e; }
+        else acc += prod * pow2_d(e - t);
+      }
+      if (acc == 0.0 || fabs(acc) < 2.2250738585072014e-308) { acc = 0.0; t = kNoExp; }
+      s_acc[i] = acc;
+      s_t[i] = t;
+      if (t != kNoExp) atomicMax(&s_emax[i & qc], t + ilogb_d(acc));
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_out; i += blockDim.x) {
+      const uint32_t o = ((uint32_t)blk << (p.mC + p.bC)) | i;
+      const int q = (int)(i & qc);
+      const double acc = s_acc[i];
+      TO v = (TO)0;
+      if (acc != 0.0) {
+        const int d = s_t[i] - s_emax[q];  // <= -ilogb(acc): |v| < 2
+        v = (TO)(acc * pow2_d(d));
+        if (below_normal(v)) atomicOr(p.flags + q, 2u);  // an entry more than float's range below its block's top
+      }
+      ((TO *)k.C)[o] = v;
+    }
+    for (int q = threadIdx.x; q <= qc; q += blockDim.x) {
+      const int em = s_emax[q] == kNoExp ? 0 : s_emax[q];
+      p.eC[(blk << p.mC) | q] = em;
+      if (p.c_double) p.root_exp[q] = em;
+    }
+    __syncthreads();
+  }
+}
+
+// Weight vectors in block-floating-point form: each entry its own exponent
+// per lane (W = mant * 2^e, mant in [1, 2)), so a weight ratio of any size
+// is kept exactly.  Layout of a leaf: mantissas [value][lane] at off, then
+// (exp_delta bytes later) exponents [value][lane].
+__global__ void k_bfp_weights(const IoDesc *io, int32_t n_vars, int32_t Q, int32_t Qp, const int64_t *off,
+                              float *arena, int64_t exp_delta, uint32_t *flags) {
+  const double *w_pos = io->w_pos;
+  const double *w_neg = io->w_neg;
+  const int64_t total = (int64_t)n_vars * Qp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = (int32_t)(i / Qp), q = (int32_t)(i % Qp);
+    if (off[x] < 0) continue;
+    const int32_t qs = q < Q ? q : Q - 1;
+    int32_t *ex = (int32_t *)((char *)(arena + off[x]) + exp_delta);
+    for (int val = 0; val < 2; ++val) {
+      const double w = val ? w_pos[(int64_t)qs * n_vars + x] : w_neg[(int64_t)qs * n_vars + x];
+      float m = 0.0f;
+      int e = 0;
+      if (w != 0.0) {
+        double aw = fabs(w);
+        int adj = 0;
+        if (aw < 2.2250738585072014e-308) { aw *= 18014398509481984.0; adj = -54; }  // subnormal: scale by 2^54
+        e = ilogb_d(aw) + adj;
+        m = (float)(w * pow2_d(-(e - adj)) * (adj ? 18014398509481984.0 : 1.0));
+        if (!isfinite(w)) atomicOr(flags + q, 2u);
+      }
+      arena[off[x] + (int64_t)val * Qp + q] = m;
+      ex[val * Qp + q] = e;
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_one_leaf(T *dst, int64_t meta, int64_t *meta_exp, unsigned long long *meta_max,
                            unsigned long long *meta_min) {

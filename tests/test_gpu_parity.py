@@ -184,6 +184,63 @@ def test_fp32_flush_falls_back_to_fp64(w):
             assert rel(res[q], want) <= TOL[FP32]
 
 
+# ------------------------------------------- block floating point (f4)
+
+@pytest.mark.parametrize("block_fp", [1, 3, 6])
+@pytest.mark.parametrize("Q", [1, 8])
+def test_block_fp_random_3cnf(w, block_fp, Q):
+    """Block-floating-point float32 (one exponent per block of 2^(block_fp-1)
+    index assignments and lane) against brute force on random 3-CNF."""
+    cnf = wmcgen.random_kcnf(20, 60, seed=block_fp)
+    wq, wnq = wmcgen.query_weights(20, Q, seed=40 + Q, lo=0.1, hi=0.9)
+    plan = plan_for(w, cnf, None, None, FP32, block_fp=block_fp)
+    res = plan.execute(wq, wnq)
+    for q in range(Q):
+        want = oracle.brute_force(cnf, wq[q], wnq[q])[0]
+        r = rel(res[q], want)
+        assert r <= TOL[FP32] and r <= res[q].rel_err_bound + 1e-16, (q, r)
+        assert not res[q].flags & (w.WMC_FLAG_FP32_FLUSH | w.WMC_FLAG_FELL_BACK_FP64)
+
+
+def test_block_fp_grid(w):
+    """The 16x100 grid (the serving network, values near 1e-300) in
+    block-floating-point form, 8 queries, against the oracle."""
+    cnf = wmcgen.grid_cnf(16, 100, 1)
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, 8, seed=3, lo=0.05, hi=0.95)
+    col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
+    plan = plan_for(w, cnf, None, None, FP32, block_fp=4)
+    res = plan.execute(wq, wnq)
+    for q in (0, 7):
+        assert rel(res[q], oracle.bucket_elim(cnf, wq[q], wnq[q], order=col)) <= TOL[FP32]
+
+
+@pytest.mark.parametrize("block_fp", [1, 2])
+def test_block_fp_keeps_weights_beyond_float_range(w, block_fp):
+    """Weight ratios far beyond float32's range inside one tensor (1e-41,
+    1e-300 against ~1): the scaled-FP32 walk flushes them (and, with the
+    fallback off, only flags the query), while block floating point keeps
+    every query within 1e-4 of the oracle in float32 storage, with no flush
+    flag and no FP64 re-execution."""
+    n = 14
+    cnf = wmcgen.random_kcnf(n, 36, seed=6)
+    cnf = wmcgen.Cnf(n, cnf.clauses + [[3]])  # x_3 forced true: its tiny weight survives
+    Q = 8
+    wq, wnq = wmcgen.query_weights(n, Q, seed=9, lo=0.1, hi=0.9)
+    for q, tiny in ((1, 1e-41), (4, 1e-41), (5, 1e-300), (6, 3e-200)):
+        wq[q, 2] = tiny
+    try:
+        w.wmc_set_fp64_fallback(0)
+        raw = plan_for(w, cnf, None, None, FP32).execute(wq, wnq)
+        res = plan_for(w, cnf, None, None, FP32, block_fp=block_fp).execute(wq, wnq)
+    finally:
+        w.wmc_set_fp64_fallback(1)
+    assert all(raw[q].flags & w.WMC_FLAG_FP32_FLUSH for q in (1, 4, 5, 6))
+    for q in range(Q):
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q])
+        assert not res[q].flags & (w.WMC_FLAG_FP32_FLUSH | w.WMC_FLAG_FELL_BACK_FP64), q
+        assert rel(res[q], want) <= TOL[FP32], (q, rel(res[q], want))
+
+
 # ------------------------------------------------------------ grids
 
 @pytest.mark.parametrize("precision", [FP64, FP32])

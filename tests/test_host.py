@@ -320,6 +320,33 @@ def test_pair_variants_listing():
         assert kinds(*sh, 1)[-1] == K["k1_generic"]
 
 
+def test_block_fp_options():
+    """Block floating point: at most 9, scaled-FP32 plans only, not with
+    index slicing, blocks of at most 2^11 outputs with the query bits; its
+    walks pass the host bounds replay, exponent arrays included."""
+    w = _lib()
+    import ctypes
+    cnf = wmcgen.random_kcnf(20, 60, seed=3)
+    net = w.Network.from_cnf(cnf)
+    for bad in (dict(block_fp=10), dict(block_fp=-1), dict(block_fp=2, precision=w.WMC_FP64),
+                dict(block_fp=2, slice_to_rank=10)):
+        kw = dict(precision=w.WMC_SCALED_FP32)
+        kw.update(bad)
+        with pytest.raises(w._abi.WmcError) as e:
+            w.Plan(net, **kw)
+        assert e.value.status == w.WMC_EINVAL
+    p = w.Plan(net, precision=w.WMC_SCALED_FP32, block_fp=5)  # blocks of 16 assignments
+    with pytest.raises(w._abi.WmcError):
+        p.info(1024)  # 10 query bits + 4 block bits > 11
+    for Q in (1, 4, 64):
+        n = ctypes.c_int64()
+        assert w.wmc_debug_check_bounds(p.handle, Q, ctypes.byref(n)) == w.WMC_OK
+        assert n.value >= p.info(Q).n_nodes  # every node (and the weight table)
+    plans = [w.Plan(net, precision=w.WMC_SCALED_FP32, block_fp=1)]
+    with pytest.raises(w._abi.WmcError):
+        w.Batch(plans)
+
+
 # ------------------------------------------------------ clause factoring
 
 def _long_clause_cnf(n, n_short, n_long, k_long, seed):
