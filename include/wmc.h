@@ -334,9 +334,10 @@ void wmc_set_autotune(int32_t on);
  * nonzero when C will be 16-byte aligned): *n receives their number, the
  * first min(*n, max_n) are written to kinds / blocks (kind 0 generic, 1
  * streaming, 2 TMA-staged streaming, 3 tiled dense, 4 outer-product dense,
- * 5 tensor-core dense, 6 tiled dense with a split summed range; blocks 0 =
- * the kernel's own count, else the block count (kind 1) or blocks per SM
- * (kind 2)); the fixed rule's variant is listed first; *chosen is the index
+ * 5 tensor-core dense, 6 tiled dense with a split summed range, 7
+ * streaming with four units per thread; blocks 0 = the kernel's own
+ * count, else the block count (kinds 1, 7) or blocks per SM (kind 2)); the
+ * fixed rule's variant is listed first; *chosen is the index
  * of the one wmc_contract_pair uses now (the tuned one once measured).
  * Host only.  Errors: WMC_EINVAL. */
 int wmc_pair_variants(int32_t precision, int32_t rank_a, const int32_t *labels_a,

@@ -268,7 +268,7 @@ def contract_pair(precision: int, labels_a, a, labels_b, b, labels_c, c,
 
 
 PAIR_KINDS = {0: "k1_generic", 1: "k2_stream", 2: "k2_tma", 3: "k4_dense", 4: "k4_outer", 5: "k4_tc",
-              6: "k4_dense split"}
+              6: "k4_dense split", 7: "k2_stream_s16q"}
 
 
 def pair_variants(precision: int, labels_a, labels_b, labels_c, c_aligned16: bool = True):

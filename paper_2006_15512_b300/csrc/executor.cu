@@ -2315,7 +2315,7 @@ cudaError_t launch_k4_tc(const dev::K4Params &p4, cudaStream_t s) {
 
 namespace {
 
-enum PairKind { PK_K1 = 0, PK_K2 = 1, PK_K2T = 2, PK_K4D = 3, PK_K4O = 4, PK_K4TC = 5, PK_K4SPLIT = 6 };
+enum PairKind { PK_K1 = 0, PK_K2 = 1, PK_K2T = 2, PK_K4D = 3, PK_K4O = 4, PK_K4TC = 5, PK_K4SPLIT = 6, PK_K2Q = 7 };
 
 struct PairChoice {
   int kind = PK_K1;
@@ -2333,6 +2333,7 @@ struct PairSetup {
   bool k2 = false, use_a = true;
   K2Params p2;
   int vmax = 1, kmax = 1, fmax = 1;
+  bool quad = false;  // k2_stream_s16q applies (four units per thread)
   bool k2t = false;
   wmc::dev::K2TParams k2tp;
   size_t k2t_smem = 0;
@@ -2360,6 +2361,16 @@ void pair_setup(PairSetup &ps) {
     ps.p2.ma = ps.use_a ? ma : mb; ps.p2.mb = ps.use_a ? mb : ma; ps.p2.mc = mc;
     ps.k2t = try_k2_tma(ps.p2, ps.use_a ? ps.LA : ps.LB, ps.use_a ? ps.LB : ps.LA, ps.f64, false, false, 1,
                         ps.k2tp, ps.k2t_smem);
+    // four units per thread: float32 with S staged, the units' two lowest
+    // bits P's and C's two lowest bits, S independent of them
+    {
+      const K2Params &q = ps.p2;
+      bool ok = !ps.f64 && q.s_staged && q.vbits == 0 && q.log2_nu >= 2 && q.f >= 1;
+      for (int i = 0; i < q.n_insA && ok; ++i) ok = q.insA[i] >= 2;
+      for (int i = 0; i < q.n_insC && ok; ++i) ok = q.insC[i] >= 2;
+      for (int i = 0; i < q.n_seg && ok; ++i) ok = q.seg_c[i] >= 2;
+      ps.quad = ok && ((uintptr_t)ps.c & 15u) == 0 && (((uintptr_t)ps.p2.A) & 15u) == 0;
+    }
     if (ps.k2t) {
       ps.k2t_tiles = 1ull << (ps.p2.log2_nu + ps.p2.vbits - ps.k2tp.tb);
       const int kf = ps.p2.k + ps.p2.f;
@@ -2391,7 +2402,7 @@ PairChoice pair_default(const PairSetup &ps) {
     else if (g_outer.load() && ps.outer_blocks) ch.kind = PK_K4O;
     else ch.kind = ps.split_g ? PK_K4SPLIT : PK_K4D;
   } else if (ps.k2) {
-    ch.kind = ps.k2t ? PK_K2T : PK_K2;
+    ch.kind = ps.k2t ? PK_K2T : (ps.quad ? PK_K2Q : PK_K2);
   } else {
     ch.kind = PK_K1;
   }
@@ -2448,6 +2459,16 @@ int pair_enqueue(PairSetup &ps, const PairChoice &ch, cudaStream_t s) {
       g_launches.fetch_add(1);
       break;
     }
+    case PK_K2Q: {
+      const uint64_t nq = 1ull << (ps.p2.log2_nu - 2);
+      const int64_t dflt = std::min<int64_t>((int64_t)((nq + dev::kThreads - 1) / dev::kThreads), 148 * 2);
+      const unsigned blocks = (unsigned)(ch.blocks > 0 ? std::min<int64_t>(dflt, ch.blocks) : dflt);
+      const size_t smem = sizeof(float) << ps.p2.s_log2;
+      if (ps.p2.s_contig) dev::k2_stream_s16q<true><<<blocks, dev::kThreads, smem, s>>>(ps.p2);
+      else dev::k2_stream_s16q<false><<<blocks, dev::kThreads, smem, s>>>(ps.p2);
+      g_launches.fetch_add(1);
+      break;
+    }
     case PK_K2: {
       Launch l;
       l.kind = L_K2; l.ti = f64 ? TD : TF; l.v = ps.vmax; l.kmax = ps.kmax; l.fmax = ps.fmax;
@@ -2488,6 +2509,7 @@ std::vector<PairChoice> pair_candidates(const PairSetup &ps, const PairChoice &d
     v.push_back(PairChoice{kind, blocks});
   };
   if (ps.k2) {
+    if (ps.quad) { add(PK_K2Q, 0); add(PK_K2Q, 148); }
     add(PK_K2, 0);
     const int64_t g = grid_for(1ull << ps.p2.log2_nu);
     for (int64_t m : {2, 4, 8})

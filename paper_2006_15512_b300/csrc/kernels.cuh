@@ -264,6 +264,7 @@ struct K2Params {
   int32_t s_staged;  // S (2^s_log2 entries) staged in shared memory, pre-scaled (k2_stream, K = 4)
   int32_t s_contig;  // staged, 4 summed bits at S's lowest 4 positions: 16-byte loads of S
   int32_t s_log2;
+  int32_t quad;      // staged float32, one query lane: four consecutive units per thread (k2_stream_s16q)
 };
 
 template <typename T, int V> struct VecT;
@@ -541,6 +542,100 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k2_stream_s1
   if (!first) publish(smax, smin, (int)(qbase & qmask_c), tmax, tmin);
   __syncthreads();
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
+// k2_stream_s16 with four consecutive work units per thread (float32, C
+// without query bits): when the two lowest bits of a unit are P's and C's
+// two lowest bits and S does not depend on them, the four units share
+// every S value, so each thread loads P's 16 summed entries of its four
+// units as 16-byte vectors, uses each staged S value for four outputs and
+// stores four outputs with one 16-byte store.  Each output adds its terms
+// in the same order as k2_stream_s16 (one FMA per summed assignment in
+// ascending order, operands scaled first), so the bits are the same.
+template <bool CONTIG>
+__global__ void __launch_bounds__(kThreads, 2) k2_stream_s16q(K2Params p) {
+  extern __shared__ __align__(16) unsigned char k2s_smem[];
+  __shared__ unsigned long long smax[1], smin[1];
+  if (threadIdx.x == 0) { smax[0] = 0; smin[0] = kNoMin; }
+  float *sS = reinterpret_cast<float *>(k2s_smem);
+  {
+    const float *Bg = (const float *)p.B;
+    for (uint32_t j = threadIdx.x; j < (1u << p.s_log2); j += blockDim.x)
+      sS[j] = p.mc.scale_inputs ? __ldg(Bg + j) * operand_scale<float>(p.mb, 0, 1) : __ldg(Bg + j);
+  }
+  __syncthreads();
+  constexpr int K = 4, NS = 16;
+  const int ns = 1 << p.k, nf = 1 << p.f;
+  const float *A = (const float *)p.A;
+  float *C = (float *)p.C;
+  const uint64_t nq = 1ull << (p.log2_nu - 2);  // quads of units
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const float sa = p.mc.scale_inputs ? operand_scale<float>(p.ma, 0, 1) : 1.0f;
+  float tmax = 0.0f, tmin = INFINITY;
+  uint32_t bsv[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) bsv[s] = (!CONTIG && s < ns) ? p.dBs[s] : 0u;
+  for (uint64_t qd = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; qd < nq; qd += stride) {
+    const uint32_t u = (uint32_t)(qd << 2);
+    uint32_t oa = u, oc = u, gb = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if (i < p.n_insA) oa = insert0(oa, p.insA[i]);
+      if (i < p.n_insC) oc = insert0(oc, p.insC[i]);
+    }
+    for (int i = 0; i < p.n_seg; ++i)
+      gb |= ((oc >> p.seg_c[i]) & ((1u << p.seg_len[i]) - 1u)) << p.seg_b[i];
+    float a[NS][4];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s < ns) v = __ldg(reinterpret_cast<const float4 *>(A + oa + p.dA[s]));
+      a[s][0] = v.x * sa; a[s][1] = v.y * sa; a[s][2] = v.z * sa; a[s][3] = v.w * sa;
+    }
+#pragma unroll 1
+    for (int f = 0; f < nf; f += 2) {
+      // two outputs of S-free assignments f, f + 1 for the four units
+      const float *s0 = sS + gb + p.dBf[f], *s1 = sS + gb + p.dBf[f + 1];
+      float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+      if constexpr (CONTIG) {
+#pragma unroll
+        for (int g4 = 0; g4 < NS; g4 += 4) {
+          float v0[4], v1[4];
+          lds4(s0 + g4, v0);
+          lds4(s1 + g4, v1);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              c0[e] = fma_t(a[g4 + r][e], v0[r], c0[e]);
+              c1[e] = fma_t(a[g4 + r][e], v1[r], c1[e]);
+            }
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+          if (s < ns) {
+            const float v0 = s0[bsv[s]], v1 = s1[bsv[s]];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              c0[e] = fma_t(a[s][e], v0, c0[e]);
+              c1[e] = fma_t(a[s][e], v1, c1[e]);
+            }
+          }
+      }
+      __stcs(reinterpret_cast<float4 *>(C + oc + p.dC[f]), make_float4(c0[0], c0[1], c0[2], c0[3]));
+      if (f + 1 < nf)
+        __stcs(reinterpret_cast<float4 *>(C + oc + p.dC[f + 1]), make_float4(c1[0], c1[1], c1[2], c1[3]));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        track(c0[e], tmax, tmin);
+        if (f + 1 < nf) track(c1[e], tmax, tmin);
+      }
+    }
+  }
+  publish_warp(smax, smin, 0, tmax, tmin, 1);
+  __syncthreads();
+  finish_meta<float>(p.ma, p.mb, p.mc, smax, smin);
 }
 
 // ------------------------------------------------- K2 with TMA staging
