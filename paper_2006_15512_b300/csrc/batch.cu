@@ -261,9 +261,12 @@ __device__ __forceinline__ void stream_geom(const BNode &nd, StreamGeom &g) {
     }
   }
   __syncthreads();
-  const int cl = nd.chunk_log2;
+  // scalar path: rows over u-local bits 0-7 and 8-15; vector path (groups
+  // of four u): bits 2-9 and 10-17, so that consecutive threads, which take
+  // consecutive groups, read consecutive entries (no bank conflicts)
+  const int cl = nd.chunk_log2, lo = nd.vec4 ? 2 : 0;
   for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255, base = (row & 1) * 8;
+    const int row = i >> 8, v = i & 255, base = lo + (row & 1) * 8;
     const int8_t *pos = row < 2 ? g.uc : (row < 4 ? g.ua : g.us);
     uint32_t o = 0;
     for (int b = 0; b < 8 && base + b < cl; ++b)
@@ -303,21 +306,28 @@ __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, cons
     if (nd.vec4) {
       // four consecutive u per group (C's and A's two lowest bits), two
       // groups per step with their loads issued first
-      for (uint32_t l0 = 8 * threadIdx.x; l0 < n_loc; l0 += 8 * blockDim.x) {
+      // groups g of four u (l = 4 g): a thread takes groups g0 and
+      // g0 + blockDim, so a warp's table reads are consecutive entries
+      const uint32_t n_grp = n_loc >> 2;
+      for (uint32_t g0 = threadIdx.x; g0 < n_grp; g0 += 2 * blockDim.x) {
         float4 a4[2][NS];
         uint32_t cb[2], sbx[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const uint32_t l = l0 + 4 * q;
-          const uint32_t ab = bA | g.lut[2][l & 255] | g.lut[3][l >> 8];
-          cb[q] = bC | g.lut[0][l & 255] | g.lut[1][l >> 8];
-          sbx[q] = bS | g.lut[4][l & 255] | g.lut[5][l >> 8];
+          // the second group is past the task when it has fewer than
+          // 2 blockDim groups (n_grp is a power of two)
+          const uint32_t gi = g0 + q * blockDim.x;
+          const uint32_t gv = gi < n_grp ? gi : g0;
+          const uint32_t ab = bA | g.lut[2][gv & 255] | g.lut[3][gv >> 8];
+          cb[q] = bC | g.lut[0][gv & 255] | g.lut[1][gv >> 8];
+          sbx[q] = bS | g.lut[4][gv & 255] | g.lut[5][gv >> 8];
 #pragma unroll
           for (int sidx = 0; sidx < NS; ++sidx)
             a4[q][sidx] = __ldcg(reinterpret_cast<const float4 *>(A + (ab | g.as[sidx])));
         }
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
+          if (q == 1 && g0 + blockDim.x >= n_grp) break;
           float a[NS][4];
 #pragma unroll
           for (int sidx = 0; sidx < NS; ++sidx) {
