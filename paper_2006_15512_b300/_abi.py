@@ -155,6 +155,7 @@ EXPORTS = {
     "wmc_set_outer_products": (None, [c_i32]),
     "wmc_set_fp64_fallback": (None, [c_i32]),
     "wmc_set_chain_runs": (None, [c_i32]),
+    "wmc_set_cta_walk": (None, [c_i32]),
     "wmc_set_batch_schedule": (None, [c_i32, c_i32]),
 }
 

@@ -46,6 +46,7 @@ static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run 
 // launch, which measured faster at every batch size on the grid walks)
 static std::atomic<int32_t> g_chain_runs{0};
 static std::atomic<int32_t> g_autotune{0};  // wmc_contract_pair: time same-order variants per shape
+static std::atomic<int32_t> g_cta_walk{1};  // small formulas: the whole walk in one block
 static std::atomic<int32_t> g_force_kind{-1};  // test hook: force one variant (-1: off)
 static std::atomic<int64_t> g_force_blocks{0};
 
@@ -60,6 +61,7 @@ static std::atomic<int32_t> g_outer{1};  // short summed ranges: k4_outer in pla
 extern "C" void wmc_set_outer_products(int32_t on) { g_outer.store(on); }
 extern "C" void wmc_set_fp64_fallback(int32_t on) { g_fp64_fallback.store(on); }
 extern "C" void wmc_set_chain_runs(int32_t max_tiles) { g_chain_runs.store(max_tiles < 0 ? 0 : max_tiles); }
+extern "C" void wmc_set_cta_walk(int32_t on) { g_cta_walk.store(on ? 1 : 0); }
 
 #define CUDA_TRY(x)                                                              \
   do {                                                                           \
@@ -92,7 +94,7 @@ constexpr int64_t kAlign = 256;
 inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ,
-            L_BFP, L_BFPW };
+            L_BFP, L_BFPW, L_CTA };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -136,6 +138,7 @@ struct WalkOpts {
   int32_t fuse = 4;         // longest chain of frontier eliminations per pass (0 or 1: none)
   int32_t small_phase = 1;  // small-node phase
   int32_t chain_runs = 0;   // runs of chains in one launch: max tiles (0: off)
+  int32_t cta_walk = 1;     // a small formula's whole walk in one block (when it fits)
 };
 
 struct ExecState {
@@ -145,6 +148,12 @@ struct ExecState {
   int32_t bfp_b = -1;
   std::vector<int64_t> t_eoff;
   std::vector<int8_t> t_bb;
+  // one-block walk: leaf descriptors (its node program is h_snodes), the
+  // shared memory it needs (metadata + tensor arena)
+  std::vector<wmc::dev::CtaLeaf> h_cta;
+  wmc::dev::CtaLeaf *d_cta = nullptr;
+  int64_t cta_smem = 0;
+  std::vector<int64_t> cta_off;  // shared-memory arena offset per tensor (-1: none; the root: none)
   uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
   int32_t Qp = 1;  // Q padded to 2^m: the query index is m bits
@@ -196,7 +205,7 @@ struct ExecState {
     for (auto &g : graphs) cudaGraphExecDestroy(g.second);
     if (capture_stream) cudaStreamDestroy(capture_stream);
     cudaFree(d_clause); cudaFree(d_first); cudaFree(d_woff); cudaFree(d_wmeta);
-    cudaFree(d_snodes); cudaFree(d_stasks); cudaFree(d_seq);
+    cudaFree(d_snodes); cudaFree(d_stasks); cudaFree(d_seq); cudaFree(d_cta);
     cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant); cudaFree(d_res_exp); cudaFree(d_res_flags);
     cudaFreeHost(h_res_mant); cudaFreeHost(h_res_exp); cudaFreeHost(h_res_flags);
   }
@@ -766,6 +775,7 @@ static WalkOpts walk_opts_now() {
   wo.fuse = g_fuse.load();
   wo.small_phase = g_small_phase.load();
   wo.chain_runs = g_chain_runs.load();
+  wo.cta_walk = g_cta_walk.load();
   return wo;
 }
 
@@ -833,6 +843,29 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   // at most 2^8 summed terms)
   std::vector<int32_t> sp_index(plan.nodes.size(), -1);
   std::vector<int64_t> sp_nodes;
+  // one-block walk: every node small, the live tensors within shared memory
+  bool cta = st.wo.cta_walk && !plain && st.bfp_b < 0 && Qp <= 4 && slots <= 1536 && !plan.nodes.empty();
+  std::vector<int64_t> cta_off(cta ? nt : 0, -1);
+  int64_t cta_meta = align_up(24 * slots);
+  if (cta) {
+    for (const Node &nd : plan.nodes) {
+      const TensorInfo &C = plan.tensors[(size_t)nd.c];
+      if ((int)C.labels.size() + (C.has_q ? m : 0) > 16 || nd.n_summed > 8) { cta = false; break; }
+    }
+  }
+  if (cta) {
+    FirstFit sf;  // leaves first, then each node's output; children freed after their node
+    for (int64_t i = 0; i < plan.n_leaves; ++i) cta_off[(size_t)i] = sf.alloc(bytes[(size_t)i]);
+    for (size_t ni = 0; ni + 1 < plan.nodes.size(); ++ni) {  // the root goes to the workspace
+      const Node &nd = plan.nodes[ni];
+      cta_off[(size_t)nd.c] = sf.alloc(bytes[(size_t)nd.c]);
+      sf.release(cta_off[(size_t)nd.a], bytes[(size_t)nd.a]);
+      sf.release(cta_off[(size_t)nd.b], bytes[(size_t)nd.b]);
+    }
+    if (cta_meta + align_up(sf.top) > 200 * 1024) cta = false;
+    else st.cta_smem = cta_meta + align_up(sf.top);
+  }
+  if (cta) { st.wo.small_phase = 0; st.cta_off = cta_off; }
   if (st.wo.small_phase && !plain) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       const Node &nd = plan.nodes[ni];
@@ -1267,6 +1300,68 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   fin.meta_c = st.t_meta[(size_t)root];
   fin.blocks = grid_for((uint64_t)Q);
   st.launches.push_back(fin);
+  if (cta) {
+    // the whole walk in one block: the metadata clears, the walk, the root
+    st.h_snodes.clear();
+    st.h_stasks.clear();
+    st.h_cta.clear();
+    for (int64_t i = 0; i < plan.n_leaves; ++i) {
+      const TensorInfo &t = plan.tensors[(size_t)i];
+      wmc::dev::CtaLeaf L;
+      std::memset(&L, 0, sizeof(L));
+      L.off = (uint32_t)cta_off[(size_t)i];
+      L.slot = (int32_t)st.t_meta[(size_t)i];
+      L.kind = t.kind;
+      L.rank = (int32_t)t.labels.size();
+      if (t.kind == LEAF_CLAUSE) {
+        L.fals = t.fals;
+        L.smask = t.clause >= 0 ? plan.clauses[(size_t)t.clause].smask : 0u;
+        L.sfals = t.clause >= 0 ? plan.clauses[(size_t)t.clause].sfals : 0u;
+      } else if (t.kind == LEAF_WEIGHT) {
+        L.var = t.labels[0];
+      }
+      st.h_cta.push_back(L);
+    }
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+      const Node &nd = plan.nodes[ni];
+      const TensorInfo &A = plan.tensors[(size_t)nd.a], &B = plan.tensors[(size_t)nd.b];
+      const TensorInfo &C = plan.tensors[(size_t)nd.c];
+      const bool is_root = nd.c == root;
+      wmc::dev::SNode sn;
+      std::memset(&sn, 0, sizeof(sn));
+      sn.a = cta_off[(size_t)nd.a];
+      sn.b = cta_off[(size_t)nd.b];
+      sn.c = is_root ? st.t_off[(size_t)nd.c] : cta_off[(size_t)nd.c];
+      sn.ma = st.t_meta[(size_t)nd.a]; sn.mb = st.t_meta[(size_t)nd.b]; sn.mc = st.t_meta[(size_t)nd.c];
+      sn.qmask_a = A.has_q ? Qp - 1 : 0;
+      sn.qmask_b = B.has_q ? Qp - 1 : 0;
+      sn.Qc = C.has_q ? Qp : 1;
+      sn.dep_a = sn.dep_b = -1;
+      int8_t pa[32], pb[32], spa[24], spb[24];
+      k1_bitmaps(full_labels(A, m), full_labels(B, m), full_labels(C, m), &sn.rC, &sn.k, pa, pb, spa, spb);
+      std::memcpy(sn.posA, pa, 16); std::memcpy(sn.posB, pb, 16);
+      std::memcpy(sn.sposA, spa, 8); std::memcpy(sn.sposB, spb, 8);
+      sn.n_chunks = 1;
+      sn.chunk_log2 = sn.rC;
+      sn.ti = st.f64 ? 1 : 0;
+      sn.to = st.t_dbl[(size_t)nd.c];
+      sn.ta = (st.f64 || is_root) ? 1 : 0;
+      st.h_snodes.push_back(sn);
+    }
+    std::vector<Launch> keep;
+    for (const Launch &l : st.launches)
+      if (l.kind == L_MEMSET && (l.memset_off == st.off_flags || l.memset_off == st.off_min)) keep.push_back(l);
+    Launch w;
+    w.kind = L_CTA;
+    w.blocks = 1;
+    w.smem = (size_t)st.cta_smem;
+    double alg = 0;
+    for (const Launch &l : st.launches) alg += l.alg_bytes;
+    w.alg_bytes = alg;
+    keep.push_back(w);
+    keep.push_back(fin);
+    st.launches.swap(keep);
+  }
   st.kernels_per_run = 0;
   for (auto &l : st.launches) st.kernels_per_run += (l.kind != L_MEMSET);
   return WMC_OK;
@@ -1456,6 +1551,7 @@ static int ensure_dev(ExecState &st) {
   if ((rc = up((void **)&st.d_snodes, st.h_snodes.data(), sizeof(wmc::dev::SNode) * st.h_snodes.size()))) return rc;
   if ((rc = up((void **)&st.d_stasks, st.h_stasks.data(), sizeof(wmc::dev::STask) * st.h_stasks.size()))) return rc;
   if ((rc = up((void **)&st.d_seq, st.h_seq.data(), sizeof(wmc::dev::K2CParams) * st.h_seq.size()))) return rc;
+  if ((rc = up((void **)&st.d_cta, st.h_cta.data(), sizeof(wmc::dev::CtaLeaf) * st.h_cta.size()))) return rc;
   CUDA_TRY(cudaStreamCreateWithFlags(&st.capture_stream, cudaStreamNonBlocking));
   st.dev_ready = true;
   return WMC_OK;
@@ -1469,11 +1565,12 @@ struct LeafTables {
   const wmc::dev::SNode *snodes;
   const wmc::dev::STask *stasks;
   const wmc::dev::K2CParams *seq;
+  const wmc::dev::CtaLeaf *cta;
 };
 
 static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
                          cudaEvent_t *events = nullptr, const LeafTables *tables = nullptr) {
-  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta, st.d_snodes, st.d_stasks, st.d_seq};
+  const LeafTables own{st.d_clause, st.d_first, st.d_woff, st.d_wmeta, st.d_snodes, st.d_stasks, st.d_seq, st.d_cta};
   const LeafTables &tb = tables ? *tables : own;
   int64_t *mexp = (int64_t *)(ws + st.off_exp);
   unsigned long long *mmax = (unsigned long long *)(ws + st.off_max);
@@ -1594,6 +1691,30 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
         p.mc.flags = flags;
         launch_k2(l, p, s);
+        break;
+      }
+      case L_CTA: {
+        wmc::dev::CtaArgs a;
+        a.ws = ws;
+        a.nodes = tb.snodes;
+        a.leaves = tb.cta;
+        a.io = io;
+        a.flags = flags;
+        a.gexp = mexp;
+        a.n_nodes = (int32_t)st.h_snodes.size();
+        a.n_leaves = (int32_t)st.h_cta.size();
+        a.n_slots = (int32_t)st.n_slots;
+        a.n_vars = plan.n_vars;
+        a.Q = st.Q;
+        a.Qp = st.Qp;
+        a.f64 = st.f64 ? 1 : 0;
+        a.meta_bytes = (uint32_t)align_up(24 * st.n_slots);
+        static bool attr_set = false;  // opt in to large dynamic shared memory once
+        if (!attr_set) {
+          cudaFuncSetAttribute(dev::k_cta_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+          attr_set = true;
+        }
+        dev::k_cta_walk<<<1, 1024, l.smem, s>>>(a);
         break;
       }
       case L_BFPW:
@@ -2009,7 +2130,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = (l.kind == L_K1 || l.kind == L_BFP) ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_CTA ? 10 : (l.kind == L_K1 || l.kind == L_BFP) ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -2749,13 +2870,15 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   const size_t b_sn = sizeof(wmc::dev::SNode) * st->h_snodes.size();
   const size_t b_stk = sizeof(wmc::dev::STask) * st->h_stasks.size();
   const size_t b_seq = sizeof(wmc::dev::K2CParams) * st->h_seq.size();
+  const size_t b_cta = sizeof(wmc::dev::CtaLeaf) * st->h_cta.size();
   const size_t o_first = (size_t)align_up((int64_t)b_clause);
   const size_t o_woff = o_first + (size_t)align_up((int64_t)b_first);
   const size_t o_wmeta = o_woff + (size_t)align_up((int64_t)b_woff);
   const size_t o_sn = o_wmeta + (size_t)align_up((int64_t)b_wmeta);
   const size_t o_stk = o_sn + (size_t)align_up((int64_t)b_sn);
   const size_t o_seq = o_stk + (size_t)align_up((int64_t)b_stk);
-  const size_t o_ws = o_seq + (size_t)align_up((int64_t)b_seq);
+  const size_t o_cta = o_seq + (size_t)align_up((int64_t)b_seq);
+  const size_t o_ws = o_cta + (size_t)align_up((int64_t)b_cta);
   const size_t need = o_ws + (size_t)st->ws_bytes;
   if (need > kNoAllocScratchBytes) {
     set_error("this plan needs %zu bytes of scratch at Q = %d; the static scratch holds %zu",
@@ -2778,7 +2901,7 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
     if (up(0, st->h_clause.data(), b_clause) || up(o_first, st->h_first.data(), b_first) ||
         up(o_woff, st->h_woff.data(), b_woff) || up(o_wmeta, st->h_wmeta.data(), b_wmeta) ||
         up(o_sn, st->h_snodes.data(), b_sn) || up(o_stk, st->h_stasks.data(), b_stk) ||
-        up(o_seq, st->h_seq.data(), b_seq)) {
+        up(o_seq, st->h_seq.data(), b_seq) || up(o_cta, st->h_cta.data(), b_cta)) {
       set_error("copying the leaf tables into the static scratch failed: %s",
                 cudaGetErrorString(cudaGetLastError()));
       return WMC_ECUDA;
@@ -2790,7 +2913,8 @@ extern "C" int wmc_execute_device_noalloc(wmc_plan_t *plan, int32_t Q, const dou
   const LeafTables tables{(const ClauseLeaf *)base, (const int64_t *)(base + o_first),
                           (const int64_t *)(base + o_woff), (const int64_t *)(base + o_wmeta),
                           (const wmc::dev::SNode *)(base + o_sn), (const wmc::dev::STask *)(base + o_stk),
-                          (const wmc::dev::K2CParams *)(base + o_seq)};
+                          (const wmc::dev::K2CParams *)(base + o_seq),
+                          (const wmc::dev::CtaLeaf *)(base + o_cta)};
   // the walk's first launch zeroes the flags and metadata it accumulates
   // into; one walk per slice assignment (index slicing), the later ones
   // adding into the outputs
@@ -2837,12 +2961,22 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
       if (sn.sposB[j] >= 0) mb |= 1ll << sn.sposB[j];
     }
     const int64_t esi = sn.ti ? 8 : 4, eso = sn.to ? 8 : 4;
-    auto within = [&](int64_t off, int64_t last_elem, int64_t es) {
+    const bool cta = !st->h_cta.empty();
+    const bool cta_root = cta && i + 1 == st->h_snodes.size();
+    auto within = [&](int64_t off, int64_t last_elem, int64_t es, bool shared) {
+      if (shared) {  // one-block walk: a tensor of the shared-memory arena
+        const int64_t arena = st->cta_smem - align_up(24 * st->n_slots);
+        for (size_t t = 0; t < st->cta_off.size(); ++t)
+          if (st->cta_off[t] == off && (last_elem + 1) * es <= st->t_bytes[t] && off + st->t_bytes[t] <= arena)
+            return true;
+        return false;
+      }
       for (size_t t = 0; t < st->t_off.size(); ++t)
         if (st->t_off[t] == off && (last_elem + 1) * es <= st->t_bytes[t]) return true;
       return false;
     };
-    if (!within(sn.a, ma, esi) || !within(sn.b, mb, esi) || !within(sn.c, (1ll << sn.rC) - 1, eso)) {
+    if (!within(sn.a, ma, esi, cta) || !within(sn.b, mb, esi, cta) ||
+        !within(sn.c, (1ll << sn.rC) - 1, eso, cta && !cta_root)) {
       set_error("small-phase node %zu: an offset leaves its tensor", i);
       return WMC_EINVAL;
     }

@@ -2776,6 +2776,191 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int
   }
 }
 
+// ------------------------------------------------------ one-CTA walk
+//
+// A formula whose whole tree is small (every node at most 2^16 outputs
+// with the query bits and 2^8 summed terms) and whose live tensors fit in
+// one block's shared memory runs as ONE block: the leaves are materialised
+// in shared memory, then the nodes run one after the other in post-order
+// with a block barrier between them -- no launches, no dependency waits
+// through global memory, no L2 round trips on the walk's critical path.
+// Every node computes exactly what the small-node phase computes (the same
+// operand scales, terms in ascending summed order, the same max/min and
+// exponents), so the results are the same bits.  The root is written to
+// the workspace for the finaliser.
+
+struct CtaLeaf {
+  uint64_t fals;      // clause: the falsifying assignment
+  uint32_t off;       // byte offset in the block's tensor arena
+  int32_t slot;       // metadata slot (per lane: slot + q)
+  int32_t kind;       // LEAF_CLAUSE 0, LEAF_WEIGHT 1, LEAF_ONE 2
+  int32_t rank;       // clause: its indices
+  int32_t var;        // weight vector: its variable
+  uint32_t smask, sfals;  // clause: sliced literals (index slicing)
+  int32_t pad;
+};
+
+struct CtaArgs {
+  char *ws;                   // workspace: the root's data and exponent slots
+  const SNode *nodes;         // post-order; a, b, c are arena byte offsets (the root's c: workspace)
+  const CtaLeaf *leaves;
+  const IoDesc *io;
+  uint32_t *flags;            // per-lane flags (workspace)
+  int64_t *gexp;              // workspace exponent slots (the root's are read by the finaliser)
+  int32_t n_nodes, n_leaves, n_slots;
+  int32_t n_vars, Q, Qp;
+  int32_t f64;
+  uint32_t meta_bytes;        // shared memory before the arena: exp, max, min per slot
+};
+
+template <typename TI, typename TA, typename TO>
+__device__ void cta_node(const CtaArgs &a, const SNode &nd, unsigned char *arena, int64_t *mexp,
+                         unsigned long long *mmax, unsigned long long *mmin, uint32_t (*lut)[256],
+                         TA *scl, unsigned long long *smax, unsigned long long *smin, bool root) {
+  const TI *A = (const TI *)(arena + nd.a);
+  const TI *B = (const TI *)(arena + nd.b);
+  TO *C = root ? (TO *)(a.ws + nd.c) : (TO *)(arena + nd.c);
+  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
+    const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+    const unsigned long long xa = mmax[nd.ma + qa], xb = mmax[nd.mb + qb];
+    scl[q] = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
+    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
+    smax[q] = 0;
+    smin[q] = kNoMin;
+    const int64_t e = mexp[nd.ma + qa] + pow2_exp_of(xa, TI()) + mexp[nd.mb + qb] + pow2_exp_of(xb, TI());
+    mexp[nd.mc + q] = e;
+    if (root) a.gexp[nd.mc + q] = e;
+    const unsigned long long na = mmin[nd.ma + qa], nb = mmin[nd.mb + qb];
+    if (na != kNoMin && nb != kNoMin) {
+      const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
+                    (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
+      if (below_normal(lo)) {
+        if (nd.Qc > 1) atomicOr(a.flags + q, 2u);
+        else
+          for (int qq = 0; qq < a.Qp; ++qq) atomicOr(a.flags + qq, 2u);
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t n_out = 1u << nd.rC, ns = 1u << nd.k;
+  for (uint32_t o = threadIdx.x; o < n_out; o += blockDim.x) {
+    const uint32_t bA = lut[0][o & 255] | lut[1][o >> 8];
+    const uint32_t bB = lut[2][o & 255] | lut[3][o >> 8];
+    const int q = (int)(o & (uint32_t)(nd.Qc - 1));
+    const TA sa = scl[q], sb = scl[nd.Qc + q];
+    TA acc = (TA)0;
+    for (uint32_t s = 0; s < ns; ++s) acc = fma_t((TA)A[bA | lut[4][s]] * sa, (TA)B[bB | lut[5][s]] * sb, acc);
+    const TO c = (TO)acc;
+    C[o] = c;
+    const unsigned long long bits = abs_bits(c);
+    if (bits) {
+      atomicMax(smax + q, bits);
+      atomicMin(smin + q, bits);
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
+    mmax[nd.mc + q] = smax[q];
+    mmin[nd.mc + q] = smin[q];
+  }
+}
+
+__global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
+  extern __shared__ __align__(16) unsigned char cta_smem[];
+  __shared__ uint32_t lut[6][256];
+  __shared__ double scl[2 * 4];
+  __shared__ unsigned long long smax[4], smin[4];
+  int64_t *mexp = (int64_t *)cta_smem;
+  unsigned long long *mmax = (unsigned long long *)(cta_smem + 8 * (size_t)a.n_slots);
+  unsigned long long *mmin = (unsigned long long *)(cta_smem + 16 * (size_t)a.n_slots);
+  unsigned char *arena = cta_smem + a.meta_bytes;
+  for (int i = threadIdx.x; i < a.n_slots; i += blockDim.x) { mexp[i] = 0; mmax[i] = 0; mmin[i] = kNoMin; }
+  __syncthreads();
+  // ---- leaves (as k_clause_leaves, k_weight_leaves and k_one_leaf)
+  const uint32_t eta = (uint32_t)a.io->slice;
+  for (int li = 0; li < a.n_leaves; ++li) {
+    const CtaLeaf L = a.leaves[li];
+    if (L.kind == 0) {
+      const bool sat = ((eta ^ L.sfals) & L.smask) != 0u;
+      for (uint32_t e = threadIdx.x; e < (1u << L.rank); e += blockDim.x) {
+        const bool z = (e == (uint32_t)L.fals && !sat);
+        if (a.f64) ((double *)(arena + L.off))[e] = z ? 0.0 : 1.0;
+        else ((float *)(arena + L.off))[e] = z ? 0.0f : 1.0f;
+      }
+      if (threadIdx.x == 0) {
+        const bool zero = L.rank == 0 && !sat;
+        mmax[L.slot] = zero ? 0ull : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
+        mmin[L.slot] = zero ? kNoMin : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
+      }
+    } else if (L.kind == 1) {
+      for (int q = threadIdx.x; q < a.Qp; q += blockDim.x) {
+        const int qs = q < a.Q ? q : a.Q - 1;
+        const double w1 = a.io->w_pos[(int64_t)qs * a.n_vars + L.var];
+        const double w0 = a.io->w_neg[(int64_t)qs * a.n_vars + L.var];
+        const double m = fmax(fabs(w0), fabs(w1));
+        int e = 0;
+        if (m > 0) {
+          e = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023;
+          if (e < -1022) e = -1022;
+          if (e > 1022) e = 1022;
+        }
+        const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+        unsigned long long b0, b1;
+        bool flush;
+        if (a.f64) {
+          const double v0 = w0 * sc, v1 = w1 * sc;
+          ((double *)(arena + L.off))[q] = v0;
+          ((double *)(arena + L.off))[a.Qp + q] = v1;
+          b0 = abs_bits(v0); b1 = abs_bits(v1);
+          flush = ((w0 * sc != 0.0) && below_normal(v0)) || ((w1 * sc != 0.0) && below_normal(v1));
+        } else {
+          const float v0 = (float)(w0 * sc), v1 = (float)(w1 * sc);
+          ((float *)(arena + L.off))[q] = v0;
+          ((float *)(arena + L.off))[a.Qp + q] = v1;
+          b0 = abs_bits(v0); b1 = abs_bits(v1);
+          flush = ((w0 * sc != 0.0) && below_normal(v0)) || ((w1 * sc != 0.0) && below_normal(v1));
+        }
+        if (flush) atomicOr(a.flags + q, 2u);
+        mexp[L.slot + q] = e;
+        mmax[L.slot + q] = b0 > b1 ? b0 : b1;
+        const unsigned long long n0 = b0 ? b0 : kNoMin, n1 = b1 ? b1 : kNoMin;
+        mmin[L.slot + q] = n0 < n1 ? n0 : n1;
+      }
+    } else if (threadIdx.x == 0) {
+      if (a.f64) *(double *)(arena + L.off) = 1.0;
+      else *(float *)(arena + L.off) = 1.0f;
+      mmax[L.slot] = mmin[L.slot] = a.f64 ? abs_bits(1.0) : abs_bits(1.0f);
+    }
+  }
+  __syncthreads();
+  // ---- the nodes, in post-order
+  for (int ni = 0; ni < a.n_nodes; ++ni) {
+    const SNode &nd = a.nodes[ni];
+    for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
+      const int row = i >> 8, v = i & 255;
+      uint32_t o = 0;
+      for (int b = 0; b < 8; ++b) {
+        if (!((v >> b) & 1)) continue;
+        if (row < 4) {
+          const int j = (row & 1) * 8 + b;
+          const int8_t pos = row < 2 ? nd.posA[j] : nd.posB[j];
+          if (j < nd.rC && pos >= 0) o |= 1u << pos;
+        } else if (b < nd.k) {
+          const int8_t pos = row == 4 ? nd.sposA[b] : nd.sposB[b];
+          if (pos >= 0) o |= 1u << pos;
+        }
+      }
+      lut[row][v] = o;
+    }
+    __syncthreads();
+    const bool root = ni == a.n_nodes - 1;
+    if (nd.ti == 1) cta_node<double, double, double>(a, nd, arena, mexp, mmax, mmin, lut, scl, smax, smin, root);
+    else if (nd.to == 1) cta_node<float, double, double>(a, nd, arena, mexp, mmax, mmin, lut, scl, smax, smin, root);
+    else cta_node<float, float, float>(a, nd, arena, mexp, mmax, mmin, lut, reinterpret_cast<float *>(scl), smax, smin, root);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------ block floating point
 //
 // Block-floating-point float32 (a plan option): every tensor's entries are
