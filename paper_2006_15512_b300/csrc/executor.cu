@@ -46,7 +46,7 @@ static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run 
 // launch, which measured faster at every batch size on the grid walks)
 static std::atomic<int32_t> g_chain_runs{0};
 static std::atomic<int32_t> g_autotune{0};  // wmc_contract_pair: time same-order variants per shape
-static std::atomic<int32_t> g_cta_walk{1};  // small formulas: the whole walk in one block
+static std::atomic<int32_t> g_cta_walk{0};  // small formulas: the whole walk in one block (opt-in)
 static std::atomic<int32_t> g_force_kind{-1};  // test hook: force one variant (-1: off)
 static std::atomic<int64_t> g_force_blocks{0};
 
@@ -138,7 +138,7 @@ struct WalkOpts {
   int32_t fuse = 4;         // longest chain of frontier eliminations per pass (0 or 1: none)
   int32_t small_phase = 1;  // small-node phase
   int32_t chain_runs = 0;   // runs of chains in one launch: max tiles (0: off)
-  int32_t cta_walk = 1;     // a small formula's whole walk in one block (when it fits)
+  int32_t cta_walk = 0;     // a small formula's whole walk in one block (when it fits)
 };
 
 struct ExecState {
@@ -152,7 +152,7 @@ struct ExecState {
   // shared memory it needs (metadata + tensor arena)
   std::vector<wmc::dev::CtaLeaf> h_cta;
   wmc::dev::CtaLeaf *d_cta = nullptr;
-  int64_t cta_smem = 0;
+  int64_t cta_smem = 0, cta_meta = 0;  // total; before the arena
   std::vector<int64_t> cta_off;  // shared-memory arena offset per tensor (-1: none; the root: none)
   uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
@@ -846,7 +846,9 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   // one-block walk: every node small, the live tensors within shared memory
   bool cta = st.wo.cta_walk && !plain && st.bfp_b < 0 && Qp <= 4 && slots <= 1536 && !plan.nodes.empty();
   std::vector<int64_t> cta_off(cta ? nt : 0, -1);
-  int64_t cta_meta = align_up(24 * slots);
+  // shared memory: metadata, the node program, the leaf descriptors, the arena
+  int64_t cta_meta = align_up(24 * slots) + align_up((int64_t)sizeof(wmc::dev::SNode) * (int64_t)plan.nodes.size()) +
+                     align_up((int64_t)sizeof(wmc::dev::CtaLeaf) * plan.n_leaves);
   if (cta) {
     for (const Node &nd : plan.nodes) {
       const TensorInfo &C = plan.tensors[(size_t)nd.c];
@@ -865,7 +867,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     if (cta_meta + align_up(sf.top) > 200 * 1024) cta = false;
     else st.cta_smem = cta_meta + align_up(sf.top);
   }
-  if (cta) { st.wo.small_phase = 0; st.cta_off = cta_off; }
+  if (cta) { st.wo.small_phase = 0; st.cta_off = cta_off; st.cta_meta = cta_meta; }
   if (st.wo.small_phase && !plain) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       const Node &nd = plan.nodes[ni];
@@ -1708,7 +1710,9 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         a.Q = st.Q;
         a.Qp = st.Qp;
         a.f64 = st.f64 ? 1 : 0;
-        a.meta_bytes = (uint32_t)align_up(24 * st.n_slots);
+        a.nodes_off = (uint32_t)align_up(24 * st.n_slots);
+        a.leaves_off = a.nodes_off + (uint32_t)align_up((int64_t)sizeof(wmc::dev::SNode) * (int64_t)st.h_snodes.size());
+        a.meta_bytes = (uint32_t)st.cta_meta;
         static bool attr_set = false;  // opt in to large dynamic shared memory once
         if (!attr_set) {
           cudaFuncSetAttribute(dev::k_cta_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -2965,7 +2969,7 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     const bool cta_root = cta && i + 1 == st->h_snodes.size();
     auto within = [&](int64_t off, int64_t last_elem, int64_t es, bool shared) {
       if (shared) {  // one-block walk: a tensor of the shared-memory arena
-        const int64_t arena = st->cta_smem - align_up(24 * st->n_slots);
+        const int64_t arena = st->cta_smem - st->cta_meta;
         for (size_t t = 0; t < st->cta_off.size(); ++t)
           if (st->cta_off[t] == off && (last_elem + 1) * es <= st->t_bytes[t] && off + st->t_bytes[t] <= arena)
             return true;

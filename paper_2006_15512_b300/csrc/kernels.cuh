@@ -2810,23 +2810,28 @@ struct CtaArgs {
   int32_t n_nodes, n_leaves, n_slots;
   int32_t n_vars, Q, Qp;
   int32_t f64;
-  uint32_t meta_bytes;        // shared memory before the arena: exp, max, min per slot
+  uint32_t nodes_off, leaves_off;  // shared-memory offsets of the node program and the leaf descriptors
+  uint32_t meta_bytes;        // shared memory before the arena: metadata, program, leaves
 };
 
+// One node of the one-block walk.  Every thread's outputs share one query
+// lane (the block is 1024 threads and there are at most 4 lanes), so its
+// max and min are folded across the warp's lanes of that query before one
+// shared atomic per warp.
 template <typename TI, typename TA, typename TO>
 __device__ void cta_node(const CtaArgs &a, const SNode &nd, unsigned char *arena, int64_t *mexp,
-                         unsigned long long *mmax, unsigned long long *mmin, uint32_t (*lut)[256],
-                         TA *scl, unsigned long long *smax, unsigned long long *smin, bool root) {
+                         const unsigned long long *mmax, const unsigned long long *mmin, uint32_t (*lut)[256],
+                         unsigned long long *smax, unsigned long long *smin, bool root) {
   const TI *A = (const TI *)(arena + nd.a);
   const TI *B = (const TI *)(arena + nd.b);
   TO *C = root ? (TO *)(a.ws + nd.c) : (TO *)(arena + nd.c);
-  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
-    const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
-    const unsigned long long xa = mmax[nd.ma + qa], xb = mmax[nd.mb + qb];
-    scl[q] = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
-    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
-    smax[q] = 0;
-    smin[q] = kNoMin;
+  const int q = (int)(threadIdx.x & (uint32_t)(nd.Qc - 1));
+  const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+  const unsigned long long xa = mmax[nd.ma + qa], xb = mmax[nd.mb + qb];
+  const TA sa = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
+  const TA sb = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
+  if ((int)threadIdx.x < nd.Qc) {
+    // C's exponent and the float32 flush test, from the operands' metadata
     const int64_t e = mexp[nd.ma + qa] + pow2_exp_of(xa, TI()) + mexp[nd.mb + qb] + pow2_exp_of(xb, TI());
     mexp[nd.mc + q] = e;
     if (root) a.gexp[nd.mc + q] = e;
@@ -2841,59 +2846,72 @@ __device__ void cta_node(const CtaArgs &a, const SNode &nd, unsigned char *arena
       }
     }
   }
-  __syncthreads();
   const uint32_t n_out = 1u << nd.rC, ns = 1u << nd.k;
+  unsigned long long bmax = 0, bmin = kNoMin;
   for (uint32_t o = threadIdx.x; o < n_out; o += blockDim.x) {
     const uint32_t bA = lut[0][o & 255] | lut[1][o >> 8];
     const uint32_t bB = lut[2][o & 255] | lut[3][o >> 8];
-    const int q = (int)(o & (uint32_t)(nd.Qc - 1));
-    const TA sa = scl[q], sb = scl[nd.Qc + q];
     TA acc = (TA)0;
     for (uint32_t s = 0; s < ns; ++s) acc = fma_t((TA)A[bA | lut[4][s]] * sa, (TA)B[bB | lut[5][s]] * sb, acc);
     const TO c = (TO)acc;
     C[o] = c;
     const unsigned long long bits = abs_bits(c);
-    if (bits) {
-      atomicMax(smax + q, bits);
-      atomicMin(smin + q, bits);
-    }
+    bmax = bits > bmax ? bits : bmax;
+    if (bits) bmin = bits < bmin ? bits : bmin;
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
-    mmax[nd.mc + q] = smax[q];
-    mmin[nd.mc + q] = smin[q];
+  for (int o = 16; o >= nd.Qc; o >>= 1) {
+    const unsigned long long xm = __shfl_xor_sync(0xffffffffu, bmax, o);
+    const unsigned long long xn = __shfl_xor_sync(0xffffffffu, bmin, o);
+    bmax = xm > bmax ? xm : bmax;
+    bmin = xn < bmin ? xn : bmin;
+  }
+  if ((int)(threadIdx.x & 31u) < nd.Qc) {
+    if (bmax) atomicMax(smax + q, bmax);
+    if (bmin != kNoMin) atomicMin(smin + q, bmin);
   }
 }
 
 __global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
+  // dynamic shared memory: metadata (exp, max, min per slot), the node
+  // program, the leaf descriptors, then the tensor arena
   extern __shared__ __align__(16) unsigned char cta_smem[];
   __shared__ uint32_t lut[6][256];
-  __shared__ double scl[2 * 4];
   __shared__ unsigned long long smax[4], smin[4];
   int64_t *mexp = (int64_t *)cta_smem;
   unsigned long long *mmax = (unsigned long long *)(cta_smem + 8 * (size_t)a.n_slots);
   unsigned long long *mmin = (unsigned long long *)(cta_smem + 16 * (size_t)a.n_slots);
+  SNode *nodes = (SNode *)(cta_smem + a.nodes_off);
+  CtaLeaf *leaves = (CtaLeaf *)(cta_smem + a.leaves_off);
   unsigned char *arena = cta_smem + a.meta_bytes;
+  static_assert(sizeof(SNode) % 4 == 0 && sizeof(CtaLeaf) % 4 == 0, "copied as 32-bit words");
+  // the program into shared memory at once (one latency, not one per node)
+  {
+    const int nw = a.n_nodes * (int)(sizeof(SNode) / 4), lw = a.n_leaves * (int)(sizeof(CtaLeaf) / 4);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x)
+      reinterpret_cast<uint32_t *>(nodes)[i] = reinterpret_cast<const uint32_t *>(a.nodes)[i];
+    for (int i = threadIdx.x; i < lw; i += blockDim.x)
+      reinterpret_cast<uint32_t *>(leaves)[i] = reinterpret_cast<const uint32_t *>(a.leaves)[i];
+  }
   for (int i = threadIdx.x; i < a.n_slots; i += blockDim.x) { mexp[i] = 0; mmax[i] = 0; mmin[i] = kNoMin; }
+  if (threadIdx.x < 4) { smax[threadIdx.x] = 0; smin[threadIdx.x] = kNoMin; }
   __syncthreads();
-  // ---- leaves (as k_clause_leaves, k_weight_leaves and k_one_leaf)
+  // ---- leaves, one thread per leaf (as k_clause_leaves, k_weight_leaves
+  // and k_one_leaf)
   const uint32_t eta = (uint32_t)a.io->slice;
-  for (int li = 0; li < a.n_leaves; ++li) {
-    const CtaLeaf L = a.leaves[li];
+  for (int li = threadIdx.x; li < a.n_leaves; li += blockDim.x) {
+    const CtaLeaf &L = leaves[li];
     if (L.kind == 0) {
       const bool sat = ((eta ^ L.sfals) & L.smask) != 0u;
-      for (uint32_t e = threadIdx.x; e < (1u << L.rank); e += blockDim.x) {
+      for (uint32_t e = 0; e < (1u << L.rank); ++e) {
         const bool z = (e == (uint32_t)L.fals && !sat);
         if (a.f64) ((double *)(arena + L.off))[e] = z ? 0.0 : 1.0;
         else ((float *)(arena + L.off))[e] = z ? 0.0f : 1.0f;
       }
-      if (threadIdx.x == 0) {
-        const bool zero = L.rank == 0 && !sat;
-        mmax[L.slot] = zero ? 0ull : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
-        mmin[L.slot] = zero ? kNoMin : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
-      }
+      const bool zero = L.rank == 0 && !sat;
+      mmax[L.slot] = zero ? 0ull : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
+      mmin[L.slot] = zero ? kNoMin : (a.f64 ? abs_bits(1.0) : abs_bits(1.0f));
     } else if (L.kind == 1) {
-      for (int q = threadIdx.x; q < a.Qp; q += blockDim.x) {
+      for (int q = 0; q < a.Qp; ++q) {
         const int qs = q < a.Q ? q : a.Q - 1;
         const double w1 = a.io->w_pos[(int64_t)qs * a.n_vars + L.var];
         const double w0 = a.io->w_neg[(int64_t)qs * a.n_vars + L.var];
@@ -2926,38 +2944,45 @@ __global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
         const unsigned long long n0 = b0 ? b0 : kNoMin, n1 = b1 ? b1 : kNoMin;
         mmin[L.slot + q] = n0 < n1 ? n0 : n1;
       }
-    } else if (threadIdx.x == 0) {
+    } else {
       if (a.f64) *(double *)(arena + L.off) = 1.0;
       else *(float *)(arena + L.off) = 1.0f;
       mmax[L.slot] = mmin[L.slot] = a.f64 ? abs_bits(1.0) : abs_bits(1.0f);
     }
   }
-  __syncthreads();
-  // ---- the nodes, in post-order
+  // ---- the nodes, in post-order: tables, barrier, outputs, barrier
   for (int ni = 0; ni < a.n_nodes; ++ni) {
-    const SNode &nd = a.nodes[ni];
-    for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
-      const int row = i >> 8, v = i & 255;
-      uint32_t o = 0;
-      for (int b = 0; b < 8; ++b) {
-        if (!((v >> b) & 1)) continue;
-        if (row < 4) {
-          const int j = (row & 1) * 8 + b;
-          const int8_t pos = row < 2 ? nd.posA[j] : nd.posB[j];
-          if (j < nd.rC && pos >= 0) o |= 1u << pos;
-        } else if (b < nd.k) {
-          const int8_t pos = row == 4 ? nd.sposA[b] : nd.sposB[b];
-          if (pos >= 0) o |= 1u << pos;
-        }
+    const SNode &nd = nodes[ni];
+    // only the entries the node reads: output bits 0-7 (2^min(8, rC)),
+    // 8-15 (2^(rC - 8)), summed bits (2^k), for A and for B
+    {
+      const int rc = nd.rC, n0 = 1 << (rc < 8 ? rc : 8), n1 = 1 << (rc > 8 ? rc - 8 : 0), ns = 1 << nd.k;
+      const int total = 2 * (n0 + n1 + ns);
+      for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int op = i & 1, k = i >> 1;  // op 0: A, 1: B
+        int row, v, base, nb;
+        const int8_t *pos;
+        if (k < n0) { row = 2 * op; v = k; base = 0; nb = rc < 8 ? rc : 8; pos = op ? nd.posB : nd.posA; }
+        else if (k < n0 + n1) { row = 2 * op + 1; v = k - n0; base = 8; nb = rc - 8; pos = op ? nd.posB : nd.posA; }
+        else { row = 4 + op; v = k - n0 - n1; base = 0; nb = nd.k; pos = op ? nd.sposB : nd.sposA; }
+        uint32_t o = 0;
+        for (int b = 0; b < nb; ++b)
+          if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
+        lut[row][v] = o;
       }
-      lut[row][v] = o;
     }
-    __syncthreads();
+    __syncthreads();  // tables; the previous node's outputs and metadata (and the leaves)
     const bool root = ni == a.n_nodes - 1;
-    if (nd.ti == 1) cta_node<double, double, double>(a, nd, arena, mexp, mmax, mmin, lut, scl, smax, smin, root);
-    else if (nd.to == 1) cta_node<float, double, double>(a, nd, arena, mexp, mmax, mmin, lut, scl, smax, smin, root);
-    else cta_node<float, float, float>(a, nd, arena, mexp, mmax, mmin, lut, reinterpret_cast<float *>(scl), smax, smin, root);
-    __syncthreads();
+    if (nd.ti == 1) cta_node<double, double, double>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
+    else if (nd.to == 1) cta_node<float, double, double>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
+    else cta_node<float, float, float>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
+    __syncthreads();  // outputs, max and min
+    if ((int)threadIdx.x < nd.Qc) {
+      mmax[nd.mc + threadIdx.x] = smax[threadIdx.x];
+      mmin[nd.mc + threadIdx.x] = smin[threadIdx.x];
+      smax[threadIdx.x] = 0;
+      smin[threadIdx.x] = kNoMin;
+    }
   }
 }
 

@@ -862,19 +862,15 @@ def test_small_phase_matches_per_node_launches(w, precision, case):
         cnf, Q, order = wmcgen.psi_family(12), 3, None
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=14, lo=0.05, hi=0.95)
     try:
-        w.wmc_set_cta_walk(0)  # (small formulas would otherwise run as one block)
-        try:
-            w.wmc_set_small_phase(0)
-            plain = plan_for(w, cnf, None, None, precision)
-            a = plain.execute(wq, wnq)
-            n_plain = plain.info(Q).launches_per_walk
-        finally:
-            w.wmc_set_small_phase(1)
-        small = plan_for(w, cnf, None, None, precision)
-        b = small.execute(wq, wnq)
-        assert small.info(Q).launches_per_walk < n_plain
+        w.wmc_set_small_phase(0)
+        plain = plan_for(w, cnf, None, None, precision)
+        a = plain.execute(wq, wnq)
+        n_plain = plain.info(Q).launches_per_walk
     finally:
-        w.wmc_set_cta_walk(1)
+        w.wmc_set_small_phase(1)
+    small = plan_for(w, cnf, None, None, precision)
+    b = small.execute(wq, wnq)
+    assert small.info(Q).launches_per_walk < n_plain
     for q in range(Q):
         assert (a[q].mant, a[q].exp2, a[q].flags) == (b[q].mant, b[q].exp2, b[q].flags), q
     for q in (0, Q - 1):
@@ -891,14 +887,14 @@ def test_cta_walk_matches_small_phase(w, precision, Q, seed):
     launches."""
     cnf = wmcgen.random_kcnf(20, 60, seed=seed)
     wq, wnq = wmcgen.query_weights(20, Q, seed=30 + seed, lo=0.1, hi=0.9)
+    ref_plan = plan_for(w, cnf, None, None, precision)
+    ref = ref_plan.execute(wq, wnq)
     try:
-        w.wmc_set_cta_walk(0)
-        ref_plan = plan_for(w, cnf, None, None, precision)
-        ref = ref_plan.execute(wq, wnq)
-    finally:
         w.wmc_set_cta_walk(1)
-    plan = plan_for(w, cnf, None, None, precision)
-    got = plan.execute(wq, wnq)
+        plan = plan_for(w, cnf, None, None, precision)
+        got = plan.execute(wq, wnq)
+    finally:
+        w.wmc_set_cta_walk(0)
     assert plan.info(Q).launches_per_walk == 2 < ref_plan.info(Q).launches_per_walk  # the walk, the finaliser
     for q in range(Q):
         assert (got[q].mant, got[q].exp2, got[q].flags) == (ref[q].mant, ref[q].exp2, ref[q].flags), q

@@ -8,8 +8,8 @@ is running (both can synchronise the device).  It runs the same walk and
 kernels as wmc_execute_device on a static scratch array, so it must return
 the same bits, on two calls in a row (the second call finds the first
 call's contents still in the shared scratch), for plans with several slice
-assignments and with runs of chains, and after another plan has used the
-scratch in between.  It must reject plans that do not fit its fixed
+assignments, with runs of chains and with the one-block walk, and after
+another plan has used the scratch in between.  It must reject plans that do not fit its fixed
 scratch.
 
 This file is collected last so that a run stopping at its first failure
@@ -153,6 +153,23 @@ def test_noalloc_with_runs_of_chains(w):
     finally:
         w.wmc_set_chain_runs(0)
     _, _, dwp, dwn = _device_inputs(cnf, Q, 41)
+    want = _execute_device(plan, Q, dwp, dwn)
+    for _ in range(2):
+        _assert_same_bits(_execute_noalloc(w, plan, Q, dwp, dwn), want)
+
+
+def test_noalloc_with_one_block_walk(w):
+    """The one-block walk (its node program and leaf descriptors sit in the
+    scratch): same bits as the device entry."""
+    cnf = wmcgen.random_kcnf(20, 60, seed=2)
+    Q = 1
+    try:
+        w.wmc_set_cta_walk(1)
+        plan = w.Plan(w.Network.from_cnf(cnf), precision=0)
+        assert plan.info(Q).launches_per_walk == 2  # the walk and the finaliser
+    finally:
+        w.wmc_set_cta_walk(0)
+    _, _, dwp, dwn = _device_inputs(cnf, Q, 51)
     want = _execute_device(plan, Q, dwp, dwn)
     for _ in range(2):
         _assert_same_bits(_execute_noalloc(w, plan, Q, dwp, dwn), want)
