@@ -2542,11 +2542,21 @@ int pair_enqueue(PairSetup &ps, const PairChoice &ch, cudaStream_t s) {
     case PK_K4TC:
       CUDA_TRY(launch_k4_tc(ps.p4, s));
       return WMC_OK;
-    case PK_K4O:
-      if (f64) dev::k4_outer<double><<<(unsigned)ps.outer_blocks, 256, 0, s>>>(ps.p4);
-      else dev::k4_outer<float><<<(unsigned)ps.outer_blocks, 256, 0, s>>>(ps.p4);
+    case PK_K4O: {
+      const unsigned ob = (unsigned)ps.outer_blocks;
+      const int ns = ps.p4.ns;  // at most 2 summed bits (k4_outer_pick)
+      if (f64) {
+        if (ns == 0) dev::k4_outer<double, 1><<<ob, 256, 0, s>>>(ps.p4);
+        else if (ns == 1) dev::k4_outer<double, 2><<<ob, 256, 0, s>>>(ps.p4);
+        else dev::k4_outer<double, 4><<<ob, 256, 0, s>>>(ps.p4);
+      } else {
+        if (ns == 0) dev::k4_outer<float, 1><<<ob, 256, 0, s>>>(ps.p4);
+        else if (ns == 1) dev::k4_outer<float, 2><<<ob, 256, 0, s>>>(ps.p4);
+        else dev::k4_outer<float, 4><<<ob, 256, 0, s>>>(ps.p4);
+      }
       g_launches.fetch_add(1);
       break;
+    }
     case PK_K4D:
     case PK_K4SPLIT: {
       dev::K4Params p4 = ps.p4;

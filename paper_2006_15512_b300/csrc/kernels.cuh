@@ -2087,8 +2087,11 @@ __global__ void __launch_bounds__(256) k4_dense(K4Params p) {
 // entries are staged in shared memory; every output is written once.  The
 // summed terms are added as k4_dense adds them (fma chain over s in order
 // from 0, operands scaled first), so the values are the same bits.
-template <typename T>
+template <typename T, int NS>
 __global__ void __launch_bounds__(256) k4_outer(K4Params p) {
+  // NS = 2^ns summed terms, a template parameter: with a runtime count the
+  // unrolled term loop issued predicated-off products on the (scarce)
+  // float64 pipe
   constexpr int LU = 10, LV = 6, NV = 1 << LV;
   __shared__ T Vs[NV][4];
   __shared__ uint32_t offC_v[NV];
@@ -2106,7 +2109,6 @@ __global__ void __launch_bounds__(256) k4_outer(K4Params p) {
   const uint32_t u_tiles = 1u << (nu - LU), v_tiles = 1u << (nv - LV);
   const uint32_t ut = blockIdx.x % u_tiles, vt = (blockIdx.x / u_tiles) % v_tiles;
   const uint32_t bb = blockIdx.x / (u_tiles * v_tiles);
-  const int NS = 1 << ns;
   if (threadIdx.x == 0) { smax[0] = 0; smin[0] = kNoMin; }
   const uint32_t baseV = scatter_bits(vt, vV + LV, nv - LV) | scatter_bits(bb, bV, p.nb);
   for (int x = threadIdx.x; x < NV * NS; x += blockDim.x) {
