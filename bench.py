@@ -47,23 +47,32 @@ GRID_H, GRID_W, GRID_SEED = 16, 100, 1
 POOL = 4096
 # DRAM traffic / algorithmic bytes of the dominant kernel (k2_chain) over a
 # serving wave's mix of chains, from one ncu capture, and the SHA-256 of the
-# kernel source it was taken on: when the source differs, the ratio no
-# longer describes the kernel and `roofline.traffic` is null.
+# chain kernel's source it was taken on (the shared helpers at the top of
+# kernels.cuh, the TMA-staged and chain kernels' section, dev_common.cuh):
+# when that source differs, the ratio no longer describes the kernel and
+# `roofline.traffic` is null.
 TRAFFIC_CAPTURE = {"ratio": 738.3e6 / 939.7e6,
-                   "kernels_cuh_sha256": "d23de3bcc1f2868743f9f8bb9e589350c1fe33581abe770595b46d1f033f24fe"}
+                   "chain_source_sha256": "dbba52e6e6bebae73904632784e3daedea5c35b2770753faebe2287f017c1185"}
 
 
 def _kernel_source_sha256() -> str:
     import hashlib
-    with open(os.path.join(ROOT, "paper_2006_15512_b300", "csrc", "kernels.cuh"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    csrc = os.path.join(ROOT, "paper_2006_15512_b300", "csrc")
+    with open(os.path.join(csrc, "kernels.cuh")) as f:
+        k = f.read()
+    with open(os.path.join(csrc, "dev_common.cuh")) as f:
+        dc = f.read()
+    pre = k[:k.index("// ------------------------------------------------------------ K1 generic")]
+    reg = k[k.index("// ------------------------------------------------- K2 with TMA staging"):
+            k.index("// ------------------------------------------ runs of chains in one launch")]
+    return hashlib.sha256((pre + reg + dc).encode()).hexdigest()
 
 
 def traffic_ratio():
     """(ratio or None, note)."""
     if TRAFFIC_CAPTURE["ratio"] is None:
         return None, "no ncu capture of the current kernel source"
-    if TRAFFIC_CAPTURE["kernels_cuh_sha256"] != _kernel_source_sha256():
+    if TRAFFIC_CAPTURE["chain_source_sha256"] != _kernel_source_sha256():
         return None, "kernel source changed since the ncu capture"
     return TRAFFIC_CAPTURE["ratio"], "ncu capture of k2_chain on this kernel source (serving wave mix)"
 

@@ -192,27 +192,36 @@ static size_t wave_take(size_t n, size_t max_b) {
 static void batcher_loop(wmc_server *srv) {
   std::unique_lock<std::mutex> lk(srv->mu);
   const size_t max_b = (size_t)srv->opts.max_batch;
+  // a partial wave starts only on an idle device (or with partial_overlap):
+  // while a wave runs, the queue grows into the next one; a full wave
+  // starts in any free slot
+  auto may_start = [&] {
+    return srv->in_flight == 0 || srv->opts.partial_overlap == 1 || srv->queue.size() >= max_b;
+  };
+  auto free_slot = [&](bool staged) {
+    for (size_t i = 0; i < srv->slots.size(); ++i)
+      if (!srv->slots[i].busy && srv->slots[i].staged == staged) return (int)i;
+    return -1;
+  };
+  // the busy slot launched first without a staged wave (expected to free first)
+  auto stage_slot = [&] {
+    int sk = -1;
+    for (size_t i = 0; i < srv->slots.size(); ++i)
+      if (srv->slots[i].busy && !srv->slots[i].staged &&
+          (sk < 0 || srv->slots[i].launched_ns < srv->slots[(size_t)sk].launched_ns))
+        sk = (int)i;
+    return sk;
+  };
+  auto can_launch = [&] { return !srv->queue.empty() && free_slot(false) >= 0 && may_start(); };
+  // a full wave queued that cannot start now: staged for a busy slot
+  auto can_stage = [&] { return srv->queue.size() >= max_b && !can_launch() && stage_slot() >= 0; };
   for (;;) {
-    // a partial wave starts only on an idle device (or with
-    // partial_overlap): while a wave runs, the queue grows into the next
-    // one; a full wave starts in any free slot
-    auto may_start = [&] {
-      return srv->in_flight == 0 || srv->opts.partial_overlap || srv->queue.size() >= max_b;
-    };
-    srv->cv_work.wait(lk, [&] {
-      if (srv->stop) return true;
-      for (auto &s : srv->slots)
-        if (!s.busy && (s.staged || (!srv->queue.empty() && may_start()))) return true;
-      if (srv->queue.size() >= max_b)
-        for (auto &s : srv->slots)
-          if (s.busy && !s.staged) return true;
-      return false;
-    });
+    // every wake-up that returns makes progress (a launch or a staging),
+    // so the loop never spins while holding the lock
+    srv->cv_work.wait(lk, [&] { return srv->stop || free_slot(true) >= 0 || can_launch() || can_stage(); });
     if (srv->stop) return;
     // a free slot with a staged wave: launch it at once
-    int sj = -1;
-    for (size_t i = 0; i < srv->slots.size(); ++i)
-      if (!srv->slots[i].busy && srv->slots[i].staged) { sj = (int)i; break; }
+    const int sj = free_slot(true);
     if (sj >= 0) {
       Slot &sl = srv->slots[(size_t)sj];
       sl.wave = std::move(sl.next);
@@ -224,7 +233,7 @@ static void batcher_loop(wmc_server *srv) {
       sl.status = WMC_OK;
       sl.launched_ns = mono_ns();
       srv->in_flight++;
-    srv->stats.max_in_flight = std::max<int64_t>(srv->stats.max_in_flight, srv->in_flight);
+      srv->stats.max_in_flight = std::max<int64_t>(srv->stats.max_in_flight, srv->in_flight);
       lk.unlock();
       int rc = submit_wave(srv, sj);
       lk.lock();
@@ -235,16 +244,10 @@ static void batcher_loop(wmc_server *srv) {
       }
       continue;
     }
-    bool any_free = false;
-    for (auto &s : srv->slots) any_free |= !s.busy;
-    if (!any_free) {
-      // every slot busy and a full wave queued: stage it for the slot that
-      // was launched first (the one expected to free first)
-      int sk = -1;
-      for (size_t i = 0; i < srv->slots.size(); ++i)
-        if (srv->slots[i].busy && !srv->slots[i].staged &&
-            (sk < 0 || srv->slots[i].launched_ns < srv->slots[(size_t)sk].launched_ns))
-          sk = (int)i;
+    if (!can_launch()) {
+      // every slot that could take it is busy and a full wave is queued:
+      // stage it for the slot expected to free first
+      const int sk = stage_slot();
       if (sk < 0 || srv->queue.size() < max_b) continue;
       Slot &sl = srv->slots[(size_t)sk];
       sl.next.clear();
@@ -263,11 +266,9 @@ static void batcher_loop(wmc_server *srv) {
       srv->cv_work.wait_for(lk, std::chrono::microseconds(srv->opts.max_wave_wait_us),
                             [&] { return srv->stop || srv->queue.size() >= max_b; });
       if (srv->stop) return;
+      if (!can_launch()) continue;
     }
-    int si = -1;
-    for (size_t i = 0; i < srv->slots.size(); ++i)
-      if (!srv->slots[i].busy) { si = (int)i; break; }
-    if (si < 0 || srv->queue.empty() || !may_start()) continue;
+    const int si = free_slot(false);
     Slot &sl = srv->slots[(size_t)si];
     sl.wave.clear();
     const size_t take = wave_take(srv->queue.size(), max_b);
