@@ -362,7 +362,10 @@ int wmc_to_scaled_fp32(const double *x, int64_t n, float *out,
  * bucket nodes that carry almost all bytes, 2^15 assignments of the
  * frontier's indices, each thread reading the frontier's entries once and
  * writing every output that differs only in the bucket tensor's own
- * indices; within a formula the nodes
+ * indices; runs of up to four consecutive frontier eliminations of a
+ * formula in one pass over the frontier, each thread holding the 2^D
+ * values over the chain's indices in registers, as wmc_set_fusion does
+ * for one plan; within a formula the nodes
  * run in post-order, across formulas and within a node concurrently; the
  * task list is built by list scheduling, the formulas with the longest
  * remaining chains first; every dependency wait is bounded at one second),
@@ -379,6 +382,13 @@ int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans,
  * over the formulas in post-order.  Results are the same bits either way
  * (a node's outputs do not depend on how they are split into tasks). */
 void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order);
+/* Longest run of frontier eliminations (Alg. 2: each step sums one index
+ * of the frontier and adds at most one) that batches created after the call
+ * execute as one pass: 2..4, or 0 (or 1) for one pass per contraction.
+ * Default 4.  A chain's inner tensors are never stored and are not
+ * rescaled between its steps (the scales are powers of two): results are
+ * the same bits either way; workspace and algorithmic bytes shrink. */
+void wmc_set_batch_fusion(int32_t max_steps);
 typedef struct {
   int64_t n_formulas, n_nodes, n_tasks;
   int64_t workspace_bytes;

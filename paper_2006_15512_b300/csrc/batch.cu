@@ -28,6 +28,7 @@
 #include <cmath>
 #include <queue>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -59,7 +60,29 @@ struct BNode {
   int8_t f;                 // stream mode: output bits absent from A ("S-free", <= 4)
   int8_t rB;                // rank of B
   int8_t pad0;
+  int32_t chain;            // chain mode (stream == 2): index of its BChain
+  int32_t pad1;
   int8_t posA[32], posB[32], sposA[24], sposB[24];
+};
+
+// Chain mode: D <= 4 consecutive frontier steps of one formula in one pass.
+// Step i contracts the running tensor with S_i, summing x_i (an index of
+// the chain's first operand A_1) and adding y_i (no index when the last
+// step `shrink`s), so C_i = sum over x_i of C_{i-1} S_i with C_0 = A_1.  A
+// work unit is one assignment u of A_1's passive indices (those no step
+// sums); the thread holds the 2^D values over the chain state in
+// registers: bit i is x_i before step i and y_i after it.  S_i may hold
+// passive indices, x_i, y_i and the two indices added last (y_{i-1},
+// y_{i-2}).
+struct BChain {
+  int64_t s[4], es[4], xs[4], ns[4];  // S_i: data, exponent, max, min slots (byte offsets)
+  int8_t D, shrink, nu, pad;          // steps, last step adds nothing, passive indices
+  int8_t rs[4];                       // rank of S_i
+  int8_t xa[4];                       // A_1 bit of x_i
+  int8_t yc[4];                       // C_D bit of y_i (-1: the shrink step)
+  int8_t sx[4], sy[4], s1[4], s2[4];  // S_i bit of x_i, y_i, y_{i-1}, y_{i-2} (-1: none)
+  int8_t ua[32], uc[32];              // u bit -> A_1 bit, C_D bit (u: passive indices in C_D order)
+  int8_t us[4][32];                   // u bit -> S_i bit (-1: none)
 };
 
 struct BTask {
@@ -82,6 +105,7 @@ struct BRoot {
 struct BatchArgs {
   char *ws;
   const BNode *nodes;
+  const BChain *chains;
   const BTask *tasks;
   int32_t n_tasks;
   uint32_t *next;           // task counter
@@ -372,6 +396,182 @@ __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, cons
   task_maxmin<T>(ws, nd, tmax, tmin, red);
 }
 
+// ---- chain mode
+struct ChainGeom {
+  uint32_t lut[12][256];  // rows 2t, 2t+1: u-local bits 0-7, 8-15 -> offset in A_1, C_D, S_1..S_4
+  uint32_t dS[4][16];     // S_i offset of (x_i, y_i, y_{i-1}, y_{i-2}) = bits 0-3 of the entry
+  uint32_t pA[16];        // A_1 offset of the x-state s (bit i = x_i)
+  uint32_t dC[16];        // C_D offset of the final state s (bit i = y_i)
+};
+
+__device__ __forceinline__ void chain_geom(const BNode &nd, const BChain &ch, ChainGeom &g) {
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < 16; ++j) {
+      uint32_t pa = 0, dc = 0;
+      for (int i = 0; i < ch.D; ++i)
+        if ((j >> i) & 1) {
+          pa |= 1u << ch.xa[i];
+          if (ch.yc[i] >= 0) dc |= 1u << ch.yc[i];
+        }
+      g.pA[j] = pa;
+      g.dC[j] = dc;
+      for (int i = 0; i < 4; ++i) {
+        uint32_t o = 0;
+        if (i < ch.D) {
+          const int8_t b[4] = {ch.sx[i], ch.sy[i], ch.s1[i], ch.s2[i]};
+          for (int t = 0; t < 4; ++t)
+            if (((j >> t) & 1) && b[t] >= 0) o |= 1u << b[t];
+        }
+        g.dS[i][j] = o;
+      }
+    }
+  }
+  const int cl = nd.chunk_log2, rows = 2 * (2 + ch.D);
+  for (int i = threadIdx.x; i < rows * 256; i += blockDim.x) {
+    const int row = i >> 8, v = i & 255, base = (row & 1) * 8, t = row >> 1;
+    const int8_t *pos = t == 0 ? ch.ua : (t == 1 ? ch.uc : ch.us[t - 2]);
+    uint32_t o = 0;
+    for (int b = 0; b < 8 && base + b < cl; ++b)
+      if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
+    g.lut[row][v] = o;
+  }
+}
+
+// C_D's exponent: A_1's and every S_i's (the intermediates are never
+// rescaled: their scales are powers of two, so only this bookkeeping
+// moves); the flush test over the smallest nonzero scaled entries of all
+// D + 1 operands, a lower bound on every product the chain forms.
+template <typename T>
+__device__ __forceinline__ void chain_exponent(char *ws, const BNode &nd, const BChain &ch,
+                                               unsigned long long ma) {
+  int64_t e = ldcg((const int64_t *)(ws + nd.ea)) + dev::pow2_exp_of(ma, T());
+  const unsigned long long na = ldcg((const unsigned long long *)(ws + nd.na));
+  bool zero = na == kNoMin;
+  T lo = zero ? (T)0 : dev::from_bits<T>(na) * dev::pow2_scale(dev::pow2_exp_of(ma, T()), T());
+  for (int i = 0; i < ch.D; ++i) {
+    const unsigned long long mb = ldcg((const unsigned long long *)(ws + ch.xs[i]));
+    const unsigned long long nb = ldcg((const unsigned long long *)(ws + ch.ns[i]));
+    e += ldcg((const int64_t *)(ws + ch.es[i])) + dev::pow2_exp_of(mb, T());
+    if (nb == kNoMin) zero = true;
+    else lo *= dev::from_bits<T>(nb) * dev::pow2_scale(dev::pow2_exp_of(mb, T()), T());
+  }
+  *(int64_t *)(ws + nd.ec) = e;
+  if (!zero && dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
+}
+
+// Step I on the register block: for each state of the other bits, the two
+// values over x_I become the values over y_I (or one value when the step
+// shrinks), each a two-term fused multiply-add chain over x_I = 0, 1 from
+// zero: the order of every other kernel for one summed index.
+template <typename T, int D, bool SHRINK, int I>
+__device__ __forceinline__ void chain_step(T (&a)[1 << D], const T *S, uint32_t sb, const uint32_t *dS) {
+  constexpr bool last = SHRINK && I == D - 1;
+  T sv[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if ((last && (j & 2)) || (I < 1 && (j & 4)) || (I < 2 && (j & 8))) continue;
+    sv[j] = S[sb | dS[j]];
+  }
+#pragma unroll
+  for (int o = 0; o < (1 << D); ++o) {
+    if (o & (1 << I)) continue;
+    const int dd = (I >= 1 ? ((o >> (I - 1)) & 1) << 2 : 0) | (I >= 2 ? ((o >> (I - 2)) & 1) << 3 : 0);
+    const T a0 = a[o], a1 = a[o | (1 << I)];
+    T c0 = dev::fma_t(a0, sv[dd], (T)0);
+    c0 = dev::fma_t(a1, sv[dd | 1], c0);
+    a[o] = c0;
+    if (!last) {
+      T c1 = dev::fma_t(a0, sv[dd | 2], (T)0);
+      c1 = dev::fma_t(a1, sv[dd | 3], c1);
+      a[o | (1 << I)] = c1;
+    }
+  }
+}
+
+template <typename T, int D, bool SHRINK, int I>
+struct ChainSteps {
+  __device__ static __forceinline__ void run(T (&a)[1 << D], const T *sS, const uint32_t (&sb)[D],
+                                             const ChainGeom &g) {
+    chain_step<T, D, SHRINK, I>(a, sS + I * kSMaxS, sb[I], g.dS[I]);
+    ChainSteps<T, D, SHRINK, I + 1>::run(a, sS, sb, g);
+  }
+};
+template <typename T, int D, bool SHRINK>
+struct ChainSteps<T, D, SHRINK, D> {
+  __device__ static __forceinline__ void run(T (&)[1 << D], const T *, const uint32_t (&)[D], const ChainGeom &) {}
+};
+
+template <typename T, int D, bool SHRINK>
+__device__ void run_chain(const BatchArgs &ba, const BNode &nd, const BChain &ch, int chunk, const ChainGeom &g,
+                          T *sS, unsigned long long *red) {
+  char *ws = ba.ws;
+  const T *A = (const T *)(ws + nd.a);
+  T *C = (T *)(ws + nd.c);
+  const unsigned long long ma = ldcg((const unsigned long long *)(ws + nd.xa));
+  const T sa = dev::pow2_scale(dev::pow2_exp_of(ma, T()), T());
+  if (chunk == 0 && threadIdx.x == 32) chain_exponent<T>(ws, nd, ch, ma);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const unsigned long long mb = ldcg((const unsigned long long *)(ws + ch.xs[i]));
+    const T sb = dev::pow2_scale(dev::pow2_exp_of(mb, T()), T());
+    const T *S = (const T *)(ws + ch.s[i]);
+    for (int j = threadIdx.x; j < (1 << ch.rs[i]); j += blockDim.x) sS[i * kSMaxS + j] = ldcg(S + j) * sb;
+  }
+  // offsets of the task's first u (its bits above the task's local bits)
+  const int cl = nd.chunk_log2;
+  const uint32_t u0 = (uint32_t)chunk << cl;
+  uint32_t bA = 0, bC = 0, bS[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) bS[i] = 0;
+  for (int j = cl; j < ch.nu; ++j)
+    if ((u0 >> j) & 1) {
+      bA |= 1u << ch.ua[j];
+      bC |= 1u << ch.uc[j];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+        if (ch.us[i][j] >= 0) bS[i] |= 1u << ch.us[i][j];
+    }
+  __syncthreads();  // sS
+  const uint32_t n_loc = 1u << cl;
+  T tmax = (T)0;
+  unsigned long long tmin = kNoMin;
+  for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
+    const uint32_t lo = l & 255, hi = l >> 8;
+    const uint32_t ab = bA | g.lut[0][lo] | g.lut[1][hi];
+    const uint32_t cb = bC | g.lut[2][lo] | g.lut[3][hi];
+    uint32_t sb[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) sb[i] = bS[i] | g.lut[4 + 2 * i][lo] | g.lut[5 + 2 * i][hi];
+    T a[1 << D];
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) a[st] = ldcg(A + (ab | g.pA[st]));
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) a[st] *= sa;
+    ChainSteps<T, D, SHRINK, 0>::run(a, sS, sb, g);
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) {
+      if (SHRINK && ((st >> (D - 1)) & 1)) continue;  // summed away
+      C[cb | g.dC[st]] = a[st];
+      track_out(a[st], tmax, tmin);
+    }
+  }
+  task_maxmin<T>(ws, nd, tmax, tmin, red);
+}
+
+template <typename T>
+__device__ __forceinline__ void chain_dispatch(const BatchArgs &ba, const BNode &nd, const BChain &ch, int chunk,
+                                               const ChainGeom &g, T *sS, unsigned long long *red) {
+  const int sel = ch.D * 2 + (ch.shrink ? 1 : 0);
+  switch (sel) {
+    case 4: run_chain<T, 2, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 5: run_chain<T, 2, true>(ba, nd, ch, chunk, g, sS, red); break;
+    case 6: run_chain<T, 3, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 7: run_chain<T, 3, true>(ba, nd, ch, chunk, g, sS, red); break;
+    case 8: run_chain<T, 4, false>(ba, nd, ch, chunk, g, sS, red); break;
+    default: run_chain<T, 4, true>(ba, nd, ch, chunk, g, sS, red); break;
+  }
+}
+
 template <typename TI, typename TA, typename TO>
 __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
                          unsigned long long *red) {
@@ -460,15 +660,17 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
   task_maxmin<TO>(ws, nd, tmax, tmin, red);
 }
 
-constexpr size_t kTabBytes = sizeof(StreamGeom) > kLutRows * 256 * 4 ? sizeof(StreamGeom) : kLutRows * 256 * 4;
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kTabBytes = cmax(cmax(sizeof(StreamGeom), kLutRows * 256 * 4), sizeof(ChainGeom));
 
 __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
   // a node's tables: the generic path's lookup rows or the stream mode's
   // geometry, and the stream mode's staged S
   __shared__ __align__(16) unsigned char s_tab[kTabBytes];
-  __shared__ __align__(16) double s_S[kSMaxS];
+  __shared__ __align__(16) double s_S[4 * kSMaxS];  // S (stream mode), S_1..S_4 (chain mode)
   uint32_t (*lut)[256] = reinterpret_cast<uint32_t (*)[256]>(s_tab);
   StreamGeom &geom = *reinterpret_cast<StreamGeom *>(s_tab);
+  ChainGeom &cgeom = *reinterpret_cast<ChainGeom *>(s_tab);
   __shared__ unsigned long long red[2];
   __shared__ int s_task, s_ok;
   int lut_node = -1;  // node whose tables the block holds
@@ -480,7 +682,8 @@ __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
     const BTask task = ba.tasks[t];
     const BNode &nd = ba.nodes[task.node];
     if (task.node != lut_node) {  // overlaps the wait for the previous node
-      if (nd.stream) stream_geom(nd, geom);
+      if (nd.stream == 2) chain_geom(nd, ba.chains[nd.chain], cgeom);
+      else if (nd.stream) stream_geom(nd, geom);
       else batch_lut(nd, lut);
       lut_node = task.node;
     }
@@ -494,7 +697,10 @@ __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
     __syncthreads();
     if (!s_ok) break;
     float *s_Sf = reinterpret_cast<float *>(s_S);
-    if (nd.stream && nd.ti == 1) {
+    if (nd.stream == 2) {
+      if (nd.ti == 1) chain_dispatch<double>(ba, nd, ba.chains[nd.chain], task.chunk, cgeom, s_S, red);
+      else chain_dispatch<float>(ba, nd, ba.chains[nd.chain], task.chunk, cgeom, s_Sf, red);
+    } else if (nd.stream && nd.ti == 1) {
       if (nd.k == 0) run_stream<double, 1>(ba, nd, task.chunk, geom, s_S, red);
       else if (nd.k == 1) run_stream<double, 2>(ba, nd, task.chunk, geom, s_S, red);
       else run_stream<double, 4>(ba, nd, task.chunk, geom, s_S, red);
@@ -594,6 +800,7 @@ struct wmc_batch {
   std::vector<Plan *> plans;
   std::vector<int64_t> base;       // byte offset of each formula's workspace
   std::vector<BNode> nodes;
+  std::vector<BChain> chains;
   std::vector<BTask> tasks;
   std::vector<BLeaf> leaves;
   std::vector<BRoot> roots;
@@ -609,6 +816,7 @@ struct wmc_batch {
   char *d_ws = nullptr;            // formulas' workspaces
   char *d_tab = nullptr;           // tables + counters
   BNode *d_nodes = nullptr;
+  BChain *d_chains = nullptr;
   BTask *d_tasks = nullptr;
   BLeaf *d_leaves = nullptr;
   BRoot *d_roots = nullptr;
@@ -641,6 +849,13 @@ static std::vector<int32_t> qlabels(const TensorInfo &t) { return t.labels; }  /
 static std::atomic<int32_t> g_batch_chunk{15};  // log2 outputs (stream mode: u) per task
 static std::atomic<int32_t> g_batch_order{0};   // 0 list scheduling, 1 round-robin
 
+// Longest chain of frontier steps run as one pass (0: none).
+static std::atomic<int32_t> g_batch_fuse{4};
+
+extern "C" void wmc_set_batch_fusion(int32_t max_steps) {
+  g_batch_fuse.store(max_steps < 2 ? 0 : std::min(4, max_steps));
+}
+
 extern "C" void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order) {
   g_batch_chunk.store(chunk_log2 <= 0 ? 15 : std::min(16, std::max(8, chunk_log2)));
   g_batch_order.store(order == 1 ? 1 : 0);
@@ -654,10 +869,109 @@ namespace {
 // block of the persistent kernel reaches on the large frontier nodes.
 double task_us(const BNode &n) {
   const double el = n.ti ? 2.0 : 1.0;  // element size in float32 units
+  if (n.stream == 2)  // 2^cl u: 2^D loads, 2^D (2^(D-1) shrinking) stores each
+    return 2.0 + 0.0009 * el * std::ldexp(1.0, n.chunk_log2) * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
   if (n.stream)  // 2^cl u: 2^k loads and 2^f stores each
     return 2.0 + 0.0009 * el * std::ldexp(1.0, n.chunk_log2) * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
   const double outputs = std::ldexp(1.0, n.chunk_log2);
   return 2.0 + outputs * 0.00091 * el * (1.0 + std::ldexp(1.0, n.k));
+}
+
+int pos_in(const std::vector<int32_t> &L, int32_t v) {
+  for (size_t i = 0; i < L.size(); ++i)
+    if (L[i] == v) return (int)i;
+  return -1;
+}
+
+// A frontier step R . S -> C: one summed index x, an index of R (the
+// running tensor), at most one added index y (-1: none), S of rank <= 8.
+bool frontier_step(const std::vector<int32_t> &LR, const std::vector<int32_t> &LS, const std::vector<int32_t> &LC,
+                   int32_t &x, int32_t &y) {
+  if (LS.size() > 8) return false;
+  int n_sum = 0, n_add = 0;
+  x = -1;
+  y = -1;
+  for (int32_t l : LR)
+    if (pos_in(LC, l) < 0) { ++n_sum; x = l; }
+  for (int32_t l : LS)
+    if (pos_in(LC, l) < 0 && pos_in(LR, l) < 0) ++n_sum;
+  for (int32_t l : LC)
+    if (pos_in(LR, l) < 0) { ++n_add; y = l; }
+  return n_sum == 1 && x >= 0 && n_add <= 1;
+}
+
+// A chain of one formula (chain mode): its nodes n_1..n_D in order, the
+// first operand A_1, S_i, and the summed and added index of each step.
+struct ChainSpec {
+  std::vector<int64_t> nodes, s;
+  std::vector<int32_t> x, y;  // y = -1: the step adds none (shrink; last only)
+  int64_t a1 = -1;
+};
+
+// Chains of consecutive frontier steps (Algorithm 2's post-order, the
+// output of each step the running operand of the next), at most max_d
+// steps each: the first step adds one index, the others one or none (a
+// step adding none ends the chain), every x_i is an index of A_1 that no
+// earlier S holds, and S_i holds no index added before y_{i-2}.
+// chain_at[n] = the chain node n starts (-1: none); absorbed[n] = 1 for the
+// other members, 2 for the nodes that run before their chain (the
+// subtrees of S_2..S_D, between n_1 and n_D in post-order).
+void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, int max_d,
+                 std::vector<ChainSpec> &chains, std::vector<int32_t> &chain_at, std::vector<uint8_t> &absorbed) {
+  const size_t nn = plan.nodes.size();
+  chain_at.assign(nn, -1);
+  absorbed.assign(nn, 0);
+  if (max_d < 2) return;
+  auto L = [&](int64_t t) -> const std::vector<int32_t> & { return plan.tensors[(size_t)t].labels; };
+  std::vector<int64_t> consumer(plan.tensors.size(), -1);
+  for (size_t ni = 0; ni < nn; ++ni) {
+    consumer[(size_t)plan.nodes[ni].a] = (int64_t)ni;
+    consumer[(size_t)plan.nodes[ni].b] = (int64_t)ni;
+  }
+  // float32 plans keep the float64 root out of chains
+  auto typed = [&](int64_t c) { return f64 || !t_dbl[(size_t)c]; };
+  for (size_t ni = 0; ni < nn; ++ni) {
+    if (absorbed[ni]) continue;
+    const Node &n0 = plan.nodes[ni];
+    int64_t r = n0.a, sid = n0.b;
+    if (L(sid).size() > L(r).size()) std::swap(r, sid);
+    int32_t x, y;
+    if (!typed(n0.c) || !frontier_step(L(r), L(sid), L(n0.c), x, y) || y < 0) continue;
+    ChainSpec cs;
+    cs.a1 = r;
+    cs.nodes.push_back((int64_t)ni);
+    cs.s.push_back(sid);
+    cs.x.push_back(x);
+    cs.y.push_back(y);
+    while ((int)cs.nodes.size() < max_d && cs.y.back() >= 0) {
+      const int64_t last = cs.nodes.back();
+      const int64_t cprev = plan.nodes[(size_t)last].c;
+      const int64_t nj = consumer[(size_t)cprev];
+      if (nj < 0 || absorbed[(size_t)nj]) break;
+      const Node &nd = plan.nodes[(size_t)nj];
+      const int64_t sj = nd.a == cprev ? nd.b : nd.a;
+      int32_t xj, yj;
+      if (!typed(nd.c) || !frontier_step(L(cprev), L(sj), L(nd.c), xj, yj)) break;
+      if (pos_in(L(r), xj) < 0) break;
+      const size_t j = cs.nodes.size();
+      bool ok = true;
+      for (size_t i = 0; i < j && ok; ++i) ok = pos_in(L(cs.s[i]), xj) < 0;
+      for (size_t i = 0; i + 2 < j && ok; ++i) ok = pos_in(L(sj), cs.y[i]) < 0;
+      for (int64_t q = last + 1; q < nj && ok; ++q) ok = !absorbed[(size_t)q] && chain_at[(size_t)q] < 0;
+      if (!ok) break;
+      cs.nodes.push_back(nj);
+      cs.s.push_back(sj);
+      cs.x.push_back(xj);
+      cs.y.push_back(yj);
+    }
+    if (cs.nodes.size() < 2) continue;
+    const int64_t last = cs.nodes.back();
+    for (size_t i = 1; i < cs.nodes.size(); ++i) absorbed[(size_t)cs.nodes[i]] = 1;
+    for (int64_t q = (int64_t)ni + 1; q < last; ++q)
+      if (!absorbed[(size_t)q]) absorbed[(size_t)q] = 2;
+    chain_at[ni] = (int32_t)chains.size();
+    chains.push_back(std::move(cs));
+  }
 }
 
 // List scheduling of the formulas' node chains onto `slots` resident
@@ -745,7 +1059,74 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
     LayoutView lv;
     int rc = exec_layout(plan, 1, &lv);
     if (rc) { delete b; return rc; }
-    const int64_t need = (lv.ws_bytes + 255) / 256 * 256;
+    const std::vector<int64_t> &tb = *lv.t_bytes;
+    auto lab = [&](int64_t t) -> const std::vector<int32_t> & { return plan.tensors[(size_t)t].labels; };
+    // chains, and the execution order: a chain's S_2..S_D subtrees run
+    // before its first step
+    std::vector<ChainSpec> specs;
+    std::vector<int32_t> chain_at;
+    std::vector<uint8_t> absorbed;
+    find_chains(plan, *lv.t_dbl, prec == WMC_FP64, g_batch_fuse.load(), specs, chain_at, absorbed);
+    std::vector<int64_t> order;
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
+      if (absorbed[ni]) continue;
+      if (chain_at[ni] >= 0)
+        for (int64_t q = (int64_t)ni + 1; q < specs[(size_t)chain_at[ni]].nodes.back(); ++q)
+          if (absorbed[(size_t)q] == 2) order.push_back(q);
+      order.push_back((int64_t)ni);
+    }
+    // the intermediates' arena, first fit in that order (a chain's inner
+    // outputs are never stored); leaves and metadata as in the plan's layout
+    std::vector<int64_t> t_off(*lv.t_off);
+    FirstFit ff;
+    auto release = [&](int64_t t) {
+      if (t >= plan.n_leaves) ff.release(t_off[(size_t)t] - lv.arena0, tb[(size_t)t]);
+    };
+    for (int64_t ni : order) {
+      const Node &nd = plan.nodes[(size_t)ni];
+      if (chain_at[(size_t)ni] >= 0) {
+        const ChainSpec &cs = specs[(size_t)chain_at[(size_t)ni]];
+        const int64_t cD = plan.nodes[(size_t)cs.nodes.back()].c;
+        t_off[(size_t)cD] = lv.arena0 + ff.alloc(tb[(size_t)cD]);
+        release(cs.a1);
+        for (int64_t sid : cs.s) release(sid);
+      } else {
+        t_off[(size_t)nd.c] = lv.arena0 + ff.alloc(tb[(size_t)nd.c]);
+        release(nd.a);
+        release(nd.b);
+      }
+    }
+    // replay of the order: every operand is live when read (a leaf, or an
+    // output not yet consumed) and no output overlaps a live tensor
+    {
+      std::map<int64_t, int64_t> live;  // tensor -> its arena block's end
+      bool ok = true;
+      auto use = [&](int64_t t) {
+        if (t < plan.n_leaves) return;
+        ok = ok && live.erase(t) == 1;
+      };
+      for (int64_t ni : order) {
+        const Node &nd = plan.nodes[(size_t)ni];
+        int64_t c = nd.c;
+        std::vector<int64_t> in{nd.a, nd.b};
+        if (chain_at[(size_t)ni] >= 0) {
+          const ChainSpec &cs = specs[(size_t)chain_at[(size_t)ni]];
+          c = plan.nodes[(size_t)cs.nodes.back()].c;
+          in.assign(cs.s.begin(), cs.s.end());
+          in.push_back(cs.a1);
+        }
+        const int64_t c0 = t_off[(size_t)c], c1 = c0 + align_up(tb[(size_t)c]);
+        for (const auto &kv : live) ok = ok && (c1 <= t_off[(size_t)kv.first] || kv.second <= c0);
+        for (int64_t t : in) use(t);
+        live[c] = c1;
+      }
+      if (!ok || live.size() != 1 || live.begin()->first != plan.nodes.back().c) {
+        delete b;
+        set_error("internal: the batch layout of formula %d failed its replay", f);
+        return WMC_EPLAN_TOO_BIG;
+      }
+    }
+    const int64_t need = align_up(lv.arena0 + align_up(ff.top));
     if (mem_budget_bytes > 0 && off + need > mem_budget_bytes) break;  // admission by workspace bytes
     b->plans.push_back(&plan);
     b->base.push_back(off);
@@ -758,7 +1139,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
       const TensorInfo &t = plan.tensors[(size_t)i];
       BLeaf L;
       std::memset(&L, 0, sizeof(L));
-      L.data = base + (*lv.t_off)[(size_t)i];
+      L.data = base + t_off[(size_t)i];
       L.e = slot(lv.off_exp, i);
       L.x = slot(lv.off_max, i);
       L.n = slot(lv.off_min, i);
@@ -775,61 +1156,123 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
     // metadata regions to clear each run: flags + error + exponents + maxima, then minima
     b->clears.push_back({base + lv.off_flags, lv.off_max + 8 * lv.n_slots - lv.off_flags, 0, 0});
     b->clears.push_back({base + lv.off_min, 8 * lv.n_slots, 0xff, 0});
-    // nodes
+    // nodes, in execution order
     std::vector<int32_t> ids;
     int32_t prev = -1;
-    for (const Node &nd : plan.nodes) {
+    for (int64_t ni : order) {
+      const Node &nd = plan.nodes[(size_t)ni];
       BNode n;
       std::memset(&n, 0, sizeof(n));
-      n.a = base + (*lv.t_off)[(size_t)nd.a];
-      n.b = base + (*lv.t_off)[(size_t)nd.b];
-      n.c = base + (*lv.t_off)[(size_t)nd.c];
-      n.ea = slot(lv.off_exp, nd.a); n.eb = slot(lv.off_exp, nd.b); n.ec = slot(lv.off_exp, nd.c);
-      n.xa = slot(lv.off_max, nd.a); n.xb = slot(lv.off_max, nd.b); n.xc = slot(lv.off_max, nd.c);
-      n.na = slot(lv.off_min, nd.a); n.nb = slot(lv.off_min, nd.b); n.nc = slot(lv.off_min, nd.c);
-      n.flags = base + lv.off_flags;
-      k1_bitmaps(qlabels(plan.tensors[(size_t)nd.a]), qlabels(plan.tensors[(size_t)nd.b]),
-                 qlabels(plan.tensors[(size_t)nd.c]), &n.rC, &n.k, n.posA, n.posB, n.sposA, n.sposB);
-      if (n.k > 24 || n.rC > 31) { delete b; set_error("node too large for the batch executor"); return WMC_EPLAN_TOO_BIG; }
-      int32_t ra = (int32_t)plan.tensors[(size_t)nd.a].labels.size();
-      int32_t rb = (int32_t)plan.tensors[(size_t)nd.b].labels.size();
-      if (rb > ra) {  // A = the operand with more indices (the product commutes, term by term)
-        std::swap(n.a, n.b); std::swap(n.ea, n.eb); std::swap(n.xa, n.xb); std::swap(n.na, n.nb);
-        for (int j = 0; j < 32; ++j) std::swap(n.posA[j], n.posB[j]);
-        for (int j = 0; j < 24; ++j) std::swap(n.sposA[j], n.sposB[j]);
-        std::swap(ra, rb);
-      }
-      n.rB = (int8_t)rb;
-      n.ti = prec == WMC_FP64 ? 1 : 0;
-      n.to = (*lv.t_dbl)[(size_t)nd.c];
-      n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
-      int32_t f = 0;
-      for (int j = 0; j < n.rC; ++j) f += n.posA[j] < 0;
-      n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && f <= 4) ? 1 : 0;
-      if (n.stream) {
-        // tasks over u, the assignments of C's indices that A holds
-        n.f = (int8_t)f;
-        n.chunk_log2 = std::min<int32_t>(n.rC - f, chunk_log2);
-        n.n_tasks = 1 << (n.rC - f - n.chunk_log2);
-        n.vec4 = (!n.ti && n.chunk_log2 >= 3 && n.rC >= 2 && n.posA[0] == 0 && n.posA[1] == 1) ? 1 : 0;
+      n.chain = -1;
+      if (chain_at[(size_t)ni] >= 0) {
+        const ChainSpec &cs = specs[(size_t)chain_at[(size_t)ni]];
+        const int D = (int)cs.nodes.size();
+        const int64_t cD = plan.nodes[(size_t)cs.nodes.back()].c;
+        const std::vector<int32_t> &LA = lab(cs.a1), &LC = lab(cD);
+        BChain ch;
+        std::memset(&ch, 0xff, sizeof(ch));  // positions: -1 = none
+        ch.D = (int8_t)D;
+        ch.shrink = cs.y.back() < 0 ? 1 : 0;
+        ch.pad = 0;
+        int nu = 0;
+        for (size_t j = 0; j < LC.size(); ++j) {
+          const int pa = pos_in(LA, LC[j]);
+          if (pa < 0) continue;  // an added index
+          ch.ua[nu] = (int8_t)pa;
+          ch.uc[nu] = (int8_t)j;
+          for (int i = 0; i < D; ++i) ch.us[i][nu] = (int8_t)pos_in(lab(cs.s[(size_t)i]), LC[j]);
+          ++nu;
+        }
+        ch.nu = (int8_t)nu;
+        if (nu + D != (int)LA.size() || (int)LC.size() != nu + D - ch.shrink) {
+          delete b;
+          set_error("internal: chain geometry does not add up");
+          return WMC_EPLAN_TOO_BIG;
+        }
+        for (int i = 0; i < D; ++i) {
+          const int64_t sid = cs.s[(size_t)i];
+          const std::vector<int32_t> &LS = lab(sid);
+          ch.s[i] = base + t_off[(size_t)sid];
+          ch.es[i] = slot(lv.off_exp, sid);
+          ch.xs[i] = slot(lv.off_max, sid);
+          ch.ns[i] = slot(lv.off_min, sid);
+          ch.rs[i] = (int8_t)LS.size();
+          ch.xa[i] = (int8_t)pos_in(LA, cs.x[(size_t)i]);
+          ch.yc[i] = cs.y[(size_t)i] >= 0 ? (int8_t)pos_in(LC, cs.y[(size_t)i]) : (int8_t)-1;
+          ch.sx[i] = (int8_t)pos_in(LS, cs.x[(size_t)i]);
+          ch.sy[i] = cs.y[(size_t)i] >= 0 ? (int8_t)pos_in(LS, cs.y[(size_t)i]) : (int8_t)-1;
+          ch.s1[i] = i >= 1 ? (int8_t)pos_in(LS, cs.y[(size_t)i - 1]) : (int8_t)-1;
+          ch.s2[i] = i >= 2 ? (int8_t)pos_in(LS, cs.y[(size_t)i - 2]) : (int8_t)-1;
+          b->alg_bytes += (double)tb[(size_t)sid];
+        }
+        n.a = base + t_off[(size_t)cs.a1];
+        n.ea = slot(lv.off_exp, cs.a1); n.xa = slot(lv.off_max, cs.a1); n.na = slot(lv.off_min, cs.a1);
+        n.b = ch.s[0]; n.eb = ch.es[0]; n.xb = ch.xs[0]; n.nb = ch.ns[0];
+        n.c = base + t_off[(size_t)cD];
+        n.ec = slot(lv.off_exp, cD); n.xc = slot(lv.off_max, cD); n.nc = slot(lv.off_min, cD);
+        n.flags = base + lv.off_flags;
+        n.rC = (int32_t)LC.size();
+        n.k = D;                        // 2^D loads per unit
+        n.f = (int8_t)(D - ch.shrink);  // 2^f stores per unit
+        n.stream = 2;
+        n.ti = n.ta = n.to = prec == WMC_FP64 ? 1 : 0;
+        // a unit moves 2^D values in and up to 2^D out (four times a
+        // stream-mode unit at D = 2): tasks of a quarter as many units
+        n.chunk_log2 = std::min<int32_t>(nu, std::max<int32_t>(8, chunk_log2 - 2));
+        n.n_tasks = 1 << (nu - n.chunk_log2);
+        n.chain = (int32_t)b->chains.size();
+        b->chains.push_back(ch);
+        b->alg_bytes += (double)tb[(size_t)cs.a1] + (double)tb[(size_t)cD];
       } else {
-        n.chunk_log2 = std::min<int32_t>(n.rC, chunk_log2);
-        n.n_tasks = 1 << (n.rC - n.chunk_log2);
-        bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
-                   n.posB[0] < 0 && n.posB[1] < 0;
-        for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
-        n.vec4 = (low && !n.ti && !n.ta && !n.to) ? 1 : 0;
+        n.a = base + t_off[(size_t)nd.a];
+        n.b = base + t_off[(size_t)nd.b];
+        n.c = base + t_off[(size_t)nd.c];
+        n.ea = slot(lv.off_exp, nd.a); n.eb = slot(lv.off_exp, nd.b); n.ec = slot(lv.off_exp, nd.c);
+        n.xa = slot(lv.off_max, nd.a); n.xb = slot(lv.off_max, nd.b); n.xc = slot(lv.off_max, nd.c);
+        n.na = slot(lv.off_min, nd.a); n.nb = slot(lv.off_min, nd.b); n.nc = slot(lv.off_min, nd.c);
+        n.flags = base + lv.off_flags;
+        k1_bitmaps(qlabels(plan.tensors[(size_t)nd.a]), qlabels(plan.tensors[(size_t)nd.b]),
+                   qlabels(plan.tensors[(size_t)nd.c]), &n.rC, &n.k, n.posA, n.posB, n.sposA, n.sposB);
+        if (n.k > 24 || n.rC > 31) { delete b; set_error("node too large for the batch executor"); return WMC_EPLAN_TOO_BIG; }
+        int32_t ra = (int32_t)plan.tensors[(size_t)nd.a].labels.size();
+        int32_t rb = (int32_t)plan.tensors[(size_t)nd.b].labels.size();
+        if (rb > ra) {  // A = the operand with more indices (the product commutes, term by term)
+          std::swap(n.a, n.b); std::swap(n.ea, n.eb); std::swap(n.xa, n.xb); std::swap(n.na, n.nb);
+          for (int j = 0; j < 32; ++j) std::swap(n.posA[j], n.posB[j]);
+          for (int j = 0; j < 24; ++j) std::swap(n.sposA[j], n.sposB[j]);
+          std::swap(ra, rb);
+        }
+        n.rB = (int8_t)rb;
+        n.ti = prec == WMC_FP64 ? 1 : 0;
+        n.to = (*lv.t_dbl)[(size_t)nd.c];
+        n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
+        int32_t f = 0;
+        for (int j = 0; j < n.rC; ++j) f += n.posA[j] < 0;
+        n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && f <= 4) ? 1 : 0;
+        if (n.stream) {
+          // tasks over u, the assignments of C's indices that A holds
+          n.f = (int8_t)f;
+          n.chunk_log2 = std::min<int32_t>(n.rC - f, chunk_log2);
+          n.n_tasks = 1 << (n.rC - f - n.chunk_log2);
+          n.vec4 = (!n.ti && n.chunk_log2 >= 3 && n.rC >= 2 && n.posA[0] == 0 && n.posA[1] == 1) ? 1 : 0;
+        } else {
+          n.chunk_log2 = std::min<int32_t>(n.rC, chunk_log2);
+          n.n_tasks = 1 << (n.rC - n.chunk_log2);
+          bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
+                     n.posB[0] < 0 && n.posB[1] < 0;
+          for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
+          n.vec4 = (low && !n.ti && !n.ta && !n.to) ? 1 : 0;
+        }
+        b->alg_bytes += (double)tb[(size_t)nd.a] + (double)tb[(size_t)nd.b] + (double)tb[(size_t)nd.c];
       }
       n.prev = prev;
       prev = (int32_t)b->nodes.size();
       ids.push_back(prev);
       b->nodes.push_back(n);
-      b->alg_bytes += (double)(*lv.t_bytes)[(size_t)nd.a] + (double)(*lv.t_bytes)[(size_t)nd.b] +
-                      (double)(*lv.t_bytes)[(size_t)nd.c];
     }
     node_ids.push_back(ids);
     const int64_t root = plan.nodes.back().c;
-    b->roots.push_back({base + (*lv.t_off)[(size_t)root], slot(lv.off_exp, root), base + lv.off_flags});
+    b->roots.push_back({base + t_off[(size_t)root], slot(lv.off_exp, root), base + lv.off_flags});
     b->max_roundings = std::max(b->max_roundings, plan.tensors[(size_t)root].roundings);
   }
   if (b->plans.empty()) { delete b; set_error("no formula fits the memory budget"); return WMC_EPLAN_TOO_BIG; }
@@ -864,6 +1307,7 @@ static int batch_ensure_device(wmc_batch *b) {
   const int64_t n_nodes = (int64_t)b->nodes.size(), n_roots = (int64_t)b->roots.size();
   int64_t o = 0;
   const int64_t o_nodes = o; o += al(sizeof(BNode) * n_nodes);
+  const int64_t o_chains = o; o += al(sizeof(BChain) * (int64_t)b->chains.size());
   const int64_t o_tasks = o; o += al(sizeof(BTask) * (int64_t)b->tasks.size());
   const int64_t o_leaves = o; o += al(sizeof(BLeaf) * (int64_t)b->leaves.size());
   const int64_t o_roots = o; o += al(sizeof(BRoot) * n_roots);
@@ -878,6 +1322,7 @@ static int batch_ensure_device(wmc_batch *b) {
   b->total_bytes = b->ws_bytes + o;
   char *t = b->d_tab;
   b->d_nodes = (BNode *)(t + o_nodes);
+  b->d_chains = (BChain *)(t + o_chains);
   b->d_tasks = (BTask *)(t + o_tasks);
   b->d_leaves = (BLeaf *)(t + o_leaves);
   b->d_roots = (BRoot *)(t + o_roots);
@@ -892,6 +1337,7 @@ static int batch_ensure_device(wmc_batch *b) {
     return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
   };
   if (up(b->d_nodes, b->nodes.data(), sizeof(BNode) * b->nodes.size()) ||
+      up(b->d_chains, b->chains.data(), sizeof(BChain) * b->chains.size()) ||
       up(b->d_tasks, b->tasks.data(), sizeof(BTask) * b->tasks.size()) ||
       up(b->d_leaves, b->leaves.data(), sizeof(BLeaf) * b->leaves.size()) ||
       up(b->d_roots, b->roots.data(), sizeof(BRoot) * b->roots.size()) ||
@@ -926,6 +1372,7 @@ static void batch_enqueue(wmc_batch *b, cudaStream_t s) {
   BatchArgs a;
   a.ws = b->d_ws;
   a.nodes = b->d_nodes;
+  a.chains = b->d_chains;
   a.tasks = b->d_tasks;
   a.n_tasks = (int32_t)b->tasks.size();
   a.next = b->d_next;

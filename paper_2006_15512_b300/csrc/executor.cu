@@ -90,8 +90,6 @@ static int dev_alloc(void **p, size_t bytes) {
 
 namespace {
 
-constexpr int64_t kAlign = 256;
-inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ,
             L_BFP, L_BFPW, L_CTA };
@@ -235,51 +233,6 @@ int pos_of(const std::vector<int32_t> &L, int32_t v) {
     if (L[i] == v) return (int)i;
   return -1;
 }
-
-struct FirstFit {
-  std::map<int64_t, int64_t> free_;  // offset -> size
-  int64_t top = 0;
-  int64_t alloc(int64_t bytes) {
-    bytes = align_up(std::max<int64_t>(bytes, 1));
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        int64_t off = it->first, sz = it->second;
-        free_.erase(it);
-        if (sz > bytes) free_[off + bytes] = sz - bytes;
-        return off;
-      }
-    }
-    // extend the top (merging a free block that ends at the top)
-    if (!free_.empty()) {
-      auto last = std::prev(free_.end());
-      if (last->first + last->second == top) {
-        int64_t off = last->first;
-        free_.erase(last);
-        top = off + bytes;
-        return off;
-      }
-    }
-    int64_t off = top;
-    top += bytes;
-    return off;
-  }
-  void release(int64_t off, int64_t bytes) {
-    bytes = align_up(std::max<int64_t>(bytes, 1));
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-};
 
 // Chooses K2 (streaming, P the operand whose kept indices stay in order)
 // when its structural conditions hold, else K1.
@@ -793,7 +746,9 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   // latency, and vector lanes let the growth and shrink steps join chains
   // (about 413 launches instead of 605 on the 16x100 grid); results are
   // the same bits at every batch size
-  if (Q == 1 && plan.precision != WMC_FP64 && !force_f64 && plan.max_rank <= 20) m = 1;
+  // (not in the one-pass layout other executors reuse: the uneven batch
+  // runs every formula on one lane)
+  if (Q == 1 && plan.precision != WMC_FP64 && !force_f64 && !plain && plan.max_rank <= 20) m = 1;
   st.m = m;
   const int32_t Qp = 1 << m;
   st.Qp = Qp;
@@ -2279,6 +2234,7 @@ int exec_layout(Plan &plan, int32_t Q, LayoutView *out) {
   out->off_max = st->off_max;
   out->off_min = st->off_min;
   out->n_slots = st->n_slots;
+  out->arena0 = st->ws_bytes - align_up(st->arena_bytes);
   out->t_off = &st->t_off;
   out->t_meta = &st->t_meta;
   out->t_bytes = &st->t_bytes;

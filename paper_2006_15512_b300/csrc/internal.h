@@ -2,7 +2,9 @@
 // Not part of the ABI (see include/wmc.h).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
+#include <iterator>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -12,6 +14,58 @@
 #include "wmc.h"
 
 namespace wmc {
+
+// Workspace regions start on 256-byte boundaries.
+constexpr int64_t kAlign = 256;
+inline int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit arena of a walk's intermediate tensors: offsets relative to
+// the arena's start, each block rounded up to kAlign; released blocks merge
+// with their free neighbours.
+struct FirstFit {
+  std::map<int64_t, int64_t> free_;  // offset -> size
+  int64_t top = 0;
+  int64_t alloc(int64_t bytes) {
+    bytes = align_up(std::max<int64_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        int64_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        return off;
+      }
+    }
+    // extend the top (merging a free block that ends at the top)
+    if (!free_.empty()) {
+      auto last = std::prev(free_.end());
+      if (last->first + last->second == top) {
+        int64_t off = last->first;
+        free_.erase(last);
+        top = off + bytes;
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += bytes;
+    return off;
+  }
+  void release(int64_t off, int64_t bytes) {
+    bytes = align_up(std::max<int64_t>(bytes, 1));
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
 
 // Thread-local error message behind wmc_last_error().
 void set_error(const char *fmt, ...);
@@ -134,6 +188,7 @@ Plan &plan_of(wmc_plan_t *p);
 struct LayoutView {
   int64_t ws_bytes = 0, off_io = 0, off_flags = 0, off_err = 0, off_exp = 0, off_max = 0,
           off_min = 0, n_slots = 0;
+  int64_t arena0 = 0;  // start of the intermediates' arena (leaves and metadata below it)
   const std::vector<int64_t> *t_off = nullptr;   // byte offset of each tensor
   const std::vector<int64_t> *t_meta = nullptr;  // first metadata slot
   const std::vector<int64_t> *t_bytes = nullptr;

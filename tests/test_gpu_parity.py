@@ -718,22 +718,44 @@ def test_uneven_batch_schedules_give_the_same_bits(w):
                 assert r <= TOL[precision], (i, r)
 
 
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_uneven_batch_chains_keep_the_bits(w, precision):
+    """Runs of frontier eliminations in one pass (chains of up to 2 and 4
+    steps) against one pass per contraction: the same bits for every formula
+    (a chain's inner tensors are not rescaled, and the scales are powers of
+    two), fewer algorithmic bytes, and the oracle's value."""
+    plans, cnfs, _ = _uneven(w, 16, precision, seed=11, n3=(20, 40), grid_w=(4, 8), grid_h=(6, 30))
+    got, infos = [], []
+    try:
+        for fz in (0, 2, 4):
+            w.wmc_set_batch_fusion(fz)
+            b = w.Batch(plans)
+            infos.append(b.info())
+            got.append([(r.mant, r.exp2, r.flags) for r in b.execute()])
+            del b
+    finally:
+        w.wmc_set_batch_fusion(4)
+    assert got[0] == got[1] == got[2]
+    assert infos[2].algorithmic_bytes < infos[1].algorithmic_bytes < infos[0].algorithmic_bytes
+    assert infos[2].n_nodes < infos[1].n_nodes < infos[0].n_nodes
+    for i in range(0, len(plans), 3):
+        cnf, wp, wn = cnfs[i]
+        want = oracle.bucket_elim(cnf, wp, wn, order=_narrow_order(cnf))
+        assert Big(got[2][i][0], got[2][i][1]).rel_diff(want) <= TOL[precision], i
+
+
 def test_uneven_batch_admission(w):
     """Admission by workspace bytes: only the prefix that fits is taken."""
-    # the batch lays each formula out with one pass per node (no chains, no
-    # small-node phase): the same workspace as a plan laid out with both off
-    try:
-        w.wmc_set_fusion(0)
-        w.wmc_set_small_phase(0)
-        plans, _, _ = _uneven(w, 10, FP32, seed=6, n3=(14, 30), grid_w=(3, 6), grid_h=(4, 20))
-        sizes = [p.info(1).workspace_bytes for p in plans]
-    finally:
-        w.wmc_set_fusion(4)
-        w.wmc_set_small_phase(1)
-    budget = sum((s_ + 255) // 256 * 256 for s_ in sizes[:4])
+    plans, _, _ = _uneven(w, 10, FP32, seed=6, n3=(14, 30), grid_w=(3, 6), grid_h=(4, 20))
+    # formula i's workspace starts where the first i formulas' end (each
+    # rounded up to 256 bytes)
+    whole = w.Batch(plans)
+    budget = whole.formula_info(4)[0]
+    del whole
     batch = w.Batch(plans, mem_budget_bytes=budget)
     assert batch.n_admitted == 4
     assert len(batch.execute()) == 4
+    assert w.Batch(plans, mem_budget_bytes=budget - 1).n_admitted == 3
 
 
 _C5_CACHE = {}

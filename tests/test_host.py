@@ -347,6 +347,34 @@ def test_block_fp_options():
         w.Batch(plans)
 
 
+def test_batch_chain_tables():
+    """Host side of the uneven batch's chains: longer chains leave fewer
+    nodes and tasks and fewer algorithmic bytes; the layout replay (every
+    operand live when read, no output over a live tensor) passes for every
+    chain length; chains need 2 steps at least."""
+    w = _lib()
+    plans = []
+    for h, wd, seed in ((30, 8, 1), (24, 7, 2), (16, 9, 3)):
+        plans.append(w.Plan(w.Network.from_cnf(wmcgen.grid_cnf(h, wd, seed)), precision=w.WMC_SCALED_FP32))
+    plans.append(w.Plan(w.Network.from_cnf(wmcgen.random_kcnf(40, 100, seed=4)), precision=w.WMC_FP64))
+    infos = {}
+    try:
+        for fz in (0, 1, 2, 3, 4, 9):
+            w.wmc_set_batch_fusion(fz)
+            for prec_plans in (plans[:3], plans[3:]):
+                b = w.Batch(prec_plans)
+                assert b.n_admitted == len(prec_plans)
+                infos.setdefault(fz, []).append(b.info())
+    finally:
+        w.wmc_set_batch_fusion(4)
+    g = {fz: v[0] for fz, v in infos.items()}  # the grids
+    assert g[0].n_nodes == g[1].n_nodes and g[0].algorithmic_bytes == g[1].algorithmic_bytes
+    assert g[4].n_nodes == g[9].n_nodes  # (at most 4 steps)
+    assert g[4].n_nodes < g[3].n_nodes < g[2].n_nodes < g[0].n_nodes
+    assert g[4].algorithmic_bytes < g[3].algorithmic_bytes < g[2].algorithmic_bytes < g[0].algorithmic_bytes
+    assert g[4].n_tasks < g[0].n_tasks
+
+
 # ------------------------------------------------------ clause factoring
 
 def _long_clause_cnf(n, n_short, n_long, k_long, seed):
