@@ -648,6 +648,7 @@ def run_other(args):
         for _, c in planned:
             kinds[c[0][:4]] = kinds.get(c[0][:4], 0) + 1
         t0 = time.perf_counter()
+        w.wmc_set_batch_fusion(args.batch_fusion)
         batch = w.Batch([p for p, _ in planned])
         create_s = time.perf_counter() - t0
         info = batch.info()
@@ -676,7 +677,9 @@ def run_other(args):
                                  "frac": achieved / hbm, "traffic": None, "peak_source": src,
                                  "kernel": "k6_persistent (one launch; timed with the batch graph's "
                                            "clear, leaf and result kernels)",
-                                 "alg_bytes": "one pass per node: |A| + |B| + |C| over the batch's nodes",
+                                 "alg_bytes": "one pass per node (|A| + |B| + |C|) or per chain of frontier "
+                                              "steps (|A_1| + sum |S_i| + |C_D|)",
+                                 "batch_fusion": args.batch_fusion,
                                  "alg_GB": info.algorithmic_bytes / 1e9},
                     "clocks": clk.summary(), "cpu_baseline": cpu,
                     "max_rel_err_sampled": max(errs) if errs else None, "sampled": len(errs),
@@ -786,6 +789,8 @@ def main():
                     choices=["serving", "random3cnf", "grid", "sweep", "uneven", "sliced"])
     ap.add_argument("--n-formulas", type=int, default=512)
     ap.add_argument("--rank-cap", type=int, default=26, help="uneven batch: largest plan rank admitted")
+    ap.add_argument("--batch-fusion", type=int, default=4,
+                    help="uneven batch: longest chain of frontier steps in one pass (0: none)")
     ap.add_argument("--sweep-rows", type=lambda x: [tuple(int(v) for v in r.split(",")) for r in x.split(";")],
                     default=[(29, 5, 2, 1), (28, 12, 4, 4), (17, 17, 2, 1), (24, 22, 0, 8), (22, 22, 0, 16)],
                     help="sweep cases 'rank_a,rank_b,batch,summed;...'")

@@ -358,8 +358,8 @@ int wmc_to_scaled_fp32(const double *x, int64_t n, float *out,
  * receives how many.  All plans must share a precision.  Each formula is
  * evaluated with its network's default weights.  Execution: one graph of
  * four kernels -- clear, leaves, a persistent task-queue contraction kernel
- * (tasks = chunks of 2^15 outputs of one node -- for the frontier-times-
- * bucket nodes that carry almost all bytes, 2^15 assignments of the
+ * (tasks = chunks of 2^14 outputs of one node -- for the frontier-times-
+ * bucket nodes that carry almost all bytes, 2^14 assignments of the
  * frontier's indices, each thread reading the frontier's entries once and
  * writing every output that differs only in the bucket tensor's own
  * indices; runs of up to four consecutive frontier eliminations of a
@@ -377,7 +377,8 @@ int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans,
                      int32_t *n_admitted);
 /* Task size and order of batches created after the call: chunk_log2 = log2
  * of the outputs per task, or of the assignments u per task for nodes in
- * stream mode (8..16; 0 = the default 15), order 0 = list
+ * stream mode (8..16; 0 = the default 14; chains take a quarter of that
+ * many units, at least 2^8), order 0 = list
  * scheduling by the formulas' remaining chains (default), 1 = round-robin
  * over the formulas in post-order.  Results are the same bits either way
  * (a node's outputs do not depend on how they are split into tasks). */
@@ -389,8 +390,20 @@ void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order);
  * rescaled between its steps (the scales are powers of two): results are
  * the same bits either way; workspace and algorithmic bytes shrink. */
 void wmc_set_batch_fusion(int32_t max_steps);
+/* Small subtrees in batches created after the call: every node of output
+ * rank <= max_rank (1..14) with at most 2^8 summed terms whose children are
+ * leaves or such nodes (the root excepted) runs inside the task of its
+ * maximal such subtree -- one block, its nodes one after another with no
+ * dependency waits, all of a formula's subtrees before its other nodes --
+ * so that a formula's strictly ordered steps are its large nodes alone.
+ * 0 = every node is a task of its own.  Default 12.  Results are the same
+ * bits either way. */
+void wmc_set_batch_subtrees(int32_t max_rank);
 typedef struct {
-  int64_t n_formulas, n_nodes, n_tasks;
+  int64_t n_formulas;
+  int64_t n_nodes;          /* scheduled units: a node, a chain, or the set of a
+                               formula's small subtrees */
+  int64_t n_tasks;
   int64_t workspace_bytes;
   double algorithmic_bytes;
   int32_t max_rank;

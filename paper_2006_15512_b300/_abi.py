@@ -158,6 +158,7 @@ EXPORTS = {
     "wmc_set_cta_walk": (None, [c_i32]),
     "wmc_set_batch_schedule": (None, [c_i32, c_i32]),
     "wmc_set_batch_fusion": (None, [c_i32]),
+    "wmc_set_batch_subtrees": (None, [c_i32]),
 }
 
 for _name, (_res, _args) in EXPORTS.items():

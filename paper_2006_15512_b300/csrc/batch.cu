@@ -60,8 +60,9 @@ struct BNode {
   int8_t f;                 // stream mode: output bits absent from A ("S-free", <= 4)
   int8_t rB;                // rank of B
   int8_t pad0;
-  int32_t chain;            // chain mode (stream == 2): index of its BChain
-  int32_t pad1;
+  int32_t chain;            // chain mode (stream == 2): index of its BChain; subtrees
+                            // (stream == 3): index of the formula's first BGroup
+  float est_us;             // subtrees: estimated microseconds per task (list scheduling)
   int8_t posA[32], posB[32], sposA[24], sposB[24];
 };
 
@@ -85,6 +86,14 @@ struct BChain {
   int8_t us[4][32];                   // u bit -> S_i bit (-1: none)
 };
 
+// One small subtree of a formula, run by one block as one task: its nodes
+// (members[first .. first + n), in post-order) one after another, each in
+// a single pass over its outputs, with no waits (every operand is a leaf
+// or an earlier member's output).
+struct BGroup {
+  int32_t first, n;
+};
+
 struct BTask {
   int32_t node;
   int32_t chunk;
@@ -106,6 +115,8 @@ struct BatchArgs {
   char *ws;
   const BNode *nodes;
   const BChain *chains;
+  const BGroup *groups;
+  const BNode *members;
   const BTask *tasks;
   int32_t n_tasks;
   uint32_t *next;           // task counter
@@ -133,40 +144,64 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t target)
 // takes consecutive tasks of one node).  A task covers 2^chunk_log2
 // consecutive outputs, at most 2^16: rows 0-1 map the task-local output
 // bits to A's offset, rows 2-3 to B's, rows 4/6/8 the summed bits 0-7,
-// 8-15, 16-23 to A's, rows 5/7/9 to B's; only the rows the node uses are
-// built.  Entry v of a row is the OR of the single-bit offsets of v's set
-// bits.
-constexpr int kLutRows = 10;
+// 8-15, 16-23 to A's, rows 5/7/9 to B's.  Entry v of a row is the OR of
+// the single-bit offsets of v's set bits.
+constexpr int kLutRows = 12;        // (12 for chain mode: 2 per operand)
+#ifndef WMC_BATCH_THREADS
+#define WMC_BATCH_THREADS 256
+#endif
+constexpr int kBThreads = WMC_BATCH_THREADS;  // threads of a persistent block
+constexpr int kBlocksPerSM = 1024 / kBThreads;  // resident blocks per SM (the launch bounds)
 
-__device__ __forceinline__ void batch_lut(const BNode &nd, uint32_t (*lut)[256]) {
-  const int lbits = nd.chunk_log2;          // task-local output bits
-  const int rows_out = lbits > 8 ? 2 : 1;
-  const int rows_sum = (nd.k + 7) >> 3;     // 0..3
-  for (int i = threadIdx.x; i < kLutRows * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255;
-    int base, nb;
-    const int8_t *pos;
-    if (row < 4) {
-      const int half = row & 1;
-      if (half >= rows_out) continue;  // (entry 0 is cleared below)
-      base = half * 8;
-      nb = min(8, lbits - base);
-      pos = (row < 2 ? nd.posA : nd.posB) + base;
-    } else {
-      const int grp = (row - 4) >> 1;
-      if (grp >= rows_sum) continue;
-      base = grp * 8;
-      nb = min(8, nd.k - base);
-      pos = ((row & 1) == 0 ? nd.sposA : nd.sposB) + base;
-    }
+// Scratch of the table builders: each row's eight single-bit offsets and
+// its two 16-entry nibble tables.
+struct RowScratch {
+  uint32_t bit[kLutRows][8];
+  uint32_t nib[kLutRows][2][16];
+};
+
+// Rows 0..n_rows-1 of 256 entries from rs.bit (filled by the caller before
+// a barrier): entry v = OR of bit[r][b] over the set bits b of v, as the
+// OR of two nibble-table entries, so every thread builds whole entries
+// with two shared loads.  Ends with a barrier.
+__device__ __forceinline__ void rows_from_bits(uint32_t (*rows)[256], RowScratch &rs, int n_rows) {
+  for (int i = threadIdx.x; i < n_rows * 32; i += blockDim.x) {
+    const int r = i >> 5, h = (i >> 4) & 1, v = i & 15;
     uint32_t o = 0;
-    for (int b = 0; b < nb; ++b)
-      if (((v >> b) & 1) && pos[b] >= 0) o |= 1u << pos[b];
-    lut[row][v] = o;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if ((v >> b) & 1) o |= rs.bit[r][4 * h + b];
+    rs.nib[r][h][v] = o;
   }
-  // entry 0 of every row is read even where the row is unused (a zero
-  // high byte): it is 0
-  if (threadIdx.x < kLutRows) lut[threadIdx.x][0] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_rows * 256; i += blockDim.x) {
+    const int r = i >> 8, v = i & 255;
+    rows[r][v] = rs.nib[r][0][v & 15] | rs.nib[r][1][v >> 4];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t bit_of(int8_t pos) { return pos >= 0 ? 1u << pos : 0u; }
+
+__device__ __forceinline__ void batch_lut(const BNode &nd, uint32_t (*lut)[256], RowScratch &rs) {
+  const int lbits = nd.chunk_log2;  // task-local output bits
+  // every row (entry 0 of the unused ones is read where an index's high
+  // byte is zero, and must be 0)
+  const int n_rows = 10;
+  for (int i = threadIdx.x; i < n_rows * 8; i += blockDim.x) {
+    const int row = i >> 3, b = i & 7;
+    uint32_t o = 0;
+    if (row < 4) {
+      const int j = (row & 1) * 8 + b;
+      if (j < lbits) o = bit_of(row < 2 ? nd.posA[j] : nd.posB[j]);
+    } else {
+      const int j = ((row - 4) >> 1) * 8 + b;
+      if (j < nd.k) o = bit_of((row & 1) == 0 ? nd.sposA[j] : nd.sposB[j]);
+    }
+    rs.bit[row][b] = o;
+  }
+  __syncthreads();
+  rows_from_bits(lut, rs, n_rows);
 }
 
 // A's and B's offsets of a task's first output (its bits above the task's
@@ -251,52 +286,58 @@ struct StreamGeom {
   uint32_t as[4], ss[4];         // summed assignment s -> A offset, S offset
   uint32_t sl[4];                // u's two lowest bits -> S offset (vector path)
   int8_t uc[32], ua[32], us[32]; // u bit -> C bit, A bit, S bit (-1: none)
+  int8_t vc[4], vs[4], nv;       // S-free bit -> C bit, S bit; their number
 };
 constexpr int kSMaxS = 256;      // S entries staged (B rank <= 8)
 
-__device__ __forceinline__ void stream_geom(const BNode &nd, StreamGeom &g) {
-  if (threadIdx.x == 0) {
-    int nu = 0, nv = 0;
-    int8_t vc[4] = {0, 0, 0, 0}, vs[4] = {0, 0, 0, 0};
-    for (int j = 0; j < nd.rC; ++j) {
-      if (nd.posA[j] >= 0) { g.uc[nu] = (int8_t)j; g.ua[nu] = nd.posA[j]; g.us[nu] = nd.posB[j]; ++nu; }
-      else if (nv < 4) { vc[nv] = (int8_t)j; vs[nv] = nd.posB[j]; ++nv; }
+__device__ __forceinline__ void stream_geom(const BNode &nd, StreamGeom &g, RowScratch &rs) {
+  // u bits (C's bits that A holds) and S-free bits, in C's order: one
+  // warp compacts them with ballots
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x;
+    const int8_t pa = j < nd.rC ? nd.posA[j] : (int8_t)-1, pb = j < nd.rC ? nd.posB[j] : (int8_t)-1;
+    const unsigned mu = __ballot_sync(0xffffffffu, j < nd.rC && pa >= 0);
+    const unsigned mv = __ballot_sync(0xffffffffu, j < nd.rC && pa < 0);
+    const unsigned below = (1u << j) - 1u;
+    if (j < nd.rC && pa >= 0) {
+      const int r = __popc(mu & below);
+      g.uc[r] = (int8_t)j; g.ua[r] = pa; g.us[r] = pb;
+    } else if (j < nd.rC) {
+      const int r = __popc(mv & below);
+      if (r < 4) { g.vc[r] = (int8_t)j; g.vs[r] = pb; }
     }
-    for (int v = 0; v < 16; ++v) {
-      uint32_t c = 0, sv = 0;
-      for (int i = 0; i < nv; ++i)
-        if ((v >> i) & 1) { c |= 1u << vc[i]; if (vs[i] >= 0) sv |= 1u << vs[i]; }
-      g.cv[v] = c; g.sv[v] = sv;
-    }
-    for (int sidx = 0; sidx < 4; ++sidx) {
-      uint32_t a = 0, sb = 0;
-      for (int i = 0; i < nd.k; ++i)
-        if ((sidx >> i) & 1) {
-          if (nd.sposA[i] >= 0) a |= 1u << nd.sposA[i];
-          if (nd.sposB[i] >= 0) sb |= 1u << nd.sposB[i];
-        }
-      g.as[sidx] = a; g.ss[sidx] = sb;
-    }
-    for (int e = 0; e < 4; ++e) {
-      uint32_t o = 0;
-      for (int i = 0; i < 2 && i < nu; ++i)
-        if (((e >> i) & 1) && g.us[i] >= 0) o |= 1u << g.us[i];
-      g.sl[e] = o;
-    }
+    if (j == 0) g.nv = (int8_t)min(4, __popc(mv));
   }
   __syncthreads();
-  // scalar path: rows over u-local bits 0-7 and 8-15; vector path (groups
-  // of four u): bits 2-9 and 10-17, so that consecutive threads, which take
-  // consecutive groups, read consecutive entries (no bank conflicts)
   const int cl = nd.chunk_log2, lo = nd.vec4 ? 2 : 0;
-  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255, base = lo + (row & 1) * 8;
-    const int8_t *pos = row < 2 ? g.uc : (row < 4 ? g.ua : g.us);
+  const int t = threadIdx.x;
+  if (t < 16) {  // S-free assignment v -> C and S offsets
+    uint32_t c = 0, sv = 0;
+    for (int i = 0; i < g.nv; ++i)
+      if ((t >> i) & 1) { c |= 1u << g.vc[i]; sv |= bit_of(g.vs[i]); }
+    g.cv[t] = c; g.sv[t] = sv;
+  } else if (t < 20) {  // summed assignment -> A and S offsets
+    const int sidx = t - 16;
+    uint32_t a = 0, sb = 0;
+    for (int i = 0; i < nd.k; ++i)
+      if ((sidx >> i) & 1) { a |= bit_of(nd.sposA[i]); sb |= bit_of(nd.sposB[i]); }
+    g.as[sidx] = a; g.ss[sidx] = sb;
+  } else if (t < 24) {  // u's two lowest bits -> S offset (vector path)
+    const int e = t - 20;
     uint32_t o = 0;
-    for (int b = 0; b < 8 && base + b < cl; ++b)
-      if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
-    g.lut[row][v] = o;
+    for (int i = 0; i < 2 && i < cl; ++i)
+      if ((e >> i) & 1) o |= bit_of(g.us[i]);
+    g.sl[e] = o;
+  } else if (t >= 32 && t < 32 + 48) {
+    // rows over u-local bits 0-7 and 8-15 (vector path, groups of four
+    // u: bits 2-9 and 10-17, so that consecutive threads, which take
+    // consecutive groups, read consecutive entries, no bank conflicts)
+    const int row = (t - 32) >> 3, b = (t - 32) & 7, jb = lo + (row & 1) * 8 + b;
+    const int8_t *pos = row < 2 ? g.uc : (row < 4 ? g.ua : g.us);
+    rs.bit[row][b] = jb < cl ? bit_of(pos[jb]) : 0u;
   }
+  __syncthreads();
+  rows_from_bits(g.lut, rs, 6);
 }
 
 template <typename T, int NS>
@@ -404,37 +445,33 @@ struct ChainGeom {
   uint32_t dC[16];        // C_D offset of the final state s (bit i = y_i)
 };
 
-__device__ __forceinline__ void chain_geom(const BNode &nd, const BChain &ch, ChainGeom &g) {
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < 16; ++j) {
+__device__ __forceinline__ void chain_geom(const BNode &nd, const BChain &ch, ChainGeom &g, RowScratch &rs) {
+  const int D = ch.D, cl = nd.chunk_log2;
+  for (int t = threadIdx.x; t < 16 + 64 + 96; t += blockDim.x) {
+    if (t < 16) {  // x-state -> A_1 offset, final state -> C_D offset
       uint32_t pa = 0, dc = 0;
-      for (int i = 0; i < ch.D; ++i)
-        if ((j >> i) & 1) {
-          pa |= 1u << ch.xa[i];
-          if (ch.yc[i] >= 0) dc |= 1u << ch.yc[i];
-        }
-      g.pA[j] = pa;
-      g.dC[j] = dc;
-      for (int i = 0; i < 4; ++i) {
-        uint32_t o = 0;
-        if (i < ch.D) {
-          const int8_t b[4] = {ch.sx[i], ch.sy[i], ch.s1[i], ch.s2[i]};
-          for (int t = 0; t < 4; ++t)
-            if (((j >> t) & 1) && b[t] >= 0) o |= 1u << b[t];
-        }
-        g.dS[i][j] = o;
+      for (int i = 0; i < D; ++i)
+        if ((t >> i) & 1) { pa |= 1u << ch.xa[i]; dc |= bit_of(ch.yc[i]); }
+      g.pA[t] = pa; g.dC[t] = dc;
+    } else if (t < 16 + 64) {  // S_i offset of (x_i, y_i, y_{i-1}, y_{i-2})
+      const int i = (t - 16) >> 4, j = (t - 16) & 15;
+      uint32_t o = 0;
+      if (i < D) {
+        if (j & 1) o |= bit_of(ch.sx[i]);
+        if (j & 2) o |= bit_of(ch.sy[i]);
+        if (j & 4) o |= bit_of(ch.s1[i]);
+        if (j & 8) o |= bit_of(ch.s2[i]);
       }
+      g.dS[i][j] = o;
+    } else {  // rows 2t'+h: u-local bits 8h..8h+7 -> A_1, C_D, S_1..S_4
+      const int row = (t - 80) >> 3, b = (t - 80) & 7, jb = (row & 1) * 8 + b, tg = row >> 1;
+      uint32_t o = 0;
+      if (jb < cl && tg < 2 + D) o = bit_of(tg == 0 ? ch.ua[jb] : (tg == 1 ? ch.uc[jb] : ch.us[tg - 2][jb]));
+      rs.bit[row][b] = o;
     }
   }
-  const int cl = nd.chunk_log2, rows = 2 * (2 + ch.D);
-  for (int i = threadIdx.x; i < rows * 256; i += blockDim.x) {
-    const int row = i >> 8, v = i & 255, base = (row & 1) * 8, t = row >> 1;
-    const int8_t *pos = t == 0 ? ch.ua : (t == 1 ? ch.uc : ch.us[t - 2]);
-    uint32_t o = 0;
-    for (int b = 0; b < 8 && base + b < cl; ++b)
-      if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
-    g.lut[row][v] = o;
-  }
+  __syncthreads();
+  rows_from_bits(g.lut, rs, 2 * (2 + D));
 }
 
 // C_D's exponent: A_1's and every S_i's (the intermediates are never
@@ -660,10 +697,29 @@ __device__ void run_task(const BatchArgs &ba, const BNode &nd, int chunk, uint32
   task_maxmin<TO>(ws, nd, tmax, tmin, red);
 }
 
+// One task of a node in the generic or the stream mode.
+__device__ __forceinline__ void run_one(const BatchArgs &ba, const BNode &nd, int chunk, uint32_t (*lut)[256],
+                                        const StreamGeom &geom, double *s_S, unsigned long long *red) {
+  float *s_Sf = reinterpret_cast<float *>(s_S);
+  if (nd.stream && nd.ti == 1) {
+    if (nd.k == 0) run_stream<double, 1>(ba, nd, chunk, geom, s_S, red);
+    else if (nd.k == 1) run_stream<double, 2>(ba, nd, chunk, geom, s_S, red);
+    else run_stream<double, 4>(ba, nd, chunk, geom, s_S, red);
+  } else if (nd.stream) {
+    if (nd.k == 0) run_stream<float, 1>(ba, nd, chunk, geom, s_Sf, red);
+    else if (nd.k == 1) run_stream<float, 2>(ba, nd, chunk, geom, s_Sf, red);
+    else run_stream<float, 4>(ba, nd, chunk, geom, s_Sf, red);
+  }
+  else if (nd.ti == 1) run_task<double, double, double>(ba, nd, chunk, lut, red);
+  else if (nd.to == 1) run_task<float, double, double>(ba, nd, chunk, lut, red);
+  else if (nd.ta == 1) run_task<float, double, float>(ba, nd, chunk, lut, red);
+  else run_task<float, float, float>(ba, nd, chunk, lut, red);
+}
+
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kTabBytes = cmax(cmax(sizeof(StreamGeom), kLutRows * 256 * 4), sizeof(ChainGeom));
 
-__global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
+__global__ void __launch_bounds__(kBThreads, kBlocksPerSM) k6_persistent(BatchArgs ba) {
   // a node's tables: the generic path's lookup rows or the stream mode's
   // geometry, and the stream mode's staged S
   __shared__ __align__(16) unsigned char s_tab[kTabBytes];
@@ -671,6 +727,7 @@ __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
   uint32_t (*lut)[256] = reinterpret_cast<uint32_t (*)[256]>(s_tab);
   StreamGeom &geom = *reinterpret_cast<StreamGeom *>(s_tab);
   ChainGeom &cgeom = *reinterpret_cast<ChainGeom *>(s_tab);
+  __shared__ RowScratch s_rows;
   __shared__ unsigned long long red[2];
   __shared__ int s_task, s_ok;
   int lut_node = -1;  // node whose tables the block holds
@@ -681,10 +738,10 @@ __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
     if (t >= ba.n_tasks) break;
     const BTask task = ba.tasks[t];
     const BNode &nd = ba.nodes[task.node];
-    if (task.node != lut_node) {  // overlaps the wait for the previous node
-      if (nd.stream == 2) chain_geom(nd, ba.chains[nd.chain], cgeom);
-      else if (nd.stream) stream_geom(nd, geom);
-      else batch_lut(nd, lut);
+    if (task.node != lut_node && nd.stream != 3) {  // overlaps the wait for the previous node
+      if (nd.stream == 2) chain_geom(nd, ba.chains[nd.chain], cgeom, s_rows);
+      else if (nd.stream) stream_geom(nd, geom, s_rows);
+      else batch_lut(nd, lut, s_rows);
       lut_node = task.node;
     }
     if (threadIdx.x == 0) {
@@ -696,23 +753,23 @@ __global__ void __launch_bounds__(kThreads, 4) k6_persistent(BatchArgs ba) {
     }
     __syncthreads();
     if (!s_ok) break;
-    float *s_Sf = reinterpret_cast<float *>(s_S);
     if (nd.stream == 2) {
       if (nd.ti == 1) chain_dispatch<double>(ba, nd, ba.chains[nd.chain], task.chunk, cgeom, s_S, red);
-      else chain_dispatch<float>(ba, nd, ba.chains[nd.chain], task.chunk, cgeom, s_Sf, red);
-    } else if (nd.stream && nd.ti == 1) {
-      if (nd.k == 0) run_stream<double, 1>(ba, nd, task.chunk, geom, s_S, red);
-      else if (nd.k == 1) run_stream<double, 2>(ba, nd, task.chunk, geom, s_S, red);
-      else run_stream<double, 4>(ba, nd, task.chunk, geom, s_S, red);
-    } else if (nd.stream) {
-      if (nd.k == 0) run_stream<float, 1>(ba, nd, task.chunk, geom, s_Sf, red);
-      else if (nd.k == 1) run_stream<float, 2>(ba, nd, task.chunk, geom, s_Sf, red);
-      else run_stream<float, 4>(ba, nd, task.chunk, geom, s_Sf, red);
+      else chain_dispatch<float>(ba, nd, ba.chains[nd.chain], task.chunk, cgeom, reinterpret_cast<float *>(s_S), red);
+    } else if (nd.stream == 3) {
+      // one small subtree: its nodes in turn, each over all its outputs
+      const BGroup grp = ba.groups[nd.chain + task.chunk];
+      for (int m = 0; m < grp.n; ++m) {
+        const BNode &mn = ba.members[grp.first + m];
+        if (mn.stream) stream_geom(mn, geom, s_rows);
+        else batch_lut(mn, lut, s_rows);
+        run_one(ba, mn, 0, lut, geom, s_S, red);
+        __syncthreads();  // outputs and metadata before the next member; tables free
+      }
+      lut_node = -1;
+    } else {
+      run_one(ba, nd, task.chunk, lut, geom, s_S, red);
     }
-    else if (nd.ti == 1) run_task<double, double, double>(ba, nd, task.chunk, lut, red);
-    else if (nd.to == 1) run_task<float, double, double>(ba, nd, task.chunk, lut, red);
-    else if (nd.ta == 1) run_task<float, double, float>(ba, nd, task.chunk, lut, red);
-    else run_task<float, float, float>(ba, nd, task.chunk, lut, red);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // this task's outputs and metadata before its completion count
@@ -801,6 +858,8 @@ struct wmc_batch {
   std::vector<int64_t> base;       // byte offset of each formula's workspace
   std::vector<BNode> nodes;
   std::vector<BChain> chains;
+  std::vector<BGroup> groups;
+  std::vector<BNode> members;      // the groups' nodes
   std::vector<BTask> tasks;
   std::vector<BLeaf> leaves;
   std::vector<BRoot> roots;
@@ -817,6 +876,8 @@ struct wmc_batch {
   char *d_tab = nullptr;           // tables + counters
   BNode *d_nodes = nullptr;
   BChain *d_chains = nullptr;
+  BGroup *d_groups = nullptr;
+  BNode *d_members = nullptr;
   BTask *d_tasks = nullptr;
   BLeaf *d_leaves = nullptr;
   BRoot *d_roots = nullptr;
@@ -846,35 +907,44 @@ struct wmc_batch {
 static std::vector<int32_t> qlabels(const TensorInfo &t) { return t.labels; }  // Q = 1
 
 // Task size and order of batches created after wmc_set_batch_schedule.
-static std::atomic<int32_t> g_batch_chunk{15};  // log2 outputs (stream mode: u) per task
+static std::atomic<int32_t> g_batch_chunk{14};  // log2 outputs (stream mode: u) per task
 static std::atomic<int32_t> g_batch_order{0};   // 0 list scheduling, 1 round-robin
 
 // Longest chain of frontier steps run as one pass (0: none).
 static std::atomic<int32_t> g_batch_fuse{4};
+
+// Largest output rank of a node that runs inside a small-subtree task (0: none).
+static std::atomic<int32_t> g_batch_sub{12};
+
+extern "C" void wmc_set_batch_subtrees(int32_t max_rank) {
+  g_batch_sub.store(max_rank <= 0 ? 0 : std::min(14, max_rank));
+}
 
 extern "C" void wmc_set_batch_fusion(int32_t max_steps) {
   g_batch_fuse.store(max_steps < 2 ? 0 : std::min(4, max_steps));
 }
 
 extern "C" void wmc_set_batch_schedule(int32_t chunk_log2, int32_t order) {
-  g_batch_chunk.store(chunk_log2 <= 0 ? 15 : std::min(16, std::max(8, chunk_log2)));
+  g_batch_chunk.store(chunk_log2 <= 0 ? 14 : std::min(16, std::max(8, chunk_log2)));
   g_batch_order.store(order == 1 ? 1 : 0);
 }
 
 namespace {
 
 // Estimated microseconds of one task (cost model of the list scheduling):
-// a fixed part (counter, tables, epilogue) and, per output, one store plus
-// 2^k loads of the operand holding the summed indices, at the rate one
-// block of the persistent kernel reaches on the large frontier nodes.
+// a fixed part (counter, tables, epilogue) and a rate per element moved,
+// as measured per block with every block of the persistent kernel busy
+// (4 per SM; float32, 512-formula batch): chains 0.34 ns per element
+// (2^D loads and up to 2^D stores per unit), stream mode 0.62 ns (2^k
+// loads and 2^f stores per unit), the generic path 1.1 ns per output and
+// summed term, small subtrees 8.7 us per node.
 double task_us(const BNode &n) {
   const double el = n.ti ? 2.0 : 1.0;  // element size in float32 units
-  if (n.stream == 2)  // 2^cl u: 2^D loads, 2^D (2^(D-1) shrinking) stores each
-    return 2.0 + 0.0009 * el * std::ldexp(1.0, n.chunk_log2) * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
-  if (n.stream)  // 2^cl u: 2^k loads and 2^f stores each
-    return 2.0 + 0.0009 * el * std::ldexp(1.0, n.chunk_log2) * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
-  const double outputs = std::ldexp(1.0, n.chunk_log2);
-  return 2.0 + outputs * 0.00091 * el * (1.0 + std::ldexp(1.0, n.k));
+  if (n.stream == 3) return n.est_us;
+  const double units = std::ldexp(1.0, n.chunk_log2);
+  if (n.stream == 2) return 2.0 + 0.00034 * el * units * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
+  if (n.stream) return 2.0 + 0.00062 * el * units * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
+  return 2.0 + 0.0011 * el * units * (1.0 + std::ldexp(1.0, n.k));
 }
 
 int pos_in(const std::vector<int32_t> &L, int32_t v) {
@@ -913,11 +983,13 @@ struct ChainSpec {
 // steps each: the first step adds one index, the others one or none (a
 // step adding none ends the chain), every x_i is an index of A_1 that no
 // earlier S holds, and S_i holds no index added before y_{i-2}.
+// Nodes of small subtrees (they run in subtree tasks) take no part.
 // chain_at[n] = the chain node n starts (-1: none); absorbed[n] = 1 for the
-// other members, 2 for the nodes that run before their chain (the
+// other members, 2 for the other nodes that run before their chain (of the
 // subtrees of S_2..S_D, between n_1 and n_D in post-order).
 void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, int max_d,
-                 std::vector<ChainSpec> &chains, std::vector<int32_t> &chain_at, std::vector<uint8_t> &absorbed) {
+                 const std::vector<uint8_t> &small, std::vector<ChainSpec> &chains, std::vector<int32_t> &chain_at,
+                 std::vector<uint8_t> &absorbed) {
   const size_t nn = plan.nodes.size();
   chain_at.assign(nn, -1);
   absorbed.assign(nn, 0);
@@ -931,7 +1003,7 @@ void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, 
   // float32 plans keep the float64 root out of chains
   auto typed = [&](int64_t c) { return f64 || !t_dbl[(size_t)c]; };
   for (size_t ni = 0; ni < nn; ++ni) {
-    if (absorbed[ni]) continue;
+    if (absorbed[ni] || small[ni]) continue;
     const Node &n0 = plan.nodes[ni];
     int64_t r = n0.a, sid = n0.b;
     if (L(sid).size() > L(r).size()) std::swap(r, sid);
@@ -947,7 +1019,7 @@ void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, 
       const int64_t last = cs.nodes.back();
       const int64_t cprev = plan.nodes[(size_t)last].c;
       const int64_t nj = consumer[(size_t)cprev];
-      if (nj < 0 || absorbed[(size_t)nj]) break;
+      if (nj < 0 || absorbed[(size_t)nj] || small[(size_t)nj]) break;
       const Node &nd = plan.nodes[(size_t)nj];
       const int64_t sj = nd.a == cprev ? nd.b : nd.a;
       int32_t xj, yj;
@@ -968,7 +1040,7 @@ void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, 
     const int64_t last = cs.nodes.back();
     for (size_t i = 1; i < cs.nodes.size(); ++i) absorbed[(size_t)cs.nodes[i]] = 1;
     for (int64_t q = (int64_t)ni + 1; q < last; ++q)
-      if (!absorbed[(size_t)q]) absorbed[(size_t)q] = 2;
+      if (!absorbed[(size_t)q] && !small[(size_t)q]) absorbed[(size_t)q] = 2;
     chain_at[ni] = (int32_t)chains.size();
     chains.push_back(std::move(cs));
   }
@@ -1061,49 +1133,103 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
     if (rc) { delete b; return rc; }
     const std::vector<int64_t> &tb = *lv.t_bytes;
     auto lab = [&](int64_t t) -> const std::vector<int32_t> & { return plan.tensors[(size_t)t].labels; };
-    // chains, and the execution order: a chain's S_2..S_D subtrees run
-    // before its first step
+    const size_t nn = plan.nodes.size();
+    auto node_of = [&](int64_t t) { return (size_t)plan.tensors[(size_t)t].node; };
+    // small subtrees: nodes of output rank <= g_batch_sub with at most 2^8
+    // summed terms whose children are leaves or such nodes (never the
+    // root); each maximal one runs as one task, all of a formula's such
+    // tasks before its other nodes
+    std::vector<uint8_t> small(nn, 0);
+    const int32_t sub_rank = g_batch_sub.load();
+    if (sub_rank > 0)
+      for (size_t ni = 0; ni + 1 < nn; ++ni) {
+        const Node &nd = plan.nodes[ni];
+        bool ok = (int32_t)lab(nd.c).size() <= sub_rank && nd.n_summed <= 8;
+        for (int64_t ch : {nd.a, nd.b})
+          if (ch >= plan.n_leaves && !small[node_of(ch)]) ok = false;
+        small[ni] = ok ? 1 : 0;
+      }
+    // each maximal small subtree's nodes, in the plan's order (children
+    // first); the node list is topologically ordered, so a subtree need not
+    // be contiguous in it
+    std::vector<std::vector<int64_t>> groups;
+    {
+      std::vector<int64_t> consumer(plan.tensors.size(), -1), stack;
+      for (size_t ni = 0; ni < nn; ++ni) {
+        consumer[(size_t)plan.nodes[ni].a] = (int64_t)ni;
+        consumer[(size_t)plan.nodes[ni].b] = (int64_t)ni;
+      }
+      for (size_t ni = 0; ni < nn; ++ni) {
+        if (!small[ni]) continue;
+        const int64_t cons = consumer[(size_t)plan.nodes[ni].c];
+        if (cons >= 0 && small[(size_t)cons]) continue;  // not a subtree's root
+        std::vector<int64_t> g;
+        stack.assign(1, (int64_t)ni);
+        while (!stack.empty()) {
+          const int64_t q = stack.back();
+          stack.pop_back();
+          g.push_back(q);
+          for (int64_t ch : {plan.nodes[(size_t)q].a, plan.nodes[(size_t)q].b})
+            if (ch >= plan.n_leaves) stack.push_back((int64_t)node_of(ch));
+        }
+        std::sort(g.begin(), g.end());
+        groups.push_back(std::move(g));
+      }
+    }
+    // chains, and the execution order of the other nodes: a chain's
+    // S_2..S_D subtrees run before its first step
     std::vector<ChainSpec> specs;
     std::vector<int32_t> chain_at;
     std::vector<uint8_t> absorbed;
-    find_chains(plan, *lv.t_dbl, prec == WMC_FP64, g_batch_fuse.load(), specs, chain_at, absorbed);
+    find_chains(plan, *lv.t_dbl, prec == WMC_FP64, g_batch_fuse.load(), small, specs, chain_at, absorbed);
     std::vector<int64_t> order;
-    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
-      if (absorbed[ni]) continue;
+    for (size_t ni = 0; ni < nn; ++ni) {
+      if (absorbed[ni] || small[ni]) continue;
       if (chain_at[ni] >= 0)
         for (int64_t q = (int64_t)ni + 1; q < specs[(size_t)chain_at[ni]].nodes.back(); ++q)
           if (absorbed[(size_t)q] == 2) order.push_back(q);
       order.push_back((int64_t)ni);
     }
-    // the intermediates' arena, first fit in that order (a chain's inner
-    // outputs are never stored); leaves and metadata as in the plan's layout
+    // layout: the small subtrees' outputs side by side after the leaves
+    // (64-byte aligned, never reused), then the other intermediates' arena,
+    // first fit in execution order (a chain's inner outputs are never
+    // stored); leaves and metadata as in the plan's layout
     std::vector<int64_t> t_off(*lv.t_off);
+    int64_t gtop = lv.arena0;
+    for (const auto &g : groups)
+      for (int64_t m : g) {
+        const int64_t c = plan.nodes[(size_t)m].c;
+        t_off[(size_t)c] = gtop;
+        gtop += (tb[(size_t)c] + 63) / 64 * 64;
+      }
+    const int64_t arena1 = align_up(gtop);
     FirstFit ff;
+    auto in_arena = [&](int64_t t) { return t >= plan.n_leaves && !small[node_of(t)]; };
     auto release = [&](int64_t t) {
-      if (t >= plan.n_leaves) ff.release(t_off[(size_t)t] - lv.arena0, tb[(size_t)t]);
+      if (in_arena(t)) ff.release(t_off[(size_t)t] - arena1, tb[(size_t)t]);
     };
     for (int64_t ni : order) {
       const Node &nd = plan.nodes[(size_t)ni];
       if (chain_at[(size_t)ni] >= 0) {
         const ChainSpec &cs = specs[(size_t)chain_at[(size_t)ni]];
         const int64_t cD = plan.nodes[(size_t)cs.nodes.back()].c;
-        t_off[(size_t)cD] = lv.arena0 + ff.alloc(tb[(size_t)cD]);
+        t_off[(size_t)cD] = arena1 + ff.alloc(tb[(size_t)cD]);
         release(cs.a1);
         for (int64_t sid : cs.s) release(sid);
       } else {
-        t_off[(size_t)nd.c] = lv.arena0 + ff.alloc(tb[(size_t)nd.c]);
+        t_off[(size_t)nd.c] = arena1 + ff.alloc(tb[(size_t)nd.c]);
         release(nd.a);
         release(nd.b);
       }
     }
-    // replay of the order: every operand is live when read (a leaf, or an
-    // output not yet consumed) and no output overlaps a live tensor
+    // replay of the order: every arena operand is live when read (an
+    // output not yet consumed; leaves and subtree outputs stay) and no
+    // output overlaps a live tensor or leaves the arena
     {
       std::map<int64_t, int64_t> live;  // tensor -> its arena block's end
       bool ok = true;
       auto use = [&](int64_t t) {
-        if (t < plan.n_leaves) return;
-        ok = ok && live.erase(t) == 1;
+        if (in_arena(t)) ok = ok && live.erase(t) == 1;
       };
       for (int64_t ni : order) {
         const Node &nd = plan.nodes[(size_t)ni];
@@ -1116,6 +1242,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
           in.push_back(cs.a1);
         }
         const int64_t c0 = t_off[(size_t)c], c1 = c0 + align_up(tb[(size_t)c]);
+        ok = ok && c0 >= arena1;
         for (const auto &kv : live) ok = ok && (c1 <= t_off[(size_t)kv.first] || kv.second <= c0);
         for (int64_t t : in) use(t);
         live[c] = c1;
@@ -1126,7 +1253,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
         return WMC_EPLAN_TOO_BIG;
       }
     }
-    const int64_t need = align_up(lv.arena0 + align_up(ff.top));
+    const int64_t need = align_up(arena1 + align_up(ff.top));
     if (mem_budget_bytes > 0 && off + need > mem_budget_bytes) break;  // admission by workspace bytes
     b->plans.push_back(&plan);
     b->base.push_back(off);
@@ -1156,15 +1283,89 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
     // metadata regions to clear each run: flags + error + exponents + maxima, then minima
     b->clears.push_back({base + lv.off_flags, lv.off_max + 8 * lv.n_slots - lv.off_flags, 0, 0});
     b->clears.push_back({base + lv.off_min, 8 * lv.n_slots, 0xff, 0});
-    // nodes, in execution order
+    // one node in the generic or the stream mode; `whole`: one task over
+    // all its outputs (a subtree member)
+    auto fill_node = [&](const Node &nd, BNode &n, bool whole) -> bool {
+      std::memset(&n, 0, sizeof(n));
+      n.chain = -1;
+      n.a = base + t_off[(size_t)nd.a];
+      n.b = base + t_off[(size_t)nd.b];
+      n.c = base + t_off[(size_t)nd.c];
+      n.ea = slot(lv.off_exp, nd.a); n.eb = slot(lv.off_exp, nd.b); n.ec = slot(lv.off_exp, nd.c);
+      n.xa = slot(lv.off_max, nd.a); n.xb = slot(lv.off_max, nd.b); n.xc = slot(lv.off_max, nd.c);
+      n.na = slot(lv.off_min, nd.a); n.nb = slot(lv.off_min, nd.b); n.nc = slot(lv.off_min, nd.c);
+      n.flags = base + lv.off_flags;
+      k1_bitmaps(qlabels(plan.tensors[(size_t)nd.a]), qlabels(plan.tensors[(size_t)nd.b]),
+                 qlabels(plan.tensors[(size_t)nd.c]), &n.rC, &n.k, n.posA, n.posB, n.sposA, n.sposB);
+      if (n.k > 24 || n.rC > 31) return false;
+      int32_t ra = (int32_t)plan.tensors[(size_t)nd.a].labels.size();
+      int32_t rb = (int32_t)plan.tensors[(size_t)nd.b].labels.size();
+      if (rb > ra) {  // A = the operand with more indices (the product commutes, term by term)
+        std::swap(n.a, n.b); std::swap(n.ea, n.eb); std::swap(n.xa, n.xb); std::swap(n.na, n.nb);
+        for (int j = 0; j < 32; ++j) std::swap(n.posA[j], n.posB[j]);
+        for (int j = 0; j < 24; ++j) std::swap(n.sposA[j], n.sposB[j]);
+        std::swap(ra, rb);
+      }
+      n.rB = (int8_t)rb;
+      n.ti = prec == WMC_FP64 ? 1 : 0;
+      n.to = (*lv.t_dbl)[(size_t)nd.c];
+      n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
+      int32_t fr = 0;
+      for (int j = 0; j < n.rC; ++j) fr += n.posA[j] < 0;
+      n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && fr <= 4) ? 1 : 0;
+      if (n.stream) {
+        // tasks over u, the assignments of C's indices that A holds
+        n.f = (int8_t)fr;
+        n.chunk_log2 = whole ? n.rC - fr : std::min<int32_t>(n.rC - fr, chunk_log2);
+        n.n_tasks = 1 << (n.rC - fr - n.chunk_log2);
+        n.vec4 = (!n.ti && n.chunk_log2 >= 3 && n.rC >= 2 && n.posA[0] == 0 && n.posA[1] == 1) ? 1 : 0;
+      } else {
+        n.chunk_log2 = whole ? n.rC : std::min<int32_t>(n.rC, chunk_log2);
+        n.n_tasks = 1 << (n.rC - n.chunk_log2);
+        bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
+                   n.posB[0] < 0 && n.posB[1] < 0;
+        for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
+        n.vec4 = (low && !n.ti && !n.ta && !n.to) ? 1 : 0;
+      }
+      b->alg_bytes += (double)tb[(size_t)nd.a] + (double)tb[(size_t)nd.b] + (double)tb[(size_t)nd.c];
+      return true;
+    };
     std::vector<int32_t> ids;
     int32_t prev = -1;
+    if (!groups.empty()) {
+      // every small subtree of the formula: one task each, no waits
+      BNode g;
+      std::memset(&g, 0, sizeof(g));
+      g.stream = 3;
+      g.prev = -1;
+      g.chain = (int32_t)b->groups.size();
+      g.n_tasks = (int32_t)groups.size();
+      int64_t n_members = 0;
+      for (const auto &gr : groups) {
+        b->groups.push_back({(int32_t)b->members.size(), (int32_t)gr.size()});
+        for (int64_t m : gr) {
+          BNode mn;
+          if (!fill_node(plan.nodes[(size_t)m], mn, true)) {
+            delete b;
+            set_error("node too large for the batch executor");
+            return WMC_EPLAN_TOO_BIG;
+          }
+          b->members.push_back(mn);
+        }
+        n_members += (int64_t)gr.size();
+      }
+      if (b->members.size() > (size_t)INT32_MAX) { delete b; set_error("batch has more than 2^31 subtree nodes"); return WMC_EPLAN_TOO_BIG; }
+      g.est_us = (float)(2.0 + 8.7 * (double)n_members / (double)groups.size());
+      prev = (int32_t)b->nodes.size();
+      ids.push_back(prev);
+      b->nodes.push_back(g);
+    }
+    // the other nodes, in execution order (the first waits for the subtrees)
     for (int64_t ni : order) {
       const Node &nd = plan.nodes[(size_t)ni];
       BNode n;
-      std::memset(&n, 0, sizeof(n));
-      n.chain = -1;
       if (chain_at[(size_t)ni] >= 0) {
+        std::memset(&n, 0, sizeof(n));
         const ChainSpec &cs = specs[(size_t)chain_at[(size_t)ni]];
         const int D = (int)cs.nodes.size();
         const int64_t cD = plan.nodes[(size_t)cs.nodes.back()].c;
@@ -1223,47 +1424,10 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
         n.chain = (int32_t)b->chains.size();
         b->chains.push_back(ch);
         b->alg_bytes += (double)tb[(size_t)cs.a1] + (double)tb[(size_t)cD];
-      } else {
-        n.a = base + t_off[(size_t)nd.a];
-        n.b = base + t_off[(size_t)nd.b];
-        n.c = base + t_off[(size_t)nd.c];
-        n.ea = slot(lv.off_exp, nd.a); n.eb = slot(lv.off_exp, nd.b); n.ec = slot(lv.off_exp, nd.c);
-        n.xa = slot(lv.off_max, nd.a); n.xb = slot(lv.off_max, nd.b); n.xc = slot(lv.off_max, nd.c);
-        n.na = slot(lv.off_min, nd.a); n.nb = slot(lv.off_min, nd.b); n.nc = slot(lv.off_min, nd.c);
-        n.flags = base + lv.off_flags;
-        k1_bitmaps(qlabels(plan.tensors[(size_t)nd.a]), qlabels(plan.tensors[(size_t)nd.b]),
-                   qlabels(plan.tensors[(size_t)nd.c]), &n.rC, &n.k, n.posA, n.posB, n.sposA, n.sposB);
-        if (n.k > 24 || n.rC > 31) { delete b; set_error("node too large for the batch executor"); return WMC_EPLAN_TOO_BIG; }
-        int32_t ra = (int32_t)plan.tensors[(size_t)nd.a].labels.size();
-        int32_t rb = (int32_t)plan.tensors[(size_t)nd.b].labels.size();
-        if (rb > ra) {  // A = the operand with more indices (the product commutes, term by term)
-          std::swap(n.a, n.b); std::swap(n.ea, n.eb); std::swap(n.xa, n.xb); std::swap(n.na, n.nb);
-          for (int j = 0; j < 32; ++j) std::swap(n.posA[j], n.posB[j]);
-          for (int j = 0; j < 24; ++j) std::swap(n.sposA[j], n.sposB[j]);
-          std::swap(ra, rb);
-        }
-        n.rB = (int8_t)rb;
-        n.ti = prec == WMC_FP64 ? 1 : 0;
-        n.to = (*lv.t_dbl)[(size_t)nd.c];
-        n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
-        int32_t f = 0;
-        for (int j = 0; j < n.rC; ++j) f += n.posA[j] < 0;
-        n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && f <= 4) ? 1 : 0;
-        if (n.stream) {
-          // tasks over u, the assignments of C's indices that A holds
-          n.f = (int8_t)f;
-          n.chunk_log2 = std::min<int32_t>(n.rC - f, chunk_log2);
-          n.n_tasks = 1 << (n.rC - f - n.chunk_log2);
-          n.vec4 = (!n.ti && n.chunk_log2 >= 3 && n.rC >= 2 && n.posA[0] == 0 && n.posA[1] == 1) ? 1 : 0;
-        } else {
-          n.chunk_log2 = std::min<int32_t>(n.rC, chunk_log2);
-          n.n_tasks = 1 << (n.rC - n.chunk_log2);
-          bool low = n.rC >= n.chunk_log2 && n.chunk_log2 >= 2 && n.posA[0] == 0 && n.posA[1] == 1 &&
-                     n.posB[0] < 0 && n.posB[1] < 0;
-          for (int j = 0; j < n.k && low; ++j) low = n.sposA[j] >= 2;
-          n.vec4 = (low && !n.ti && !n.ta && !n.to) ? 1 : 0;
-        }
-        b->alg_bytes += (double)tb[(size_t)nd.a] + (double)tb[(size_t)nd.b] + (double)tb[(size_t)nd.c];
+      } else if (!fill_node(nd, n, false)) {
+        delete b;
+        set_error("node too large for the batch executor");
+        return WMC_EPLAN_TOO_BIG;
       }
       n.prev = prev;
       prev = (int32_t)b->nodes.size();
@@ -1277,7 +1441,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
   }
   if (b->plans.empty()) { delete b; set_error("no formula fits the memory budget"); return WMC_EPLAN_TOO_BIG; }
   b->ws_bytes = off;
-  // tasks: list scheduling onto the resident blocks (8 per SM on 148 SMs;
+  // tasks: list scheduling onto the resident blocks (4 per SM on 148 SMs;
   // the order stays valid for any block count), or round-robin over the
   // formulas, each formula in post-order
   int64_t n_tasks = 0;
@@ -1285,7 +1449,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
   if (n_tasks > INT32_MAX) { delete b; set_error("batch has more than 2^31 tasks"); return WMC_EPLAN_TOO_BIG; }
   b->tasks.reserve((size_t)n_tasks);
   if (g_batch_order.load() == 0) {
-    list_schedule(b->nodes, node_ids, 148 * 8, 2.0, b->tasks);
+    list_schedule(b->nodes, node_ids, 148 * kBlocksPerSM, 2.0, b->tasks);
   } else {
     size_t longest = 0;
     for (auto &v : node_ids) longest = std::max(longest, v.size());
@@ -1308,6 +1472,8 @@ static int batch_ensure_device(wmc_batch *b) {
   int64_t o = 0;
   const int64_t o_nodes = o; o += al(sizeof(BNode) * n_nodes);
   const int64_t o_chains = o; o += al(sizeof(BChain) * (int64_t)b->chains.size());
+  const int64_t o_groups = o; o += al(sizeof(BGroup) * (int64_t)b->groups.size());
+  const int64_t o_members = o; o += al(sizeof(BNode) * (int64_t)b->members.size());
   const int64_t o_tasks = o; o += al(sizeof(BTask) * (int64_t)b->tasks.size());
   const int64_t o_leaves = o; o += al(sizeof(BLeaf) * (int64_t)b->leaves.size());
   const int64_t o_roots = o; o += al(sizeof(BRoot) * n_roots);
@@ -1323,6 +1489,8 @@ static int batch_ensure_device(wmc_batch *b) {
   char *t = b->d_tab;
   b->d_nodes = (BNode *)(t + o_nodes);
   b->d_chains = (BChain *)(t + o_chains);
+  b->d_groups = (BGroup *)(t + o_groups);
+  b->d_members = (BNode *)(t + o_members);
   b->d_tasks = (BTask *)(t + o_tasks);
   b->d_leaves = (BLeaf *)(t + o_leaves);
   b->d_roots = (BRoot *)(t + o_roots);
@@ -1338,6 +1506,8 @@ static int batch_ensure_device(wmc_batch *b) {
   };
   if (up(b->d_nodes, b->nodes.data(), sizeof(BNode) * b->nodes.size()) ||
       up(b->d_chains, b->chains.data(), sizeof(BChain) * b->chains.size()) ||
+      up(b->d_groups, b->groups.data(), sizeof(BGroup) * b->groups.size()) ||
+      up(b->d_members, b->members.data(), sizeof(BNode) * b->members.size()) ||
       up(b->d_tasks, b->tasks.data(), sizeof(BTask) * b->tasks.size()) ||
       up(b->d_leaves, b->leaves.data(), sizeof(BLeaf) * b->leaves.size()) ||
       up(b->d_roots, b->roots.data(), sizeof(BRoot) * b->roots.size()) ||
@@ -1354,7 +1524,7 @@ static int batch_ensure_device(wmc_batch *b) {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k6_persistent, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k6_persistent, kBThreads, 0);
   b->grid = std::max(1, per_sm) * std::max(1, sms);
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) { set_error("stream creation failed"); return WMC_ECUDA; }
   return WMC_OK;
@@ -1373,12 +1543,14 @@ static void batch_enqueue(wmc_batch *b, cudaStream_t s) {
   a.ws = b->d_ws;
   a.nodes = b->d_nodes;
   a.chains = b->d_chains;
+  a.groups = b->d_groups;
+  a.members = b->d_members;
   a.tasks = b->d_tasks;
   a.n_tasks = (int32_t)b->tasks.size();
   a.next = b->d_next;
   a.done = b->d_done;
   a.err = b->d_err;
-  k6_persistent<<<(unsigned)b->grid, kThreads, 0, s>>>(a);
+  k6_persistent<<<(unsigned)b->grid, kBThreads, 0, s>>>(a);
   const int32_t nr = (int32_t)b->roots.size();
   k6_finalize<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(b->d_ws, b->d_roots, nr, b->d_err, b->d_mant,
                                                           b->d_exp, b->d_flags);

@@ -719,25 +719,30 @@ def test_uneven_batch_schedules_give_the_same_bits(w):
 
 
 @pytest.mark.parametrize("precision", [FP32, FP64])
-def test_uneven_batch_chains_keep_the_bits(w, precision):
+def test_uneven_batch_chains_and_subtrees_keep_the_bits(w, precision):
     """Runs of frontier eliminations in one pass (chains of up to 2 and 4
-    steps) against one pass per contraction: the same bits for every formula
-    (a chain's inner tensors are not rescaled, and the scales are powers of
-    two), fewer algorithmic bytes, and the oracle's value."""
+    steps) and small subtrees as one task each (output ranks <= 6 and <=
+    12), against one pass per contraction, every node a task: the same bits
+    for every formula (a chain's inner tensors are not rescaled, and the
+    scales are powers of two), fewer algorithmic bytes, and the oracle's
+    value."""
     plans, cnfs, _ = _uneven(w, 16, precision, seed=11, n3=(20, 40), grid_w=(4, 8), grid_h=(6, 30))
     got, infos = [], []
     try:
-        for fz in (0, 2, 4):
+        for fz, sub in ((0, 0), (2, 0), (4, 0), (0, 6), (4, 6), (4, 12)):
             w.wmc_set_batch_fusion(fz)
+            w.wmc_set_batch_subtrees(sub)
             b = w.Batch(plans)
             infos.append(b.info())
             got.append([(r.mant, r.exp2, r.flags) for r in b.execute()])
             del b
     finally:
         w.wmc_set_batch_fusion(4)
-    assert got[0] == got[1] == got[2]
+        w.wmc_set_batch_subtrees(12)
+    assert all(g == got[0] for g in got)
     assert infos[2].algorithmic_bytes < infos[1].algorithmic_bytes < infos[0].algorithmic_bytes
     assert infos[2].n_nodes < infos[1].n_nodes < infos[0].n_nodes
+    assert infos[3].algorithmic_bytes == infos[0].algorithmic_bytes and infos[3].n_nodes < infos[0].n_nodes
     for i in range(0, len(plans), 3):
         cnf, wp, wn = cnfs[i]
         want = oracle.bucket_elim(cnf, wp, wn, order=_narrow_order(cnf))

@@ -348,10 +348,11 @@ def test_block_fp_options():
 
 
 def test_batch_chain_tables():
-    """Host side of the uneven batch's chains: longer chains leave fewer
-    nodes and tasks and fewer algorithmic bytes; the layout replay (every
-    operand live when read, no output over a live tensor) passes for every
-    chain length; chains need 2 steps at least."""
+    """Host side of the uneven batch's chains and small-subtree tasks:
+    longer chains leave fewer nodes and tasks and fewer algorithmic bytes;
+    subtree tasks leave the bytes and cut the scheduled units; the layout
+    replay (every operand live when read, no output over a live tensor)
+    passes for every setting; chains need 2 steps at least."""
     w = _lib()
     plans = []
     for h, wd, seed in ((30, 8, 1), (24, 7, 2), (16, 9, 3)):
@@ -359,20 +360,29 @@ def test_batch_chain_tables():
     plans.append(w.Plan(w.Network.from_cnf(wmcgen.random_kcnf(40, 100, seed=4)), precision=w.WMC_FP64))
     infos = {}
     try:
-        for fz in (0, 1, 2, 3, 4, 9):
-            w.wmc_set_batch_fusion(fz)
-            for prec_plans in (plans[:3], plans[3:]):
-                b = w.Batch(prec_plans)
-                assert b.n_admitted == len(prec_plans)
-                infos.setdefault(fz, []).append(b.info())
+        for sub in (0, 6):
+            w.wmc_set_batch_subtrees(sub)
+            for fz in (0, 1, 2, 3, 4, 9):
+                w.wmc_set_batch_fusion(fz)
+                for prec_plans in (plans[:3], plans[3:]):
+                    b = w.Batch(prec_plans)
+                    assert b.n_admitted == len(prec_plans)
+                    infos.setdefault((sub, fz), []).append(b.info())
     finally:
         w.wmc_set_batch_fusion(4)
-    g = {fz: v[0] for fz, v in infos.items()}  # the grids
+        w.wmc_set_batch_subtrees(12)
+    g = {fz: v[0] for (sub, fz), v in infos.items() if sub == 0}  # the grids, every node a task
     assert g[0].n_nodes == g[1].n_nodes and g[0].algorithmic_bytes == g[1].algorithmic_bytes
     assert g[4].n_nodes == g[9].n_nodes  # (at most 4 steps)
     assert g[4].n_nodes < g[3].n_nodes < g[2].n_nodes < g[0].n_nodes
     assert g[4].algorithmic_bytes < g[3].algorithmic_bytes < g[2].algorithmic_bytes < g[0].algorithmic_bytes
     assert g[4].n_tasks < g[0].n_tasks
+    # small subtrees (output rank <= 6) as one task each: the same
+    # contractions (bytes), far fewer scheduled units, in both precisions
+    for i in range(2):
+        assert infos[(6, 0)][i].algorithmic_bytes == infos[(0, 0)][i].algorithmic_bytes
+        assert infos[(6, 0)][i].n_nodes < infos[(0, 0)][i].n_nodes / 2
+        assert infos[(6, 4)][i].n_nodes <= infos[(6, 0)][i].n_nodes
 
 
 # ------------------------------------------------------ clause factoring
