@@ -513,10 +513,15 @@ typedef struct {
 int wmc_autotune_plan(wmc_plan_t *plan, int32_t Q, void *stream, wmc_tune_report *out);
 
 /* Execution option: the longest run of consecutive frontier eliminations
- * contracted in one pass over the frontier tensor (k2_chain; the
- * intermediates never reach memory), 2..4; 0 or 1 turns fusion off;
- * default 4.  Affects plans laid out after the call (a plan caches its
- * layout per Q). */
+ * contracted in one pass over the frontier tensor (the intermediates never
+ * reach memory), 2..6; 0 or 1 turns fusion off; negative (the default):
+ * up to 6 for walks of at most 16 query lanes, up to 4 for wider ones.
+ * Runs of up to four (k2_chain) take vector lanes and growth steps and
+ * stage the frontier through shared memory; runs of five or six
+ * (k2_chain_direct, float32) hold 64 values of one lane per thread, load
+ * them directly and take no growth step -- fewer launches for small walks,
+ * slower than four-step runs where the walk is bound by HBM.  Affects
+ * plans laid out after the call (a plan caches its layout per Q). */
 void wmc_set_fusion(int32_t on);
 /* Execution option (default on): every node whose whole subtree is small
  * (at most 2^16 outputs including the query bits, at most 2^8 summed

@@ -36,7 +36,7 @@ static std::atomic<int32_t> g_fail_allocs{0};
 static std::atomic<int32_t> g_debug_stall{0};
 // fusion of consecutive frontier eliminations into one k2_chain launch:
 // chains of up to this many (0 or 1: off)
-static std::atomic<int32_t> g_fuse{4};
+static std::atomic<int32_t> g_fuse{-1};  // -1: by the walk's lane count
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
 static std::atomic<int32_t> g_tensor_cores{1};  // dense float32 pair contractions on tcgen05
@@ -45,6 +45,9 @@ static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run 
 // execute as one k2_chain_seq launch (0, the default: every chain its own
 // launch, which measured faster at every batch size on the grid walks)
 static std::atomic<int32_t> g_chain_runs{0};
+// dynamic shared memory a run of chains may use: 227 KB per block less the
+// run kernel's static part (two chains' parameters and its barriers)
+constexpr size_t kSeqDynSmem = 227 * 1024 - 2 * sizeof(wmc::dev::K2CParams) - 2048;
 static std::atomic<int32_t> g_autotune{0};  // wmc_contract_pair: time same-order variants per shape
 static std::atomic<int32_t> g_cta_walk{0};  // small formulas: the whole walk in one block (opt-in)
 static std::atomic<int32_t> g_force_kind{-1};  // test hook: force one variant (-1: off)
@@ -106,9 +109,9 @@ struct Launch {
   wmc::dev::K4Params k4;
   wmc::dev::K2CParams k2c;
   int chain_d = 0, chain_fast = 0, chain_grow = 0, chain_shrink = 0;
-  int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};  // chain: S_1..S_D
-  int64_t off_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};
-  int64_t meta_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1};
+  int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};  // chain: S_1..S_D
+  int64_t off_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
+  int64_t meta_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
   size_t smem = 0;
   // relative byte offsets (patched with the workspace base at capture)
   int64_t off_a = -1, off_b = -1, off_c = -1;
@@ -133,7 +136,7 @@ static std::atomic<uint64_t> g_state_serial{0};
 // Walk options of one execution state (the process-wide defaults come from
 // the wmc_set_* calls; the plan tuner builds states with others).
 struct WalkOpts {
-  int32_t fuse = 4;         // longest chain of frontier eliminations per pass (0 or 1: none)
+  int32_t fuse = -1;        // longest chain of frontier eliminations per pass (0 or 1: none; -1 by lanes)
   int32_t small_phase = 1;  // small-node phase
   int32_t chain_runs = 0;   // runs of chains in one launch: max tiles (0: off)
   int32_t cta_walk = 0;     // a small formula's whole walk in one block (when it fits)
@@ -449,6 +452,10 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
     cur = want;
   }
   if (grow && shrink) return false;  // P and C of one size: not needed by any layout seen
+  // five or six steps: float32, no growth step, one lane (direct loads,
+  // k2_chain_direct)
+  const bool direct = D > 4;
+  if (direct && (f64 || grow)) return false;
   const std::vector<int32_t> &LCD = LC.back();
   const int NB = D + grow;
   std::memset(&cp, 0, sizeof(cp));
@@ -461,9 +468,9 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   std::sort(insc.begin(), insc.end());
   // lanes: at most 64 registers of chain values per thread, 32 KB tiles
   int vbits = f64 ? (NB <= 3 ? 1 : 0) : (NB <= 3 ? 2 : 1);
-  if (vbits < 0 || rP - D < vbits || ins[0] < vbits || (!insc.empty() && insc[0] < vbits)) vbits = 0;
+  if (direct || vbits < 0 || rP - D < vbits || ins[0] < vbits || (!insc.empty() && insc[0] < vbits)) vbits = 0;
   const int V = 1 << vbits;
-  if ((grow || shrink) && (f64 || V == 1)) return false;  // instantiated for float lanes only
+  if ((grow || shrink) && (f64 || (V == 1 && !direct))) return false;  // instantiated for float lanes only
   if (p_has_q && (nthr * V) % Qp != 0) return false;
   cp.vbits = vbits;
   cp.log2_nu = rP - D - vbits;
@@ -527,8 +534,10 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
     const int sx = pos_of(S, x[(size_t)i]);
     const int sy = y[(size_t)i] != INT32_MIN ? pos_of(S, y[(size_t)i]) : -1;
     const int sz = (i == 0 && grow) ? pos_of(S, z) : -1;
+    const uint32_t n_av = (grow && i == 0) ? 4u : 2u;  // added-value combinations the step reads
+    if ((n_av << NB) > (uint32_t)wmc::dev::kChainDRow) return false;
     for (uint32_t st = 0; st < (1u << NB); ++st)
-      for (uint32_t av = 0; av < 4; ++av) {
+      for (uint32_t av = 0; av < n_av; ++av) {
         uint32_t o = 0;
         if ((st >> i) & 1u) o |= 1u << sx;
         if ((av & 1u) && sy >= 0) o |= 1u << sy;
@@ -546,6 +555,41 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   }
   // growth and shrink steps: FAST variants with contiguous lanes only
   if ((grow || shrink) && (!fast || any_broadcast)) return false;
+  if (direct) {
+    // units are the assignments of P's other indices; a thread's units
+    // share its lane (the stride is a multiple of the lane count), so no
+    // added index may sit below the query bits
+    if (!fast) return false;
+    int m = 0;
+    while ((1 << m) < Qp) ++m;
+    if ((p_has_q && ins[0] < m) || (!insc.empty() && insc[0] < m)) return false;
+    cp.units = 1;
+    cp.tb = 0;
+    for (uint32_t st = 0; st < (1u << D); ++st) {
+      uint32_t da = 0;
+      for (int j = 0; j < D; ++j)
+        if ((st >> j) & 1u) da |= 1u << p[(size_t)j];
+      cp.pA[st] = da;  // element offset in P
+    }
+    for (uint32_t st = 0; st < (1u << NB); ++st) {
+      uint32_t dc = 0;
+      for (int j = 0; j < NB; ++j)
+        if (((st >> j) & 1u) && y[(size_t)j] != INT32_MIN) dc |= 1u << pos_of(LCD, y[(size_t)j]);
+      cp.dC[st] = dc;
+    }
+    size_t s_off = 0, s_copy = 0;
+    for (int i = 0; i < D; ++i) {
+      cp.s_bytes_off[i] = (uint32_t)s_off;
+      s_off += ((es << cp.s_log2[i]) + 15) & ~(size_t)15;
+      s_copy += es << cp.s_log2[i];
+    }
+    cp.s_bytes_off[D] = (uint32_t)s_off;
+    cp.s_copy_bytes = (uint32_t)s_copy;
+    smem = s_off + 16 * (size_t)Qp;
+    if (smem > 220 * 1024) return false;
+    v_out = 1;
+    return true;
+  }
   // tiling of P over its kept indices: 2 work units per thread when 16
   // chain states would leave runs of only 2 KB (bulk copies that short
   // lower the read rate); a growth chain's 32 states per unit already
@@ -950,7 +994,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     }
     std::vector<int64_t> fuse_next(plan.nodes.size(), -1);
     std::vector<uint8_t> absorbed(plan.nodes.size(), 0);
-    const int fuse_level = plain ? 0 : st.wo.fuse;
+    // by default, runs of up to six on walks of at most 16 lanes (launch
+    // bound: fewer, longer passes win), up to four on wider ones (bound by
+    // HBM, where the staged four-step kernel moves the bytes faster)
+    const int fuse_level = plain ? 0 : (st.wo.fuse < 0 ? (Qp <= 16 ? 6 : 4) : st.wo.fuse);
     // frontier steps: one summed index; f added ones (1 in place, 2 growth,
     // 0 shrink); a chain starts with f >= 1 and ends at its first f = 0
     auto frontier_f = [&](const Launch &l) { return (l.kind == L_K2T && l.k2.k == 1) ? l.k2.f : -1; };
@@ -1012,10 +1059,16 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       f.k2c.mc.Qc = CD.has_q ? Qp : 1;
       f.k2c.mc.Q = Qp;
       f.k2c.mc.scale_inputs = 1;
-      const uint64_t n_tiles = 1ull << (f.k2c.log2_nu + f.k2c.vbits - f.k2c.tb);
       const int per_sm = std::max<int>(1, std::min<int>(2, (int)((227u * 1024u) / (f.smem + 2048))));
-      // (registers: NW*32+32 threads of at most 96 registers leave room for two blocks)
-      f.blocks = (int64_t)std::min<uint64_t>(n_tiles, 148ull * (uint64_t)per_sm);
+      if (d_ok > 4) {  // direct loads: one unit per thread at a time, grid-stride
+        const uint64_t units = 1ull << f.k2c.log2_nu;
+        const uint64_t need = (units + wmc::dev::kDirectThreads - 1) / wmc::dev::kDirectThreads;
+        f.blocks = (int64_t)std::max<uint64_t>(1, std::min<uint64_t>(need, 148ull * (uint64_t)per_sm));
+      } else {
+        const uint64_t n_tiles = 1ull << (f.k2c.log2_nu + f.k2c.vbits - f.k2c.tb);
+        // (registers: NW*32+32 threads of at most 96 registers leave room for two blocks)
+        f.blocks = (int64_t)std::min<uint64_t>(n_tiles, 148ull * (uint64_t)per_sm);
+      }
       fuse_next[ni] = nlast;
       for (int i = 1; i < d_ok; ++i) absorbed[(size_t)chain[(size_t)i]] = 1;
       for (int64_t q = (int64_t)ni + 1; q < nlast; ++q)
@@ -1193,6 +1246,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       if (l.kind != L_K2C || l.ti != TF || l.chain_d != 4 || !l.chain_fast || (l.v != 1 && l.v != 2)) return false;
       for (int i = 0; i < l.chain_d; ++i)
         if (l.v > 1 && l.k2c.b_vec[i] != 1) return false;
+      // (the run kernel keeps two chains' parameters in static shared memory)
+      if (l.smem > kSeqDynSmem) return false;
       const int64_t tiles = int64_t(1) << (l.k2c.log2_nu + l.k2c.vbits - l.k2c.tb);
       return tiles <= (int64_t)st.wo.chain_runs;
     };
@@ -1445,8 +1500,35 @@ static void launch_k2c_plain(const Launch &l, const wmc::dev::K2CParams &p, cuda
 
 // instantiated (T, V, D) as try_chain chooses them: V at its largest for
 // the state size, or 1 when the chain positions leave no vector lanes
+template <int D, bool SHRINK>
+static void launch_k2c_direct(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(dev::k2_chain_direct<float, D, SHRINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)l.blocks);
+  cfg.blockDim = dim3(dev::kDirectThreads);
+  cfg.dynamicSmemBytes = l.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, dev::k2_chain_direct<float, D, SHRINK>, p);
+}
+
 static void launch_k2c(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
   const int D = l.chain_d, V = l.v, NB = D + l.chain_grow;
+  if (D > 4) {  // five or six steps, float32, one lane
+    if (D == 5) { if (l.chain_shrink) launch_k2c_direct<5, true>(l, p, s); else launch_k2c_direct<5, false>(l, p, s); }
+    else if (l.chain_shrink) launch_k2c_direct<6, true>(l, p, s);
+    else launch_k2c_direct<6, false>(l, p, s);
+    return;
+  }
   if (l.ti == TF) {
     if (V == 1) {
       if (D == 2) launch_k2c_plain<float, 1, 2>(l, p, s);
@@ -1473,7 +1555,7 @@ static void launch_k2cseq_t(const Launch &l, const wmc::dev::K2CParams *seq, cha
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(dev::k2_chain_seq<float, V, 4, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         220 * 1024);
+                         (int)kSeqDynSmem);
     attr_set = true;
   }
   dev::k2_chain_seq<float, V, 4, true, 0><<<(unsigned)l.blocks, dev::kChainNW * 32 + 32, l.smem, s>>>(
@@ -1620,8 +1702,9 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         cp.mc.exp = mexp + l.meta_c; cp.mc.maxb = mmax + l.meta_c; cp.mc.minb = mmin + l.meta_c;
         cp.mc.flags = flags;
         cp.err = (uint32_t *)(ws + st.off_err);
-        cp.debug_stall = stall_armed ? 1 : 0;
-        stall_armed = false;
+        // (the test hook stalls a staged copy: direct-load chains have none)
+        cp.debug_stall = (stall_armed && l.chain_d <= 4) ? 1 : 0;
+        if (l.chain_d <= 4) stall_armed = false;
         launch_k2c(l, cp, s);
         break;
       }
@@ -1832,7 +1915,7 @@ extern "C" int wmc_autotune_plan(wmc_plan_t *cplan, int32_t Q, void *stream, wmc
     WalkOpts w; w.fuse = fuse; w.small_phase = sp; w.chain_runs = runs;
     cands.push_back(w);
   };
-  add(4, 1, 0); add(3, 1, 0); add(2, 1, 0); add(0, 1, 0); add(4, 0, 0);
+  add(6, 1, 0); add(4, 1, 0); add(3, 1, 0); add(2, 1, 0); add(0, 1, 0); add(6, 0, 0);
   if (!f64) add(4, 1, 512);
   // inputs: the network's default weights for every query
   const size_t nv = (size_t)plan.n_vars;
@@ -3026,7 +3109,7 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
           for (int j = 0; j < cp.n_seg[i]; ++j)
             g |= ((oc >> cp.seg_c[i][j]) & ((1u << cp.seg_len[i][j]) - 1u)) << cp.seg_b[i][j];
           const int64_t ns = int64_t(1) << cp.s_log2[i];
-          for (int c = 0; c < (4 << NB); ++c)
+          for (int c = 0; c < std::min(4 << NB, wmc::dev::kChainDRow); ++c)
             for (int e = 0; e < V; ++e) {
               const int64_t lane = cp.b_vec[i] == 1 ? e : (cp.b_vec[i] == 2 ? 0 : cp.dv[i][e]);
               const int64_t o = (int64_t)g + cp.d[i][c] / es + lane;
@@ -3036,6 +3119,16 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
         for (int c = 0; c < (1 << NB); ++c)
           if ((int64_t)(oc | cp.dC[c]) + V - 1 >= nc) return badc("C", (int64_t)(oc | cp.dC[c]) + V - 1, nc);
         ++checked;
+      }
+      if (D > 4) {  // direct loads: no tiles; staged S_i and per-lane max/min
+        for (int i = 0; i < D; ++i)
+          if (cp.s_bytes_off[i] % 16 || cp.s_bytes_off[i] + ((size_t)es << cp.s_log2[i]) > cp.s_bytes_off[i + 1])
+            return badc("staged S", i, D);
+        const size_t need = cp.s_bytes_off[D] + 16 * (size_t)cp.mc.Qc;
+        if (V != 1 || l.chain_grow || need > l.smem || l.smem > 220 * 1024 ||
+            ((uint64_t)l.blocks * wmc::dev::kDirectThreads) % (uint64_t)cp.mc.Qc)
+          return badc("direct chain launch", (int64_t)need, (int64_t)l.smem);
+        continue;
       }
       const uint64_t n_tiles = 1ull << (cp.log2_nu + cp.vbits - cp.tb);
       const int64_t run_len = 1ll << cp.run_log2;

@@ -1067,7 +1067,10 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
 // staged tile by tile by bulk async copies that the whole producer warp
 // issues, with NW consumer warps.
 
-constexpr int kMaxChain = 4;
+// Up to 4 eliminations with vector lanes or a growth step (2^(D + GROW)
+// values per lane), up to 6 on one lane (64 values per thread).
+constexpr int kMaxChain = 6;
+constexpr int kChainDRow = 128;  // entries of one step's S offset table (2^NB x added values)
 constexpr int kMaxStagesC = 4;
 constexpr int kChainNW = 8;  // consumer warps
 
@@ -1100,9 +1103,9 @@ struct K2CParams {
   uint32_t dv[kMaxChain][4];      // S_i element offset of lane e (mode 0)
   // S_i byte offset of (state s, added value(s) a): d[i][s | a << NB], NB =
   // D + GROW state bits; a = y_i, or y_0 + 2 z for a growth step, or 0
-  uint32_t d[kMaxChain][4 << (kMaxChain + 1)];
+  uint32_t d[kMaxChain][kChainDRow];
   uint32_t pA[1 << kMaxChain];    // stage byte offset of P for x-state s
-  uint32_t dC[2 << kMaxChain];    // C element offset of final state s
+  uint32_t dC[1 << kMaxChain];    // C element offset of final state s (2^NB <= 64)
   uint32_t *err;
   int32_t debug_stall;
   int32_t units;                  // work units per consumer thread per tile (1, 2)
@@ -1216,7 +1219,17 @@ __device__ __forceinline__ void chain_step_m(const K2CParams &cp, uint32_t g, T 
 #pragma unroll
     for (uint32_t to = 0; to < (1u << nO); ++to) {
       const uint32_t s0 = sg | pdep_c(to, O), s1 = s0 | XB;
-      if (KIND == 1) {
+      if (KIND == 1 && V == 1 && sizeof(T) == 4) {
+        // one lane: the two outputs (y = 0, 1) of the pair as the halves of
+        // one packed FP32 FMA chain (each half an ordinary fma)
+        const float2 c = __ffma2_rn(make_float2((float)a[s1][0], (float)a[s1][0]),
+                                    make_float2((float)b[1][0][0], (float)b[1][NA - 1][0]),
+                                    __ffma2_rn(make_float2((float)a[s0][0], (float)a[s0][0]),
+                                               make_float2((float)b[0][0][0], (float)b[0][NA - 1][0]),
+                                               make_float2(0.f, 0.f)));
+        a[s0][0] = (T)c.x;
+        a[s1][0] = (T)c.y;
+      } else if (KIND == 1) {
         T c0[V], c1[V];
         fma2terms<T, V>(a[s0], a[s1], b[0][0], b[1][0], c0);
         fma2terms<T, V>(a[s0], a[s1], b[0][NA - 1], b[1][NA - 1], c1);
@@ -1271,6 +1284,41 @@ struct ChainSteps<T, V, D, FAST, BC, GROW, SHRINK, D> {
 };
 
 // min over nonzero bit patterns, tracked as (bits - 1) with zero wrapping
+
+// End of a chain launch, after the block's tiles: block 0 writes C_D's
+// exponent -- P's and every S_i's (the intermediates are never rescaled) --
+// and runs the flush test over the smallest nonzero scaled entries of all
+// D + 1 operands (a lower bound on every product the chain forms); every
+// block merges its per-lane max and min of |C_D| (smax, smin) into C_D's.
+template <typename T, int D>
+__device__ __forceinline__ void chain_epilogue(const K2CParams &cp, const unsigned long long *smax,
+                                               const unsigned long long *smin) {
+  if (blockIdx.x == 0) {
+    for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+      const int qp = q & cp.mp.qmask;
+      int64_t e = cp.mp.exp[qp] + pow2_exp_of(cp.mp.maxb[qp], T());
+      bool any_zero = cp.mp.minb[qp] == kNoMin;
+      T lo = any_zero ? (T)0 : from_bits<T>(cp.mp.minb[qp]) * operand_scale<T>(cp.mp, qp, 1);
+#pragma unroll
+      for (int s = 0; s < D; ++s) {
+        const int qs = q & cp.ms[s].qmask;
+        e += cp.ms[s].exp[qs] + pow2_exp_of(cp.ms[s].maxb[qs], T());
+        if (cp.ms[s].minb[qs] == kNoMin) any_zero = true;
+        else lo *= from_bits<T>(cp.ms[s].minb[qs]) * operand_scale<T>(cp.ms[s], qs, 1);
+      }
+      cp.mc.exp[q] = e;
+      if (cp.mc.flags && !any_zero && below_normal(lo)) {
+        if (cp.mc.Qc > 1) atomicOr(cp.mc.flags + q, 2u);
+        else
+          for (int qq = 0; qq < cp.mc.Q; ++qq) atomicOr(cp.mc.flags + qq, 2u);
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
+    if (smax[q]) atomicMax(cp.mc.maxb + q, smax[q]);
+    if (smin[q] != kNoMin) atomicMin(cp.mc.minb + q, smin[q]);
+  }
+}
 
 template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) {
@@ -1505,34 +1553,107 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
   }
   __syncthreads();
   grid_dependents_launch();  // this block's tiles are done: the next launch may start
-  // C_D's exponent: P and every S_i (the intermediates are never
-  // rescaled); flush test over the smallest nonzero scaled entries of all
-  // D + 1 operands (a lower bound on every product the chain forms)
-  if (blockIdx.x == 0) {
-    for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
-      const int qp = q & cp.mp.qmask;
-      int64_t e = cp.mp.exp[qp] + pow2_exp_of(cp.mp.maxb[qp], T());
-      bool any_zero = cp.mp.minb[qp] == kNoMin;
-      T lo = any_zero ? (T)0 : from_bits<T>(cp.mp.minb[qp]) * operand_scale<T>(cp.mp, qp, 1);
+  chain_epilogue<T, D>(cp, smax, smin);
+}
+
+// ----------------------------------------- long chains, direct loads
+//
+// Runs of D = 5..6 frontier eliminations on one lane (no growth step):
+// 2^D values per work unit, one unit per thread at a time.  The thread
+// loads its unit's 2^D values of P straight from global memory (for a
+// fixed chain state a warp's lanes read consecutive units when P's lowest
+// indices are kept ones), applies the D steps in registers with the step
+// code of k2_chain (FAST layout, P's scale folded into the staged S_1) and
+// stores C_D.  There is no staging ring: 2^D independent loads per thread
+// keep enough bytes in flight, and tiles of 64-state units would leave
+// bulk copies of only 1 KB.  pA and dC hold element offsets of the chain
+// states in P and C_D; units are the assignments of P's other indices.
+constexpr int kDirectThreads = 256;
+
+template <typename T, int D, bool SHRINK>
+__global__ void __launch_bounds__(kDirectThreads, 2) k2_chain_direct(K2CParams cp) {
+  typedef typename Bits<T>::t BT;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  unsigned char *s_area = dyn_smem;
+  unsigned long long *smax = reinterpret_cast<unsigned long long *>(s_area + cp.s_bytes_off[D]);
+  unsigned long long *smin = smax + cp.mc.Qc;
+  __shared__ int s_skip;
+  // Part 1, independent of the previous launch of the walk: the raw S_i
+  // (they come from launches that completed before the previous one began)
 #pragma unroll
-      for (int s = 0; s < D; ++s) {
-        const int qs = q & cp.ms[s].qmask;
-        e += cp.ms[s].exp[qs] + pow2_exp_of(cp.ms[s].maxb[qs], T());
-        if (cp.ms[s].minb[qs] == kNoMin) any_zero = true;
-        else lo *= from_bits<T>(cp.ms[s].minb[qs]) * operand_scale<T>(cp.ms[s], qs, 1);
-      }
-      cp.mc.exp[q] = e;
-      if (cp.mc.flags && !any_zero && below_normal(lo)) {
-        if (cp.mc.Qc > 1) atomicOr(cp.mc.flags + q, 2u);
-        else
-          for (int qq = 0; qq < cp.mc.Q; ++qq) atomicOr(cp.mc.flags + qq, 2u);
-      }
-    }
+  for (int sidx = 0; sidx < D; ++sidx) {
+    const T *S = static_cast<const T *>(cp.S[sidx]);
+    T *dst = reinterpret_cast<T *>(s_area + cp.s_bytes_off[sidx]);
+    for (uint32_t j = threadIdx.x; j < (1u << cp.s_log2[sidx]); j += blockDim.x) dst[j] = __ldg(S + j);
   }
   for (int q = threadIdx.x; q < cp.mc.Qc; q += blockDim.x) {
-    if (smax[q]) atomicMax(cp.mc.maxb + q, smax[q]);
-    if (smin[q] != kNoMin) atomicMin(cp.mc.minb + q, smin[q]);
+    smax[q] = 0;
+    smin[q] = kNoMin;
   }
+  // Part 2: P, its metadata and the error word are the previous launch's
+  grid_dependency_wait();
+  if (threadIdx.x == 0) s_skip = (cp.err && *(volatile uint32_t *)cp.err) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;  // an earlier launch of this walk gave up
+#pragma unroll
+  for (int sidx = 0; sidx < D; ++sidx) {
+    T *dst = reinterpret_cast<T *>(s_area + cp.s_bytes_off[sidx]);
+    const uint32_t qm = (uint32_t)cp.ms[sidx].qmask;
+    for (uint32_t j = threadIdx.x; j < (1u << cp.s_log2[sidx]); j += blockDim.x) {
+      T v = operand_scale<T>(cp.ms[sidx], (int)(j & qm), 1);
+      if (sidx == 0) v *= operand_scale<T>(cp.mp, (int)(j & qm), 1);
+      dst[j] *= v;
+    }
+  }
+  __syncthreads();
+  const T *P = static_cast<const T *>(cp.P);
+  T *C = static_cast<T *>(cp.C);
+  constexpr uint32_t es = (uint32_t)sizeof(T);
+  uint32_t pmask = 0, cmask = 0;
+  for (int j = 0; j < cp.n_ins; ++j) pmask |= 1u << cp.ins[j];
+  for (int j = 0; j < cp.n_insc; ++j) cmask |= 1u << cp.insc[j];
+  const uint32_t n_units = 1u << cp.log2_nu;
+  uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t op = u, oc = u, dp = stride, dc = stride;
+  for (int j = 0; j < cp.n_ins; ++j) { op = insert0(op, cp.ins[j]); dp = insert0(dp, cp.ins[j]); }
+  for (int j = 0; j < cp.n_insc; ++j) { oc = insert0(oc, cp.insc[j]); dc = insert0(dc, cp.insc[j]); }
+  const uint32_t s_area0 = smem_addr(s_area);
+  T tmax = (T)0;
+  BT tminm1 = (BT)~(BT)0;
+  for (; u < n_units; u += stride) {
+    T a[1 << D][1];
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) a[st][0] = __ldcs(P + (op | cp.pA[st]));
+    uint32_t g[D];
+#pragma unroll
+    for (int sidx = 0; sidx < D; ++sidx) {
+      uint32_t gg = 0;
+      for (int jj = 0; jj < cp.n_seg[sidx]; ++jj)
+        gg |= ((oc >> cp.seg_c[sidx][jj]) & ((1u << cp.seg_len[sidx][jj]) - 1u)) << cp.seg_b[sidx][jj];
+      g[sidx] = s_area0 + cp.s_bytes_off[sidx] + gg * es;
+    }
+    ChainSteps<T, 1, D, true, 0, 0, SHRINK, 0>::run(cp, g, a);
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) {
+      if (SHRINK && ((st >> (D - 1)) & 1)) continue;  // summed away
+      C[oc | cp.dC[st]] = a[st][0];
+      tmax = max_abs(tmax, a[st][0]);
+      tminm1 = min_m1(to_bits(a[st][0]), tminm1);
+    }
+    op = ((op | pmask) + dp) & ~pmask;
+    oc = ((oc | cmask) + dc) & ~cmask;
+  }
+  // the lane of every unit this thread took (the stride is a multiple of
+  // the lane count and the lane bits are C's lowest)
+  {
+    const int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) & (uint32_t)(cp.mc.Qc - 1));
+    if (tmax != (T)0) atomicMax(smax + q, abs_bits(tmax));
+    if (tminm1 != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1 + (BT)1));
+  }
+  __syncthreads();
+  grid_dependents_launch();  // this block's units are done: the next launch may start
+  chain_epilogue<T, D>(cp, smax, smin);
 }
 
 // ------------------------------------------ runs of chains in one launch

@@ -672,7 +672,7 @@ def test_uneven_batch_with_chain_sized_formulas(w):
         unfused = [plan_for(w, c, *wmcgen.weights_complementary(c.n_vars, 4, 0.05, 0.95), FP32) for c in cnfs]
         n_unfused = [p.info(1).launches_per_walk for p in unfused]
     finally:
-        w.wmc_set_fusion(4)
+        w.wmc_set_fusion(-1)
     assert any(p.info(1).launches_per_walk < n for p, n in zip(plans, n_unfused))  # chains formed
     batch = w.Batch(plans)
     assert batch.n_admitted == len(plans)
@@ -846,26 +846,31 @@ def test_uneven_batch_full_scale(w, precision):
 @pytest.mark.parametrize("precision", [FP64, FP32])
 def test_fused_chains_match_unfused(w, precision):
     """Consecutive frontier eliminations contracted in one pass (k2_chain,
-    chains of up to 2, 3, 4) give the same values as one pass per
-    elimination (the intermediates' pow2 scales only move into the
-    exponent), and match the oracle; longer chains move fewer bytes."""
+    chains of up to 2, 3, 4; k2_chain_direct, runs of 5 and 6 in float32)
+    give the same values as one pass per elimination (the intermediates'
+    pow2 scales only move into the exponent), and match the oracle; longer
+    chains move fewer bytes."""
     H, W_ = 16, 100
     cnf = wmcgen.grid_cnf(H, W_, 1)
     Q = 64
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=12, lo=0.05, hi=0.95)
     res, nbytes = {}, {}
     try:
-        for level in (0, 1, 2, 3, 4):
+        for level in (0, 1, 2, 3, 4, 5, 6):
             w.wmc_set_fusion(level)
             plan = plan_for(w, cnf, None, None, precision)
             res[level] = plan.execute(wq, wnq)
             nbytes[level] = plan.info(Q).algorithmic_bytes
     finally:
-        w.wmc_set_fusion(4)
+        w.wmc_set_fusion(-1)
     assert nbytes[4] < 0.7 * nbytes[0]
     assert nbytes[4] < nbytes[2] <= nbytes[0]
+    if precision == FP32:
+        # (a 16-step grid column: growth 4 + 6 + shrink 6 at six; still four
+        # passes at five, 4 + 5 + 5 + 2)
+        assert nbytes[6] < 0.8 * nbytes[4] and nbytes[5] <= nbytes[4]
     a = res[0]
-    for level in (1, 2, 3, 4):
+    for level in (1, 2, 3, 4, 5, 6):
         b = res[level]
         for q in range(Q):
             assert (a[q].mant, a[q].exp2) == (b[q].mant, b[q].exp2), (level, q)
@@ -1208,10 +1213,11 @@ def test_chain_runs_match_single_launches(w, Q):
     oracle's values."""
     cnf = wmcgen.grid_cnf(16, 100, 1)
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=12, lo=0.05, hi=0.95)
-    single = plan_for(w, cnf, None, None, FP32)
-    n1 = single.info(Q).launches_per_walk
-    r1 = single.execute(wq, wnq)
     try:
+        w.wmc_set_fusion(4)  # (runs join chains of four steps)
+        single = plan_for(w, cnf, None, None, FP32)
+        n1 = single.info(Q).launches_per_walk
+        r1 = single.execute(wq, wnq)
         w.wmc_set_chain_runs(512)
         runs = plan_for(w, cnf, None, None, FP32)
         n2 = runs.info(Q).launches_per_walk
@@ -1219,6 +1225,7 @@ def test_chain_runs_match_single_launches(w, Q):
         r2 = runs.execute(wq, wnq)
     finally:
         w.wmc_set_chain_runs(0)
+        w.wmc_set_fusion(-1)
     assert n2 * 4 < n1
     for q in range(Q):
         assert (r1[q].mant, r1[q].exp2, r1[q].flags) == (r2[q].mant, r2[q].exp2, r2[q].flags)
@@ -1235,11 +1242,13 @@ def test_chain_runs_on_two_streams(w):
     Q = 8
     wq, wnq = wmcgen.query_weights(cnf.n_vars, 2 * Q, seed=13, lo=0.05, hi=0.95)
     try:
+        w.wmc_set_fusion(4)  # (runs join chains of four steps)
         w.wmc_set_chain_runs(512)
         plan = plan_for(w, cnf, None, None, FP32)
         info = plan.info(Q)
     finally:
         w.wmc_set_chain_runs(0)
+        w.wmc_set_fusion(-1)
     ref = [plan.execute(wq[k * Q:(k + 1) * Q], wnq[k * Q:(k + 1) * Q]) for k in range(2)]
     dev = torch.device("cuda", 0)
     streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
@@ -1273,6 +1282,7 @@ def test_chain_run_bounded_wait_times_out_cleanly(w):
     cnf = wmcgen.grid_cnf(16, 100, 1)
     Q = 8
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=14, lo=0.05, hi=0.95)
+    w.wmc_set_fusion(4)  # (runs join chains of four steps)
     w.wmc_set_chain_runs(512)
     try:
         probe = plan_for(w, cnf, None, None, FP32)
@@ -1285,6 +1295,7 @@ def test_chain_run_bounded_wait_times_out_cleanly(w):
     finally:
         w.wmc_debug_stall_copies(0)
         w.wmc_set_chain_runs(0)
+        w.wmc_set_fusion(-1)
     plan2 = plan_for(w, cnf, None, None, FP32)
     res = plan2.execute(wq, wnq)
     col = [i * 100 + j + 1 for j in range(100) for i in range(16)]
@@ -1350,12 +1361,12 @@ def test_single_lane_chains_match_unfused(w):
     wp, wn = wmcgen.weights_complementary(4800, 1, 0.05, 0.95)
     out = {}
     try:
-        for fuse in (4, 0):
+        for fuse in (4, 6, 0):
             w.wmc_set_fusion(fuse)
             plan = plan_for(w, cnf, wp, wn, FP32)
             r = plan.execute()[0]
             out[fuse] = (r.mant, r.exp2, plan.info(1).launches_per_walk)
     finally:
-        w.wmc_set_fusion(4)
-    assert out[4][2] * 2 < out[0][2]
-    assert out[4][:2] == out[0][:2]
+        w.wmc_set_fusion(-1)
+    assert out[4][2] * 2 < out[0][2] and out[6][2] < out[4][2]
+    assert out[4][:2] == out[0][:2] == out[6][:2]

@@ -147,11 +147,13 @@ def test_noalloc_with_runs_of_chains(w):
     cnf = wmcgen.grid_cnf(16, 100, 1)
     Q = 4
     try:
+        w.wmc_set_fusion(4)  # (runs join chains of four steps)
         w.wmc_set_chain_runs(512)
         plan = w.Plan(w.Network.from_cnf(cnf), precision=1)
         assert plan.info(Q).launches_per_walk < 100  # chains were grouped into runs
     finally:
         w.wmc_set_chain_runs(0)
+        w.wmc_set_fusion(-1)
     _, _, dwp, dwn = _device_inputs(cnf, Q, 41)
     want = _execute_device(plan, Q, dwp, dwn)
     for _ in range(2):
