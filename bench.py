@@ -51,8 +51,8 @@ POOL = 4096
 # kernels.cuh, the TMA-staged and chain kernels' section, dev_common.cuh):
 # when that source differs, the ratio no longer describes the kernel and
 # `roofline.traffic` is null.
-TRAFFIC_CAPTURE = {"ratio": 738.3e6 / 939.7e6,
-                   "chain_source_sha256": "dbba52e6e6bebae73904632784e3daedea5c35b2770753faebe2287f017c1185"}
+TRAFFIC_CAPTURE = {"ratio": 736.2e6 / 939.7e6,
+                   "chain_source_sha256": "2989a1d9e254375b4095ade9199a235787ebcabf5f24c0e765318f6f2023fc9f"}
 
 
 def _kernel_source_sha256() -> str:
@@ -228,8 +228,23 @@ def poisson_run(srv, wq, wnq, rate, n):
     """n queries arriving as a Poisson stream at `rate` per second (seed 2),
     open loop: every arrival that is due is submitted at once (one
     wmc_submit_many call for all of them), so the client keeps up at high
-    rates.  Latency = server-stamped completion - scheduled arrival."""
+    rates.  Latency = server-stamped completion - scheduled arrival.  The
+    client's garbage collector is paused during the loop: a full collection
+    over the objects an earlier run left (tens of milliseconds) would submit
+    a burst of arrivals late and charge the pause to the server."""
+    import gc
     arr = wmcgen.poisson_arrivals(n, rate, seed=2)
+    gc.collect()
+    gc_was_on = gc.isenabled()
+    gc.disable()
+    try:
+        return _poisson_loop(srv, wq, wnq, rate, n, arr)
+    finally:
+        if gc_was_on:
+            gc.enable()
+
+
+def _poisson_loop(srv, wq, wnq, rate, n, arr):
     pool = wq.shape[0]
     tickets = []
     st0 = srv.stats()
@@ -262,6 +277,7 @@ def poisson_run(srv, wq, wnq, rate, n):
 def run_ours(args, rank, world):
     import torch
     import paper_2006_15512_b300 as w
+    w.wmc_set_fusion(args.fusion)
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
@@ -548,6 +564,7 @@ def run_other(args):
     """Measurements of the non-headline configs (one JSON line each)."""
     import torch
     import paper_2006_15512_b300 as w
+    w.wmc_set_fusion(args.fusion)
     hbm, src = peaks()
     out = {"workload": args.workload}
     if args.workload == "random3cnf":
@@ -785,6 +802,8 @@ def main():
     ap.add_argument("--plain-queries", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the fixed walk layout (no autotuning)")
+    ap.add_argument("--fusion", type=int, default=-1,
+                    help="longest chain of frontier eliminations per pass (-1: by the walk's lane count)")
     ap.add_argument("--workload", default="serving",
                     choices=["serving", "random3cnf", "grid", "sweep", "uneven", "sliced"])
     ap.add_argument("--n-formulas", type=int, default=512)

@@ -408,7 +408,7 @@ bool try_k2_tma(const K2Params &p2, const std::vector<int32_t> &LP, const std::v
 bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int32_t>> &LS,
                const std::vector<std::vector<int32_t>> &LC, bool f64, bool p_has_q, bool s1_has_q,
                int32_t Qp, bool allow_gs, wmc::dev::K2CParams &cp, int &v_out, bool &fast, int &grow,
-               int &shrink, size_t &smem) {
+               int &shrink, size_t &smem, bool one_lane = false) {
   const int D = (int)LS.size();
   if (D < 2 || D > wmc::dev::kMaxChain || (int)LC.size() != D) return false;
   const int rP = (int)LP.size();
@@ -468,7 +468,8 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   std::sort(insc.begin(), insc.end());
   // lanes: at most 64 registers of chain values per thread, 32 KB tiles
   int vbits = f64 ? (NB <= 3 ? 1 : 0) : (NB <= 3 ? 2 : 1);
-  if (direct || vbits < 0 || rP - D < vbits || ins[0] < vbits || (!insc.empty() && insc[0] < vbits)) vbits = 0;
+  if ((direct && one_lane) || vbits < 0 || rP - D < vbits || ins[0] < vbits || (!insc.empty() && insc[0] < vbits))
+    vbits = 0;
   const int V = 1 << vbits;
   if ((grow || shrink) && (f64 || (V == 1 && !direct))) return false;  // instantiated for float lanes only
   if (p_has_q && (nthr * V) % Qp != 0) return false;
@@ -556,10 +557,10 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
   // growth and shrink steps: FAST variants with contiguous lanes only
   if ((grow || shrink) && (!fast || any_broadcast)) return false;
   if (direct) {
-    // units are the assignments of P's other indices; a thread's units
-    // share its lane (the stride is a multiple of the lane count), so no
-    // added index may sit below the query bits
-    if (!fast) return false;
+    // units are the assignments of P's other indices (with V lanes); a
+    // thread's units share its lanes (the stride is a multiple of the lane
+    // count), so no added index may sit below the query bits
+    if (!fast || (V > 1 && any_broadcast)) return false;
     int m = 0;
     while ((1 << m) < Qp) ++m;
     if ((p_has_q && ins[0] < m) || (!insc.empty() && insc[0] < m)) return false;
@@ -587,7 +588,7 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
     cp.s_copy_bytes = (uint32_t)s_copy;
     smem = s_off + 16 * (size_t)Qp;
     if (smem > 220 * 1024) return false;
-    v_out = 1;
+    v_out = V;
     return true;
   }
   // tiling of P over its kept indices: 2 work units per thread when 16
@@ -1031,8 +1032,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
         const bool s1q = plan.tensors[(size_t)node_l[ni].id_b].has_q;
         bool fast = false;
         int grow = 0, shrink = 0;
+        // (five or six steps on one lane: two lanes of 64 states each were
+        // slower, 254 registers and one block per SM)
         if (try_chain(full_labels(P, m), LS, LC, st.f64, P.has_q, s1q, Qp, true, f.k2c, f.v, fast, grow, shrink,
-                      f.smem)) {
+                      f.smem, D > 4)) {
           d_ok = D;
           f.chain_fast = fast ? 1 : 0;
           f.chain_grow = grow;
@@ -1063,7 +1066,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       if (d_ok > 4) {  // direct loads: one unit per thread at a time, grid-stride
         const uint64_t units = 1ull << f.k2c.log2_nu;
         const uint64_t need = (units + wmc::dev::kDirectThreads - 1) / wmc::dev::kDirectThreads;
-        f.blocks = (int64_t)std::max<uint64_t>(1, std::min<uint64_t>(need, 148ull * (uint64_t)per_sm));
+        const uint64_t resident = 148ull * (uint64_t)(f.v == 1 ? per_sm : 1);  // (launch bounds)
+        f.blocks = (int64_t)std::max<uint64_t>(1, std::min<uint64_t>(need, resident));
       } else {
         const uint64_t n_tiles = 1ull << (f.k2c.log2_nu + f.k2c.vbits - f.k2c.tb);
         // (registers: NW*32+32 threads of at most 96 registers leave room for two blocks)
@@ -1500,11 +1504,11 @@ static void launch_k2c_plain(const Launch &l, const wmc::dev::K2CParams &p, cuda
 
 // instantiated (T, V, D) as try_chain chooses them: V at its largest for
 // the state size, or 1 when the chain positions leave no vector lanes
-template <int D, bool SHRINK>
+template <int V, int D, bool SHRINK>
 static void launch_k2c_direct(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(dev::k2_chain_direct<float, D, SHRINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(dev::k2_chain_direct<float, V, D, SHRINK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          220 * 1024);
     attr_set = true;
   }
@@ -1518,15 +1522,19 @@ static void launch_k2c_direct(const Launch &l, const wmc::dev::K2CParams &p, cud
   attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, dev::k2_chain_direct<float, D, SHRINK>, p);
+  cudaLaunchKernelEx(&cfg, dev::k2_chain_direct<float, V, D, SHRINK>, p);
 }
 
 static void launch_k2c(const Launch &l, const wmc::dev::K2CParams &p, cudaStream_t s) {
   const int D = l.chain_d, V = l.v, NB = D + l.chain_grow;
   if (D > 4) {  // five or six steps, float32, one lane
-    if (D == 5) { if (l.chain_shrink) launch_k2c_direct<5, true>(l, p, s); else launch_k2c_direct<5, false>(l, p, s); }
-    else if (l.chain_shrink) launch_k2c_direct<6, true>(l, p, s);
-    else launch_k2c_direct<6, false>(l, p, s);
+    if (D == 5) {
+      if (l.chain_shrink) launch_k2c_direct<1, 5, true>(l, p, s); else launch_k2c_direct<1, 5, false>(l, p, s);
+    } else if (l.chain_shrink) {
+      launch_k2c_direct<1, 6, true>(l, p, s);
+    } else {
+      launch_k2c_direct<1, 6, false>(l, p, s);
+    }
     return;
   }
   if (l.ti == TF) {
@@ -3125,8 +3133,8 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
           if (cp.s_bytes_off[i] % 16 || cp.s_bytes_off[i] + ((size_t)es << cp.s_log2[i]) > cp.s_bytes_off[i + 1])
             return badc("staged S", i, D);
         const size_t need = cp.s_bytes_off[D] + 16 * (size_t)cp.mc.Qc;
-        if (V != 1 || l.chain_grow || need > l.smem || l.smem > 220 * 1024 ||
-            ((uint64_t)l.blocks * wmc::dev::kDirectThreads) % (uint64_t)cp.mc.Qc)
+        if (V > 2 || l.chain_grow || need > l.smem || l.smem > 220 * 1024 ||
+            ((uint64_t)l.blocks * wmc::dev::kDirectThreads * (uint64_t)V) % (uint64_t)cp.mc.Qc)
           return badc("direct chain launch", (int64_t)need, (int64_t)l.smem);
         continue;
       }

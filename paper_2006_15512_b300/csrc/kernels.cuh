@@ -1219,17 +1219,7 @@ __device__ __forceinline__ void chain_step_m(const K2CParams &cp, uint32_t g, T 
 #pragma unroll
     for (uint32_t to = 0; to < (1u << nO); ++to) {
       const uint32_t s0 = sg | pdep_c(to, O), s1 = s0 | XB;
-      if (KIND == 1 && V == 1 && sizeof(T) == 4) {
-        // one lane: the two outputs (y = 0, 1) of the pair as the halves of
-        // one packed FP32 FMA chain (each half an ordinary fma)
-        const float2 c = __ffma2_rn(make_float2((float)a[s1][0], (float)a[s1][0]),
-                                    make_float2((float)b[1][0][0], (float)b[1][NA - 1][0]),
-                                    __ffma2_rn(make_float2((float)a[s0][0], (float)a[s0][0]),
-                                               make_float2((float)b[0][0][0], (float)b[0][NA - 1][0]),
-                                               make_float2(0.f, 0.f)));
-        a[s0][0] = (T)c.x;
-        a[s1][0] = (T)c.y;
-      } else if (KIND == 1) {
+      if (KIND == 1) {
         T c0[V], c1[V];
         fma2terms<T, V>(a[s0], a[s1], b[0][0], b[1][0], c0);
         fma2terms<T, V>(a[s0], a[s1], b[0][NA - 1], b[1][NA - 1], c1);
@@ -1558,20 +1548,30 @@ __global__ void __launch_bounds__(kChainNW * 32 + 32, 1) k2_chain(K2CParams cp) 
 
 // ----------------------------------------- long chains, direct loads
 //
-// Runs of D = 5..6 frontier eliminations on one lane (no growth step):
-// 2^D values per work unit, one unit per thread at a time.  The thread
-// loads its unit's 2^D values of P straight from global memory (for a
-// fixed chain state a warp's lanes read consecutive units when P's lowest
-// indices are kept ones), applies the D steps in registers with the step
-// code of k2_chain (FAST layout, P's scale folded into the staged S_1) and
+// Runs of D = 5..6 frontier eliminations (no growth step): 2^D values per
+// work unit and lane, one unit of V lanes (V = 1 in the walks: two lanes of
+// 64 states took 254 registers and ran slower) per thread at a time.  The thread loads its unit's
+// 2^D values of P straight from global memory (for a fixed chain state a
+// warp's lanes read consecutive units when P's lowest indices are kept
+// ones), applies the D steps in registers with the step code of k2_chain
+// (FAST layout, contiguous lanes, P's scale folded into the staged S_1) and
 // stores C_D.  There is no staging ring: 2^D independent loads per thread
 // keep enough bytes in flight, and tiles of 64-state units would leave
 // bulk copies of only 1 KB.  pA and dC hold element offsets of the chain
 // states in P and C_D; units are the assignments of P's other indices.
 constexpr int kDirectThreads = 256;
 
-template <typename T, int D, bool SHRINK>
-__global__ void __launch_bounds__(kDirectThreads, 2) k2_chain_direct(K2CParams cp) {
+template <typename T, int V>
+__device__ __forceinline__ void vload_cs(const T *p, T (&r)[V]) {
+  typedef typename VecT<T, V>::t VT;
+  VT v = __ldcs(reinterpret_cast<const VT *>(p));
+  const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+  for (int i = 0; i < V; ++i) r[i] = e[i];
+}
+
+template <typename T, int V, int D, bool SHRINK>
+__global__ void __launch_bounds__(kDirectThreads, V == 1 ? 2 : 1) k2_chain_direct(K2CParams cp) {
   typedef typename Bits<T>::t BT;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   unsigned char *s_area = dyn_smem;
@@ -1615,16 +1615,18 @@ __global__ void __launch_bounds__(kDirectThreads, 2) k2_chain_direct(K2CParams c
   const uint32_t n_units = 1u << cp.log2_nu;
   uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t stride = gridDim.x * blockDim.x;
-  uint32_t op = u, oc = u, dp = stride, dc = stride;
+  uint32_t op = u << cp.vbits, oc = u << cp.vbits, dp = stride << cp.vbits, dc = stride << cp.vbits;
   for (int j = 0; j < cp.n_ins; ++j) { op = insert0(op, cp.ins[j]); dp = insert0(dp, cp.ins[j]); }
   for (int j = 0; j < cp.n_insc; ++j) { oc = insert0(oc, cp.insc[j]); dc = insert0(dc, cp.insc[j]); }
   const uint32_t s_area0 = smem_addr(s_area);
-  T tmax = (T)0;
-  BT tminm1 = (BT)~(BT)0;
-  for (; u < n_units; u += stride) {
-    T a[1 << D][1];
+  T tmax[V];
+  BT tminm1[V];
 #pragma unroll
-    for (int st = 0; st < (1 << D); ++st) a[st][0] = __ldcs(P + (op | cp.pA[st]));
+  for (int e = 0; e < V; ++e) { tmax[e] = (T)0; tminm1[e] = (BT)~(BT)0; }
+  for (; u < n_units; u += stride) {
+    T a[1 << D][V];
+#pragma unroll
+    for (int st = 0; st < (1 << D); ++st) vload_cs<T, V>(P + (op | cp.pA[st]), a[st]);
     uint32_t g[D];
 #pragma unroll
     for (int sidx = 0; sidx < D; ++sidx) {
@@ -1633,23 +1635,27 @@ __global__ void __launch_bounds__(kDirectThreads, 2) k2_chain_direct(K2CParams c
         gg |= ((oc >> cp.seg_c[sidx][jj]) & ((1u << cp.seg_len[sidx][jj]) - 1u)) << cp.seg_b[sidx][jj];
       g[sidx] = s_area0 + cp.s_bytes_off[sidx] + gg * es;
     }
-    ChainSteps<T, 1, D, true, 0, 0, SHRINK, 0>::run(cp, g, a);
+    ChainSteps<T, V, D, true, 0, 0, SHRINK, 0>::run(cp, g, a);
 #pragma unroll
     for (int st = 0; st < (1 << D); ++st) {
       if (SHRINK && ((st >> (D - 1)) & 1)) continue;  // summed away
-      C[oc | cp.dC[st]] = a[st][0];
-      tmax = max_abs(tmax, a[st][0]);
-      tminm1 = min_m1(to_bits(a[st][0]), tminm1);
+      vstore<T, V>(C + (oc | cp.dC[st]), a[st]);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        tmax[e] = max_abs(tmax[e], a[st][e]);
+        tminm1[e] = min_m1(to_bits(a[st][e]), tminm1[e]);
+      }
     }
     op = ((op | pmask) + dp) & ~pmask;
     oc = ((oc | cmask) + dc) & ~cmask;
   }
   // the lane of every unit this thread took (the stride is a multiple of
   // the lane count and the lane bits are C's lowest)
-  {
-    const int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) & (uint32_t)(cp.mc.Qc - 1));
-    if (tmax != (T)0) atomicMax(smax + q, abs_bits(tmax));
-    if (tminm1 != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1 + (BT)1));
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    const int q = (int)((((blockIdx.x * blockDim.x + threadIdx.x) << cp.vbits) + e) & (uint32_t)(cp.mc.Qc - 1));
+    if (tmax[e] != (T)0) atomicMax(smax + q, abs_bits(tmax[e]));
+    if (tminm1[e] != (BT)~(BT)0) atomicMin(smin + q, (unsigned long long)(tminm1[e] + (BT)1));
   }
   __syncthreads();
   grid_dependents_launch();  // this block's units are done: the next launch may start
