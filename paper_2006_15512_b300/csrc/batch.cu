@@ -77,11 +77,14 @@ struct BNode {
 // y_{i-2}).
 struct BChain {
   int64_t s[4], es[4], xs[4], ns[4];  // S_i: data, exponent, max, min slots (byte offsets)
-  int8_t D, shrink, nu, pad;          // steps, last step adds nothing, passive indices
+  int8_t D, shrink, nu, grow;         // steps, last step adds nothing, passive indices, first adds two
   int8_t rs[4];                       // rank of S_i
   int8_t xa[4];                       // A_1 bit of x_i
   int8_t yc[4];                       // C_D bit of y_i (-1: the shrink step)
-  int8_t sx[4], sy[4], s1[4], s2[4];  // S_i bit of x_i, y_i, y_{i-1}, y_{i-2} (-1: none)
+  int8_t zc, pad2[3];                 // C_D bit of z, the second index a growth step adds
+  // S_i bit of x_i, y_i and of the two indices added last before step i
+  // (in the order y_0, z, y_1, ...), or of z at a growth step (-1: none)
+  int8_t sx[4], sy[4], s1[4], s2[4];
   int8_t ua[32], uc[32];              // u bit -> A_1 bit, C_D bit (u: passive indices in C_D order)
   int8_t us[4][32];                   // u bit -> S_i bit (-1: none)
 };
@@ -442,7 +445,7 @@ struct ChainGeom {
   uint32_t lut[12][256];  // rows 2t, 2t+1: u-local bits 0-7, 8-15 -> offset in A_1, C_D, S_1..S_4
   uint32_t dS[4][16];     // S_i offset of (x_i, y_i, y_{i-1}, y_{i-2}) = bits 0-3 of the entry
   uint32_t pA[16];        // A_1 offset of the x-state s (bit i = x_i)
-  uint32_t dC[16];        // C_D offset of the final state s (bit i = y_i)
+  uint32_t dC[16];        // C_D offset of the final state s (bit i = y_i, bit D = z)
 };
 
 __device__ __forceinline__ void chain_geom(const BNode &nd, const BChain &ch, ChainGeom &g, RowScratch &rs) {
@@ -452,6 +455,7 @@ __device__ __forceinline__ void chain_geom(const BNode &nd, const BChain &ch, Ch
       uint32_t pa = 0, dc = 0;
       for (int i = 0; i < D; ++i)
         if ((t >> i) & 1) { pa |= 1u << ch.xa[i]; dc |= bit_of(ch.yc[i]); }
+      if (ch.grow && ((t >> D) & 1)) dc |= bit_of(ch.zc);
       g.pA[t] = pa; g.dC[t] = dc;
     } else if (t < 16 + 64) {  // S_i offset of (x_i, y_i, y_{i-1}, y_{i-2})
       const int i = (t - 16) >> 4, j = (t - 16) & 15;
@@ -496,24 +500,56 @@ __device__ __forceinline__ void chain_exponent(char *ws, const BNode &nd, const 
   if (!zero && dev::below_normal(lo)) atomicOr((uint32_t *)(ws + nd.flags), 2u);
 }
 
-// Step I on the register block: for each state of the other bits, the two
-// values over x_I become the values over y_I (or one value when the step
-// shrinks), each a two-term fused multiply-add chain over x_I = 0, 1 from
-// zero: the order of every other kernel for one summed index.
-template <typename T, int D, bool SHRINK, int I>
-__device__ __forceinline__ void chain_step(T (&a)[1 << D], const T *S, uint32_t sb, const uint32_t *dS) {
+// State bit of the index added `back` additions before step I (0: the last
+// one, 1: the one before), in the order y_0, z (growth), y_1, y_2, ...; -1
+// when there is none.  y_j sits at bit j, z at bit D.
+__host__ __device__ constexpr int added_bit(int D, bool GROW, int I, int back) {
+  int seq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int n = 0;
+  for (int j = 0; j < I; ++j) {
+    seq[n++] = j;
+    if (j == 0 && GROW) seq[n++] = D;
+  }
+  return n - 1 - back >= 0 ? seq[n - 1 - back] : -1;
+}
+
+// Step I on the register block.  In place (the usual step): for each state
+// of the other bits, the two values over x_I become the values over y_I (one
+// value when the last step shrinks).  Growth (step 0 of a growth chain): the
+// two values over x_0 become four over (y_0, z).  Every output is a
+// two-term fused multiply-add chain over x_I = 0, 1 from zero: the order of
+// every other kernel for one summed index.  S_I's value for a state is
+// sv[x | y << 1 | d1 << 2 | d2 << 3] with d1, d2 the two indices added last
+// (at a growth step: sv[x | y_0 << 1 | z << 2]).
+template <typename T, int D, bool SHRINK, bool GROW, int I>
+__device__ __forceinline__ void chain_step(T (&a)[1 << (D + GROW)], const T *S, uint32_t sb, const uint32_t *dS) {
+  constexpr int NB = D + GROW;
   constexpr bool last = SHRINK && I == D - 1;
+  constexpr bool growth = GROW && I == 0;
+  constexpr int b1 = added_bit(D, GROW, I, 0), b2 = added_bit(D, GROW, I, 1);
   T sv[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    if ((last && (j & 2)) || (I < 1 && (j & 4)) || (I < 2 && (j & 8))) continue;
+    if ((last && (j & 2)) || ((growth ? 0 : b1) < 0 && (j & 4)) || (b2 < 0 && (j & 8)) || (growth && (j & 8)))
+      continue;
     sv[j] = S[sb | dS[j]];
   }
 #pragma unroll
-  for (int o = 0; o < (1 << D); ++o) {
+  for (int o = 0; o < (1 << NB); ++o) {
     if (o & (1 << I)) continue;
-    const int dd = (I >= 1 ? ((o >> (I - 1)) & 1) << 2 : 0) | (I >= 2 ? ((o >> (I - 2)) & 1) << 3 : 0);
+    if (growth && (o & (1 << D))) continue;  // z is not there yet
     const T a0 = a[o], a1 = a[o | (1 << I)];
+    if (growth) {
+#pragma unroll
+      for (int yz = 0; yz < 4; ++yz) {
+        const int j = (yz & 1) << 1 | (yz >> 1) << 2;
+        T c = dev::fma_t(a0, sv[j], (T)0);
+        c = dev::fma_t(a1, sv[j | 1], c);
+        a[o | ((yz & 1) << I) | ((yz >> 1) << D)] = c;
+      }
+      continue;
+    }
+    const int dd = (b1 >= 0 ? ((o >> b1) & 1) << 2 : 0) | (b2 >= 0 ? ((o >> b2) & 1) << 3 : 0);
     T c0 = dev::fma_t(a0, sv[dd], (T)0);
     c0 = dev::fma_t(a1, sv[dd | 1], c0);
     a[o] = c0;
@@ -525,22 +561,24 @@ __device__ __forceinline__ void chain_step(T (&a)[1 << D], const T *S, uint32_t 
   }
 }
 
-template <typename T, int D, bool SHRINK, int I>
+template <typename T, int D, bool SHRINK, bool GROW, int I>
 struct ChainSteps {
-  __device__ static __forceinline__ void run(T (&a)[1 << D], const T *sS, const uint32_t (&sb)[D],
+  __device__ static __forceinline__ void run(T (&a)[1 << (D + GROW)], const T *sS, const uint32_t (&sb)[D],
                                              const ChainGeom &g) {
-    chain_step<T, D, SHRINK, I>(a, sS + I * kSMaxS, sb[I], g.dS[I]);
-    ChainSteps<T, D, SHRINK, I + 1>::run(a, sS, sb, g);
+    chain_step<T, D, SHRINK, GROW, I>(a, sS + I * kSMaxS, sb[I], g.dS[I]);
+    ChainSteps<T, D, SHRINK, GROW, I + 1>::run(a, sS, sb, g);
   }
 };
-template <typename T, int D, bool SHRINK>
-struct ChainSteps<T, D, SHRINK, D> {
-  __device__ static __forceinline__ void run(T (&)[1 << D], const T *, const uint32_t (&)[D], const ChainGeom &) {}
+template <typename T, int D, bool SHRINK, bool GROW>
+struct ChainSteps<T, D, SHRINK, GROW, D> {
+  __device__ static __forceinline__ void run(T (&)[1 << (D + GROW)], const T *, const uint32_t (&)[D],
+                                             const ChainGeom &) {}
 };
 
-template <typename T, int D, bool SHRINK>
+template <typename T, int D, bool SHRINK, bool GROW>
 __device__ void run_chain(const BatchArgs &ba, const BNode &nd, const BChain &ch, int chunk, const ChainGeom &g,
                           T *sS, unsigned long long *red) {
+  constexpr int NB = D + GROW;
   char *ws = ba.ws;
   const T *A = (const T *)(ws + nd.a);
   T *C = (T *)(ws + nd.c);
@@ -574,19 +612,19 @@ __device__ void run_chain(const BatchArgs &ba, const BNode &nd, const BChain &ch
   unsigned long long tmin = kNoMin;
   for (uint32_t l = threadIdx.x; l < n_loc; l += blockDim.x) {
     const uint32_t lo = l & 255, hi = l >> 8;
-    const uint32_t ab = bA | g.lut[0][lo] | g.lut[1][hi];
     const uint32_t cb = bC | g.lut[2][lo] | g.lut[3][hi];
     uint32_t sb[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) sb[i] = bS[i] | g.lut[4 + 2 * i][lo] | g.lut[5 + 2 * i][hi];
-    T a[1 << D];
+    const uint32_t ab = bA | g.lut[0][lo] | g.lut[1][hi];
+    T a[1 << NB];
 #pragma unroll
     for (int st = 0; st < (1 << D); ++st) a[st] = ldcg(A + (ab | g.pA[st]));
 #pragma unroll
     for (int st = 0; st < (1 << D); ++st) a[st] *= sa;
-    ChainSteps<T, D, SHRINK, 0>::run(a, sS, sb, g);
+    ChainSteps<T, D, SHRINK, GROW, 0>::run(a, sS, sb, g);
 #pragma unroll
-    for (int st = 0; st < (1 << D); ++st) {
+    for (int st = 0; st < (1 << NB); ++st) {
       if (SHRINK && ((st >> (D - 1)) & 1)) continue;  // summed away
       C[cb | g.dC[st]] = a[st];
       track_out(a[st], tmax, tmin);
@@ -598,14 +636,19 @@ __device__ void run_chain(const BatchArgs &ba, const BNode &nd, const BChain &ch
 template <typename T>
 __device__ __forceinline__ void chain_dispatch(const BatchArgs &ba, const BNode &nd, const BChain &ch, int chunk,
                                                const ChainGeom &g, T *sS, unsigned long long *red) {
+  if (ch.grow) {  // growth chains: two or three steps, no shrink
+    if (ch.D == 2) run_chain<T, 2, false, true>(ba, nd, ch, chunk, g, sS, red);
+    else run_chain<T, 3, false, true>(ba, nd, ch, chunk, g, sS, red);
+    return;
+  }
   const int sel = ch.D * 2 + (ch.shrink ? 1 : 0);
   switch (sel) {
-    case 4: run_chain<T, 2, false>(ba, nd, ch, chunk, g, sS, red); break;
-    case 5: run_chain<T, 2, true>(ba, nd, ch, chunk, g, sS, red); break;
-    case 6: run_chain<T, 3, false>(ba, nd, ch, chunk, g, sS, red); break;
-    case 7: run_chain<T, 3, true>(ba, nd, ch, chunk, g, sS, red); break;
-    case 8: run_chain<T, 4, false>(ba, nd, ch, chunk, g, sS, red); break;
-    default: run_chain<T, 4, true>(ba, nd, ch, chunk, g, sS, red); break;
+    case 4: run_chain<T, 2, false, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 5: run_chain<T, 2, true, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 6: run_chain<T, 3, false, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 7: run_chain<T, 3, true, false>(ba, nd, ch, chunk, g, sS, red); break;
+    case 8: run_chain<T, 4, false, false>(ba, nd, ch, chunk, g, sS, red); break;
+    default: run_chain<T, 4, true, false>(ba, nd, ch, chunk, g, sS, red); break;
   }
 }
 
@@ -954,20 +997,20 @@ int pos_in(const std::vector<int32_t> &L, int32_t v) {
 }
 
 // A frontier step R . S -> C: one summed index x, an index of R (the
-// running tensor), at most one added index y (-1: none), S of rank <= 8.
+// running tensor), at most two added indices y, z (-1: none), S of rank
+// <= 8.
 bool frontier_step(const std::vector<int32_t> &LR, const std::vector<int32_t> &LS, const std::vector<int32_t> &LC,
-                   int32_t &x, int32_t &y) {
+                   int32_t &x, int32_t &y, int32_t &z) {
   if (LS.size() > 8) return false;
   int n_sum = 0, n_add = 0;
-  x = -1;
-  y = -1;
+  x = y = z = -1;
   for (int32_t l : LR)
     if (pos_in(LC, l) < 0) { ++n_sum; x = l; }
   for (int32_t l : LS)
     if (pos_in(LC, l) < 0 && pos_in(LR, l) < 0) ++n_sum;
   for (int32_t l : LC)
-    if (pos_in(LR, l) < 0) { ++n_add; y = l; }
-  return n_sum == 1 && x >= 0 && n_add <= 1;
+    if (pos_in(LR, l) < 0) { (n_add == 0 ? y : z) = l; ++n_add; }
+  return n_sum == 1 && x >= 0 && n_add <= 2;
 }
 
 // A chain of one formula (chain mode): its nodes n_1..n_D in order, the
@@ -975,14 +1018,17 @@ bool frontier_step(const std::vector<int32_t> &LR, const std::vector<int32_t> &L
 struct ChainSpec {
   std::vector<int64_t> nodes, s;
   std::vector<int32_t> x, y;  // y = -1: the step adds none (shrink; last only)
+  int32_t z = -1;             // second index the first step adds (growth chains)
   int64_t a1 = -1;
 };
 
 // Chains of consecutive frontier steps (Algorithm 2's post-order, the
 // output of each step the running operand of the next), at most max_d
-// steps each: the first step adds one index, the others one or none (a
-// step adding none ends the chain), every x_i is an index of A_1 that no
-// earlier S holds, and S_i holds no index added before y_{i-2}.
+// steps each: the first step adds one index, or two (a growth chain, then
+// at most 3 steps and no shrink), the others one or none (a step adding
+// none ends the chain), every x_i is an index of A_1 that no earlier S
+// holds, and the indices added so far (in the order y_0, z, y_1, ...) that
+// S_i holds are among the two added last.
 // Nodes of small subtrees (they run in subtree tasks) take no part.
 // chain_at[n] = the chain node n starts (-1: none); absorbed[n] = 1 for the
 // other members, 2 for the other nodes that run before their chain (of the
@@ -1007,34 +1053,39 @@ void find_chains(const Plan &plan, const std::vector<uint8_t> &t_dbl, bool f64, 
     const Node &n0 = plan.nodes[ni];
     int64_t r = n0.a, sid = n0.b;
     if (L(sid).size() > L(r).size()) std::swap(r, sid);
-    int32_t x, y;
-    if (!typed(n0.c) || !frontier_step(L(r), L(sid), L(n0.c), x, y) || y < 0) continue;
+    int32_t x, y, z;
+    if (!typed(n0.c) || !frontier_step(L(r), L(sid), L(n0.c), x, y, z) || y < 0) continue;
     ChainSpec cs;
     cs.a1 = r;
+    cs.z = z;
     cs.nodes.push_back((int64_t)ni);
     cs.s.push_back(sid);
     cs.x.push_back(x);
     cs.y.push_back(y);
-    while ((int)cs.nodes.size() < max_d && cs.y.back() >= 0) {
+    std::vector<int32_t> added{y};
+    if (z >= 0) added.push_back(z);
+    const int cap = z >= 0 ? std::min(max_d, 3) : max_d;
+    while ((int)cs.nodes.size() < cap && cs.y.back() >= 0) {
       const int64_t last = cs.nodes.back();
       const int64_t cprev = plan.nodes[(size_t)last].c;
       const int64_t nj = consumer[(size_t)cprev];
       if (nj < 0 || absorbed[(size_t)nj] || small[(size_t)nj]) break;
       const Node &nd = plan.nodes[(size_t)nj];
       const int64_t sj = nd.a == cprev ? nd.b : nd.a;
-      int32_t xj, yj;
-      if (!typed(nd.c) || !frontier_step(L(cprev), L(sj), L(nd.c), xj, yj)) break;
-      if (pos_in(L(r), xj) < 0) break;
+      int32_t xj, yj, zj;
+      if (!typed(nd.c) || !frontier_step(L(cprev), L(sj), L(nd.c), xj, yj, zj) || zj >= 0) break;
+      if (pos_in(L(r), xj) < 0 || (cs.z >= 0 && yj < 0)) break;
       const size_t j = cs.nodes.size();
       bool ok = true;
       for (size_t i = 0; i < j && ok; ++i) ok = pos_in(L(cs.s[i]), xj) < 0;
-      for (size_t i = 0; i + 2 < j && ok; ++i) ok = pos_in(L(sj), cs.y[i]) < 0;
+      for (size_t i = 0; i + 2 < added.size() && ok; ++i) ok = pos_in(L(sj), added[i]) < 0;
       for (int64_t q = last + 1; q < nj && ok; ++q) ok = !absorbed[(size_t)q] && chain_at[(size_t)q] < 0;
       if (!ok) break;
       cs.nodes.push_back(nj);
       cs.s.push_back(sj);
       cs.x.push_back(xj);
       cs.y.push_back(yj);
+      if (yj >= 0) added.push_back(yj);
     }
     if (cs.nodes.size() < 2) continue;
     const int64_t last = cs.nodes.back();
@@ -1374,7 +1425,8 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
         std::memset(&ch, 0xff, sizeof(ch));  // positions: -1 = none
         ch.D = (int8_t)D;
         ch.shrink = cs.y.back() < 0 ? 1 : 0;
-        ch.pad = 0;
+        ch.grow = cs.z >= 0 ? 1 : 0;
+        ch.zc = ch.grow ? (int8_t)pos_in(LC, cs.z) : (int8_t)-1;
         int nu = 0;
         for (size_t j = 0; j < LC.size(); ++j) {
           const int pa = pos_in(LA, LC[j]);
@@ -1385,7 +1437,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
           ++nu;
         }
         ch.nu = (int8_t)nu;
-        if (nu + D != (int)LA.size() || (int)LC.size() != nu + D - ch.shrink) {
+        if (nu + D != (int)LA.size() || (int)LC.size() != nu + D - ch.shrink + ch.grow) {
           delete b;
           set_error("internal: chain geometry does not add up");
           return WMC_EPLAN_TOO_BIG;
@@ -1402,8 +1454,13 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
           ch.yc[i] = cs.y[(size_t)i] >= 0 ? (int8_t)pos_in(LC, cs.y[(size_t)i]) : (int8_t)-1;
           ch.sx[i] = (int8_t)pos_in(LS, cs.x[(size_t)i]);
           ch.sy[i] = cs.y[(size_t)i] >= 0 ? (int8_t)pos_in(LS, cs.y[(size_t)i]) : (int8_t)-1;
-          ch.s1[i] = i >= 1 ? (int8_t)pos_in(LS, cs.y[(size_t)i - 1]) : (int8_t)-1;
-          ch.s2[i] = i >= 2 ? (int8_t)pos_in(LS, cs.y[(size_t)i - 2]) : (int8_t)-1;
+          // the indices behind the state bits the step's S may depend on
+          // (at a growth step: z)
+          auto label_of_bit = [&](int bit) { return bit < 0 ? -1 : (bit == D ? cs.z : cs.y[(size_t)bit]); };
+          const int b1 = added_bit(D, ch.grow != 0, i, 0), b2 = added_bit(D, ch.grow != 0, i, 1);
+          const int32_t l1 = (ch.grow && i == 0) ? cs.z : label_of_bit(b1), l2 = label_of_bit(b2);
+          ch.s1[i] = l1 >= 0 ? (int8_t)pos_in(LS, l1) : (int8_t)-1;
+          ch.s2[i] = l2 >= 0 ? (int8_t)pos_in(LS, l2) : (int8_t)-1;
           b->alg_bytes += (double)tb[(size_t)sid];
         }
         n.a = base + t_off[(size_t)cs.a1];
@@ -1414,7 +1471,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
         n.flags = base + lv.off_flags;
         n.rC = (int32_t)LC.size();
         n.k = D;                        // 2^D loads per unit
-        n.f = (int8_t)(D - ch.shrink);  // 2^f stores per unit
+        n.f = (int8_t)(D + ch.grow - ch.shrink);  // 2^f stores per unit
         n.stream = 2;
         n.ti = n.ta = n.to = prec == WMC_FP64 ? 1 : 0;
         // a unit moves 2^D values in and up to 2^D out (four times a
