@@ -1212,7 +1212,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       k1_bitmaps(full_labels(A, m), full_labels(B, m), full_labels(C, m), &sn.rC, &sn.k, pa, pb, spa, spb);
       std::memcpy(sn.posA, pa, 16); std::memcpy(sn.posB, pb, 16);
       std::memcpy(sn.sposA, spa, 8); std::memcpy(sn.sposB, spb, 8);
-      sn.chunk_log2 = std::min<int32_t>(sn.rC, 12);
+      // up to 16 chunks of at least 256 outputs (one per thread): a node on
+      // the tree's critical path spreads over blocks instead of one block
+      // walking its outputs one L2 round trip after another
+      sn.chunk_log2 = std::min<int32_t>(sn.rC, std::max<int32_t>(8, std::min<int32_t>(12, sn.rC - 4)));
       sn.n_chunks = 1 << (sn.rC - sn.chunk_log2);
       sn.ti = st.f64 ? 1 : 0;
       sn.to = st.t_dbl[(size_t)nd.c];

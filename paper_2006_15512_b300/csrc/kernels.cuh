@@ -2667,11 +2667,12 @@ __device__ __forceinline__ bool wait_ctr(const uint32_t *ctr, uint32_t target) {
 }
 
 // The node's per-byte lookup tables (they depend on the node alone, so they
-// are built before its children are waited for).
-__device__ __forceinline__ void small_lut(const SNode &nd, uint32_t (*lut)[256]) {
-  // lookup tables: rows 0-1 A, 2-3 B (output bits), 4 A, 5 B (summed bits).
-  // Entry v is the OR over v's set bits of that bit's offset: the single-bit
-  // offsets first, then entries [2^b, 2^(b+1)) = entry 2^b OR entries [0, 2^b)
+// are built before its children are waited for, and kept while a block
+// takes consecutive chunks of one node): rows 0-1 A, 2-3 B (output bits),
+// 4 A, 5 B (summed bits).  Entry v is the OR over v's set bits of that
+// bit's offset, built as the OR of two 16-entry nibble tables.
+__device__ __forceinline__ void small_lut(const SNode &nd, uint32_t (*lut)[256], uint32_t (*bits)[8],
+                                          uint32_t (*nib)[2][16]) {
   if (threadIdx.x < 6 * 8) {
     const int row = threadIdx.x >> 3, bit = threadIdx.x & 7;
     uint32_t o = 0;
@@ -2683,17 +2684,21 @@ __device__ __forceinline__ void small_lut(const SNode &nd, uint32_t (*lut)[256])
       const int8_t pos = row == 4 ? nd.sposA[bit] : nd.sposB[bit];
       if (pos >= 0) o = 1u << pos;
     }
-    lut[row][1 << bit] = o;
-    if (bit == 0) lut[row][0] = 0u;
+    bits[row][bit] = o;
   }
   __syncthreads();
-  for (int b = 1; b < 8; ++b) {
-    const int half = 1 << b;
-    for (int i = threadIdx.x; i < 6 * (half - 1); i += blockDim.x) {
-      const int row = i / (half - 1), v = 1 + i % (half - 1);
-      lut[row][half + v] = lut[row][half] | lut[row][v];
-    }
-    __syncthreads();
+  for (int i = threadIdx.x; i < 6 * 32; i += blockDim.x) {
+    const int row = i >> 5, h = (i >> 4) & 1, v = i & 15;
+    uint32_t o = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if ((v >> t) & 1) o |= bits[row][4 * h + t];
+    nib[row][h][v] = o;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
+    const int row = i >> 8, v = i & 255;
+    lut[row][v] = nib[row][0][v & 15] | nib[row][1][v >> 4];
   }
 }
 
@@ -2773,9 +2778,11 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
 
 __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
   __shared__ uint32_t lut[6][256];
+  __shared__ uint32_t lut_bits[6][8], lut_nib[6][2][16];
   __shared__ double scl_d[2 * kMaxQ];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   __shared__ int s_task, s_ok;
+  int lut_node = -1;  // node whose tables the block holds
   for (;;) {
     if (threadIdx.x == 0) s_task = (int)atomicAdd(a.next, 1u);
     __syncthreads();
@@ -2783,7 +2790,10 @@ __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
     if (t >= a.n_tasks) break;
     const STask task = a.tasks[t];
     const SNode &nd = a.nodes[task.node];
-    small_lut(nd, lut);  // overlaps the wait for the children
+    if (task.node != lut_node) {  // overlaps the wait for the children
+      small_lut(nd, lut, lut_bits, lut_nib);
+      lut_node = task.node;
+    }
     if (threadIdx.x == 0) {
       bool ok = *(volatile uint32_t *)a.err == 0;
       if (ok && nd.dep_a >= 0) ok = wait_ctr(a.done + nd.dep_a, (uint32_t)a.nodes[nd.dep_a].n_chunks);
