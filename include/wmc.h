@@ -476,8 +476,11 @@ void wmc_server_destroy(wmc_server_t *srv);
  * launch i (i < min(n_max, launch count)): node_ms[i] = its device time,
  * kind[i] = 0 generic contraction, 1 streaming contraction, 4 streaming
  * contraction with TMA-staged operand, 5 dense tiled contraction, 6 fused
- * pair of eliminations, 7 small-node phase (one persistent launch), 2 leaf
- * or bookkeeping kernel, 3 memset; alg_bytes[i] = the bytes a contraction
+ * pair of eliminations, 7 small-node phase (one persistent launch), 8 run
+ * of frontier eliminations in one pass, 9 runs of such chains in one
+ * launch, 10 one-block walk, 11 batched small contraction (two large
+ * operands, few free and summed indices), 2 leaf or bookkeeping kernel,
+ * 3 memset; alg_bytes[i] = the bytes a contraction
  * must move (|A| + |B| + |C| in its element type).  Returns the launch
  * count through *n_launches.  Same arguments and errors as
  * wmc_execute_device; creates and destroys its own events. */

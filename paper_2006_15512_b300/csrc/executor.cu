@@ -95,7 +95,7 @@ namespace {
 
 
 enum Kind { L_K1, L_K2, L_K2T, L_K4, L_K2C, L_SMALL, L_CLAUSES, L_WEIGHTS, L_ONE, L_FINAL, L_MEMSET, L_K2CSEQ,
-            L_BFP, L_BFPW, L_CTA };
+            L_BFP, L_BFPW, L_CTA, L_K2B };
 enum Ty { TF = 0, TD = 1 };
 
 struct Launch {
@@ -107,6 +107,7 @@ struct Launch {
   K2Params k2;
   wmc::dev::K2TParams k2t;
   wmc::dev::K4Params k4;
+  wmc::dev::K2BParams k2b;
   wmc::dev::K2CParams k2c;
   int chain_d = 0, chain_fast = 0, chain_grow = 0, chain_shrink = 0;
   int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};  // chain: S_1..S_D
@@ -672,6 +673,65 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
 // Dense batched-matrix-product form (K4): every summed index in both
 // operands, at least 2^6 values of i and of j, 2^5 of s; query bits only
 // as batch indices.
+// Batched small contraction (K2B): every index of A and of B either batch
+// (in A, B and C), free in one operand (at most 4 bits of A, 3 of B, 5
+// together) or summed in both (at most 2 bits, and fA + k <= 4, k + fB <=
+// 3); at least 2^8 assignments of the batch indices, enumerated in C's
+// order.  A query-lane index (label < 0) that one operand lacks is a batch
+// index the other broadcasts over.
+bool try_k2b(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB, const std::vector<int32_t> &LC,
+             wmc::dev::K2BParams &p) {
+  std::vector<int32_t> bA, bB, bC, fa, fb, sm;
+  for (int32_t l : LA) {
+    const bool inB = pos_of(LB, l) >= 0, inC = pos_of(LC, l) >= 0;
+    if (inC && (inB || l < 0)) bA.push_back(l);
+    else if (inC) fa.push_back(l);
+    else if (inB) sm.push_back(l);
+    else return false;  // summed in A only
+  }
+  for (int32_t l : LB) {
+    const bool inA = pos_of(LA, l) >= 0, inC = pos_of(LC, l) >= 0;
+    if (inC && (inA || l < 0)) bB.push_back(l);
+    else if (inC) fb.push_back(l);
+    else if (!inA) return false;  // summed in B only
+  }
+  for (int32_t l : LC)
+    if ((pos_of(LA, l) >= 0 && pos_of(LB, l) >= 0) || (l < 0 && (pos_of(LA, l) >= 0 || pos_of(LB, l) >= 0)))
+      bC.push_back(l);
+  const int nfa = (int)fa.size(), nfb = (int)fb.size(), k = (int)sm.size();
+  if (k > 2 || nfa > 4 || nfb > 3 || nfa + k > 4 || k + nfb > 3 || nfa + nfb > 5) return false;
+  if (bC.size() < 8 || bC.size() > 31) return false;
+  std::memset(&p, 0, sizeof(p));
+  p.log2_nu = (int32_t)bC.size();
+  p.fA = nfa; p.fB = nfb; p.k = k;
+  for (size_t j = 0; j < LC.size(); ++j)
+    if (std::find(bC.begin(), bC.end(), LC[j]) == bC.end()) p.insC[p.n_insC++] = (int8_t)j;
+  for (size_t j = 0; j < bC.size(); ++j) {
+    p.posA[j] = (int8_t)pos_of(LA, bC[j]);
+    p.posB[j] = (int8_t)pos_of(LB, bC[j]);
+  }
+  auto bit = [&](const std::vector<int32_t> &L, int32_t l) { return 1u << pos_of(L, l); };
+  for (int i = 0; i < (1 << (nfa + k)); ++i) {
+    uint32_t o = 0;
+    for (int j = 0; j < nfa; ++j) if ((i >> j) & 1) o |= bit(LA, fa[(size_t)j]);
+    for (int j = 0; j < k; ++j) if ((i >> (nfa + j)) & 1) o |= bit(LA, sm[(size_t)j]);
+    p.offA[i] = o;
+  }
+  for (int i = 0; i < (1 << (k + nfb)); ++i) {
+    uint32_t o = 0;
+    for (int j = 0; j < k; ++j) if ((i >> j) & 1) o |= bit(LB, sm[(size_t)j]);
+    for (int j = 0; j < nfb; ++j) if ((i >> (k + j)) & 1) o |= bit(LB, fb[(size_t)j]);
+    p.offB[i] = o;
+  }
+  for (int i = 0; i < (1 << (nfa + nfb)); ++i) {
+    uint32_t o = 0;
+    for (int j = 0; j < nfa; ++j) if ((i >> j) & 1) o |= bit(LC, fa[(size_t)j]);
+    for (int j = 0; j < nfb; ++j) if ((i >> (nfa + j)) & 1) o |= bit(LC, fb[(size_t)j]);
+    p.offC[i] = o;
+  }
+  return true;
+}
+
 bool try_k4(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB,
             const std::vector<int32_t> &LC, bool f64, wmc::dev::K4Params &p) {
   std::vector<int32_t> iv, jv, sv, bv;
@@ -844,7 +904,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   std::vector<int32_t> sp_index(plan.nodes.size(), -1);
   std::vector<int64_t> sp_nodes;
   // one-block walk: every node small, the live tensors within shared memory
-  bool cta = st.wo.cta_walk && !plain && st.bfp_b < 0 && Qp <= 4 && slots <= 1536 && !plan.nodes.empty();
+  bool cta = st.wo.cta_walk && !plain && st.bfp_b < 0 && Qp <= 4 && slots <= 1536 && !plan.nodes.empty() &&
+             plan.slice_vars.empty();
   std::vector<int64_t> cta_off(cta ? nt : 0, -1);
   // shared memory: metadata, the node program, the leaf descriptors, the arena
   int64_t cta_meta = align_up(24 * slots) + align_up((int64_t)sizeof(wmc::dev::SNode) * (int64_t)plan.nodes.size()) +
@@ -961,6 +1022,25 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       l.k4.mb.qmask = B.has_q ? Qp - 1 : 0;
       l.blocks = (int64_t)1 << (p4.ni - 6 + p4.nj - 6 + p4.nb);
     }
+    // batched small contraction: both operands large, few free and summed
+    // indices; the query lanes (if any) batch indices of all three
+    // (either operand as A: A takes up to 4 free bits, B up to 3)
+    bool k2b_swap = false;
+    if (!used_k2 && !is_root && (try_k2b(LA, LB, LC, l.k2b) || (k2b_swap = try_k2b(LB, LA, LC, l.k2b)))) {
+      used_k2 = true;
+      l.kind = L_K2B;
+      l.ti = st.f64 ? TD : TF;
+      l.id_a = k2b_swap ? nd.b : nd.a;
+      l.id_b = k2b_swap ? nd.a : nd.b;
+      l.k2b.ma.qmask = A.has_q ? Qp - 1 : 0;
+      l.k2b.mb.qmask = B.has_q ? Qp - 1 : 0;
+      // (grid-stride: the stride must be a multiple of the lane count)
+      const uint64_t units = 1ull << l.k2b.log2_nu;
+      const int64_t g = (C.has_q && Qp > 256) ? Qp / 256 : 1;
+      const bool ct = l.k2b.k == 1 && l.k2b.fA <= 3 && l.k2b.fB <= 2;  // (compile-time shape: 3 blocks per SM)
+      l.blocks = (int64_t)std::min<uint64_t>((units + 255) / 256, 148ull * (ct ? 3 : 2));
+      l.blocks = std::max<int64_t>(g, l.blocks / g * g);
+    }
     if (!used_k2) {
       l.kind = L_K1;
       fill_k1(LA, LB, LC, l.k1);
@@ -976,7 +1056,7 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     }
     l.id_c = nd.c;
     l.alg_bytes = (double)bytes[(size_t)nd.a] + (double)bytes[(size_t)nd.b] + (double)bytes[(size_t)nd.c];
-    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : (l.kind == L_K4 ? l.k4.mc : l.k2.mc);
+    dev::OutMeta &mc = l.kind == L_K1 ? l.k1.mc : (l.kind == L_K4 ? l.k4.mc : (l.kind == L_K2B ? l.k2b.mc : l.k2.mc));
     mc.Qc = C.has_q ? Qp : 1;
     mc.Q = Qp;
     mc.scale_inputs = 1;
@@ -1161,10 +1241,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     L.rank = (int32_t)t.labels.size();
     L.smask = t.clause >= 0 ? plan.clauses[(size_t)t.clause].smask : 0u;
     L.sfals = t.clause >= 0 ? plan.clauses[(size_t)t.clause].sfals : 0u;
-    L.pad = 0;
+    L.lbits = t.has_q ? m : 0;  // (a clause with a sliced literal carries the lanes)
     st.h_clause.push_back(L);
     st.h_first.push_back(entries);
-    entries += int64_t(1) << L.rank;
+    entries += int64_t(1) << (L.rank + L.lbits);
   }
   st.n_clause_entries = entries;
   if (!st.h_clause.empty()) {
@@ -1457,6 +1537,33 @@ static void launch_k2t(const Launch &l, const wmc::dev::K2TParams &p, cudaStream
   }
 }
 
+// batched small contractions: one summed index with up to 3 free bits of A
+// and 2 of B at compile time, the other shapes at run time
+template <typename T>
+static void launch_k2b_t(const Launch &l, const wmc::dev::K2BParams &p, cudaStream_t s) {
+  const unsigned g = (unsigned)l.blocks, b = dev::kThreads;
+  const int code = p.k == 1 && p.fA <= 3 && p.fB <= 2 ? p.fA * 3 + p.fB : -1;
+  switch (code) {
+    case 0: dev::k2_batched<T, 1, 0, 0><<<g, b, 0, s>>>(p); break;
+    case 1: dev::k2_batched<T, 1, 0, 1><<<g, b, 0, s>>>(p); break;
+    case 2: dev::k2_batched<T, 1, 0, 2><<<g, b, 0, s>>>(p); break;
+    case 3: dev::k2_batched<T, 1, 1, 0><<<g, b, 0, s>>>(p); break;
+    case 4: dev::k2_batched<T, 1, 1, 1><<<g, b, 0, s>>>(p); break;
+    case 5: dev::k2_batched<T, 1, 1, 2><<<g, b, 0, s>>>(p); break;
+    case 6: dev::k2_batched<T, 1, 2, 0><<<g, b, 0, s>>>(p); break;
+    case 7: dev::k2_batched<T, 1, 2, 1><<<g, b, 0, s>>>(p); break;
+    case 8: dev::k2_batched<T, 1, 2, 2><<<g, b, 0, s>>>(p); break;
+    case 9: dev::k2_batched<T, 1, 3, 0><<<g, b, 0, s>>>(p); break;
+    case 10: dev::k2_batched<T, 1, 3, 1><<<g, b, 0, s>>>(p); break;
+    case 11: dev::k2_batched<T, 1, 3, 2><<<g, b, 0, s>>>(p); break;
+    default: dev::k2_batched<T, -1, 0, 0><<<g, b, 0, s>>>(p); break;
+  }
+}
+static void launch_k2b(const Launch &l, const wmc::dev::K2BParams &p, cudaStream_t s) {
+  if (l.ti == TD) launch_k2b_t<double>(l, p, s);
+  else launch_k2b_t<float>(l, p, s);
+}
+
 template <typename T, int V, int D, bool FAST, int BC, int GROW, int SHRINK>
 static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
@@ -1734,6 +1841,16 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         else dev::k4_dense<float><<<(unsigned)l.blocks, 256, 0, s>>>(p);
         break;
       }
+      case L_K2B: {
+        wmc::dev::K2BParams p = l.k2b;
+        p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
+        p.ma.exp = mexp + l.meta_a; p.ma.maxb = mmax + l.meta_a; p.ma.minb = mmin + l.meta_a;
+        p.mb.exp = mexp + l.meta_b; p.mb.maxb = mmax + l.meta_b; p.mb.minb = mmin + l.meta_b;
+        p.mc.exp = mexp + l.meta_c; p.mc.maxb = mmax + l.meta_c; p.mc.minb = mmin + l.meta_c;
+        p.mc.flags = flags;
+        launch_k2b(l, p, s);
+        break;
+      }
       case L_K2: {
         K2Params p = l.k2;
         p.A = ws + l.off_a; p.B = ws + l.off_b; p.C = ws + l.off_c;
@@ -1877,9 +1994,12 @@ static int64_t n_slices(const Plan &plan) { return int64_t(1) << plan.slice_vars
 // Runs the walk for a power-of-two batch Qp >= Q on device pointers, once
 // per slice assignment in [slice_lo, slice_hi) (index slicing: the results
 // accumulate in the outputs; an unsliced plan has the single slice 0).
+// With lanes_per_slice > 0 it runs one walk whose lane l (l < n_lanes)
+// takes slice slice_lo + l / lanes_per_slice.
 static int run_device(Plan &plan, ExecState &st, const double *d_wp, const double *d_wn,
                       char *ws, double *d_mant, int64_t *d_exp, uint32_t *d_flags,
-                      cudaStream_t s, int64_t slice_lo = 0, int64_t slice_hi = -1) {
+                      cudaStream_t s, int64_t slice_lo = 0, int64_t slice_hi = -1, int32_t lanes_per_slice = 0,
+                      int32_t n_lanes = 0) {
   if (slice_hi < 0) slice_hi = n_slices(plan);
   if (slice_lo < 0 || slice_lo >= slice_hi || slice_hi > n_slices(plan)) {
     set_error("slice range [%lld, %lld) outside [0, %lld)", (long long)slice_lo, (long long)slice_hi,
@@ -1895,6 +2015,15 @@ static int run_device(Plan &plan, ExecState &st, const double *d_wp, const doubl
   }
   if (rc) return rc;
   IoDesc io = io_desc(plan, d_wp, d_wn, d_mant, d_exp, d_flags);
+  if (lanes_per_slice > 0) {
+    io.slice = (uint64_t)slice_lo;
+    io.lanes_per_slice = lanes_per_slice;
+    io.n_lanes = n_lanes;
+    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(ge, s));
+    g_launches.fetch_add(st.kernels_per_run);
+    return WMC_OK;
+  }
   for (int64_t eta = slice_lo; eta < slice_hi; ++eta) {
     io.slice = (uint64_t)eta;
     io.accumulate = eta != slice_lo;
@@ -2045,7 +2174,10 @@ static void fill_result(const ExecState &st, double mant, int64_t e,
     r->rel_err_bound += ds * std::ldexp(1.0, -53);
   }
   if (negative) r->flags |= WMC_FLAG_NO_BOUND;
-  if (unit && st.f64 && mant != 0.0 && r->exp2 <= 53 && std::ldexp(fr, (int)r->exp2) == std::floor(std::ldexp(fr, (int)r->exp2)))
+  // (a zero count with unit weights is exactly zero: a slice's share that a
+  // clause rules out keeps the sum over slices exact)
+  if (unit && st.f64 &&
+      (mant == 0.0 || (r->exp2 <= 53 && std::ldexp(fr, (int)r->exp2) == std::floor(std::ldexp(fr, (int)r->exp2)))))
     r->flags |= WMC_FLAG_EXACT_INT;
   r->reserved = 0;
 }
@@ -2183,7 +2315,7 @@ extern "C" int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_p
     CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     const Launch &l = st->launches[i];
     if (node_ms) node_ms[i] = ms;
-    if (kind) kind[i] = l.kind == L_CTA ? 10 : (l.kind == L_K1 || l.kind == L_BFP) ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_MEMSET ? 3 : 2;
+    if (kind) kind[i] = l.kind == L_CTA ? 10 : (l.kind == L_K1 || l.kind == L_BFP) ? 0 : l.kind == L_K2 ? 1 : l.kind == L_K2T ? 4 : l.kind == L_K4 ? 5 : l.kind == L_SMALL ? 7 : l.kind == L_K2C ? 8 : l.kind == L_K2CSEQ ? 9 : l.kind == L_K2B ? 11 : l.kind == L_MEMSET ? 3 : 2;
     if (alg_bytes) alg_bytes[i] = l.alg_bytes;
   }
   for (auto &e : ev) cudaEventDestroy(e);
@@ -2223,7 +2355,8 @@ extern "C" int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_p
 
 // One walk of state `st` with host weights, results filled into out[Q].
 static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_pos_q, const double *w_neg_q,
-                    int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
+                    int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out, int32_t lanes_per_slice = 0,
+                    int32_t n_lanes = 0) {
   int rc = WMC_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nv = (size_t)plan->n_vars;
@@ -2260,7 +2393,7 @@ static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_
     }
   }
   rc = run_device(*plan, *st, st->d_w, st->d_w + (size_t)Q * nv, (char *)st->own_ws,
-                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s, slice_lo, slice_hi);
+                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s, slice_lo, slice_hi, lanes_per_slice, n_lanes);
   if (rc) return rc;
   CUDA_TRY(cudaMemcpyAsync(st->h_res_mant, st->d_res_mant, sizeof(double) * (size_t)Q, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(st->h_res_exp, st->d_res_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
@@ -2276,16 +2409,64 @@ static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_
   return WMC_OK;
 }
 
+// Index slicing with the slice assignments along the lanes, as queries are
+// batched: lane c Q + q is query q under slice lo + c, so one walk of
+// Q x C lanes evaluates C slices of every query (the clause tensors with
+// sliced literals carry the lanes; every other tensor does already).  Each
+// query's partial counts are then summed exponent-aligned (Thm 4.2, as
+// wmc_combine_results does).  C: the most slices whose lanes keep every
+// tensor within 2^28 entries and at most 256 lanes; returns 1 (nothing
+// done) when that is a single slice.
+static int execute_slice_lanes(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
+                               int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
+  int mq = 0;
+  while ((1 << mq) < Q) ++mq;
+  const int m_max = std::min(8, std::max(0, 28 - plan->max_rank));
+  const int64_t C = std::min<int64_t>(int64_t(1) << std::max(0, m_max - mq), slice_hi - slice_lo);
+  if (C < 2) return 1;
+  const int32_t Qe = (int32_t)(Q * C);
+  ExecState *st = nullptr;
+  int rc = get_state(*plan, Qe, &st);
+  if (rc) return rc;
+  const size_t nv = (size_t)plan->n_vars;
+  std::vector<double> wp((size_t)Qe * std::max<size_t>(nv, 1)), wn(wp.size());
+  for (int64_t c = 0; c < C; ++c)
+    for (int32_t q = 0; q < Q; ++q) {
+      const size_t d = ((size_t)c * (size_t)Q + (size_t)q) * nv;
+      for (size_t v = 0; v < nv; ++v) {
+        wp[d + v] = w_pos_q ? w_pos_q[(size_t)q * nv + v] : plan->w_pos[v];
+        wn[d + v] = w_neg_q ? w_neg_q[(size_t)q * nv + v] : plan->w_neg[v];
+      }
+    }
+  std::vector<std::vector<wmc_result>> parts((size_t)Q);
+  std::vector<wmc_result> lane_out((size_t)Qe);
+  for (int64_t b = slice_lo; b < slice_hi; b += C) {
+    const int64_t cnt = std::min<int64_t>(C, slice_hi - b);
+    if ((rc = run_host(plan, st, Qe, wp.data(), wn.data(), b, b + 1, stream, lane_out.data(), Q,
+                       (int32_t)(Q * cnt))))
+      return rc;
+    for (int64_t c = 0; c < cnt; ++c)
+      for (int32_t q = 0; q < Q; ++q) parts[(size_t)q].push_back(lane_out[(size_t)(c * Q + q)]);
+  }
+  for (int32_t q = 0; q < Q; ++q)
+    if ((rc = wmc_combine_results(parts[(size_t)q].data(), (int64_t)parts[(size_t)q].size(), out + q))) return rc;
+  return WMC_OK;
+}
+
 static int execute_host(wmc_plan_t *plan, int32_t Q, const double *w_pos_q, const double *w_neg_q,
                         int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out) {
   if (!plan || !out) { set_error("NULL argument"); return WMC_EINVAL; }
   if (check_q(Q)) return WMC_EINVAL;
   if ((w_pos_q == nullptr) != (w_neg_q == nullptr)) { set_error("give both weight arrays or neither"); return WMC_EINVAL; }
-  ExecState *st = nullptr;
-  int rc = get_state(*plan, Q, &st);
-  if (rc) return rc;
-  rc = run_host(plan, st, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
-  if (rc || st->f64 || !g_fp64_fallback.load()) return rc;
+  int rc = 1;
+  if (!plan->slice_vars.empty() && slice_hi - slice_lo > 1)
+    rc = execute_slice_lanes(plan, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
+  if (rc == 1) {  // one walk per slice
+    ExecState *st = nullptr;
+    if ((rc = get_state(*plan, Q, &st))) return rc;
+    rc = run_host(plan, st, Q, w_pos_q, w_neg_q, slice_lo, slice_hi, stream, out);
+  }
+  if (rc || plan->precision == WMC_FP64 || !g_fp64_fallback.load()) return rc;
   // queries whose float32 walk may have flushed run again in float64
   std::vector<int32_t> redo;
   for (int32_t q = 0; q < Q; ++q)
@@ -3013,6 +3194,18 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
   int rc = get_state(*plan, Q, &st);
   if (rc) return rc;
   int64_t checked = 0;
+  // clause leaves: 2^(rank + lane bits) elements and 2^(lane bits) metadata
+  // slots inside their tensor's allocation and slots
+  for (size_t i = 0; i < st->h_clause.size(); ++i) {
+    const ClauseLeaf &L = st->h_clause[i];
+    const int64_t es = st->f64 ? 8 : 4;
+    bool ok = false;
+    for (size_t t = 0; t < st->t_off.size() && !ok; ++t)
+      ok = st->t_off[t] == L.off * es && (int64_t(1) << (L.rank + L.lbits)) * es <= st->t_bytes[t] &&
+           L.meta + (int64_t(1) << L.lbits) <= st->t_meta[t] + st->t_qc[t] && L.meta >= st->t_meta[t];
+    if (!ok) { set_error("clause leaf %zu: elements or metadata slots outside its tensor", i); return WMC_EINVAL; }
+    ++checked;
+  }
   for (size_t i = 0; i < st->h_snodes.size(); ++i) {
     const wmc::dev::SNode &sn = st->h_snodes[i];
     int64_t ma = 0, mb = 0;
@@ -3169,6 +3362,29 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
           return badc("staged S", i, D);
       if (need > l.smem || l.smem > 220 * 1024 || cp.n_stages < 2 || cp.n_stages > wmc::dev::kMaxStagesC)
         return badc("shared memory", (int64_t)need, (int64_t)l.smem);
+      continue;
+    }
+    if (l.kind == L_K2B) {
+      // every unit's offsets (batch bits deposited) plus the small tables
+      const wmc::dev::K2BParams &p = l.k2b;
+      const int64_t es = l.ti == TD ? 8 : 4;
+      const int64_t na = st->t_bytes[(size_t)l.id_a] / es, nb = st->t_bytes[(size_t)l.id_b] / es,
+                    nc = st->t_bytes[(size_t)l.id_c] / es;
+      const uint32_t last = (uint32_t)((1ull << p.log2_nu) - 1);
+      uint32_t oa = 0, ob = 0, oc = last;
+      for (int j = 0; j < p.log2_nu; ++j) {
+        if (p.posA[j] >= 0) oa |= 1u << p.posA[j];
+        if (p.posB[j] >= 0) ob |= 1u << p.posB[j];
+      }
+      for (int j = 0; j < p.n_insC; ++j) oc = h_insert0(oc, p.insC[j]);
+      bool ok = (int64_t)(oa | p.offA[(1 << (p.fA + p.k)) - 1]) < na && (int64_t)(ob | p.offB[(1 << (p.k + p.fB)) - 1]) < nb &&
+                (int64_t)(oc | p.offC[(1 << (p.fA + p.fB)) - 1]) < nc;
+      for (int i = 0; i < (1 << (p.fA + p.k)) && ok; ++i) ok = (p.offA[i] & oa) == 0;
+      for (int i = 0; i < (1 << (p.k + p.fB)) && ok; ++i) ok = (p.offB[i] & ob) == 0;
+      for (int i = 0; i < (1 << (p.fA + p.fB)) && ok; ++i) ok = (p.offC[i] & oc) == 0;
+      ok = ok && ((uint64_t)l.blocks * 256) % (uint64_t)p.mc.Qc == 0;
+      if (!ok) { set_error("launch %zu: batched contraction offsets outside their tensors", li); return WMC_EINVAL; }
+      ++checked;
       continue;
     }
     if (l.kind == L_BFP) {

@@ -1039,6 +1039,114 @@ __global__ void __launch_bounds__(kThreads + 32, (K + F <= 2 ? 3 : (K + F <= 4 ?
   finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
 }
 
+// ------------------------------------------- batched small contractions
+//
+// Joins of two large operands whose free and summed sets are small: C[u,
+// fa, fb] = sum over s of A[u, fa, s] B[u, s, fb], u the batch indices
+// (shared and kept, the query lanes among them), fa / fb the free indices
+// of A / B (at most 4 / 3 bits), s the summed ones (at most 2 bits; every
+// summed index in both operands).  A thread takes one u at a time
+// (grid-stride): it loads A's 2^(fA+k) and B's 2^(k+fB) values, forms the
+// 2^(fA+fB) outputs in registers (each a fused multiply-add chain over s
+// ascending from zero: the order of every other kernel) and stores them.
+// For a fixed (fa, s) a warp reads 32 consecutive u when the operands'
+// lowest indices are batch ones (the lanes), so every access is coalesced,
+// and each operand crosses memory once.  u enumerates the batch indices in
+// C's order: its bits are deposited around C's other positions (insC,
+// ascending) and mapped to A's and B's positions (any order) through
+// per-block tables over u's four bytes.
+constexpr int kBatchedNA = 16, kBatchedNB = 8, kBatchedNC = 32;
+
+struct K2BParams {
+  const void *A, *B;
+  void *C;
+  Meta ma, mb;
+  OutMeta mc;
+  int32_t log2_nu;               // batch bits
+  int32_t n_insC;
+  int8_t insC[8];                // C's positions of the free indices, ascending
+  int8_t posA[32], posB[32];     // u bit j -> A's, B's position (-1: a lane the operand lacks)
+  int32_t fA, fB, k;
+  uint32_t offA[kBatchedNA];     // A offset of (fa, s): index fa | s << fA
+  uint32_t offB[kBatchedNB];     // B offset of (s, fb): index s | fb << k
+  uint32_t offC[kBatchedNC];     // C offset of (fa, fb): index fa | fb << fA
+};
+
+// KS, FA, FB >= 0: the shape at compile time (register arrays with static
+// indices); -1: the runtime shape (arrays indexed at run time, in local
+// memory)
+template <typename T, int KS, int FA, int FB>
+__global__ void __launch_bounds__(kThreads, KS >= 0 ? 3 : 2) k2_batched(K2BParams p) {
+  __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
+  __shared__ uint32_t lutA[4][256], lutB[4][256];  // u's byte r -> A's, B's offset
+  for (int q = threadIdx.x; q < p.mc.Qc; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const int r = i >> 8, v = i & 255;
+    uint32_t oa = 0, ob = 0;
+    for (int bb = 0; bb < 8 && 8 * r + bb < p.log2_nu; ++bb)
+      if ((v >> bb) & 1) {
+        if (p.posA[8 * r + bb] >= 0) oa |= 1u << p.posA[8 * r + bb];  // (-1: broadcast over it)
+        if (p.posB[8 * r + bb] >= 0) ob |= 1u << p.posB[8 * r + bb];
+      }
+    lutA[r][v] = oa;
+    lutB[r][v] = ob;
+  }
+  __syncthreads();
+  const T *A = static_cast<const T *>(p.A);
+  const T *B = static_cast<const T *>(p.B);
+  T *C = static_cast<T *>(p.C);
+  uint32_t mc = 0;
+  for (int j = 0; j < p.n_insC; ++j) mc |= 1u << p.insC[j];
+  const uint32_t n_units = 1u << p.log2_nu;
+  uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t oc = u, dc = stride;
+  for (int j = 0; j < p.n_insC; ++j) { oc = insert0(oc, p.insC[j]); dc = insert0(dc, p.insC[j]); }
+  auto offA = [&](uint32_t x) { return lutA[0][x & 255] | lutA[1][(x >> 8) & 255] | lutA[2][(x >> 16) & 255] | lutA[3][x >> 24]; };
+  auto offB = [&](uint32_t x) { return lutB[0][x & 255] | lutB[1][(x >> 8) & 255] | lutB[2][(x >> 16) & 255] | lutB[3][x >> 24]; };
+  const uint32_t oa0 = offA(u), ob0 = offB(u);
+  // a thread's units share their lanes (the stride is a multiple of the
+  // lane count and the lanes are the lowest batch bits)
+  const int qa = (int)(oa0 & (uint32_t)p.ma.qmask), qb = (int)(ob0 & (uint32_t)p.mb.qmask);
+  const T sa = operand_scale<T>(p.ma, qa, p.mc.scale_inputs), sb = operand_scale<T>(p.mb, qb, p.mc.scale_inputs);
+  constexpr bool CT = KS >= 0;
+  const int fA = CT ? FA : p.fA, fB = CT ? FB : p.fB, kk = CT ? KS : p.k;
+  const int na = 1 << (fA + kk), nb = 1 << (kk + fB), nfa = 1 << fA, nfb = 1 << fB, ns = 1 << kk;
+  T tmax = (T)0, tmin = (T)INFINITY;
+  for (; u < n_units; u += stride) {
+    const uint32_t oa = offA(u), ob = offB(u);
+    T a[kBatchedNA], b[kBatchedNB];
+#pragma unroll
+    for (int i = 0; i < kBatchedNA; ++i)
+      if (i < na) a[i] = __ldcs(A + (oa | p.offA[i])) * sa;
+#pragma unroll
+    for (int i = 0; i < kBatchedNB; ++i)
+      if (i < nb) b[i] = __ldcs(B + (ob | p.offB[i])) * sb;
+#pragma unroll
+    for (int fb = 0; fb < kBatchedNB; ++fb) {
+      if (fb >= nfb) break;
+#pragma unroll
+      for (int fa = 0; fa < kBatchedNA; ++fa) {
+        if (fa >= nfa) break;
+        T acc = (T)0;
+#pragma unroll
+        for (int sidx = 0; sidx < 4; ++sidx)
+          if (sidx < ns) acc = fma_t(a[fa | (sidx << fA)], b[sidx | (fb << kk)], acc);
+        C[oc | p.offC[fa | (fb << fA)]] = acc;
+        track(acc, tmax, tmin);
+      }
+    }
+    oc = ((oc | mc) + dc) & ~mc;
+  }
+  {
+    const int qc = (int)((blockIdx.x * blockDim.x + threadIdx.x) & (uint32_t)(p.mc.Qc - 1));
+    if (tmax != (T)0) atomicMax(smax + qc, abs_bits(tmax));
+    if (tmin != (T)INFINITY) atomicMin(smin + qc, abs_bits(tmin));
+  }
+  __syncthreads();
+  finish_meta<T>(p.ma, p.mb, p.mc, smax, smin);
+}
+
 // ---------------------------------------------- chain of frontier eliminations
 //
 // D consecutive frontier contractions C_i = C_{i-1} . S_i (C_0 = P) in one
@@ -2831,6 +2939,11 @@ struct IoDesc {
   int32_t accumulate;
   int32_t n_slice;
   int32_t slice_var[24];
+  // slice assignments along the lanes (0: every lane has `slice`): lane l
+  // (l < n_lanes; padding lanes repeat lane n_lanes - 1) has slice
+  // slice + l / lanes_per_slice
+  int32_t lanes_per_slice;
+  int32_t n_lanes;
 };
 
 struct ClauseLeaf {
@@ -2840,19 +2953,20 @@ struct ClauseLeaf {
   int32_t rank;
   uint32_t smask;   // index slicing: the clause's sliced variables (slice bits)
   uint32_t sfals;   // ... and their falsifying values
-  uint32_t pad;
+  int32_t lbits;    // lane bits (the clause depends on the slice: log2 Qp, else 0)
 };
 
 // Clause tensors B_C (Thm 3.2): 1 everywhere except 0 at the falsifying
 // assignment.  One thread per entry of a flat list; `first` holds the
 // first flat entry of each leaf (sorted), n_leaves entries.  Under index
-// slicing a clause that a sliced literal satisfies is 1 everywhere.
+// slicing a clause that a sliced literal satisfies is 1 everywhere; such a
+// clause carries the lanes, each lane its own slice assignment when the
+// slices run along the lanes.
 template <typename T>
 __global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, int64_t n_leaves,
                                 int64_t n_entries, T *arena, int64_t *meta_exp,
                                 unsigned long long *meta_max, unsigned long long *meta_min,
                                 const IoDesc *io) {
-  const uint32_t eta = (uint32_t)io->slice;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_entries;
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t lo = 0, hi = n_leaves - 1;
@@ -2861,15 +2975,21 @@ __global__ void k_clause_leaves(const ClauseLeaf *leaves, const int64_t *first, 
       if (first[mid] <= i) lo = mid; else hi = mid - 1;
     }
     const ClauseLeaf L = leaves[lo];
+    // element (a, lane): the lane bits are the lowest
+    const uint64_t e = (uint64_t)(i - first[lo]);
+    const uint32_t lane = (uint32_t)(e & ((1ull << L.lbits) - 1ull));
+    const uint64_t a = e >> L.lbits;
+    uint32_t eta = (uint32_t)io->slice;
+    if (io->lanes_per_slice > 0)
+      eta += (uint32_t)(min((int32_t)lane, io->n_lanes - 1) / io->lanes_per_slice);
     const bool sat = ((eta ^ L.sfals) & L.smask) != 0u;
-    const uint64_t a = (uint64_t)(i - first[lo]);
-    arena[L.off + (int64_t)a] = (a == L.fals && !sat) ? (T)0 : (T)1;
+    arena[L.off + (int64_t)e] = (a == L.fals && !sat) ? (T)0 : (T)1;
     if (a == 0) {
-      meta_exp[L.meta] = 0;
+      meta_exp[L.meta + lane] = 0;
       // max is 1 unless the tensor is a rank-0 clause with value 0
       const bool zero = L.rank == 0 && !sat;
-      meta_max[L.meta] = zero ? 0ull : abs_bits((T)1);
-      meta_min[L.meta] = zero ? kNoMin : abs_bits((T)1);
+      meta_max[L.meta + lane] = zero ? 0ull : abs_bits((T)1);
+      meta_min[L.meta + lane] = zero ? kNoMin : abs_bits((T)1);
     }
   }
 }
@@ -3301,9 +3421,9 @@ __global__ void k_one_leaf(T *dst, int64_t meta, int64_t *meta_exp, unsigned lon
 // float64 (its exponents already account for its inputs' scales).
 // The root (float64 mantissa and int64 exponent per query) into the
 // outputs.  Under index slicing the value is multiplied by the sliced
-// variables' weights at the slice assignment (Thm 4.2: the slice's share of
-// W) and, after the first slice, added to the outputs with the exponents
-// aligned (all terms nonnegative for nonnegative weights).
+// variables' weights at the lane's slice assignment (Thm 4.2: the slice's
+// share of W) and, after the first slice, added to the outputs with the
+// exponents aligned (all terms nonnegative for nonnegative weights).
 __global__ void k_finalize(const IoDesc *io, const double *root, const int64_t *root_exp,
                            int32_t root_qc, const uint32_t *flags, const uint32_t *err,
                            int32_t Q, int32_t n_vars) {
@@ -3314,9 +3434,12 @@ __global__ void k_finalize(const IoDesc *io, const double *root, const int64_t *
     const int qr = root_qc > 1 ? q : 0;
     double m = root[qr];
     int64_t e = root_exp[qr];
+    // this lane's slice assignment (slices along the lanes: see IoDesc)
+    uint64_t eta = io->slice;
+    if (io->lanes_per_slice > 0) eta += (uint64_t)(min(q, io->n_lanes - 1) / io->lanes_per_slice);
     for (int k = 0; k < io->n_slice; ++k) {
       const int64_t at = (int64_t)q * n_vars + io->slice_var[k];
-      m *= ((io->slice >> k) & 1ull) ? io->w_pos[at] : io->w_neg[at];
+      m *= ((eta >> k) & 1ull) ? io->w_pos[at] : io->w_neg[at];
       int fe = 0;
       m = frexp(m, &fe);
       e += fe;

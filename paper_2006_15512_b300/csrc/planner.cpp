@@ -219,6 +219,10 @@ bool build_tree(const Network &net, const std::vector<int32_t> &order, int32_t r
     t.kind = LEAF_CLAUSE;
     t.fals = net.clauses[c].fals;
     t.clause = (int64_t)c;
+    // under index slicing a clause with a sliced literal depends on the
+    // slice assignment: it carries the lanes, so that slices can run along
+    // them as queries do
+    t.has_q = net.clauses[c].smask != 0;
     T.push_back(t);
   }
   for (int32_t x = 0; x < net.n_vars; ++x) {
