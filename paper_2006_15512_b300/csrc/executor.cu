@@ -673,33 +673,42 @@ bool try_chain(const std::vector<int32_t> &LP, const std::vector<std::vector<int
 // Dense batched-matrix-product form (K4): every summed index in both
 // operands, at least 2^6 values of i and of j, 2^5 of s; query bits only
 // as batch indices.
-// Batched small contraction (K2B): every index of A and of B either batch
-// (in A, B and C), free in one operand (at most 4 bits of A, 3 of B, 5
-// together) or summed in both (at most 2 bits, and fA + k <= 4, k + fB <=
-// 3); at least 2^8 assignments of the batch indices, enumerated in C's
-// order.  A query-lane index (label < 0) that one operand lacks is a batch
-// index the other broadcasts over.
+// Batched small contraction (K2B): every index of A and of B either kept
+// (in C) or summed in both (at most 2 bits).  Of the kept indices that
+// only one operand holds, up to fA + k <= 4 of A's and k + fB <= 3 of B's
+// (fA + fB <= 5) are free indices held in registers; the rest, and the
+// query lanes, are batch indices, enumerated in C's order (at least 2^8
+// assignments), over which an operand that lacks one is broadcast.
 bool try_k2b(const std::vector<int32_t> &LA, const std::vector<int32_t> &LB, const std::vector<int32_t> &LC,
-             wmc::dev::K2BParams &p) {
-  std::vector<int32_t> bA, bB, bC, fa, fb, sm;
+             wmc::dev::K2BParams &p, int64_t bytes_a = 0, int64_t bytes_b = 0) {
+  std::vector<int32_t> fa, fb, sm;
   for (int32_t l : LA) {
     const bool inB = pos_of(LB, l) >= 0, inC = pos_of(LC, l) >= 0;
-    if (inC && (inB || l < 0)) bA.push_back(l);
-    else if (inC) fa.push_back(l);
-    else if (inB) sm.push_back(l);
-    else return false;  // summed in A only
+    if (!inC && inB) sm.push_back(l);
+    else if (!inC) return false;  // summed in A only
+    else if (!inB && l >= 0) fa.push_back(l);
   }
   for (int32_t l : LB) {
     const bool inA = pos_of(LA, l) >= 0, inC = pos_of(LC, l) >= 0;
-    if (inC && (inA || l < 0)) bB.push_back(l);
-    else if (inC) fb.push_back(l);
-    else if (!inA) return false;  // summed in B only
+    if (!inC && !inA) return false;  // summed in B only
+    if (inC && !inA && l >= 0) fb.push_back(l);
   }
+  const int k = (int)sm.size();
+  if (k > 2) return false;
+  // free indices beyond the registers' budget become batch indices the
+  // other operand is broadcast over (re-read from L2: only when it is at
+  // most 32 MB)
+  const size_t keep_a = std::min<size_t>(fa.size(), (size_t)(4 - k));
+  const size_t keep_b = std::min<size_t>({fb.size(), (size_t)(3 - k), (size_t)5 - keep_a});
+  const int64_t kL2 = int64_t(32) << 20;
+  if ((fa.size() > keep_a && bytes_b > kL2) || (fb.size() > keep_b && bytes_a > kL2)) return false;
+  fa.resize(keep_a);
+  fb.resize(keep_b);
+  const int nfa = (int)fa.size(), nfb = (int)fb.size();
+  std::vector<int32_t> bC;  // every other index of C, in C's order
   for (int32_t l : LC)
-    if ((pos_of(LA, l) >= 0 && pos_of(LB, l) >= 0) || (l < 0 && (pos_of(LA, l) >= 0 || pos_of(LB, l) >= 0)))
+    if (std::find(fa.begin(), fa.end(), l) == fa.end() && std::find(fb.begin(), fb.end(), l) == fb.end())
       bC.push_back(l);
-  const int nfa = (int)fa.size(), nfb = (int)fb.size(), k = (int)sm.size();
-  if (k > 2 || nfa > 4 || nfb > 3 || nfa + k > 4 || k + nfb > 3 || nfa + nfb > 5) return false;
   if (bC.size() < 8 || bC.size() > 31) return false;
   std::memset(&p, 0, sizeof(p));
   p.log2_nu = (int32_t)bC.size();
@@ -1026,7 +1035,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     // indices; the query lanes (if any) batch indices of all three
     // (either operand as A: A takes up to 4 free bits, B up to 3)
     bool k2b_swap = false;
-    if (!used_k2 && !is_root && (try_k2b(LA, LB, LC, l.k2b) || (k2b_swap = try_k2b(LB, LA, LC, l.k2b)))) {
+    if (!used_k2 && !is_root && (try_k2b(LA, LB, LC, l.k2b, bytes[(size_t)nd.a], bytes[(size_t)nd.b]) ||
+                                 (k2b_swap = try_k2b(LB, LA, LC, l.k2b, bytes[(size_t)nd.b], bytes[(size_t)nd.a])))) {
       used_k2 = true;
       l.kind = L_K2B;
       l.ti = st.f64 ? TD : TF;
