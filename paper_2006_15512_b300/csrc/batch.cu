@@ -59,7 +59,7 @@ struct BNode {
   int8_t stream;            // stream mode (below); chunk_log2 then counts u, not outputs
   int8_t f;                 // stream mode: output bits absent from A ("S-free", <= 4)
   int8_t rB;                // rank of B
-  int8_t pad0;
+  int8_t bglob;             // stream mode: B read from global memory (L2), not staged (rank > 8)
   int32_t chain;            // chain mode (stream == 2): index of its BChain; subtrees
                             // (stream == 3): index of the formula's first BGroup
   float est_us;             // subtrees: estimated microseconds per task (list scheduling)
@@ -343,7 +343,7 @@ __device__ __forceinline__ void stream_geom(const BNode &nd, StreamGeom &g, RowS
   rows_from_bits(g.lut, rs, 6);
 }
 
-template <typename T, int NS>
+template <typename T, int NS, bool BG>
 __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, const StreamGeom &g, T *sS,
                            unsigned long long *red) {
   char *ws = ba.ws;
@@ -355,7 +355,10 @@ __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, cons
   const T sa = dev::pow2_scale(dev::pow2_exp_of(ma, T()), T());
   const T sb = dev::pow2_scale(dev::pow2_exp_of(mb, T()), T());
   if (chunk == 0 && threadIdx.x == 32) node_exponent<T>(ws, nd, ma, mb);
-  for (int i = threadIdx.x; i < (1 << nd.rB); i += blockDim.x) sS[i] = ldcg(B + i) * sb;
+  if (!BG)
+    for (int i = threadIdx.x; i < (1 << nd.rB); i += blockDim.x) sS[i] = ldcg(B + i) * sb;
+  // S's entry at `off`: staged and pre-scaled, or (BG: a large B) from L2
+  auto sval = [&](uint32_t off) { return BG ? ldcg(B + off) * sb : sS[off]; };
   // offsets of the task's first u (its bits above the task's local bits)
   const uint32_t u0 = (uint32_t)chunk << nd.chunk_log2;
   uint32_t bC = 0, bA = 0, bS = 0;
@@ -410,7 +413,7 @@ __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, cons
               float acc = 0.0f;
 #pragma unroll
               for (int sidx = 0; sidx < NS; ++sidx)
-                acc = dev::fma_t(a[sidx][e], sS[so | g.ss[sidx]], acc);
+                acc = dev::fma_t(a[sidx][e], sval(so | g.ss[sidx]), acc);
               out[e] = acc;
               track_out(acc, tmax, tmin);
             }
@@ -432,7 +435,7 @@ __device__ void run_stream(const BatchArgs &ba, const BNode &nd, int chunk, cons
     for (int v = 0; v < nv; ++v) {
       T acc = (T)0;
 #pragma unroll
-      for (int sidx = 0; sidx < NS; ++sidx) acc = dev::fma_t(a[sidx], sS[sbx | g.sv[v] | g.ss[sidx]], acc);
+      for (int sidx = 0; sidx < NS; ++sidx) acc = dev::fma_t(a[sidx], sval(sbx | g.sv[v] | g.ss[sidx]), acc);
       C[cb | g.cv[v]] = acc;
       track_out(acc, tmax, tmin);
     }
@@ -745,13 +748,23 @@ __device__ __forceinline__ void run_one(const BatchArgs &ba, const BNode &nd, in
                                         const StreamGeom &geom, double *s_S, unsigned long long *red) {
   float *s_Sf = reinterpret_cast<float *>(s_S);
   if (nd.stream && nd.ti == 1) {
-    if (nd.k == 0) run_stream<double, 1>(ba, nd, chunk, geom, s_S, red);
-    else if (nd.k == 1) run_stream<double, 2>(ba, nd, chunk, geom, s_S, red);
-    else run_stream<double, 4>(ba, nd, chunk, geom, s_S, red);
+    if (nd.bglob) {
+      if (nd.k == 0) run_stream<double, 1, true>(ba, nd, chunk, geom, s_S, red);
+      else if (nd.k == 1) run_stream<double, 2, true>(ba, nd, chunk, geom, s_S, red);
+      else run_stream<double, 4, true>(ba, nd, chunk, geom, s_S, red);
+    }
+    else if (nd.k == 0) run_stream<double, 1, false>(ba, nd, chunk, geom, s_S, red);
+    else if (nd.k == 1) run_stream<double, 2, false>(ba, nd, chunk, geom, s_S, red);
+    else run_stream<double, 4, false>(ba, nd, chunk, geom, s_S, red);
   } else if (nd.stream) {
-    if (nd.k == 0) run_stream<float, 1>(ba, nd, chunk, geom, s_Sf, red);
-    else if (nd.k == 1) run_stream<float, 2>(ba, nd, chunk, geom, s_Sf, red);
-    else run_stream<float, 4>(ba, nd, chunk, geom, s_Sf, red);
+    if (nd.bglob) {
+      if (nd.k == 0) run_stream<float, 1, true>(ba, nd, chunk, geom, s_Sf, red);
+      else if (nd.k == 1) run_stream<float, 2, true>(ba, nd, chunk, geom, s_Sf, red);
+      else run_stream<float, 4, true>(ba, nd, chunk, geom, s_Sf, red);
+    }
+    else if (nd.k == 0) run_stream<float, 1, false>(ba, nd, chunk, geom, s_Sf, red);
+    else if (nd.k == 1) run_stream<float, 2, false>(ba, nd, chunk, geom, s_Sf, red);
+    else run_stream<float, 4, false>(ba, nd, chunk, geom, s_Sf, red);
   }
   else if (nd.ti == 1) run_task<double, double, double>(ba, nd, chunk, lut, red);
   else if (nd.to == 1) run_task<float, double, double>(ba, nd, chunk, lut, red);
@@ -1363,7 +1376,11 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
       n.ta = (prec == WMC_FP64 || n.to || n.k > 16) ? 1 : 0;
       int32_t fr = 0;
       for (int j = 0; j < n.rC; ++j) fr += n.posA[j] < 0;
-      n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && rb <= 8 && fr <= 4) ? 1 : 0;
+      // (a B of rank 9..22 -- at most 16 MB in float32 -- is read from L2
+      // instead of staged: joins whose B-only indices are few)
+      const bool b_l2 = rb > 8 && (int64_t(1) << rb) * (n.ti ? 8 : 4) <= (int64_t(16) << 20);
+      n.stream = (n.ti == n.ta && n.ta == n.to && n.k <= 2 && (rb <= 8 || b_l2) && fr <= 4) ? 1 : 0;
+      n.bglob = (n.stream && rb > 8) ? 1 : 0;
       if (n.stream) {
         // tasks over u, the assignments of C's indices that A holds
         n.f = (int8_t)fr;
