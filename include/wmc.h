@@ -553,6 +553,12 @@ void wmc_set_dependent_launch(int32_t on);
  * off, on the scalar tiled kernel.  The two agree within float32 rounding,
  * not bit for bit. */
 void wmc_set_tensor_cores(int32_t on);
+/* Execution option (default on): walk nodes that join two large operands
+ * with at most 2 summed indices run on the batched small-contraction
+ * kernel (a thread per batch assignment, the few free indices in
+ * registers) instead of the generic one; the same bits either way.
+ * Affects plans laid out after the call. */
+void wmc_set_batched_pairs(int32_t on);
 /* Execution option (default on): wmc_contract_pair runs dense products
  * with at most 4 summed values whose C has one operand's first 10 free
  * indices as its lowest 10 bits, at least 2^24 outputs and a 16-byte

@@ -153,6 +153,7 @@ EXPORTS = {
     "wmc_set_dependent_launch": (None, [c_i32]),
     "wmc_set_tensor_cores": (None, [c_i32]),
     "wmc_set_outer_products": (None, [c_i32]),
+    "wmc_set_batched_pairs": (None, [c_i32]),
     "wmc_set_fp64_fallback": (None, [c_i32]),
     "wmc_set_chain_runs": (None, [c_i32]),
     "wmc_set_cta_walk": (None, [c_i32]),

@@ -61,6 +61,8 @@ extern "C" void wmc_set_small_phase(int32_t on) { g_small_phase.store(on); }
 extern "C" void wmc_set_dependent_launch(int32_t on) { g_pdl.store(on); }
 extern "C" void wmc_set_tensor_cores(int32_t on) { g_tensor_cores.store(on); }
 static std::atomic<int32_t> g_outer{1};  // short summed ranges: k4_outer in place of k4_dense
+static std::atomic<int32_t> g_batched{1};  // walk nodes: k2_batched in place of the generic kernel
+extern "C" void wmc_set_batched_pairs(int32_t on) { g_batched.store(on); }
 extern "C" void wmc_set_outer_products(int32_t on) { g_outer.store(on); }
 extern "C" void wmc_set_fp64_fallback(int32_t on) { g_fp64_fallback.store(on); }
 extern "C" void wmc_set_chain_runs(int32_t max_tiles) { g_chain_runs.store(max_tiles < 0 ? 0 : max_tiles); }
@@ -1035,7 +1037,8 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
     // indices; the query lanes (if any) batch indices of all three
     // (either operand as A: A takes up to 4 free bits, B up to 3)
     bool k2b_swap = false;
-    if (!used_k2 && !is_root && (try_k2b(LA, LB, LC, l.k2b, bytes[(size_t)nd.a], bytes[(size_t)nd.b]) ||
+    if (!used_k2 && !is_root && g_batched.load() &&
+        (try_k2b(LA, LB, LC, l.k2b, bytes[(size_t)nd.a], bytes[(size_t)nd.b]) ||
                                  (k2b_swap = try_k2b(LB, LA, LC, l.k2b, bytes[(size_t)nd.b], bytes[(size_t)nd.a])))) {
       used_k2 = true;
       l.kind = L_K2B;

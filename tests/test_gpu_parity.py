@@ -956,6 +956,33 @@ def test_sliced_walk_matches_unsliced(w, precision):
         assert rel(got[q], want) <= got[q].rel_err_bound  # the stated bound holds
 
 
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_batched_pairs_match_generic(w, precision):
+    """Joins of two large operands with few free and summed indices on the
+    batched small-contraction kernel (operands' batch indices in any order,
+    query lanes one operand lacks broadcast, many free indices on one side
+    as broadcast batch indices): the same bits as the generic kernel, and the
+    oracle's value, for several queries."""
+    cnf = wmcgen.random_kcnf(34, 110, seed=0)  # (max rank 21)
+    Q = 5
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=21, lo=0.1, hi=0.9)
+    out = {}
+    try:
+        for on in (1, 0):
+            w.wmc_set_batched_pairs(on)
+            plan = plan_for(w, cnf, None, None, precision)
+            kinds = _launch_kinds(w, plan, Q, wq, wnq)
+            out[on] = ([(r.mant, r.exp2, r.flags) for r in plan.execute(wq, wnq)], kinds)
+    finally:
+        w.wmc_set_batched_pairs(1)
+    assert 11 in out[1][1] and 11 not in out[0][1]
+    assert out[1][0] == out[0][0]
+    order = _narrow_order(cnf)
+    for q in (0, Q - 1):
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q], order=order)
+        assert Big(out[1][0][q][0], out[1][0][q][1]).rel_diff(want) <= TOL[precision], q
+
+
 def test_sliced_unweighted_count_is_exact(w):
     """Unit weights in FP64: the sliced count is the exact model count."""
     cnf = wmcgen.random_kcnf(20, 60, seed=5)
