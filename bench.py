@@ -52,7 +52,7 @@ POOL = 4096
 # when that source differs, the ratio no longer describes the kernel and
 # `roofline.traffic` is null.
 TRAFFIC_CAPTURE = {"ratio": 736.2e6 / 939.7e6,
-                   "chain_source_sha256": "2989a1d9e254375b4095ade9199a235787ebcabf5f24c0e765318f6f2023fc9f"}
+                   "chain_source_sha256": "869b1e344008fb48e90f0cdc05e382ea3b2bf8220381d04400614e18e0fa7f07"}
 
 
 def _kernel_source_sha256() -> str:
@@ -63,9 +63,11 @@ def _kernel_source_sha256() -> str:
     with open(os.path.join(csrc, "dev_common.cuh")) as f:
         dc = f.read()
     pre = k[:k.index("// ------------------------------------------------------------ K1 generic")]
-    reg = k[k.index("// ------------------------------------------------- K2 with TMA staging"):
-            k.index("// ------------------------------------------ runs of chains in one launch")]
-    return hashlib.sha256((pre + reg + dc).encode()).hexdigest()
+    tma = k[k.index("// ------------------------------------------------- K2 with TMA staging"):
+            k.index("// ------------------------------------------- batched small contractions")]
+    chain = k[k.index("// ---------------------------------------------- chain of frontier eliminations"):
+              k.index("// ----------------------------------------- long chains, direct loads")]
+    return hashlib.sha256((pre + tma + chain + dc).encode()).hexdigest()
 
 
 def traffic_ratio():

@@ -2812,17 +2812,22 @@ __device__ __forceinline__ void small_lut(const SNode &nd, uint32_t (*lut)[256],
 
 template <typename TI, typename TA, typename TO>
 __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uint32_t (*lut)[256],
-                           unsigned long long *smax, unsigned long long *smin) {
+                           TA *scl, unsigned long long *smax, unsigned long long *smin) {
   char *ws = sa_.ws;
   const TI *A = (const TI *)(ws + nd.a);
   const TI *B = (const TI *)(ws + nd.b);
   TO *C = (TO *)(ws + nd.c);
-  // chunk 0 writes C's exponents and runs the flush test, from the
-  // children's metadata alone (their max patterns are final: children done)
-  if (chunk == 0)
-    for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
-      const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
-      const unsigned long long xa = __ldcg(sa_.mmax + nd.ma + qa), xb = __ldcg(sa_.mmax + nd.mb + qb);
+  // per-lane operand scales (their max patterns are final: children done);
+  // chunk 0 also writes C's exponents and runs the flush test now, from the
+  // children's metadata alone (off the path that waits for the outputs)
+  for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
+    const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+    const unsigned long long xa = __ldcg(sa_.mmax + nd.ma + qa), xb = __ldcg(sa_.mmax + nd.mb + qb);
+    scl[q] = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
+    scl[nd.Qc + q] = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
+    smax[q] = 0;
+    smin[q] = kNoMin;
+    if (chunk == 0) {
       sa_.mexp[nd.mc + q] = __ldcg(sa_.mexp + nd.ma + qa) + pow2_exp_of(xa, TI()) +
                             __ldcg(sa_.mexp + nd.mb + qb) + pow2_exp_of(xb, TI());
       const unsigned long long na = __ldcg(sa_.mmin + nd.ma + qa), nb = __ldcg(sa_.mmin + nd.mb + qb);
@@ -2836,11 +2841,8 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
         }
       }
     }
-  // the operands' per-lane scales, read beside their values (no barrier on
-  // the path from the children's completion to the loads)
-  auto scale_of = [&](int64_t slot) {
-    return (TA)pow2_scale(pow2_exp_of(__ldcg(sa_.mmax + slot), TI()), TI());
-  };
+  }
+  __syncthreads();
   const uint32_t o0 = (uint32_t)chunk << nd.chunk_log2, o1 = o0 + (1u << nd.chunk_log2);
   const uint32_t ns = 1u << nd.k;
   // a thread's outputs share one query lane when the lanes divide the block
@@ -2853,7 +2855,7 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
     const uint32_t bA = lut[0][o & 255] | lut[1][(o >> 8) & 255];
     const uint32_t bB = lut[2][o & 255] | lut[3][(o >> 8) & 255];
     const int q = (int)(o & (uint32_t)(nd.Qc - 1));
-    const TA sa = scale_of(nd.ma + (q & nd.qmask_a)), sb = scale_of(nd.mb + (q & nd.qmask_b));
+    const TA sa = scl[q], sb = scl[nd.Qc + q];
     TA acc = (TA)0;
     for (uint32_t s = 0; s < ns; ++s) {
       const TA a = (TA)__ldcg(A + (bA | lut[4][s])) * sa;
@@ -2879,29 +2881,21 @@ __device__ void small_task(const SmallArgs &sa_, const SNode &nd, int chunk, uin
   for (int q = threadIdx.x; q < nd.Qc; q += blockDim.x) {
     if (smax[q]) atomicMax(sa_.mmax + nd.mc + q, smax[q]);
     if (smin[q] != kNoMin) atomicMin(sa_.mmin + nd.mc + q, smin[q]);
-    smax[q] = 0;  // (clear for the block's next task)
-    smin[q] = kNoMin;
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
   __shared__ uint32_t lut[6][256];
   __shared__ uint32_t lut_bits[6][8], lut_nib[6][2][16];
+  __shared__ double scl_d[2 * kMaxQ];
   __shared__ unsigned long long smax[kMaxQ], smin[kMaxQ];
   __shared__ int s_task, s_ok;
   int lut_node = -1;  // node whose tables the block holds
-  for (int q = threadIdx.x; q < kMaxQ; q += blockDim.x) { smax[q] = 0; smin[q] = kNoMin; }
-  // thread 0 takes the block's next task index while the block runs the
-  // current one (tasks still run in index order per block, so every wait
-  // is on a task some running block holds)
-  int next_task = 0;
-  if (threadIdx.x == 0) next_task = (int)atomicAdd(a.next, 1u);
   for (;;) {
-    if (threadIdx.x == 0) s_task = next_task;
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(a.next, 1u);
     __syncthreads();
     const int t = s_task;
     if (t >= a.n_tasks) break;
-    if (threadIdx.x == 0) next_task = (int)atomicAdd(a.next, 1u);
     const STask task = a.tasks[t];
     const SNode &nd = a.nodes[task.node];
     if (task.node != lut_node) {  // overlaps the wait for the children
@@ -2918,9 +2912,9 @@ __global__ void __launch_bounds__(kThreads) k_small_phase(SmallArgs a) {
     }
     __syncthreads();
     if (!s_ok) break;
-    if (nd.ti == 1) small_task<double, double, double>(a, nd, task.chunk, lut, smax, smin);
-    else if (nd.to == 1) small_task<float, double, double>(a, nd, task.chunk, lut, smax, smin);
-    else small_task<float, float, float>(a, nd, task.chunk, lut, smax, smin);
+    if (nd.ti == 1) small_task<double, double, double>(a, nd, task.chunk, lut, scl_d, smax, smin);
+    else if (nd.to == 1) small_task<float, double, double>(a, nd, task.chunk, lut, scl_d, smax, smin);
+    else small_task<float, float, float>(a, nd, task.chunk, lut, reinterpret_cast<float *>(scl_d), smax, smin);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // outputs and metadata before the completion count
