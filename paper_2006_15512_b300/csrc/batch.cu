@@ -990,15 +990,15 @@ namespace {
 // Estimated microseconds of one task (cost model of the list scheduling):
 // a fixed part (counter, tables, epilogue) and a rate per element moved,
 // as measured per block with every block of the persistent kernel busy
-// (4 per SM; float32, 512-formula batch): chains 0.34 ns per element
-// (2^D loads and up to 2^D stores per unit), stream mode 0.62 ns (2^k
+// (4 per SM; float32, 512-formula batch): chains 0.53 ns per element
+// (2^D loads and up to 2^(D+1) stores per unit), stream mode 0.62 ns (2^k
 // loads and 2^f stores per unit), the generic path 1.1 ns per output and
-// summed term, small subtrees 8.7 us per node.
+// summed term, small subtrees 5.5 us per node.
 double task_us(const BNode &n) {
   const double el = n.ti ? 2.0 : 1.0;  // element size in float32 units
   if (n.stream == 3) return n.est_us;
   const double units = std::ldexp(1.0, n.chunk_log2);
-  if (n.stream == 2) return 2.0 + 0.00034 * el * units * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
+  if (n.stream == 2) return 2.0 + 0.00053 * el * units * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
   if (n.stream) return 2.0 + 0.00062 * el * units * (std::ldexp(1.0, n.k) + std::ldexp(1.0, n.f));
   return 2.0 + 0.0011 * el * units * (1.0 + std::ldexp(1.0, n.k));
 }
@@ -1423,7 +1423,7 @@ extern "C" int wmc_batch_create(wmc_plan_t *const *plans, int32_t n_plans, int64
         n_members += (int64_t)gr.size();
       }
       if (b->members.size() > (size_t)INT32_MAX) { delete b; set_error("batch has more than 2^31 subtree nodes"); return WMC_EPLAN_TOO_BIG; }
-      g.est_us = (float)(2.0 + 8.7 * (double)n_members / (double)groups.size());
+      g.est_us = (float)(2.0 + 5.5 * (double)n_members / (double)groups.size());
       prev = (int32_t)b->nodes.size();
       ids.push_back(prev);
       b->nodes.push_back(g);
