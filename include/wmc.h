@@ -491,9 +491,9 @@ int wmc_profile_walk(wmc_plan_t *plan, int32_t Q, const double *d_w_pos,
                      float *node_ms, int32_t *kind, double *alg_bytes,
                      int64_t *n_launches);
 
-/* Autotuning of a plan's walk (the benchmark spec's tuner of kernel shape against
- * the index split, at the level of the whole walk): for batch size Q, times
- * the walk under up to eight layouts -- chains of up to 4, 3 or 2
+/* Autotuning of a plan's walk (the tuner of kernel shape against the
+ * index split, at the level of the whole walk): for batch size Q, times
+ * the walk under up to eight layouts -- chains of up to 6, 4, 3 or 2
  * consecutive frontier eliminations per pass or none, the small-node phase
  * on or off, runs of chains in one launch (float32) -- on the network's
  * default weights (median of five walks after two warm-up walks, on
