@@ -196,12 +196,18 @@ struct ExecState {
   // resources of the host-pointer path
   void *own_ws = nullptr;
   double *d_w = nullptr;          // [2][Q][n_vars]
-  double *d_res_mant = nullptr;   // [Q]
+  // results: [Q] mantissas, [Q] exponents, [Q] flags in one allocation
+  // (one device-to-host copy), mirrored in pinned host memory
+  double *d_res_mant = nullptr;
   int64_t *d_res_exp = nullptr;
   uint32_t *d_res_flags = nullptr;
-  double *h_res_mant = nullptr;   // pinned
+  double *h_res_mant = nullptr;
   int64_t *h_res_exp = nullptr;
   uint32_t *h_res_flags = nullptr;
+  // pinned staging of small calls' inputs: the call descriptor, then the
+  // weights (w_pos, w_neg), so that each crosses in one copy from pinned
+  // memory instead of through the driver's pageable path
+  unsigned char *h_stage = nullptr;
   std::mutex run_mu;    // the owned workspace of the host-pointer path
   std::mutex graph_mu;  // graphs map
 
@@ -210,8 +216,8 @@ struct ExecState {
     if (capture_stream) cudaStreamDestroy(capture_stream);
     cudaFree(d_clause); cudaFree(d_first); cudaFree(d_woff); cudaFree(d_wmeta);
     cudaFree(d_snodes); cudaFree(d_stasks); cudaFree(d_seq); cudaFree(d_cta);
-    cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant); cudaFree(d_res_exp); cudaFree(d_res_flags);
-    cudaFreeHost(h_res_mant); cudaFreeHost(h_res_exp); cudaFreeHost(h_res_flags);
+    cudaFree(own_ws); cudaFree(d_w); cudaFree(d_res_mant);
+    cudaFreeHost(h_res_mant); cudaFreeHost(h_stage);
   }
 };
 
@@ -2012,7 +2018,7 @@ static int64_t n_slices(const Plan &plan) { return int64_t(1) << plan.slice_vars
 static int run_device(Plan &plan, ExecState &st, const double *d_wp, const double *d_wn,
                       char *ws, double *d_mant, int64_t *d_exp, uint32_t *d_flags,
                       cudaStream_t s, int64_t slice_lo = 0, int64_t slice_hi = -1, int32_t lanes_per_slice = 0,
-                      int32_t n_lanes = 0) {
+                      int32_t n_lanes = 0, IoDesc *h_io = nullptr) {
   if (slice_hi < 0) slice_hi = n_slices(plan);
   if (slice_lo < 0 || slice_lo >= slice_hi || slice_hi > n_slices(plan)) {
     set_error("slice range [%lld, %lld) outside [0, %lld)", (long long)slice_lo, (long long)slice_hi,
@@ -2032,15 +2038,20 @@ static int run_device(Plan &plan, ExecState &st, const double *d_wp, const doubl
     io.slice = (uint64_t)slice_lo;
     io.lanes_per_slice = lanes_per_slice;
     io.n_lanes = n_lanes;
-    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    if (h_io) *h_io = io;
+    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, h_io ? h_io : &io, sizeof(io), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));
     g_launches.fetch_add(st.kernels_per_run);
     return WMC_OK;
   }
+  // (the pinned descriptor serves one launch: a later one would overwrite
+  // it before the earlier copy has run)
+  if (slice_hi - slice_lo != 1) h_io = nullptr;
   for (int64_t eta = slice_lo; eta < slice_hi; ++eta) {
     io.slice = (uint64_t)eta;
     io.accumulate = eta != slice_lo;
-    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, &io, sizeof(io), cudaMemcpyHostToDevice, s));
+    if (h_io) *h_io = io;
+    CUDA_TRY(cudaMemcpyAsync(ws + st.off_io, h_io ? h_io : &io, sizeof(io), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaGraphLaunch(ge, s));
     g_launches.fetch_add(st.kernels_per_run);
   }
@@ -2367,6 +2378,11 @@ extern "C" int wmc_execute_slices(wmc_plan_t *plan, int32_t Q, const double *w_p
 }
 
 // One walk of state `st` with host weights, results filled into out[Q].
+// pinned staging per execution state: the call descriptor (256-byte slot)
+// and up to 64 KB of weights (larger inputs take the pageable path)
+static constexpr size_t kStageIoBytes = (sizeof(IoDesc) + 255) / 256 * 256;
+static constexpr size_t kStageWeightBytes = size_t(64) << 10;
+
 static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_pos_q, const double *w_neg_q,
                     int64_t slice_lo, int64_t slice_hi, void *stream, wmc_result *out, int32_t lanes_per_slice = 0,
                     int32_t n_lanes = 0) {
@@ -2378,20 +2394,32 @@ static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_
     if (!st->own_ws) {
       if ((rc = dev_alloc(&st->own_ws, (size_t)st->ws_bytes))) return rc;
       if ((rc = dev_alloc((void **)&st->d_w, sizeof(double) * 2 * (size_t)Q * std::max<size_t>(nv, 1)))) return rc;
-      if ((rc = dev_alloc((void **)&st->d_res_mant, sizeof(double) * (size_t)Q))) return rc;
-      if ((rc = dev_alloc((void **)&st->d_res_exp, sizeof(int64_t) * (size_t)Q))) return rc;
-      if ((rc = dev_alloc((void **)&st->d_res_flags, sizeof(uint32_t) * (size_t)Q))) return rc;
-      CUDA_TRY(cudaMallocHost(&st->h_res_mant, sizeof(double) * (size_t)Q));
-      CUDA_TRY(cudaMallocHost(&st->h_res_exp, sizeof(int64_t) * (size_t)Q));
-      CUDA_TRY(cudaMallocHost(&st->h_res_flags, sizeof(uint32_t) * (size_t)Q));
+      const size_t res_bytes = 20 * (size_t)Q;
+      if ((rc = dev_alloc((void **)&st->d_res_mant, res_bytes))) return rc;
+      st->d_res_exp = (int64_t *)(st->d_res_mant + Q);
+      st->d_res_flags = (uint32_t *)(st->d_res_exp + Q);
+      CUDA_TRY(cudaMallocHost(&st->h_res_mant, res_bytes));
+      st->h_res_exp = (int64_t *)(st->h_res_mant + Q);
+      st->h_res_flags = (uint32_t *)(st->h_res_exp + Q);
+      if (kStageWeightBytes > 0)
+        CUDA_TRY(cudaMallocHost(&st->h_stage, kStageIoBytes + kStageWeightBytes));
     }
   }
+  IoDesc *h_io = st->h_stage ? (IoDesc *)st->h_stage : nullptr;
+  double *h_w = st->h_stage ? (double *)(st->h_stage + kStageIoBytes) : nullptr;
+  const size_t w_bytes = sizeof(double) * 2 * (size_t)Q * nv;  // w_pos then w_neg
   bool unit = true, negative = false;
   if (nv) {
     double *d_wp = st->d_w, *d_wn = st->d_w + (size_t)Q * nv;
-    if (w_pos_q) {
+    if (w_pos_q && h_w && w_bytes <= kStageWeightBytes) {  // small: one copy from pinned staging
+      std::memcpy(h_w, w_pos_q, w_bytes / 2);
+      std::memcpy(h_w + (size_t)Q * nv, w_neg_q, w_bytes / 2);
+      CUDA_TRY(cudaMemcpyAsync(d_wp, h_w, w_bytes, cudaMemcpyHostToDevice, s));
+    } else if (w_pos_q) {
       CUDA_TRY(cudaMemcpyAsync(d_wp, w_pos_q, sizeof(double) * (size_t)Q * nv, cudaMemcpyHostToDevice, s));
       CUDA_TRY(cudaMemcpyAsync(d_wn, w_neg_q, sizeof(double) * (size_t)Q * nv, cudaMemcpyHostToDevice, s));
+    }
+    if (w_pos_q) {
       for (size_t i = 0; i < (size_t)Q * nv; ++i) {
         unit &= (w_pos_q[i] == 1.0) & (w_neg_q[i] == 1.0);
         negative |= (w_pos_q[i] < 0.0) | (w_neg_q[i] < 0.0);
@@ -2406,12 +2434,11 @@ static int run_host(wmc_plan_t *plan, ExecState *st, int32_t Q, const double *w_
     }
   }
   rc = run_device(*plan, *st, st->d_w, st->d_w + (size_t)Q * nv, (char *)st->own_ws,
-                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s, slice_lo, slice_hi, lanes_per_slice, n_lanes);
+                  st->d_res_mant, st->d_res_exp, st->d_res_flags, s, slice_lo, slice_hi, lanes_per_slice, n_lanes,
+                  h_io);
   if (rc) return rc;
-  CUDA_TRY(cudaMemcpyAsync(st->h_res_mant, st->d_res_mant, sizeof(double) * (size_t)Q, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(st->h_res_exp, st->d_res_exp, sizeof(int64_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaMemcpyAsync(st->h_res_flags, st->d_res_flags, sizeof(uint32_t) * (size_t)Q, cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaMemcpyAsync(st->h_res_mant, st->d_res_mant, 20 * (size_t)Q, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));  // (also frees the staging for the next call)
   for (int32_t q = 0; q < Q; ++q)
     if (st->h_res_flags[q] & WMC_FLAG_DEVICE_TIMEOUT) {
       set_error("a bounded wait inside a contraction kernel timed out; results discarded");
