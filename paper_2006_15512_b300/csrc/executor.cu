@@ -157,6 +157,11 @@ struct ExecState {
   std::vector<wmc::dev::CtaLeaf> h_cta;
   wmc::dev::CtaLeaf *d_cta = nullptr;
   int64_t cta_smem = 0, cta_meta = 0;  // total; before the arena
+  // one-block walk: the nodes by level (a level's nodes are independent),
+  // and the shared-memory offset and size (words) of the per-level tables
+  std::vector<int64_t> cta_order;
+  std::vector<int32_t> cta_level_end;  // per position: one past its level's last
+  int64_t cta_lut_off = 0, cta_lut_words = 0;
   std::vector<int64_t> cta_off;  // shared-memory arena offset per tensor (-1: none; the root: none)
   uint64_t serial = ++g_state_serial;  // unique per state for the life of the process
   int32_t Q = 1, m = 0;
@@ -933,19 +938,63 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       if ((int)C.labels.size() + (C.has_q ? m : 0) > 16 || nd.n_summed > 8) { cta = false; break; }
     }
   }
+  std::vector<int64_t> cta_order;
+  std::vector<int32_t> cta_level_end;
+  int64_t cta_lut_words = 0;
   if (cta) {
-    FirstFit sf;  // leaves first, then each node's output; children freed after their node
-    for (int64_t i = 0; i < plan.n_leaves; ++i) cta_off[(size_t)i] = sf.alloc(bytes[(size_t)i]);
-    for (size_t ni = 0; ni + 1 < plan.nodes.size(); ++ni) {  // the root goes to the workspace
-      const Node &nd = plan.nodes[ni];
-      cta_off[(size_t)nd.c] = sf.alloc(bytes[(size_t)nd.c]);
-      sf.release(cta_off[(size_t)nd.a], bytes[(size_t)nd.a]);
-      sf.release(cta_off[(size_t)nd.b], bytes[(size_t)nd.b]);
+    // levels, as late as possible: the root's is the tree's height, every
+    // other node's one below its parent's, so a node runs just before its
+    // parent and its output lives for one level (children always sit at
+    // lower levels).  The block runs one level at a time, so outputs are
+    // placed level by level and a level's children freed after it.
+    std::vector<int32_t> depth(plan.nodes.size(), 0);
+    int32_t top = 0;
+    for (size_t r = plan.nodes.size(); r-- > 0;) {  // parents before children
+      const Node &nd = plan.nodes[r];
+      for (int64_t t : {nd.a, nd.b}) {
+        const int64_t ch = plan.tensors[(size_t)t].node;
+        if (ch >= 0) depth[(size_t)ch] = depth[r] + 1;
+      }
+      top = std::max(top, depth[r] + 1);
     }
-    if (cta_meta + align_up(sf.top) > 200 * 1024) cta = false;
-    else st.cta_smem = cta_meta + align_up(sf.top);
+    std::vector<int32_t> lev(plan.nodes.size(), 0);
+    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) lev[ni] = top - depth[ni];
+    for (int32_t L = 1; L <= top; ++L)
+      for (size_t ni = 0; ni < plan.nodes.size(); ++ni)
+        if (lev[ni] == L) cta_order.push_back((int64_t)ni);
+    if (plan.nodes[(size_t)cta_order.back()].c != root) cta = false;  // (the root is the one top node)
+    FirstFit sf;
+    for (int64_t i = 0; i < plan.n_leaves; ++i) cta_off[(size_t)i] = sf.alloc(bytes[(size_t)i]);
+    for (size_t f0 = 0; cta && f0 < cta_order.size();) {
+      size_t f1 = f0;
+      int64_t words = 0;
+      while (f1 < cta_order.size() && lev[(size_t)cta_order[f1]] == lev[(size_t)cta_order[f0]]) {
+        const Node &nd = plan.nodes[(size_t)cta_order[f1]];
+        const TensorInfo &C = plan.tensors[(size_t)nd.c];
+        const int rC = (int)C.labels.size() + (C.has_q ? m : 0);
+        words += 2 * ((1 << std::min(rC, 8)) + (1 << std::max(rC - 8, 0)) + (1 << nd.n_summed));
+        if (nd.c != root) cta_off[(size_t)nd.c] = sf.alloc(bytes[(size_t)nd.c]);
+        ++f1;
+      }
+      for (size_t f = f0; f < f1; ++f) {
+        const Node &nd = plan.nodes[(size_t)cta_order[f]];
+        sf.release(cta_off[(size_t)nd.a], bytes[(size_t)nd.a]);
+        sf.release(cta_off[(size_t)nd.b], bytes[(size_t)nd.b]);
+        cta_level_end.push_back((int32_t)f1);
+      }
+      cta_lut_words = std::max(cta_lut_words, words);
+      f0 = f1;
+    }
+    const int64_t need = cta_meta + align_up(sf.top) + align_up(4 * cta_lut_words);
+    if (need > 200 * 1024) cta = false;
+    else {
+      st.cta_smem = need;
+      st.cta_lut_off = cta_meta + align_up(sf.top);
+      st.cta_lut_words = cta_lut_words;
+    }
   }
-  if (cta) { st.wo.small_phase = 0; st.cta_off = cta_off; st.cta_meta = cta_meta; }
+  if (cta) { st.wo.small_phase = 0; st.cta_off = cta_off; st.cta_meta = cta_meta; st.cta_order = cta_order;
+    st.cta_level_end = cta_level_end; }
   if (st.wo.small_phase && !plain) {
     for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
       const Node &nd = plan.nodes[ni];
@@ -1440,8 +1489,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       }
       st.h_cta.push_back(L);
     }
-    for (size_t ni = 0; ni < plan.nodes.size(); ++ni) {
-      const Node &nd = plan.nodes[ni];
+    int32_t lut_base = 0, out_base = 0;
+    for (size_t oi = 0; oi < st.cta_order.size(); ++oi) {
+      const int64_t ni = st.cta_order[oi];
+      const Node &nd = plan.nodes[(size_t)ni];
       const TensorInfo &A = plan.tensors[(size_t)nd.a], &B = plan.tensors[(size_t)nd.b];
       const TensorInfo &C = plan.tensors[(size_t)nd.c];
       const bool is_root = nd.c == root;
@@ -1464,6 +1515,13 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       sn.ti = st.f64 ? 1 : 0;
       sn.to = st.t_dbl[(size_t)nd.c];
       sn.ta = (st.f64 || is_root) ? 1 : 0;
+      // (the order lists the levels one after another)
+      if (oi == 0 || st.cta_level_end[oi - 1] == (int32_t)oi) { lut_base = 0; out_base = 0; }
+      sn.level_end = st.cta_level_end[oi];
+      sn.lut_base = lut_base;
+      sn.out_base = out_base;
+      lut_base += 2 * ((1 << std::min<int32_t>(sn.rC, 8)) + (1 << std::max<int32_t>(sn.rC - 8, 0)) + (1 << sn.k));
+      out_base += 1 << sn.rC;
       st.h_snodes.push_back(sn);
     }
     std::vector<Launch> keep;
@@ -1898,6 +1956,7 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         a.nodes_off = (uint32_t)align_up(24 * st.n_slots);
         a.leaves_off = a.nodes_off + (uint32_t)align_up((int64_t)sizeof(wmc::dev::SNode) * (int64_t)st.h_snodes.size());
         a.meta_bytes = (uint32_t)st.cta_meta;
+        a.lut_off = (uint32_t)st.cta_lut_off;
         static bool attr_set = false;  // opt in to large dynamic shared memory once
         if (!attr_set) {
           cudaFuncSetAttribute(dev::k_cta_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -3262,7 +3321,7 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     const bool cta_root = cta && i + 1 == st->h_snodes.size();
     auto within = [&](int64_t off, int64_t last_elem, int64_t es, bool shared) {
       if (shared) {  // one-block walk: a tensor of the shared-memory arena
-        const int64_t arena = st->cta_smem - st->cta_meta;
+        const int64_t arena = st->cta_lut_off - st->cta_meta;  // (the level tables follow it)
         for (size_t t = 0; t < st->cta_off.size(); ++t)
           if (st->cta_off[t] == off && (last_elem + 1) * es <= st->t_bytes[t] && off + st->t_bytes[t] <= arena)
             return true;
@@ -3279,6 +3338,31 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
     }
     if (sn.chunk_log2 > sn.rC || sn.k > 8 || sn.rC > 16) { set_error("small-phase node %zu: bad shape", i); return WMC_EINVAL; }
     ++checked;
+  }
+  // one-block walk: levels partition the node list, each level's tables
+  // and outputs are laid out back to back, the tables fit their region
+  if (!st->h_cta.empty()) {
+    const size_t n = st->h_snodes.size();
+    for (size_t i = 0; i < n;) {
+      const size_t e = (size_t)st->h_snodes[i].level_end;
+      if (e <= i || e > n) { set_error("one-block walk: level of node %zu ends at %zu", i, e); return WMC_EINVAL; }
+      int64_t words = 0, outs = 0;
+      for (size_t j = i; j < e; ++j) {
+        const wmc::dev::SNode &sn = st->h_snodes[j];
+        if (sn.lut_base != words || sn.out_base != outs || (size_t)sn.level_end != e) {
+          set_error("one-block walk: node %zu's table or output offset", j);
+          return WMC_EINVAL;
+        }
+        words += 2 * ((1 << std::min<int32_t>(sn.rC, 8)) + (1 << std::max<int32_t>(sn.rC - 8, 0)) + (1 << sn.k));
+        outs += int64_t(1) << sn.rC;
+      }
+      if (words > st->cta_lut_words || st->cta_lut_off + 4 * words > st->cta_smem || outs > (int64_t(1) << 31)) {
+        set_error("one-block walk: a level's tables (%lld words) exceed their region", (long long)words);
+        return WMC_EINVAL;
+      }
+      i = e;
+      ++checked;
+    }
   }
   // weight leaves: every variable's table entry is its own leaf or -1
   {

@@ -2745,6 +2745,10 @@ struct SNode {
   int32_t rC, k;
   int8_t ti, ta, to, pad;
   int8_t posA[16], posB[16], sposA[8], sposB[8];
+  // one-block walk (nodes ordered by level): the node's lookup tables at
+  // word lut_base of its level's tables, its outputs at out_base of the
+  // level's outputs, and one past the level's last node
+  int32_t lut_base, out_base, level_end, pad2;
 };
 
 struct STask {
@@ -3071,62 +3075,83 @@ struct CtaArgs {
   int32_t f64;
   uint32_t nodes_off, leaves_off;  // shared-memory offsets of the node program and the leaf descriptors
   uint32_t meta_bytes;        // shared memory before the arena: metadata, program, leaves
+  uint32_t lut_off;           // shared memory of one level's lookup tables (after the arena)
 };
 
-// One node of the one-block walk.  Every thread's outputs share one query
-// lane (the block is 1024 threads and there are at most 4 lanes), so its
-// max and min are folded across the warp's lanes of that query before one
-// shared atomic per warp.
+// The one-block walk runs the tree level by level: a node's level is one
+// more than its children's (leaves 0), so the nodes of a level are
+// independent.  Per level: every node's lookup tables and C's exponents
+// and flush test (from the children's metadata), a barrier, all the
+// level's outputs spread over the block's threads (max and min straight
+// into C's metadata slots by shared atomics), a barrier.  The barriers
+// follow the tree's height instead of its node count.
+//
+// A node's tables (2 (n0 + n1 + ns) words at lut_base): A's offsets of
+// output bits 0-7 (n0 = 2^min(8, rC)), of bits 8-15 (n1 = 2^max(0, rC - 8))
+// and of the summed bits (ns = 2^k), then the same for B.
+__device__ __forceinline__ void cta_table_entry(const SNode &nd, uint32_t *T, int i) {
+  const int rc = nd.rC, n0 = 1 << (rc < 8 ? rc : 8), n1 = 1 << (rc > 8 ? rc - 8 : 0), ns = 1 << nd.k;
+  const int half = n0 + n1 + ns;
+  const int op = i >= half ? 1 : 0, k = i - op * half;
+  int v, base, nb;
+  const int8_t *pos;
+  if (k < n0) { v = k; base = 0; nb = rc < 8 ? rc : 8; pos = op ? nd.posB : nd.posA; }
+  else if (k < n0 + n1) { v = k - n0; base = 8; nb = rc - 8; pos = op ? nd.posB : nd.posA; }
+  else { v = k - n0 - n1; base = 0; nb = nd.k; pos = op ? nd.sposB : nd.sposA; }
+  uint32_t o = 0;
+  for (int b = 0; b < nb; ++b)
+    if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
+  T[i] = o;
+}
+
+// C's exponent per lane and the float32 flush test, from the operands'
+// metadata (their max and min are final: earlier levels)
+template <typename TI>
+__device__ __forceinline__ void cta_node_meta(const CtaArgs &a, const SNode &nd, int q, int64_t *mexp,
+                                              const unsigned long long *mmax, const unsigned long long *mmin,
+                                              bool root) {
+  const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
+  const unsigned long long xa = mmax[nd.ma + qa], xb = mmax[nd.mb + qb];
+  const int64_t e = mexp[nd.ma + qa] + pow2_exp_of(xa, TI()) + mexp[nd.mb + qb] + pow2_exp_of(xb, TI());
+  mexp[nd.mc + q] = e;
+  if (root) a.gexp[nd.mc + q] = e;
+  const unsigned long long na = mmin[nd.ma + qa], nb = mmin[nd.mb + qb];
+  if (na != kNoMin && nb != kNoMin) {
+    const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
+                  (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
+    if (below_normal(lo)) {
+      if (nd.Qc > 1) atomicOr(a.flags + q, 2u);
+      else
+        for (int qq = 0; qq < a.Qp; ++qq) atomicOr(a.flags + qq, 2u);
+    }
+  }
+}
+
+// Output o of a node: its terms in ascending summed order (the canonical
+// chain of every other kernel), operands scaled per lane by their pow2
+// scales
 template <typename TI, typename TA, typename TO>
-__device__ void cta_node(const CtaArgs &a, const SNode &nd, unsigned char *arena, int64_t *mexp,
-                         const unsigned long long *mmax, const unsigned long long *mmin, uint32_t (*lut)[256],
-                         unsigned long long *smax, unsigned long long *smin, bool root) {
+__device__ __forceinline__ void cta_output(const CtaArgs &a, const SNode &nd, uint32_t o, unsigned char *arena,
+                                           unsigned long long *mmax, unsigned long long *mmin, const uint32_t *T,
+                                           bool root) {
   const TI *A = (const TI *)(arena + nd.a);
   const TI *B = (const TI *)(arena + nd.b);
   TO *C = root ? (TO *)(a.ws + nd.c) : (TO *)(arena + nd.c);
-  const int q = (int)(threadIdx.x & (uint32_t)(nd.Qc - 1));
-  const int qa = q & nd.qmask_a, qb = q & nd.qmask_b;
-  const unsigned long long xa = mmax[nd.ma + qa], xb = mmax[nd.mb + qb];
-  const TA sa = (TA)pow2_scale(pow2_exp_of(xa, TI()), TI());
-  const TA sb = (TA)pow2_scale(pow2_exp_of(xb, TI()), TI());
-  if ((int)threadIdx.x < nd.Qc) {
-    // C's exponent and the float32 flush test, from the operands' metadata
-    const int64_t e = mexp[nd.ma + qa] + pow2_exp_of(xa, TI()) + mexp[nd.mb + qb] + pow2_exp_of(xb, TI());
-    mexp[nd.mc + q] = e;
-    if (root) a.gexp[nd.mc + q] = e;
-    const unsigned long long na = mmin[nd.ma + qa], nb = mmin[nd.mb + qb];
-    if (na != kNoMin && nb != kNoMin) {
-      const TI lo = (from_bits<TI>(na) * pow2_scale(pow2_exp_of(xa, TI()), TI())) *
-                    (from_bits<TI>(nb) * pow2_scale(pow2_exp_of(xb, TI()), TI()));
-      if (below_normal(lo)) {
-        if (nd.Qc > 1) atomicOr(a.flags + q, 2u);
-        else
-          for (int qq = 0; qq < a.Qp; ++qq) atomicOr(a.flags + qq, 2u);
-      }
-    }
-  }
-  const uint32_t n_out = 1u << nd.rC, ns = 1u << nd.k;
-  unsigned long long bmax = 0, bmin = kNoMin;
-  for (uint32_t o = threadIdx.x; o < n_out; o += blockDim.x) {
-    const uint32_t bA = lut[0][o & 255] | lut[1][o >> 8];
-    const uint32_t bB = lut[2][o & 255] | lut[3][o >> 8];
-    TA acc = (TA)0;
-    for (uint32_t s = 0; s < ns; ++s) acc = fma_t((TA)A[bA | lut[4][s]] * sa, (TA)B[bB | lut[5][s]] * sb, acc);
-    const TO c = (TO)acc;
-    C[o] = c;
-    const unsigned long long bits = abs_bits(c);
-    bmax = bits > bmax ? bits : bmax;
-    if (bits) bmin = bits < bmin ? bits : bmin;
-  }
-  for (int o = 16; o >= nd.Qc; o >>= 1) {
-    const unsigned long long xm = __shfl_xor_sync(0xffffffffu, bmax, o);
-    const unsigned long long xn = __shfl_xor_sync(0xffffffffu, bmin, o);
-    bmax = xm > bmax ? xm : bmax;
-    bmin = xn < bmin ? xn : bmin;
-  }
-  if ((int)(threadIdx.x & 31u) < nd.Qc) {
-    if (bmax) atomicMax(smax + q, bmax);
-    if (bmin != kNoMin) atomicMin(smin + q, bmin);
+  const int q = (int)(o & (uint32_t)(nd.Qc - 1));
+  const TA sa = (TA)pow2_scale(pow2_exp_of(mmax[nd.ma + (q & nd.qmask_a)], TI()), TI());
+  const TA sb = (TA)pow2_scale(pow2_exp_of(mmax[nd.mb + (q & nd.qmask_b)], TI()), TI());
+  const uint32_t n0 = 1u << (nd.rC < 8 ? nd.rC : 8), n1 = 1u << (nd.rC > 8 ? nd.rC - 8 : 0), ns = 1u << nd.k;
+  const uint32_t *TA0 = T, *TA1 = TA0 + n0, *TSA = TA1 + n1, *TB0 = TSA + ns, *TB1 = TB0 + n0, *TSB = TB1 + n1;
+  const uint32_t bA = TA0[o & 255] | TA1[o >> 8];
+  const uint32_t bB = TB0[o & 255] | TB1[o >> 8];
+  TA acc = (TA)0;
+  for (uint32_t s = 0; s < ns; ++s) acc = fma_t((TA)A[bA | TSA[s]] * sa, (TA)B[bB | TSB[s]] * sb, acc);
+  const TO c = (TO)acc;
+  C[o] = c;
+  const unsigned long long bits = abs_bits(c);
+  if (bits) {
+    atomicMax(mmax + nd.mc + q, bits);
+    atomicMin(mmin + nd.mc + q, bits);
   }
 }
 
@@ -3134,8 +3159,6 @@ __global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
   // dynamic shared memory: metadata (exp, max, min per slot), the node
   // program, the leaf descriptors, then the tensor arena
   extern __shared__ __align__(16) unsigned char cta_smem[];
-  __shared__ uint32_t lut[6][256];
-  __shared__ unsigned long long smax[4], smin[4];
   int64_t *mexp = (int64_t *)cta_smem;
   unsigned long long *mmax = (unsigned long long *)(cta_smem + 8 * (size_t)a.n_slots);
   unsigned long long *mmin = (unsigned long long *)(cta_smem + 16 * (size_t)a.n_slots);
@@ -3152,7 +3175,6 @@ __global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
       reinterpret_cast<uint32_t *>(leaves)[i] = reinterpret_cast<const uint32_t *>(a.leaves)[i];
   }
   for (int i = threadIdx.x; i < a.n_slots; i += blockDim.x) { mexp[i] = 0; mmax[i] = 0; mmin[i] = kNoMin; }
-  if (threadIdx.x < 4) { smax[threadIdx.x] = 0; smin[threadIdx.x] = kNoMin; }
   __syncthreads();
   // ---- leaves, one thread per leaf (as k_clause_leaves, k_weight_leaves
   // and k_one_leaf)
@@ -3209,39 +3231,48 @@ __global__ void __launch_bounds__(1024, 1) k_cta_walk(CtaArgs a) {
       mmax[L.slot] = mmin[L.slot] = a.f64 ? abs_bits(1.0) : abs_bits(1.0f);
     }
   }
-  // ---- the nodes, in post-order: tables, barrier, outputs, barrier
-  for (int ni = 0; ni < a.n_nodes; ++ni) {
-    const SNode &nd = nodes[ni];
-    // only the entries the node reads: output bits 0-7 (2^min(8, rC)),
-    // 8-15 (2^(rC - 8)), summed bits (2^k), for A and for B
-    {
-      const int rc = nd.rC, n0 = 1 << (rc < 8 ? rc : 8), n1 = 1 << (rc > 8 ? rc - 8 : 0), ns = 1 << nd.k;
-      const int total = 2 * (n0 + n1 + ns);
-      for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int op = i & 1, k = i >> 1;  // op 0: A, 1: B
-        int row, v, base, nb;
-        const int8_t *pos;
-        if (k < n0) { row = 2 * op; v = k; base = 0; nb = rc < 8 ? rc : 8; pos = op ? nd.posB : nd.posA; }
-        else if (k < n0 + n1) { row = 2 * op + 1; v = k - n0; base = 8; nb = rc - 8; pos = op ? nd.posB : nd.posA; }
-        else { row = 4 + op; v = k - n0 - n1; base = 0; nb = nd.k; pos = op ? nd.sposB : nd.sposA; }
-        uint32_t o = 0;
-        for (int b = 0; b < nb; ++b)
-          if (((v >> b) & 1) && pos[base + b] >= 0) o |= 1u << pos[base + b];
-        lut[row][v] = o;
+  // ---- the nodes, level by level
+  uint32_t *luts = (uint32_t *)(cta_smem + a.lut_off);
+  for (int f0 = 0; f0 < a.n_nodes;) {
+    const int f1 = nodes[f0].level_end;
+    const SNode &last = nodes[f1 - 1];
+    const int n_words = last.lut_base + 2 * ((1 << (last.rC < 8 ? last.rC : 8)) +
+                                             (1 << (last.rC > 8 ? last.rC - 8 : 0)) + (1 << last.k));
+    const uint32_t n_out = (uint32_t)last.out_base + (1u << last.rC);
+    // __syncthreads() before: the previous level's outputs, max and min (and the leaves)
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_words; i += blockDim.x) {
+      int lo = f0, hi = f1 - 1;  // the node whose tables hold word i
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nodes[mid].lut_base <= i) lo = mid; else hi = mid - 1;
       }
+      cta_table_entry(nodes[lo], luts + nodes[lo].lut_base, i - nodes[lo].lut_base);
     }
-    __syncthreads();  // tables; the previous node's outputs and metadata (and the leaves)
-    const bool root = ni == a.n_nodes - 1;
-    if (nd.ti == 1) cta_node<double, double, double>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
-    else if (nd.to == 1) cta_node<float, double, double>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
-    else cta_node<float, float, float>(a, nd, arena, mexp, mmax, mmin, lut, smax, smin, root);
-    __syncthreads();  // outputs, max and min
-    if ((int)threadIdx.x < nd.Qc) {
-      mmax[nd.mc + threadIdx.x] = smax[threadIdx.x];
-      mmin[nd.mc + threadIdx.x] = smin[threadIdx.x];
-      smax[threadIdx.x] = 0;
-      smin[threadIdx.x] = kNoMin;
+    for (int i = threadIdx.x; i < 4 * (f1 - f0); i += blockDim.x) {
+      const SNode &nd = nodes[f0 + (i >> 2)];
+      const int q = i & 3;
+      if (q >= nd.Qc) continue;
+      const bool root = f0 + (i >> 2) == a.n_nodes - 1;
+      if (nd.ti == 1) cta_node_meta<double>(a, nd, q, mexp, mmax, mmin, root);
+      else cta_node_meta<float>(a, nd, q, mexp, mmax, mmin, root);
     }
+    __syncthreads();  // tables
+    for (uint32_t g = threadIdx.x; g < n_out; g += blockDim.x) {
+      int lo = f0, hi = f1 - 1;  // the node of output g
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)nodes[mid].out_base <= g) lo = mid; else hi = mid - 1;
+      }
+      const SNode &nd = nodes[lo];
+      const uint32_t o = g - (uint32_t)nd.out_base;
+      const bool root = lo == a.n_nodes - 1;
+      const uint32_t *T = luts + nd.lut_base;
+      if (nd.ti == 1) cta_output<double, double, double>(a, nd, o, arena, mmax, mmin, T, root);
+      else if (nd.to == 1) cta_output<float, double, double>(a, nd, o, arena, mmax, mmin, T, root);
+      else cta_output<float, float, float>(a, nd, o, arena, mmax, mmin, T, root);
+    }
+    f0 = f1;
   }
 }
 

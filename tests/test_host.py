@@ -221,6 +221,27 @@ def test_bounds_check_of_every_launch(Q):
             assert n.value > 0
 
 
+@pytest.mark.parametrize("Q", [1, 2, 4])
+def test_bounds_check_of_one_block_walks(Q):
+    """The one-block walk's level layout on the CPU: levels partition the
+    node list, each level's lookup tables and outputs sit back to back in
+    their shared-memory region, and every node's operands and output stay
+    inside their arena tensors (children are freed only after their whole
+    level)."""
+    import ctypes
+    w = _lib()
+    try:
+        w.wmc_set_cta_walk(1)
+        for seed in range(6):
+            for precision in (0, 1):
+                plan = w.Plan(w.Network.from_cnf(wmcgen.random_kcnf(20, 60, seed)), precision=precision)
+                n = ctypes.c_int64()
+                assert w.wmc_debug_check_bounds(plan.handle, Q, ctypes.byref(n)) == 0, w.wmc_last_error()
+                assert n.value > 0
+    finally:
+        w.wmc_set_cta_walk(0)
+
+
 def test_slicing_plan_meets_its_target():
     """Index slicing (Alg. 3): the planner fixes variables until the largest
     tensor fits the target; the sliced variables are distinct, appear in no
