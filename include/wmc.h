@@ -534,12 +534,14 @@ void wmc_set_small_phase(int32_t on);
 /* Execution option (default off): a formula whose every node has at most
  * 2^16 outputs (with the query bits) and 2^8 summed terms, with at most 4
  * query lanes, and whose live tensors fit in 200 KB, runs its whole walk in
- * one thread block: leaves and intermediates in shared memory, the nodes in
- * post-order with a block barrier between them (no launch per node and no
- * dependency waits through global memory).  Results are the same bits as
- * the small-node phase.  Measured slower than the small-node phase on the
- * random 3-CNF n = 20 walks (one SM issues every node's instructions), so
- * it is off by default.  Affects plans laid out after the call. */
+ * one thread block: leaves and intermediates in shared memory, the nodes
+ * level by level (each node at the latest level below its parent; a level's
+ * nodes are independent, so each level is one phase between block
+ * barriers), with no launch per node and no dependency waits through
+ * global memory.  Results are the same bits as the small-node phase.
+ * Measured level with the small-node phase on the random 3-CNF n = 20
+ * walks (in FP64 one SM's FP64 rate bounds it), so it is off by default.
+ * Affects plans laid out after the call. */
 void wmc_set_cta_walk(int32_t on);
 /* Execution option (default on): chain kernels are launched as programmatic
  * dependent launches, so that each one's set-up overlaps the tail of the

@@ -914,9 +914,9 @@ def test_small_phase_matches_per_node_launches(w, precision, case):
 @pytest.mark.parametrize("Q,seed", [(1, 1), (1, 5), (2, 2), (1, 6)])
 def test_cta_walk_matches_small_phase(w, precision, Q, seed):
     """A small formula's whole walk in one block (leaves and intermediates in
-    shared memory, nodes in post-order with block barriers) gives the bits
-    of the small-node phase and the oracle's value, in a handful of
-    launches."""
+    shared memory, the nodes level by level between block barriers) gives
+    the bits of the small-node phase and the oracle's value, in a handful
+    of launches."""
     cnf = wmcgen.random_kcnf(20, 60, seed=seed)
     wq, wnq = wmcgen.query_weights(20, Q, seed=30 + seed, lo=0.1, hi=0.9)
     ref_plan = plan_for(w, cnf, None, None, precision)
