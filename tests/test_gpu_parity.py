@@ -124,6 +124,47 @@ def test_query_batch_matches_oracle_and_is_batch_invariant(w, precision):
         assert rel(alone[i], want) <= TOL[precision]
 
 
+def _fuzz_cases():
+    """Seeded mix of formula families, widths and batch sizes: random
+    k-CNF (k = 2..5, clause ratios around each k's hard region), small
+    grids and the psi family, with odd query counts (padded lanes)."""
+    rng = np.random.default_rng(2006)
+    cases = []
+    for i in range(16):
+        fam = ("kcnf", "kcnf", "kcnf", "grid", "psi")[i % 5]
+        if fam == "kcnf":
+            k = int(rng.integers(2, 6))
+            n = int(rng.integers(10, 33))
+            ratio = {2: 1.0, 3: 3.2, 4: 7.0, 5: 14.0}[k] * float(rng.uniform(0.6, 1.1))
+            cnf = wmcgen.random_kcnf(n, max(1, int(ratio * n)), seed=100 + i, k=k)
+        elif fam == "grid":
+            cnf = wmcgen.grid_cnf(int(rng.integers(3, 9)), int(rng.integers(4, 30)), seed=100 + i)
+        else:
+            cnf = wmcgen.psi_family(int(rng.integers(4, 18)))
+        cases.append((i, cnf, int((1, 5, 33)[i % 3])))
+    return cases
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+@pytest.mark.parametrize("case", range(16))
+def test_walk_fuzz_against_the_oracle(w, precision, case):
+    """Default walk layout on a seeded mix of families and batch sizes:
+    every sampled query within the tolerance of the oracle's bucket
+    elimination and within the result's stated bound, and each query's
+    bits the same alone as in its batch."""
+    i, cnf, Q = _fuzz_cases()[case]
+    wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=200 + i, lo=0.05, hi=0.95)
+    plan = plan_for(w, cnf, None, None, precision)
+    got = plan.execute(wq, wnq)
+    for q in sorted({0, Q // 2, Q - 1}):
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q])
+        r = rel(got[q], want)
+        assert r <= TOL[precision], (q, r)
+        assert r <= got[q].rel_err_bound + 1e-16, (q, r)
+        alone = plan.execute(wq[q:q + 1], wnq[q:q + 1])[0]
+        assert (alone.mant, alone.exp2) == (got[q].mant, got[q].exp2), q
+
+
 def test_evidence_zero_weight(w):
     """Evidence as a zero weight equals conditioning (Thm 4.2)."""
     cnf = wmcgen.random_kcnf(16, 40, seed=3)
