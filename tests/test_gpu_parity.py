@@ -150,12 +150,21 @@ def _fuzz_cases():
 def test_walk_fuzz_against_the_oracle(w, precision, case):
     """Default walk layout on a seeded mix of families and batch sizes:
     every sampled query within the tolerance of the oracle's bucket
-    elimination and within the result's stated bound, and each query's
-    bits the same alone as in its batch."""
+    elimination and within the result's stated bound, each query's bits
+    the same alone as in its batch, and the same bits with one pass per
+    contraction and with runs of six frontier eliminations."""
     i, cnf, Q = _fuzz_cases()[case]
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=200 + i, lo=0.05, hi=0.95)
     plan = plan_for(w, cnf, None, None, precision)
     got = plan.execute(wq, wnq)
+    try:
+        for fuse in (0, 6):
+            w.wmc_set_fusion(fuse)
+            other = plan_for(w, cnf, None, None, precision).execute(wq, wnq)
+            for q in range(Q):
+                assert (other[q].mant, other[q].exp2) == (got[q].mant, got[q].exp2), (fuse, q)
+    finally:
+        w.wmc_set_fusion(-1)
     for q in sorted({0, Q // 2, Q - 1}):
         want = oracle.bucket_elim(cnf, wq[q], wnq[q])
         r = rel(got[q], want)
