@@ -142,18 +142,23 @@ def _fuzz_cases():
         else:
             cnf = wmcgen.psi_family(int(rng.integers(4, 18)))
         cases.append((i, cnf, int((1, 5, 33)[i % 3])))
-    return cases
+    # taller grids: frontiers past the small-node phase, so the walk runs
+    # streaming passes and chains of frontier eliminations
+    # (the oracle eliminates these column by column)
+    for j, (h, wd, Q) in enumerate(((12, 24, 1), (14, 30, 3), (16, 22, 17), (18, 20, 2))):
+        cases.append((16 + j, wmcgen.grid_cnf(h, wd, seed=300 + j), Q, wmcgen.grid_column_order(h, wd)))
+    return [c if len(c) == 4 else c + (None,) for c in cases]
 
 
 @pytest.mark.parametrize("precision", [FP64, FP32])
-@pytest.mark.parametrize("case", range(16))
+@pytest.mark.parametrize("case", range(20))
 def test_walk_fuzz_against_the_oracle(w, precision, case):
     """Default walk layout on a seeded mix of families and batch sizes:
     every sampled query within the tolerance of the oracle's bucket
     elimination and within the result's stated bound, each query's bits
     the same alone as in its batch, and the same bits with one pass per
     contraction and with runs of six frontier eliminations."""
-    i, cnf, Q = _fuzz_cases()[case]
+    i, cnf, Q, order = _fuzz_cases()[case]
     wq, wnq = wmcgen.query_weights(cnf.n_vars, Q, seed=200 + i, lo=0.05, hi=0.95)
     plan = plan_for(w, cnf, None, None, precision)
     got = plan.execute(wq, wnq)
@@ -166,7 +171,7 @@ def test_walk_fuzz_against_the_oracle(w, precision, case):
     finally:
         w.wmc_set_fusion(-1)
     for q in sorted({0, Q // 2, Q - 1}):
-        want = oracle.bucket_elim(cnf, wq[q], wnq[q])
+        want = oracle.bucket_elim(cnf, wq[q], wnq[q], order=order)
         r = rel(got[q], want)
         assert r <= TOL[precision], (q, r)
         assert r <= got[q].rel_err_bound + 1e-16, (q, r)
