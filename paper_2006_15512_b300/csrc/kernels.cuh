@@ -3044,9 +3044,9 @@ __global__ void k_weight_leaves(const IoDesc *io, int32_t n_vars, int32_t Q, int
 // A formula whose whole tree is small (every node at most 2^16 outputs
 // with the query bits and 2^8 summed terms) and whose live tensors fit in
 // one block's shared memory runs as ONE block: the leaves are materialised
-// in shared memory, then the nodes run one after the other in post-order
-// with a block barrier between them -- no launches, no dependency waits
-// through global memory, no L2 round trips on the walk's critical path.
+// in shared memory, then the nodes run level by level with block barriers
+// between the levels -- no launches, no dependency waits through global
+// memory, no L2 round trips on the walk's critical path.
 // Every node computes exactly what the small-node phase computes (the same
 // operand scales, terms in ascending summed order, the same max/min and
 // exponents), so the results are the same bits.  The root is written to
