@@ -112,6 +112,7 @@ struct Launch {
   wmc::dev::K2BParams k2b;
   wmc::dev::K2CParams k2c;
   int chain_d = 0, chain_fast = 0, chain_grow = 0, chain_shrink = 0;
+  int threads = 0;  // block size of a direct-load chain (0: kDirectThreads)
   int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};  // chain: S_1..S_D
   int64_t off_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
   int64_t meta_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
@@ -1213,8 +1214,19 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
       const int per_sm = std::max<int>(1, std::min<int>(2, (int)((227u * 1024u) / (f.smem + 2048))));
       if (d_ok > 4) {  // direct loads: one unit per thread at a time, grid-stride
         const uint64_t units = 1ull << f.k2c.log2_nu;
-        const uint64_t need = (units + wmc::dev::kDirectThreads - 1) / wmc::dev::kDirectThreads;
-        const uint64_t resident = 148ull * (uint64_t)(f.v == 1 ? per_sm : 1);  // (launch bounds)
+        // fewer units than one full block per SM (small walks, launch
+        // bound): smaller blocks spread them over more SMs, so that each
+        // warp has a scheduler to itself (at least 32 lanes per block, a
+        // multiple of the lane count), while every block's copy of the
+        // staged S_i stays at most 4 entries per thread
+        int threads = wmc::dev::kDirectThreads;
+        const uint64_t s_words = f.k2c.s_copy_bytes / 4;
+        while (threads > 32 && (uint64_t)threads * 148ull > units && s_words <= (uint64_t)(threads / 2) * 4 &&
+               ((threads / 2) * f.v) % std::max<int>(1, f.k2c.mc.Qc) == 0)
+          threads /= 2;
+        f.threads = threads;
+        const uint64_t need = (units + (uint64_t)threads - 1) / (uint64_t)threads;
+        const uint64_t resident = 148ull * (uint64_t)(f.v == 1 ? per_sm : 1) * (uint64_t)(wmc::dev::kDirectThreads / threads);
         f.blocks = (int64_t)std::max<uint64_t>(1, std::min<uint64_t>(need, resident));
       } else {
         const uint64_t n_tiles = 1ull << (f.k2c.log2_nu + f.k2c.vbits - f.k2c.tb);
@@ -1701,7 +1713,7 @@ static void launch_k2c_direct(const Launch &l, const wmc::dev::K2CParams &p, cud
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)l.blocks);
-  cfg.blockDim = dim3(dev::kDirectThreads);
+  cfg.blockDim = dim3(l.threads > 0 ? (unsigned)l.threads : (unsigned)dev::kDirectThreads);
   cfg.dynamicSmemBytes = l.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -3454,7 +3466,9 @@ extern "C" int wmc_debug_check_bounds(wmc_plan_t *plan, int32_t Q, int64_t *n_ch
             return badc("staged S", i, D);
         const size_t need = cp.s_bytes_off[D] + 16 * (size_t)cp.mc.Qc;
         if (V > 2 || l.chain_grow || need > l.smem || l.smem > 220 * 1024 ||
-            ((uint64_t)l.blocks * wmc::dev::kDirectThreads * (uint64_t)V) % (uint64_t)cp.mc.Qc)
+            (l.threads != 0 && (l.threads < 32 || l.threads > wmc::dev::kDirectThreads || l.threads % 32)) ||
+            ((uint64_t)l.blocks * (uint64_t)(l.threads ? l.threads : wmc::dev::kDirectThreads) * (uint64_t)V) %
+                (uint64_t)cp.mc.Qc)
           return badc("direct chain launch", (int64_t)need, (int64_t)l.smem);
         continue;
       }
