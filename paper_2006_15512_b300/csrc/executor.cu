@@ -1218,10 +1218,10 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
         // bound): smaller blocks spread them over more SMs, so that each
         // warp has a scheduler to itself (at least 32 lanes per block, a
         // multiple of the lane count), while every block's copy of the
-        // staged S_i stays at most 4 entries per thread
+        // staged S_i stays at most 8 entries per thread
         int threads = wmc::dev::kDirectThreads;
         const uint64_t s_words = f.k2c.s_copy_bytes / 4;
-        while (threads > 32 && (uint64_t)threads * 148ull > units && s_words <= (uint64_t)(threads / 2) * 4 &&
+        while (threads > 32 && (uint64_t)threads * 148ull > units && s_words <= (uint64_t)(threads / 2) * 8 &&
                ((threads / 2) * f.v) % std::max<int>(1, f.k2c.mc.Qc) == 0)
           threads /= 2;
         f.threads = threads;
