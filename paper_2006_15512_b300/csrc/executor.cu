@@ -39,6 +39,7 @@ static std::atomic<int32_t> g_debug_stall{0};
 static std::atomic<int32_t> g_fuse{-1};  // -1: by the walk's lane count
 static std::atomic<int32_t> g_small_phase{1};  // small nodes in one persistent launch
 static std::atomic<int32_t> g_pdl{1};  // programmatic dependent launch of chain kernels
+static thread_local bool t_chain_pdl = true;  // the chain being launched may overlap the launch in front
 static std::atomic<int32_t> g_tensor_cores{1};  // dense float32 pair contractions on tcgen05
 static std::atomic<int32_t> g_fp64_fallback{1};  // flushed float32 queries run again in float64
 // runs of consecutive chains whose every chain has at most this many tiles
@@ -113,6 +114,7 @@ struct Launch {
   wmc::dev::K2CParams k2c;
   int chain_d = 0, chain_fast = 0, chain_grow = 0, chain_shrink = 0;
   int threads = 0;  // block size of a direct-load chain (0: kDirectThreads)
+  int no_pdl = 0;   // chain launched in plain stream order (its launch before writes an S_i)
   int64_t id_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};  // chain: S_1..S_D
   int64_t off_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
   int64_t meta_sc[wmc::dev::kMaxChain] = {-1, -1, -1, -1, -1, -1};
@@ -1478,6 +1480,26 @@ static int build_exec(Plan &plan, int32_t Q, ExecState &st, bool plain = false, 
   fin.off_c = st.t_off[(size_t)root];
   fin.meta_c = st.t_meta[(size_t)root];
   fin.blocks = grid_for((uint64_t)Q);
+  // A chain copies its S_i before it waits for the launch in front of it
+  // (programmatic dependent launch): that is safe when the launch in front
+  // is another chain (it writes only its C, this chain's P, read after the
+  // wait) or a single node whose output is no S_i; otherwise the chain
+  // starts in plain stream order.
+  for (size_t i = 0; i < st.launches.size(); ++i) {
+    Launch &l = st.launches[i];
+    if (l.kind != L_K2C) continue;
+    bool safe = false;
+    if (i > 0) {
+      const Launch &pv = st.launches[i - 1];
+      if (pv.kind == L_K2C) {
+        safe = true;
+      } else if (pv.kind == L_K1 || pv.kind == L_K2 || pv.kind == L_K2T || pv.kind == L_K4 || pv.kind == L_K2B) {
+        safe = true;
+        for (int j = 0; j < l.chain_d; ++j) safe &= pv.id_c != l.id_sc[j];
+      }
+    }
+    l.no_pdl = safe ? 0 : 1;
+  }
   st.launches.push_back(fin);
   if (cta) {
     // the whole walk in one block: the metadata clears, the walk, the root
@@ -1671,7 +1693,7 @@ static void launch_k2c_t(const wmc::dev::K2CParams &p, int64_t blocks, size_t sm
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed = (g_pdl.load() && t_chain_pdl) ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, dev::k2_chain<T, V, D, FAST, BC, GROW, SHRINK>, p);
@@ -1718,7 +1740,7 @@ static void launch_k2c_direct(const Launch &l, const wmc::dev::K2CParams &p, cud
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load() ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed = (g_pdl.load() && t_chain_pdl) ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, dev::k2_chain_direct<float, V, D, SHRINK>, p);
@@ -1909,6 +1931,7 @@ static void enqueue_walk(Plan &plan, ExecState &st, char *ws, cudaStream_t s,
         cp.mc.exp = mexp + l.meta_c; cp.mc.maxb = mmax + l.meta_c; cp.mc.minb = mmin + l.meta_c;
         cp.mc.flags = flags;
         cp.err = (uint32_t *)(ws + st.off_err);
+        t_chain_pdl = l.no_pdl == 0;
         // (the test hook stalls a staged copy: direct-load chains have none)
         cp.debug_stall = (stall_armed && l.chain_d <= 4) ? 1 : 0;
         if (l.chain_d <= 4) stall_armed = false;
